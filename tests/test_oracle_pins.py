@@ -1,0 +1,375 @@
+"""Pins of the FP64 oracle against mathematics and the paper (no GPU).
+
+Each test checks the oracle against something other than itself: a closed
+form, a conservation law, a brute-force recomputation with a different
+algorithm, a textbook value, or central finite differences.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2605_13794_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _scene(n, seed, opacity_max=None, depth=(2.0, 6.0), scale=(1e-3, 5e-2)):
+    rng = np.random.default_rng(seed)
+    g = synth.plain_scene(n, seed)
+    g.mean[2] = rng.uniform(*depth, n).astype(np.float32)
+    g.log_scale[:] = rng.uniform(math.log(scale[0]), math.log(scale[1]), (3, n)).astype(np.float32)
+    if opacity_max is not None:
+        o = rng.uniform(0.05, opacity_max, n)
+        g.opacity_logit[:] = np.log(o / (1 - o)).astype(np.float32)
+    return g
+
+
+# ---- spherical harmonics ------------------------------------------------
+
+def test_sh_orthonormal_by_quadrature(oracle_mod):
+    # Gauss-Legendre in cos(theta) x uniform in phi integrates degree <= 6 exactly
+    z, wz = np.polynomial.legendre.leggauss(12)
+    nphi = 16
+    phi = (np.arange(nphi) + 0.5) * 2 * np.pi / nphi
+    Z, PHI = np.meshgrid(z, phi, indexing="ij")
+    S = np.sqrt(1 - Z ** 2)
+    dirs = np.stack([S * np.cos(PHI), S * np.sin(PHI), Z], -1).reshape(-1, 3)
+    w = (wz[:, None] * np.full(nphi, 2 * np.pi / nphi)[None, :]).reshape(-1)
+    Y = oracle_mod.sh_basis(dirs)
+    gram = (Y * w[:, None]).T @ Y
+    assert np.abs(gram - np.eye(16)).max() < 1e-12
+
+
+def test_sh_addition_theorem(oracle_mod):
+    # Unsold: sum_m Y_lm(d)^2 = (2l+1)/(4 pi) for every unit d
+    rng = np.random.default_rng(5)
+    d = rng.standard_normal((200, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    Y = oracle_mod.sh_basis(d)
+    for l in range(4):
+        band = (Y[:, l * l:(l + 1) ** 2] ** 2).sum(1)
+        assert np.allclose(band, (2 * l + 1) / (4 * np.pi), atol=1e-13)
+
+
+def test_sh_textbook_values(oracle_mod):
+    cases = json.load(open(os.path.join(GOLDEN, "sh_values.json")))["cases"]
+    for c in cases:
+        Y = oracle_mod.sh_basis(np.array(c["dir"], float))
+        assert abs(Y[0, c["k"]] - c["value"]) < 1e-12, c
+
+
+def test_sh_gradient_fd(oracle_mod):
+    rng = np.random.default_rng(6)
+    d = rng.standard_normal((20, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    _, dY = oracle_mod.sh_basis(d, with_grad=True)
+    h = 1e-6
+    for e in range(3):
+        dp, dm = d.copy(), d.copy()
+        dp[:, e] += h
+        dm[:, e] -= h
+        fd = (oracle_mod.sh_basis(dp) - oracle_mod.sh_basis(dm)) / (2 * h)
+        assert np.abs(fd - dY[:, :, e]).max() < 1e-8
+
+
+# ---- projection -----------------------------------------------------------
+
+def _one(mean, log_s, quat, opac_logit, sh_dc=(0.0, 0.0, 0.0)):
+    g = synth.GaussianSet(
+        mean=np.array(mean, np.float32).reshape(3, 1), log_scale=np.array(log_s, np.float32).reshape(3, 1),
+        quat=np.array(quat, np.float32).reshape(4, 1), opacity_logit=np.array([opac_logit], np.float32),
+        sh=np.zeros((16, 3, 1), np.float32), lod=np.zeros(1, np.uint8))
+    g.sh[0, :, 0] = np.array(sh_dc, np.float32)
+    return g
+
+
+@pytest.mark.parametrize("sigma,z", [(0.01, 3.0), (0.03, 2.5), (0.002, 5.0)])
+def test_isotropic_on_axis_closed_form(oracle_mod, sigma, z):
+    cam = synth.plain_camera(64, 64, 300.0)
+    P = oracle_mod.Params()
+    rng = np.random.default_rng(7)
+    q = rng.standard_normal(4)
+    dc = 0.3
+    g = _one([0.0, 0.0, z], [math.log(sigma)] * 3, q, 0.8, (dc, dc, dc))
+    g64 = oracle_mod.gaussians64(g)
+    pr = oracle_mod.project(g64, cam, P)
+    f = float(np.float32(300.0))
+    dil = float(np.float32(0.3))
+    s_stored = math.exp(float(np.float32(math.log(sigma))))  # the scale the stored log-scale encodes
+    s2 = (f * s_stored / z) ** 2 + dil
+    # conic of (s2) I, and the extent uses max(0.1, mid^2 - det) = 0.1 for a disc
+    assert pr["status"][0] == oracle_mod.ACTIVE
+    assert np.allclose(pr["conic"][0], [1 / s2, 0.0, 1 / s2], rtol=1e-12, atol=1e-12)
+    assert pr["radius"][0] == math.ceil(3 * math.sqrt(s2 + math.sqrt(0.1)))
+    assert np.allclose(pr["uv"][0], [32.0, 32.0])
+    # image: alpha(rho) c at every pixel, zero below alpha_min, one Gaussian never stops early
+    fwd = oracle_mod.forward_view(g64, cam, P)
+    o = 1 / (1 + math.exp(-float(np.float32(0.8))))
+    c = float(np.float32(dc)) * 0.28209479177387814 + 0.5
+    ys, xs = np.mgrid[0:64, 0:64] + 0.5
+    rho2 = (xs - 32.0) ** 2 + (ys - 32.0) ** 2
+    alpha = np.minimum(float(np.float32(0.99)), o * np.exp(-0.5 * rho2 / s2))
+    alpha[alpha < float(np.float32(1 / 255))] = 0.0
+    r = pr["radius"][0]
+    # pixels whose tile lies outside the footprint rectangle receive nothing
+    rect = pr["rect"][0]
+    tx, ty = (xs // 16).astype(int), (ys // 16).astype(int)
+    inside = (tx >= rect[0]) & (tx < rect[2]) & (ty >= rect[1]) & (ty < rect[3])
+    alpha[~inside] = 0.0
+    assert r > 0
+    np.testing.assert_allclose(fwd["image"][0], alpha * c, atol=1e-12)
+    np.testing.assert_allclose(fwd["T"], 1 - alpha, atol=1e-12)
+    # importance of the single Gaussian: w = sum alpha T (T = 1), a = pixels with alpha >= alpha_min
+    assert abs(fwd["w"][0] - alpha.sum()) < 1e-10
+    assert fwd["a"][0] == np.count_nonzero(alpha)
+
+
+def test_lod_gate_table(oracle_mod):
+    gold = json.load(open(os.path.join(GOLDEN, "lod_gate.json")))
+    cam = synth.plain_camera(64, 64, 300.0)
+    P = oracle_mod.Params(lod_enable=True, lod_d0=gold["d0"], lod_f=gold["f"], lod_Lmax=gold["Lmax"])
+    for d, L in gold["cases"]:
+        for lod in range(7):
+            g = _one([0.0, 0.0, d], [0.0] * 3, [1, 0, 0, 0], 0.0)
+            g.lod[0] = lod
+            pr = oracle_mod.project(oracle_mod.gaussians64(g), cam, P)
+            gated = pr["status"][0] == oracle_mod.GATED_LOD
+            assert gated == (lod > L), (d, lod, L)
+
+
+def test_near_plane_and_cull_mask(oracle_mod):
+    cam = synth.plain_camera(64, 64, 300.0)
+    P = oracle_mod.Params(cull_enable=True)
+    g = _one([0.0, 0.0, 0.1], [math.log(0.01)] * 3, [1, 0, 0, 0], 0.0)
+    assert oracle_mod.project(oracle_mod.gaussians64(g), cam, P)["status"][0] == oracle_mod.NEAR
+    g = _one([0.0, 0.0, 3.0], [math.log(0.01)] * 3, [1, 0, 0, 0], 0.0)
+    pr = oracle_mod.project(oracle_mod.gaussians64(g), cam, P, cull=np.array([1], np.uint32))
+    assert pr["status"][0] == oracle_mod.GATED_CULL
+    pr = oracle_mod.project(oracle_mod.gaussians64(g), cam, P, cull=np.array([0], np.uint32))
+    assert pr["status"][0] == oracle_mod.ACTIVE
+
+
+# ---- compositing --------------------------------------------------------
+
+def test_two_gaussians_by_hand(oracle_mod):
+    # two tiny Gaussians centred on the same pixel centre; the nearer composites first
+    cam = synth.plain_camera(16, 16, 300.0)
+    cam.cx = cam.cy = 8.5  # pixel (8, 8) centre on the optical axis
+    P = oracle_mod.Params()
+    ls = math.log(1e-4)
+    g = _one([0.0, 0.0, 3.0], [ls] * 3, [1, 0, 0, 0], math.log(0.6 / 0.4), (1.0, 0.0, 0.0))
+    g2 = _one([0.0, 0.0, 2.0], [ls] * 3, [1, 0, 0, 0], math.log(0.5 / 0.5), (0.0, 1.0, 0.0))
+    both = synth.GaussianSet(*[np.concatenate([getattr(g, k), getattr(g2, k)], axis=-1)
+                               for k in ("mean", "log_scale", "quat", "opacity_logit", "sh", "lod")])
+    fwd = oracle_mod.forward_view(oracle_mod.gaussians64(both), cam, P)
+    C0 = 0.28209479177387814
+    o1 = 1 / (1 + math.exp(-float(np.float32(math.log(0.6 / 0.4)))))
+    o2 = 0.5
+    c1 = np.array([C0 + 0.5, 0.5, 0.5])
+    c2 = np.array([0.5, C0 + 0.5, 0.5])
+    # at the centre the dilated footprint peaks at exp(0) = 1, so alpha = opacity
+    expect = o2 * c2 + (1 - o2) * o1 * c1
+    np.testing.assert_allclose(fwd["image"][:, 8, 8], expect, atol=1e-12)
+    assert abs(fwd["T"][8, 8] - (1 - o1) * (1 - o2)) < 1e-12
+    assert fwd["n_contrib"][8, 8] == 2
+    # tile list order: Gaussian 1 (nearer) before Gaussian 0
+    ts, lst = fwd["bins"]
+    assert list(lst[ts[0]:ts[1]]) == [1, 0]
+
+
+def test_equal_depth_ties_by_index(oracle_mod):
+    cam = synth.plain_camera(16, 16, 300.0)
+    P = oracle_mod.Params()
+    g = synth.plain_scene(6, 11)
+    g.mean[:] = np.array([[0.0], [0.0], [3.0]], np.float32)
+    g.log_scale[:] = np.float32(math.log(0.01))
+    fwd = oracle_mod.forward_view(oracle_mod.gaussians64(g), cam, P)
+    ts, lst = fwd["bins"]
+    assert list(lst[ts[0]:ts[1]]) == sorted(lst[ts[0]:ts[1]])
+
+
+def test_transmittance_invariant(oracle_mod):
+    # all colours 1 and bg 0: C(p) = sum alpha_i T_i = 1 - T_final (telescoping product)
+    g = synth.plain_scene(3000, 21)
+    g.sh[:] = 0.0
+    g.sh[0] = np.float32(0.5 / 0.28209479177387814)
+    cam = synth.plain_camera(96, 80, 200.0)
+    P = oracle_mod.Params()
+    fwd = oracle_mod.forward_view(oracle_mod.gaussians64(g), cam, P)
+    assert fwd["T"].min() < 0.01  # the test covers saturated pixels
+    for c in range(3):
+        np.testing.assert_allclose(fwd["image"][c], 1.0 - fwd["T"], atol=1e-6)
+    # importance: sum_i w_i = sum_p (1 - T_final)
+    assert abs(fwd["w"].sum() - (1 - fwd["T"]).sum()) < 1e-8 * fwd["T"].size
+
+
+def test_bg_colour_enters_through_final_transmittance(oracle_mod):
+    g = synth.plain_scene(2000, 22)
+    cam = synth.plain_camera(64, 64, 200.0)
+    P0 = oracle_mod.Params()
+    P1 = oracle_mod.Params(bg=(0.25, 0.5, 1.0))
+    g64 = oracle_mod.gaussians64(g)
+    f0 = oracle_mod.forward_view(g64, cam, P0)
+    f1 = oracle_mod.forward_view(g64, cam, P1)
+    bg = np.array([np.float32(0.25), np.float32(0.5), np.float32(1.0)], float)
+    np.testing.assert_allclose(f1["image"], f0["image"] + bg[:, None, None] * f0["T"][None], atol=1e-12)
+
+
+def test_tiled_equals_untiled_brute_force(oracle_mod):
+    # With opacity below alpha_min * e^{4.5} = 0.35 every fragment outside a
+    # Gaussian's 3-sigma rectangle has alpha < alpha_min, so compositing all
+    # Gaussians at every pixel (no tiles, no rectangles) must give the same image.
+    g = _scene(1500, 23, opacity_max=0.34)
+    cam = synth.plain_camera(80, 64, 250.0)
+    P = oracle_mod.Params()
+    g64 = oracle_mod.gaussians64(g)
+    fwd = oracle_mod.forward_view(g64, cam, P)
+    img, T = oracle_mod.render_brute(fwd["proj"], cam, P)
+    assert np.array_equal(img, fwd["image"])
+    assert np.array_equal(T, fwd["T"])
+
+
+def test_binning_brute_force(oracle_mod):
+    g = synth.plain_scene(800, 24)
+    cam = synth.plain_camera(100, 70, 250.0)
+    P = oracle_mod.Params()
+    pr = oracle_mod.project(oracle_mod.gaussians64(g), cam, P)
+    ts, lst = oracle_mod.bin_tiles(pr, cam, P)
+    tx, ty = oracle_mod.tiles_of(cam, P)
+    for t in range(tx * ty):
+        x, y = t % tx, t // tx
+        members = [i for i in range(g.n) if pr["status"][i] == oracle_mod.ACTIVE and
+                   pr["rect"][i, 0] <= x < pr["rect"][i, 2] and pr["rect"][i, 1] <= y < pr["rect"][i, 3]]
+        members.sort(key=lambda i: (pr["depth32"][i].view(np.uint32), i))
+        assert list(lst[ts[t]:ts[t + 1]]) == members
+
+
+# ---- backward: central finite differences of the FP64 forward -------------
+
+def _loss_and_state(oracle_mod, g64, cam, P, dL):
+    f = oracle_mod.forward_view(g64, cam, P)
+    state = (f["proj"]["status"].tobytes(), f["proj"]["rect"].tobytes(), f["n_contrib"].tobytes(),
+             f["proj"]["clamp"].tobytes())
+    return float((f["image"] * dL).sum()), state, f
+
+
+@pytest.mark.parametrize("seed", [31, 32])
+def test_backward_matches_central_differences(oracle_mod, seed):
+    rng = np.random.default_rng(seed)
+    g = _scene(14, seed, opacity_max=0.9, depth=(2.0, 3.0), scale=(0.01, 0.04))
+    g.mean[0] = rng.uniform(-0.25, 0.25, g.n).astype(np.float32)
+    g.mean[1] = rng.uniform(-0.25, 0.25, g.n).astype(np.float32)
+    cam = synth.plain_camera(48, 40, 120.0)
+    P = oracle_mod.Params()
+    g64 = oracle_mod.gaussians64(g)
+    dL = rng.standard_normal((3, cam.height, cam.width))
+    L0, st0, f0 = _loss_and_state(oracle_mod, g64, cam, P, dL)
+    assert (f0["proj"]["status"] == oracle_mod.ACTIVE).all()
+    grads = oracle_mod.backward_view(g64, f0, cam, P, dL)
+    checked = 0
+    for name in ("mean", "log_scale", "quat", "opacity_logit", "sh"):
+        arr = g64[name]
+        flat = arr.reshape(-1)
+        gflat = grads[name].reshape(-1)
+        idx = range(flat.size) if name != "sh" else rng.choice(flat.size, 120, replace=False)
+        for k in idx:
+            x0 = flat[k]
+            h = 1e-6 * max(1.0, abs(x0))
+            flat[k] = x0 + h
+            Lp, stp, _ = _loss_and_state(oracle_mod, g64, cam, P, dL)
+            flat[k] = x0 - h
+            Lm, stm, _ = _loss_and_state(oracle_mod, g64, cam, P, dL)
+            flat[k] = x0
+            if stp != st0 or stm != st0:
+                continue  # a discrete decision moved: the derivative is not defined there
+            fd = (Lp - Lm) / (2 * h)
+            assert abs(fd - gflat[k]) <= 1e-5 * max(1.0, abs(fd)), (name, k, fd, gflat[k])
+            checked += 1
+    assert checked > 0.9 * (g.n * (3 + 3 + 4 + 1) + 120)
+
+
+# ---- importance selection -----------------------------------------------------
+
+def test_visible_set_is_minimal_by_exhaustion(oracle_mod):
+    rng = np.random.default_rng(41)
+    for trial in range(40):
+        n = 9
+        w = rng.choice([0.0, 0.5, 1.0, 2.0, rng.uniform(0, 3)], size=n) if trial % 2 else rng.uniform(0, 1, n)
+        total = w.sum()
+        vis = oracle_mod.visible_top_mass(w, 0.99)
+        if total == 0:
+            assert not vis.any()
+            continue
+        # smallest cardinality of any subset carrying 99 %
+        best = min(bin(m).count("1") for m in range(1 << n)
+                   if sum(w[i] for i in range(n) if m >> i & 1) >= 0.99 * total)
+        assert vis.sum() == best
+        assert w[vis].sum() >= 0.99 * total
+        # the chosen members are the largest w, ties resolved toward lower index
+        order = sorted(range(n), key=lambda i: (-w[i], i))
+        assert set(np.nonzero(vis)[0]) == set(order[:best])
+
+
+# ---- loss and optimizer -----------------------------------------------------------
+
+def test_ssim_identity_and_gradient(oracle_mod):
+    rng = np.random.default_rng(51)
+    x = rng.uniform(0, 1, (3, 20, 24))
+    s, gs = oracle_mod.ssim_and_grad(x, x)
+    assert abs(s - 1.0) < 1e-12 and np.abs(gs).max() < 1e-12
+    y = rng.uniform(0, 1, (3, 20, 24))
+    s, gs = oracle_mod.ssim_and_grad(x, y)
+    h = 1e-6
+    for _ in range(25):
+        idx = tuple(rng.integers(0, d) for d in x.shape)
+        xp, xm = x.copy(), x.copy()
+        xp[idx] += h
+        xm[idx] -= h
+        fd = (oracle_mod.ssim_and_grad(xp, y)[0] - oracle_mod.ssim_and_grad(xm, y)[0]) / (2 * h)
+        assert abs(fd - gs[idx]) < 1e-7
+
+
+def test_photometric_loss_gradient(oracle_mod):
+    rng = np.random.default_rng(52)
+    x = rng.uniform(0, 1, (2, 3, 16, 18))
+    y = rng.uniform(0, 1, (2, 3, 16, 18))
+    L, g = oracle_mod.photometric_loss(x, y)
+    L0, _ = oracle_mod.photometric_loss(y, y)
+    assert abs(L0) < 1e-12
+    h = 1e-6
+    for _ in range(20):
+        idx = tuple(rng.integers(0, d) for d in x.shape)
+        xp, xm = x.copy(), x.copy()
+        xp[idx] += h
+        xm[idx] -= h
+        fd = (oracle_mod.photometric_loss(xp, y)[0] - oracle_mod.photometric_loss(xm, y)[0]) / (2 * h)
+        assert abs(fd - g[idx]) < 1e-7
+
+
+def test_scale_regulariser(oracle_mod):
+    ls = np.log(np.array([[0.1, 0.5, 2.0], [0.2, 0.05, 3.0], [0.3, 0.6, 0.7]]))
+    vis = np.array([True, True, False])
+    val, g = oracle_mod.scale_regulariser(ls, vis, beta=10.0)
+    assert abs(val - 10.0 * (0.1 + 0.05) / 2) < 1e-12
+    h = 1e-7
+    for idx in np.ndindex(ls.shape):
+        lp, lm = ls.copy(), ls.copy()
+        lp[idx] += h
+        lm[idx] -= h
+        fd = (oracle_mod.scale_regulariser(lp, vis)[0] - oracle_mod.scale_regulariser(lm, vis)[0]) / (2 * h)
+        assert abs(fd - g[idx]) < 1e-6
+
+
+def test_adam_first_step_closed_form(oracle_mod):
+    rng = np.random.default_rng(53)
+    p = rng.standard_normal(100)
+    g = rng.standard_normal(100)
+    z = np.zeros(100)
+    p1, m1, v1 = oracle_mod.adam_step(p, g, z, z, step=1, lr=0.01, eps=1e-15)
+    # bias-corrected moments equal g and g^2 after one step
+    np.testing.assert_allclose(p1, p - 0.01 * g / (np.abs(g) + 1e-15), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(m1, 0.1 * g)
+    np.testing.assert_allclose(v1, 0.001 * g * g)
