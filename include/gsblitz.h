@@ -1,0 +1,236 @@
+/* gsblitz.h -- C ABI of the GB300 (sm_103a) 3D Gaussian Splatting hot path.
+ *
+ * Implements the per-iteration render of BlitzGS (arXiv 2605.13794) on one GPU:
+ *   gs_preprocess  view gate (Sec. 3.3, Eq. 1-3) + EWA projection and SH colour
+ *                  (App. A: "projected to screen-space ellipses", c_i(d) by SH)
+ *   gs_bin_sort    tile/depth keys and a device radix sort (App. A: tile-based,
+ *                  depth-ordered projected Gaussians)
+ *   gs_render_fwd  front-to-back alpha compositing (App. A, Eq. for C(p), T_i)
+ *   gs_render_bwd  its adjoint and the adjoint of the projection, plus the
+ *                  scale regulariser of Eq. 5
+ *   gs_importance  the instrumented colourless sweep of Sec. 3.2 / Fig. 2:
+ *                  w = sum_p alpha T, a = qualifying pixels, s, c^rad, c^vis, Cull
+ *   gs_photometric_loss  L1 + lambda (1 - SSIM) of Eq. 4
+ *   gs_adam_step   the optimizer step of "standard 3DGS" training
+ *
+ * Conventions for every call:
+ *   - Every pointer argument that names an array is a DEVICE pointer unless the
+ *     comment says "host".  Arrays are owned by the caller; the library never
+ *     frees or retains them beyond the call.
+ *   - Calls are asynchronous on the given stream and allocate nothing: all
+ *     scratch lives in a gs_workspace created once by gs_workspace_create.
+ *     A NULL stream means the legacy default stream.
+ *   - Every call returns a gs_status.  Argument errors are reported at once.
+ *     Errors found by kernels (capacity overflow, a bounded wait that gave up)
+ *     are recorded in the workspace's device error word and returned by the
+ *     next gs_sync_status / gs_workspace_counts call; the outputs of the
+ *     failing step are then undefined.  The library never aborts, exits or
+ *     traps.  gs_last_error() describes the last error of the calling thread.
+ *   - Floating point is FP32 throughout.
+ */
+#ifndef GSBLITZ_H
+#define GSBLITZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *gs_stream; /* same handle as cudaStream_t */
+typedef struct gs_workspace gs_workspace;
+
+#define GS_MAX_CAMERAS 64
+#define GS_TILE 16
+#define GS_MAX_ADAM_GROUPS 16
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = -1, /* bad argument (NULL, size, alignment) */
+    GS_ERR_OOM = -2,         /* workspace allocation failed */
+    GS_ERR_CAPACITY = -3,    /* a workspace capacity was exceeded; see gs_counts */
+    GS_ERR_CUDA = -4,        /* a CUDA runtime call failed */
+    GS_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+    GS_ERR_DEVICE = -6       /* other device-side error */
+} gs_status;
+
+/* Workspace capacities.  Records are active (Gaussian, camera) pairs after
+ * the view gate and culling; instances are (record, tile) pairs. */
+typedef struct {
+    int64_t max_gaussians;
+    int64_t max_records;
+    int64_t max_instances;
+    int64_t max_tiles;    /* sum over the cameras of one call of tiles_x * tiles_y */
+    int64_t max_pixels;   /* sum over the cameras of one call of width * height */
+    int32_t max_cameras;  /* <= GS_MAX_CAMERAS */
+    int32_t reserved;
+} gs_capacity;
+
+/* Gaussian parameters, structure of arrays, FP32, all rows of length n:
+ *   mean          [3][n]   world-space centre mu
+ *   log_scale     [3][n]   log of the per-axis standard deviations
+ *   quat          [4][n]   rotation (w, x, y, z); normalised before use
+ *   opacity_logit [n]      opacity = sigmoid(opacity_logit)
+ *   sh            [16][3][n] degree-3 SH, coefficient-major, then channel
+ *   lod           [n]      uint8 LOD level (Sec. 3.3); NULL = all level 0
+ * Each base pointer must be 4-byte aligned. */
+typedef struct {
+    int64_t n;
+    const float *mean;
+    const float *log_scale;
+    const float *quat;
+    const float *opacity_logit;
+    const float *sh;
+    const uint8_t *lod;
+} gs_gaussians;
+
+/* Gradients with the layout of gs_gaussians (no lod). */
+typedef struct {
+    float *mean;
+    float *log_scale;
+    float *quat;
+    float *opacity_logit;
+    float *sh;
+} gs_gaussian_grads;
+
+/* Pinhole camera: x_cam = R x_world + t (R row-major), looking along +z,
+ * image x right and y down.  Pixel (px, py) is centred at (px + 0.5, py + 0.5);
+ * (cx, cy) is the principal point.  campos is the camera centre in world
+ * coordinates (-R^T t), used by the LOD gate (Eq. 1) and the SH direction. */
+typedef struct {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    float campos[3];
+    int32_t width, height;
+} gs_camera;
+
+/* Render parameters; gs_default_params fills the standard values. */
+typedef struct {
+    int32_t tile_size;   /* must be GS_TILE */
+    int32_t lod_enable;  /* distance LOD gate of Eq. 1-2 */
+    int32_t lod_Lmax;    /* L_max(t) of Eq. 1 */
+    int32_t cull_enable; /* per-view Cull column of Eq. 3 */
+    float bg[3];         /* background colour, added as T_final * bg */
+    float alpha_min;     /* 1/255: fragments with alpha below are skipped */
+    float alpha_max;     /* 0.99: alpha = min(alpha_max, o G') */
+    float T_min;         /* 1e-4: a pixel stops before T would drop below */
+    float dilation;      /* 0.3 added to the diagonal of the 2D covariance */
+    float znear;         /* 0.2: Gaussians with camera z <= znear are culled */
+    float fov_clamp;     /* 1.3: Jacobian evaluated at x/z clamped to fov_clamp * tan(fov/2) */
+    float lod_d0;        /* d0 of Eq. 1 */
+    float lod_f;         /* f of Eq. 1 (2) */
+    float eps_score;     /* epsilon of the importance score s_i (Sec. 3.2) */
+    float vis_mass;      /* 0.99: c^vis keeps the top vis_mass of each view's w mass */
+} gs_render_params;
+
+/* Device-side counters of the last preprocess / bin_sort, read by
+ * gs_workspace_counts (which synchronises the stream). */
+typedef struct {
+    int64_t n_records;        /* active (Gaussian, camera) pairs */
+    int64_t n_instances;      /* (record, tile) pairs */
+    int64_t n_visible;        /* Gaussians with at least one record */
+    int64_t records_needed;   /* equals n_records unless capacity was exceeded */
+    int64_t instances_needed; /* equals n_instances unless capacity was exceeded */
+    int32_t error;            /* device error word: 0 or a gs_status */
+    int32_t error_site;       /* kernel that set it (implementation detail) */
+} gs_counts;
+
+typedef struct {
+    float *param;
+    const float *grad;
+    float *m;
+    float *v;
+    int64_t n;
+    float lr, beta1, beta2, eps;
+} gs_adam_group;
+
+/* Internal buffers exposed for inspection (debugging, tests).  Pointers are
+ * device pointers owned by the workspace; counts are capacities. */
+typedef enum {
+    GS_BUF_REC_GAUSSIAN = 0, /* uint32 [max_records]: Gaussian of each record */
+    GS_BUF_REC_CAMERA = 1,   /* uint16 [max_records]: camera of each record */
+    GS_BUF_REC_RECT = 2,     /* uint32 [max_records][2]: x0|y0<<16, x1|y1<<16 (tiles) */
+    GS_BUF_REC_TILES = 3,    /* uint32 [max_records]: tiles touched */
+    GS_BUF_REC_DEPTH = 4,    /* uint32 [max_records]: FP32 bits of camera z (valid until gs_bin_sort) */
+    GS_BUF_REC_XY_CONIC = 5, /* float4 [max_records]: u, v, A, B */
+    GS_BUF_REC_C_OPAC_RG = 6,/* float4 [max_records]: C, opacity, r, g */
+    GS_BUF_REC_B = 7,        /* float  [max_records]: b */
+    GS_BUF_REC_OFFSET = 8,   /* uint32 [max_gaussians + 1]: first record of each Gaussian */
+    GS_BUF_SORTED_VALUES = 9,/* uint32 [max_instances]: record of each sorted instance */
+    GS_BUF_TILE_RANGES = 10, /* uint32 [max_tiles][2]: [start, end) of each tile */
+    GS_BUF_N_CONTRIB = 11    /* uint32 [max_pixels]: last composited entry + 1 */
+} gs_buffer_id;
+
+void gs_default_params(gs_render_params *p);
+const char *gs_last_error(void);
+
+/* Creates a workspace on the current CUDA device.  cap: host pointer. */
+int gs_workspace_create(const gs_capacity *cap, gs_workspace **out);
+int gs_workspace_destroy(gs_workspace *ws);
+/* Bytes of device memory a workspace with these capacities holds. */
+int64_t gs_workspace_bytes(const gs_capacity *cap);
+
+/* View gate, projection and colour of every Gaussian for each of n_cams
+ * cameras (host array, <= GS_MAX_CAMERAS).  cull: device bit array
+ * [n_cams][ceil(n/32)], bit i%32 of word i/32 set = Gaussian i culled in that
+ * view (Eq. 3); may be NULL when params->cull_enable == 0.  The Gaussian
+ * arrays must stay unchanged until gs_render_bwd of the same step. */
+int gs_preprocess(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams, int32_t n_cams,
+                  const uint32_t *cull, const gs_render_params *params, gs_stream stream);
+
+/* Tile keys, device radix sort by (camera, tile, depth, record), tile ranges. */
+int gs_bin_sort(gs_workspace *ws, gs_stream stream);
+
+/* Front-to-back compositing.  rgb_out: [sum over cameras of 3*H*W], camera c's
+ * planar [3][H][W] image at offset 3 * (pixels of cameras < c).  T_out: final
+ * transmittance [sum of H*W], same camera order; may be NULL. */
+int gs_render_fwd(gs_workspace *ws, float *rgb_out, float *T_out, gs_stream stream);
+
+/* Adjoint of preprocess + compositing for dL_drgb (layout of rgb_out).
+ * g must be the arrays given to gs_preprocess.  grads: written (accumulate=0,
+ * every Gaussian, zeros where no record) or added to (accumulate=1).
+ * absgrad: [n], += |dL/d(u,v)| per record (densification statistic); may be
+ * NULL.  scale_reg_beta > 0 adds beta * mean over visible Gaussians of the
+ * smallest scale (Eq. 5) to the loss; its value goes to *scale_reg_value
+ * (device float, may be NULL). */
+int gs_render_bwd(gs_workspace *ws, const gs_gaussians *g, const float *dL_drgb, const gs_gaussian_grads *grads,
+                  int32_t accumulate, float *absgrad, float scale_reg_beta, float *scale_reg_value,
+                  gs_stream stream);
+
+/* Instrumented colourless sweep over the binned cameras (Sec. 3.2, Fig. 2).
+ * Per camera v and Gaussian i: w[v][i] = sum over composited pixels of alpha T,
+ * a[v][i] = number of those pixels (w, a: [n_cams][n], written, may be NULL).
+ * Accumulated over views (+=): s_accum[i] += w/(a + eps) when a > 0,
+ * crad_accum[i] += 1 when the Gaussian has a record (in frustum, radius > 0),
+ * cvis_accum[i] += 1 when w lies in the view's top vis_mass of w mass.
+ * cull_out: [n_cams][ceil(n/32)] written, bit = 1 - c^vis.  Any of the
+ * accumulators may be NULL. */
+int gs_importance(gs_workspace *ws, float *w, uint32_t *a, float *s_accum, uint32_t *crad_accum,
+                  uint32_t *cvis_accum, uint32_t *cull_out, gs_stream stream);
+
+/* Eq. 4 over a batch of planar images [batch][3][H][W]:
+ * loss = mean_b (1 - lambda) mean|I - I*| + lambda (1 - SSIM(I, I*)), SSIM with
+ * an 11x11 Gaussian window (sigma 1.5), C1 = 0.01^2, C2 = 0.03^2, zero padding.
+ * Writes *loss_out (device float) and dL_dimage (same layout).  Uses the
+ * workspace's scratch (max_pixels must cover batch * H * W). */
+int gs_photometric_loss(gs_workspace *ws, const float *image, const float *target, int32_t batch, int32_t height,
+                        int32_t width, float lambda, float *loss_out, float *dL_dimage, gs_stream stream);
+
+/* One Adam step (Kingma and Ba, bias-corrected) over n_groups (host array,
+ * <= GS_MAX_ADAM_GROUPS) parameter groups; step counts from 1. */
+int gs_adam_step(const gs_adam_group *groups, int32_t n_groups, int32_t step, gs_stream stream);
+
+/* Synchronises the stream and returns the device error word as a status. */
+int gs_sync_status(gs_workspace *ws, gs_stream stream);
+/* Synchronises the stream and reads the counters (host pointer out). */
+int gs_workspace_counts(gs_workspace *ws, gs_counts *out, gs_stream stream);
+/* Clears the device error word. */
+int gs_clear_error(gs_workspace *ws, gs_stream stream);
+/* Device pointer and element capacity of an internal buffer. */
+int gs_workspace_buffer(gs_workspace *ws, int32_t which, void **ptr, int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSBLITZ_H */

@@ -1,0 +1,358 @@
+"""ctypes binding of libgsblitz.so (include/gsblitz.h), argument marshalling only.
+
+Every compute step runs in the CUDA library; this module converts torch CUDA
+tensors and Python objects into the C structs and passes device pointers and
+the current CUDA stream.  If the library is missing the import of its symbols
+fails loudly: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgsblitz.so")
+
+GS_OK, GS_ERR_INVALID_ARG, GS_ERR_OOM, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_DEVICE = 0, -1, -2, -3, -4, -5, -6
+GS_MAX_CAMERAS = 64
+GS_TILE = 16
+(GS_BUF_REC_GAUSSIAN, GS_BUF_REC_CAMERA, GS_BUF_REC_RECT, GS_BUF_REC_TILES, GS_BUF_REC_DEPTH, GS_BUF_REC_XY_CONIC,
+ GS_BUF_REC_C_OPAC_RG, GS_BUF_REC_B, GS_BUF_REC_OFFSET, GS_BUF_SORTED_VALUES, GS_BUF_TILE_RANGES,
+ GS_BUF_N_CONTRIB) = range(12)
+
+EXPORTS = ("gs_default_params", "gs_last_error", "gs_workspace_create", "gs_workspace_destroy", "gs_workspace_bytes",
+           "gs_preprocess", "gs_bin_sort", "gs_render_fwd", "gs_render_bwd", "gs_importance", "gs_photometric_loss",
+           "gs_adam_step", "gs_sync_status", "gs_workspace_counts", "gs_clear_error", "gs_workspace_buffer")
+
+
+class GSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"gsblitz error {code}: {msg}")
+        self.code = code
+
+
+class GSCapacity(ctypes.Structure):
+    _fields_ = [("max_gaussians", ctypes.c_int64), ("max_records", ctypes.c_int64),
+                ("max_instances", ctypes.c_int64), ("max_tiles", ctypes.c_int64), ("max_pixels", ctypes.c_int64),
+                ("max_cameras", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class GSGaussians(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("mean", ctypes.c_void_p), ("log_scale", ctypes.c_void_p),
+                ("quat", ctypes.c_void_p), ("opacity_logit", ctypes.c_void_p), ("sh", ctypes.c_void_p),
+                ("lod", ctypes.c_void_p)]
+
+
+class GSGaussianGrads(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_void_p), ("log_scale", ctypes.c_void_p), ("quat", ctypes.c_void_p),
+                ("opacity_logit", ctypes.c_void_p), ("sh", ctypes.c_void_p)]
+
+
+class GSCamera(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("campos", ctypes.c_float * 3), ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class GSRenderParams(ctypes.Structure):
+    _fields_ = [("tile_size", ctypes.c_int32), ("lod_enable", ctypes.c_int32), ("lod_Lmax", ctypes.c_int32),
+                ("cull_enable", ctypes.c_int32), ("bg", ctypes.c_float * 3), ("alpha_min", ctypes.c_float),
+                ("alpha_max", ctypes.c_float), ("T_min", ctypes.c_float), ("dilation", ctypes.c_float),
+                ("znear", ctypes.c_float), ("fov_clamp", ctypes.c_float), ("lod_d0", ctypes.c_float),
+                ("lod_f", ctypes.c_float), ("eps_score", ctypes.c_float), ("vis_mass", ctypes.c_float)]
+
+
+class GSCounts(ctypes.Structure):
+    _fields_ = [("n_records", ctypes.c_int64), ("n_instances", ctypes.c_int64), ("n_visible", ctypes.c_int64),
+                ("records_needed", ctypes.c_int64), ("instances_needed", ctypes.c_int64),
+                ("error", ctypes.c_int32), ("error_site", ctypes.c_int32)]
+
+
+class GSAdamGroup(ctypes.Structure):
+    _fields_ = [("param", ctypes.c_void_p), ("grad", ctypes.c_void_p), ("m", ctypes.c_void_p),
+                ("v", ctypes.c_void_p), ("n", ctypes.c_int64), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libgsblitz.so from the package directory (raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2605_13794_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.gs_default_params.argtypes = [vp]
+        L.gs_default_params.restype = None
+        L.gs_last_error.restype = ctypes.c_char_p
+        L.gs_workspace_create.argtypes = [vp, vp]
+        L.gs_workspace_destroy.argtypes = [vp]
+        L.gs_workspace_bytes.argtypes = [vp]
+        L.gs_workspace_bytes.restype = i64
+        L.gs_preprocess.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+        L.gs_bin_sort.argtypes = [vp, vp]
+        L.gs_render_fwd.argtypes = [vp, vp, vp, vp]
+        L.gs_render_bwd.argtypes = [vp, vp, vp, vp, i32, vp, ctypes.c_float, vp, vp]
+        L.gs_importance.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+        L.gs_photometric_loss.argtypes = [vp, vp, vp, i32, i32, i32, ctypes.c_float, vp, vp, vp]
+        L.gs_adam_step.argtypes = [vp, i32, i32, vp]
+        L.gs_sync_status.argtypes = [vp, vp]
+        L.gs_workspace_counts.argtypes = [vp, vp, vp]
+        L.gs_clear_error.argtypes = [vp, vp]
+        L.gs_workspace_buffer.argtypes = [vp, i32, vp, vp]
+        for name in EXPORTS:
+            if name not in ("gs_default_params", "gs_last_error", "gs_workspace_bytes"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != GS_OK:
+        raise GSError(rc, lib().gs_last_error().decode(errors="replace"))
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    if t is None:
+        return ctypes.c_void_p(0)
+    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+@dataclasses.dataclass
+class RenderParams:
+    """Mirror of gs_render_params; defaults come from gs_default_params."""
+
+    bg: tuple = (0.0, 0.0, 0.0)
+    alpha_min: float | None = None
+    alpha_max: float | None = None
+    T_min: float | None = None
+    dilation: float | None = None
+    znear: float | None = None
+    fov_clamp: float | None = None
+    lod_enable: bool = False
+    lod_d0: float | None = None
+    lod_f: float | None = None
+    lod_Lmax: int | None = None
+    cull_enable: bool = False
+    eps_score: float | None = None
+    vis_mass: float | None = None
+
+    def c(self) -> GSRenderParams:
+        p = GSRenderParams()
+        lib().gs_default_params(ctypes.byref(p))
+        p.bg = (ctypes.c_float * 3)(*self.bg)
+        p.lod_enable = int(self.lod_enable)
+        p.cull_enable = int(self.cull_enable)
+        for name in ("alpha_min", "alpha_max", "T_min", "dilation", "znear", "fov_clamp", "lod_d0", "lod_f",
+                     "lod_Lmax", "eps_score", "vis_mass"):
+            v = getattr(self, name)
+            if v is not None:
+                setattr(p, name, v)
+        return p
+
+
+@dataclasses.dataclass
+class GaussianTensors:
+    """Gaussian parameters as CUDA tensors in the library's SoA layout."""
+
+    mean: torch.Tensor          # (3, N) float32
+    log_scale: torch.Tensor     # (3, N)
+    quat: torch.Tensor          # (4, N)
+    opacity_logit: torch.Tensor # (N,)
+    sh: torch.Tensor            # (16, 3, N)
+    lod: torch.Tensor | None    # (N,) uint8
+
+    @property
+    def n(self) -> int:
+        return int(self.opacity_logit.shape[0])
+
+    @staticmethod
+    def from_host(g, device="cuda") -> "GaussianTensors":
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        return GaussianTensors(t(g.mean), t(g.log_scale), t(g.quat), t(g.opacity_logit), t(g.sh),
+                               t(g.lod) if g.lod is not None else None)
+
+    def zeros_like(self) -> "GaussianTensors":
+        z = torch.zeros_like
+        return GaussianTensors(z(self.mean), z(self.log_scale), z(self.quat), z(self.opacity_logit), z(self.sh), None)
+
+    def params(self):
+        return [self.mean, self.log_scale, self.quat, self.opacity_logit, self.sh]
+
+    def c(self) -> GSGaussians:
+        return GSGaussians(self.n, _ptr(self.mean), _ptr(self.log_scale), _ptr(self.quat), _ptr(self.opacity_logit),
+                           _ptr(self.sh), _ptr(self.lod))
+
+    def c_grads(self) -> GSGaussianGrads:
+        return GSGaussianGrads(_ptr(self.mean), _ptr(self.log_scale), _ptr(self.quat), _ptr(self.opacity_logit),
+                               _ptr(self.sh))
+
+
+def camera_c(cam) -> GSCamera:
+    c = GSCamera()
+    c.R = (ctypes.c_float * 9)(*np.asarray(cam.R, np.float32).ravel())
+    c.t = (ctypes.c_float * 3)(*np.asarray(cam.t, np.float32))
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.campos = (ctypes.c_float * 3)(*np.asarray(cam.campos, np.float32))
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+def tiles_of(cam) -> int:
+    return ((cam.width + GS_TILE - 1) // GS_TILE) * ((cam.height + GS_TILE - 1) // GS_TILE)
+
+
+class Workspace:
+    """Owns a gs_workspace (all scratch of the render path) on the current device."""
+
+    def __init__(self, max_gaussians: int, max_records: int, max_instances: int, max_tiles: int,
+                 max_pixels: int, max_cameras: int = 1):
+        self.cap = GSCapacity(max_gaussians, max_records, max_instances, max_tiles, max_pixels, max_cameras, 0)
+        self._ws = ctypes.c_void_p()
+        _check(lib().gs_workspace_create(ctypes.byref(self.cap), ctypes.byref(self._ws)))
+        self.cams = []
+
+    @staticmethod
+    def bytes_for(**cap) -> int:
+        c = GSCapacity(cap["max_gaussians"], cap["max_records"], cap["max_instances"], cap["max_tiles"],
+                       cap["max_pixels"], cap.get("max_cameras", 1), 0)
+        return int(lib().gs_workspace_bytes(ctypes.byref(c)))
+
+    def close(self):
+        if self._ws:
+            _check(lib().gs_workspace_destroy(self._ws))
+            self._ws = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def preprocess(self, g: GaussianTensors, cams, params: RenderParams, cull=None, stream=None):
+        arr = (GSCamera * len(cams))(*[camera_c(c) for c in cams])
+        self.cams = list(cams)
+        self._g = g  # keep the parameter tensors alive until the backward
+        gc, pc = g.c(), params.c()
+        _check(lib().gs_preprocess(self._ws, ctypes.byref(gc), arr, len(cams), _ptr(cull), ctypes.byref(pc),
+                                   _stream(stream)))
+
+    def bin_sort(self, stream=None):
+        _check(lib().gs_bin_sort(self._ws, _stream(stream)))
+
+    @property
+    def total_pixels(self) -> int:
+        return sum(c.width * c.height for c in self.cams)
+
+    def render_fwd(self, rgb_out, T_out=None, stream=None):
+        _check(lib().gs_render_fwd(self._ws, _ptr(rgb_out), _ptr(T_out), _stream(stream)))
+
+    def render_bwd(self, g: GaussianTensors, dL_drgb, grads: GaussianTensors, accumulate=False, absgrad=None,
+                   scale_reg_beta=0.0, scale_reg_value=None, stream=None):
+        gc, gr = g.c(), grads.c_grads()
+        _check(lib().gs_render_bwd(self._ws, ctypes.byref(gc), _ptr(dL_drgb), ctypes.byref(gr), int(accumulate),
+                                   _ptr(absgrad), float(scale_reg_beta), _ptr(scale_reg_value), _stream(stream)))
+
+    def importance(self, w=None, a=None, s_accum=None, crad=None, cvis=None, cull_out=None, stream=None):
+        _check(lib().gs_importance(self._ws, _ptr(w), _ptr(a), _ptr(s_accum), _ptr(crad), _ptr(cvis), _ptr(cull_out),
+                                   _stream(stream)))
+
+    def photometric_loss(self, image, target, lam, loss_out, dL_dimage, stream=None):
+        B, C, H, W = image.shape
+        assert C == 3
+        _check(lib().gs_photometric_loss(self._ws, _ptr(image), _ptr(target), B, H, W, float(lam), _ptr(loss_out),
+                                         _ptr(dL_dimage), _stream(stream)))
+
+    def counts(self, stream=None) -> dict:
+        c = GSCounts()
+        _check(lib().gs_workspace_counts(self._ws, ctypes.byref(c), _stream(stream)))
+        return {f[0]: getattr(c, f[0]) for f in GSCounts._fields_}
+
+    def sync_status(self, stream=None):
+        _check(lib().gs_sync_status(self._ws, _stream(stream)))
+
+    def clear_error(self, stream=None):
+        _check(lib().gs_clear_error(self._ws, _stream(stream)))
+
+    def buffer(self, which: int):
+        p, n = ctypes.c_void_p(), ctypes.c_int64()
+        _check(lib().gs_workspace_buffer(self._ws, which, ctypes.byref(p), ctypes.byref(n)))
+        return p.value, n.value
+
+    def read_buffer(self, which: int, dtype, count: int, width: int = 1) -> np.ndarray:
+        """Copies `count` entries (each `width` items of `dtype`) of an internal
+        buffer to the host, after synchronising the device (debug/tests)."""
+        ptr, cap = self.buffer(which)
+        assert count <= cap
+        out = np.empty((count, width) if width > 1 else count, dtype=dtype)
+        if count:
+            torch.cuda.synchronize()
+            _memcpy_d2h(out.ctypes.data, ptr, out.nbytes)
+        return out
+
+
+_cudart = None
+
+
+def _memcpy_d2h(dst: int, src: int, nbytes: int):
+    """Device-to-host copy through the CUDA runtime libgsblitz.so is linked with."""
+    global _cudart
+    if _cudart is None:
+        _cudart = ctypes.CDLL("libcudart.so.13")
+        _cudart.cudaMemcpy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+    rc = _cudart.cudaMemcpy(ctypes.c_void_p(dst), ctypes.c_void_p(src), nbytes, 2)  # cudaMemcpyDeviceToHost
+    if rc != 0:
+        raise RuntimeError(f"cudaMemcpy failed with {rc}")
+
+
+def adam_step(groups, step: int, stream=None):
+    """groups: list of (param, grad, m, v, lr, beta1, beta2, eps) CUDA tensors/floats."""
+    arr = (GSAdamGroup * len(groups))()
+    for k, (p, g, m, v, lr, b1, b2, eps) in enumerate(groups):
+        arr[k] = GSAdamGroup(_ptr(p), _ptr(g), _ptr(m), _ptr(v), p.numel(), lr, b1, b2, eps)
+    _check(lib().gs_adam_step(arr, len(groups), int(step), _stream(stream)))
+
+
+class RenderFunction(torch.autograd.Function):
+    """Differentiable render through the library: forward = preprocess +
+    bin_sort + render_fwd, backward = render_bwd (the hand-written adjoint)."""
+
+    @staticmethod
+    def forward(ctx, ws, cams, params, cull, lod, mean, log_scale, quat, opacity_logit, sh):
+        g = GaussianTensors(mean.detach().contiguous(), log_scale.detach().contiguous(), quat.detach().contiguous(),
+                            opacity_logit.detach().contiguous(), sh.detach().contiguous(), lod)
+        ws.preprocess(g, cams, params, cull)
+        ws.bin_sort()
+        P = ws.total_pixels
+        rgb = torch.empty(3 * P, device=mean.device, dtype=torch.float32)
+        T = torch.empty(P, device=mean.device, dtype=torch.float32)
+        ws.render_fwd(rgb, T)
+        ctx.ws, ctx.g = ws, g
+        ctx.mark_non_differentiable(T)
+        return rgb, T
+
+    @staticmethod
+    def backward(ctx, dL_drgb, dL_dT):
+        g = ctx.g
+        grads = g.zeros_like()
+        ctx.ws.render_bwd(g, dL_drgb.contiguous(), grads, accumulate=False)
+        return (None, None, None, None, None, grads.mean, grads.log_scale, grads.quat, grads.opacity_logit, grads.sh)
+
+
+def render(ws: Workspace, g: GaussianTensors, cams, params: RenderParams, cull=None):
+    """Differentiable render of g (tensors may require grad) into the cameras.
+    Returns (rgb [3*sum(H*W)] planar per camera, T_final [sum(H*W)])."""
+    return RenderFunction.apply(ws, cams, params, cull, g.lod, g.mean, g.log_scale, g.quat, g.opacity_logit, g.sh)

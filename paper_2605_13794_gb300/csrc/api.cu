@@ -1,0 +1,441 @@
+// api.cu -- host side of the C ABI declared in gsblitz.h: argument checks,
+// workspace layout, and the order of kernel launches for each call.
+#include <math.h>
+#include <new>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "gs_internal.cuh"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(GS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                                                                       \
+    do {                                                                                                      \
+        cudaError_t e_ = (call);                                                                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where);                                                   \
+    } while (0)
+
+struct Layout {
+    size_t off = 0;
+    template <typename T>
+    size_t take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        size_t o = off;
+        off += count * sizeof(T);
+        return o;
+    }
+};
+
+struct Offsets {
+    size_t rec_off, rec_g, rec_cam, rd0, rd1, rd2, rect, tt, inst_off, clampm, rgrad, dkey0, dkey1, dval0, dval1;
+    size_t tkey0, tkey1, tval0, tval1, slots, ranges, n_contrib, T_final, imp_w, imp_a, sel_cum;
+    size_t selk0, selk1, selv0, selv1, loss_maps, loss_partial, lb_status, rx_status, rx_hist, rx_off, red_partial,
+        ctr;
+    size_t total;
+    size_t lb_words, rx_words, red_words, loss_partial_words;
+};
+
+Offsets plan(const gs_capacity &c)
+{
+    Offsets o;
+    Layout L;
+    const size_t N = (size_t)c.max_gaussians, R = (size_t)c.max_records, I = (size_t)c.max_instances;
+    const size_t T = (size_t)c.max_tiles, P = (size_t)c.max_pixels;
+    o.rec_off = L.take<uint32_t>(N + 1);
+    o.rec_g = L.take<uint32_t>(R);
+    o.rec_cam = L.take<uint16_t>(R);
+    o.rd0 = L.take<float4>(R);
+    o.rd1 = L.take<float4>(R);
+    o.rd2 = L.take<float>(R);
+    o.rect = L.take<uint2>(R);
+    o.tt = L.take<uint32_t>(R);
+    o.inst_off = L.take<uint32_t>(R);
+    o.clampm = L.take<uint8_t>(R);
+    o.rgrad = L.take<float>(R * gs::kSlotFloats);
+    o.dkey0 = L.take<uint32_t>(R);
+    o.dkey1 = L.take<uint32_t>(R);
+    o.dval0 = L.take<uint32_t>(R);
+    o.dval1 = L.take<uint32_t>(R);
+    o.tkey0 = L.take<uint32_t>(I);
+    o.tkey1 = L.take<uint32_t>(I);
+    o.tval0 = L.take<uint32_t>(I);
+    o.tval1 = L.take<uint32_t>(I);
+    o.slots = L.take<float>(I * gs::kSlotFloats);
+    o.ranges = L.take<uint2>(T);
+    o.n_contrib = L.take<uint32_t>(P);
+    o.T_final = L.take<float>(P);
+    o.imp_w = L.take<float>(R);
+    o.imp_a = L.take<uint32_t>(R);
+    o.sel_cum = L.take<double>(R);
+    o.selk0 = L.take<uint32_t>(R);
+    o.selk1 = L.take<uint32_t>(R);
+    o.selv0 = L.take<uint32_t>(R);
+    o.selv1 = L.take<uint32_t>(R);
+    o.loss_maps = L.take<float>(P * 3 * 3);
+    o.loss_partial_words = 2 * 3 * (P / 1024 + 65536);
+    o.loss_partial = L.take<float>(o.loss_partial_words);
+    const size_t nb = (N > R ? N : R) / 256 + 2;
+    o.lb_words = nb + 1;
+    o.lb_status = L.take<unsigned long long>(o.lb_words);
+    const size_t items = (R > I ? R : I);
+    o.rx_words = (items / gs::kSortTile + 1) * 256 + 1;
+    o.rx_status = L.take<uint32_t>(o.rx_words);
+    o.rx_hist = L.take<uint32_t>(4 * 256);
+    o.rx_off = L.take<uint32_t>(4 * 256);
+    const size_t k8 = N / 128 + 2, sel = 2 * (R / 4096 + 2);
+    o.red_words = k8 > sel ? k8 : sel;
+    o.red_partial = L.take<float>(o.red_words);
+    o.ctr = L.take<gs::DevCounters>(1);
+    o.total = (L.off + 255) & ~(size_t)255;
+    return o;
+}
+
+int check_cap(const gs_capacity *c)
+{
+    if (!c) return fail(GS_ERR_INVALID_ARG, "capacity is NULL");
+    if (c->max_gaussians < 0 || c->max_records < 0 || c->max_instances < 0 || c->max_tiles < 0 || c->max_pixels < 0)
+        return fail(GS_ERR_INVALID_ARG, "negative capacity");
+    if (c->max_cameras < 1 || c->max_cameras > GS_MAX_CAMERAS)
+        return fail(GS_ERR_INVALID_ARG, "max_cameras must be in [1, %d]", GS_MAX_CAMERAS);
+    if (c->max_instances >= (1ll << 30) || c->max_records >= (1ll << 30))
+        return fail(GS_ERR_INVALID_ARG, "max_instances and max_records must be below 2^30");
+    if (c->max_gaussians >= (1ll << 32) - 1) return fail(GS_ERR_INVALID_ARG, "max_gaussians must be below 2^32 - 1");
+    return GS_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+void gs_default_params(gs_render_params *p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->tile_size = GS_TILE;
+    p->lod_enable = 0;
+    p->lod_Lmax = 5;
+    p->cull_enable = 0;
+    p->alpha_min = 1.f / 255.f;
+    p->alpha_max = 0.99f;
+    p->T_min = 1e-4f;
+    p->dilation = 0.3f;
+    p->znear = 0.2f;
+    p->fov_clamp = 1.3f;
+    p->lod_d0 = 1600.f;
+    p->lod_f = 2.f;
+    p->eps_score = 1e-6f;
+    p->vis_mass = 0.99f;
+}
+
+const char *gs_last_error(void) { return g_err; }
+
+int64_t gs_workspace_bytes(const gs_capacity *cap)
+{
+    if (check_cap(cap) != GS_OK) return -1;
+    return (int64_t)plan(*cap).total;
+}
+
+int gs_workspace_create(const gs_capacity *cap, gs_workspace **out)
+{
+    if (!out) return fail(GS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = check_cap(cap);
+    if (rc != GS_OK) return rc;
+    Offsets o = plan(*cap);
+    gs_workspace *ws = new (std::nothrow) gs_workspace();
+    if (!ws) return fail(GS_ERR_OOM, "host allocation failed");
+    ws->cap = *cap;
+    cudaGetDevice(&ws->device);
+    cudaError_t e = cudaMalloc(&ws->base, o.total);
+    if (e != cudaSuccess) {
+        delete ws;
+        cudaGetLastError();
+        return fail(GS_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", o.total, cudaGetErrorString(e));
+    }
+    ws->bytes = o.total;
+    char *b = (char *)ws->base;
+    ws->rec_off = (uint32_t *)(b + o.rec_off);
+    ws->rec_g = (uint32_t *)(b + o.rec_g);
+    ws->rec_cam = (uint16_t *)(b + o.rec_cam);
+    ws->rd0 = (float4 *)(b + o.rd0);
+    ws->rd1 = (float4 *)(b + o.rd1);
+    ws->rd2 = (float *)(b + o.rd2);
+    ws->rect = (uint2 *)(b + o.rect);
+    ws->tt = (uint32_t *)(b + o.tt);
+    ws->inst_off = (uint32_t *)(b + o.inst_off);
+    ws->clampm = (uint8_t *)(b + o.clampm);
+    ws->rgrad = (float *)(b + o.rgrad);
+    ws->dkey[0] = (uint32_t *)(b + o.dkey0); ws->dkey[1] = (uint32_t *)(b + o.dkey1);
+    ws->dval[0] = (uint32_t *)(b + o.dval0); ws->dval[1] = (uint32_t *)(b + o.dval1);
+    ws->tkey[0] = (uint32_t *)(b + o.tkey0); ws->tkey[1] = (uint32_t *)(b + o.tkey1);
+    ws->tval[0] = (uint32_t *)(b + o.tval0); ws->tval[1] = (uint32_t *)(b + o.tval1);
+    ws->slots = (float *)(b + o.slots);
+    ws->ranges = (uint2 *)(b + o.ranges);
+    ws->n_contrib = (uint32_t *)(b + o.n_contrib);
+    ws->T_final = (float *)(b + o.T_final);
+    ws->imp_w = (float *)(b + o.imp_w);
+    ws->imp_a = (uint32_t *)(b + o.imp_a);
+    ws->sel_cum = (double *)(b + o.sel_cum);
+    ws->selk[0] = (uint32_t *)(b + o.selk0); ws->selk[1] = (uint32_t *)(b + o.selk1);
+    ws->selv[0] = (uint32_t *)(b + o.selv0); ws->selv[1] = (uint32_t *)(b + o.selv1);
+    ws->loss_maps = (float *)(b + o.loss_maps);
+    ws->loss_partial = (float *)(b + o.loss_partial);
+    ws->loss_partial_words = o.loss_partial_words;
+    ws->lb_status = (unsigned long long *)(b + o.lb_status);
+    ws->lb_words = o.lb_words;
+    ws->rx_status = (uint32_t *)(b + o.rx_status);
+    ws->rx_words = o.rx_words;
+    ws->rx_hist = (uint32_t *)(b + o.rx_hist);
+    ws->rx_off = (uint32_t *)(b + o.rx_off);
+    ws->red_partial = (float *)(b + o.red_partial);
+    ws->red_words = o.red_words;
+    ws->ctr = (gs::DevCounters *)(b + o.ctr);
+    e = cudaMemset(ws->ctr, 0, sizeof(gs::DevCounters));
+    if (e != cudaSuccess) {
+        cudaFree(ws->base);
+        delete ws;
+        return cuda_fail(e, "gs_workspace_create");
+    }
+    *out = ws;
+    return GS_OK;
+}
+
+int gs_workspace_destroy(gs_workspace *ws)
+{
+    if (!ws) return GS_OK;
+    cudaError_t e = cudaFree(ws->base);
+    delete ws;
+    if (e != cudaSuccess) return cuda_fail(e, "gs_workspace_destroy");
+    return GS_OK;
+}
+
+static bool aligned4(const void *p) { return ((uintptr_t)p & 3u) == 0; }
+
+int gs_preprocess(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams, int32_t n_cams,
+                  const uint32_t *cull, const gs_render_params *params, gs_stream stream)
+{
+    if (!ws || !g || !cams || !params) return fail(GS_ERR_INVALID_ARG, "gs_preprocess: NULL argument");
+    if (n_cams < 1 || n_cams > ws->cap.max_cameras)
+        return fail(GS_ERR_INVALID_ARG, "gs_preprocess: n_cams %d outside [1, %d]", n_cams, ws->cap.max_cameras);
+    if (g->n < 0 || g->n > ws->cap.max_gaussians)
+        return fail(GS_ERR_CAPACITY, "gs_preprocess: n = %lld exceeds max_gaussians %lld", (long long)g->n,
+                    (long long)ws->cap.max_gaussians);
+    if (params->tile_size != GS_TILE) return fail(GS_ERR_INVALID_ARG, "gs_preprocess: tile_size must be %d", GS_TILE);
+    if (g->n > 0 && (!g->mean || !g->log_scale || !g->quat || !g->opacity_logit || !g->sh))
+        return fail(GS_ERR_INVALID_ARG, "gs_preprocess: NULL Gaussian array");
+    if (!aligned4(g->mean) || !aligned4(g->log_scale) || !aligned4(g->quat) || !aligned4(g->opacity_logit) ||
+        !aligned4(g->sh))
+        return fail(GS_ERR_INVALID_ARG, "gs_preprocess: Gaussian arrays must be 4-byte aligned");
+    if (params->cull_enable && !cull) return fail(GS_ERR_INVALID_ARG, "gs_preprocess: cull_enable needs a cull array");
+    if (params->lod_enable && (params->lod_Lmax < 0 || !(params->lod_f > 1.f) || !(params->lod_d0 > 0.f)))
+        return fail(GS_ERR_INVALID_ARG, "gs_preprocess: LOD gate needs lod_Lmax >= 0, lod_f > 1, lod_d0 > 0");
+    gs::CamTable ct;
+    memset(&ct, 0, sizeof(ct));
+    ct.n = n_cams;
+    long long tiles = 0, pix = 0;
+    for (int c = 0; c < n_cams; c++) {
+        const gs_camera &s = cams[c];
+        if (s.width <= 0 || s.height <= 0 || s.width > 65535 * GS_TILE || s.height > 65535 * GS_TILE)
+            return fail(GS_ERR_INVALID_ARG, "gs_preprocess: camera %d has size %dx%d", c, s.width, s.height);
+        if (!(s.fx > 0.f) || !(s.fy > 0.f)) return fail(GS_ERR_INVALID_ARG, "gs_preprocess: camera %d focal", c);
+        gs::CamInfo &d = ct.c[c];
+        memcpy(d.R, s.R, sizeof(d.R));
+        memcpy(d.t, s.t, sizeof(d.t));
+        d.fx = s.fx; d.fy = s.fy; d.cx = s.cx; d.cy = s.cy;
+        memcpy(d.campos, s.campos, sizeof(d.campos));
+        d.width = s.width; d.height = s.height;
+        d.tiles_x = (s.width + GS_TILE - 1) / GS_TILE;
+        d.tiles_y = (s.height + GS_TILE - 1) / GS_TILE;
+        d.tile_base = (int)tiles;
+        d.pix_base = pix;
+        tiles += (long long)d.tiles_x * d.tiles_y;
+        pix += (long long)s.width * s.height;
+    }
+    if (tiles > ws->cap.max_tiles) return fail(GS_ERR_CAPACITY, "gs_preprocess: %lld tiles > max_tiles", tiles);
+    if (pix > ws->cap.max_pixels) return fail(GS_ERR_CAPACITY, "gs_preprocess: %lld pixels > max_pixels", pix);
+    ct.total_tiles = (int)tiles;
+    gs::RenderConsts rc;
+    memcpy(rc.bg, params->bg, sizeof(rc.bg));
+    rc.alpha_min = params->alpha_min; rc.alpha_max = params->alpha_max; rc.T_min = params->T_min;
+    rc.dilation = params->dilation; rc.znear = params->znear; rc.fov_clamp = params->fov_clamp;
+    rc.lod_d0 = params->lod_d0; rc.lod_f = params->lod_f;
+    rc.lod_enable = params->lod_enable; rc.lod_Lmax = params->lod_Lmax; rc.cull_enable = params->cull_enable;
+    rc.eps_score = params->eps_score; rc.vis_mass = params->vis_mass;
+    ws->cams = ct;
+    ws->rc = rc;
+    ws->g = *g;
+    ws->have_preprocess = 1;
+    ws->have_binning = 0;
+    CK(gs::launch_preprocess(ws, (cudaStream_t)stream, cull), "gs_preprocess");
+    return GS_OK;
+}
+
+int gs_bin_sort(gs_workspace *ws, gs_stream stream)
+{
+    if (!ws) return fail(GS_ERR_INVALID_ARG, "gs_bin_sort: NULL workspace");
+    if (!ws->have_preprocess) return fail(GS_ERR_INVALID_ARG, "gs_bin_sort: no preprocess on this workspace");
+    cudaStream_t st = (cudaStream_t)stream;
+    // 1. depth order of the records
+    int ob = 0;
+    CK(gs::launch_radix_sort(ws, st, ws->dkey, ws->dval, &ws->ctr->n_records, (unsigned long long)ws->cap.max_records,
+                             32, true, false, ob),
+       "gs_bin_sort(depth)");
+    ws->depth_buf = ob;
+    // 2. emission of (tile, record) instances in depth order
+    CK(cudaMemsetAsync(&ws->ctr->n_instances, 0, sizeof(unsigned long long), st), "gs_bin_sort");
+    CK(cudaMemsetAsync(&ws->ctr->instances_needed, 0, sizeof(unsigned long long), st), "gs_bin_sort");
+    CK(gs::launch_emit(ws, st), "gs_bin_sort(emit)");
+    // 3. stable sort by global tile id
+    int bits = 0;
+    while ((1ll << bits) < (long long)ws->cams.total_tiles) bits++;
+    CK(gs::launch_radix_sort(ws, st, ws->tkey, ws->tval, &ws->ctr->n_instances,
+                             (unsigned long long)ws->cap.max_instances, bits, false, false, ob),
+       "gs_bin_sort(tiles)");
+    ws->tile_buf = ob;
+    // 4. tile ranges
+    CK(gs::launch_ranges(ws, st), "gs_bin_sort(ranges)");
+    ws->have_binning = 1;
+    return GS_OK;
+}
+
+int gs_render_fwd(gs_workspace *ws, float *rgb_out, float *T_out, gs_stream stream)
+{
+    if (!ws || !rgb_out) return fail(GS_ERR_INVALID_ARG, "gs_render_fwd: NULL argument");
+    if (!ws->have_binning) return fail(GS_ERR_INVALID_ARG, "gs_render_fwd: call gs_bin_sort first");
+    CK(gs::launch_render_fwd(ws, (cudaStream_t)stream, rgb_out, T_out), "gs_render_fwd");
+    return GS_OK;
+}
+
+int gs_render_bwd(gs_workspace *ws, const gs_gaussians *g, const float *dL_drgb, const gs_gaussian_grads *grads,
+                  int32_t accumulate, float *absgrad, float scale_reg_beta, float *scale_reg_value, gs_stream stream)
+{
+    if (!ws || !g || !dL_drgb || !grads) return fail(GS_ERR_INVALID_ARG, "gs_render_bwd: NULL argument");
+    if (!ws->have_binning) return fail(GS_ERR_INVALID_ARG, "gs_render_bwd: call gs_bin_sort and gs_render_fwd first");
+    if (g->n != ws->g.n) return fail(GS_ERR_INVALID_ARG, "gs_render_bwd: Gaussian count differs from preprocess");
+    if (g->n > 0 && (!grads->mean || !grads->log_scale || !grads->quat || !grads->opacity_logit || !grads->sh))
+        return fail(GS_ERR_INVALID_ARG, "gs_render_bwd: NULL gradient array");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(gs::launch_render_bwd(ws, st, dL_drgb), "gs_render_bwd(raster)");
+    CK(gs::launch_reduce_slots(ws, st), "gs_render_bwd(reduce)");
+    CK(gs::launch_preprocess_bwd(ws, st, *g, *grads, accumulate, absgrad, scale_reg_beta, scale_reg_value),
+       "gs_render_bwd(preprocess)");
+    return GS_OK;
+}
+
+int gs_importance(gs_workspace *ws, float *w, uint32_t *a, float *s_accum, uint32_t *crad_accum,
+                  uint32_t *cvis_accum, uint32_t *cull_out, gs_stream stream)
+{
+    if (!ws) return fail(GS_ERR_INVALID_ARG, "gs_importance: NULL workspace");
+    if (!ws->have_binning) return fail(GS_ERR_INVALID_ARG, "gs_importance: call gs_bin_sort first");
+    CK(gs::launch_importance(ws, (cudaStream_t)stream, w, a, s_accum, crad_accum, cvis_accum, cull_out),
+       "gs_importance");
+    return GS_OK;
+}
+
+int gs_photometric_loss(gs_workspace *ws, const float *image, const float *target, int32_t batch, int32_t height,
+                        int32_t width, float lambda, float *loss_out, float *dL_dimage, gs_stream stream)
+{
+    if (!ws || !image || !target || !loss_out || !dL_dimage)
+        return fail(GS_ERR_INVALID_ARG, "gs_photometric_loss: NULL argument");
+    if (batch < 1 || height < 1 || width < 1) return fail(GS_ERR_INVALID_ARG, "gs_photometric_loss: empty batch");
+    const long long px = (long long)batch * height * width;
+    if (px > ws->cap.max_pixels)
+        return fail(GS_ERR_CAPACITY, "gs_photometric_loss: batch*H*W = %lld exceeds max_pixels", px);
+    const long long blocks = (long long)((width + 31) / 32) * ((height + 31) / 32) * batch * 3;
+    if (2 * blocks > (long long)ws->loss_partial_words)
+        return fail(GS_ERR_CAPACITY, "gs_photometric_loss: image too large for the workspace's partial sums");
+    CK(gs::launch_loss(ws, (cudaStream_t)stream, image, target, batch, height, width, lambda, loss_out, dL_dimage),
+       "gs_photometric_loss");
+    return GS_OK;
+}
+
+int gs_adam_step(const gs_adam_group *groups, int32_t n_groups, int32_t step, gs_stream stream)
+{
+    if (!groups || n_groups < 1 || n_groups > GS_MAX_ADAM_GROUPS)
+        return fail(GS_ERR_INVALID_ARG, "gs_adam_step: 1..%d groups required", GS_MAX_ADAM_GROUPS);
+    if (step < 1) return fail(GS_ERR_INVALID_ARG, "gs_adam_step: step counts from 1");
+    for (int k = 0; k < n_groups; k++) {
+        const gs_adam_group &gr = groups[k];
+        if (gr.n < 0 || (gr.n > 0 && (!gr.param || !gr.grad || !gr.m || !gr.v)))
+            return fail(GS_ERR_INVALID_ARG, "gs_adam_step: group %d invalid", k);
+    }
+    CK(gs::launch_adam(groups, n_groups, step, (cudaStream_t)stream), "gs_adam_step");
+    return GS_OK;
+}
+
+int gs_sync_status(gs_workspace *ws, gs_stream stream)
+{
+    gs_counts c;
+    int rc = gs_workspace_counts(ws, &c, stream);
+    if (rc != GS_OK) return rc;
+    if (c.error)
+        return fail(c.error, "device error %d at site %d (records needed %lld of %lld, instances needed %lld of %lld)",
+                    c.error, c.error_site, (long long)c.records_needed, (long long)ws->cap.max_records,
+                    (long long)c.instances_needed, (long long)ws->cap.max_instances);
+    return GS_OK;
+}
+
+int gs_workspace_counts(gs_workspace *ws, gs_counts *out, gs_stream stream)
+{
+    if (!ws || !out) return fail(GS_ERR_INVALID_ARG, "gs_workspace_counts: NULL argument");
+    gs::DevCounters d;
+    CK(cudaMemcpyAsync(&d, ws->ctr, sizeof(d), cudaMemcpyDeviceToHost, (cudaStream_t)stream), "gs_workspace_counts");
+    CK(cudaStreamSynchronize((cudaStream_t)stream), "gs_workspace_counts");
+    out->n_records = (int64_t)d.n_records;
+    out->n_instances = (int64_t)d.n_instances;
+    out->n_visible = (int64_t)d.n_visible;
+    out->records_needed = (int64_t)d.records_needed;
+    out->instances_needed = (int64_t)d.instances_needed;
+    out->error = d.error;
+    out->error_site = d.error_site;
+    return GS_OK;
+}
+
+int gs_clear_error(gs_workspace *ws, gs_stream stream)
+{
+    if (!ws) return fail(GS_ERR_INVALID_ARG, "gs_clear_error: NULL workspace");
+    CK(cudaMemsetAsync(&ws->ctr->error, 0, 2 * sizeof(int), (cudaStream_t)stream), "gs_clear_error");
+    return GS_OK;
+}
+
+int gs_workspace_buffer(gs_workspace *ws, int32_t which, void **ptr, int64_t *count)
+{
+    if (!ws || !ptr || !count) return fail(GS_ERR_INVALID_ARG, "gs_workspace_buffer: NULL argument");
+    const gs_capacity &c = ws->cap;
+    switch (which) {
+    case GS_BUF_REC_GAUSSIAN: *ptr = ws->rec_g; *count = c.max_records; break;
+    case GS_BUF_REC_CAMERA: *ptr = ws->rec_cam; *count = c.max_records; break;
+    case GS_BUF_REC_RECT: *ptr = ws->rect; *count = c.max_records; break;
+    case GS_BUF_REC_TILES: *ptr = ws->tt; *count = c.max_records; break;
+    case GS_BUF_REC_DEPTH: *ptr = ws->dkey[0]; *count = c.max_records; break;
+    case GS_BUF_REC_XY_CONIC: *ptr = ws->rd0; *count = c.max_records; break;
+    case GS_BUF_REC_C_OPAC_RG: *ptr = ws->rd1; *count = c.max_records; break;
+    case GS_BUF_REC_B: *ptr = ws->rd2; *count = c.max_records; break;
+    case GS_BUF_REC_OFFSET: *ptr = ws->rec_off; *count = c.max_gaussians + 1; break;
+    case GS_BUF_SORTED_VALUES: *ptr = ws->tval[ws->tile_buf]; *count = c.max_instances; break;
+    case GS_BUF_TILE_RANGES: *ptr = ws->ranges; *count = c.max_tiles; break;
+    case GS_BUF_N_CONTRIB: *ptr = ws->n_contrib; *count = c.max_pixels; break;
+    default: return fail(GS_ERR_INVALID_ARG, "gs_workspace_buffer: unknown buffer %d", which);
+    }
+    return GS_OK;
+}
+
+} // extern "C"

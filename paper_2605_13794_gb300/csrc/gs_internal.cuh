@@ -1,0 +1,256 @@
+// gs_internal.cuh -- device-side building blocks shared by the gsblitz kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gsblitz.h"
+
+namespace gs {
+
+constexpr int kTile = GS_TILE;          // 16 x 16 pixel tiles
+constexpr int kTilePix = kTile * kTile; // 256 pixels = one 256-thread block
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;          // keys per thread in a radix pass
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kSlotFloats = 9;          // per (record, tile) gradient slot: du dv dA dB dC do dr dg db
+constexpr unsigned long long kSpinLimit = 1ull << 22;
+
+// Error sites recorded next to the error word (which kernel gave up).
+enum ErrorSite {
+    kSitePreprocess = 1, kSiteEmit = 2, kSiteRadix = 3, kSiteSelect = 4, kSiteScanF64 = 5,
+};
+
+// Device counters of one workspace.
+struct DevCounters {
+    unsigned long long n_records;
+    unsigned long long n_instances;
+    unsigned long long n_visible;
+    unsigned long long records_needed;
+    unsigned long long instances_needed;
+    int error;
+    int error_site;
+    unsigned long long sel_count[GS_MAX_CAMERAS]; // w > 0 entries per camera (importance)
+};
+
+// Per-camera constants passed by value to the kernels.
+struct CamInfo {
+    float R[9], t[3];
+    float fx, fy, cx, cy;
+    float campos[3];
+    int width, height;
+    int tiles_x, tiles_y;
+    int tile_base;        // first global tile id of this camera
+    long long pix_base;   // first pixel of this camera in the concatenated outputs
+};
+
+struct CamTable {
+    int n;
+    int total_tiles;
+    CamInfo c[GS_MAX_CAMERAS];
+};
+
+// Render-time constants (FP32, as the kernels compare them).
+struct RenderConsts {
+    float bg[3];
+    float alpha_min, alpha_max, T_min;
+    float dilation, znear, fov_clamp;
+    float lod_d0, lod_f;
+    int lod_enable, lod_Lmax, cull_enable;
+    float eps_score, vis_mass;
+};
+
+__device__ __forceinline__ void set_error(DevCounters *ctr, int code, int site)
+{
+    if (atomicCAS(&ctr->error, 0, code) == 0) ctr->error_site = site;
+}
+
+// Camera of a global tile id (binary search over tile bases).
+__device__ __forceinline__ int camera_of_tile(const CamTable &ct, int tile)
+{
+    int lo = 0, hi = ct.n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (ct.c[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Rectangle of a record, packed as (x0 | y0 << 16, x1 | y1 << 16) in tiles.
+__device__ __forceinline__ void unpack_rect(uint2 r, int &x0, int &y0, int &x1, int &y1)
+{
+    x0 = (int)(r.x & 0xffffu); y0 = (int)(r.x >> 16);
+    x1 = (int)(r.y & 0xffffu); y1 = (int)(r.y >> 16);
+}
+
+// ---- decoupled look-back (Merrill & Garland single-pass scan) -------------
+// Status words: bits 63..62 = 0 empty, 1 block aggregate, 2 inclusive prefix.
+constexpr unsigned long long kLbAgg = 1ull << 62;
+constexpr unsigned long long kLbInc = 2ull << 62;
+constexpr unsigned long long kLbVal = (1ull << 62) - 1;
+
+__device__ __forceinline__ void lb_store(unsigned long long *p, unsigned long long v)
+{
+    *(volatile unsigned long long *)p = v;
+}
+
+__device__ __forceinline__ unsigned long long lb_load(const unsigned long long *p)
+{
+    return *(volatile const unsigned long long *)p;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Called by one full warp of block `bid`.  Publishes the block aggregate,
+// walks back over predecessors 32 at a time and returns the exclusive prefix
+// of this block (to every lane), then publishes the inclusive prefix.  Every
+// wait is bounded: on timeout the error word is set and the walk stops.
+__device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long long *status, unsigned bid,
+                                                                 unsigned long long aggregate, DevCounters *ctr,
+                                                                 int site)
+{
+    const int lane = threadIdx.x & 31;
+    if (bid == 0) {
+        if (lane == 0) lb_store(&status[0], kLbInc | aggregate);
+        return 0ull;
+    }
+    if (lane == 0) lb_store(&status[bid], kLbAgg | aggregate);
+    unsigned long long excl = 0;
+    long long pred = (long long)bid - 1;
+    while (true) {
+        long long idx = pred - lane;
+        unsigned long long s = kLbInc; // before block 0: inclusive prefix 0
+        if (idx >= 0) {
+            unsigned long long spins = 0;
+            while (true) {
+                s = lb_load(&status[idx]);
+                if ((s >> 62) != 0) break;
+                if (++spins > kSpinLimit) {
+                    set_error(ctr, GS_ERR_TIMEOUT, site);
+                    s = kLbInc;
+                    break;
+                }
+                __nanosleep(40);
+            }
+        }
+        unsigned incl = __ballot_sync(0xffffffffu, (s >> 62) == 2);
+        unsigned long long v = s & kLbVal;
+        if (incl) {
+            int first = __ffs(incl) - 1;
+            if (lane > first) v = 0;
+            excl += warp_sum_u64(v);
+            break;
+        }
+        excl += warp_sum_u64(v);
+        pred -= 32;
+    }
+    if (lane == 0) lb_store(&status[bid], kLbInc | (excl + aggregate));
+    return excl;
+}
+
+// Block-wide exclusive scan of one value per thread (blockDim.x == 256).
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan_256(T v, T *smem_warp /*[8]*/, T &total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem_warp[warp] = x;
+    __syncthreads();
+    T wpre = 0, tot = 0;
+    for (int w = 0; w < 8; w++) {
+        T s = smem_warp[w];
+        if (w < warp) wpre += s;
+        tot += s;
+    }
+    __syncthreads();
+    total = tot;
+    return wpre + x - v;
+}
+
+} // namespace gs
+
+// ---- workspace (host struct, device buffers) -------------------------------
+struct gs_workspace {
+    gs_capacity cap;
+    int device;
+    void *base;          // one device allocation, carved into the buffers below
+    size_t bytes;
+    // per Gaussian
+    uint32_t *rec_off;   // [N+1]
+    // per record
+    uint32_t *rec_g;
+    uint16_t *rec_cam;
+    float4 *rd0;         // u, v, A, B
+    float4 *rd1;         // C, opacity, r, g
+    float *rd2;          // b
+    uint2 *rect;
+    uint32_t *tt;
+    uint32_t *inst_off;
+    uint8_t *clampm;
+    float *rgrad;        // [R][9] per-record summed gradients of u v A B C o r g b
+    uint32_t *dkey[2], *dval[2];
+    // per instance
+    uint32_t *tkey[2], *tval[2];
+    float *slots;        // [I][9]
+    // per tile
+    uint2 *ranges;       // [T]
+    // per pixel
+    uint32_t *n_contrib;
+    float *T_final;
+    // importance
+    float *imp_w;        // [R] per-record alpha-weight
+    uint32_t *imp_a;     // [R]
+    double *sel_cum;     // [R] scratch for the FP64 mass scan
+    uint32_t *selk[2], *selv[2]; // [R] selection sort pairs
+    // loss scratch: 3 maps of [P][3]
+    float *loss_maps;
+    float *loss_partial; // [2 * blocks]
+    size_t loss_partial_words;
+    // scan / sort scratch
+    unsigned long long *lb_status; // [max(blocks)+1] single-value look-back + ticket
+    size_t lb_words;
+    uint32_t *rx_status; // [blocks * 256 + 1] radix look-back + ticket
+    size_t rx_words;
+    uint32_t *rx_hist;   // [4][256]
+    uint32_t *rx_off;    // [4][256]
+    float *red_partial;  // [blocks] generic reduction partials
+    size_t red_words;
+    gs::DevCounters *ctr;
+    // state of the last preprocess
+    gs::CamTable cams;
+    gs::RenderConsts rc;
+    gs_gaussians g;
+    int have_preprocess;
+    int have_binning;
+    int depth_buf;       // buffer holding sorted depth order
+    int tile_buf;        // buffer holding sorted instances
+};
+
+namespace gs {
+// Kernel launchers (defined in the .cu files).
+cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t *cull);
+cudaError_t launch_radix_sort(gs_workspace *ws, cudaStream_t st, uint32_t *keys[2], uint32_t *vals[2],
+                              const unsigned long long *count, unsigned long long cap, int bits, bool vals_identity,
+                              bool descending_keys_in_place, int &out_buf);
+cudaError_t launch_emit(gs_workspace *ws, cudaStream_t st);
+cudaError_t launch_ranges(gs_workspace *ws, cudaStream_t st);
+cudaError_t launch_render_fwd(gs_workspace *ws, cudaStream_t st, float *rgb, float *T_out);
+cudaError_t launch_render_bwd(gs_workspace *ws, cudaStream_t st, const float *dL_drgb);
+cudaError_t launch_reduce_slots(gs_workspace *ws, cudaStream_t st);
+cudaError_t launch_preprocess_bwd(gs_workspace *ws, cudaStream_t st, const gs_gaussians &g,
+                                  const gs_gaussian_grads &gr, int accumulate, float *absgrad, float beta,
+                                  float *scale_reg_value);
+cudaError_t launch_importance(gs_workspace *ws, cudaStream_t st, float *w, uint32_t *a, float *s_accum,
+                              uint32_t *crad, uint32_t *cvis, uint32_t *cull_out);
+cudaError_t launch_loss(gs_workspace *ws, cudaStream_t st, const float *img, const float *tgt, int B, int H, int W,
+                        float lambda, float *loss_out, float *dL);
+cudaError_t launch_adam(const gs_adam_group *groups, int n_groups, int step, cudaStream_t st);
+} // namespace gs

@@ -1,0 +1,601 @@
+// preprocess.cu -- view gate, EWA projection, SH colour (forward) and the
+// adjoint of the projection and colour (backward).
+//
+// Forward, one thread per Gaussian, all cameras of the call:
+//   LOD gate (Sec. 3.3, Eq. 1-2) and Cull column (Eq. 3), near cull,
+//   Sigma = R(q) S S^T R(q)^T, Sigma' = J W Sigma W^T J^T + dilation I,
+//   conic, radius ceil(3 sqrt(lambda_max)), tile rectangle (App. A),
+//   degree-3 SH colour, sigmoid opacity.
+// Active (Gaussian, camera) pairs become records, compacted in (Gaussian,
+// camera) order by a single-pass decoupled look-back scan, so later stages
+// only touch active work.  The integer decisions (gate, near cull, det sign,
+// radius, rectangle) are computed with explicitly rounded FP32 operations
+// (no contraction) so they are reproducible on any FP32 IEEE implementation.
+#include "gs_internal.cuh"
+
+namespace gs {
+
+#define FMUL __fmul_rn
+#define FADD __fadd_rn
+#define FSUB __fsub_rn
+#define FDIV __fdiv_rn
+#define FSQRT __fsqrt_rn
+
+struct GaussPtrs {
+    const float *mean, *log_scale, *quat, *opacity_logit, *sh;
+    const uint8_t *lod;
+    long long n;
+};
+
+struct Proj {
+    float u, v, A, B, C, depth;
+    int radius;
+    int x0, y0, x1, y1;
+};
+
+// SH basis, degree 3, real form with the Condon-Shortley phase, m = -l..l,
+// evaluated as homogeneous polynomials of the unit direction (x, y, z).
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float Y[16])
+{
+    const float C0 = 0.28209479177387814f, C1 = 0.4886025119029199f;
+    const float C2a = 1.0925484305920792f, C2b = 0.31539156525252005f, C2c = 0.5462742152960396f;
+    const float C3a = 0.5900435899266435f, C3b = 2.890611442640554f, C3c = 0.4570457994644658f;
+    const float C3d = 0.3731763325901154f, C3e = 1.445305721320277f;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[0] = C0;
+    Y[1] = -C1 * y;
+    Y[2] = C1 * z;
+    Y[3] = -C1 * x;
+    Y[4] = C2a * x * y;
+    Y[5] = -C2a * y * z;
+    Y[6] = C2b * (2.f * zz - xx - yy);
+    Y[7] = -C2a * x * z;
+    Y[8] = C2c * (xx - yy);
+    Y[9] = -C3a * y * (3.f * xx - yy);
+    Y[10] = C3b * x * y * z;
+    Y[11] = -C3c * y * (4.f * zz - xx - yy);
+    Y[12] = C3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+    Y[13] = -C3c * x * (4.f * zz - xx - yy);
+    Y[14] = C3e * z * (xx - yy);
+    Y[15] = -C3a * x * (xx - 3.f * yy);
+}
+
+// Gradient of each basis polynomial with respect to (x, y, z).
+__device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float dY[16][3])
+{
+    const float C1 = 0.4886025119029199f;
+    const float C2a = 1.0925484305920792f, C2b = 0.31539156525252005f, C2c = 0.5462742152960396f;
+    const float C3a = 0.5900435899266435f, C3b = 2.890611442640554f, C3c = 0.4570457994644658f;
+    const float C3d = 0.3731763325901154f, C3e = 1.445305721320277f;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    dY[0][0] = 0.f; dY[0][1] = 0.f; dY[0][2] = 0.f;
+    dY[1][0] = 0.f; dY[1][1] = -C1; dY[1][2] = 0.f;
+    dY[2][0] = 0.f; dY[2][1] = 0.f; dY[2][2] = C1;
+    dY[3][0] = -C1; dY[3][1] = 0.f; dY[3][2] = 0.f;
+    dY[4][0] = C2a * y; dY[4][1] = C2a * x; dY[4][2] = 0.f;
+    dY[5][0] = 0.f; dY[5][1] = -C2a * z; dY[5][2] = -C2a * y;
+    dY[6][0] = -2.f * C2b * x; dY[6][1] = -2.f * C2b * y; dY[6][2] = 4.f * C2b * z;
+    dY[7][0] = -C2a * z; dY[7][1] = 0.f; dY[7][2] = -C2a * x;
+    dY[8][0] = 2.f * C2c * x; dY[8][1] = -2.f * C2c * y; dY[8][2] = 0.f;
+    dY[9][0] = -C3a * 6.f * x * y; dY[9][1] = -C3a * (3.f * xx - 3.f * yy); dY[9][2] = 0.f;
+    dY[10][0] = C3b * y * z; dY[10][1] = C3b * x * z; dY[10][2] = C3b * x * y;
+    dY[11][0] = C3c * 2.f * x * y; dY[11][1] = -C3c * (4.f * zz - xx - 3.f * yy); dY[11][2] = -C3c * 8.f * y * z;
+    dY[12][0] = -C3d * 6.f * x * z; dY[12][1] = -C3d * 6.f * y * z; dY[12][2] = C3d * (6.f * zz - 3.f * xx - 3.f * yy);
+    dY[13][0] = -C3c * (4.f * zz - 3.f * xx - yy); dY[13][1] = C3c * 2.f * x * y; dY[13][2] = -C3c * 8.f * x * z;
+    dY[14][0] = C3e * 2.f * x * z; dY[14][1] = -C3e * 2.f * y * z; dY[14][2] = C3e * (xx - yy);
+    dY[15][0] = -C3a * (3.f * xx - 3.f * yy); dY[15][1] = C3a * 6.f * x * y; dY[15][2] = 0.f;
+}
+
+__device__ __forceinline__ float clampf(float x, float lo, float hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+// View gate + projection of one Gaussian into one camera.  Returns false when
+// the Gaussian is gated, culled, behind the near plane, degenerate, or has an
+// empty tile rectangle.
+__device__ __forceinline__ bool project_gaussian(const float m[3], const float ls[3], const float qin[4], int lod,
+                                                 bool culled, const CamInfo &cam, const RenderConsts &rc, Proj &o)
+{
+    if (rc.lod_enable) {
+        float dx = FSUB(m[0], cam.campos[0]), dy = FSUB(m[1], cam.campos[1]), dz = FSUB(m[2], cam.campos[2]);
+        float d = FSQRT(FADD(FADD(FMUL(dx, dx), FMUL(dy, dy)), FMUL(dz, dz)));
+        int L;
+        if (d > 0.f) {
+            float x = FDIV(log2f(FDIV(rc.lod_d0, d)), log2f(rc.lod_f));
+            float r = x >= 0.f ? floorf(FADD(x, 0.5f)) : -floorf(FADD(-x, 0.5f)); // half away from zero
+            L = (int)r;
+        } else {
+            L = rc.lod_Lmax;
+        }
+        L = L < 0 ? 0 : (L > rc.lod_Lmax ? rc.lod_Lmax : L);
+        if (lod > L) return false;
+    }
+    if (rc.cull_enable && culled) return false;
+
+    const float *R = cam.R;
+    float tx = FADD(FADD(FADD(FMUL(R[0], m[0]), FMUL(R[1], m[1])), FMUL(R[2], m[2])), cam.t[0]);
+    float ty = FADD(FADD(FADD(FMUL(R[3], m[0]), FMUL(R[4], m[1])), FMUL(R[5], m[2])), cam.t[1]);
+    float tz = FADD(FADD(FADD(FMUL(R[6], m[0]), FMUL(R[7], m[1])), FMUL(R[8], m[2])), cam.t[2]);
+    if (!(tz > rc.znear)) return false;
+
+    float qw = qin[0], qx = qin[1], qy = qin[2], qz = qin[3];
+    float qn = FSQRT(FADD(FADD(FADD(FMUL(qw, qw), FMUL(qx, qx)), FMUL(qy, qy)), FMUL(qz, qz)));
+    qw = FDIV(qw, qn); qx = FDIV(qx, qn); qy = FDIV(qy, qn); qz = FDIV(qz, qn);
+    float Q[3][3];
+    Q[0][0] = FSUB(1.f, FMUL(2.f, FADD(FMUL(qy, qy), FMUL(qz, qz))));
+    Q[0][1] = FMUL(2.f, FSUB(FMUL(qx, qy), FMUL(qw, qz)));
+    Q[0][2] = FMUL(2.f, FADD(FMUL(qx, qz), FMUL(qw, qy)));
+    Q[1][0] = FMUL(2.f, FADD(FMUL(qx, qy), FMUL(qw, qz)));
+    Q[1][1] = FSUB(1.f, FMUL(2.f, FADD(FMUL(qx, qx), FMUL(qz, qz))));
+    Q[1][2] = FMUL(2.f, FSUB(FMUL(qy, qz), FMUL(qw, qx)));
+    Q[2][0] = FMUL(2.f, FSUB(FMUL(qx, qz), FMUL(qw, qy)));
+    Q[2][1] = FMUL(2.f, FADD(FMUL(qy, qz), FMUL(qw, qx)));
+    Q[2][2] = FSUB(1.f, FMUL(2.f, FADD(FMUL(qx, qx), FMUL(qy, qy))));
+    float s[3] = {expf(ls[0]), expf(ls[1]), expf(ls[2])};
+    float M[3][3], S[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) M[i][j] = FMUL(Q[i][j], s[j]);
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+            S[i][j] = FADD(FADD(FMUL(M[i][0], M[j][0]), FMUL(M[i][1], M[j][1])), FMUL(M[i][2], M[j][2]));
+
+    const float fx = cam.fx, fy = cam.fy;
+    float limx = FMUL(rc.fov_clamp, FDIV((float)cam.width, FMUL(2.f, fx)));
+    float limy = FMUL(rc.fov_clamp, FDIV((float)cam.height, FMUL(2.f, fy)));
+    float xr = FDIV(tx, tz), yr = FDIV(ty, tz);
+    float txc = FMUL(clampf(xr, -limx, limx), tz);
+    float tyc = FMUL(clampf(yr, -limy, limy), tz);
+    float tz2 = FMUL(tz, tz);
+    float j00 = FDIV(fx, tz), j02 = FDIV(-FMUL(fx, txc), tz2);
+    float j11 = FDIV(fy, tz), j12 = FDIV(-FMUL(fy, tyc), tz2);
+    float T[2][3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        T[0][k] = FADD(FMUL(j00, R[k]), FMUL(j02, R[6 + k]));
+        T[1][k] = FADD(FMUL(j11, R[3 + k]), FMUL(j12, R[6 + k]));
+    }
+    float V[2][3];
+#pragma unroll
+    for (int r = 0; r < 2; r++)
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            V[r][k] = FADD(FADD(FMUL(T[r][0], S[0][k]), FMUL(T[r][1], S[1][k])), FMUL(T[r][2], S[2][k]));
+    float s00 = FADD(FADD(FMUL(V[0][0], T[0][0]), FMUL(V[0][1], T[0][1])), FMUL(V[0][2], T[0][2]));
+    float s01 = FADD(FADD(FMUL(V[0][0], T[1][0]), FMUL(V[0][1], T[1][1])), FMUL(V[0][2], T[1][2]));
+    float s11 = FADD(FADD(FMUL(V[1][0], T[1][0]), FMUL(V[1][1], T[1][1])), FMUL(V[1][2], T[1][2]));
+    float a = FADD(s00, rc.dilation), b = s01, c = FADD(s11, rc.dilation);
+    float det = FSUB(FMUL(a, c), FMUL(b, b));
+    if (!(det > 0.f)) return false;
+    float mid = FMUL(0.5f, FADD(a, c));
+    float disc = FSUB(FMUL(mid, mid), det);
+    if (disc < 0.1f) disc = 0.1f;
+    float lam = FADD(mid, FSQRT(disc));
+    float ext = FMUL(3.f, FSQRT(lam));
+    int radius = (int)ceilf(ext);
+    float u = FADD(FDIV(FMUL(fx, tx), tz), cam.cx);
+    float v = FADD(FDIV(FMUL(fy, ty), tz), cam.cy);
+    float rr = (float)radius, ts = (float)kTile;
+    int x0 = (int)floorf(FDIV(FSUB(u, rr), ts)), y0 = (int)floorf(FDIV(FSUB(v, rr), ts));
+    int x1 = (int)floorf(FDIV(FADD(u, rr), ts)) + 1, y1 = (int)floorf(FDIV(FADD(v, rr), ts)) + 1;
+    x0 = min(max(x0, 0), cam.tiles_x); x1 = min(max(x1, 0), cam.tiles_x);
+    y0 = min(max(y0, 0), cam.tiles_y); y1 = min(max(y1, 0), cam.tiles_y);
+    if (x1 <= x0 || y1 <= y0) return false;
+    o.u = u; o.v = v;
+    o.A = FDIV(c, det); o.B = FDIV(-b, det); o.C = FDIV(a, det);
+    o.depth = tz;
+    o.radius = radius;
+    o.x0 = x0; o.y0 = y0; o.x1 = x1; o.y1 = y1;
+    return true;
+}
+
+struct PreOut {
+    uint32_t *rec_off, *rec_g, *tt, *dkey;
+    uint16_t *rec_cam;
+    float4 *rd0, *rd1;
+    float *rd2;
+    uint2 *rect;
+    uint8_t *clampm;
+    unsigned long long *lb_status;
+    unsigned int *ticket;
+    DevCounters *ctr;
+    long long max_records;
+    const uint32_t *cull;
+    long long cull_words;
+};
+
+template <bool MULTI>
+__global__ void __launch_bounds__(256) preprocess_kernel(GaussPtrs g, PreOut o, CamTable ct, RenderConsts rc)
+{
+    __shared__ unsigned s_bid;
+    __shared__ unsigned long long s_warp[8];
+    __shared__ unsigned long long s_base;
+    __shared__ unsigned s_vis[8];
+    if (threadIdx.x == 0) s_bid = atomicAdd(o.ticket, 1u);
+    __syncthreads();
+    const unsigned bid = s_bid;
+    const long long n = g.n;
+    const long long i = (long long)bid * 256 + threadIdx.x;
+    const bool valid = i < n;
+
+    float m[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0};
+    int lod = 0;
+    if (valid) {
+        m[0] = g.mean[i]; m[1] = g.mean[n + i]; m[2] = g.mean[2 * n + i];
+        ls[0] = g.log_scale[i]; ls[1] = g.log_scale[n + i]; ls[2] = g.log_scale[2 * n + i];
+        q[0] = g.quat[i]; q[1] = g.quat[n + i]; q[2] = g.quat[2 * n + i]; q[3] = g.quat[3 * n + i];
+        lod = g.lod ? (int)g.lod[i] : 0;
+    }
+    unsigned long long mask = 0;
+    Proj p0;
+    if (valid) {
+        for (int c = 0; c < ct.n; c++) {
+            bool culled = o.cull ? ((o.cull[c * o.cull_words + (i >> 5)] >> (i & 31)) & 1u) : false;
+            Proj p;
+            if (project_gaussian(m, ls, q, lod, culled, ct.c[c], rc, p)) {
+                mask |= 1ull << c;
+                if (!MULTI) p0 = p;
+            }
+        }
+    }
+    const unsigned long long cnt = __popcll(mask);
+    unsigned long long total;
+    const unsigned long long excl = block_exclusive_scan_256<unsigned long long>(cnt, s_warp, total);
+    if (threadIdx.x < 32) {
+        unsigned long long b = lookback_exclusive(o.lb_status + 1, bid, total, o.ctr, kSitePreprocess);
+        if (threadIdx.x == 0) s_base = b;
+    }
+    // count Gaussians with at least one record (visible set of Eq. 5)
+    unsigned vis = __ballot_sync(0xffffffffu, cnt > 0);
+    if ((threadIdx.x & 31) == 0) s_vis[threadIdx.x >> 5] = __popc(vis);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned tv = 0;
+        for (int w = 0; w < 8; w++) tv += s_vis[w];
+        if (tv) atomicAdd(&o.ctr->n_visible, (unsigned long long)tv);
+    }
+    const unsigned long long base = s_base + excl;
+    if (!valid) return;
+    o.rec_off[i] = (uint32_t)base;
+    if (i == n - 1) {
+        unsigned long long end = base + cnt;
+        o.rec_off[n] = (uint32_t)(end < (unsigned long long)o.max_records ? end : o.max_records);
+        o.ctr->records_needed = end;
+        o.ctr->n_records = end < (unsigned long long)o.max_records ? end : o.max_records;
+    }
+    if (!mask) return;
+
+    const float op = 1.f / (1.f + expf(-g.opacity_logit[i]));
+    unsigned long long r = base;
+    for (unsigned long long mm = mask; mm; mm &= mm - 1, r++) {
+        const int c = __ffsll((long long)mm) - 1;
+        if (r >= (unsigned long long)o.max_records) {
+            set_error(o.ctr, GS_ERR_CAPACITY, kSitePreprocess);
+            break;
+        }
+        Proj p;
+        if (MULTI) project_gaussian(m, ls, q, lod, false, ct.c[c], rc, p); // same inputs: same (passing) result
+        else p = p0;
+        const CamInfo &cam = ct.c[c];
+        // view direction and SH colour
+        float dx = m[0] - cam.campos[0], dy = m[1] - cam.campos[1], dz = m[2] - cam.campos[2];
+        float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+        float Y[16];
+        sh_basis(dx * inv, dy * inv, dz * inv, Y);
+        float col[3];
+        uint8_t cm = 0;
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < 16; k++) acc = fmaf(g.sh[(long long)(3 * k + ch) * n + i], Y[k], acc);
+            acc += 0.5f;
+            if (acc < 0.f) { acc = 0.f; cm |= (uint8_t)(1u << ch); }
+            col[ch] = acc;
+        }
+        o.rec_g[r] = (uint32_t)i;
+        o.rec_cam[r] = (uint16_t)c;
+        o.rd0[r] = make_float4(p.u, p.v, p.A, p.B);
+        o.rd1[r] = make_float4(p.C, op, col[0], col[1]);
+        o.rd2[r] = col[2];
+        o.rect[r] = make_uint2((uint32_t)p.x0 | ((uint32_t)p.y0 << 16), (uint32_t)p.x1 | ((uint32_t)p.y1 << 16));
+        o.tt[r] = (uint32_t)((p.x1 - p.x0) * (p.y1 - p.y0));
+        o.dkey[r] = __float_as_uint(p.depth);
+        o.clampm[r] = cm;
+    }
+}
+
+cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t *cull)
+{
+    const long long n = ws->g.n;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    cudaError_t e;
+    // reset counters and the look-back state (ticket in word 0)
+    if ((e = cudaMemsetAsync(ws->ctr, 0, sizeof(DevCounters), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ws->lb_status, 0, (blocks + 1) * sizeof(unsigned long long), st)) != cudaSuccess)
+        return e;
+    if (n == 0) return cudaSuccess;
+    GaussPtrs gp{ws->g.mean, ws->g.log_scale, ws->g.quat, ws->g.opacity_logit, ws->g.sh, ws->g.lod, n};
+    PreOut o;
+    o.rec_off = ws->rec_off; o.rec_g = ws->rec_g; o.tt = ws->tt; o.dkey = ws->dkey[0];
+    o.rec_cam = ws->rec_cam; o.rd0 = ws->rd0; o.rd1 = ws->rd1; o.rd2 = ws->rd2; o.rect = ws->rect;
+    o.clampm = ws->clampm; o.lb_status = ws->lb_status; o.ticket = (unsigned int *)ws->lb_status;
+    o.ctr = ws->ctr; o.max_records = ws->cap.max_records;
+    o.cull = ws->rc.cull_enable ? cull : nullptr;
+    o.cull_words = (n + 31) / 32;
+    if (ws->cams.n == 1)
+        preprocess_kernel<false><<<blocks, 256, 0, st>>>(gp, o, ws->cams, ws->rc);
+    else
+        preprocess_kernel<true><<<blocks, 256, 0, st>>>(gp, o, ws->cams, ws->rc);
+    return cudaGetLastError();
+}
+
+// ---- backward ---------------------------------------------------------------
+
+// Sum of the per-(record, tile) gradient slots of each record.  Records are
+// visited in depth order, in which their slots are contiguous.
+__global__ void __launch_bounds__(256) reduce_slots_kernel(const uint32_t *drec, const uint32_t *inst_off,
+                                                           const uint32_t *tt, const float *slots, float *rgrad,
+                                                           const DevCounters *ctr)
+{
+    const unsigned long long k = (unsigned long long)blockIdx.x * 256 + threadIdx.x;
+    if (k >= ctr->n_records) return;
+    const uint32_t r = drec[k];
+    const unsigned long long off = inst_off[r], cnt = tt[r];
+    if (off + cnt > ctr->n_instances) return; // capacity error already recorded
+    float acc[kSlotFloats];
+#pragma unroll
+    for (int j = 0; j < kSlotFloats; j++) acc[j] = 0.f;
+    const float *s = slots + off * kSlotFloats;
+    for (unsigned long long t = 0; t < cnt; t++, s += kSlotFloats)
+#pragma unroll
+        for (int j = 0; j < kSlotFloats; j++) acc[j] += s[j];
+#pragma unroll
+    for (int j = 0; j < kSlotFloats; j++) rgrad[(unsigned long long)r * kSlotFloats + j] = acc[j];
+}
+
+cudaError_t launch_reduce_slots(gs_workspace *ws, cudaStream_t st)
+{
+    const long long cap = ws->cap.max_records;
+    const unsigned blocks = (unsigned)((cap + 255) / 256);
+    reduce_slots_kernel<<<blocks, 256, 0, st>>>(ws->dval[ws->depth_buf], ws->inst_off, ws->tt, ws->slots, ws->rgrad,
+                                                ws->ctr);
+    return cudaGetLastError();
+}
+
+struct BwdArgs {
+    GaussPtrs g;
+    float *gmean, *gls, *gquat, *gop, *gsh;
+    const uint32_t *rec_off;
+    const uint16_t *rec_cam;
+    const uint8_t *clampm;
+    const float *rgrad;
+    float *absgrad;
+    int accumulate;
+    float beta;
+    float *red_partial;
+    const DevCounters *ctr;
+};
+
+__device__ __forceinline__ void store_grad(float *p, float v, int accumulate)
+{
+    if (accumulate) *p += v; else *p = v;
+}
+
+// Chain rule from the gradients of (u, v, conic A B C, opacity, rgb) of each
+// record to the parameters of its Gaussian, summed over the Gaussian's records.
+__global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, CamTable ct, RenderConsts rc)
+{
+    __shared__ float s_red[4];
+    const long long n = a.g.n;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float smin_val = 0.f;
+    if (i < n) {
+        const unsigned long long nrec = a.ctr->n_records;
+        unsigned long long r0 = a.rec_off[i], r1 = a.rec_off[i + 1];
+        if (r1 > nrec) r1 = nrec;
+        if (r0 > r1) r0 = r1;
+        float gm[3] = {0, 0, 0}, gls[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gop = 0.f;
+        float gsh[48];
+#pragma unroll
+        for (int k = 0; k < 48; k++) gsh[k] = 0.f;
+        const float m[3] = {a.g.mean[i], a.g.mean[n + i], a.g.mean[2 * n + i]};
+        const float ls[3] = {a.g.log_scale[i], a.g.log_scale[n + i], a.g.log_scale[2 * n + i]};
+        const bool has = r1 > r0;
+        if (has) {
+            const float qr[4] = {a.g.quat[i], a.g.quat[n + i], a.g.quat[2 * n + i], a.g.quat[3 * n + i]};
+            const float qn = sqrtf(qr[0] * qr[0] + qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]);
+            const float q[4] = {qr[0] / qn, qr[1] / qn, qr[2] / qn, qr[3] / qn};
+            const float w = q[0], x = q[1], y = q[2], z = q[3];
+            float Q[3][3];
+            Q[0][0] = 1.f - 2.f * (y * y + z * z); Q[0][1] = 2.f * (x * y - w * z); Q[0][2] = 2.f * (x * z + w * y);
+            Q[1][0] = 2.f * (x * y + w * z); Q[1][1] = 1.f - 2.f * (x * x + z * z); Q[1][2] = 2.f * (y * z - w * x);
+            Q[2][0] = 2.f * (x * z - w * y); Q[2][1] = 2.f * (y * z + w * x); Q[2][2] = 1.f - 2.f * (x * x + y * y);
+            const float s[3] = {expf(ls[0]), expf(ls[1]), expf(ls[2])};
+            float M[3][3], Sg[3][3];
+            for (int p = 0; p < 3; p++)
+                for (int c = 0; c < 3; c++) M[p][c] = Q[p][c] * s[c];
+            for (int p = 0; p < 3; p++)
+                for (int c = 0; c < 3; c++) Sg[p][c] = M[p][0] * M[c][0] + M[p][1] * M[c][1] + M[p][2] * M[c][2];
+            const float o = 1.f / (1.f + expf(-a.g.opacity_logit[i]));
+            float gSsum[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+            float absacc = 0.f;
+            for (unsigned long long r = r0; r < r1; r++) {
+                const CamInfo &cam = ct.c[a.rec_cam[r]];
+                const float *rg = a.rgrad + r * kSlotFloats;
+                const float gu = rg[0], gv = rg[1], gA = rg[2], gB = rg[3], gC = rg[4], go = rg[5];
+                const float grgb[3] = {rg[6], rg[7], rg[8]};
+                absacc += sqrtf(gu * gu + gv * gv);
+                const float *W = cam.R;
+                float t[3];
+                for (int k = 0; k < 3; k++) t[k] = W[3 * k] * m[0] + W[3 * k + 1] * m[1] + W[3 * k + 2] * m[2] + cam.t[k];
+                const float fx = cam.fx, fy = cam.fy;
+                const float limx = rc.fov_clamp * ((float)cam.width / (2.f * fx));
+                const float limy = rc.fov_clamp * ((float)cam.height / (2.f * fy));
+                const float xr = t[0] / t[2], yr = t[1] / t[2];
+                const bool clx = xr < -limx || xr > limx, cly = yr < -limy || yr > limy;
+                const float xc = clampf(xr, -limx, limx), yc = clampf(yr, -limy, limy);
+                const float tz = t[2], itz = 1.f / tz, itz2 = itz * itz;
+                float J[2][3] = {{fx * itz, 0.f, -fx * xc * itz}, {0.f, fy * itz, -fy * yc * itz}};
+                float T[2][3];
+                for (int r2 = 0; r2 < 2; r2++)
+                    for (int k = 0; k < 3; k++) T[r2][k] = J[r2][0] * W[k] + J[r2][1] * W[3 + k] + J[r2][2] * W[6 + k];
+                float S2[2][2];
+                for (int r2 = 0; r2 < 2; r2++)
+                    for (int c2 = 0; c2 < 2; c2++) {
+                        float acc = 0.f;
+                        for (int p = 0; p < 3; p++) {
+                            float tp = T[r2][0] * Sg[0][p] + T[r2][1] * Sg[1][p] + T[r2][2] * Sg[2][p];
+                            acc += tp * T[c2][p];
+                        }
+                        S2[r2][c2] = acc;
+                    }
+                const float aa = S2[0][0] + rc.dilation, bb = S2[0][1], cc = S2[1][1] + rc.dilation;
+                const float det = aa * cc - bb * bb, idet = 1.f / det, idet2 = idet * idet;
+                // conic (A, B, C) = (c, -b, a) / det
+                const float ga = gA * (-cc * cc * idet2) + gB * (bb * cc * idet2) + gC * (idet - aa * cc * idet2);
+                const float gb = gA * (2.f * bb * cc * idet2) + gB * (-idet - 2.f * bb * bb * idet2) + gC * (2.f * aa * bb * idet2);
+                const float gc = gA * (idet - aa * cc * idet2) + gB * (aa * bb * idet2) + gC * (-aa * aa * idet2);
+                const float G2[2][2] = {{ga, 0.5f * gb}, {0.5f * gb, gc}};
+                // dL/dSigma = T^T G2 T ; dL/dT = 2 G2 T Sigma
+                float GT[2][3];
+                for (int r2 = 0; r2 < 2; r2++)
+                    for (int k = 0; k < 3; k++) GT[r2][k] = G2[r2][0] * T[0][k] + G2[r2][1] * T[1][k];
+                for (int p = 0; p < 3; p++)
+                    for (int c2 = 0; c2 < 3; c2++) gSsum[p][c2] += T[0][p] * GT[0][c2] + T[1][p] * GT[1][c2];
+                float gT[2][3];
+                for (int r2 = 0; r2 < 2; r2++)
+                    for (int k = 0; k < 3; k++)
+                        gT[r2][k] = 2.f * (GT[r2][0] * Sg[0][k] + GT[r2][1] * Sg[1][k] + GT[r2][2] * Sg[2][k]);
+                float gJ[2][3];
+                for (int r2 = 0; r2 < 2; r2++)
+                    for (int k = 0; k < 3; k++) gJ[r2][k] = gT[r2][0] * W[3 * k] + gT[r2][1] * W[3 * k + 1] + gT[r2][2] * W[3 * k + 2];
+                float gt[3] = {0.f, 0.f, 0.f};
+                gt[2] += gJ[0][0] * (-fx * itz2) + gJ[1][1] * (-fy * itz2);
+                if (!clx) { gt[0] += gJ[0][2] * (-fx * itz2); gt[2] += gJ[0][2] * (2.f * fx * t[0] * itz2 * itz); }
+                else      { gt[2] += gJ[0][2] * (fx * xc * itz2); }
+                if (!cly) { gt[1] += gJ[1][2] * (-fy * itz2); gt[2] += gJ[1][2] * (2.f * fy * t[1] * itz2 * itz); }
+                else      { gt[2] += gJ[1][2] * (fy * yc * itz2); }
+                gt[0] += gu * fx * itz;
+                gt[1] += gv * fy * itz;
+                gt[2] += -(gu * fx * t[0] + gv * fy * t[1]) * itz2;
+                for (int k = 0; k < 3; k++) gm[k] += W[k] * gt[0] + W[3 + k] * gt[1] + W[6 + k] * gt[2];
+                gop += go * o * (1.f - o);
+                // colour: rgb = max(sum_k sh_k Y_k(d) + 0.5, 0), d = (mu - campos) / |mu - campos|
+                const float dv[3] = {m[0] - cam.campos[0], m[1] - cam.campos[1], m[2] - cam.campos[2]};
+                const float dn = sqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+                const float idn = 1.f / dn;
+                const float d[3] = {dv[0] * idn, dv[1] * idn, dv[2] * idn};
+                float Y[16], dY[16][3];
+                sh_basis(d[0], d[1], d[2], Y);
+                sh_basis_grad(d[0], d[1], d[2], dY);
+                const uint8_t cm = a.clampm[r];
+                float gd[3] = {0.f, 0.f, 0.f};
+                for (int ch = 0; ch < 3; ch++) {
+                    if (cm & (1u << ch)) continue;
+                    const float gr = grgb[ch];
+                    for (int k = 0; k < 16; k++) {
+                        const float coef = a.g.sh[(long long)(3 * k + ch) * n + i];
+                        gsh[3 * k + ch] += gr * Y[k];
+                        gd[0] += gr * coef * dY[k][0];
+                        gd[1] += gr * coef * dY[k][1];
+                        gd[2] += gr * coef * dY[k][2];
+                    }
+                }
+                const float ddot = d[0] * gd[0] + d[1] * gd[1] + d[2] * gd[2];
+                for (int e = 0; e < 3; e++) gm[e] += (gd[e] - d[e] * ddot) * idn;
+            }
+            // Sigma = M M^T with M = Q diag(s)
+            float gSs[3][3];
+            for (int p = 0; p < 3; p++)
+                for (int c2 = 0; c2 < 3; c2++) gSs[p][c2] = 0.5f * (gSsum[p][c2] + gSsum[c2][p]);
+            float gM[3][3];
+            for (int p = 0; p < 3; p++)
+                for (int c2 = 0; c2 < 3; c2++)
+                    gM[p][c2] = 2.f * (gSs[p][0] * M[0][c2] + gSs[p][1] * M[1][c2] + gSs[p][2] * M[2][c2]);
+            float gs[3] = {0.f, 0.f, 0.f}, gQ[3][3];
+            for (int p = 0; p < 3; p++)
+                for (int c2 = 0; c2 < 3; c2++) { gs[c2] += gM[p][c2] * Q[p][c2]; gQ[p][c2] = gM[p][c2] * s[c2]; }
+            for (int k = 0; k < 3; k++) gls[k] = gs[k] * s[k];
+            // rotation matrix of the unit quaternion
+            gq[0] = 2.f * (-z * gQ[0][1] + y * gQ[0][2] + z * gQ[1][0] - x * gQ[1][2] - y * gQ[2][0] + x * gQ[2][1]);
+            gq[1] = 2.f * (y * gQ[0][1] + z * gQ[0][2] + y * gQ[1][0] - 2.f * x * gQ[1][1] - w * gQ[1][2] + z * gQ[2][0] + w * gQ[2][1] - 2.f * x * gQ[2][2]);
+            gq[2] = 2.f * (-2.f * y * gQ[0][0] + x * gQ[0][1] + w * gQ[0][2] + x * gQ[1][0] + z * gQ[1][2] - w * gQ[2][0] + z * gQ[2][1] - 2.f * y * gQ[2][2]);
+            gq[3] = 2.f * (-2.f * z * gQ[0][0] - w * gQ[0][1] + x * gQ[0][2] + w * gQ[1][0] - 2.f * z * gQ[1][1] + y * gQ[1][2] + x * gQ[2][0] + y * gQ[2][1]);
+            const float qdot = q[0] * gq[0] + q[1] * gq[1] + q[2] * gq[2] + q[3] * gq[3];
+            for (int k = 0; k < 4; k++) gq[k] = (gq[k] - q[k] * qdot) / qn;
+            if (a.absgrad) a.absgrad[i] += absacc;
+            // scale regulariser (Eq. 5): beta / |V| * min_j s_j on the first smallest axis
+            if (a.beta > 0.f) {
+                int jm = 0;
+                if (s[1] < s[jm]) jm = 1;
+                if (s[2] < s[jm]) jm = 2;
+                const float nv = (float)a.ctr->n_visible;
+                gls[jm] += a.beta * s[jm] / nv;
+                smin_val = s[jm];
+            }
+        }
+        if (has || !a.accumulate) {
+            for (int k = 0; k < 3; k++) {
+                store_grad(&a.gmean[k * n + i], gm[k], a.accumulate);
+                store_grad(&a.gls[k * n + i], gls[k], a.accumulate);
+            }
+            for (int k = 0; k < 4; k++) store_grad(&a.gquat[k * n + i], gq[k], a.accumulate);
+            store_grad(&a.gop[i], gop, a.accumulate);
+            for (int k = 0; k < 48; k++) store_grad(&a.gsh[(long long)k * n + i], gsh[k], a.accumulate);
+        }
+    }
+    if (a.red_partial) {
+        float v = smin_val;
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) a.red_partial[blockIdx.x] = s_red[0] + s_red[1] + s_red[2] + s_red[3];
+    }
+}
+
+__global__ void scale_reg_finalize_kernel(const float *partial, int nblocks, float beta, const DevCounters *ctr,
+                                          float *out)
+{
+    __shared__ double s[256];
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += 256) acc += (double)partial[b];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double nv = (double)ctr->n_visible;
+        *out = nv > 0 ? (float)(beta * s[0] / nv) : 0.f;
+    }
+}
+
+cudaError_t launch_preprocess_bwd(gs_workspace *ws, cudaStream_t st, const gs_gaussians &g,
+                                  const gs_gaussian_grads &gr, int accumulate, float *absgrad, float beta,
+                                  float *scale_reg_value)
+{
+    const long long n = g.n;
+    if (n == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((n + 127) / 128);
+    BwdArgs a;
+    a.g = GaussPtrs{g.mean, g.log_scale, g.quat, g.opacity_logit, g.sh, g.lod, n};
+    a.gmean = gr.mean; a.gls = gr.log_scale; a.gquat = gr.quat; a.gop = gr.opacity_logit; a.gsh = gr.sh;
+    a.rec_off = ws->rec_off; a.rec_cam = ws->rec_cam; a.clampm = ws->clampm; a.rgrad = ws->rgrad;
+    a.absgrad = absgrad; a.accumulate = accumulate; a.beta = beta;
+    const bool reduce = beta > 0.f && scale_reg_value && blocks <= ws->red_words;
+    a.red_partial = reduce ? ws->red_partial : nullptr;
+    a.ctr = ws->ctr;
+    preprocess_bwd_kernel<<<blocks, 128, 0, st>>>(a, ws->cams, ws->rc);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (reduce) {
+        scale_reg_finalize_kernel<<<1, 256, 0, st>>>(ws->red_partial, (int)blocks, beta, ws->ctr, scale_reg_value);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+} // namespace gs

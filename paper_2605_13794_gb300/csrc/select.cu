@@ -1,0 +1,276 @@
+// select.cu -- importance-pass outputs (Sec. 3.2, Fig. 2; Sec. 3.3, Eq. 3).
+//
+// From the per-(record, tile) slots of the colourless sweep:
+//   w_{i,v}, a_{i,v}             per record, summed over its tiles in order;
+//   s_i += w/(a + eps) (a > 0), c^rad_i += 1   per Gaussian over its records;
+//   c^vis_{i,v}: the smallest set of largest w carrying vis_mass of the view's
+//   total w, ties toward the lower Gaussian index; Cull = 1 - c^vis.
+// The selection sorts each view's records by w (descending, stable), takes an
+// FP64 inclusive scan in a fixed (reduce-then-scan) association, and marks
+// every entry whose exclusive prefix is still below vis_mass * total.
+#include "gs_internal.cuh"
+
+namespace gs {
+
+cudaError_t launch_importance_raster(gs_workspace *ws, cudaStream_t st);
+
+__global__ void __launch_bounds__(256) imp_reduce_kernel(const uint32_t *drec, const uint32_t *inst_off,
+                                                         const uint32_t *tt, const float2 *slots, float *imp_w,
+                                                         uint32_t *imp_a, const DevCounters *ctr)
+{
+    const unsigned long long k = (unsigned long long)blockIdx.x * 256 + threadIdx.x;
+    if (k >= ctr->n_records) return;
+    const uint32_t r = drec[k];
+    const unsigned long long off = inst_off[r], cnt = tt[r];
+    float w = 0.f;
+    uint32_t a = 0;
+    if (off + cnt <= ctr->n_instances) {
+        for (unsigned long long t = 0; t < cnt; t++) {
+            const float2 s = slots[off + t];
+            w += s.x;
+            a += __float_as_uint(s.y);
+        }
+    }
+    imp_w[r] = w;
+    imp_a[r] = a;
+}
+
+struct ImpGaussArgs {
+    const uint32_t *rec_off;
+    const uint16_t *rec_cam;
+    const float *imp_w;
+    const uint32_t *imp_a;
+    float *w_out;
+    uint32_t *a_out;
+    float *s_accum;
+    uint32_t *crad;
+    long long n;
+    float eps;
+    const DevCounters *ctr;
+};
+
+__global__ void __launch_bounds__(256) imp_gauss_kernel(ImpGaussArgs a)
+{
+    const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (i >= a.n) return;
+    const unsigned long long nrec = a.ctr->n_records;
+    unsigned long long r0 = a.rec_off[i], r1 = a.rec_off[i + 1];
+    if (r1 > nrec) r1 = nrec;
+    if (r0 >= r1) return;
+    float s = 0.f;
+    for (unsigned long long r = r0; r < r1; r++) {
+        const float w = a.imp_w[r];
+        const uint32_t cnt = a.imp_a[r];
+        if (cnt > 0) s += w / ((float)cnt + a.eps);
+        const int c = a.rec_cam[r];
+        if (a.w_out) a.w_out[(long long)c * a.n + i] = w;
+        if (a.a_out) a.a_out[(long long)c * a.n + i] = cnt;
+    }
+    if (a.s_accum) a.s_accum[i] += s;
+    if (a.crad) a.crad[i] += (uint32_t)(r1 - r0);
+}
+
+// keys = bit-complement of the FP32 bits of w (w >= 0), so ascending keys are
+// descending w and w = 0 sorts last.
+__global__ void sel_keys_kernel(const float *imp_w, uint32_t *keys, const DevCounters *ctr)
+{
+    const unsigned long long r = (unsigned long long)blockIdx.x * 256 + threadIdx.x;
+    if (r < ctr->n_records) keys[r] = ~__float_as_uint(imp_w[r]);
+}
+
+__global__ void sel_camkeys_kernel(const uint32_t *vals, const uint16_t *rec_cam, uint32_t *keys,
+                                   const DevCounters *ctr)
+{
+    const unsigned long long k = (unsigned long long)blockIdx.x * 256 + threadIdx.x;
+    if (k < ctr->n_records) keys[k] = rec_cam[vals[k]];
+}
+
+constexpr int kScanTile = 4096;
+
+// Per-block FP64 sums of w in sorted order (fixed association).
+__global__ void __launch_bounds__(256) sel_block_sum_kernel(const uint32_t *vals, const float *imp_w, double *bsum,
+                                                            const DevCounters *ctr)
+{
+    __shared__ double s[256];
+    const unsigned long long n = ctr->n_records;
+    const unsigned long long base = (unsigned long long)blockIdx.x * kScanTile;
+    double acc = 0.0;
+    if (base < n) {
+        for (int j = 0; j < kScanTile / 256; j++) {
+            const unsigned long long k = base + (unsigned long long)threadIdx.x * (kScanTile / 256) + j;
+            if (k < n) acc += (double)imp_w[vals[k]];
+        }
+    }
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = s[0];
+}
+
+// Exclusive scan of the block sums, one block, sequential chunks per thread.
+__global__ void sel_block_scan_kernel(double *bsum, int nblocks)
+{
+    __shared__ double s[256];
+    const int per = (nblocks + 255) / 256;
+    const int b0 = threadIdx.x * per;
+    double acc = 0.0;
+    for (int b = b0; b < b0 + per && b < nblocks; b++) acc += bsum[b];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double run = 0.0;
+        for (int t = 0; t < 256; t++) { const double v = s[t]; s[t] = run; run += v; }
+    }
+    __syncthreads();
+    double run = s[threadIdx.x];
+    for (int b = b0; b < b0 + per && b < nblocks; b++) { const double v = bsum[b]; bsum[b] = run; run += v; }
+}
+
+// Inclusive prefix of w in sorted order: cum[k].
+__global__ void __launch_bounds__(256) sel_scan_kernel(const uint32_t *vals, const float *imp_w, const double *boff,
+                                                       double *cum, const DevCounters *ctr)
+{
+    __shared__ double s[256];
+    const unsigned long long n = ctr->n_records;
+    const unsigned long long base = (unsigned long long)blockIdx.x * kScanTile;
+    if (base >= n) return;
+    constexpr int per = kScanTile / 256;
+    double v[per];
+    double acc = 0.0;
+    for (int j = 0; j < per; j++) {
+        const unsigned long long k = base + (unsigned long long)threadIdx.x * per + j;
+        v[j] = k < n ? (double)imp_w[vals[k]] : 0.0;
+        acc += v[j];
+    }
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double run = boff[blockIdx.x];
+        for (int t = 0; t < 256; t++) { const double x = s[t]; s[t] = run; run += x; }
+    }
+    __syncthreads();
+    double run = s[threadIdx.x];
+    for (int j = 0; j < per; j++) {
+        const unsigned long long k = base + (unsigned long long)threadIdx.x * per + j;
+        run += v[j];
+        if (k < n) cum[k] = run;
+    }
+}
+
+// Camera segments of the cam-major sorted order.
+__global__ void sel_segments_kernel(const uint32_t *vals, const uint16_t *rec_cam, uint2 *seg, const DevCounters *ctr)
+{
+    const unsigned long long n = ctr->n_records;
+    for (unsigned long long k = (unsigned long long)blockIdx.x * 256 + threadIdx.x; k < n;
+         k += (unsigned long long)gridDim.x * 256) {
+        const int c = rec_cam[vals[k]];
+        if (k == 0 || rec_cam[vals[k - 1]] != c) seg[c].x = (uint32_t)k;
+        if (k == n - 1 || rec_cam[vals[k + 1]] != c) seg[c].y = (uint32_t)(k + 1);
+    }
+}
+
+struct SelApplyArgs {
+    const uint32_t *vals;
+    const uint32_t *rec_g;
+    const uint16_t *rec_cam;
+    const float *imp_w;
+    const double *cum;
+    const uint2 *seg;
+    uint32_t *cull_out;
+    uint32_t *cvis;
+    long long words;
+    float vis_mass;
+    const DevCounters *ctr;
+};
+
+__global__ void sel_apply_kernel(SelApplyArgs a)
+{
+    const unsigned long long n = a.ctr->n_records;
+    for (unsigned long long k = (unsigned long long)blockIdx.x * 256 + threadIdx.x; k < n;
+         k += (unsigned long long)gridDim.x * 256) {
+        const uint32_t r = a.vals[k];
+        const float w = a.imp_w[r];
+        if (!(w > 0.f)) continue;
+        const int c = a.rec_cam[r];
+        const uint2 sg = a.seg[c];
+        const double before = sg.x > 0 ? a.cum[sg.x - 1] : 0.0;
+        const double total = a.cum[sg.y - 1] - before;
+        const double excl = (k > 0 ? a.cum[k - 1] : 0.0) - before;
+        if (excl < (double)a.vis_mass * total) {
+            const uint32_t g = a.rec_g[r];
+            if (a.cull_out) atomicAnd(&a.cull_out[(long long)c * a.words + (g >> 5)], ~(1u << (g & 31)));
+            if (a.cvis) atomicAdd(&a.cvis[g], 1u);
+        }
+    }
+}
+
+// Cull words start at "culled" for every valid bit.
+__global__ void cull_init_kernel(uint32_t *cull, long long words, long long n, int n_cams)
+{
+    const long long total = words * n_cams;
+    for (long long k = (long long)blockIdx.x * 256 + threadIdx.x; k < total; k += (long long)gridDim.x * 256) {
+        const long long wi = k % words;
+        const long long bits = n - wi * 32;
+        cull[k] = bits >= 32 ? 0xffffffffu : ((1u << bits) - 1u);
+    }
+}
+
+cudaError_t launch_importance(gs_workspace *ws, cudaStream_t st, float *w, uint32_t *a, float *s_accum,
+                              uint32_t *crad, uint32_t *cvis, uint32_t *cull_out)
+{
+    cudaError_t e;
+    const long long n = ws->g.n;
+    const int ncam = ws->cams.n;
+    const unsigned long long rcap = (unsigned long long)ws->cap.max_records;
+    const unsigned rblocks = (unsigned)((rcap + 255) / 256);
+    if ((e = launch_importance_raster(ws, st)) != cudaSuccess) return e;
+    imp_reduce_kernel<<<rblocks, 256, 0, st>>>(ws->dval[ws->depth_buf], ws->inst_off, ws->tt,
+                                                reinterpret_cast<const float2 *>(ws->slots), ws->imp_w, ws->imp_a,
+                                                ws->ctr);
+    if (w && (e = cudaMemsetAsync(w, 0, (size_t)ncam * n * sizeof(float), st)) != cudaSuccess) return e;
+    if (a && (e = cudaMemsetAsync(a, 0, (size_t)ncam * n * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    if (n > 0) {
+        ImpGaussArgs ga{ws->rec_off, ws->rec_cam, ws->imp_w, ws->imp_a, w, a, s_accum, crad, n, ws->rc.eps_score,
+                        ws->ctr};
+        imp_gauss_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ga);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (!cull_out && !cvis) return cudaSuccess;
+    const long long words = (n + 31) / 32;
+    if (cull_out && words > 0)
+        cull_init_kernel<<<1216, 256, 0, st>>>(cull_out, words, n, ncam);
+    // sort records by w descending (stable), then by camera (stable); own
+    // buffers, so the depth order stays valid for a later backward
+    uint32_t *sk[2] = {ws->selk[0], ws->selk[1]};
+    uint32_t *sv[2] = {ws->selv[0], ws->selv[1]};
+    sel_keys_kernel<<<rblocks, 256, 0, st>>>(ws->imp_w, sk[0], ws->ctr);
+    int ob = 0;
+    const unsigned long long *cnt = &ws->ctr->n_records;
+    if ((e = launch_radix_sort(ws, st, sk, sv, cnt, rcap, 32, true, false, ob)) != cudaSuccess) return e;
+    uint32_t *sorted = sv[ob];
+    if (ncam > 1) {
+        uint32_t *k2[2] = {sk[ob ^ 1], sk[ob]};
+        uint32_t *v2[2] = {sv[ob], sv[ob ^ 1]};
+        sel_camkeys_kernel<<<rblocks, 256, 0, st>>>(v2[0], ws->rec_cam, k2[0], ws->ctr);
+        int ob2 = 0;
+        if ((e = launch_radix_sort(ws, st, k2, v2, cnt, rcap, 8, false, false, ob2)) != cudaSuccess) return e;
+        sorted = v2[ob2];
+    }
+    const unsigned sblocks = (unsigned)((rcap + kScanTile - 1) / kScanTile);
+    double *bsum = reinterpret_cast<double *>(ws->red_partial);
+    sel_block_sum_kernel<<<sblocks, 256, 0, st>>>(sorted, ws->imp_w, bsum, ws->ctr);
+    sel_block_scan_kernel<<<1, 256, 0, st>>>(bsum, (int)sblocks);
+    sel_scan_kernel<<<sblocks, 256, 0, st>>>(sorted, ws->imp_w, bsum, ws->sel_cum, ws->ctr);
+    uint2 *seg = reinterpret_cast<uint2 *>(ws->rx_hist); // 64 uint2 fit in the histogram scratch
+    if ((e = cudaMemsetAsync(seg, 0, GS_MAX_CAMERAS * sizeof(uint2), st)) != cudaSuccess) return e;
+    sel_segments_kernel<<<1216, 256, 0, st>>>(sorted, ws->rec_cam, seg, ws->ctr);
+    SelApplyArgs sa{sorted, ws->rec_g, ws->rec_cam, ws->imp_w, ws->sel_cum, seg, cull_out, cvis, words,
+                    ws->rc.vis_mass, ws->ctr};
+    sel_apply_kernel<<<1216, 256, 0, st>>>(sa);
+    return cudaGetLastError();
+}
+
+} // namespace gs

@@ -1,0 +1,345 @@
+// sort.cu -- tile/depth binning (App. A: tile-based rasterisation of
+// depth-ordered projected Gaussians).
+//
+// Order of the work:
+//   1. depth sort of the active records: LSD radix sort of the FP32 bits of
+//      camera z (positive, so the bits order like the values), stable, so
+//      equal depths keep record order = (Gaussian, camera) order;
+//   2. emission in depth order: each record writes (global tile id, record)
+//      for every tile of its rectangle; a single-pass look-back scan of the
+//      tiles-touched counts gives the offsets;
+//   3. stable LSD radix sort of the instances by global tile id, which keeps
+//      the depth order inside each tile: the final order is
+//      (camera, tile, depth bits, Gaussian) without ever sorting 64-bit keys;
+//   4. tile ranges from the sorted tile ids.
+// The radix passes are single-pass ("onesweep"): each 4096-key block ranks its
+// keys in shared memory, publishes per-digit counts and finds its global
+// offsets by a per-digit decoupled look-back, so every pass reads and writes
+// each key once.  Item counts stay on the device, so nothing here needs a
+// host synchronisation.
+#include "gs_internal.cuh"
+
+namespace gs {
+
+constexpr uint32_t kRxAgg = 1u << 30;
+constexpr uint32_t kRxInc = 2u << 30;
+constexpr uint32_t kRxVal = (1u << 30) - 1;
+
+__device__ __forceinline__ unsigned long long clamp_count(const unsigned long long *count, unsigned long long cap)
+{
+    unsigned long long c = *count;
+    return c < cap ? c : cap;
+}
+
+// Histograms of all passes in one read of the keys.
+__global__ void __launch_bounds__(256) radix_hist_kernel(const uint32_t *keys, const unsigned long long *count,
+                                                         unsigned long long cap, int passes, uint32_t *hist)
+{
+    __shared__ uint32_t h[4][256];
+    for (int k = threadIdx.x; k < 4 * 256; k += 256) (&h[0][0])[k] = 0;
+    __syncthreads();
+    const unsigned long long n = clamp_count(count, cap);
+    for (unsigned long long i = (unsigned long long)blockIdx.x * 256 + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * 256) {
+        const uint32_t k = keys[i];
+        for (int p = 0; p < passes; p++) atomicAdd(&h[p][(k >> (8 * p)) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < passes * 256; k += 256) {
+        const uint32_t v = (&h[0][0])[k];
+        if (v) atomicAdd(&hist[k], v);
+    }
+}
+
+// Exclusive scan of each pass's 256-bucket histogram.
+__global__ void radix_offsets_kernel(const uint32_t *hist, uint32_t *off, int passes)
+{
+    __shared__ uint32_t s[256];
+    for (int p = 0; p < passes; p++) {
+        uint32_t v = hist[p * 256 + threadIdx.x];
+        s[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < 256; o <<= 1) {
+            uint32_t y = threadIdx.x >= o ? s[threadIdx.x - o] : 0u;
+            __syncthreads();
+            s[threadIdx.x] += y;
+            __syncthreads();
+        }
+        off[p * 256 + threadIdx.x] = s[threadIdx.x] - v;
+        __syncthreads();
+    }
+}
+
+// One stable LSD pass over digit (key >> shift) & 255.
+template <bool VALS_IDENTITY, bool WRITE_KEYS>
+__global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
+    const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
+    uint32_t *__restrict__ vals_out, const unsigned long long *count, unsigned long long cap, int shift,
+    const uint32_t *__restrict__ bucket_off, uint32_t *status /* ticket at [0], then [blocks][256] */,
+    DevCounters *ctr)
+{
+    __shared__ uint32_t s_keys[kSortTile];
+    __shared__ uint32_t s_vals[kSortTile];
+    __shared__ uint32_t s_wcnt[8][256];
+    __shared__ uint32_t s_blk[256];
+    __shared__ uint32_t s_glob[256];
+    __shared__ uint32_t s_warp[8];
+    __shared__ unsigned s_bid;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_bid = atomicAdd(&status[0], 1u);
+    for (int k = tid; k < 8 * 256; k += kSortThreads) (&s_wcnt[0][0])[k] = 0;
+    __syncthreads();
+    const unsigned bid = s_bid;
+    const unsigned long long n = clamp_count(count, cap);
+    const unsigned long long base = (unsigned long long)bid * kSortTile;
+    if (base >= n) return;
+    uint32_t *st = status + 1;
+
+    // load in warp-striped order: item j of lane l is base + warp*512 + j*32 + l
+    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+    const unsigned lt_mask = (1u << lane) - 1u;
+#pragma unroll
+    for (int j = 0; j < kSortItems; j++) {
+        const unsigned long long idx = base + (unsigned long long)warp * (32 * kSortItems) + j * 32 + lane;
+        const bool valid = idx < n;
+        key[j] = valid ? keys_in[idx] : 0u;
+        val[j] = valid ? (VALS_IDENTITY ? (uint32_t)idx : vals_in[idx]) : 0u;
+        const uint32_t d = (key[j] >> shift) & 255u;
+        // peers with the same digit (and valid) via 8 ballots
+        unsigned peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+        for (int b = 0; b < 8; b++) {
+            const unsigned bits = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? bits : ~bits;
+        }
+        const uint32_t before = s_wcnt[warp][d];
+        __syncwarp();
+        rank[j] = before + __popc(peers & lt_mask);
+        if (valid && (peers & lt_mask) == 0) s_wcnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+        if (!valid) key[j] = 0xffffffffu, rank[j] = 0xffffffffu; // marks invalid
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps, block total
+    const int d = tid;
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < 8; w++) {
+        const uint32_t c = s_wcnt[w][d];
+        s_wcnt[w][d] = run;
+        run += c;
+    }
+    const uint32_t dtotal = run;
+    // block-local exclusive scan over digits
+    uint32_t tot;
+    const uint32_t dexcl = block_exclusive_scan_256<uint32_t>(dtotal, s_warp, tot);
+    s_blk[d] = dexcl;
+    // publish aggregate, then per-digit look-back (one thread per digit)
+    volatile uint32_t *vst = st;
+    if (bid == 0) {
+        vst[d] = kRxInc | dtotal;
+        s_glob[d] = bucket_off[d];
+    } else {
+        vst[(unsigned long long)bid * 256 + d] = kRxAgg | dtotal;
+        uint32_t excl = 0;
+        long long pred = (long long)bid - 1;
+        while (pred >= 0) {
+            uint32_t s;
+            unsigned long long spins = 0;
+            while (((s = vst[(unsigned long long)pred * 256 + d]) >> 30) == 0) {
+                if (++spins > kSpinLimit) {
+                    set_error(ctr, GS_ERR_TIMEOUT, kSiteRadix);
+                    s = kRxInc;
+                    break;
+                }
+                __nanosleep(40);
+            }
+            excl += s & kRxVal;
+            if ((s >> 30) == 2) break;
+            pred--;
+        }
+        vst[(unsigned long long)bid * 256 + d] = kRxInc | (excl + dtotal);
+        s_glob[d] = bucket_off[d] + excl;
+    }
+    __syncthreads();
+    // scatter into shared memory in block-sorted order
+#pragma unroll
+    for (int j = 0; j < kSortItems; j++) {
+        if (rank[j] == 0xffffffffu) continue;
+        const uint32_t dd = (key[j] >> shift) & 255u;
+        const uint32_t pos = s_blk[dd] + s_wcnt[warp][dd] + rank[j];
+        s_keys[pos] = key[j];
+        s_vals[pos] = val[j];
+    }
+    __syncthreads();
+    const unsigned long long rem = n - base;
+    const int nvalid = rem < (unsigned long long)kSortTile ? (int)rem : kSortTile;
+    for (int i = tid; i < nvalid; i += kSortThreads) {
+        const uint32_t k = s_keys[i];
+        const uint32_t dd = (k >> shift) & 255u;
+        const unsigned long long out = (unsigned long long)s_glob[dd] + (uint32_t)(i - (int)s_blk[dd]);
+        if (WRITE_KEYS) keys_out[out] = k;
+        vals_out[out] = s_vals[i];
+    }
+}
+
+// LSD radix sort of (key, value) pairs, `bits` significant key bits, count on
+// the device (clamped to cap).  keys[0]/vals[0] hold the input; the sorted
+// result lands in keys[out_buf]/vals[out_buf].  With vals_identity the input
+// values are the item indices and vals[0] is not read.
+cudaError_t launch_radix_sort(gs_workspace *ws, cudaStream_t st, uint32_t *keys[2], uint32_t *vals[2],
+                              const unsigned long long *count, unsigned long long cap, int bits, bool vals_identity,
+                              bool /*unused*/, int &out_buf)
+{
+    const int passes = bits <= 0 ? 1 : (bits + 7) / 8;
+    const unsigned long long blocks = (cap + kSortTile - 1) / kSortTile;
+    cudaError_t e;
+    out_buf = 0;
+    if (cap == 0) return cudaSuccess;
+    if ((e = cudaMemsetAsync(ws->rx_hist, 0, 4 * 256 * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    unsigned hblocks = (unsigned)((cap + 255) / 256);
+    if (hblocks > 1216) hblocks = 1216;
+    radix_hist_kernel<<<hblocks, 256, 0, st>>>(keys[0], count, cap, passes, ws->rx_hist);
+    radix_offsets_kernel<<<1, 256, 0, st>>>(ws->rx_hist, ws->rx_off, passes);
+    int src = 0;
+    for (int p = 0; p < passes; p++) {
+        const int dst = src ^ 1;
+        if ((e = cudaMemsetAsync(ws->rx_status, 0, (blocks * 256 + 1) * sizeof(uint32_t), st)) != cudaSuccess)
+            return e;
+        const bool ident = vals_identity && p == 0;
+        const bool last = p == passes - 1;
+        // the keys of the last pass are needed by the tile-range kernel only
+        if (ident)
+            radix_pass_kernel<true, true><<<(unsigned)blocks, kSortThreads, 0, st>>>(
+                keys[src], vals[src], keys[dst], vals[dst], count, cap, 8 * p, ws->rx_off + 256 * p, ws->rx_status,
+                ws->ctr);
+        else
+            radix_pass_kernel<false, true><<<(unsigned)blocks, kSortThreads, 0, st>>>(
+                keys[src], vals[src], keys[dst], vals[dst], count, cap, 8 * p, ws->rx_off + 256 * p, ws->rx_status,
+                ws->ctr);
+        (void)last;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        src = dst;
+    }
+    out_buf = src;
+    return cudaSuccess;
+}
+
+// ---- emission -------------------------------------------------------------
+
+struct EmitArgs {
+    const uint32_t *drec;   // records in depth order
+    const uint32_t *tt;
+    const uint2 *rect;
+    const uint16_t *rec_cam;
+    uint32_t *inst_off;
+    uint32_t *tkey, *tval;
+    unsigned long long *lb_status; // ticket at word 0
+    DevCounters *ctr;
+    unsigned long long max_instances;
+};
+
+__global__ void __launch_bounds__(256) emit_kernel(EmitArgs a, CamTable ct)
+{
+    __shared__ unsigned s_bid;
+    __shared__ unsigned long long s_warp[8];
+    __shared__ unsigned long long s_base;
+    __shared__ unsigned long long s_incl[256];
+    __shared__ uint32_t s_rec[256];
+    __shared__ uint2 s_rect[256];
+    __shared__ int s_tb[256], s_tx[256];
+    if (threadIdx.x == 0) s_bid = atomicAdd((unsigned *)a.lb_status, 1u);
+    __syncthreads();
+    const unsigned bid = s_bid;
+    const unsigned long long nrec = a.ctr->n_records;
+    const unsigned long long k = (unsigned long long)bid * 256 + threadIdx.x;
+    if ((unsigned long long)bid * 256 >= nrec) return;
+    const bool valid = k < nrec;
+    uint32_t r = 0;
+    unsigned long long c = 0;
+    if (valid) {
+        r = a.drec[k];
+        c = a.tt[r];
+        const int cam = a.rec_cam[r];
+        s_rect[threadIdx.x] = a.rect[r];
+        s_tb[threadIdx.x] = ct.c[cam].tile_base;
+        s_tx[threadIdx.x] = ct.c[cam].tiles_x;
+    }
+    s_rec[threadIdx.x] = r;
+    unsigned long long total;
+    const unsigned long long excl = block_exclusive_scan_256<unsigned long long>(c, s_warp, total);
+    s_incl[threadIdx.x] = excl + c;
+    if (threadIdx.x < 32) {
+        unsigned long long b = lookback_exclusive(a.lb_status + 1, bid, total, a.ctr, kSiteEmit);
+        if (threadIdx.x == 0) s_base = b;
+    }
+    __syncthreads();
+    const unsigned long long base = s_base;
+    if (valid) a.inst_off[r] = (uint32_t)(base + excl);
+    if (k == nrec - 1) {
+        const unsigned long long end = base + excl + c;
+        a.ctr->instances_needed = end;
+        a.ctr->n_instances = end < a.max_instances ? end : a.max_instances;
+        if (end > a.max_instances) set_error(a.ctr, GS_ERR_CAPACITY, kSiteEmit);
+    }
+    // cooperative, coalesced emission of the block's instances
+    for (unsigned long long j = threadIdx.x; j < total; j += 256) {
+        const unsigned long long gi = base + j;
+        if (gi >= a.max_instances) break;
+        // record kk: first with inclusive prefix > j
+        int lo = 0, hi = 255;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s_incl[mid] > j) hi = mid; else lo = mid + 1;
+        }
+        const unsigned long long first = lo ? s_incl[lo - 1] : 0ull;
+        const uint32_t local = (uint32_t)(j - first);
+        int x0, y0, x1, y1;
+        unpack_rect(s_rect[lo], x0, y0, x1, y1);
+        const uint32_t w = (uint32_t)(x1 - x0);
+        const int tx = x0 + (int)(local % w), ty = y0 + (int)(local / w);
+        a.tkey[gi] = (uint32_t)(s_tb[lo] + ty * s_tx[lo] + tx);
+        a.tval[gi] = s_rec[lo];
+    }
+}
+
+cudaError_t launch_emit(gs_workspace *ws, cudaStream_t st)
+{
+    const unsigned long long cap = (unsigned long long)ws->cap.max_records;
+    const unsigned blocks = (unsigned)((cap + 255) / 256);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(ws->lb_status, 0, (blocks + 1) * sizeof(unsigned long long), st)) != cudaSuccess)
+        return e;
+    EmitArgs a;
+    a.drec = ws->dval[ws->depth_buf];
+    a.tt = ws->tt; a.rect = ws->rect; a.rec_cam = ws->rec_cam; a.inst_off = ws->inst_off;
+    a.tkey = ws->tkey[0]; a.tval = ws->tval[0];
+    a.lb_status = ws->lb_status; a.ctr = ws->ctr; a.max_instances = (unsigned long long)ws->cap.max_instances;
+    emit_kernel<<<blocks, 256, 0, st>>>(a, ws->cams);
+    return cudaGetLastError();
+}
+
+// ---- tile ranges ------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) ranges_kernel(const uint32_t *keys, const DevCounters *ctr, uint2 *ranges)
+{
+    const unsigned long long n = ctr->n_instances;
+    for (unsigned long long s = (unsigned long long)blockIdx.x * 256 + threadIdx.x; s < n;
+         s += (unsigned long long)gridDim.x * 256) {
+        const uint32_t t = keys[s];
+        if (s == 0 || keys[s - 1] != t) ranges[t].x = (uint32_t)s;
+        if (s == n - 1 || keys[s + 1] != t) ranges[t].y = (uint32_t)(s + 1);
+    }
+}
+
+cudaError_t launch_ranges(gs_workspace *ws, cudaStream_t st)
+{
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(ws->ranges, 0, (size_t)ws->cams.total_tiles * sizeof(uint2), st)) != cudaSuccess)
+        return e;
+    ranges_kernel<<<152 * 8, 256, 0, st>>>(ws->tkey[ws->tile_buf], ws->ctr, ws->ranges);
+    return cudaGetLastError();
+}
+
+} // namespace gs

@@ -1,0 +1,312 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Bars: bit-exact for integer work (active records, tile rectangles and counts,
+sorted per-tile lists, n_contrib); images within 1e-4 max-abs; gradients and
+importance scores within 1e-3 relative.  Decisions that the oracle flags as
+lying within its tie band of a threshold are excluded from exact comparison
+and must stay rare.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2605_13794_gb300 import binding as B
+from paper_2605_13794_gb300 import synth
+from tests.gpu_helpers import GpuRun, assert_grad_close, capacity_for, gpu_params, grads_to_host, unpack_rect
+
+pytestmark = pytest.mark.gpu
+
+GEOM_TIES = O.TIE_LOD | O.TIE_NEAR | O.TIE_DET | O.TIE_RADIUS | O.TIE_RECT
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2605_13794_gb300 import build
+    build.build()
+    O.build()
+    assert torch.cuda.is_available()
+
+
+def _compare_view(run: GpuRun, c, g64, cam, P, cull=None, check_image=True):
+    """Compares one camera of a GPU run with the oracle; returns the oracle forward."""
+    fwd = O.forward_view(g64, cam, P, cull)
+    pr = fwd["proj"]
+    n = g64["opacity_logit"].shape[0]
+    tie = (pr["tie"] & GEOM_TIES) != 0
+    ora_active = pr["status"] == O.ACTIVE
+    recs = run.records_of(c)
+    gpu_active = np.zeros(n, bool)
+    gpu_active[list(recs.keys())] = True
+    mism = np.nonzero(gpu_active != ora_active)[0]
+    assert tie[mism].all(), f"active-set mismatch outside tie bands: {mism[~tie[mism]][:10]}"
+    assert tie.sum() <= max(3, 1e-3 * n)
+    both = np.nonzero(gpu_active & ora_active & ~tie)[0]
+    ridx = np.array([recs[i] for i in both], np.int64)
+    # integer parity: rectangles, tiles touched, depth key bits
+    assert np.array_equal(unpack_rect(run.rect[ridx]), pr["rect"][both])
+    assert np.array_equal(run.tt[ridx].astype(np.int64), pr["tiles"][both].astype(np.int64))
+    assert np.array_equal(run.depth_bits[ridx], pr["depth32"][both].view(np.uint32))
+    # continuous projected values (FP32 vs FP64)
+    np.testing.assert_allclose(run.rd0[ridx, :2], pr["uv"][both], rtol=0, atol=2e-3)
+    con = np.concatenate([run.rd0[ridx, 2:4], run.rd1[ridx, :1]], 1)
+    np.testing.assert_allclose(con, pr["conic"][both], rtol=2e-4, atol=1e-7)
+    np.testing.assert_allclose(run.rd1[ridx, 1], pr["opacity"][both], rtol=1e-6, atol=1e-7)
+    rgb = np.concatenate([run.rd1[ridx, 2:4], run.rd2[ridx, None]], 1)
+    np.testing.assert_allclose(rgb, pr["rgb"][both], rtol=0, atol=2e-5)
+    # sorted per-tile lists (ties removed from both sides)
+    ts, lst = fwd["bins"]
+    glists = run.tile_lists(c)
+    tied = set(np.nonzero(tie)[0].tolist())
+    for t, gl in enumerate(glists):
+        ol = lst[ts[t]:ts[t + 1]]
+        if tied:
+            gl = [x for x in gl.tolist() if x not in tied]
+            ol = [x for x in ol.tolist() if x not in tied]
+        assert np.array_equal(np.asarray(gl, np.int64), np.asarray(ol, np.int64)), f"tile {t} list differs"
+    if not check_image:
+        return fwd
+    # image: 1e-4 max-abs outside flagged pixels and outside tiles of tied Gaussians
+    ok = fwd["flags"] == 0
+    if tied:
+        tx, _ = O.tiles_of(cam, P)
+        for i in tied:
+            x0, y0, x1, y1 = pr["rect"][i]
+            ok[max(0, y0 - 1) * 16:(y1 + 1) * 16, max(0, x0 - 1) * 16:(x1 + 1) * 16] = False
+    assert ok.mean() > 0.99
+    img = run.image(c)
+    err = np.abs(img - fwd["image"]).max(axis=0)
+    assert err[ok].max() <= 1e-4, f"image max err {err[ok].max():.3e}"
+    assert np.abs(run.T_final(c) - fwd["T"])[ok].max() <= 1e-4
+    assert np.array_equal(run.n_contrib_img(c)[ok], fwd["n_contrib"][ok].astype(np.int64))
+    return fwd
+
+
+def test_plain_view_forward_parity():
+    g = synth.plain_scene()
+    cam = synth.plain_camera()
+    P = O.Params()
+    run = GpuRun(g, [cam], P)
+    assert run.counts["n_records"] == run.counts["records_needed"]
+    _compare_view(run, 0, O.gaussians64(g), cam, P)
+
+
+@pytest.mark.parametrize("bg", [(0.0, 0.0, 0.0), (0.2, 0.5, 1.0)])
+def test_ragged_image_and_background(bg):
+    # 250 x 170: partial tiles on the right and bottom edges
+    g = synth.plain_scene(6000, seed=7)
+    cam = synth.plain_camera(250, 170, 260.0)
+    P = O.Params(bg=bg)
+    run = GpuRun(g, [cam], P)
+    _compare_view(run, 0, O.gaussians64(g), cam, P)
+
+
+def test_multi_camera_forward_parity():
+    g = synth.plain_scene(8000, seed=9)
+    cams = [synth.plain_camera(256, 256, 300.0), synth.plain_camera(200, 120, 180.0),
+            synth.look_at_camera((0.6, -0.4, -0.5), (0.0, 0.0, 4.0), (0.0, -1.0, 0.0), 160, 144, 60.0)]
+    P = O.Params()
+    run = GpuRun(g, cams, P)
+    g64 = O.gaussians64(g)
+    for c, cam in enumerate(cams):
+        _compare_view(run, c, g64, cam, P)
+
+
+def test_lod_gate_and_cull_mask_parity():
+    rng = np.random.default_rng(12)
+    g = synth.plain_scene(8000, seed=13)
+    g.lod[:] = rng.integers(0, 6, g.n).astype(np.uint8)
+    cam = synth.plain_camera(192, 192, 220.0)
+    cull = synth.random_cull_bits(g.n, 0.3, seed=14)
+    # d0 so that distances 2..6 fall across levels 1..3
+    P = O.Params(lod_enable=True, lod_d0=16.0, lod_Lmax=4, cull_enable=True)
+    run = GpuRun(g, [cam], P, cull=cull)
+    fwd = _compare_view(run, 0, O.gaussians64(g), cam, P, cull=cull)
+    st = fwd["proj"]["status"]
+    assert (st == O.GATED_LOD).sum() > 1000 and (st == O.GATED_CULL).sum() > 1000
+
+
+def test_empty_and_fully_gated_scenes():
+    cam = synth.plain_camera(64, 48, 100.0)
+    P = O.Params()
+    g = synth.plain_scene(500, seed=15)
+    g.mean[2] = -1.0  # all behind the camera
+    run = GpuRun(g, [cam], P)
+    assert run.counts["n_records"] == 0 and run.counts["n_instances"] == 0
+    assert np.allclose(run.image(0), 0.0) and np.allclose(run.T_final(0), 1.0)
+    g0 = synth.plain_scene(0, seed=16)
+    run0 = GpuRun(g0, [cam], P, cap=capacity_for(1, [cam]))
+    assert run0.counts["n_records"] == 0 and np.allclose(run0.T_final(0), 1.0)
+
+
+def test_capacity_overflow_is_reported():
+    g = synth.plain_scene(4000, seed=17)
+    cam = synth.plain_camera()
+    P = O.Params()
+    cap = capacity_for(g.n, [cam], instances=2000)
+    with pytest.raises(B.GSError) as ei:
+        GpuRun(g, [cam], P, cap=cap)
+    assert ei.value.code == B.GS_ERR_CAPACITY
+
+
+def _backward(run: GpuRun, dL):
+    grads = run.gt.zeros_like()
+    dLt = torch.from_numpy(np.ascontiguousarray(dL, np.float32).ravel()).cuda()
+    run.ws.render_bwd(run.gt, dLt, grads, accumulate=False)
+    run.ws.sync_status()
+    return grads_to_host(grads)
+
+
+@pytest.mark.parametrize("seed", [21, 22])
+def test_backward_parity(seed):
+    g = synth.plain_scene(3000, seed=seed)
+    cam = synth.plain_camera(128, 112, 160.0)
+    P = O.Params()
+    run = GpuRun(g, [cam], P)
+    g64 = O.gaussians64(g)
+    fwd = _compare_view(run, 0, g64, cam, P)
+    dL = np.random.default_rng(seed + 100).standard_normal((3, cam.height, cam.width))
+    gg = _backward(run, dL)
+    og = O.backward_view(g64, fwd, cam, P, dL)
+    for k in ("mean", "log_scale", "quat", "opacity_logit", "sh"):
+        assert_grad_close(k, gg[k], og[k])
+
+
+def test_backward_multi_camera_accumulates():
+    g = synth.plain_scene(3000, seed=23)
+    cams = [synth.plain_camera(128, 128, 160.0), synth.plain_camera(96, 80, 120.0)]
+    P = O.Params(bg=(0.1, 0.2, 0.3))
+    run = GpuRun(g, cams, P)
+    g64 = O.gaussians64(g)
+    rng = np.random.default_rng(24)
+    dLs = [rng.standard_normal((3, c.height, c.width)) for c in cams]
+    gg = _backward(run, np.concatenate([d.ravel() for d in dLs]))
+    og = O.zero_grads(g.n)
+    for c, cam in enumerate(cams):
+        fwd = _compare_view(run, c, g64, cam, P)
+        O.backward_view(g64, fwd, cam, P, dLs[c], og)
+    for k in ("mean", "log_scale", "quat", "opacity_logit", "sh"):
+        assert_grad_close(k, gg[k], og[k])
+
+
+def test_deterministic_reruns():
+    g = synth.plain_scene(5000, seed=25)
+    cam = synth.plain_camera()
+    P = O.Params()
+    dL = np.random.default_rng(26).standard_normal((3, cam.height, cam.width))
+    outs = []
+    for _ in range(2):
+        run = GpuRun(g, [cam], P)
+        gg = _backward(run, dL)
+        outs.append((run.image(0), gg))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    for k in outs[0][1]:
+        assert np.array_equal(outs[0][1][k], outs[1][1][k]), k
+
+
+def _importance(run: GpuRun, n, ncam):
+    dev = "cuda"
+    w = torch.zeros(ncam * n, device=dev)
+    a = torch.zeros(ncam * n, device=dev, dtype=torch.int32)
+    s = torch.zeros(n, device=dev)
+    crad = torch.zeros(n, device=dev, dtype=torch.int32)
+    cvis = torch.zeros(n, device=dev, dtype=torch.int32)
+    words = (n + 31) // 32
+    cull = torch.zeros(ncam * words, device=dev, dtype=torch.int32)
+    run.ws.importance(w, a, s, crad, cvis, cull)
+    run.ws.sync_status()
+    h = lambda t: t.cpu().numpy()
+    return dict(w=h(w).reshape(ncam, n).astype(np.float64), a=h(a).reshape(ncam, n), s=h(s).astype(np.float64),
+                crad=h(crad), cvis=h(cvis), cull=h(cull).view(np.uint32).reshape(ncam, words))
+
+
+def _check_visible_set(vis_gpu, w_ref, vis_mass):
+    """c^vis validity: the GPU set differs from the oracle's only by entries
+    whose w is within 1e-3 of the oracle's cut value, and carries the mass."""
+    vis_ref = O.visible_top_mass(w_ref, vis_mass)
+    diff = np.nonzero(vis_gpu != vis_ref)[0]
+    if vis_ref.any():
+        cut = w_ref[vis_ref].min()
+        assert np.all(np.abs(w_ref[diff] - cut) <= 1e-3 * cut + 1e-12), diff[:10]
+    total = w_ref.sum()
+    assert w_ref[vis_gpu].sum() >= vis_mass * total * (1 - 1e-5)
+    assert not np.any(vis_gpu & (w_ref == 0))
+
+
+def test_importance_parity():
+    g = synth.plain_scene(6000, seed=31)
+    cams = [synth.plain_camera(), synth.plain_camera(160, 200, 200.0)]
+    P = O.Params()
+    run = GpuRun(g, cams, P)
+    g64 = O.gaussians64(g)
+    imp = _importance(run, g.n, len(cams))
+    acc = O.new_importance(g.n)
+    vm = float(np.float32(P.vis_mass))
+    for c, cam in enumerate(cams):
+        fwd = _compare_view(run, c, g64, cam, P, check_image=False)
+        view = O.importance_update(acc, fwd["w"], fwd["a"], fwd["proj"], vm, float(np.float32(P.eps_score)))
+        # Gaussians with a flagged pixel in their footprint may differ by one fragment
+        assert_grad_close(f"w[{c}]", imp["w"][c], fwd["w"])
+        a_diff = np.nonzero(imp["a"][c] != fwd["a"].astype(np.int64))[0]
+        assert len(a_diff) <= max(2, int(2e-3 * g.n)), a_diff[:10]
+        vis_gpu = ~synth.unpack_bits(imp["cull"][c], g.n)
+        _check_visible_set(vis_gpu, fwd["w"], vm)
+        # with identical w the sets would be identical; FP32 w moves only near-cut entries
+        assert (vis_gpu != view["cvis"]).sum() <= 2
+    assert_grad_close("s", imp["s"], acc["s"])
+    assert np.array_equal(imp["crad"], acc["crad"])
+    assert np.abs(imp["cvis"] - acc["cvis"]).max() <= 1
+
+
+def test_photometric_loss_parity():
+    rng = np.random.default_rng(41)
+    B_, H, W = 2, 70, 90
+    x = rng.uniform(0, 1, (B_, 3, H, W)).astype(np.float32)
+    y = rng.uniform(0, 1, (B_, 3, H, W)).astype(np.float32)
+    ws = B.Workspace(**capacity_for(1, [synth.plain_camera(W, H)] * B_))
+    xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    loss = torch.zeros(1, device="cuda")
+    dL = torch.empty_like(xt)
+    ws.photometric_loss(xt, yt, 0.2, loss, dL)
+    torch.cuda.synchronize()
+    L_ref, g_ref = O.photometric_loss(x, y, lam=float(np.float32(0.2)))
+    assert abs(loss.item() - L_ref) <= 1e-5 * abs(L_ref)
+    assert_grad_close("dL/dimage", dL.double().cpu().numpy(), g_ref, rtol=1e-3)
+
+
+def test_adam_parity():
+    rng = np.random.default_rng(42)
+    sizes = [1000, 37, 4096]
+    groups, host = [], []
+    for k, n in enumerate(sizes):
+        p, g = rng.standard_normal(n).astype(np.float32), rng.standard_normal(n).astype(np.float32)
+        m, v = (0.1 * rng.standard_normal(n)).astype(np.float32), np.abs(0.1 * rng.standard_normal(n)).astype(np.float32)
+        host.append((p, g, m, v, 1e-3 * (k + 1)))
+        groups.append([torch.from_numpy(a).cuda() for a in (p, g, m, v)] + [1e-3 * (k + 1), 0.9, 0.999, 1e-15])
+    B.adam_step(groups, step=3)
+    torch.cuda.synchronize()
+    for (p, g, m, v, lr), dev in zip(host, groups):
+        pr, mr, vr = O.adam_step(p, g, m, v, 3, float(np.float32(lr)), float(np.float32(0.9)), float(np.float32(0.999)),
+                                 float(np.float32(1e-15)))
+        np.testing.assert_allclose(dev[0].cpu().numpy(), pr, rtol=1e-5, atol=1e-7)
+        np.testing.assert_allclose(dev[2].cpu().numpy(), mr, rtol=1e-5, atol=1e-8)
+        np.testing.assert_allclose(dev[3].cpu().numpy(), vr, rtol=1e-5, atol=1e-10)
+
+
+def test_scale_regulariser_parity():
+    g = synth.plain_scene(2000, seed=43)
+    cam = synth.plain_camera()
+    P = O.Params()
+    run = GpuRun(g, [cam], P)
+    grads = run.gt.zeros_like()
+    val = torch.zeros(1, device="cuda")
+    zero = torch.zeros(3 * cam.pixels, device="cuda")
+    run.ws.render_bwd(run.gt, zero, grads, accumulate=False, scale_reg_beta=10.0, scale_reg_value=val)
+    torch.cuda.synchronize()
+    pr = O.project(O.gaussians64(g), cam, P)
+    vis = pr["status"] == O.ACTIVE
+    ref_val, ref_g = O.scale_regulariser(g.log_scale.astype(np.float64), vis, beta=10.0)
+    assert abs(val.item() - ref_val) <= 1e-5 * ref_val
+    assert_grad_close("log_scale", grads.log_scale.double().cpu().numpy(), ref_g)
