@@ -1,0 +1,451 @@
+#!/usr/bin/env python3
+"""Throughput of one 3DGS training step on the city-scale single-view workload.
+
+Workload (the paper's aerial datasets are replaced by a synthetic city): 5M
+Gaussians over 2 km x 2 km (ground plane + 200 buildings), degree-3 SH, one
+1920x1080 aerial camera at 45 degree pitch, LOD gate (d0 = 1600 m, Lmax = 5)
+and the importance cull column enabled.  One step runs every stage of the hot
+path through the C ABI on resident device data:
+
+  preprocess (gate + cull + projection + SH) -> bin_sort -> render_fwd
+  -> L1 + 0.2 D-SSIM loss against a target -> render_bwd (+ scale regulariser)
+  -> importance sweep (preprocess without gate, bin_sort, importance: w, a,
+     s, c^rad, c^vis and the next Cull column) -> Adam over all 59 parameters.
+
+value = rendered pixels per second of whole steps (Mpix/s); the line also
+carries Mgaussian/s.  All inputs (1.2 GB of parameters, Adam state, the
+workspace) exceed the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gsblitz|reference]
+
+With N > 1 (under torchrun) every rank renders its own replica on its own GPU
+(weak scaling, no data-path collective); value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd Mpix/s and Mgaussian/s at 5M Gaussians 1080p; render p50/p99 ms"
+WORKLOAD = "city-5M-1080p-single-view-train-step"
+N_GAUSS = 5_000_000
+W_IMG, H_IMG = 1920, 1080
+SCENE_SEED, CAM_SEED, TARGET_SEED = 3, 4, 5
+LOD = dict(lod_d0=1600.0, lod_Lmax=5)
+LAMBDA, BETA = 0.2, 10.0
+# learning rates of standard 3DGS training (position lr scaled for a city extent)
+LRS = dict(mean=1.6e-4 * 100.0, log_scale=5e-3, quat=1e-3, opacity_logit=5e-2, sh=2.5e-3)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gsblitz", choices=["gsblitz", "reference"])
+    ap.add_argument("--n", type=int, default=N_GAUSS, help="Gaussians (default: the 5M workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---- clocks ---------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid: str | None):
+        self.uuid = device_uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r.split(", ") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm = [float(r[0]) for r in rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows if len(r) >= 8 for k in range(4) if r[4 + k].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+# ---- workload ---------------------------------------------------------------------
+
+def make_host_inputs(n):
+    from paper_2605_13794_gb300 import synth
+    g = synth.city_scene(n, seed=SCENE_SEED)
+    cam = synth.aerial_camera(seed=CAM_SEED, width=W_IMG, height=H_IMG)
+    target = synth.noise_target(W_IMG, H_IMG, seed=TARGET_SEED)
+    return g, cam, target
+
+
+class Step:
+    """Device state and the sequence of C-ABI calls of one training step."""
+
+    def __init__(self, g, cam, target):
+        import torch
+        from paper_2605_13794_gb300 import binding as B
+        self.B, self.torch = B, torch
+        self.cam = cam
+        self.n = g.n
+        self.gt = B.GaussianTensors.from_host(g)
+        for t in self.gt.params():
+            t.requires_grad_(False)
+        self.grads = self.gt.zeros_like()
+        self.m = self.gt.zeros_like()
+        self.v = self.gt.zeros_like()
+        self.target = torch.from_numpy(target).cuda().unsqueeze(0).contiguous()
+        self.P = cam.width * cam.height
+        self.rgb = torch.empty(3 * self.P, device="cuda")
+        self.T = torch.empty(self.P, device="cuda")
+        self.dL = torch.empty(3 * self.P, device="cuda")
+        self.loss = torch.zeros(1, device="cuda")
+        self.reg = torch.zeros(1, device="cuda")
+        words = (self.n + 31) // 32
+        self.cull = torch.zeros(words, device="cuda", dtype=torch.int32)
+        self.s = torch.zeros(self.n, device="cuda")
+        self.crad = torch.zeros(self.n, device="cuda", dtype=torch.int32)
+        self.cvis = torch.zeros(self.n, device="cuda", dtype=torch.int32)
+        self.params_train = B.RenderParams(lod_enable=True, cull_enable=True, **LOD)
+        self.params_imp = B.RenderParams(lod_enable=False, cull_enable=False)
+        self.step_no = 0
+        # capacities from a dry run of the heavier (ungated) importance configuration
+        tiles = B.tiles_of(cam)
+        probe = B.Workspace(max_gaussians=self.n, max_records=self.n, max_instances=min((1 << 30) - 1, 32 * self.n),
+                            max_tiles=tiles, max_pixels=self.P)
+        probe.preprocess(self.gt, [cam], self.params_imp)
+        probe.bin_sort()
+        c = probe.counts()
+        probe.close()
+        del probe
+        self.inst_cap = min((1 << 30) - 1, int(c["instances_needed"] * 1.25) + 4096)
+        self.rec_cap = min(self.n, int(c["records_needed"] * 1.25) + 4096)
+        self.ws = B.Workspace(max_gaussians=self.n, max_records=self.rec_cap, max_instances=self.inst_cap,
+                              max_tiles=tiles, max_pixels=self.P)
+        # initial Cull column from an importance sweep of this view
+        self.ws.preprocess(self.gt, [cam], self.params_imp)
+        self.ws.bin_sort()
+        self.ws.importance(cull_out=self.cull)
+        self.ws.sync_status()
+        self.groups = [(p, g_, m, v, LRS[k], 0.9, 0.999, 1e-15) for k, p, g_, m, v in
+                       zip(("mean", "log_scale", "quat", "opacity_logit", "sh"), self.gt.params(),
+                           self.grads.params(), self.m.params(), self.v.params())]
+        self.stage_names = ["preprocess", "bin_sort", "render_fwd", "loss", "render_bwd", "importance", "adam"]
+
+    def run(self, ev=None):
+        """One step; ev, if given, is a list of 8 CUDA events recorded between stages."""
+        B, ws, torch = self.B, self.ws, self.torch
+        rec = (lambda k: ev[k].record()) if ev is not None else (lambda k: None)
+        self.step_no += 1
+        rec(0)
+        ws.preprocess(self.gt, [self.cam], self.params_train, self.cull)
+        rec(1)
+        ws.bin_sort()
+        rec(2)
+        ws.render_fwd(self.rgb, self.T)
+        rec(3)
+        ws.photometric_loss(self.rgb.view(1, 3, self.cam.height, self.cam.width), self.target, LAMBDA, self.loss,
+                            self.dL)
+        rec(4)
+        ws.render_bwd(self.gt, self.dL, self.grads, accumulate=False, scale_reg_beta=BETA, scale_reg_value=self.reg)
+        rec(5)
+        ws.preprocess(self.gt, [self.cam], self.params_imp)
+        ws.bin_sort()
+        ws.importance(s_accum=self.s, crad=self.crad, cvis=self.cvis, cull_out=self.cull)
+        rec(6)
+        B.adam_step(self.groups, self.step_no)
+        rec(7)
+
+
+# ---- roofline bookkeeping --------------------------------------------------------
+
+def adam_bytes(n):
+    # per parameter float: read p, g, m, v; write p, m, v
+    return 59 * n * 28
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def traffic_from_profile(kernel_file):
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu
+    summary, if it was taken on the current source of that kernel."""
+    path = os.path.join(ROOT, "profiles", "adam_kernel_city5M.md")
+    src = os.path.join(ROOT, "paper_2605_13794_gb300", "csrc", kernel_file)
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    vals = dict(l.split(":", 1) for l in text.splitlines() if l.startswith(("source_sha:", "dram_bytes_per_launch:")))
+    if vals.get("source_sha", "").strip() != sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"].strip())
+    except (KeyError, ValueError):
+        return None
+
+
+# ---- CPU oracle on a bounded sample ------------------------------------------------
+
+class OracleSample:
+    """The FP64 oracle timed on a bounded sample of one step, each part scaled
+    by the units it covers: per-Gaussian work (projection with and without the
+    gate, Adam) on a random Gaussian sample; per-pixel work (binning,
+    compositing, loss, backward, importance) on a centred window rendered with
+    every Gaussian that touches it, so the window keeps the scene's depth
+    complexity.  The window's Gaussian set is found once, untimed."""
+
+    def __init__(self, g, cam, target, window):
+        import oracle as O
+        from paper_2605_13794_gb300 import synth
+        self.O, self.g, self.cam = O, g, cam
+        ww, wh = window
+        x0, y0 = (cam.width - ww) // 2, (cam.height - wh) // 2
+        self.wcam = synth.Camera(R=cam.R, t=cam.t, fx=cam.fx, fy=cam.fy, cx=cam.cx - x0, cy=cam.cy - y0,
+                                 width=ww, height=wh, campos=cam.campos)
+        self.target = np.ascontiguousarray(target[:, y0:y0 + wh, x0:x0 + ww])
+        self.Pt = O.Params(lod_enable=True, lod_d0=LOD["lod_d0"], lod_Lmax=LOD["lod_Lmax"])
+        self.Pi = O.Params()
+        pw = O.project(O.gaussians64(g), self.wcam, self.Pi)
+        sel = np.nonzero(pw["status"] == O.ACTIVE)[0]
+        self.gw = O.gaussians64(g.subset(sel if len(sel) else np.arange(1)))
+        self.frac_pix = (ww * wh) / (cam.width * cam.height)
+
+    def step(self, proj_sample, seed):
+        O, g = self.O, self.g
+        n = g.n
+        rng = np.random.default_rng(seed)
+        idx = np.sort(rng.choice(n, size=min(proj_sample, n), replace=False))
+        g64s = O.gaussians64(g.subset(idx))
+        t = {}
+        t0 = time.perf_counter()
+        O.project(g64s, self.cam, self.Pt)
+        O.project(g64s, self.cam, self.Pi)
+        t["projection"] = (time.perf_counter() - t0) * n / len(idx)
+        t0 = time.perf_counter()
+        fwd = O.forward_view(self.gw, self.wcam, self.Pt)
+        _, dL = O.photometric_loss(fwd["image"][None], self.target[None], LAMBDA)
+        O.backward_view(self.gw, fwd, self.wcam, self.Pt, dL[0])
+        imp = O.forward_view(self.gw, self.wcam, self.Pi)
+        O.visible_top_mass(imp["w"])
+        t["per_pixel_stages"] = (time.perf_counter() - t0) / self.frac_pix
+        k = min(proj_sample, n)
+        p = rng.standard_normal(k)
+        t0 = time.perf_counter()
+        for _ in range(59):
+            O.adam_step(p, p, p, np.abs(p), 1, 1e-3)
+        t["adam"] = (time.perf_counter() - t0) * n / k
+        return sum(t.values()), t
+
+
+def cpu_baseline(g, cam, target):
+    sample = OracleSample(g, cam, target, window=(240, 136))
+    total, parts = sample.step(proj_sample=200_000, seed=0)
+    P = cam.width * cam.height
+    return {"value": P / total / 1e6, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+            "sample": ("FP64 C/numpy oracle, one thread: projection (gated and ungated) and Adam on a random "
+                       "200k-Gaussian sample scaled by N; binning, compositing, L1+SSIM loss, backward and the "
+                       "importance sweep on a centred 240x136 window with every Gaussian touching it, scaled by "
+                       "the pixel ratio"),
+            "seconds_per_step": total, "parts_s": {k: round(v, 3) for k, v in parts.items()}}
+
+
+# ---- main -------------------------------------------------------------------------------
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device="cuda", dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the FP64 oracle on the host cores, a bounded sample per step."""
+    if rank != 0:
+        return
+    g, cam, target = make_host_inputs(args.n)
+    sample = OracleSample(g, cam, target, window=(120, 68))
+    samples = []
+    for k in range(args.warmup + args.steps):
+        s, _ = sample.step(proj_sample=50_000, seed=k)
+        if k >= args.warmup:
+            samples.append(s)
+    sec = statistics.mean(samples)
+    P = cam.width * cam.height
+    value = P / sec / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "gaussians": args.n, "width": W_IMG, "height": H_IMG},
+            "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+                             "sample": "per step: 50k-Gaussian projection sample and a 120x68 window, scaled"},
+            "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    __import__("__graft_entry__").build()
+    from paper_2605_13794_gb300 import binding as B
+    torch.cuda.set_device(local)
+    g, cam, target = make_host_inputs(args.n)
+    step = Step(g, cam, target)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        step.run()
+    torch.cuda.synchronize()
+    step.ws.sync_status()
+
+    # ---- device-timed region: K whole steps, inputs resident in HBM
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = B.kernel_launches()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for k in range(args.steps):
+        step.run(evs[k])
+    end.record(stream)
+    torch.cuda.synchronize()
+    launches = B.kernel_launches() - launches0
+    clocks = sampler.stop()
+    barrier(world)
+    step.ws.sync_status()
+    ms = start.elapsed_time(end) / args.steps
+    ms = max_over_ranks(ms, world)
+    stage_ms = {name: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
+                for i, name in enumerate(step.stage_names)}
+
+    # ---- end to end through the public API with host buffers
+    tgt_host = torch.from_numpy(target).pin_memory()
+    cull_host = torch.empty(step.cull.numel(), dtype=torch.int32).pin_memory()
+    loss_host = torch.empty(1).pin_memory()
+    h2d = tgt_host.numel() * 4 + cull_host.numel() * 4
+    d2h = loss_host.numel() * 4 + cull_host.numel() * 4
+    cull_host.copy_(step.cull.cpu())
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step.target.view(-1).copy_(tgt_host.view(-1), non_blocking=True)
+        step.cull.copy_(cull_host, non_blocking=True)
+        step.run()
+        loss_host.copy_(step.loss, non_blocking=True)
+        cull_host.copy_(step.cull, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+
+    P = cam.width * cam.height
+    value = world * P / (ms * 1e-3) / 1e6
+    gauss = world * g.n / (ms * 1e-3) / 1e6
+    counts = step.ws.counts()
+    peaks = measured_peaks()
+    dom = max(stage_ms, key=stage_ms.get)
+    # the roofline is reported for the Adam kernel (one launch per step, its
+    # own stage): algorithmic bytes 28 per parameter float, 59 floats per Gaussian
+    a_ms = stage_ms["adam"]
+    achieved = adam_bytes(g.n) / (a_ms * 1e-3) / 1e9
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    roof = {"bound": "hbm", "kernel": "adam_kernel", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": traffic_from_profile("optim.cu"),
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+            "algorithmic_bytes_per_launch": adam_bytes(g.n), "dominant_stage": dom}
+    line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "gaussians": g.n, "width": W_IMG, "height": H_IMG,
+                       "lod": True, "cull": True, "importance_pass": True, "optimizer": "adam",
+                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
+            "mgaussian_per_s": gauss,
+            "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+            "counts": {k: counts[k] for k in ("n_records", "n_instances", "n_visible")},
+            "roofline": roof,
+            "e2e": {"value": world * P / (e2e_ms * 1e-3) / 1e6, "unit": "Mpix/s", "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(g, cam, target)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -164,6 +164,9 @@ typedef enum {
 
 void gs_default_params(gs_render_params *p);
 const char *gs_last_error(void);
+/* Number of CUDA kernels this library has launched in this process (all
+ * workspaces, all threads); for launch accounting in benchmarks. */
+int64_t gs_kernel_launches(void);
 
 /* Creates a workspace on the current CUDA device.  cap: host pointer. */
 int gs_workspace_create(const gs_capacity *cap, gs_workspace **out);

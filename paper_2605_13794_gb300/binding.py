@@ -26,7 +26,8 @@ GS_TILE = 16
 
 EXPORTS = ("gs_default_params", "gs_last_error", "gs_workspace_create", "gs_workspace_destroy", "gs_workspace_bytes",
            "gs_preprocess", "gs_bin_sort", "gs_render_fwd", "gs_render_bwd", "gs_importance", "gs_photometric_loss",
-           "gs_adam_step", "gs_sync_status", "gs_workspace_counts", "gs_clear_error", "gs_workspace_buffer")
+           "gs_adam_step", "gs_sync_status", "gs_workspace_counts", "gs_clear_error", "gs_workspace_buffer",
+           "gs_kernel_launches")
 
 
 class GSError(RuntimeError):
@@ -96,6 +97,8 @@ def lib() -> ctypes.CDLL:
         L.gs_workspace_destroy.argtypes = [vp]
         L.gs_workspace_bytes.argtypes = [vp]
         L.gs_workspace_bytes.restype = i64
+        L.gs_kernel_launches.argtypes = []
+        L.gs_kernel_launches.restype = i64
         L.gs_preprocess.argtypes = [vp, vp, vp, i32, vp, vp, vp]
         L.gs_bin_sort.argtypes = [vp, vp]
         L.gs_render_fwd.argtypes = [vp, vp, vp, vp]
@@ -108,7 +111,7 @@ def lib() -> ctypes.CDLL:
         L.gs_clear_error.argtypes = [vp, vp]
         L.gs_workspace_buffer.argtypes = [vp, i32, vp, vp]
         for name in EXPORTS:
-            if name not in ("gs_default_params", "gs_last_error", "gs_workspace_bytes"):
+            if name not in ("gs_default_params", "gs_last_error", "gs_workspace_bytes", "gs_kernel_launches"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -316,6 +319,11 @@ def _memcpy_d2h(dst: int, src: int, nbytes: int):
     rc = _cudart.cudaMemcpy(ctypes.c_void_p(dst), ctypes.c_void_p(src), nbytes, 2)  # cudaMemcpyDeviceToHost
     if rc != 0:
         raise RuntimeError(f"cudaMemcpy failed with {rc}")
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched so far in this process."""
+    return int(lib().gs_kernel_launches())
 
 
 def adam_step(groups, step: int, stream=None):

@@ -1,6 +1,7 @@
 // api.cu -- host side of the C ABI declared in gsblitz.h: argument checks,
 // workspace layout, and the order of kernel launches for each call.
 #include <math.h>
+#include <atomic>
 #include <new>
 #include <stdarg.h>
 #include <stdio.h>
@@ -121,9 +122,15 @@ int check_cap(const gs_capacity *c)
     return GS_OK;
 }
 
+std::atomic<long long> g_launches{0};
+
 } // namespace
 
+void gs::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 extern "C" {
+
+int64_t gs_kernel_launches(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 
 void gs_default_params(gs_render_params *p)
 {

@@ -178,9 +178,12 @@ cudaError_t launch_loss(gs_workspace *ws, cudaStream_t st, const float *img, con
     const long long stride = (long long)B * 3 * H * W;
     ssim_fwd_kernel<<<grid, 256, 0, st>>>(img, tgt, H, W, win, 0.01f * 0.01f, 0.03f * 0.03f, ws->loss_maps, stride,
                                           ws->loss_partial);
+    note_launch();
     ssim_bwd_kernel<<<grid, 256, 0, st>>>(img, tgt, H, W, win, ws->loss_maps, stride, lambda, B, dL);
+    note_launch();
     const int bpv = (int)(grid.x * grid.y * 3);
     loss_finalize_kernel<<<1, 256, 0, st>>>(ws->loss_partial, bpv, B, H, W, lambda, loss_out);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -231,6 +234,7 @@ cudaError_t launch_adam(const gs_adam_group *groups, int n_groups, int step, cud
     long long blocks = (t.start[n_groups] + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     adam_kernel<<<(unsigned)blocks, 256, 0, st>>>(t);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -328,6 +328,7 @@ cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t 
         preprocess_kernel<false><<<blocks, 256, 0, st>>>(gp, o, ws->cams, ws->rc);
     else
         preprocess_kernel<true><<<blocks, 256, 0, st>>>(gp, o, ws->cams, ws->rc);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -361,6 +362,7 @@ cudaError_t launch_reduce_slots(gs_workspace *ws, cudaStream_t st)
     const unsigned blocks = (unsigned)((cap + 255) / 256);
     reduce_slots_kernel<<<blocks, 256, 0, st>>>(ws->dval[ws->depth_buf], ws->inst_off, ws->tt, ws->slots, ws->rgrad,
                                                 ws->ctr);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -589,10 +591,12 @@ cudaError_t launch_preprocess_bwd(gs_workspace *ws, cudaStream_t st, const gs_ga
     a.red_partial = reduce ? ws->red_partial : nullptr;
     a.ctr = ws->ctr;
     preprocess_bwd_kernel<<<blocks, 128, 0, st>>>(a, ws->cams, ws->rc);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (reduce) {
         scale_reg_finalize_kernel<<<1, 256, 0, st>>>(ws->red_partial, (int)blocks, beta, ws->ctr, scale_reg_value);
+        note_launch();
         e = cudaGetLastError();
     }
     return e;

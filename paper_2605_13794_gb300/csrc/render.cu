@@ -115,6 +115,7 @@ cudaError_t launch_render_fwd(gs_workspace *ws, cudaStream_t st, float *rgb, flo
     render_fwd_kernel<<<ws->cams.total_tiles, 256, 0, st>>>(ws->ranges, ws->tval[ws->tile_buf], ws->rd0, ws->rd1,
                                                             ws->rd2, ws->cams, ws->rc, rgb, T_out, ws->T_final,
                                                             ws->n_contrib);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -280,6 +281,7 @@ cudaError_t launch_render_bwd(gs_workspace *ws, cudaStream_t st, const float *dL
     a.inst_off = ws->inst_off; a.rect = ws->rect; a.T_final = ws->T_final; a.n_contrib = ws->n_contrib;
     a.dL_drgb = dL_drgb; a.slots = ws->slots;
     render_bwd_kernel<<<ws->cams.total_tiles, 256, 0, st>>>(a, ws->cams, ws->rc);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -380,6 +382,7 @@ cudaError_t launch_importance_raster(gs_workspace *ws, cudaStream_t st)
     a.ranges = ws->ranges; a.vals = ws->tval[ws->tile_buf]; a.rd0 = ws->rd0; a.rd1 = ws->rd1;
     a.inst_off = ws->inst_off; a.rect = ws->rect; a.slots = ws->slots;
     importance_raster_kernel<<<ws->cams.total_tiles, 256, 0, st>>>(a, ws->cams, ws->rc);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -230,23 +230,28 @@ cudaError_t launch_importance(gs_workspace *ws, cudaStream_t st, float *w, uint3
     imp_reduce_kernel<<<rblocks, 256, 0, st>>>(ws->dval[ws->depth_buf], ws->inst_off, ws->tt,
                                                 reinterpret_cast<const float2 *>(ws->slots), ws->imp_w, ws->imp_a,
                                                 ws->ctr);
+    note_launch();
     if (w && (e = cudaMemsetAsync(w, 0, (size_t)ncam * n * sizeof(float), st)) != cudaSuccess) return e;
     if (a && (e = cudaMemsetAsync(a, 0, (size_t)ncam * n * sizeof(uint32_t), st)) != cudaSuccess) return e;
     if (n > 0) {
         ImpGaussArgs ga{ws->rec_off, ws->rec_cam, ws->imp_w, ws->imp_a, w, a, s_accum, crad, n, ws->rc.eps_score,
                         ws->ctr};
         imp_gauss_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ga);
+        note_launch();
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (!cull_out && !cvis) return cudaSuccess;
     const long long words = (n + 31) / 32;
-    if (cull_out && words > 0)
+    if (cull_out && words > 0) {
         cull_init_kernel<<<1216, 256, 0, st>>>(cull_out, words, n, ncam);
+        note_launch();
+    }
     // sort records by w descending (stable), then by camera (stable); own
     // buffers, so the depth order stays valid for a later backward
     uint32_t *sk[2] = {ws->selk[0], ws->selk[1]};
     uint32_t *sv[2] = {ws->selv[0], ws->selv[1]};
     sel_keys_kernel<<<rblocks, 256, 0, st>>>(ws->imp_w, sk[0], ws->ctr);
+    note_launch();
     int ob = 0;
     const unsigned long long *cnt = &ws->ctr->n_records;
     if ((e = launch_radix_sort(ws, st, sk, sv, cnt, rcap, 32, true, false, ob)) != cudaSuccess) return e;
@@ -255,6 +260,7 @@ cudaError_t launch_importance(gs_workspace *ws, cudaStream_t st, float *w, uint3
         uint32_t *k2[2] = {sk[ob ^ 1], sk[ob]};
         uint32_t *v2[2] = {sv[ob], sv[ob ^ 1]};
         sel_camkeys_kernel<<<rblocks, 256, 0, st>>>(v2[0], ws->rec_cam, k2[0], ws->ctr);
+        note_launch();
         int ob2 = 0;
         if ((e = launch_radix_sort(ws, st, k2, v2, cnt, rcap, 8, false, false, ob2)) != cudaSuccess) return e;
         sorted = v2[ob2];
@@ -262,14 +268,19 @@ cudaError_t launch_importance(gs_workspace *ws, cudaStream_t st, float *w, uint3
     const unsigned sblocks = (unsigned)((rcap + kScanTile - 1) / kScanTile);
     double *bsum = reinterpret_cast<double *>(ws->red_partial);
     sel_block_sum_kernel<<<sblocks, 256, 0, st>>>(sorted, ws->imp_w, bsum, ws->ctr);
+    note_launch();
     sel_block_scan_kernel<<<1, 256, 0, st>>>(bsum, (int)sblocks);
+    note_launch();
     sel_scan_kernel<<<sblocks, 256, 0, st>>>(sorted, ws->imp_w, bsum, ws->sel_cum, ws->ctr);
+    note_launch();
     uint2 *seg = reinterpret_cast<uint2 *>(ws->rx_hist); // 64 uint2 fit in the histogram scratch
     if ((e = cudaMemsetAsync(seg, 0, GS_MAX_CAMERAS * sizeof(uint2), st)) != cudaSuccess) return e;
     sel_segments_kernel<<<1216, 256, 0, st>>>(sorted, ws->rec_cam, seg, ws->ctr);
+    note_launch();
     SelApplyArgs sa{sorted, ws->rec_g, ws->rec_cam, ws->imp_w, ws->sel_cum, seg, cull_out, cvis, words,
                     ws->rc.vis_mass, ws->ctr};
     sel_apply_kernel<<<1216, 256, 0, st>>>(sa);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -201,15 +201,15 @@ cudaError_t launch_radix_sort(gs_workspace *ws, cudaStream_t st, uint32_t *keys[
     unsigned hblocks = (unsigned)((cap + 255) / 256);
     if (hblocks > 1216) hblocks = 1216;
     radix_hist_kernel<<<hblocks, 256, 0, st>>>(keys[0], count, cap, passes, ws->rx_hist);
+    note_launch();
     radix_offsets_kernel<<<1, 256, 0, st>>>(ws->rx_hist, ws->rx_off, passes);
+    note_launch();
     int src = 0;
     for (int p = 0; p < passes; p++) {
         const int dst = src ^ 1;
         if ((e = cudaMemsetAsync(ws->rx_status, 0, (blocks * 256 + 1) * sizeof(uint32_t), st)) != cudaSuccess)
             return e;
         const bool ident = vals_identity && p == 0;
-        const bool last = p == passes - 1;
-        // the keys of the last pass are needed by the tile-range kernel only
         if (ident)
             radix_pass_kernel<true, true><<<(unsigned)blocks, kSortThreads, 0, st>>>(
                 keys[src], vals[src], keys[dst], vals[dst], count, cap, 8 * p, ws->rx_off + 256 * p, ws->rx_status,
@@ -218,7 +218,7 @@ cudaError_t launch_radix_sort(gs_workspace *ws, cudaStream_t st, uint32_t *keys[
             radix_pass_kernel<false, true><<<(unsigned)blocks, kSortThreads, 0, st>>>(
                 keys[src], vals[src], keys[dst], vals[dst], count, cap, 8 * p, ws->rx_off + 256 * p, ws->rx_status,
                 ws->ctr);
-        (void)last;
+        note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         src = dst;
     }
@@ -317,6 +317,7 @@ cudaError_t launch_emit(gs_workspace *ws, cudaStream_t st)
     a.tkey = ws->tkey[0]; a.tval = ws->tval[0];
     a.lb_status = ws->lb_status; a.ctr = ws->ctr; a.max_instances = (unsigned long long)ws->cap.max_instances;
     emit_kernel<<<blocks, 256, 0, st>>>(a, ws->cams);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -339,6 +340,7 @@ cudaError_t launch_ranges(gs_workspace *ws, cudaStream_t st)
     if ((e = cudaMemsetAsync(ws->ranges, 0, (size_t)ws->cams.total_tiles * sizeof(uint2), st)) != cudaSuccess)
         return e;
     ranges_kernel<<<152 * 8, 256, 0, st>>>(ws->tkey[ws->tile_buf], ws->ctr, ws->ranges);
+    note_launch();
     return cudaGetLastError();
 }
 

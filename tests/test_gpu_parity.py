@@ -43,6 +43,14 @@ def _compare_view(run: GpuRun, c, g64, cam, P, cull=None, check_image=True):
     mism = np.nonzero(gpu_active != ora_active)[0]
     assert tie[mism].all(), f"active-set mismatch outside tie bands: {mism[~tie[mism]][:10]}"
     assert tie.sum() <= max(3, 1e-3 * n)
+    # a tie-band Gaussian whose decisions still agree is compared like any other
+    agree = gpu_active & ora_active
+    tie_both = np.nonzero(agree & tie)[0]
+    if len(tie_both):
+        tr = np.array([recs[i] for i in tie_both], np.int64)
+        same = (unpack_rect(run.rect[tr]) == pr["rect"][tie_both]).all(1)
+        tie[tie_both[same]] = False
+    tie[np.nonzero(~gpu_active & ~ora_active)[0]] = False
     both = np.nonzero(gpu_active & ora_active & ~tie)[0]
     ridx = np.array([recs[i] for i in both], np.int64)
     # integer parity: rectangles, tiles touched, depth key bits
@@ -52,7 +60,10 @@ def _compare_view(run: GpuRun, c, g64, cam, P, cull=None, check_image=True):
     # continuous projected values (FP32 vs FP64)
     np.testing.assert_allclose(run.rd0[ridx, :2], pr["uv"][both], rtol=0, atol=2e-3)
     con = np.concatenate([run.rd0[ridx, 2:4], run.rd1[ridx, :1]], 1)
-    np.testing.assert_allclose(con, pr["conic"][both], rtol=2e-4, atol=1e-7)
+    ref = pr["conic"][both]
+    # the off-diagonal term comes from a cancellation: scale errors by the conic's size
+    scale = np.maximum(np.abs(ref[:, 0]), np.abs(ref[:, 2]))[:, None]
+    assert (np.abs(con - ref) <= 2e-4 * scale).all(), np.abs(con - ref).max()
     np.testing.assert_allclose(run.rd1[ridx, 1], pr["opacity"][both], rtol=1e-6, atol=1e-7)
     rgb = np.concatenate([run.rd1[ridx, 2:4], run.rd2[ridx, None]], 1)
     np.testing.assert_allclose(rgb, pr["rgb"][both], rtol=0, atol=2e-5)
@@ -244,8 +255,10 @@ def test_importance_parity():
     imp = _importance(run, g.n, len(cams))
     acc = O.new_importance(g.n)
     vm = float(np.float32(P.vis_mass))
+    view_a = []
     for c, cam in enumerate(cams):
         fwd = _compare_view(run, c, g64, cam, P, check_image=False)
+        view_a.append(fwd["a"])
         view = O.importance_update(acc, fwd["w"], fwd["a"], fwd["proj"], vm, float(np.float32(P.eps_score)))
         # Gaussians with a flagged pixel in their footprint may differ by one fragment
         assert_grad_close(f"w[{c}]", imp["w"][c], fwd["w"])
@@ -255,7 +268,13 @@ def test_importance_parity():
         _check_visible_set(vis_gpu, fwd["w"], vm)
         # with identical w the sets would be identical; FP32 w moves only near-cut entries
         assert (vis_gpu != view["cvis"]).sum() <= 2
-    assert_grad_close("s", imp["s"], acc["s"])
+    # s_i = sum w/(a+eps): a Gaussian whose pixel count moved at a flagged alpha_min
+    # decision changes by ~1/a, so it is compared only where every view's a agrees
+    a_ok = np.ones(g.n, bool)
+    for c, cam in enumerate(cams):
+        a_ok &= imp["a"][c] == np.rint(view_a[c]).astype(np.int64)
+    assert (~a_ok).sum() <= max(2, int(4e-3 * g.n))
+    assert_grad_close("s", imp["s"][a_ok], acc["s"][a_ok])
     assert np.array_equal(imp["crad"], acc["crad"])
     assert np.abs(imp["cvis"] - acc["cvis"]).max() <= 1
 
