@@ -8,9 +8,12 @@ and the importance cull column enabled.  One step runs every stage of the hot
 path through the C ABI on resident device data:
 
   preprocess (gate + cull + projection + SH) -> bin_sort -> render_fwd
-  -> L1 + 0.2 D-SSIM loss against a target -> render_bwd (+ scale regulariser)
-  -> importance sweep (preprocess without gate, bin_sort, importance: w, a,
-     s, c^rad, c^vis and the next Cull column) -> Adam over all 59 parameters.
+  -> L1 + 0.2 D-SSIM loss against a target -> render backward (+ scale
+     regulariser) into compact per-Gaussian gradient rows -> Adam over all 59
+     parameters of all Gaussians (fused with the gradient rows, no dense
+     gradient array) -> importance sweep (preprocess with the LOD gate but
+     without the Cull column it recomputes, bin_sort, importance: w, a, s,
+     c^rad, c^vis and the next Cull column).
 
 value = rendered pixels per second of whole steps (Mpix/s); the line also
 carries Mgaussian/s.  All inputs (1.2 GB of parameters, Adam state, the
@@ -125,7 +128,6 @@ class Step:
         self.gt = B.GaussianTensors.from_host(g)
         for t in self.gt.params():
             t.requires_grad_(False)
-        self.grads = self.gt.zeros_like()
         self.m = self.gt.zeros_like()
         self.v = self.gt.zeros_like()
         self.target = torch.from_numpy(target).cuda().unsqueeze(0).contiguous()
@@ -141,9 +143,11 @@ class Step:
         self.crad = torch.zeros(self.n, device="cuda", dtype=torch.int32)
         self.cvis = torch.zeros(self.n, device="cuda", dtype=torch.int32)
         self.params_train = B.RenderParams(lod_enable=True, cull_enable=True, **LOD)
-        self.params_imp = B.RenderParams(lod_enable=False, cull_enable=False)
+        # the scoring sweep after density control (the paper's T2 pass) renders with the LOD gate
+        # engaged and never applies the Cull mask it recomputes
+        self.params_imp = B.RenderParams(lod_enable=True, cull_enable=False, **LOD)
         self.step_no = 0
-        # capacities from a dry run of the heavier (ungated) importance configuration
+        # capacities from a dry run of the importance configuration (no Cull column)
         tiles = B.tiles_of(cam)
         probe = B.Workspace(max_gaussians=self.n, max_records=self.n, max_instances=min((1 << 30) - 1, 32 * self.n),
                             max_tiles=tiles, max_pixels=self.P)
@@ -161,10 +165,8 @@ class Step:
         self.ws.bin_sort()
         self.ws.importance(cull_out=self.cull)
         self.ws.sync_status()
-        self.groups = [(p, g_, m, v, LRS[k], 0.9, 0.999, 1e-15) for k, p, g_, m, v in
-                       zip(("mean", "log_scale", "quat", "opacity_logit", "sh"), self.gt.params(),
-                           self.grads.params(), self.m.params(), self.v.params())]
-        self.stage_names = ["preprocess", "bin_sort", "render_fwd", "loss", "render_bwd", "importance", "adam"]
+        self.lr = [LRS[k] for k in ("mean", "log_scale", "quat", "opacity_logit", "sh")]
+        self.stage_names = ["preprocess", "bin_sort", "render_fwd", "loss", "render_bwd", "adam", "importance"]
 
     def run(self, ev=None):
         """One step; ev, if given, is a list of 8 CUDA events recorded between stages."""
@@ -181,21 +183,24 @@ class Step:
         ws.photometric_loss(self.rgb.view(1, 3, self.cam.height, self.cam.width), self.target, LAMBDA, self.loss,
                             self.dL)
         rec(4)
-        ws.render_bwd(self.gt, self.dL, self.grads, accumulate=False, scale_reg_beta=BETA, scale_reg_value=self.reg)
+        ws.render_bwd_compact(self.gt, self.dL, scale_reg_beta=BETA, scale_reg_value=self.reg)
         rec(5)
+        # Adam on all Gaussians with the compact gradients (zero for Gaussians without a record)
+        ws.adam_step_compact(self.gt, self.m, self.v, self.lr, self.step_no)
+        rec(6)
+        # importance sweep of the updated model; its Cull column gates the next step
         ws.preprocess(self.gt, [self.cam], self.params_imp)
         ws.bin_sort()
         ws.importance(s_accum=self.s, crad=self.crad, cvis=self.cvis, cull_out=self.cull)
-        rec(6)
-        B.adam_step(self.groups, self.step_no)
         rec(7)
 
 
 # ---- roofline bookkeeping --------------------------------------------------------
 
-def adam_bytes(n):
-    # per parameter float: read p, g, m, v; write p, m, v
-    return 59 * n * 28
+def adam_bytes(n, n_visible):
+    # per parameter float: read and write p, m, v (24 bytes); per Gaussian the
+    # first-record index (4 bytes); per Gaussian with a record its 59-float row
+    return 59 * n * 24 + 4 * n + 59 * 4 * n_visible
 
 
 def measured_peaks():
@@ -244,7 +249,7 @@ class OracleSample:
                                  width=ww, height=wh, campos=cam.campos)
         self.target = np.ascontiguousarray(target[:, y0:y0 + wh, x0:x0 + ww])
         self.Pt = O.Params(lod_enable=True, lod_d0=LOD["lod_d0"], lod_Lmax=LOD["lod_Lmax"])
-        self.Pi = O.Params()
+        self.Pi = O.Params(lod_enable=True, lod_d0=LOD["lod_d0"], lod_Lmax=LOD["lod_Lmax"])
         pw = O.project(O.gaussians64(g), self.wcam, self.Pi)
         sel = np.nonzero(pw["status"] == O.ACTIVE)[0]
         self.gw = O.gaussians64(g.subset(sel if len(sel) else np.arange(1)))
@@ -360,6 +365,9 @@ def main():
         step.run()
     torch.cuda.synchronize()
     step.ws.sync_status()
+    # Gaussians with a record in the training render (sizes the compact gradient rows)
+    step.ws.preprocess(step.gt, [cam], step.params_train, step.cull)
+    step.nvis_train = step.ws.counts()["n_visible"]
 
     # ---- device-timed region: K whole steps, inputs resident in HBM
     uuid = None
@@ -416,14 +424,16 @@ def main():
     peaks = measured_peaks()
     dom = max(stage_ms, key=stage_ms.get)
     # the roofline is reported for the Adam kernel (one launch per step, its
-    # own stage): algorithmic bytes 28 per parameter float, 59 floats per Gaussian
+    # own stage): algorithmic bytes 24 per parameter float, 59 floats per
+    # Gaussian, plus the index and the compact rows of the visible Gaussians
     a_ms = stage_ms["adam"]
-    achieved = adam_bytes(g.n) / (a_ms * 1e-3) / 1e9
+    nvis_train = step.nvis_train
+    achieved = adam_bytes(g.n, nvis_train) / (a_ms * 1e-3) / 1e9
     hbm = peaks.get("hbm_gbs", 6800.0)
     roof = {"bound": "hbm", "kernel": "adam_kernel", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": traffic_from_profile("optim.cu"),
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-            "algorithmic_bytes_per_launch": adam_bytes(g.n), "dominant_stage": dom}
+            "algorithmic_bytes_per_launch": adam_bytes(g.n, nvis_train), "dominant_stage": dom}
     line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",

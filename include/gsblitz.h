@@ -66,14 +66,17 @@ typedef struct {
     int32_t reserved;
 } gs_capacity;
 
-/* Gaussian parameters, structure of arrays, FP32, all rows of length n:
- *   mean          [3][n]   world-space centre mu
- *   log_scale     [3][n]   log of the per-axis standard deviations
- *   quat          [4][n]   rotation (w, x, y, z); normalised before use
- *   opacity_logit [n]      opacity = sigmoid(opacity_logit)
- *   sh            [16][3][n] degree-3 SH, coefficient-major, then channel
- *   lod           [n]      uint8 LOD level (Sec. 3.3); NULL = all level 0
- * Each base pointer must be 4-byte aligned. */
+/* Gaussian parameters, one row per Gaussian for each attribute (the layout of
+ * PyTorch 3DGS code), FP32:
+ *   mean          [n][3]     world-space centre mu
+ *   log_scale     [n][3]     log of the per-axis standard deviations
+ *   quat          [n][4]     rotation (w, x, y, z); normalised before use
+ *   opacity_logit [n]        opacity = sigmoid(opacity_logit)
+ *   sh            [n][16][3] degree-3 SH: coefficient, then channel
+ *   lod           [n]        uint8 LOD level (Sec. 3.3); NULL = all level 0
+ * Rows keep a Gaussian's attribute contiguous, so the sparse passes (only
+ * active Gaussians) read few cache sectors while the dense passes stay
+ * coalesced.  Base pointers must be 16-byte aligned. */
 typedef struct {
     int64_t n;
     const float *mean;
@@ -146,7 +149,8 @@ typedef struct {
 } gs_adam_group;
 
 /* Internal buffers exposed for inspection (debugging, tests).  Pointers are
- * device pointers owned by the workspace; counts are capacities. */
+ * device pointers owned by the workspace; counts are capacities.  Records are
+ * stored in (Gaussian, camera) order, so a Gaussian's records are contiguous. */
 typedef enum {
     GS_BUF_REC_GAUSSIAN = 0, /* uint32 [max_records]: Gaussian of each record */
     GS_BUF_REC_CAMERA = 1,   /* uint16 [max_records]: camera of each record */
@@ -156,10 +160,9 @@ typedef enum {
     GS_BUF_REC_XY_CONIC = 5, /* float4 [max_records]: u, v, A, B */
     GS_BUF_REC_C_OPAC_RG = 6,/* float4 [max_records]: C, opacity, r, g */
     GS_BUF_REC_B = 7,        /* float  [max_records]: b */
-    GS_BUF_REC_OFFSET = 8,   /* uint32 [max_gaussians + 1]: first record of each Gaussian */
-    GS_BUF_SORTED_VALUES = 9,/* uint32 [max_instances]: record of each sorted instance */
-    GS_BUF_TILE_RANGES = 10, /* uint32 [max_tiles][2]: [start, end) of each tile */
-    GS_BUF_N_CONTRIB = 11    /* uint32 [max_pixels]: last composited entry + 1 */
+    GS_BUF_SORTED_VALUES = 8,/* uint32 [max_instances]: record of each sorted instance */
+    GS_BUF_TILE_RANGES = 9,  /* uint32 [max_tiles][2]: [start, end) of each tile */
+    GS_BUF_N_CONTRIB = 10    /* uint32 [max_pixels]: last composited entry + 1 */
 } gs_buffer_id;
 
 void gs_default_params(gs_render_params *p);
@@ -200,6 +203,31 @@ int gs_render_fwd(gs_workspace *ws, float *rgb_out, float *T_out, gs_stream stre
 int gs_render_bwd(gs_workspace *ws, const gs_gaussians *g, const float *dL_drgb, const gs_gaussian_grads *grads,
                   int32_t accumulate, float *absgrad, float scale_reg_beta, float *scale_reg_value,
                   gs_stream stream);
+
+/* Backward into the workspace: as gs_render_bwd, but each Gaussian's 59
+ * parameter gradients (mean, log-scale, quat, opacity, SH, in that order) are
+ * kept as one compact row in the workspace, only for Gaussians with a record;
+ * nothing is written for the others.  Consumed by gs_adam_step_compact. */
+int gs_render_bwd_compact(gs_workspace *ws, const gs_gaussians *g, const float *dL_drgb, float *absgrad,
+                          float scale_reg_beta, float *scale_reg_value, gs_stream stream);
+
+/* One Adam step (Kingma and Ba, bias-corrected; step counts from 1) of every
+ * Gaussian with the gradients of the last gs_render_bwd_compact: Gaussians
+ * without a record take a zero-gradient step.  The arrays of g are UPDATED in
+ * place (the const of gs_gaussians does not apply here); m and v are the first
+ * and second moments in the layout of g; lr: learning rates of mean,
+ * log-scale, quat, opacity and SH.  One streaming pass reads and writes the
+ * parameters and both moments (24 bytes per parameter) and never a dense
+ * gradient array. */
+int gs_adam_step_compact(gs_workspace *ws, const gs_gaussians *g, const gs_gaussian_grads *m,
+                         const gs_gaussian_grads *v, const float lr[5], float beta1, float beta2, float eps,
+                         int32_t step, gs_stream stream);
+
+/* gs_render_bwd_compact followed by gs_adam_step_compact: the backward fused
+ * with the optimizer step, no gradient array materialised. */
+int gs_render_bwd_adam(gs_workspace *ws, const gs_gaussians *g, const float *dL_drgb, const gs_gaussian_grads *m,
+                       const gs_gaussian_grads *v, const float lr[5], float beta1, float beta2, float eps,
+                       int32_t step, float *absgrad, float scale_reg_beta, float *scale_reg_value, gs_stream stream);
 
 /* Instrumented colourless sweep over the binned cameras (Sec. 3.2, Fig. 2).
  * Per camera v and Gaussian i: w[v][i] = sum over composited pixels of alpha T,

@@ -137,10 +137,19 @@ def _d(a):
 
 
 def gaussians64(g) -> dict:
-    """FP64 copies of a GaussianSet's arrays (exact: the inputs are FP32)."""
-    return dict(mean=_d(g.mean), log_scale=_d(g.log_scale), quat=_d(g.quat),
-                opacity_logit=_d(g.opacity_logit), sh=_d(g.sh),
-                lod=np.ascontiguousarray(g.lod, np.uint8))
+    """FP64 copies of a GaussianSet's arrays (exact: the inputs are FP32) in
+    the oracle's own attribute-major layout: mean (3, n), log_scale (3, n),
+    quat (4, n), opacity_logit (n,), sh (16, 3, n)."""
+    return dict(mean=_d(np.asarray(g.mean).T), log_scale=_d(np.asarray(g.log_scale).T),
+                quat=_d(np.asarray(g.quat).T), opacity_logit=_d(g.opacity_logit),
+                sh=_d(np.asarray(g.sh).transpose(1, 2, 0)), lod=np.ascontiguousarray(g.lod, np.uint8))
+
+
+def grads_per_gaussian(grads: dict) -> dict:
+    """The oracle's attribute-major gradients in the per-Gaussian row layout
+    of the inputs: mean (n, 3), log_scale (n, 3), quat (n, 4), sh (n, 16, 3)."""
+    return dict(mean=grads["mean"].T, log_scale=grads["log_scale"].T, quat=grads["quat"].T,
+                opacity_logit=grads["opacity_logit"], sh=grads["sh"].transpose(2, 0, 1))
 
 
 def project(g64: dict, cam, params: Params, cull=None) -> dict:
@@ -373,7 +382,8 @@ def photometric_loss(images, targets, lam=0.2):
 
 def scale_regulariser(log_scale, visible, beta=10.0):
     """Eq. 5: beta * mean over visible Gaussians of the smallest scale; returns
-    (value, dL/dlog_scale).  The derivative goes to the first smallest axis."""
+    (value, dL/dlog_scale).  log_scale is (3, n); the derivative goes to the
+    first smallest axis."""
     ls = np.asarray(log_scale, np.float64)
     vis = np.asarray(visible, bool)
     g = np.zeros_like(ls)

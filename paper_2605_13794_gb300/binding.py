@@ -21,13 +21,12 @@ GS_OK, GS_ERR_INVALID_ARG, GS_ERR_OOM, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_TIME
 GS_MAX_CAMERAS = 64
 GS_TILE = 16
 (GS_BUF_REC_GAUSSIAN, GS_BUF_REC_CAMERA, GS_BUF_REC_RECT, GS_BUF_REC_TILES, GS_BUF_REC_DEPTH, GS_BUF_REC_XY_CONIC,
- GS_BUF_REC_C_OPAC_RG, GS_BUF_REC_B, GS_BUF_REC_OFFSET, GS_BUF_SORTED_VALUES, GS_BUF_TILE_RANGES,
- GS_BUF_N_CONTRIB) = range(12)
+ GS_BUF_REC_C_OPAC_RG, GS_BUF_REC_B, GS_BUF_SORTED_VALUES, GS_BUF_TILE_RANGES, GS_BUF_N_CONTRIB) = range(11)
 
 EXPORTS = ("gs_default_params", "gs_last_error", "gs_workspace_create", "gs_workspace_destroy", "gs_workspace_bytes",
            "gs_preprocess", "gs_bin_sort", "gs_render_fwd", "gs_render_bwd", "gs_importance", "gs_photometric_loss",
            "gs_adam_step", "gs_sync_status", "gs_workspace_counts", "gs_clear_error", "gs_workspace_buffer",
-           "gs_kernel_launches")
+           "gs_kernel_launches", "gs_render_bwd_adam", "gs_render_bwd_compact", "gs_adam_step_compact")
 
 
 class GSError(RuntimeError):
@@ -103,6 +102,10 @@ def lib() -> ctypes.CDLL:
         L.gs_bin_sort.argtypes = [vp, vp]
         L.gs_render_fwd.argtypes = [vp, vp, vp, vp]
         L.gs_render_bwd.argtypes = [vp, vp, vp, vp, i32, vp, ctypes.c_float, vp, vp]
+        f32 = ctypes.c_float
+        L.gs_render_bwd_adam.argtypes = [vp, vp, vp, vp, vp, vp, f32, f32, f32, i32, vp, f32, vp, vp]
+        L.gs_render_bwd_compact.argtypes = [vp, vp, vp, vp, f32, vp, vp]
+        L.gs_adam_step_compact.argtypes = [vp, vp, vp, vp, vp, f32, f32, f32, i32, vp]
         L.gs_importance.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
         L.gs_photometric_loss.argtypes = [vp, vp, vp, i32, i32, i32, ctypes.c_float, vp, vp, vp]
         L.gs_adam_step.argtypes = [vp, i32, i32, vp]
@@ -268,6 +271,30 @@ class Workspace:
         gc, gr = g.c(), grads.c_grads()
         _check(lib().gs_render_bwd(self._ws, ctypes.byref(gc), _ptr(dL_drgb), ctypes.byref(gr), int(accumulate),
                                    _ptr(absgrad), float(scale_reg_beta), _ptr(scale_reg_value), _stream(stream)))
+
+    def render_bwd_adam(self, g: GaussianTensors, dL_drgb, m: GaussianTensors, v: GaussianTensors, lr, step,
+                        beta1=0.9, beta2=0.999, eps=1e-15, absgrad=None, scale_reg_beta=0.0, scale_reg_value=None,
+                        stream=None):
+        """Backward fused with an Adam step: g's arrays are updated in place.
+        lr: five learning rates (mean, log-scale, quat, opacity, SH)."""
+        gc, mc, vc = g.c(), m.c_grads(), v.c_grads()
+        lrs = (ctypes.c_float * 5)(*lr)
+        _check(lib().gs_render_bwd_adam(self._ws, ctypes.byref(gc), _ptr(dL_drgb), ctypes.byref(mc), ctypes.byref(vc),
+                                        lrs, float(beta1), float(beta2), float(eps), int(step), _ptr(absgrad),
+                                        float(scale_reg_beta), _ptr(scale_reg_value), _stream(stream)))
+
+    def render_bwd_compact(self, g: GaussianTensors, dL_drgb, absgrad=None, scale_reg_beta=0.0, scale_reg_value=None,
+                           stream=None):
+        gc = g.c()
+        _check(lib().gs_render_bwd_compact(self._ws, ctypes.byref(gc), _ptr(dL_drgb), _ptr(absgrad),
+                                           float(scale_reg_beta), _ptr(scale_reg_value), _stream(stream)))
+
+    def adam_step_compact(self, g: GaussianTensors, m: GaussianTensors, v: GaussianTensors, lr, step, beta1=0.9,
+                          beta2=0.999, eps=1e-15, stream=None):
+        gc, mc, vc = g.c(), m.c_grads(), v.c_grads()
+        lrs = (ctypes.c_float * 5)(*lr)
+        _check(lib().gs_adam_step_compact(self._ws, ctypes.byref(gc), ctypes.byref(mc), ctypes.byref(vc), lrs,
+                                          float(beta1), float(beta2), float(eps), int(step), _stream(stream)))
 
     def importance(self, w=None, a=None, s_accum=None, crad=None, cvis=None, cull_out=None, stream=None):
         _check(lib().gs_importance(self._ws, _ptr(w), _ptr(a), _ptr(s_accum), _ptr(crad), _ptr(cvis), _ptr(cull_out),

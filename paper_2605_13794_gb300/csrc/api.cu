@@ -46,7 +46,7 @@ struct Layout {
 };
 
 struct Offsets {
-    size_t rec_off, rec_g, rec_cam, rd0, rd1, rd2, rect, tt, inst_off, clampm, rgrad, dkey0, dkey1, dval0, dval1;
+    size_t cand_g, cand_mask, rec_first, cgrad, rec_g, rec_cam, rd0, rd1, rd2, rect, tt, inst_off, clampm, rgrad, dkey0, dkey1, dval0, dval1;
     size_t tkey0, tkey1, tval0, tval1, slots, ranges, n_contrib, T_final, imp_w, imp_a, sel_cum;
     size_t selk0, selk1, selv0, selv1, loss_maps, loss_partial, lb_status, rx_status, rx_hist, rx_off, red_partial,
         ctr;
@@ -60,7 +60,10 @@ Offsets plan(const gs_capacity &c)
     Layout L;
     const size_t N = (size_t)c.max_gaussians, R = (size_t)c.max_records, I = (size_t)c.max_instances;
     const size_t T = (size_t)c.max_tiles, P = (size_t)c.max_pixels;
-    o.rec_off = L.take<uint32_t>(N + 1);
+    o.cand_g = L.take<uint32_t>(N);
+    o.cand_mask = L.take<unsigned long long>(N);
+    o.rec_first = L.take<uint32_t>(N);
+    o.cgrad = L.take<float>(R * gs::kGradRow);
     o.rec_g = L.take<uint32_t>(R);
     o.rec_cam = L.take<uint16_t>(R);
     o.rd0 = L.take<float4>(R);
@@ -101,7 +104,7 @@ Offsets plan(const gs_capacity &c)
     o.rx_status = L.take<uint32_t>(o.rx_words);
     o.rx_hist = L.take<uint32_t>(4 * 256);
     o.rx_off = L.take<uint32_t>(4 * 256);
-    const size_t k8 = N / 128 + 2, sel = 2 * (R / 4096 + 2);
+    const size_t k8 = R / 128 + 2, sel = 2 * (R / 4096 + 2);
     o.red_words = k8 > sel ? k8 : sel;
     o.red_partial = L.take<float>(o.red_words);
     o.ctr = L.take<gs::DevCounters>(1);
@@ -179,7 +182,10 @@ int gs_workspace_create(const gs_capacity *cap, gs_workspace **out)
     }
     ws->bytes = o.total;
     char *b = (char *)ws->base;
-    ws->rec_off = (uint32_t *)(b + o.rec_off);
+    ws->cand_g = (uint32_t *)(b + o.cand_g);
+    ws->cand_mask = (unsigned long long *)(b + o.cand_mask);
+    ws->rec_first = (uint32_t *)(b + o.rec_first);
+    ws->cgrad = (float *)(b + o.cgrad);
     ws->rec_g = (uint32_t *)(b + o.rec_g);
     ws->rec_cam = (uint16_t *)(b + o.rec_cam);
     ws->rd0 = (float4 *)(b + o.rd0);
@@ -234,7 +240,7 @@ int gs_workspace_destroy(gs_workspace *ws)
     return GS_OK;
 }
 
-static bool aligned4(const void *p) { return ((uintptr_t)p & 3u) == 0; }
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 int gs_preprocess(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams, int32_t n_cams,
                   const uint32_t *cull, const gs_render_params *params, gs_stream stream)
@@ -248,12 +254,14 @@ int gs_preprocess(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams
     if (params->tile_size != GS_TILE) return fail(GS_ERR_INVALID_ARG, "gs_preprocess: tile_size must be %d", GS_TILE);
     if (g->n > 0 && (!g->mean || !g->log_scale || !g->quat || !g->opacity_logit || !g->sh))
         return fail(GS_ERR_INVALID_ARG, "gs_preprocess: NULL Gaussian array");
-    if (!aligned4(g->mean) || !aligned4(g->log_scale) || !aligned4(g->quat) || !aligned4(g->opacity_logit) ||
-        !aligned4(g->sh))
-        return fail(GS_ERR_INVALID_ARG, "gs_preprocess: Gaussian arrays must be 4-byte aligned");
+    if (!aligned16(g->mean) || !aligned16(g->log_scale) || !aligned16(g->quat) || !aligned16(g->opacity_logit) ||
+        !aligned16(g->sh))
+        return fail(GS_ERR_INVALID_ARG, "gs_preprocess: Gaussian arrays must be 16-byte aligned");
     if (params->cull_enable && !cull) return fail(GS_ERR_INVALID_ARG, "gs_preprocess: cull_enable needs a cull array");
-    if (params->lod_enable && (params->lod_Lmax < 0 || !(params->lod_f > 1.f) || !(params->lod_d0 > 0.f)))
-        return fail(GS_ERR_INVALID_ARG, "gs_preprocess: LOD gate needs lod_Lmax >= 0, lod_f > 1, lod_d0 > 0");
+    if (params->lod_enable && (params->lod_Lmax < 0 || params->lod_Lmax > gs::kMaxLod || !(params->lod_f > 1.f) ||
+                               !(params->lod_d0 > 0.f)))
+        return fail(GS_ERR_INVALID_ARG, "gs_preprocess: LOD gate needs 0 <= lod_Lmax <= %d, lod_f > 1, lod_d0 > 0",
+                    gs::kMaxLod);
     gs::CamTable ct;
     memset(&ct, 0, sizeof(ct));
     ct.n = n_cams;
@@ -273,6 +281,11 @@ int gs_preprocess(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams
         d.tiles_y = (s.height + GS_TILE - 1) / GS_TILE;
         d.tile_base = (int)tiles;
         d.pix_base = pix;
+        {
+            const double lx = (double)params->fov_clamp * s.width / (2.0 * s.fx);
+            const double ly = (double)params->fov_clamp * s.height / (2.0 * s.fy);
+            d.jbound = (float)(1.001 * ((double)s.fx * s.fx * (1 + lx * lx) + (double)s.fy * s.fy * (1 + ly * ly)));
+        }
         tiles += (long long)d.tiles_x * d.tiles_y;
         pix += (long long)s.width * s.height;
     }
@@ -286,11 +299,17 @@ int gs_preprocess(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams
     rc.lod_d0 = params->lod_d0; rc.lod_f = params->lod_f;
     rc.lod_enable = params->lod_enable; rc.lod_Lmax = params->lod_Lmax; rc.cull_enable = params->cull_enable;
     rc.eps_score = params->eps_score; rc.vis_mass = params->vis_mass;
+    // round(log_f(d0 / d)) >= l  <=>  d <= d0 f^(0.5 - l)  (half away from zero, l >= 1)
+    for (int l = 0; l <= gs::kMaxLod; l++) {
+        const double thr = (double)params->lod_d0 * pow((double)params->lod_f, 0.5 - l);
+        rc.lod_thr2[l] = l == 0 ? INFINITY : (float)(thr * thr);
+    }
     ws->cams = ct;
     ws->rc = rc;
     ws->g = *g;
     ws->have_preprocess = 1;
     ws->have_binning = 0;
+    ws->have_compact = 0;
     CK(gs::launch_preprocess(ws, (cudaStream_t)stream, cull), "gs_preprocess");
     return GS_OK;
 }
@@ -342,9 +361,59 @@ int gs_render_bwd(gs_workspace *ws, const gs_gaussians *g, const float *dL_drgb,
     cudaStream_t st = (cudaStream_t)stream;
     CK(gs::launch_render_bwd(ws, st, dL_drgb), "gs_render_bwd(raster)");
     CK(gs::launch_reduce_slots(ws, st), "gs_render_bwd(reduce)");
-    CK(gs::launch_preprocess_bwd(ws, st, *g, *grads, accumulate, absgrad, scale_reg_beta, scale_reg_value),
+    CK(gs::launch_preprocess_bwd(ws, st, *g, *grads, accumulate, absgrad, scale_reg_beta, scale_reg_value, nullptr),
        "gs_render_bwd(preprocess)");
     return GS_OK;
+}
+
+int gs_render_bwd_compact(gs_workspace *ws, const gs_gaussians *g, const float *dL_drgb, float *absgrad,
+                          float scale_reg_beta, float *scale_reg_value, gs_stream stream)
+{
+    if (!ws || !g || !dL_drgb) return fail(GS_ERR_INVALID_ARG, "gs_render_bwd_compact: NULL argument");
+    if (!ws->have_binning)
+        return fail(GS_ERR_INVALID_ARG, "gs_render_bwd_compact: call gs_bin_sort and gs_render_fwd first");
+    if (g->n != ws->g.n) return fail(GS_ERR_INVALID_ARG, "gs_render_bwd_compact: Gaussian count differs from preprocess");
+    cudaStream_t st = (cudaStream_t)stream;
+    gs_gaussian_grads none;
+    memset(&none, 0, sizeof(none));
+    CK(gs::launch_render_bwd(ws, st, dL_drgb), "gs_render_bwd_compact(raster)");
+    CK(gs::launch_reduce_slots(ws, st), "gs_render_bwd_compact(reduce)");
+    CK(gs::launch_preprocess_bwd(ws, st, *g, none, 0, absgrad, scale_reg_beta, scale_reg_value, ws->cgrad),
+       "gs_render_bwd_compact(preprocess)");
+    ws->have_compact = 1;
+    return GS_OK;
+}
+
+int gs_adam_step_compact(gs_workspace *ws, const gs_gaussians *g, const gs_gaussian_grads *m,
+                         const gs_gaussian_grads *v, const float lr[5], float beta1, float beta2, float eps,
+                         int32_t step, gs_stream stream)
+{
+    if (!ws || !g || !m || !v || !lr) return fail(GS_ERR_INVALID_ARG, "gs_adam_step_compact: NULL argument");
+    if (!ws->have_compact)
+        return fail(GS_ERR_INVALID_ARG, "gs_adam_step_compact: no gs_render_bwd_compact since the last preprocess");
+    if (g->n != ws->g.n) return fail(GS_ERR_INVALID_ARG, "gs_adam_step_compact: Gaussian count differs from preprocess");
+    if (step < 1) return fail(GS_ERR_INVALID_ARG, "gs_adam_step_compact: step counts from 1");
+    if (g->n > 0 && (!m->mean || !m->log_scale || !m->quat || !m->opacity_logit || !m->sh || !v->mean ||
+                     !v->log_scale || !v->quat || !v->opacity_logit || !v->sh))
+        return fail(GS_ERR_INVALID_ARG, "gs_adam_step_compact: NULL moment array");
+    gs_gaussian_grads param;
+    param.mean = const_cast<float *>(g->mean);
+    param.log_scale = const_cast<float *>(g->log_scale);
+    param.quat = const_cast<float *>(g->quat);
+    param.opacity_logit = const_cast<float *>(g->opacity_logit);
+    param.sh = const_cast<float *>(g->sh);
+    CK(gs::launch_adam_sparse(ws, (cudaStream_t)stream, param, *m, *v, g->n, lr, beta1, beta2, eps, step),
+       "gs_adam_step_compact");
+    return GS_OK;
+}
+
+int gs_render_bwd_adam(gs_workspace *ws, const gs_gaussians *g, const float *dL_drgb, const gs_gaussian_grads *m,
+                       const gs_gaussian_grads *v, const float lr[5], float beta1, float beta2, float eps,
+                       int32_t step, float *absgrad, float scale_reg_beta, float *scale_reg_value, gs_stream stream)
+{
+    int rc = gs_render_bwd_compact(ws, g, dL_drgb, absgrad, scale_reg_beta, scale_reg_value, stream);
+    if (rc != GS_OK) return rc;
+    return gs_adam_step_compact(ws, g, m, v, lr, beta1, beta2, eps, step, stream);
 }
 
 int gs_importance(gs_workspace *ws, float *w, uint32_t *a, float *s_accum, uint32_t *crad_accum,
@@ -436,7 +505,6 @@ int gs_workspace_buffer(gs_workspace *ws, int32_t which, void **ptr, int64_t *co
     case GS_BUF_REC_XY_CONIC: *ptr = ws->rd0; *count = c.max_records; break;
     case GS_BUF_REC_C_OPAC_RG: *ptr = ws->rd1; *count = c.max_records; break;
     case GS_BUF_REC_B: *ptr = ws->rd2; *count = c.max_records; break;
-    case GS_BUF_REC_OFFSET: *ptr = ws->rec_off; *count = c.max_gaussians + 1; break;
     case GS_BUF_SORTED_VALUES: *ptr = ws->tval[ws->tile_buf]; *count = c.max_instances; break;
     case GS_BUF_TILE_RANGES: *ptr = ws->ranges; *count = c.max_tiles; break;
     case GS_BUF_N_CONTRIB: *ptr = ws->n_contrib; *count = c.max_pixels; break;

@@ -14,7 +14,9 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;          // keys per thread in a radix pass
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kSlotFloats = 9;          // per (record, tile) gradient slot: du dv dA dB dC do dr dg db
+constexpr int kGradRow = 59;            // parameters per Gaussian: mean 3, log-scale 3, quat 4, opacity 1, SH 48
 constexpr unsigned long long kSpinLimit = 1ull << 22;
+constexpr int kMaxLod = 15;             // largest supported L_max
 
 // Error sites recorded next to the error word (which kernel gave up).
 enum ErrorSite {
@@ -28,6 +30,7 @@ struct DevCounters {
     unsigned long long n_visible;
     unsigned long long records_needed;
     unsigned long long instances_needed;
+    unsigned long long n_candidates;   // Gaussians passing the gate stage of preprocess
     int error;
     int error_site;
     unsigned long long sel_count[GS_MAX_CAMERAS]; // w > 0 entries per camera (importance)
@@ -42,6 +45,7 @@ struct CamInfo {
     int tiles_x, tiles_y;
     int tile_base;        // first global tile id of this camera
     long long pix_base;   // first pixel of this camera in the concatenated outputs
+    float jbound;         // >= fx^2 (1 + limx^2) + fy^2 (1 + limy^2): bounds |J|_F^2 tz^2
 };
 
 struct CamTable {
@@ -58,6 +62,9 @@ struct RenderConsts {
     float lod_d0, lod_f;
     int lod_enable, lod_Lmax, cull_enable;
     float eps_score, vis_mass;
+    // LOD gate in squared-distance form: a level-l Gaussian (1 <= l <= Lmax)
+    // passes Eq. 1-2 iff d^2 <= lod_thr2[l] = (d0 f^(0.5 - l))^2
+    float lod_thr2[kMaxLod + 1];
 };
 
 __device__ __forceinline__ void set_error(DevCounters *ctr, int code, int site)
@@ -183,8 +190,11 @@ struct gs_workspace {
     int device;
     void *base;          // one device allocation, carved into the buffers below
     size_t bytes;
-    // per Gaussian
-    uint32_t *rec_off;   // [N+1]
+    // per Gaussian (candidates of the gate stage, in index order)
+    uint32_t *cand_g;              // [N]
+    unsigned long long *cand_mask; // [N] bit per camera
+    uint32_t *rec_first;           // [N] first record of each Gaussian, ~0 when none
+    float *cgrad;                  // [R][59] compact gradient rows (fused backward + Adam)
     // per record
     uint32_t *rec_g;
     uint16_t *rec_cam;
@@ -230,6 +240,7 @@ struct gs_workspace {
     gs_gaussians g;
     int have_preprocess;
     int have_binning;
+    int have_compact;    // compact gradient rows of the current binning exist
     int depth_buf;       // buffer holding sorted depth order
     int tile_buf;        // buffer holding sorted instances
 };
@@ -249,7 +260,12 @@ cudaError_t launch_render_bwd(gs_workspace *ws, cudaStream_t st, const float *dL
 cudaError_t launch_reduce_slots(gs_workspace *ws, cudaStream_t st);
 cudaError_t launch_preprocess_bwd(gs_workspace *ws, cudaStream_t st, const gs_gaussians &g,
                                   const gs_gaussian_grads &gr, int accumulate, float *absgrad, float beta,
-                                  float *scale_reg_value);
+                                  float *scale_reg_value, float *cgrad);
+// Adam over the five parameter arrays with gradients taken from the compact
+// rows (zero for Gaussians without a record).
+cudaError_t launch_adam_sparse(gs_workspace *ws, cudaStream_t st, const gs_gaussian_grads &param,
+                               const gs_gaussian_grads &m, const gs_gaussian_grads &v, long long n,
+                               const float lr[5], float beta1, float beta2, float eps, int step);
 cudaError_t launch_importance(gs_workspace *ws, cudaStream_t st, float *w, uint32_t *a, float *s_accum,
                               uint32_t *crad, uint32_t *cvis, uint32_t *cull_out);
 cudaError_t launch_loss(gs_workspace *ws, cudaStream_t st, const float *img, const float *tgt, int B, int H, int W,

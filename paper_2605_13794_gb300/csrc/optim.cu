@@ -191,51 +191,208 @@ cudaError_t launch_loss(gs_workspace *ws, cudaStream_t st, const float *img, con
 
 struct AdamTable {
     int n;
-    long long start[GS_MAX_ADAM_GROUPS + 1];
+    unsigned block_start[GS_MAX_ADAM_GROUPS + 1]; // first block of each group
+    long long count[GS_MAX_ADAM_GROUPS];
+    int vec[GS_MAX_ADAM_GROUPS];                  // all four arrays 16-byte aligned
     float *p[GS_MAX_ADAM_GROUPS];
     const float *g[GS_MAX_ADAM_GROUPS];
     float *m[GS_MAX_ADAM_GROUPS];
     float *v[GS_MAX_ADAM_GROUPS];
+    // sparse gradient source (fused backward): element e of the group belongs to
+    // Gaussian e / per_g; its gradient is cgrad[rec_first[gauss] * 59 + col + e % per_g],
+    // or 0 when rec_first[gauss] == ~0 (no record this step)
+    const uint32_t *rec_first[GS_MAX_ADAM_GROUPS];
+    const float *cgrad;
+    int col[GS_MAX_ADAM_GROUPS], per_g[GS_MAX_ADAM_GROUPS];
     float lr_c[GS_MAX_ADAM_GROUPS];   // lr / (1 - beta1^t)
     float ibc2[GS_MAX_ADAM_GROUPS];   // 1 / sqrt(1 - beta2^t)
     float b1[GS_MAX_ADAM_GROUPS], b2[GS_MAX_ADAM_GROUPS], eps[GS_MAX_ADAM_GROUPS];
 };
 
+constexpr int kAdamPerThread = 4;  // float4 chunks per thread
+constexpr int kAdamBlockElems = 256 * 4 * kAdamPerThread;
+
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// m <- b1 m + (1 - b1) g;  v <- b2 v + (1 - b2) g^2;  p <- p - lr_c m / (sqrt(v) ibc2 + eps)
+// with lr_c = lr / (1 - b1^t), ibc2 = 1 / sqrt(1 - b2^t) (bias correction folded in).
+__device__ __forceinline__ void adam_one(float &p, float g, float &m, float &v, float b1, float b2, float lr_c,
+                                         float ibc2, float eps)
+{
+    m = fmaf(b1, m, (1.f - b1) * g);
+    v = fmaf(b2, v, (1.f - b2) * g * g);
+    p = fmaf(-lr_c * m, rcp_approx(fmaf(sqrt_approx(v), ibc2, eps)), p);
+}
+
+// Gradient of element e of a group with PER elements per Gaussian taken from
+// the compact rows: 0 unless Gaussian e / PER has a record.
+template <int PER>
+__device__ __forceinline__ float sparse_grad(const uint32_t *rec_first, const float *cgrad, int col, long long e)
+{
+    const long long gauss = (long long)((unsigned long long)e / (unsigned)PER);
+    const uint32_t rh = rec_first[gauss];
+    return rh == 0xffffffffu ? 0.f : cgrad[(long long)rh * kGradRow + col + (e - gauss * PER)];
+}
+
+template <int PER>
+__device__ __forceinline__ float4 sparse_grad4(const uint32_t *rec_first, const float *cgrad, int col, long long e)
+{
+    if (PER % 4 == 0) { // the chunk lies in one Gaussian's row: one lookup
+        const long long gauss = (long long)((unsigned long long)e / (unsigned)PER);
+        const uint32_t rh = rec_first[gauss];
+        if (rh == 0xffffffffu) return make_float4(0.f, 0.f, 0.f, 0.f);
+        const float *row = cgrad + (long long)rh * kGradRow + col + (e - gauss * PER);
+        return make_float4(row[0], row[1], row[2], row[3]);
+    }
+    return make_float4(sparse_grad<PER>(rec_first, cgrad, col, e), sparse_grad<PER>(rec_first, cgrad, col, e + 1),
+                       sparse_grad<PER>(rec_first, cgrad, col, e + 2), sparse_grad<PER>(rec_first, cgrad, col, e + 3));
+}
+
+// One block's range of one group.  PER == 0: dense gradient array; PER > 0:
+// gradients from the compact rows, PER elements per Gaussian.
+template <int PER>
+__device__ __forceinline__ void adam_block(const AdamTable &t, int gi, long long base)
+{
+    const long long n = t.count[gi];
+    const float b1 = t.b1[gi], b2 = t.b2[gi], lr_c = t.lr_c[gi], ibc2 = t.ibc2[gi], eps = t.eps[gi];
+    float *P = t.p[gi], *M = t.m[gi], *V = t.v[gi];
+    const float *G = t.g[gi];
+    const uint32_t *rf = t.rec_first[gi];
+    const float *cg = t.cgrad;
+    const int col = t.col[gi];
+    if (t.vec[gi]) {
+        float4 pv[kAdamPerThread], gv[kAdamPerThread], mv[kAdamPerThread], vv[kAdamPerThread];
+        // every streaming load of this thread first ...
+#pragma unroll
+        for (int k = 0; k < kAdamPerThread; k++) {
+            const long long e = base + 4ll * (threadIdx.x + 256 * k);
+            if (e + 3 < n) {
+                pv[k] = __ldcs(reinterpret_cast<const float4 *>(P + e));
+                mv[k] = __ldcs(reinterpret_cast<const float4 *>(M + e));
+                vv[k] = __ldcs(reinterpret_cast<const float4 *>(V + e));
+                if (PER == 0) gv[k] = __ldcs(reinterpret_cast<const float4 *>(G + e));
+            }
+        }
+        // ... then the (mostly empty) compact-row lookups
+        if (PER > 0) {
+#pragma unroll
+            for (int k = 0; k < kAdamPerThread; k++) {
+                const long long e = base + 4ll * (threadIdx.x + 256 * k);
+                if (e + 3 < n) gv[k] = sparse_grad4<(PER > 0 ? PER : 1)>(rf, cg, col, e);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kAdamPerThread; k++) {
+            const long long e = base + 4ll * (threadIdx.x + 256 * k);
+            if (e + 3 < n) {
+                adam_one(pv[k].x, gv[k].x, mv[k].x, vv[k].x, b1, b2, lr_c, ibc2, eps);
+                adam_one(pv[k].y, gv[k].y, mv[k].y, vv[k].y, b1, b2, lr_c, ibc2, eps);
+                adam_one(pv[k].z, gv[k].z, mv[k].z, vv[k].z, b1, b2, lr_c, ibc2, eps);
+                adam_one(pv[k].w, gv[k].w, mv[k].w, vv[k].w, b1, b2, lr_c, ibc2, eps);
+                __stcs(reinterpret_cast<float4 *>(P + e), pv[k]);
+                __stcs(reinterpret_cast<float4 *>(M + e), mv[k]);
+                __stcs(reinterpret_cast<float4 *>(V + e), vv[k]);
+            } else {
+                for (long long q = e; q < n && q < e + 4; q++)
+                    adam_one(P[q], PER == 0 ? G[q] : sparse_grad<(PER > 0 ? PER : 1)>(rf, cg, col, q), M[q], V[q],
+                             b1, b2, lr_c, ibc2, eps);
+            }
+        }
+    } else {
+        for (int k = 0; k < 4 * kAdamPerThread; k++) {
+            const long long q = base + threadIdx.x + 256ll * k;
+            if (q < n)
+                adam_one(P[q], PER == 0 ? G[q] : sparse_grad<(PER > 0 ? PER : 1)>(rf, cg, col, q), M[q], V[q], b1,
+                         b2, lr_c, ibc2, eps);
+        }
+    }
+}
+
+// One block range per group; the group's gradient source is resolved once per
+// block.  Streaming: 28 bytes of HBM traffic per parameter with a dense
+// gradient, 24 with the compact rows.
 __global__ void __launch_bounds__(256) adam_kernel(AdamTable t)
 {
-    const long long total = t.start[t.n];
-    for (long long k = (long long)blockIdx.x * 256 + threadIdx.x; k < total; k += (long long)gridDim.x * 256) {
-        int gi = 0;
-        while (k >= t.start[gi + 1]) gi++;
-        const long long i = k - t.start[gi];
-        const float g = t.g[gi][i];
-        const float m = t.b1[gi] * t.m[gi][i] + (1.f - t.b1[gi]) * g;
-        const float v = t.b2[gi] * t.v[gi][i] + (1.f - t.b2[gi]) * g * g;
-        t.m[gi][i] = m;
-        t.v[gi][i] = v;
-        t.p[gi][i] -= t.lr_c[gi] * m / (sqrtf(v) * t.ibc2[gi] + t.eps[gi]);
+    int gi = 0;
+    while (blockIdx.x >= t.block_start[gi + 1]) gi++;
+    const long long base = (long long)(blockIdx.x - t.block_start[gi]) * kAdamBlockElems;
+    if (!t.rec_first[gi]) { adam_block<0>(t, gi, base); return; }
+    switch (t.per_g[gi]) {
+    case 48: adam_block<48>(t, gi, base); break;
+    case 4: adam_block<4>(t, gi, base); break;
+    case 3: adam_block<3>(t, gi, base); break;
+    default: adam_block<1>(t, gi, base); break;
     }
+}
+
+static cudaError_t run_adam(AdamTable &t, int n_groups, cudaStream_t st)
+{
+    for (int k = n_groups; k < GS_MAX_ADAM_GROUPS; k++) t.block_start[k + 1] = t.block_start[k];
+    if (t.block_start[n_groups] == 0) return cudaSuccess;
+    adam_kernel<<<t.block_start[n_groups], 256, 0, st>>>(t);
+    note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_adam(const gs_adam_group *groups, int n_groups, int step, cudaStream_t st)
 {
     AdamTable t;
     t.n = n_groups;
-    t.start[0] = 0;
+    t.cgrad = nullptr;
+    t.block_start[0] = 0;
+    auto al16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
     for (int k = 0; k < n_groups; k++) {
         const gs_adam_group &g = groups[k];
-        t.start[k + 1] = t.start[k] + g.n;
+        const long long blocks = (g.n + kAdamBlockElems - 1) / kAdamBlockElems;
+        t.block_start[k + 1] = t.block_start[k] + (unsigned)blocks;
+        t.count[k] = g.n;
+        t.vec[k] = al16(g.param) && al16(g.grad) && al16(g.m) && al16(g.v);
         t.p[k] = g.param; t.g[k] = g.grad; t.m[k] = g.m; t.v[k] = g.v;
         t.lr_c[k] = (float)(g.lr / (1.0 - pow((double)g.beta1, step)));
         t.ibc2[k] = (float)(1.0 / sqrt(1.0 - pow((double)g.beta2, step)));
         t.b1[k] = g.beta1; t.b2[k] = g.beta2; t.eps[k] = g.eps;
+        t.rec_first[k] = nullptr; t.col[k] = 0; t.per_g[k] = 1;
     }
-    if (t.start[n_groups] == 0) return cudaSuccess;
-    long long blocks = (t.start[n_groups] + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    adam_kernel<<<(unsigned)blocks, 256, 0, st>>>(t);
-    note_launch();
-    return cudaGetLastError();
+    return run_adam(t, n_groups, st);
+}
+
+cudaError_t launch_adam_sparse(gs_workspace *ws, cudaStream_t st, const gs_gaussian_grads &param,
+                               const gs_gaussian_grads &m, const gs_gaussian_grads &v, long long n,
+                               const float lr[5], float beta1, float beta2, float eps, int step)
+{
+    AdamTable t;
+    t.n = 5;
+    t.cgrad = ws->cgrad;
+    t.block_start[0] = 0;
+    float *P[5] = {param.mean, param.log_scale, param.quat, param.opacity_logit, param.sh};
+    float *M[5] = {m.mean, m.log_scale, m.quat, m.opacity_logit, m.sh};
+    float *V[5] = {v.mean, v.log_scale, v.quat, v.opacity_logit, v.sh};
+    const int per[5] = {3, 3, 4, 1, 48}, col[5] = {0, 3, 6, 10, 11};
+    auto al16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
+    for (int k = 0; k < 5; k++) {
+        const long long cnt = n * per[k];
+        t.block_start[k + 1] = t.block_start[k] + (unsigned)((cnt + kAdamBlockElems - 1) / kAdamBlockElems);
+        t.count[k] = cnt;
+        t.vec[k] = al16(P[k]) && al16(M[k]) && al16(V[k]);
+        t.p[k] = P[k]; t.g[k] = nullptr; t.m[k] = M[k]; t.v[k] = V[k];
+        t.rec_first[k] = ws->rec_first; t.col[k] = col[k]; t.per_g[k] = per[k];
+        t.lr_c[k] = (float)(lr[k] / (1.0 - pow((double)beta1, step)));
+        t.ibc2[k] = (float)(1.0 / sqrt(1.0 - pow((double)beta2, step)));
+        t.b1[k] = beta1; t.b2[k] = beta2; t.eps[k] = eps;
+    }
+    return run_adam(t, 5, st);
 }
 
 } // namespace gs

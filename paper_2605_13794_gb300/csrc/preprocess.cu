@@ -88,34 +88,50 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float d
 
 __device__ __forceinline__ float clampf(float x, float lo, float hi) { return x < lo ? lo : (x > hi ? hi : x); }
 
-// View gate + projection of one Gaussian into one camera.  Returns false when
-// the Gaussian is gated, culled, behind the near plane, degenerate, or has an
-// empty tile rectangle.
-__device__ __forceinline__ bool project_gaussian(const float m[3], const float ls[3], const float qin[4], int lod,
-                                                 bool culled, const CamInfo &cam, const RenderConsts &rc, Proj &o)
+// Distance LOD gate (Sec. 3.3, Eq. 1-2) in its squared-distance form:
+// keep level l iff l == 0, or l <= Lmax and |mu - c|^2 <= (d0 f^(0.5 - l))^2,
+// which is l <= clamp(round(log_f(d0 / d)), 0, Lmax) with half-away rounding.
+__device__ __forceinline__ bool lod_pass(const float m[3], int lod, const CamInfo &cam, const RenderConsts &rc)
 {
-    if (rc.lod_enable) {
-        float dx = FSUB(m[0], cam.campos[0]), dy = FSUB(m[1], cam.campos[1]), dz = FSUB(m[2], cam.campos[2]);
-        float d = FSQRT(FADD(FADD(FMUL(dx, dx), FMUL(dy, dy)), FMUL(dz, dz)));
-        int L;
-        if (d > 0.f) {
-            float x = FDIV(log2f(FDIV(rc.lod_d0, d)), log2f(rc.lod_f));
-            float r = x >= 0.f ? floorf(FADD(x, 0.5f)) : -floorf(FADD(-x, 0.5f)); // half away from zero
-            L = (int)r;
-        } else {
-            L = rc.lod_Lmax;
-        }
-        L = L < 0 ? 0 : (L > rc.lod_Lmax ? rc.lod_Lmax : L);
-        if (lod > L) return false;
-    }
-    if (rc.cull_enable && culled) return false;
+    if (!rc.lod_enable || lod == 0) return true;
+    if (lod > rc.lod_Lmax) return false;
+    const float dx = FSUB(m[0], cam.campos[0]), dy = FSUB(m[1], cam.campos[1]), dz = FSUB(m[2], cam.campos[2]);
+    const float d2 = FADD(FADD(FMUL(dx, dx), FMUL(dy, dy)), FMUL(dz, dz));
+    return d2 <= rc.lod_thr2[lod];
+}
 
+__device__ __forceinline__ void camera_point(const float m[3], const CamInfo &cam, float &tx, float &ty, float &tz)
+{
     const float *R = cam.R;
-    float tx = FADD(FADD(FADD(FMUL(R[0], m[0]), FMUL(R[1], m[1])), FMUL(R[2], m[2])), cam.t[0]);
-    float ty = FADD(FADD(FADD(FMUL(R[3], m[0]), FMUL(R[4], m[1])), FMUL(R[5], m[2])), cam.t[1]);
-    float tz = FADD(FADD(FADD(FMUL(R[6], m[0]), FMUL(R[7], m[1])), FMUL(R[8], m[2])), cam.t[2]);
-    if (!(tz > rc.znear)) return false;
+    tx = FADD(FADD(FADD(FMUL(R[0], m[0]), FMUL(R[1], m[1])), FMUL(R[2], m[2])), cam.t[0]);
+    ty = FADD(FADD(FADD(FMUL(R[3], m[0]), FMUL(R[4], m[1])), FMUL(R[5], m[2])), cam.t[1]);
+    tz = FADD(FADD(FADD(FMUL(R[6], m[0]), FMUL(R[7], m[1])), FMUL(R[8], m[2])), cam.t[2]);
+}
 
+// Conservative screen test run before the exact covariance: false only when
+// the exact tile rectangle is certainly empty.  lambda_max(Sigma') <=
+// |J|_F^2 max_j s_j^2 + dilation, |J|_F^2 <= jbound / tz^2 (clamped Jacobian),
+// plus sqrt(0.1) for the clamp of the discriminant, with margins for rounding.
+__device__ __forceinline__ bool maybe_on_screen(float tx, float ty, float tz, float smax, const CamInfo &cam,
+                                                const RenderConsts &rc)
+{
+    const float itz = 1.f / tz;
+    const float u = cam.fx * tx * itz + cam.cx, v = cam.fy * ty * itz + cam.cy;
+    const float lam = 1.01f * (cam.jbound * itz * itz * smax * smax + rc.dilation) + 0.33f;
+    const float R = 3.f * sqrtf(lam) + 2.f;
+    const float ru = R + 1e-5f * fabsf(u), rv = R + 1e-5f * fabsf(v);
+    return !(u + ru < 0.f || u - ru >= (float)(cam.tiles_x * kTile) || v + rv < 0.f ||
+             v - rv >= (float)(cam.tiles_y * kTile));
+}
+
+// Exact projection of one Gaussian into one camera (after the gate and the
+// near cull).  Returns false when the 2D covariance is degenerate or the tile
+// rectangle is empty.
+__device__ __forceinline__ bool project_gaussian(const float m[3], const float ls[3], const float qin[4],
+                                                 float tx, float ty, float tz, const CamInfo &cam,
+                                                 const RenderConsts &rc, Proj &o)
+{
+    const float *R = cam.R;
     float qw = qin[0], qx = qin[1], qy = qin[2], qz = qin[3];
     float qn = FSQRT(FADD(FADD(FADD(FMUL(qw, qw), FMUL(qx, qx)), FMUL(qy, qy)), FMUL(qz, qz)));
     qw = FDIV(qw, qn); qx = FDIV(qx, qn); qy = FDIV(qy, qn); qz = FDIV(qz, qn);
@@ -191,107 +207,216 @@ __device__ __forceinline__ bool project_gaussian(const float m[3], const float l
 }
 
 struct PreOut {
-    uint32_t *rec_off, *rec_g, *tt, *dkey;
+    uint32_t *rec_g, *tt, *dkey;
     uint16_t *rec_cam;
     float4 *rd0, *rd1;
     float *rd2;
     uint2 *rect;
     uint8_t *clampm;
-    unsigned long long *lb_status;
-    unsigned int *ticket;
+    uint32_t *cand_g;
+    unsigned long long *cand_mask;
+    uint32_t *rec_first;           // first record of each Gaussian, ~0 when it has none
+    unsigned long long *lb_status; // word 0: ticket
     DevCounters *ctr;
     long long max_records;
     const uint32_t *cull;
     long long cull_words;
 };
 
-template <bool MULTI>
-__global__ void __launch_bounds__(256) preprocess_kernel(GaussPtrs g, PreOut o, CamTable ct, RenderConsts rc)
+struct GaussLoad {
+    float m[3], ls[3], q[4];
+    float smax;
+    bool have_shape;
+};
+
+__device__ __forceinline__ void load_shape(const GaussPtrs &g, long long i, GaussLoad &L)
+{
+    if (L.have_shape) return;
+    const long long n = g.n;
+    L.ls[0] = g.log_scale[3 * i]; L.ls[1] = g.log_scale[3 * i + 1]; L.ls[2] = g.log_scale[3 * i + 2];
+    const float4 q = *reinterpret_cast<const float4 *>(g.quat + 4 * i); // 16-byte aligned rows
+    L.q[0] = q.x; L.q[1] = q.y; L.q[2] = q.z; L.q[3] = q.w;
+    L.smax = expf(fmaxf(L.ls[0], fmaxf(L.ls[1], L.ls[2])));
+    L.have_shape = true;
+}
+
+constexpr int kGateItems = 8; // Gaussians per thread of the gate kernel: 2048 per block
+
+__device__ __forceinline__ bool cull_bit(const PreOut &o, int c, long long i)
+{
+    return o.cull ? ((o.cull[c * o.cull_words + (i >> 5)] >> (i & 31)) & 1u) : false;
+}
+
+// Stage 1, streaming over all Gaussians: the view gate (LOD, Cull), the near
+// plane and the conservative screen test -- everything that is cheap and
+// rejects most of a city scene -- producing an order-preserving list of
+// candidate Gaussians with a bit per camera that may still be active.
+// Thread t of block b owns Gaussians b*2048 + k*256 + t (k < 8).
+__global__ void __launch_bounds__(256) gate_kernel(GaussPtrs g, PreOut o, CamTable ct, RenderConsts rc)
+{
+    __shared__ unsigned s_bid;
+    __shared__ unsigned s_cnt[kGateItems][8];
+    __shared__ unsigned s_total;
+    __shared__ unsigned long long s_base;
+    if (threadIdx.x == 0) s_bid = atomicAdd((unsigned *)o.lb_status, 1u);
+    __syncthreads();
+    const unsigned bid = s_bid;
+    const long long n = g.n;
+    const long long block0 = (long long)bid * 256 * kGateItems;
+    float mx[kGateItems], my[kGateItems], mz[kGateItems];
+    int lod[kGateItems];
+#pragma unroll
+    for (int k = 0; k < kGateItems; k++) {
+        const long long i = block0 + k * 256 + threadIdx.x;
+        const bool ok = i < n;
+        mx[k] = ok ? g.mean[3 * i] : 0.f;
+        my[k] = ok ? g.mean[3 * i + 1] : 0.f;
+        mz[k] = ok ? g.mean[3 * i + 2] : 0.f;
+        lod[k] = (ok && rc.lod_enable && g.lod) ? (int)g.lod[i] : 0;
+    }
+    unsigned long long mask[kGateItems];
+#pragma unroll
+    for (int k = 0; k < kGateItems; k++) {
+        mask[k] = 0;
+        const long long i = block0 + k * 256 + threadIdx.x;
+        if (i >= n) continue;
+        const float m[3] = {mx[k], my[k], mz[k]};
+        float smax = -1.f;
+        for (int c = 0; c < ct.n; c++) {
+            const CamInfo &cam = ct.c[c];
+            if (!lod_pass(m, lod[k], cam, rc)) continue;
+            if (rc.cull_enable && cull_bit(o, c, i)) continue;
+            float tx, ty, tz;
+            camera_point(m, cam, tx, ty, tz);
+            if (!(tz > rc.znear)) continue;
+            if (smax < 0.f)
+                smax = expf(fmaxf(g.log_scale[3 * i], fmaxf(g.log_scale[3 * i + 1], g.log_scale[3 * i + 2])));
+            if (maybe_on_screen(tx, ty, tz, smax, cam, rc)) mask[k] |= 1ull << c;
+        }
+    }
+    // order-preserving compaction: item (k, thread) precedes (k', thread') iff
+    // k < k', or k == k' and thread < thread'
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned bal[kGateItems];
+#pragma unroll
+    for (int k = 0; k < kGateItems; k++) {
+        bal[k] = __ballot_sync(0xffffffffu, mask[k] != 0);
+        if (lane == 0) s_cnt[k][warp] = __popc(bal[k]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned run = 0;
+        for (int k = 0; k < kGateItems; k++)
+            for (int w = 0; w < 8; w++) { const unsigned c = s_cnt[k][w]; s_cnt[k][w] = run; run += c; }
+        s_total = run;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const unsigned long long b = lookback_exclusive(o.lb_status + 1, bid, s_total, o.ctr, kSitePreprocess);
+        if (threadIdx.x == 0) s_base = b;
+    }
+    __syncthreads();
+    const unsigned long long base = s_base;
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int k = 0; k < kGateItems; k++) {
+        if (mask[k]) {
+            const unsigned long long pos = base + s_cnt[k][warp] + __popc(bal[k] & lt);
+            o.cand_g[pos] = (uint32_t)(block0 + k * 256 + threadIdx.x);
+            o.cand_mask[pos] = mask[k];
+        }
+    }
+    const unsigned long long run = base + s_total;
+    if (bid == gridDim.x - 1 && threadIdx.x == 0) o.ctr->n_candidates = run;
+}
+
+// Stage 2, one thread per candidate (converged warps): the exact FP32
+// projection decides which cameras are active; the records are compacted in
+// (Gaussian, camera) order with a look-back scan and written with their
+// conic, colour, opacity, rectangle and depth key.
+__global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, CamTable ct, RenderConsts rc)
 {
     __shared__ unsigned s_bid;
     __shared__ unsigned long long s_warp[8];
     __shared__ unsigned long long s_base;
-    __shared__ unsigned s_vis[8];
-    if (threadIdx.x == 0) s_bid = atomicAdd(o.ticket, 1u);
+    if (threadIdx.x == 0) s_bid = atomicAdd((unsigned *)o.lb_status, 1u);
     __syncthreads();
     const unsigned bid = s_bid;
+    const unsigned long long ncand = o.ctr->n_candidates;
+    if ((unsigned long long)bid * 256 >= ncand) return;
     const long long n = g.n;
-    const long long i = (long long)bid * 256 + threadIdx.x;
-    const bool valid = i < n;
-
-    float m[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0};
-    int lod = 0;
-    if (valid) {
-        m[0] = g.mean[i]; m[1] = g.mean[n + i]; m[2] = g.mean[2 * n + i];
-        ls[0] = g.log_scale[i]; ls[1] = g.log_scale[n + i]; ls[2] = g.log_scale[2 * n + i];
-        q[0] = g.quat[i]; q[1] = g.quat[n + i]; q[2] = g.quat[2 * n + i]; q[3] = g.quat[3 * n + i];
-        lod = g.lod ? (int)g.lod[i] : 0;
-    }
-    unsigned long long mask = 0;
-    Proj p0;
-    if (valid) {
-        for (int c = 0; c < ct.n; c++) {
-            bool culled = o.cull ? ((o.cull[c * o.cull_words + (i >> 5)] >> (i & 31)) & 1u) : false;
+    const unsigned long long j = (unsigned long long)bid * 256 + threadIdx.x;
+    GaussLoad L;
+    L.have_shape = false;
+    long long i = 0;
+    unsigned long long act = 0;
+    if (j < ncand) {
+        i = o.cand_g[j];
+        const unsigned long long cm = o.cand_mask[j];
+        L.m[0] = g.mean[3 * i]; L.m[1] = g.mean[3 * i + 1]; L.m[2] = g.mean[3 * i + 2];
+        load_shape(g, i, L);
+        for (unsigned long long mm = cm; mm; mm &= mm - 1) {
+            const int c = __ffsll((long long)mm) - 1;
+            float tx, ty, tz;
+            camera_point(L.m, ct.c[c], tx, ty, tz);
             Proj p;
-            if (project_gaussian(m, ls, q, lod, culled, ct.c[c], rc, p)) {
-                mask |= 1ull << c;
-                if (!MULTI) p0 = p;
-            }
+            if (project_gaussian(L.m, L.ls, L.q, tx, ty, tz, ct.c[c], rc, p)) act |= 1ull << c;
         }
     }
-    const unsigned long long cnt = __popcll(mask);
-    unsigned long long total;
+    const unsigned long long cnt = __popcll(act);
+    unsigned long long total, tvis;
     const unsigned long long excl = block_exclusive_scan_256<unsigned long long>(cnt, s_warp, total);
+    block_exclusive_scan_256<unsigned long long>((unsigned long long)(cnt > 0), s_warp, tvis);
     if (threadIdx.x < 32) {
-        unsigned long long b = lookback_exclusive(o.lb_status + 1, bid, total, o.ctr, kSitePreprocess);
-        if (threadIdx.x == 0) s_base = b;
+        const unsigned long long b = lookback_exclusive(o.lb_status + 1, bid, total, o.ctr, kSitePreprocess);
+        if (threadIdx.x == 0) {
+            s_base = b;
+            if (tvis) atomicAdd(&o.ctr->n_visible, tvis); // the visible set of Eq. 5
+        }
     }
-    // count Gaussians with at least one record (visible set of Eq. 5)
-    unsigned vis = __ballot_sync(0xffffffffu, cnt > 0);
-    if ((threadIdx.x & 31) == 0) s_vis[threadIdx.x >> 5] = __popc(vis);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned tv = 0;
-        for (int w = 0; w < 8; w++) tv += s_vis[w];
-        if (tv) atomicAdd(&o.ctr->n_visible, (unsigned long long)tv);
-    }
     const unsigned long long base = s_base + excl;
-    if (!valid) return;
-    o.rec_off[i] = (uint32_t)base;
-    if (i == n - 1) {
-        unsigned long long end = base + cnt;
-        o.rec_off[n] = (uint32_t)(end < (unsigned long long)o.max_records ? end : o.max_records);
+    if (j == ncand - 1) {
+        const unsigned long long end = base + cnt;
         o.ctr->records_needed = end;
         o.ctr->n_records = end < (unsigned long long)o.max_records ? end : o.max_records;
     }
-    if (!mask) return;
-
+    if (!act) return;
+    if (base < (unsigned long long)o.max_records) o.rec_first[i] = (uint32_t)base;
     const float op = 1.f / (1.f + expf(-g.opacity_logit[i]));
     unsigned long long r = base;
-    for (unsigned long long mm = mask; mm; mm &= mm - 1, r++) {
+    for (unsigned long long mm = act; mm; mm &= mm - 1, r++) {
         const int c = __ffsll((long long)mm) - 1;
         if (r >= (unsigned long long)o.max_records) {
             set_error(o.ctr, GS_ERR_CAPACITY, kSitePreprocess);
             break;
         }
-        Proj p;
-        if (MULTI) project_gaussian(m, ls, q, lod, false, ct.c[c], rc, p); // same inputs: same (passing) result
-        else p = p0;
         const CamInfo &cam = ct.c[c];
-        // view direction and SH colour
-        float dx = m[0] - cam.campos[0], dy = m[1] - cam.campos[1], dz = m[2] - cam.campos[2];
-        float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+        float tx, ty, tz;
+        camera_point(L.m, cam, tx, ty, tz);
+        Proj p;
+        project_gaussian(L.m, L.ls, L.q, tx, ty, tz, cam, rc, p); // same inputs: same (passing) result
+        const float dx = L.m[0] - cam.campos[0], dy = L.m[1] - cam.campos[1], dz = L.m[2] - cam.campos[2];
+        const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
         float Y[16];
         sh_basis(dx * inv, dy * inv, dz * inv, Y);
-        float col[3];
-        uint8_t cm = 0;
+        float col[3] = {0.f, 0.f, 0.f};
+        uint8_t clm = 0;
+        const float4 *shv = reinterpret_cast<const float4 *>(g.sh + 48 * i); // [16][3], 16-byte aligned
+#pragma unroll
+        for (int v4 = 0; v4 < 12; v4++) {
+            const float4 c4 = shv[v4];
+            const float cc[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int flat = 4 * v4 + e; // coefficient flat / 3, channel flat % 3
+                col[flat % 3] = fmaf(cc[e], Y[flat / 3], col[flat % 3]);
+            }
+        }
 #pragma unroll
         for (int ch = 0; ch < 3; ch++) {
-            float acc = 0.f;
-#pragma unroll
-            for (int k = 0; k < 16; k++) acc = fmaf(g.sh[(long long)(3 * k + ch) * n + i], Y[k], acc);
-            acc += 0.5f;
-            if (acc < 0.f) { acc = 0.f; cm |= (uint8_t)(1u << ch); }
+            float acc = col[ch] + 0.5f;
+            if (acc < 0.f) { acc = 0.f; clm |= (uint8_t)(1u << ch); }
             col[ch] = acc;
         }
         o.rec_g[r] = (uint32_t)i;
@@ -302,66 +427,85 @@ __global__ void __launch_bounds__(256) preprocess_kernel(GaussPtrs g, PreOut o, 
         o.rect[r] = make_uint2((uint32_t)p.x0 | ((uint32_t)p.y0 << 16), (uint32_t)p.x1 | ((uint32_t)p.y1 << 16));
         o.tt[r] = (uint32_t)((p.x1 - p.x0) * (p.y1 - p.y0));
         o.dkey[r] = __float_as_uint(p.depth);
-        o.clampm[r] = cm;
+        o.clampm[r] = clm;
     }
 }
 
 cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t *cull)
 {
     const long long n = ws->g.n;
-    const unsigned blocks = (unsigned)((n + 255) / 256);
+    const unsigned gblocks = (unsigned)((n + 256 * kGateItems - 1) / (256 * kGateItems));
+    const unsigned pblocks = (unsigned)((n + 255) / 256);
     cudaError_t e;
-    // reset counters and the look-back state (ticket in word 0)
+    // counters, then the look-back state of each stage (ticket in word 0)
     if ((e = cudaMemsetAsync(ws->ctr, 0, sizeof(DevCounters), st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(ws->lb_status, 0, (blocks + 1) * sizeof(unsigned long long), st)) != cudaSuccess)
-        return e;
     if (n == 0) return cudaSuccess;
     GaussPtrs gp{ws->g.mean, ws->g.log_scale, ws->g.quat, ws->g.opacity_logit, ws->g.sh, ws->g.lod, n};
     PreOut o;
-    o.rec_off = ws->rec_off; o.rec_g = ws->rec_g; o.tt = ws->tt; o.dkey = ws->dkey[0];
+    o.rec_g = ws->rec_g; o.tt = ws->tt; o.dkey = ws->dkey[0];
     o.rec_cam = ws->rec_cam; o.rd0 = ws->rd0; o.rd1 = ws->rd1; o.rd2 = ws->rd2; o.rect = ws->rect;
-    o.clampm = ws->clampm; o.lb_status = ws->lb_status; o.ticket = (unsigned int *)ws->lb_status;
+    o.clampm = ws->clampm; o.cand_g = ws->cand_g; o.cand_mask = ws->cand_mask; o.rec_first = ws->rec_first;
+    o.lb_status = ws->lb_status;
     o.ctr = ws->ctr; o.max_records = ws->cap.max_records;
     o.cull = ws->rc.cull_enable ? cull : nullptr;
     o.cull_words = (n + 31) / 32;
-    if (ws->cams.n == 1)
-        preprocess_kernel<false><<<blocks, 256, 0, st>>>(gp, o, ws->cams, ws->rc);
-    else
-        preprocess_kernel<true><<<blocks, 256, 0, st>>>(gp, o, ws->cams, ws->rc);
+    if ((e = cudaMemsetAsync(ws->rec_first, 0xff, (size_t)n * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ws->lb_status, 0, (gblocks + 1) * sizeof(unsigned long long), st)) != cudaSuccess)
+        return e;
+    gate_kernel<<<gblocks, 256, 0, st>>>(gp, o, ws->cams, ws->rc);
+    note_launch();
+    if ((e = cudaMemsetAsync(ws->lb_status, 0, (pblocks + 1) * sizeof(unsigned long long), st)) != cudaSuccess)
+        return e;
+    project_kernel<<<pblocks, 256, 0, st>>>(gp, o, ws->cams, ws->rc);
     note_launch();
     return cudaGetLastError();
 }
 
 // ---- backward ---------------------------------------------------------------
 
-// Sum of the per-(record, tile) gradient slots of each record.  Records are
-// visited in depth order, in which their slots are contiguous.
+// Sum of the per-(record, tile) gradient slots of each record.  One warp per
+// record (records in depth order, whose slots are contiguous): lanes read the
+// slots strided by 32, then a fixed shuffle tree adds the lanes, so the sum is
+// the same on every run and no record's size serialises a thread.
 __global__ void __launch_bounds__(256) reduce_slots_kernel(const uint32_t *drec, const uint32_t *inst_off,
                                                            const uint32_t *tt, const float *slots, float *rgrad,
                                                            const DevCounters *ctr)
 {
-    const unsigned long long k = (unsigned long long)blockIdx.x * 256 + threadIdx.x;
-    if (k >= ctr->n_records) return;
-    const uint32_t r = drec[k];
-    const unsigned long long off = inst_off[r], cnt = tt[r];
-    if (off + cnt > ctr->n_instances) return; // capacity error already recorded
-    float acc[kSlotFloats];
+    const unsigned long long nrec = ctr->n_records, ninst = ctr->n_instances;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nwarps = (unsigned long long)gridDim.x * 8;
+    for (unsigned long long k = (unsigned long long)blockIdx.x * 8 + (threadIdx.x >> 5); k < nrec; k += nwarps) {
+        const uint32_t r = drec[k];
+        const unsigned long long off = inst_off[r], cnt = tt[r];
+        if (off + cnt > ninst) continue; // capacity error already recorded
+        float acc[kSlotFloats];
 #pragma unroll
-    for (int j = 0; j < kSlotFloats; j++) acc[j] = 0.f;
-    const float *s = slots + off * kSlotFloats;
-    for (unsigned long long t = 0; t < cnt; t++, s += kSlotFloats)
+        for (int j = 0; j < kSlotFloats; j++) acc[j] = 0.f;
+        for (unsigned long long t = lane; t < cnt; t += 32) {
+            const float *s = slots + (off + t) * kSlotFloats;
 #pragma unroll
-        for (int j = 0; j < kSlotFloats; j++) acc[j] += s[j];
+            for (int j = 0; j < kSlotFloats; j++) acc[j] += s[j];
+        }
 #pragma unroll
-    for (int j = 0; j < kSlotFloats; j++) rgrad[(unsigned long long)r * kSlotFloats + j] = acc[j];
+        for (int j = 0; j < kSlotFloats; j++)
+            for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+        if (lane < kSlotFloats) {
+            float v = acc[0];
+#pragma unroll
+            for (int j = 1; j < kSlotFloats; j++) v = lane == j ? acc[j] : v;
+            rgrad[(unsigned long long)r * kSlotFloats + lane] = v;
+        }
+    }
 }
 
 cudaError_t launch_reduce_slots(gs_workspace *ws, cudaStream_t st)
 {
     const long long cap = ws->cap.max_records;
-    const unsigned blocks = (unsigned)((cap + 255) / 256);
-    reduce_slots_kernel<<<blocks, 256, 0, st>>>(ws->dval[ws->depth_buf], ws->inst_off, ws->tt, ws->slots, ws->rgrad,
-                                                ws->ctr);
+    long long blocks = (cap + 7) / 8;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    reduce_slots_kernel<<<(unsigned)blocks, 256, 0, st>>>(ws->dval[ws->depth_buf], ws->inst_off, ws->tt, ws->slots,
+                                                         ws->rgrad, ws->ctr);
     note_launch();
     return cudaGetLastError();
 }
@@ -369,10 +513,11 @@ cudaError_t launch_reduce_slots(gs_workspace *ws, cudaStream_t st)
 struct BwdArgs {
     GaussPtrs g;
     float *gmean, *gls, *gquat, *gop, *gsh;
-    const uint32_t *rec_off;
+    const uint32_t *rec_g;
     const uint16_t *rec_cam;
     const uint8_t *clampm;
     const float *rgrad;
+    float *cgrad;      // non-NULL: write each Gaussian's gradient row here (at its first record) instead
     float *absgrad;
     int accumulate;
     float beta;
@@ -380,33 +525,29 @@ struct BwdArgs {
     const DevCounters *ctr;
 };
 
-__device__ __forceinline__ void store_grad(float *p, float v, int accumulate)
-{
-    if (accumulate) *p += v; else *p = v;
-}
-
 // Chain rule from the gradients of (u, v, conic A B C, opacity, rgb) of each
 // record to the parameters of its Gaussian, summed over the Gaussian's records.
 __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, CamTable ct, RenderConsts rc)
 {
     __shared__ float s_red[4];
     const long long n = a.g.n;
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // one thread per Gaussian that has records: the thread of its first record
+    const unsigned long long rh = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned long long nrec = a.ctr->n_records;
     float smin_val = 0.f;
-    if (i < n) {
-        const unsigned long long nrec = a.ctr->n_records;
-        unsigned long long r0 = a.rec_off[i], r1 = a.rec_off[i + 1];
-        if (r1 > nrec) r1 = nrec;
-        if (r0 > r1) r0 = r1;
+    const bool head = rh < nrec && (rh == 0 || a.rec_g[rh - 1] != a.rec_g[rh]);
+    if (head) {
+        const long long i = a.rec_g[rh];
+        unsigned long long r0 = rh, r1 = rh + 1; // a Gaussian's records are contiguous
+        while (r1 < nrec && a.rec_g[r1] == (uint32_t)i) r1++;
         float gm[3] = {0, 0, 0}, gls[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gop = 0.f;
         float gsh[48];
 #pragma unroll
         for (int k = 0; k < 48; k++) gsh[k] = 0.f;
-        const float m[3] = {a.g.mean[i], a.g.mean[n + i], a.g.mean[2 * n + i]};
-        const float ls[3] = {a.g.log_scale[i], a.g.log_scale[n + i], a.g.log_scale[2 * n + i]};
-        const bool has = r1 > r0;
-        if (has) {
-            const float qr[4] = {a.g.quat[i], a.g.quat[n + i], a.g.quat[2 * n + i], a.g.quat[3 * n + i]};
+        const float m[3] = {a.g.mean[3 * i], a.g.mean[3 * i + 1], a.g.mean[3 * i + 2]};
+        const float ls[3] = {a.g.log_scale[3 * i], a.g.log_scale[3 * i + 1], a.g.log_scale[3 * i + 2]};
+        {
+            const float qr[4] = {a.g.quat[4 * i], a.g.quat[4 * i + 1], a.g.quat[4 * i + 2], a.g.quat[4 * i + 3]};
             const float qn = sqrtf(qr[0] * qr[0] + qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]);
             const float q[4] = {qr[0] / qn, qr[1] / qn, qr[2] / qn, qr[3] / qn};
             const float w = q[0], x = q[1], y = q[2], z = q[3];
@@ -498,7 +639,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, CamTable
                     if (cm & (1u << ch)) continue;
                     const float gr = grgb[ch];
                     for (int k = 0; k < 16; k++) {
-                        const float coef = a.g.sh[(long long)(3 * k + ch) * n + i];
+                        const float coef = a.g.sh[48 * i + 3 * k + ch];
                         gsh[3 * k + ch] += gr * Y[k];
                         gd[0] += gr * coef * dY[k][0];
                         gd[1] += gr * coef * dY[k][1];
@@ -538,14 +679,22 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, CamTable
                 smin_val = s[jm];
             }
         }
-        if (has || !a.accumulate) {
+        if (a.cgrad) {
+            // compact row of 59 gradients (mean, log-scale, quat, opacity, SH) at the first record
+            float *row = a.cgrad + rh * kGradRow;
+            for (int k = 0; k < 3; k++) { row[k] = gm[k]; row[3 + k] = gls[k]; }
+            for (int k = 0; k < 4; k++) row[6 + k] = gq[k];
+            row[10] = gop;
+            for (int k = 0; k < 48; k++) row[11 + k] = gsh[k];
+        } else {
+            // the grads of Gaussians without records were zeroed (overwrite mode) or are left as they are
             for (int k = 0; k < 3; k++) {
-                store_grad(&a.gmean[k * n + i], gm[k], a.accumulate);
-                store_grad(&a.gls[k * n + i], gls[k], a.accumulate);
+                a.gmean[3 * i + k] += gm[k];
+                a.gls[3 * i + k] += gls[k];
             }
-            for (int k = 0; k < 4; k++) store_grad(&a.gquat[k * n + i], gq[k], a.accumulate);
-            store_grad(&a.gop[i], gop, a.accumulate);
-            for (int k = 0; k < 48; k++) store_grad(&a.gsh[(long long)k * n + i], gsh[k], a.accumulate);
+            for (int k = 0; k < 4; k++) a.gquat[4 * i + k] += gq[k];
+            a.gop[i] += gop;
+            for (int k = 0; k < 48; k++) a.gsh[48 * i + k] += gsh[k];
         }
     }
     if (a.red_partial) {
@@ -577,22 +726,32 @@ __global__ void scale_reg_finalize_kernel(const float *partial, int nblocks, flo
 
 cudaError_t launch_preprocess_bwd(gs_workspace *ws, cudaStream_t st, const gs_gaussians &g,
                                   const gs_gaussian_grads &gr, int accumulate, float *absgrad, float beta,
-                                  float *scale_reg_value)
+                                  float *scale_reg_value, float *cgrad)
 {
     const long long n = g.n;
     if (n == 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)((n + 127) / 128);
+    cudaError_t e;
+    if (!accumulate && !cgrad) {
+        // overwrite mode: Gaussians without a record get zero gradients
+        float *arr[5] = {gr.mean, gr.log_scale, gr.quat, gr.opacity_logit, gr.sh};
+        const int rows[5] = {3, 3, 4, 1, 48};
+        for (int k = 0; k < 5; k++)
+            if ((e = cudaMemsetAsync(arr[k], 0, (size_t)rows[k] * n * sizeof(float), st)) != cudaSuccess) return e;
+    }
+    const unsigned blocks = (unsigned)((ws->cap.max_records + 127) / 128);
     BwdArgs a;
     a.g = GaussPtrs{g.mean, g.log_scale, g.quat, g.opacity_logit, g.sh, g.lod, n};
     a.gmean = gr.mean; a.gls = gr.log_scale; a.gquat = gr.quat; a.gop = gr.opacity_logit; a.gsh = gr.sh;
-    a.rec_off = ws->rec_off; a.rec_cam = ws->rec_cam; a.clampm = ws->clampm; a.rgrad = ws->rgrad;
+    a.rec_g = ws->rec_g; a.rec_cam = ws->rec_cam; a.clampm = ws->clampm;
+    a.rgrad = ws->rgrad;
+    a.cgrad = cgrad;
     a.absgrad = absgrad; a.accumulate = accumulate; a.beta = beta;
     const bool reduce = beta > 0.f && scale_reg_value && blocks <= ws->red_words;
     a.red_partial = reduce ? ws->red_partial : nullptr;
     a.ctr = ws->ctr;
     preprocess_bwd_kernel<<<blocks, 128, 0, st>>>(a, ws->cams, ws->rc);
     note_launch();
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (reduce) {
         scale_reg_finalize_kernel<<<1, 256, 0, st>>>(ws->red_partial, (int)blocks, beta, ws->ctr, scale_reg_value);

@@ -2,10 +2,11 @@
 // adjoint, and the instrumented colourless sweep of the importance pass
 // (Sec. 3.2, Fig. 2).
 //
-// One 256-thread block per 16x16 tile; each thread owns one pixel.  The tile's
-// depth-ordered list is staged through shared memory in batches; every
+// One 64-thread block per 16x16 tile; each thread owns a 2x2 pixel quad.  The
+// tile's depth-ordered list is staged through shared memory in batches; every
 // pixel walks the same entry at the same time, so per-Gaussian quantities are
-// block reductions rather than per-pixel global atomics.  The backward and
+// block reductions (thread over its quad, warp shuffles, then two warp
+// partials) rather than per-pixel global atomics.  The backward and
 // the importance sweep write one gradient/score slot per (record, tile) --
 // slot index = the record's first instance + the tile's position inside the
 // record's rectangle -- and a later per-record pass sums a record's slots in
@@ -14,114 +15,79 @@
 
 namespace gs {
 
-// Pixel-to-thread map: warp w covers an 8x4 pixel block of the tile.
-__device__ __forceinline__ void pixel_of_thread(int tid, int &lx, int &ly)
+constexpr int kRT = 64;            // threads per 16x16 tile: 2 warps, one 2x2 pixel quad each
+constexpr int kQ = 4;              // pixels per thread
+
+// Thread t owns the quad (qx, qy) = (t % 8, t / 8): warp 0 covers pixel rows
+// 0-7 and warp 1 rows 8-15.  Pixel k of the quad is (2 qx + k % 2, 2 qy + k / 2).
+struct TileGeom {
+    int cam, tx, ty;
+    int px0, py0;              // pixel of quad element 0
+    const CamInfo *ci;
+};
+
+__device__ __forceinline__ TileGeom tile_geom(const CamTable &ct, int tile)
 {
-    const int w = tid >> 5, l = tid & 31;
-    lx = (w & 1) * 8 + (l & 7);
-    ly = (w >> 1) * 4 + (l >> 3);
+    TileGeom t;
+    t.cam = camera_of_tile(ct, tile);
+    t.ci = &ct.c[t.cam];
+    const int lt = tile - t.ci->tile_base;
+    t.tx = lt % t.ci->tiles_x;
+    t.ty = lt / t.ci->tiles_x;
+    t.px0 = t.tx * kTile + 2 * (threadIdx.x & 7);
+    t.py0 = t.ty * kTile + 2 * (threadIdx.x >> 3);
+    return t;
 }
 
-// Gaussian exponent at pixel offset (dx, dy) with explicitly rounded
-// operations, so the forward, backward and importance kernels take the same
-// skip decisions bit for bit.
-__device__ __forceinline__ float gs_power(float A, float B, float C, float dx, float dy)
+// ---- packed quad arithmetic (Blackwell FP32x2) ----------------------------------
+// A thread's quad is two rows of two pixels; each row pair is one float2, so
+// the exponent, alpha, transmittance and colour updates are packed FP32x2
+// operations.  The conic is pre-scaled so the exponent is in base 2:
+// G = exp(power) = 2^(log2(e) power).  Every kernel that takes skip decisions
+// (forward, backward, importance) evaluates these same functions.
+constexpr float kLog2e = 1.4426950408889634f;
+
+__device__ __forceinline__ float ex2_approx(float x)
 {
-    const float q = __fmaf_rn(__fmul_rn(C, dy), dy, __fmul_rn(__fmul_rn(A, dx), dx));
-    return __fmaf_rn(-0.5f, q, -__fmul_rn(__fmul_rn(B, dx), dy));
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
-__device__ __forceinline__ float gs_alpha(float o, float power, float alpha_max)
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+struct QuadPow {
+    float2 r0, r1; // base-2 exponents of the two row pairs
+};
+
+// e0 = (u, v, A, B), C: conic of the entry; px2 = pixel-centre x of the pair,
+// pya, pyb = the two rows' centre y.
+__device__ __forceinline__ QuadPow quad_power(float4 e0, float C, float2 px2, float pya, float pyb)
 {
-    return fminf(alpha_max, __fmul_rn(o, __expf(power)));
-}
-
-// ---- forward --------------------------------------------------------------
-
-__global__ void __launch_bounds__(256) render_fwd_kernel(const uint2 *__restrict__ ranges,
-                                                         const uint32_t *__restrict__ vals,
-                                                         const float4 *__restrict__ rd0,
-                                                         const float4 *__restrict__ rd1,
-                                                         const float *__restrict__ rd2, CamTable ct, RenderConsts rc,
-                                                         float *__restrict__ rgb_out, float *__restrict__ T_out,
-                                                         float *__restrict__ T_ws, uint32_t *__restrict__ n_contrib)
-{
-    __shared__ float4 s0[256];
-    __shared__ float4 s1[256];
-    __shared__ float s2[256];
-    const int tile = blockIdx.x;
-    const int c = camera_of_tile(ct, tile);
-    const CamInfo &cam = ct.c[c];
-    const int lt = tile - cam.tile_base;
-    const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-    int lx, ly;
-    pixel_of_thread(threadIdx.x, lx, ly);
-    const int px = tx * kTile + lx, py = ty * kTile + ly;
-    const bool inside = px < cam.width && py < cam.height;
-    const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
-    const uint2 rg = ranges[tile];
-    const int start = (int)rg.x, end = (int)rg.y;
-
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    uint32_t contrib = 0, last = 0;
-    bool done = !inside;
-    for (int b = start; b < end; b += 256) {
-        if (__syncthreads_count(done) == 256) break;
-        const int s = b + threadIdx.x;
-        if (s < end) {
-            const uint32_t r = vals[s];
-            s0[threadIdx.x] = rd0[r];
-            s1[threadIdx.x] = rd1[r];
-            s2[threadIdx.x] = rd2[r];
-        }
-        __syncthreads();
-        const int cnt = min(256, end - b);
-        for (int j = 0; j < cnt && !done; j++) {
-            contrib++;
-            const float4 p0 = s0[j];
-            const float dx = __fsub_rn(pxf, p0.x), dy = __fsub_rn(pyf, p0.y);
-            const float power = gs_power(p0.z, p0.w, s1[j].x, dx, dy);
-            if (power > 0.f) continue;
-            const float4 p1 = s1[j];
-            const float alpha = gs_alpha(p1.y, power, rc.alpha_max);
-            if (alpha < rc.alpha_min) continue;
-            const float test_T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-            if (test_T < rc.T_min) { done = true; continue; }
-            const float wgt = alpha * T;
-            C0 = fmaf(wgt, p1.z, C0);
-            C1 = fmaf(wgt, p1.w, C1);
-            C2 = fmaf(wgt, s2[j], C2);
-            T = test_T;
-            last = contrib;
-        }
+    const float As = __fmul_rn(e0.z, -0.5f * kLog2e), Bs = __fmul_rn(e0.w, -kLog2e), Cs = __fmul_rn(C, -0.5f * kLog2e);
+    const float2 dx = __fadd2_rn(px2, f2(-e0.x));
+    const float2 A2 = f2(As);
+    QuadPow q;
+    {
+        const float dy = __fsub_rn(pya, e0.y);
+        const float bd = __fmul_rn(Bs, dy), cd = __fmul_rn(__fmul_rn(Cs, dy), dy);
+        q.r0 = __ffma2_rn(__ffma2_rn(A2, dx, f2(bd)), dx, f2(cd));
     }
-    if (inside) {
-        const long long pix = (long long)py * cam.width + px;
-        const long long np = (long long)cam.width * cam.height;
-        float *img = rgb_out + 3 * cam.pix_base;
-        img[pix] = C0 + T * rc.bg[0];
-        img[np + pix] = C1 + T * rc.bg[1];
-        img[2 * np + pix] = C2 + T * rc.bg[2];
-        const long long gp = cam.pix_base + pix;
-        if (T_out) T_out[gp] = T;
-        T_ws[gp] = T;
-        n_contrib[gp] = last;
+    {
+        const float dy = __fsub_rn(pyb, e0.y);
+        const float bd = __fmul_rn(Bs, dy), cd = __fmul_rn(__fmul_rn(Cs, dy), dy);
+        q.r1 = __ffma2_rn(__ffma2_rn(A2, dx, f2(bd)), dx, f2(cd));
     }
+    return q;
 }
 
-cudaError_t launch_render_fwd(gs_workspace *ws, cudaStream_t st, float *rgb, float *T_out)
+// alpha = min(alpha_max, o 2^p) of a pixel pair
+__device__ __forceinline__ float2 pair_alpha(float2 p, float o, float amax, float2 &G)
 {
-    if (ws->cams.total_tiles == 0) return cudaSuccess;
-    render_fwd_kernel<<<ws->cams.total_tiles, 256, 0, st>>>(ws->ranges, ws->tval[ws->tile_buf], ws->rd0, ws->rd1,
-                                                            ws->rd2, ws->cams, ws->rc, rgb, T_out, ws->T_final,
-                                                            ws->n_contrib);
-    note_launch();
-    return cudaGetLastError();
+    G = make_float2(ex2_approx(p.x), ex2_approx(p.y));
+    const float2 og = __fmul2_rn(f2(o), G);
+    return make_float2(fminf(amax, og.x), fminf(amax, og.y));
 }
-
-// ---- backward ---------------------------------------------------------------
-
-constexpr int kBwdBatch = 32;
 
 __device__ __forceinline__ float warp_sum_f(float v)
 {
@@ -140,6 +106,108 @@ __device__ __forceinline__ unsigned long long slot_of(const uint32_t *inst_off, 
     return (unsigned long long)inst_off[r] + (unsigned long long)((ty - y0) * (x1 - x0) + (tx - x0));
 }
 
+// ---- forward --------------------------------------------------------------
+
+__global__ void __launch_bounds__(kRT) render_fwd_kernel(const uint2 *__restrict__ ranges,
+                                                         const uint32_t *__restrict__ vals,
+                                                         const float4 *__restrict__ rd0,
+                                                         const float4 *__restrict__ rd1,
+                                                         const float *__restrict__ rd2, CamTable ct, RenderConsts rc,
+                                                         float *__restrict__ rgb_out, float *__restrict__ T_out,
+                                                         float *__restrict__ T_ws, uint32_t *__restrict__ n_contrib)
+{
+    __shared__ float4 s0[kRT];
+    __shared__ float4 s1[kRT];
+    __shared__ float s2[kRT];
+    const TileGeom tg = tile_geom(ct, blockIdx.x);
+    const CamInfo &cam = *tg.ci;
+    const uint2 rg = ranges[blockIdx.x];
+    const int start = (int)rg.x, end = (int)rg.y;
+
+    // pixel pair of row 0 (quad elements 0, 1) and row 1 (2, 3)
+    const float2 px2 = make_float2((float)tg.px0 + 0.5f, (float)tg.px0 + 1.5f);
+    const float pya = (float)tg.py0 + 0.5f, pyb = (float)tg.py0 + 1.5f;
+    float2 T[2] = {f2(1.f), f2(1.f)}, Cr[2] = {f2(0.f), f2(0.f)}, Cg[2] = {f2(0.f), f2(0.f)},
+           Cb[2] = {f2(0.f), f2(0.f)};
+    uint32_t last[kQ] = {0, 0, 0, 0};
+    bool dn[kQ];
+#pragma unroll
+    for (int k = 0; k < kQ; k++)
+        dn[k] = tg.px0 + (k & 1) >= cam.width || tg.py0 + (k >> 1) >= cam.height;
+    for (int b = start; b < end; b += kRT) {
+        if (__syncthreads_count(dn[0] && dn[1] && dn[2] && dn[3]) == kRT) break;
+        const int s = b + threadIdx.x;
+        if (s < end) {
+            const uint32_t r = vals[s];
+            s0[threadIdx.x] = rd0[r];
+            s1[threadIdx.x] = rd1[r];
+            s2[threadIdx.x] = rd2[r];
+        }
+        __syncthreads();
+        const int cnt = min(kRT, end - b);
+        for (int j = 0; j < cnt && !(dn[0] && dn[1] && dn[2] && dn[3]); j++) {
+            const float4 p0 = s0[j], p1 = s1[j];
+            const float cb = s2[j];
+            const uint32_t pos = (uint32_t)(b - start + j + 1);
+            const QuadPow q = quad_power(p0, p1.x, px2, pya, pyb);
+#pragma unroll
+            for (int row = 0; row < 2; row++) {
+                float2 G;
+                const float2 al = pair_alpha(row ? q.r1 : q.r0, p1.y, rc.alpha_max, G);
+                const float2 tT = __ffma2_rn(make_float2(-T[row].x, -T[row].y), al, T[row]); // T (1 - alpha)
+                const int k0 = 2 * row, k1 = 2 * row + 1;
+                const bool ok0 = !dn[k0] && al.x >= rc.alpha_min, ok1 = !dn[k1] && al.y >= rc.alpha_min;
+                const bool st0 = ok0 && tT.x < rc.T_min, st1 = ok1 && tT.y < rc.T_min;
+                const bool c0 = ok0 && !st0, c1 = ok1 && !st1;
+                dn[k0] = dn[k0] || st0;
+                dn[k1] = dn[k1] || st1;
+                const float2 ae = make_float2(c0 ? al.x : 0.f, c1 ? al.y : 0.f); // skipped fragments add nothing
+                const float2 w = __fmul2_rn(ae, T[row]);
+                Cr[row] = __ffma2_rn(w, f2(p1.z), Cr[row]);
+                Cg[row] = __ffma2_rn(w, f2(p1.w), Cg[row]);
+                Cb[row] = __ffma2_rn(w, f2(cb), Cb[row]);
+                T[row] = __ffma2_rn(make_float2(-T[row].x, -T[row].y), ae, T[row]);
+                last[k0] = c0 ? pos : last[k0];
+                last[k1] = c1 ? pos : last[k1];
+            }
+        }
+    }
+    const long long np = (long long)cam.width * cam.height;
+    float *img = rgb_out + 3 * cam.pix_base;
+#pragma unroll
+    for (int k = 0; k < kQ; k++) {
+        const int px = tg.px0 + (k & 1), py = tg.py0 + (k >> 1);
+        if (px >= cam.width || py >= cam.height) continue;
+        const int row = k >> 1;
+        const float Tk = (k & 1) ? T[row].y : T[row].x;
+        const float cr = (k & 1) ? Cr[row].y : Cr[row].x;
+        const float cg = (k & 1) ? Cg[row].y : Cg[row].x;
+        const float cbk = (k & 1) ? Cb[row].y : Cb[row].x;
+        const long long pix = (long long)py * cam.width + px;
+        img[pix] = cr + Tk * rc.bg[0];
+        img[np + pix] = cg + Tk * rc.bg[1];
+        img[2 * np + pix] = cbk + Tk * rc.bg[2];
+        const long long gp = cam.pix_base + pix;
+        if (T_out) T_out[gp] = Tk;
+        T_ws[gp] = Tk;
+        n_contrib[gp] = last[k];
+    }
+}
+
+cudaError_t launch_render_fwd(gs_workspace *ws, cudaStream_t st, float *rgb, float *T_out)
+{
+    if (ws->cams.total_tiles == 0) return cudaSuccess;
+    render_fwd_kernel<<<ws->cams.total_tiles, kRT, 0, st>>>(ws->ranges, ws->tval[ws->tile_buf], ws->rd0, ws->rd1,
+                                                            ws->rd2, ws->cams, ws->rc, rgb, T_out, ws->T_final,
+                                                            ws->n_contrib);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// ---- backward ---------------------------------------------------------------
+
+constexpr int kBwdBatch = 32;
+
 struct BwdRenderArgs {
     const uint2 *ranges;
     const uint32_t *vals;
@@ -153,51 +221,55 @@ struct BwdRenderArgs {
     float *slots;
 };
 
-__global__ void __launch_bounds__(256) render_bwd_kernel(BwdRenderArgs a, CamTable ct, RenderConsts rc)
+// Reverse traversal from each pixel's last composited entry, recovering T by
+// T / (1 - alpha) from the final transmittance.  Per entry, each thread sums
+// the gradient over its 4 pixels, each warp reduces over its 32 threads, and
+// the two warp partials are added once per batch into the entry's slot.
+__global__ void __launch_bounds__(kRT) render_bwd_kernel(BwdRenderArgs a, CamTable ct, RenderConsts rc)
 {
     __shared__ float4 s0[kBwdBatch];
     __shared__ float4 s1[kBwdBatch];
     __shared__ float s2[kBwdBatch];
     __shared__ unsigned long long s_slot[kBwdBatch];
-    __shared__ float s_red[8][kBwdBatch][kSlotFloats];
+    __shared__ float s_red[2][kBwdBatch][kSlotFloats];
     __shared__ int s_max;
-    const int tile = blockIdx.x;
-    const int c = camera_of_tile(ct, tile);
-    const CamInfo &cam = ct.c[c];
-    const int lt = tile - cam.tile_base;
-    const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-    int lx, ly;
-    pixel_of_thread(threadIdx.x, lx, ly);
-    const int px = tx * kTile + lx, py = ty * kTile + ly;
-    const bool inside = px < cam.width && py < cam.height;
-    const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
-    const uint2 rg = a.ranges[tile];
+    const TileGeom tg = tile_geom(ct, blockIdx.x);
+    const CamInfo &cam = *tg.ci;
+    const uint2 rg = a.ranges[blockIdx.x];
     const int start = (int)rg.x, end = (int)rg.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    int nc = 0;
-    if (inside) {
-        const long long pix = (long long)py * cam.width + px;
-        const long long np = (long long)cam.width * cam.height;
-        const float *gimg = a.dL_drgb + 3 * cam.pix_base;
-        g0 = gimg[pix]; g1 = gimg[np + pix]; g2 = gimg[2 * np + pix];
-        T = a.T_final[cam.pix_base + pix];
-        nc = (int)a.n_contrib[cam.pix_base + pix];
+    float T[kQ], g0[kQ], g1[kQ], g2[kQ], tgb[kQ], S0[kQ], S1[kQ], S2[kQ], pxf[kQ], pyf[kQ];
+    int nc[kQ];
+    const float2 px2 = make_float2((float)tg.px0 + 0.5f, (float)tg.px0 + 1.5f);
+    const float pya = (float)tg.py0 + 0.5f, pyb = (float)tg.py0 + 1.5f;
+    int mymax = 0;
+    const long long np = (long long)cam.width * cam.height;
+    const float *gimg = a.dL_drgb + 3 * cam.pix_base;
+#pragma unroll
+    for (int k = 0; k < kQ; k++) {
+        const int px = tg.px0 + (k & 1), py = tg.py0 + (k >> 1);
+        pxf[k] = (float)px + 0.5f; pyf[k] = (float)py + 0.5f;
+        T[k] = 1.f; g0[k] = g1[k] = g2[k] = 0.f; nc[k] = 0;
+        S0[k] = S1[k] = S2[k] = 0.f;
+        if (px < cam.width && py < cam.height) {
+            const long long pix = (long long)py * cam.width + px;
+            g0[k] = gimg[pix]; g1[k] = gimg[np + pix]; g2[k] = gimg[2 * np + pix];
+            T[k] = a.T_final[cam.pix_base + pix];
+            nc[k] = (int)a.n_contrib[cam.pix_base + pix];
+        }
+        // d/dalpha of the background term: -T_final (g . bg) / (1 - alpha)
+        tgb[k] = T[k] * (g0[k] * rc.bg[0] + g1[k] * rc.bg[1] + g2[k] * rc.bg[2]);
+        mymax = max(mymax, nc[k]);
     }
-    const float Tfin = T;
-    const float gbg = g0 * rc.bg[0] + g1 * rc.bg[1] + g2 * rc.bg[2];
-    float S0 = 0.f, S1 = 0.f, S2 = 0.f; // sum over later fragments of alpha T c
-
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
-    atomicMax(&s_max, nc);
+    atomicMax(&s_max, mymax);
     __syncthreads();
     const int last = start + s_max;
     // entries after the last contribution of every pixel carry zero gradient
-    for (int s = last + threadIdx.x; s < end; s += 256) {
-        const unsigned long long slot = slot_of(a.inst_off, a.rect, a.vals[s], tx, ty);
-        float *dst = a.slots + slot * kSlotFloats;
+    for (int s = last + threadIdx.x; s < end; s += kRT) {
+        float *dst = a.slots + slot_of(a.inst_off, a.rect, a.vals[s], tg.tx, tg.ty) * kSlotFloats;
 #pragma unroll
         for (int k = 0; k < kSlotFloats; k++) dst[k] = 0.f;
     }
@@ -209,65 +281,65 @@ __global__ void __launch_bounds__(256) render_bwd_kernel(BwdRenderArgs a, CamTab
             s0[threadIdx.x] = a.rd0[r];
             s1[threadIdx.x] = a.rd1[r];
             s2[threadIdx.x] = a.rd2[r];
-            s_slot[threadIdx.x] = slot_of(a.inst_off, a.rect, r, tx, ty);
+            s_slot[threadIdx.x] = slot_of(a.inst_off, a.rect, r, tg.tx, tg.ty);
         }
         __syncthreads();
         for (int jj = cnt - 1; jj >= 0; jj--) {
             const int j = lo + jj - start; // position in the tile list
+            const float4 p0 = s0[jj], p1 = s1[jj];
+            const float cb = s2[jj];
+            // the forward's own exponent and alpha (same functions, same bits)
+            const QuadPow qp = quad_power(p0, p1.x, px2, pya, pyb);
+            float2 Gr[2], alr[2];
+            alr[0] = pair_alpha(qp.r0, p1.y, rc.alpha_max, Gr[0]);
+            alr[1] = pair_alpha(qp.r1, p1.y, rc.alpha_max, Gr[1]);
             float v[kSlotFloats];
 #pragma unroll
-            for (int k = 0; k < kSlotFloats; k++) v[k] = 0.f;
+            for (int q = 0; q < kSlotFloats; q++) v[q] = 0.f;
             bool act = false;
-            if (j < nc) {
-                const float4 p0 = s0[jj], p1 = s1[jj];
-                const float dx = __fsub_rn(pxf, p0.x), dy = __fsub_rn(pyf, p0.y);
-                const float power = gs_power(p0.z, p0.w, p1.x, dx, dy);
-                if (power <= 0.f) {
-                    const float G = __expf(power);
-                    const float og = __fmul_rn(p1.y, G);
-                    const float alpha = fminf(rc.alpha_max, og);
-                    if (alpha >= rc.alpha_min) {
-                        act = true;
-                        const float cb = s2[jj];
-                        const float oma = 1.f - alpha;
-                        const float inv = 1.f / oma;
-                        const float Tj = T * inv; // transmittance in front of this fragment
-                        const float aT = alpha * Tj;
-                        v[6] = aT * g0; v[7] = aT * g1; v[8] = aT * g2;
-                        float dalpha = g0 * (Tj * p1.z - S0 * inv) + g1 * (Tj * p1.w - S1 * inv) +
-                                       g2 * (Tj * cb - S2 * inv) - Tfin * gbg * inv;
-                        S0 = fmaf(aT, p1.z, S0);
-                        S1 = fmaf(aT, p1.w, S1);
-                        S2 = fmaf(aT, cb, S2);
-                        T = Tj;
-                        if (og < rc.alpha_max) {
-                            v[5] = G * dalpha;
-                            const float dpow = G * p1.y * dalpha;
-                            v[0] = dpow * (p0.z * dx + p0.w * dy);
-                            v[1] = dpow * (p1.x * dy + p0.w * dx);
-                            v[2] = -0.5f * dpow * dx * dx;
-                            v[3] = -dpow * dx * dy;
-                            v[4] = -0.5f * dpow * dy * dy;
-                        }
-                    }
+#pragma unroll
+            for (int k = 0; k < kQ; k++) {
+                const float alpha = (k & 1) ? alr[k >> 1].y : alr[k >> 1].x;
+                if (j >= nc[k] || alpha < rc.alpha_min) continue;
+                const float G = (k & 1) ? Gr[k >> 1].y : Gr[k >> 1].x;
+                const float og = p1.y * G;
+                const float dx = pxf[k] - p0.x, dy = pyf[k] - p0.y;
+                act = true;
+                const float inv = 1.f / (1.f - alpha);
+                const float Tj = T[k] * inv; // transmittance in front of this fragment
+                const float aT = alpha * Tj;
+                v[6] = fmaf(aT, g0[k], v[6]);
+                v[7] = fmaf(aT, g1[k], v[7]);
+                v[8] = fmaf(aT, g2[k], v[8]);
+                const float dalpha = g0[k] * (Tj * p1.z - S0[k] * inv) + g1[k] * (Tj * p1.w - S1[k] * inv) +
+                                     g2[k] * (Tj * cb - S2[k] * inv) - tgb[k] * inv;
+                S0[k] = fmaf(aT, p1.z, S0[k]);
+                S1[k] = fmaf(aT, p1.w, S1[k]);
+                S2[k] = fmaf(aT, cb, S2[k]);
+                T[k] = Tj;
+                if (og < rc.alpha_max) {
+                    v[5] = fmaf(G, dalpha, v[5]);
+                    const float dpow = G * p1.y * dalpha;
+                    v[0] = fmaf(dpow, p0.z * dx + p0.w * dy, v[0]);
+                    v[1] = fmaf(dpow, p1.x * dy + p0.w * dx, v[1]);
+                    v[2] = fmaf(-0.5f * dpow, dx * dx, v[2]);
+                    v[3] = fmaf(-dpow, dx * dy, v[3]);
+                    v[4] = fmaf(-0.5f * dpow, dy * dy, v[4]);
                 }
             }
             if (__any_sync(0xffffffffu, act)) {
 #pragma unroll
-                for (int k = 0; k < kSlotFloats; k++) v[k] = warp_sum_f(v[k]);
+                for (int q = 0; q < kSlotFloats; q++) v[q] = warp_sum_f(v[q]);
             }
             if (lane == 0) {
 #pragma unroll
-                for (int k = 0; k < kSlotFloats; k++) s_red[warp][jj][k] = v[k];
+                for (int q = 0; q < kSlotFloats; q++) s_red[warp][jj][q] = v[q];
             }
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < cnt * kSlotFloats; idx += 256) {
-            const int jj = idx / kSlotFloats, k = idx - jj * kSlotFloats;
-            float sum = 0.f;
-#pragma unroll
-            for (int w = 0; w < 8; w++) sum += s_red[w][jj][k];
-            a.slots[s_slot[jj] * kSlotFloats + k] = sum;
+        for (int idx = threadIdx.x; idx < cnt * kSlotFloats; idx += kRT) {
+            const int jj = idx / kSlotFloats, q = idx - jj * kSlotFloats;
+            a.slots[s_slot[jj] * kSlotFloats + q] = s_red[0][jj][q] + s_red[1][jj][q];
         }
         __syncthreads();
     }
@@ -280,14 +352,12 @@ cudaError_t launch_render_bwd(gs_workspace *ws, cudaStream_t st, const float *dL
     a.ranges = ws->ranges; a.vals = ws->tval[ws->tile_buf]; a.rd0 = ws->rd0; a.rd1 = ws->rd1; a.rd2 = ws->rd2;
     a.inst_off = ws->inst_off; a.rect = ws->rect; a.T_final = ws->T_final; a.n_contrib = ws->n_contrib;
     a.dL_drgb = dL_drgb; a.slots = ws->slots;
-    render_bwd_kernel<<<ws->cams.total_tiles, 256, 0, st>>>(a, ws->cams, ws->rc);
+    render_bwd_kernel<<<ws->cams.total_tiles, kRT, 0, st>>>(a, ws->cams, ws->rc);
     note_launch();
     return cudaGetLastError();
 }
 
 // ---- importance sweep (colourless forward) -------------------------------------
-
-constexpr int kImpBatch = 64;
 
 struct ImpArgs {
     const uint2 *ranges;
@@ -298,79 +368,76 @@ struct ImpArgs {
     float *slots; // [I][2]: alpha-weight (float), composited pixels (uint32 bits)
 };
 
-__global__ void __launch_bounds__(256) importance_raster_kernel(ImpArgs a, CamTable ct, RenderConsts rc)
+__global__ void __launch_bounds__(kRT) importance_raster_kernel(ImpArgs a, CamTable ct, RenderConsts rc)
 {
-    __shared__ float4 s0[kImpBatch];
-    __shared__ float2 s1[kImpBatch];
-    __shared__ unsigned long long s_slot[kImpBatch];
-    __shared__ float s_w[8][kImpBatch];
-    __shared__ uint32_t s_a[8][kImpBatch];
-    const int tile = blockIdx.x;
-    const int c = camera_of_tile(ct, tile);
-    const CamInfo &cam = ct.c[c];
-    const int lt = tile - cam.tile_base;
-    const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-    int lx, ly;
-    pixel_of_thread(threadIdx.x, lx, ly);
-    const int px = tx * kTile + lx, py = ty * kTile + ly;
-    const bool inside = px < cam.width && py < cam.height;
-    const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
-    const uint2 rg = a.ranges[tile];
+    __shared__ float4 s0[kRT];
+    __shared__ float2 s1[kRT];
+    __shared__ unsigned long long s_slot[kRT];
+    __shared__ float s_w[2][kRT];
+    __shared__ uint32_t s_a[2][kRT];
+    const TileGeom tg = tile_geom(ct, blockIdx.x);
+    const CamInfo &cam = *tg.ci;
+    const uint2 rg = a.ranges[blockIdx.x];
     const int start = (int)rg.x, end = (int)rg.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float T = 1.f;
-    bool done = !inside;
+    const float2 px2 = make_float2((float)tg.px0 + 0.5f, (float)tg.px0 + 1.5f);
+    const float pya = (float)tg.py0 + 0.5f, pyb = (float)tg.py0 + 1.5f;
+    float2 T[2] = {f2(1.f), f2(1.f)};
+    bool dn[kQ];
+#pragma unroll
+    for (int k = 0; k < kQ; k++)
+        dn[k] = tg.px0 + (k & 1) >= cam.width || tg.py0 + (k >> 1) >= cam.height;
     int b = start;
-    for (; b < end; b += kImpBatch) {
-        if (__syncthreads_count(done) == 256) break;
-        const int cnt = min(kImpBatch, end - b);
+    for (; b < end; b += kRT) {
+        if (__syncthreads_count(dn[0] && dn[1] && dn[2] && dn[3]) == kRT) break;
+        const int cnt = min(kRT, end - b);
         if (threadIdx.x < cnt) {
             const uint32_t r = a.vals[b + threadIdx.x];
             s0[threadIdx.x] = a.rd0[r];
             const float4 p1 = a.rd1[r];
             s1[threadIdx.x] = make_float2(p1.x, p1.y);
-            s_slot[threadIdx.x] = slot_of(a.inst_off, a.rect, r, tx, ty);
+            s_slot[threadIdx.x] = slot_of(a.inst_off, a.rect, r, tg.tx, tg.ty);
         }
         __syncthreads();
         for (int j = 0; j < cnt; j++) {
+            const float4 p0 = s0[j];
+            const float2 p1 = s1[j];
+            const QuadPow q = quad_power(p0, p1.x, px2, pya, pyb);
             float wv = 0.f;
             uint32_t av = 0;
-            if (!done) {
-                const float4 p0 = s0[j];
-                const float2 p1 = s1[j];
-                const float dx = __fsub_rn(pxf, p0.x), dy = __fsub_rn(pyf, p0.y);
-                const float power = gs_power(p0.z, p0.w, p1.x, dx, dy);
-                if (power <= 0.f) {
-                    const float alpha = gs_alpha(p1.y, power, rc.alpha_max);
-                    if (alpha >= rc.alpha_min) {
-                        const float test_T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-                        if (test_T < rc.T_min) {
-                            done = true;
-                        } else {
-                            wv = alpha * T;
-                            av = 1;
-                            T = test_T;
-                        }
-                    }
-                }
+#pragma unroll
+            for (int row = 0; row < 2; row++) {
+                float2 G;
+                const float2 al = pair_alpha(row ? q.r1 : q.r0, p1.y, rc.alpha_max, G);
+                const float2 tT = __ffma2_rn(make_float2(-T[row].x, -T[row].y), al, T[row]);
+                const int k0 = 2 * row, k1 = 2 * row + 1;
+                const bool ok0 = !dn[k0] && al.x >= rc.alpha_min, ok1 = !dn[k1] && al.y >= rc.alpha_min;
+                const bool st0 = ok0 && tT.x < rc.T_min, st1 = ok1 && tT.y < rc.T_min;
+                const bool c0 = ok0 && !st0, c1 = ok1 && !st1;
+                dn[k0] = dn[k0] || st0;
+                dn[k1] = dn[k1] || st1;
+                const float2 ae = make_float2(c0 ? al.x : 0.f, c1 ? al.y : 0.f);
+                const float2 w = __fmul2_rn(ae, T[row]);
+                wv += w.x + w.y;
+                av += (uint32_t)c0 + (uint32_t)c1;
+                T[row] = __ffma2_rn(make_float2(-T[row].x, -T[row].y), ae, T[row]);
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, av);
-            if (bal) wv = warp_sum_f(wv);
-            if (lane == 0) { s_w[warp][j] = wv; s_a[warp][j] = __popc(bal); }
+            if (__any_sync(0xffffffffu, av != 0)) {
+                wv = warp_sum_f(wv);
+                av = __reduce_add_sync(0xffffffffu, av);
+            }
+            if (lane == 0) { s_w[warp][j] = wv; s_a[warp][j] = av; }
         }
         __syncthreads();
         if (threadIdx.x < cnt) {
-            float ws = 0.f;
-            uint32_t as = 0;
-#pragma unroll
-            for (int w = 0; w < 8; w++) { ws += s_w[w][threadIdx.x]; as += s_a[w][threadIdx.x]; }
-            float2 out = make_float2(ws, __uint_as_float(as));
+            const float2 out = make_float2(s_w[0][threadIdx.x] + s_w[1][threadIdx.x],
+                                           __uint_as_float(s_a[0][threadIdx.x] + s_a[1][threadIdx.x]));
             reinterpret_cast<float2 *>(a.slots)[s_slot[threadIdx.x]] = out;
         }
     }
     // entries never reached (every pixel of the tile had stopped)
-    for (int s = b + threadIdx.x; s < end; s += 256) {
-        const unsigned long long slot = slot_of(a.inst_off, a.rect, a.vals[s], tx, ty);
+    for (int s = b + threadIdx.x; s < end; s += kRT) {
+        const unsigned long long slot = slot_of(a.inst_off, a.rect, a.vals[s], tg.tx, tg.ty);
         reinterpret_cast<float2 *>(a.slots)[slot] = make_float2(0.f, 0.f);
     }
 }
@@ -381,7 +448,7 @@ cudaError_t launch_importance_raster(gs_workspace *ws, cudaStream_t st)
     ImpArgs a;
     a.ranges = ws->ranges; a.vals = ws->tval[ws->tile_buf]; a.rd0 = ws->rd0; a.rd1 = ws->rd1;
     a.inst_off = ws->inst_off; a.rect = ws->rect; a.slots = ws->slots;
-    importance_raster_kernel<<<ws->cams.total_tiles, 256, 0, st>>>(a, ws->cams, ws->rc);
+    importance_raster_kernel<<<ws->cams.total_tiles, kRT, 0, st>>>(a, ws->cams, ws->rc);
     note_launch();
     return cudaGetLastError();
 }

@@ -8,35 +8,46 @@
 // The selection sorts each view's records by w (descending, stable), takes an
 // FP64 inclusive scan in a fixed (reduce-then-scan) association, and marks
 // every entry whose exclusive prefix is still below vis_mass * total.
+#include <algorithm>
+
 #include "gs_internal.cuh"
 
 namespace gs {
 
 cudaError_t launch_importance_raster(gs_workspace *ws, cudaStream_t st);
 
+// w and a of each record: one warp per record, lanes strided over its slots
+// (contiguous in depth order), fixed shuffle tree.
 __global__ void __launch_bounds__(256) imp_reduce_kernel(const uint32_t *drec, const uint32_t *inst_off,
                                                          const uint32_t *tt, const float2 *slots, float *imp_w,
                                                          uint32_t *imp_a, const DevCounters *ctr)
 {
-    const unsigned long long k = (unsigned long long)blockIdx.x * 256 + threadIdx.x;
-    if (k >= ctr->n_records) return;
-    const uint32_t r = drec[k];
-    const unsigned long long off = inst_off[r], cnt = tt[r];
-    float w = 0.f;
-    uint32_t a = 0;
-    if (off + cnt <= ctr->n_instances) {
-        for (unsigned long long t = 0; t < cnt; t++) {
-            const float2 s = slots[off + t];
-            w += s.x;
-            a += __float_as_uint(s.y);
+    const unsigned long long nrec = ctr->n_records, ninst = ctr->n_instances;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nwarps = (unsigned long long)gridDim.x * 8;
+    for (unsigned long long k = (unsigned long long)blockIdx.x * 8 + (threadIdx.x >> 5); k < nrec; k += nwarps) {
+        const uint32_t r = drec[k];
+        const unsigned long long off = inst_off[r], cnt = tt[r];
+        float w = 0.f;
+        uint32_t a = 0;
+        if (off + cnt <= ninst) {
+            for (unsigned long long t = lane; t < cnt; t += 32) {
+                const float2 s = slots[off + t];
+                w += s.x;
+                a += __float_as_uint(s.y);
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        a = __reduce_add_sync(0xffffffffu, a);
+        if (lane == 0) {
+            imp_w[r] = w;
+            imp_a[r] = a;
         }
     }
-    imp_w[r] = w;
-    imp_a[r] = a;
 }
 
 struct ImpGaussArgs {
-    const uint32_t *rec_off;
+    const uint32_t *rec_g;
     const uint16_t *rec_cam;
     const float *imp_w;
     const uint32_t *imp_a;
@@ -49,16 +60,17 @@ struct ImpGaussArgs {
     const DevCounters *ctr;
 };
 
+// One thread per Gaussian with records (the thread of its first record; a
+// Gaussian's records are contiguous).
 __global__ void __launch_bounds__(256) imp_gauss_kernel(ImpGaussArgs a)
 {
-    const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
-    if (i >= a.n) return;
+    const unsigned long long rh = (unsigned long long)blockIdx.x * 256 + threadIdx.x;
     const unsigned long long nrec = a.ctr->n_records;
-    unsigned long long r0 = a.rec_off[i], r1 = a.rec_off[i + 1];
-    if (r1 > nrec) r1 = nrec;
-    if (r0 >= r1) return;
+    if (rh >= nrec || (rh > 0 && a.rec_g[rh - 1] == a.rec_g[rh])) return;
+    const long long i = a.rec_g[rh];
     float s = 0.f;
-    for (unsigned long long r = r0; r < r1; r++) {
+    uint32_t nr = 0;
+    for (unsigned long long r = rh; r < nrec && a.rec_g[r] == (uint32_t)i; r++, nr++) {
         const float w = a.imp_w[r];
         const uint32_t cnt = a.imp_a[r];
         if (cnt > 0) s += w / ((float)cnt + a.eps);
@@ -67,7 +79,7 @@ __global__ void __launch_bounds__(256) imp_gauss_kernel(ImpGaussArgs a)
         if (a.a_out) a.a_out[(long long)c * a.n + i] = cnt;
     }
     if (a.s_accum) a.s_accum[i] += s;
-    if (a.crad) a.crad[i] += (uint32_t)(r1 - r0);
+    if (a.crad) a.crad[i] += nr;
 }
 
 // keys = bit-complement of the FP32 bits of w (w >= 0), so ascending keys are
@@ -227,16 +239,17 @@ cudaError_t launch_importance(gs_workspace *ws, cudaStream_t st, float *w, uint3
     const unsigned long long rcap = (unsigned long long)ws->cap.max_records;
     const unsigned rblocks = (unsigned)((rcap + 255) / 256);
     if ((e = launch_importance_raster(ws, st)) != cudaSuccess) return e;
-    imp_reduce_kernel<<<rblocks, 256, 0, st>>>(ws->dval[ws->depth_buf], ws->inst_off, ws->tt,
+    imp_reduce_kernel<<<(unsigned)std::max<unsigned long long>(1, std::min<unsigned long long>((rcap + 7) / 8, 152 * 16)), 256, 0, st>>>(
+        ws->dval[ws->depth_buf], ws->inst_off, ws->tt,
                                                 reinterpret_cast<const float2 *>(ws->slots), ws->imp_w, ws->imp_a,
                                                 ws->ctr);
     note_launch();
     if (w && (e = cudaMemsetAsync(w, 0, (size_t)ncam * n * sizeof(float), st)) != cudaSuccess) return e;
     if (a && (e = cudaMemsetAsync(a, 0, (size_t)ncam * n * sizeof(uint32_t), st)) != cudaSuccess) return e;
     if (n > 0) {
-        ImpGaussArgs ga{ws->rec_off, ws->rec_cam, ws->imp_w, ws->imp_a, w, a, s_accum, crad, n, ws->rc.eps_score,
+        ImpGaussArgs ga{ws->rec_g, ws->rec_cam, ws->imp_w, ws->imp_a, w, a, s_accum, crad, n, ws->rc.eps_score,
                         ws->ctr};
-        imp_gauss_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ga);
+        imp_gauss_kernel<<<rblocks, 256, 0, st>>>(ga);
         note_launch();
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

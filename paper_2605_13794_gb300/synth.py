@@ -30,11 +30,10 @@ SH_COEFFS = 16  # degree 3
 
 @dataclasses.dataclass
 class GaussianSet:
-    """Structure-of-arrays Gaussian parameters, float32, C-contiguous.
+    """Gaussian parameters, float32, C-contiguous, one row per Gaussian:
 
-    mean (3, N), log_scale (3, N), quat (4, N) as (w, x, y, z),
-    opacity_logit (N,), sh (16, 3, N) coefficient-major then channel,
-    lod (N,) uint8.
+    mean (N, 3), log_scale (N, 3), quat (N, 4) as (w, x, y, z),
+    opacity_logit (N,), sh (N, 16, 3) coefficient then channel, lod (N,) uint8.
     """
 
     mean: np.ndarray
@@ -54,13 +53,7 @@ class GaussianSet:
 
     def subset(self, idx) -> "GaussianSet":
         idx = np.asarray(idx)
-        return GaussianSet(
-            mean=np.ascontiguousarray(self.mean[:, idx]),
-            log_scale=np.ascontiguousarray(self.log_scale[:, idx]),
-            quat=np.ascontiguousarray(self.quat[:, idx]),
-            opacity_logit=np.ascontiguousarray(self.opacity_logit[idx]),
-            sh=np.ascontiguousarray(self.sh[:, :, idx]),
-            lod=np.ascontiguousarray(self.lod[idx]))
+        return GaussianSet(**{k: np.ascontiguousarray(v[idx]) for k, v in self.arrays().items()})
 
     def copy(self) -> "GaussianSet":
         return GaussianSet(**{k: v.copy() for k, v in self.arrays().items()})
@@ -95,13 +88,13 @@ def _f32(a):
 def _random_quats(rng, n):
     q = rng.standard_normal((4, n))
     q /= np.linalg.norm(q, axis=0, keepdims=True)
-    return _f32(q)
+    return _f32(q.T)
 
 
 def _sh(rng, n, dc=0.5, sigma=0.2):
     sh = rng.normal(0.0, sigma, size=(SH_COEFFS, 3, n))
     sh[0] += dc
-    return _f32(sh)
+    return _f32(sh.transpose(2, 0, 1))
 
 
 def _logit(p):
@@ -120,7 +113,7 @@ def plain_scene(n: int = 10_000, seed: int = 1) -> GaussianSet:
     opacity_logit = rng.standard_normal(n)  # opacity = sigmoid(N(0,1))
     sh = _sh(rng, n)
     lod = np.zeros(n, np.uint8)
-    return GaussianSet(_f32(mean), _f32(log_scale), quat, _f32(opacity_logit), sh, lod)
+    return GaussianSet(_f32(mean.T), _f32(log_scale.T), quat, _f32(opacity_logit), sh, lod)
 
 
 def plain_camera(width: int = 256, height: int = 256, f: float = 300.0) -> Camera:
@@ -193,7 +186,7 @@ def city_scene(n: int, seed: int = 3, extent: float = 2000.0, n_boxes: int = 200
     sh = _sh(rng, n)
     mean_scale = np.exp(log_scale).mean(axis=0)
     lod = np.clip(np.round(np.log2(2.4 / mean_scale)), 0, n_levels - 1).astype(np.uint8)
-    return GaussianSet(_f32(mean), _f32(log_scale), quat, _f32(opacity_logit), sh, lod)
+    return GaussianSet(_f32(mean.T), _f32(log_scale.T), quat, _f32(opacity_logit), sh, lod)
 
 
 def aerial_camera(seed: int, width: int = 1920, height: int = 1080, hfov_deg: float = 60.0,
@@ -214,7 +207,7 @@ def perturbed_copy(g: GaussianSet, seed: int, mean_sigma: float = 0.1, dc_sigma:
     out = g.copy()
     out.mean = _f32(out.mean + rng.normal(0.0, mean_sigma, size=out.mean.shape))
     out.sh = out.sh.copy()
-    out.sh[0] = (out.sh[0] + rng.normal(0.0, dc_sigma, size=out.sh[0].shape)).astype(np.float32)
+    out.sh[:, 0] = (out.sh[:, 0] + rng.normal(0.0, dc_sigma, size=out.sh[:, 0].shape)).astype(np.float32)
     return out
 
 

@@ -19,8 +19,8 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 def _scene(n, seed, opacity_max=None, depth=(2.0, 6.0), scale=(1e-3, 5e-2)):
     rng = np.random.default_rng(seed)
     g = synth.plain_scene(n, seed)
-    g.mean[2] = rng.uniform(*depth, n).astype(np.float32)
-    g.log_scale[:] = rng.uniform(math.log(scale[0]), math.log(scale[1]), (3, n)).astype(np.float32)
+    g.mean[:, 2] = rng.uniform(*depth, n).astype(np.float32)
+    g.log_scale[:] = rng.uniform(math.log(scale[0]), math.log(scale[1]), (n, 3)).astype(np.float32)
     if opacity_max is not None:
         o = rng.uniform(0.05, opacity_max, n)
         g.opacity_logit[:] = np.log(o / (1 - o)).astype(np.float32)
@@ -79,10 +79,10 @@ def test_sh_gradient_fd(oracle_mod):
 
 def _one(mean, log_s, quat, opac_logit, sh_dc=(0.0, 0.0, 0.0)):
     g = synth.GaussianSet(
-        mean=np.array(mean, np.float32).reshape(3, 1), log_scale=np.array(log_s, np.float32).reshape(3, 1),
-        quat=np.array(quat, np.float32).reshape(4, 1), opacity_logit=np.array([opac_logit], np.float32),
-        sh=np.zeros((16, 3, 1), np.float32), lod=np.zeros(1, np.uint8))
-    g.sh[0, :, 0] = np.array(sh_dc, np.float32)
+        mean=np.array(mean, np.float32).reshape(1, 3), log_scale=np.array(log_s, np.float32).reshape(1, 3),
+        quat=np.array(quat, np.float32).reshape(1, 4), opacity_logit=np.array([opac_logit], np.float32),
+        sh=np.zeros((1, 16, 3), np.float32), lod=np.zeros(1, np.uint8))
+    g.sh[0, 0, :] = np.array(sh_dc, np.float32)
     return g
 
 
@@ -162,7 +162,7 @@ def test_two_gaussians_by_hand(oracle_mod):
     ls = math.log(1e-4)
     g = _one([0.0, 0.0, 3.0], [ls] * 3, [1, 0, 0, 0], math.log(0.6 / 0.4), (1.0, 0.0, 0.0))
     g2 = _one([0.0, 0.0, 2.0], [ls] * 3, [1, 0, 0, 0], math.log(0.5 / 0.5), (0.0, 1.0, 0.0))
-    both = synth.GaussianSet(*[np.concatenate([getattr(g, k), getattr(g2, k)], axis=-1)
+    both = synth.GaussianSet(*[np.concatenate([getattr(g, k), getattr(g2, k)], axis=0)
                                for k in ("mean", "log_scale", "quat", "opacity_logit", "sh", "lod")])
     fwd = oracle_mod.forward_view(oracle_mod.gaussians64(both), cam, P)
     C0 = 0.28209479177387814
@@ -184,7 +184,7 @@ def test_equal_depth_ties_by_index(oracle_mod):
     cam = synth.plain_camera(16, 16, 300.0)
     P = oracle_mod.Params()
     g = synth.plain_scene(6, 11)
-    g.mean[:] = np.array([[0.0], [0.0], [3.0]], np.float32)
+    g.mean[:] = np.array([[0.0, 0.0, 3.0]], np.float32)
     g.log_scale[:] = np.float32(math.log(0.01))
     fwd = oracle_mod.forward_view(oracle_mod.gaussians64(g), cam, P)
     ts, lst = fwd["bins"]
@@ -195,7 +195,7 @@ def test_transmittance_invariant(oracle_mod):
     # all colours 1 and bg 0: C(p) = sum alpha_i T_i = 1 - T_final (telescoping product)
     g = synth.plain_scene(3000, 21)
     g.sh[:] = 0.0
-    g.sh[0] = np.float32(0.5 / 0.28209479177387814)
+    g.sh[:, 0, :] = np.float32(0.5 / 0.28209479177387814)
     cam = synth.plain_camera(96, 80, 200.0)
     P = oracle_mod.Params()
     fwd = oracle_mod.forward_view(oracle_mod.gaussians64(g), cam, P)
@@ -260,8 +260,8 @@ def _loss_and_state(oracle_mod, g64, cam, P, dL):
 def test_backward_matches_central_differences(oracle_mod, seed):
     rng = np.random.default_rng(seed)
     g = _scene(14, seed, opacity_max=0.9, depth=(2.0, 3.0), scale=(0.01, 0.04))
-    g.mean[0] = rng.uniform(-0.25, 0.25, g.n).astype(np.float32)
-    g.mean[1] = rng.uniform(-0.25, 0.25, g.n).astype(np.float32)
+    g.mean[:, 0] = rng.uniform(-0.25, 0.25, g.n).astype(np.float32)
+    g.mean[:, 1] = rng.uniform(-0.25, 0.25, g.n).astype(np.float32)
     cam = synth.plain_camera(48, 40, 120.0)
     P = oracle_mod.Params()
     g64 = oracle_mod.gaussians64(g)
