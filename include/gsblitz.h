@@ -252,6 +252,26 @@ int gs_photometric_loss(gs_workspace *ws, const float *image, const float *targe
  * <= GS_MAX_ADAM_GROUPS) parameter groups; step counts from 1. */
 int gs_adam_step(const gs_adam_group *groups, int32_t n_groups, int32_t step, gs_stream stream);
 
+/* The Cull column of one view (the selection step of gs_importance) without
+ * any allocation and without a workspace.  The paper has no counterpart: this
+ * entry point exists for callers that may not allocate device memory -- code
+ * where a cudaMalloc is forbidden or would stall other work (it can
+ * synchronise the device), such as a latency-critical serving thread, a host
+ * callback or a plugin whose memory belongs to another allocator.
+ *   w        [n] device: the view's per-Gaussian alpha-weights (gs_importance's w)
+ *   cull_out [ceil(n/32)] device, written: bit = 1 - c^vis (top vis_mass of the w mass)
+ *   cvis_accum [n] device, += 1 where visible; may be NULL
+ * n <= 2^20: the scratch (about 24.6 MB) is one fixed device array of the
+ * library, which every GPU that loads its module keeps until the process
+ * exits; larger n is rejected with GS_ERR_CAPACITY.  The first call on a
+ * device looks the array's device address up (cudaGetSymbolAddress, with that
+ * device current), so make that first call before any stream capture.  All
+ * calls share the array: calls whose work overlaps on the GPU race and must be
+ * serialised by the caller.  Asynchronous on stream; kernel-side waits are
+ * bounded and leave the output undefined if one gives up. */
+int gs_visible_set_static(const float *w, int64_t n, float vis_mass, uint32_t *cull_out, uint32_t *cvis_accum,
+                          gs_stream stream);
+
 /* Synchronises the stream and returns the device error word as a status. */
 int gs_sync_status(gs_workspace *ws, gs_stream stream);
 /* Synchronises the stream and reads the counters (host pointer out). */

@@ -26,7 +26,8 @@ GS_TILE = 16
 EXPORTS = ("gs_default_params", "gs_last_error", "gs_workspace_create", "gs_workspace_destroy", "gs_workspace_bytes",
            "gs_preprocess", "gs_bin_sort", "gs_render_fwd", "gs_render_bwd", "gs_importance", "gs_photometric_loss",
            "gs_adam_step", "gs_sync_status", "gs_workspace_counts", "gs_clear_error", "gs_workspace_buffer",
-           "gs_kernel_launches", "gs_render_bwd_adam", "gs_render_bwd_compact", "gs_adam_step_compact")
+           "gs_kernel_launches", "gs_render_bwd_adam", "gs_render_bwd_compact", "gs_adam_step_compact",
+           "gs_visible_set_static")
 
 
 class GSError(RuntimeError):
@@ -106,6 +107,7 @@ def lib() -> ctypes.CDLL:
         L.gs_render_bwd_adam.argtypes = [vp, vp, vp, vp, vp, vp, f32, f32, f32, i32, vp, f32, vp, vp]
         L.gs_render_bwd_compact.argtypes = [vp, vp, vp, vp, f32, vp, vp]
         L.gs_adam_step_compact.argtypes = [vp, vp, vp, vp, vp, f32, f32, f32, i32, vp]
+        L.gs_visible_set_static.argtypes = [vp, i64, f32, vp, vp, vp]
         L.gs_importance.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
         L.gs_photometric_loss.argtypes = [vp, vp, vp, i32, i32, i32, ctypes.c_float, vp, vp, vp]
         L.gs_adam_step.argtypes = [vp, i32, i32, vp]
@@ -346,6 +348,13 @@ def _memcpy_d2h(dst: int, src: int, nbytes: int):
     rc = _cudart.cudaMemcpy(ctypes.c_void_p(dst), ctypes.c_void_p(src), nbytes, 2)  # cudaMemcpyDeviceToHost
     if rc != 0:
         raise RuntimeError(f"cudaMemcpy failed with {rc}")
+
+
+def visible_set_static(w, vis_mass, cull_out, cvis_accum=None, stream=None):
+    """Cull column of one view from its per-Gaussian w without any allocation
+    (fixed library scratch, n <= 2^20; see gs_visible_set_static)."""
+    _check(lib().gs_visible_set_static(_ptr(w), int(w.numel()), float(vis_mass), _ptr(cull_out), _ptr(cvis_accum),
+                                       _stream(stream)))
 
 
 def kernel_launches() -> int:

@@ -131,6 +131,11 @@ std::atomic<long long> g_launches{0};
 
 void gs::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+int gs::report_error(int code, const char *msg)
+{
+    return fail(code, "%s", msg);
+}
+
 extern "C" {
 
 int64_t gs_kernel_launches(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }

@@ -248,6 +248,8 @@ struct gs_workspace {
 namespace gs {
 // Counts one kernel launch of this library (process-wide, see gs_kernel_launches).
 void note_launch();
+// Records msg as the calling thread's gs_last_error() and returns code.
+int report_error(int code, const char *msg);
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t *cull);
 cudaError_t launch_radix_sort(gs_workspace *ws, cudaStream_t st, uint32_t *keys[2], uint32_t *vals[2],

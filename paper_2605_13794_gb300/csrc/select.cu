@@ -184,6 +184,23 @@ __global__ void sel_segments_kernel(const uint32_t *vals, const uint16_t *rec_ca
     }
 }
 
+// The fixed-association FP64 prefix of w in sorted order with explicit
+// buffers (no workspace): bsum [ceil(cap / 4096)] doubles, cum [cap] doubles;
+// the item count is ctr->n_records.
+cudaError_t launch_mass_scan(cudaStream_t st, const uint32_t *sorted, const float *w, double *bsum, double *cum,
+                             const DevCounters *ctr, unsigned long long cap)
+{
+    const unsigned sblocks = (unsigned)((cap + kScanTile - 1) / kScanTile);
+    if (sblocks == 0) return cudaSuccess;
+    sel_block_sum_kernel<<<sblocks, 256, 0, st>>>(sorted, w, bsum, ctr);
+    note_launch();
+    sel_block_scan_kernel<<<1, 256, 0, st>>>(bsum, (int)sblocks);
+    note_launch();
+    sel_scan_kernel<<<sblocks, 256, 0, st>>>(sorted, w, bsum, cum, ctr);
+    note_launch();
+    return cudaGetLastError();
+}
+
 struct SelApplyArgs {
     const uint32_t *vals;
     const uint32_t *rec_g;

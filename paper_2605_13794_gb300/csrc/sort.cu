@@ -226,6 +226,44 @@ cudaError_t launch_radix_sort(gs_workspace *ws, cudaStream_t st, uint32_t *keys[
     return cudaSuccess;
 }
 
+// The same LSD sort with every scratch buffer passed in (no workspace):
+// status [ceil(cap / 4096) * 256 + 1] uint32, hist and off [4 * 256] uint32,
+// ctr receives a timeout error.  Used by the entry point without allocation.
+cudaError_t launch_radix_sort_scratch(cudaStream_t st, uint32_t *keys[2], uint32_t *vals[2],
+                                      const unsigned long long *count, unsigned long long cap, int bits,
+                                      bool vals_identity, uint32_t *status, uint32_t *hist, uint32_t *off,
+                                      DevCounters *ctr, int &out_buf)
+{
+    const int passes = bits <= 0 ? 1 : (bits + 7) / 8;
+    const unsigned long long blocks = (cap + kSortTile - 1) / kSortTile;
+    cudaError_t e;
+    out_buf = 0;
+    if (cap == 0) return cudaSuccess;
+    if ((e = cudaMemsetAsync(hist, 0, 4 * 256 * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    unsigned hblocks = (unsigned)((cap + 255) / 256);
+    if (hblocks > 1216) hblocks = 1216;
+    radix_hist_kernel<<<hblocks, 256, 0, st>>>(keys[0], count, cap, passes, hist);
+    note_launch();
+    radix_offsets_kernel<<<1, 256, 0, st>>>(hist, off, passes);
+    note_launch();
+    int src = 0;
+    for (int p = 0; p < passes; p++) {
+        const int dst = src ^ 1;
+        if ((e = cudaMemsetAsync(status, 0, (blocks * 256 + 1) * sizeof(uint32_t), st)) != cudaSuccess) return e;
+        if (vals_identity && p == 0)
+            radix_pass_kernel<true, true><<<(unsigned)blocks, kSortThreads, 0, st>>>(
+                keys[src], vals[src], keys[dst], vals[dst], count, cap, 8 * p, off + 256 * p, status, ctr);
+        else
+            radix_pass_kernel<false, true><<<(unsigned)blocks, kSortThreads, 0, st>>>(
+                keys[src], vals[src], keys[dst], vals[dst], count, cap, 8 * p, off + 256 * p, status, ctr);
+        note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        src = dst;
+    }
+    out_buf = src;
+    return cudaSuccess;
+}
+
 // ---- emission -------------------------------------------------------------
 
 struct EmitArgs {
