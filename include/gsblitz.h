@@ -157,9 +157,11 @@ typedef enum {
     GS_BUF_REC_RECT = 2,     /* uint32 [max_records][2]: x0|y0<<16, x1|y1<<16 (tiles) */
     GS_BUF_REC_TILES = 3,    /* uint32 [max_records]: tiles touched */
     GS_BUF_REC_DEPTH = 4,    /* uint32 [max_records]: FP32 bits of camera z (valid until gs_bin_sort) */
-    GS_BUF_REC_XY_CONIC = 5, /* float4 [max_records]: u, v, A, B */
-    GS_BUF_REC_C_OPAC_RG = 6,/* float4 [max_records]: C, opacity, r, g */
-    GS_BUF_REC_B = 7,        /* float  [max_records]: b */
+    GS_BUF_REC_XY_CONIC = 5, /* float4 [max_records]: u, v (the floats nearest the projected mean), A, k */
+    GS_BUF_REC_C_OPAC_RG = 6,/* float4 [max_records]: D, opacity, r, g */
+    GS_BUF_REC_B_LO = 7,     /* float4 [max_records]: b, u_lo, v_lo, 0; the mean is u + u_lo, v + v_lo.
+                              * The conic is held as A (x + k y)^2 + D y^2, i.e. k = B / A and
+                              * D = C - B^2 / A of the conic (A, B; B, C). */
     GS_BUF_SORTED_VALUES = 8,/* uint32 [max_instances]: record of each sorted instance */
     GS_BUF_TILE_RANGES = 9,  /* uint32 [max_tiles][2]: [start, end) of each tile */
     GS_BUF_N_CONTRIB = 10    /* uint32 [max_pixels]: last composited entry + 1 */

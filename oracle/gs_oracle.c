@@ -191,6 +191,8 @@ typedef struct {
     int32_t *radius;    /* n */
     int32_t *rect;      /* 4n */
     int32_t *tiles;     /* n */
+    double *ldl32;      /* 3n: (A, k, D) of the FP32 instance's conic, NULL if not wanted */
+    double *uv32;       /* 2n: projected mean in double, before the FP32 instance rounds it */
 } or_proj_out;
 
 static int cull_bit(const uint32_t *cull, int64_t i)
@@ -221,6 +223,13 @@ int or_project(int64_t n, const double *mean, const double *log_scale, const dou
         out->tiles[i] = d32.status == OR_ACTIVE ? (d32.rect[2] - d32.rect[0]) * (d32.rect[3] - d32.rect[1]) : 0;
         out->uv[2 * i] = d64.u;
         out->uv[2 * i + 1] = d64.v;
+        if (out->ldl32) {
+            out->ldl32[3 * i] = d32.ldlA;
+            out->ldl32[3 * i + 1] = d32.ldlK;
+            out->ldl32[3 * i + 2] = d32.ldlD;
+            out->uv32[2 * i] = d32.ud;
+            out->uv32[2 * i + 1] = d32.vd;
+        }
         out->conic[3 * i] = d64.conA;
         out->conic[3 * i + 1] = d64.conB;
         out->conic[3 * i + 2] = d64.conC;
@@ -312,53 +321,100 @@ typedef struct {
     uint8_t flags;
 } pix_t;
 
-static int near_rel(double x, double thr, double band)
+/* x within a relative distance band of thr, measured in log space so that an
+ * error bound on an exponent applies directly (band ~ |log(x / thr)|). */
+static int near_log(double x, double thr, double band)
 {
-    return fabs(x - thr) <= band * fabs(thr);
+    return x > 0.0 && fabs(log(x / thr)) <= band;
+}
+
+/* How far an FP32 renderer's exponent for this fragment can be from the exact
+ * one.  An FP32 renderer composites with the FP32 instance's conic, held as
+ * A (x + k y)^2 + D y^2 (ldl32), and a mean kept to double precision (uv32).
+ * The exponent these give, evaluated exactly, differs from the exact exponent
+ * by the projection's own rounding; evaluating that form in FP32 adds, per
+ * operation, a relative 2^-24 of the terms it combines, and 2^x in FP32 a few
+ * more units.  A fragment whose alpha lies within this of a threshold may be
+ * decided the other way by a correct FP32 renderer. */
+static double fp32_power_err(const double *ldl32, const double *uv32, int32_t g, double px, double py,
+                             double power)
+{
+    const double eps32 = 5.9604644775390625e-08; /* 2^-24 */
+    if (!ldl32) return 16.0 * eps32 * (fabs(power) + 1.0);
+    const double A = ldl32[3 * g], k = ldl32[3 * g + 1], D = ldl32[3 * g + 2];
+    const double dx = px - uv32[2 * g], dy = py - uv32[2 * g + 1];
+    const double e = dx + k * dy;
+    const double p32 = -0.5 * (A * e * e + D * dy * dy);
+    const double de = 2.0 * eps32 * (fabs(dx) + 2.0 * fabs(k * dy));
+    const double eval = 0.5 * A * (2.0 * fabs(e) * de + de * de) + 4.0 * eps32 * (fabs(p32) + 1.0);
+    return 2.0 * (fabs(p32 - power) + eval);
 }
 
 /* Composites the ordered Gaussians ids[0..len) at pixel centre (px, py).
- * Optional w/a accumulate the importance alpha-weight and pixel count. */
+ * Optional w/a accumulate the importance alpha-weight and pixel count.
+ * Flags: a fragment within tie band (comp_band, widened by its own FP32 error
+ * bound) of the alpha_min or T_min threshold, or at the exponent's maximum 0.
+ * When the pixel is flagged and gcount is given, every Gaussian the pixel
+ * composited or nearly composited has its count of such pixels raised. */
 static void composite_pixel(const or_params *P, double px, double py, const int32_t *ids, int64_t len,
                             const double *uv, const double *conic, const double *opacity,
-                            const double *rgb, pix_t *o, double *w, double *a)
+                            const double *rgb, pix_t *o, double *w, double *a, int32_t *gcount,
+                            const double *ldl32, const double *uv32)
 {
     double T = 1.0, C[3] = {0, 0, 0};
+    double T_relerr = 0.0; /* bound on the relative error of T in FP32 */
     int32_t nc = 0;
     uint8_t fl = 0;
+    int64_t jstop = len;
     for (int64_t j = 0; j < len; j++) {
         int32_t g = ids[j];
         double dx = px - uv[2 * g], dy = py - uv[2 * g + 1];
         double A = conic[3 * g], B = conic[3 * g + 1], Cc = conic[3 * g + 2];
         double power = -0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy;
-        if (power > -1e-6) fl |= OR_PIX_POWER; /* exponent at its maximum 0 */
-        if (power > 0.0) continue;
+        const double perr = fp32_power_err(ldl32, uv32, g, px, py, power);
+        if (power > 0.0) { fl |= OR_PIX_POWER; continue; } /* only from rounding at the centre */
         double G = exp(power);
         double og = opacity[g] * G;
-        if (near_rel(og, P->alpha_max, P->comp_band)) fl |= OR_PIX_ALPHA_MAX;
-        double alpha = og < P->alpha_max ? og : P->alpha_max;
-        if (near_rel(alpha, P->alpha_min, P->comp_band)) fl |= OR_PIX_ALPHA_MIN;
+        if (near_log(og, P->alpha_max, P->comp_band + perr)) fl |= OR_PIX_ALPHA_MAX;
+        const int clamped = og >= P->alpha_max;
+        double alpha = clamped ? P->alpha_max : og;
+        if (near_log(alpha, P->alpha_min, P->comp_band + perr)) fl |= OR_PIX_ALPHA_MIN;
         if (alpha < P->alpha_min) continue;
         double testT = T * (1.0 - alpha);
-        if (near_rel(testT, P->T_min, P->comp_band)) fl |= OR_PIX_T_MIN;
-        if (testT < P->T_min) break;
+        const double trel = T_relerr + (clamped ? 0.0 : perr * alpha / (1.0 - alpha));
+        if (near_log(testT, P->T_min, P->comp_band + trel)) fl |= OR_PIX_T_MIN;
+        if (testT < P->T_min) { jstop = j; break; }
         for (int c = 0; c < 3; c++) C[c] += alpha * T * rgb[3 * g + c];
         if (w) w[g] += alpha * T;
         if (a) a[g] += 1.0;
         T = testT;
+        T_relerr = trel + 2.0 * 5.9604644775390625e-08;
         nc = (int32_t)(j + 1);
     }
     for (int c = 0; c < 3; c++) o->C[c] = C[c] + T * P->bg[c];
     o->T = T;
     o->n_contrib = nc;
     o->flags = fl;
+    if (fl && gcount) {
+        for (int64_t j = 0; j <= jstop && j < len; j++) {
+            int32_t g = ids[j];
+            double dx = px - uv[2 * g], dy = py - uv[2 * g + 1];
+            double power = -0.5 * (conic[3 * g] * dx * dx + conic[3 * g + 2] * dy * dy) - conic[3 * g + 1] * dx * dy;
+            if (opacity[g] * exp(power) >= 0.5 * P->alpha_min) gcount[g] += 1;
+        }
+    }
 }
 
 /* Tiled render: image (3,H,W) planar, T_final (H,W), n_contrib (H,W), flags
- * (H,W); w, a (n) accumulate the importance signals when non-NULL. */
+ * (H,W); w, a (n) accumulate the importance signals when non-NULL; gcount (n)
+ * counts, per Gaussian, the flagged pixels it takes part in, when non-NULL.
+ * ldl32 (3n) and uv32 (2n), from the projection's FP32 instance, widen the
+ * flag bands by how far an FP32 renderer's exponents can be from the exact
+ * ones; NULL leaves only the fixed bands. */
 int or_render(const or_camera *cam, const or_params *P, int64_t n, const double *uv, const double *conic,
               const double *opacity, const double *rgb, const int64_t *tile_start, const int32_t *list,
-              double *image, double *T_final, int32_t *n_contrib, uint8_t *flags, double *w, double *a)
+              double *image, double *T_final, int32_t *n_contrib, uint8_t *flags, double *w, double *a,
+              int32_t *gcount, const double *ldl32, const double *uv32)
 {
     (void)n;
     const int W = cam->width, H = cam->height, ts = P->tile;
@@ -368,7 +424,7 @@ int or_render(const or_camera *cam, const or_params *P, int64_t n, const double 
             int64_t t = (int64_t)(py / ts) * tiles_x + px / ts;
             pix_t o;
             composite_pixel(P, px + 0.5, py + 0.5, list + tile_start[t], tile_start[t + 1] - tile_start[t],
-                            uv, conic, opacity, rgb, &o, w, a);
+                            uv, conic, opacity, rgb, &o, w, a, gcount, ldl32, uv32);
             int64_t p = (int64_t)py * W + px;
             for (int c = 0; c < 3; c++) image[(int64_t)c * W * H + p] = o.C[c];
             T_final[p] = o.T;
@@ -395,7 +451,7 @@ int or_render_brute(const or_camera *cam, const or_params *P, int64_t n, const i
     for (int py = 0; py < H; py++)
         for (int px = 0; px < W; px++) {
             pix_t o;
-            composite_pixel(P, px + 0.5, py + 0.5, ids, m, uv, conic, opacity, rgb, &o, NULL, NULL);
+            composite_pixel(P, px + 0.5, py + 0.5, ids, m, uv, conic, opacity, rgb, &o, NULL, NULL, NULL, NULL, NULL);
             int64_t p = (int64_t)py * W + px;
             for (int c = 0; c < 3; c++) image[(int64_t)c * W * H + p] = o.C[c];
             T_final[p] = o.T;
@@ -414,7 +470,8 @@ int or_render_pixels(const or_params *P, int64_t npix, const int32_t *pxy, const
     for (int64_t k = 0; k < npix; k++) {
         pix_t o;
         composite_pixel(P, pxy[2 * k] + 0.5, pxy[2 * k + 1] + 0.5, lists + list_start[k],
-                        list_start[k + 1] - list_start[k], uv, conic, opacity, rgb, &o, NULL, NULL);
+                        list_start[k + 1] - list_start[k], uv, conic, opacity, rgb, &o, NULL, NULL, NULL, NULL,
+                        NULL);
         for (int c = 0; c < 3; c++) C[3 * k + c] = o.C[c];
         T[k] = o.T;
         n_contrib[k] = o.n_contrib;

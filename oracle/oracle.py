@@ -68,7 +68,8 @@ class ORParams(ctypes.Structure):
 
 class ORProjOut(ctypes.Structure):
     _fields_ = [(name, ctypes.c_void_p) for name in
-                ("status", "tie", "uv", "depth", "depth32", "conic", "opacity", "rgb", "clamp", "radius", "rect", "tiles")]
+                ("status", "tie", "uv", "depth", "depth32", "conic", "opacity", "rgb", "clamp", "radius", "rect", "tiles",
+                 "ldl32", "uv32")]
 
 
 def lib():
@@ -79,7 +80,7 @@ def lib():
         _lib.or_project.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         _lib.or_bin.argtypes = [i64, vp, vp, vp, i32, i32, vp, vp, i64]
         _lib.or_bin.restype = i64
-        _lib.or_render.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        _lib.or_render.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         _lib.or_render_brute.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
         _lib.or_render_pixels.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         _lib.or_render_bwd.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -158,7 +159,8 @@ def project(g64: dict, cam, params: Params, cull=None) -> dict:
     out = dict(status=np.zeros(n, np.int8), tie=np.zeros(n, np.uint8), uv=np.zeros((n, 2)),
                depth=np.zeros(n), depth32=np.zeros(n, np.float32), conic=np.zeros((n, 3)),
                opacity=np.zeros(n), rgb=np.zeros((n, 3)), clamp=np.zeros(n, np.uint8),
-               radius=np.zeros(n, np.int32), rect=np.zeros((n, 4), np.int32), tiles=np.zeros(n, np.int32))
+               radius=np.zeros(n, np.int32), rect=np.zeros((n, 4), np.int32), tiles=np.zeros(n, np.int32),
+               ldl32=np.zeros((n, 3)), uv32=np.zeros((n, 2)))
     po = ORProjOut(*[out[f[0]].ctypes.data for f in ORProjOut._fields_])
     cull_arr = None if cull is None else np.ascontiguousarray(cull, np.uint32)
     cam_c, par_c = camera_c(cam), params.c()
@@ -190,11 +192,12 @@ def render(proj: dict, bins, cam, params: Params) -> dict:
     n = proj["status"].shape[0]
     W, H = cam.width, cam.height
     out = dict(image=np.zeros((3, H, W)), T=np.zeros((H, W)), n_contrib=np.zeros((H, W), np.int32),
-               flags=np.zeros((H, W), np.uint8), w=np.zeros(n), a=np.zeros(n))
+               flags=np.zeros((H, W), np.uint8), w=np.zeros(n), a=np.zeros(n), gcount=np.zeros(n, np.int32))
     lst = np.ascontiguousarray(lst, np.int32) if lst.size else np.zeros(1, np.int32)
     lib().or_render(ctypes.byref(camera_c(cam)), ctypes.byref(params.c()), n, _p(proj["uv"]), _p(proj["conic"]),
                     _p(proj["opacity"]), _p(proj["rgb"]), _p(tile_start), _p(lst), _p(out["image"]), _p(out["T"]),
-                    _p(out["n_contrib"]), _p(out["flags"]), _p(out["w"]), _p(out["a"]))
+                    _p(out["n_contrib"]), _p(out["flags"]), _p(out["w"]), _p(out["a"]), _p(out["gcount"]),
+                    _p(proj.get("ldl32")), _p(proj.get("uv32")))
     return out
 
 

@@ -21,7 +21,7 @@ GS_OK, GS_ERR_INVALID_ARG, GS_ERR_OOM, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_TIME
 GS_MAX_CAMERAS = 64
 GS_TILE = 16
 (GS_BUF_REC_GAUSSIAN, GS_BUF_REC_CAMERA, GS_BUF_REC_RECT, GS_BUF_REC_TILES, GS_BUF_REC_DEPTH, GS_BUF_REC_XY_CONIC,
- GS_BUF_REC_C_OPAC_RG, GS_BUF_REC_B, GS_BUF_SORTED_VALUES, GS_BUF_TILE_RANGES, GS_BUF_N_CONTRIB) = range(11)
+ GS_BUF_REC_C_OPAC_RG, GS_BUF_REC_B_LO, GS_BUF_SORTED_VALUES, GS_BUF_TILE_RANGES, GS_BUF_N_CONTRIB) = range(11)
 
 EXPORTS = ("gs_default_params", "gs_last_error", "gs_workspace_create", "gs_workspace_destroy", "gs_workspace_bytes",
            "gs_preprocess", "gs_bin_sort", "gs_render_fwd", "gs_render_bwd", "gs_importance", "gs_photometric_loss",

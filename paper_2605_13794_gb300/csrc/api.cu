@@ -68,7 +68,7 @@ Offsets plan(const gs_capacity &c)
     o.rec_cam = L.take<uint16_t>(R);
     o.rd0 = L.take<float4>(R);
     o.rd1 = L.take<float4>(R);
-    o.rd2 = L.take<float>(R);
+    o.rd2 = L.take<float4>(R);
     o.rect = L.take<uint2>(R);
     o.tt = L.take<uint32_t>(R);
     o.inst_off = L.take<uint32_t>(R);
@@ -195,7 +195,7 @@ int gs_workspace_create(const gs_capacity *cap, gs_workspace **out)
     ws->rec_cam = (uint16_t *)(b + o.rec_cam);
     ws->rd0 = (float4 *)(b + o.rd0);
     ws->rd1 = (float4 *)(b + o.rd1);
-    ws->rd2 = (float *)(b + o.rd2);
+    ws->rd2 = (float4 *)(b + o.rd2);
     ws->rect = (uint2 *)(b + o.rect);
     ws->tt = (uint32_t *)(b + o.tt);
     ws->inst_off = (uint32_t *)(b + o.inst_off);
@@ -509,7 +509,7 @@ int gs_workspace_buffer(gs_workspace *ws, int32_t which, void **ptr, int64_t *co
     case GS_BUF_REC_DEPTH: *ptr = ws->dkey[0]; *count = c.max_records; break;
     case GS_BUF_REC_XY_CONIC: *ptr = ws->rd0; *count = c.max_records; break;
     case GS_BUF_REC_C_OPAC_RG: *ptr = ws->rd1; *count = c.max_records; break;
-    case GS_BUF_REC_B: *ptr = ws->rd2; *count = c.max_records; break;
+    case GS_BUF_REC_B_LO: *ptr = ws->rd2; *count = c.max_records; break;
     case GS_BUF_SORTED_VALUES: *ptr = ws->tval[ws->tile_buf]; *count = c.max_instances; break;
     case GS_BUF_TILE_RANGES: *ptr = ws->ranges; *count = c.max_tiles; break;
     case GS_BUF_N_CONTRIB: *ptr = ws->n_contrib; *count = c.max_pixels; break;

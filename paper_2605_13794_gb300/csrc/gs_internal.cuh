@@ -198,9 +198,9 @@ struct gs_workspace {
     // per record
     uint32_t *rec_g;
     uint16_t *rec_cam;
-    float4 *rd0;         // u, v, A, B
-    float4 *rd1;         // C, opacity, r, g
-    float *rd2;          // b
+    float4 *rd0;         // u, v (nearest floats to the mean), conic A, k
+    float4 *rd1;         // conic D, opacity, r, g
+    float4 *rd2;         // b, u_lo, v_lo (mean = u + u_lo), 0
     uint2 *rect;
     uint32_t *tt;
     uint32_t *inst_off;

@@ -27,8 +27,16 @@ struct GaussPtrs {
     long long n;
 };
 
+// One projected (Gaussian, camera) pair.  The mean is kept to about 48 bits
+// as u + u_lo (u = the float nearest the double-precision mean): pixel
+// coordinates near 2000 carry only 1e-4 px in one float, and at the edge of a
+// small footprint that is a relative 1e-3 of alpha.  The conic is held as
+// A (x + k y)^2 + D y^2, whose terms stay accurate for long thin footprints at
+// any orientation (the A, B, C form loses them to cancellation).
 struct Proj {
-    float u, v, A, B, C, depth;
+    float u, v, u_lo, v_lo; // projected mean
+    float A, k, D;          // conic: A = c / det, k = -b / c, D = 1 / c
+    float depth;
     int radius;
     int x0, y0, x1, y1;
 };
@@ -100,38 +108,70 @@ __device__ __forceinline__ bool lod_pass(const float m[3], int lod, const CamInf
     return d2 <= rc.lod_thr2[lod];
 }
 
-__device__ __forceinline__ void camera_point(const float m[3], const CamInfo &cam, float &tx, float &ty, float &tz)
+// Camera-space mean in float, for the gate only, with a bound on its distance
+// from the double-precision value the projection uses: three additions and
+// the final rounding each err by at most 2^-24 of a partial sum bounded by
+// sum_k |R_jk m_k| + |t_j|.
+__device__ __forceinline__ void camera_point(const float m[3], const CamInfo &cam, float t[3], float err[3])
 {
     const float *R = cam.R;
-    tx = FADD(FADD(FADD(FMUL(R[0], m[0]), FMUL(R[1], m[1])), FMUL(R[2], m[2])), cam.t[0]);
-    ty = FADD(FADD(FADD(FMUL(R[3], m[0]), FMUL(R[4], m[1])), FMUL(R[5], m[2])), cam.t[1]);
-    tz = FADD(FADD(FADD(FMUL(R[6], m[0]), FMUL(R[7], m[1])), FMUL(R[8], m[2])), cam.t[2]);
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        t[j] = FADD(FADD(FADD(FMUL(R[3 * j], m[0]), FMUL(R[3 * j + 1], m[1])), FMUL(R[3 * j + 2], m[2])), cam.t[j]);
+        const float mag = fabsf(R[3 * j] * m[0]) + fabsf(R[3 * j + 1] * m[1]) + fabsf(R[3 * j + 2] * m[2]) +
+                          fabsf(cam.t[j]);
+        err[j] = 8.f * 5.9604645e-8f * mag + 1e-30f;
+    }
+}
+
+// Camera-space mean in double: x_cam = R x + t.  float * float is exact in
+// double, so only the three additions round.
+__device__ __forceinline__ void camera_point_d(const float m[3], const CamInfo &cam, double t[3])
+{
+    const float *R = cam.R;
+#pragma unroll
+    for (int j = 0; j < 3; j++)
+        t[j] = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn((double)R[3 * j], (double)m[0]),
+                                             __dmul_rn((double)R[3 * j + 1], (double)m[1])),
+                                   __dmul_rn((double)R[3 * j + 2], (double)m[2])),
+                         (double)cam.t[j]);
 }
 
 // Conservative screen test run before the exact covariance: false only when
 // the exact tile rectangle is certainly empty.  lambda_max(Sigma') <=
 // |J|_F^2 max_j s_j^2 + dilation, |J|_F^2 <= jbound / tz^2 (clamped Jacobian),
-// plus sqrt(0.1) for the clamp of the discriminant, with margins for rounding.
-__device__ __forceinline__ bool maybe_on_screen(float tx, float ty, float tz, float smax, const CamInfo &cam,
+// plus sqrt(0.1) for the clamp of the discriminant, with margins for the
+// rounding of this float evaluation (t, e from camera_point).
+__device__ __forceinline__ bool maybe_on_screen(const float t[3], const float e[3], float smax, const CamInfo &cam,
                                                 const RenderConsts &rc)
 {
-    const float itz = 1.f / tz;
-    const float u = cam.fx * tx * itz + cam.cx, v = cam.fy * ty * itz + cam.cy;
-    const float lam = 1.01f * (cam.jbound * itz * itz * smax * smax + rc.dilation) + 0.33f;
+    const float tzl = t[2] - e[2]; // lower bound of the exact depth
+    if (!(tzl > 1e-6f)) return true;
+    const float itz = 1.f / t[2], itzl = 1.f / tzl;
+    const float u = cam.fx * t[0] * itz + cam.cx, v = cam.fy * t[1] * itz + cam.cy;
+    const float lam = 1.01f * (cam.jbound * itzl * itzl * smax * smax + rc.dilation) + 0.33f;
     const float R = 3.f * sqrtf(lam) + 2.f;
-    const float ru = R + 1e-5f * fabsf(u), rv = R + 1e-5f * fabsf(v);
+    // |d(tx / tz)| <= (e_x + |tx / tz| e_z) / tz_low
+    const float du = 1.01f * cam.fx * (e[0] + fabsf(t[0] * itz) * e[2]) * itzl;
+    const float dv = 1.01f * cam.fy * (e[1] + fabsf(t[1] * itz) * e[2]) * itzl;
+    const float ru = R + du + 1e-5f * fabsf(u), rv = R + dv + 1e-5f * fabsf(v);
     return !(u + ru < 0.f || u - ru >= (float)(cam.tiles_x * kTile) || v + rv < 0.f ||
              v - rv >= (float)(cam.tiles_y * kTile));
 }
 
-// Exact projection of one Gaussian into one camera (after the gate and the
-// near cull).  Returns false when the 2D covariance is degenerate or the tile
-// rectangle is empty.
-__device__ __forceinline__ bool project_gaussian(const float m[3], const float ls[3], const float qin[4],
-                                                 float tx, float ty, float tz, const CamInfo &cam,
-                                                 const RenderConsts &rc, Proj &o)
+// Exact projection of one Gaussian into one camera, from the double-precision
+// camera-space mean td (the near plane already passed).  Every float
+// operation is one explicitly rounded IEEE operation in a fixed order, so the
+// integer results (radius, rectangle, depth key) are reproducible bit for bit.
+// Sigma' = V V^T + dilation I with V = T M (T = J W, M = R(q) diag(s)); its
+// determinant comes from the Cauchy-Binet identity (sum of the squared 2x2
+// minors of V, plus the dilation terms), which is free of the cancellation of
+// a c - b^2.  Returns false when the tile rectangle is empty.
+__device__ __forceinline__ bool project_gaussian(const float ls[3], const float qin[4], const double td[3],
+                                                 const CamInfo &cam, const RenderConsts &rc, Proj &o)
 {
     const float *R = cam.R;
+    const float tx = __double2float_rn(td[0]), ty = __double2float_rn(td[1]), tz = __double2float_rn(td[2]);
     float qw = qin[0], qx = qin[1], qy = qin[2], qz = qin[3];
     float qn = FSQRT(FADD(FADD(FADD(FMUL(qw, qw), FMUL(qx, qx)), FMUL(qy, qy)), FMUL(qz, qz)));
     qw = FDIV(qw, qn); qx = FDIV(qx, qn); qy = FDIV(qy, qn); qz = FDIV(qz, qn);
@@ -146,16 +186,11 @@ __device__ __forceinline__ bool project_gaussian(const float m[3], const float l
     Q[2][1] = FMUL(2.f, FADD(FMUL(qy, qz), FMUL(qw, qx)));
     Q[2][2] = FSUB(1.f, FMUL(2.f, FADD(FMUL(qx, qx), FMUL(qy, qy))));
     float s[3] = {expf(ls[0]), expf(ls[1]), expf(ls[2])};
-    float M[3][3], S[3][3];
+    float M[3][3];
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) M[i][j] = FMUL(Q[i][j], s[j]);
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++)
-            S[i][j] = FADD(FADD(FMUL(M[i][0], M[j][0]), FMUL(M[i][1], M[j][1])), FMUL(M[i][2], M[j][2]));
 
     const float fx = cam.fx, fy = cam.fy;
     float limx = FMUL(rc.fov_clamp, FDIV((float)cam.width, FMUL(2.f, fx)));
@@ -177,12 +212,17 @@ __device__ __forceinline__ bool project_gaussian(const float m[3], const float l
     for (int r = 0; r < 2; r++)
 #pragma unroll
         for (int k = 0; k < 3; k++)
-            V[r][k] = FADD(FADD(FMUL(T[r][0], S[0][k]), FMUL(T[r][1], S[1][k])), FMUL(T[r][2], S[2][k]));
-    float s00 = FADD(FADD(FMUL(V[0][0], T[0][0]), FMUL(V[0][1], T[0][1])), FMUL(V[0][2], T[0][2]));
-    float s01 = FADD(FADD(FMUL(V[0][0], T[1][0]), FMUL(V[0][1], T[1][1])), FMUL(V[0][2], T[1][2]));
-    float s11 = FADD(FADD(FMUL(V[1][0], T[1][0]), FMUL(V[1][1], T[1][1])), FMUL(V[1][2], T[1][2]));
-    float a = FADD(s00, rc.dilation), b = s01, c = FADD(s11, rc.dilation);
-    float det = FSUB(FMUL(a, c), FMUL(b, b));
+            V[r][k] = FADD(FADD(FMUL(T[r][0], M[0][k]), FMUL(T[r][1], M[1][k])), FMUL(T[r][2], M[2][k]));
+    const float dil = rc.dilation;
+    float s00 = FADD(FADD(FMUL(V[0][0], V[0][0]), FMUL(V[0][1], V[0][1])), FMUL(V[0][2], V[0][2]));
+    float s01 = FADD(FADD(FMUL(V[0][0], V[1][0]), FMUL(V[0][1], V[1][1])), FMUL(V[0][2], V[1][2]));
+    float s11 = FADD(FADD(FMUL(V[1][0], V[1][0]), FMUL(V[1][1], V[1][1])), FMUL(V[1][2], V[1][2]));
+    float a = FADD(s00, dil), b = s01, c = FADD(s11, dil);
+    float m01 = FSUB(FMUL(V[0][0], V[1][1]), FMUL(V[0][1], V[1][0]));
+    float m02 = FSUB(FMUL(V[0][0], V[1][2]), FMUL(V[0][2], V[1][0]));
+    float m12 = FSUB(FMUL(V[0][1], V[1][2]), FMUL(V[0][2], V[1][1]));
+    float det = FADD(FADD(FADD(FADD(FMUL(m01, m01), FMUL(m02, m02)), FMUL(m12, m12)), FMUL(dil, FADD(s00, s11))),
+                     FMUL(dil, dil));
     if (!(det > 0.f)) return false;
     float mid = FMUL(0.5f, FADD(a, c));
     float disc = FSUB(FMUL(mid, mid), det);
@@ -190,8 +230,9 @@ __device__ __forceinline__ bool project_gaussian(const float m[3], const float l
     float lam = FADD(mid, FSQRT(disc));
     float ext = FMUL(3.f, FSQRT(lam));
     int radius = (int)ceilf(ext);
-    float u = FADD(FDIV(FMUL(fx, tx), tz), cam.cx);
-    float v = FADD(FDIV(FMUL(fy, ty), tz), cam.cy);
+    const double ud = __dadd_rn(__ddiv_rn(__dmul_rn((double)fx, td[0]), td[2]), (double)cam.cx);
+    const double vd = __dadd_rn(__ddiv_rn(__dmul_rn((double)fy, td[1]), td[2]), (double)cam.cy);
+    float u = __double2float_rn(ud), v = __double2float_rn(vd);
     float rr = (float)radius, ts = (float)kTile;
     int x0 = (int)floorf(FDIV(FSUB(u, rr), ts)), y0 = (int)floorf(FDIV(FSUB(v, rr), ts));
     int x1 = (int)floorf(FDIV(FADD(u, rr), ts)) + 1, y1 = (int)floorf(FDIV(FADD(v, rr), ts)) + 1;
@@ -199,7 +240,9 @@ __device__ __forceinline__ bool project_gaussian(const float m[3], const float l
     y0 = min(max(y0, 0), cam.tiles_y); y1 = min(max(y1, 0), cam.tiles_y);
     if (x1 <= x0 || y1 <= y0) return false;
     o.u = u; o.v = v;
-    o.A = FDIV(c, det); o.B = FDIV(-b, det); o.C = FDIV(a, det);
+    o.u_lo = __double2float_rn(__dsub_rn(ud, (double)u));
+    o.v_lo = __double2float_rn(__dsub_rn(vd, (double)v));
+    o.A = FDIV(c, det); o.k = FDIV(-b, c); o.D = FDIV(1.f, c);
     o.depth = tz;
     o.radius = radius;
     o.x0 = x0; o.y0 = y0; o.x1 = x1; o.y1 = y1;
@@ -209,8 +252,7 @@ __device__ __forceinline__ bool project_gaussian(const float m[3], const float l
 struct PreOut {
     uint32_t *rec_g, *tt, *dkey;
     uint16_t *rec_cam;
-    float4 *rd0, *rd1;
-    float *rd2;
+    float4 *rd0, *rd1, *rd2;
     uint2 *rect;
     uint8_t *clampm;
     uint32_t *cand_g;
@@ -232,7 +274,6 @@ struct GaussLoad {
 __device__ __forceinline__ void load_shape(const GaussPtrs &g, long long i, GaussLoad &L)
 {
     if (L.have_shape) return;
-    const long long n = g.n;
     L.ls[0] = g.log_scale[3 * i]; L.ls[1] = g.log_scale[3 * i + 1]; L.ls[2] = g.log_scale[3 * i + 2];
     const float4 q = *reinterpret_cast<const float4 *>(g.quat + 4 * i); // 16-byte aligned rows
     L.q[0] = q.x; L.q[1] = q.y; L.q[2] = q.z; L.q[3] = q.w;
@@ -286,12 +327,12 @@ __global__ void __launch_bounds__(256) gate_kernel(GaussPtrs g, PreOut o, CamTab
             const CamInfo &cam = ct.c[c];
             if (!lod_pass(m, lod[k], cam, rc)) continue;
             if (rc.cull_enable && cull_bit(o, c, i)) continue;
-            float tx, ty, tz;
-            camera_point(m, cam, tx, ty, tz);
-            if (!(tz > rc.znear)) continue;
+            float t[3], te[3];
+            camera_point(m, cam, t, te);
+            if (!(t[2] + te[2] > rc.znear)) continue; // the exact near test is the projection's
             if (smax < 0.f)
                 smax = expf(fmaxf(g.log_scale[3 * i], fmaxf(g.log_scale[3 * i + 1], g.log_scale[3 * i + 2])));
-            if (maybe_on_screen(tx, ty, tz, smax, cam, rc)) mask[k] |= 1ull << c;
+            if (maybe_on_screen(t, te, smax, cam, rc)) mask[k] |= 1ull << c;
         }
     }
     // order-preserving compaction: item (k, thread) precedes (k', thread') iff
@@ -344,7 +385,6 @@ __global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, 
     const unsigned bid = s_bid;
     const unsigned long long ncand = o.ctr->n_candidates;
     if ((unsigned long long)bid * 256 >= ncand) return;
-    const long long n = g.n;
     const unsigned long long j = (unsigned long long)bid * 256 + threadIdx.x;
     GaussLoad L;
     L.have_shape = false;
@@ -357,10 +397,11 @@ __global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, 
         load_shape(g, i, L);
         for (unsigned long long mm = cm; mm; mm &= mm - 1) {
             const int c = __ffsll((long long)mm) - 1;
-            float tx, ty, tz;
-            camera_point(L.m, ct.c[c], tx, ty, tz);
+            double td[3];
+            camera_point_d(L.m, ct.c[c], td);
+            if (!(__double2float_rn(td[2]) > rc.znear)) continue;
             Proj p;
-            if (project_gaussian(L.m, L.ls, L.q, tx, ty, tz, ct.c[c], rc, p)) act |= 1ull << c;
+            if (project_gaussian(L.ls, L.q, td, ct.c[c], rc, p)) act |= 1ull << c;
         }
     }
     const unsigned long long cnt = __popcll(act);
@@ -392,10 +433,10 @@ __global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, 
             break;
         }
         const CamInfo &cam = ct.c[c];
-        float tx, ty, tz;
-        camera_point(L.m, cam, tx, ty, tz);
+        double td[3];
+        camera_point_d(L.m, cam, td);
         Proj p;
-        project_gaussian(L.m, L.ls, L.q, tx, ty, tz, cam, rc, p); // same inputs: same (passing) result
+        project_gaussian(L.ls, L.q, td, cam, rc, p); // same inputs: same (passing) result
         const float dx = L.m[0] - cam.campos[0], dy = L.m[1] - cam.campos[1], dz = L.m[2] - cam.campos[2];
         const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
         float Y[16];
@@ -421,9 +462,9 @@ __global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, 
         }
         o.rec_g[r] = (uint32_t)i;
         o.rec_cam[r] = (uint16_t)c;
-        o.rd0[r] = make_float4(p.u, p.v, p.A, p.B);
-        o.rd1[r] = make_float4(p.C, op, col[0], col[1]);
-        o.rd2[r] = col[2];
+        o.rd0[r] = make_float4(p.u, p.v, p.A, p.k);
+        o.rd1[r] = make_float4(p.D, op, col[0], col[1]);
+        o.rd2[r] = make_float4(col[2], p.u_lo, p.v_lo, 0.f);
         o.rect[r] = make_uint2((uint32_t)p.x0 | ((uint32_t)p.y0 << 16), (uint32_t)p.x1 | ((uint32_t)p.y1 << 16));
         o.tt[r] = (uint32_t)((p.x1 - p.x0) * (p.y1 - p.y0));
         o.dkey[r] = __float_as_uint(p.depth);
@@ -530,7 +571,6 @@ struct BwdArgs {
 __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, CamTable ct, RenderConsts rc)
 {
     __shared__ float s_red[4];
-    const long long n = a.g.n;
     // one thread per Gaussian that has records: the thread of its first record
     const unsigned long long rh = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned long long nrec = a.ctr->n_records;
@@ -556,13 +596,11 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, CamTable
             Q[1][0] = 2.f * (x * y + w * z); Q[1][1] = 1.f - 2.f * (x * x + z * z); Q[1][2] = 2.f * (y * z - w * x);
             Q[2][0] = 2.f * (x * z - w * y); Q[2][1] = 2.f * (y * z + w * x); Q[2][2] = 1.f - 2.f * (x * x + y * y);
             const float s[3] = {expf(ls[0]), expf(ls[1]), expf(ls[2])};
-            float M[3][3], Sg[3][3];
+            float M[3][3];
             for (int p = 0; p < 3; p++)
                 for (int c = 0; c < 3; c++) M[p][c] = Q[p][c] * s[c];
-            for (int p = 0; p < 3; p++)
-                for (int c = 0; c < 3; c++) Sg[p][c] = M[p][0] * M[c][0] + M[p][1] * M[c][1] + M[p][2] * M[c][2];
             const float o = 1.f / (1.f + expf(-a.g.opacity_logit[i]));
-            float gSsum[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+            float gM[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}; // dL/dM, M = Q diag(s)
             float absacc = 0.f;
             for (unsigned long long r = r0; r < r1; r++) {
                 const CamInfo &cam = ct.c[a.rec_cam[r]];
@@ -571,8 +609,9 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, CamTable
                 const float grgb[3] = {rg[6], rg[7], rg[8]};
                 absacc += sqrtf(gu * gu + gv * gv);
                 const float *W = cam.R;
-                float t[3];
-                for (int k = 0; k < 3; k++) t[k] = W[3 * k] * m[0] + W[3 * k + 1] * m[1] + W[3 * k + 2] * m[2] + cam.t[k];
+                double td[3];
+                camera_point_d(m, cam, td); // the camera-space mean the forward projected
+                const float t[3] = {__double2float_rn(td[0]), __double2float_rn(td[1]), __double2float_rn(td[2])};
                 const float fx = cam.fx, fy = cam.fy;
                 const float limx = rc.fov_clamp * ((float)cam.width / (2.f * fx));
                 const float limy = rc.fov_clamp * ((float)cam.height / (2.f * fy));
@@ -584,33 +623,48 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, CamTable
                 float T[2][3];
                 for (int r2 = 0; r2 < 2; r2++)
                     for (int k = 0; k < 3; k++) T[r2][k] = J[r2][0] * W[k] + J[r2][1] * W[3 + k] + J[r2][2] * W[6 + k];
-                float S2[2][2];
+                // Sigma' = V V^T + dilation I, V = T M; determinant by Cauchy-Binet
+                float V[2][3];
                 for (int r2 = 0; r2 < 2; r2++)
-                    for (int c2 = 0; c2 < 2; c2++) {
-                        float acc = 0.f;
-                        for (int p = 0; p < 3; p++) {
-                            float tp = T[r2][0] * Sg[0][p] + T[r2][1] * Sg[1][p] + T[r2][2] * Sg[2][p];
-                            acc += tp * T[c2][p];
-                        }
-                        S2[r2][c2] = acc;
-                    }
-                const float aa = S2[0][0] + rc.dilation, bb = S2[0][1], cc = S2[1][1] + rc.dilation;
-                const float det = aa * cc - bb * bb, idet = 1.f / det, idet2 = idet * idet;
-                // conic (A, B, C) = (c, -b, a) / det
-                const float ga = gA * (-cc * cc * idet2) + gB * (bb * cc * idet2) + gC * (idet - aa * cc * idet2);
-                const float gb = gA * (2.f * bb * cc * idet2) + gB * (-idet - 2.f * bb * bb * idet2) + gC * (2.f * aa * bb * idet2);
-                const float gc = gA * (idet - aa * cc * idet2) + gB * (aa * bb * idet2) + gC * (-aa * aa * idet2);
-                const float G2[2][2] = {{ga, 0.5f * gb}, {0.5f * gb, gc}};
-                // dL/dSigma = T^T G2 T ; dL/dT = 2 G2 T Sigma
-                float GT[2][3];
-                for (int r2 = 0; r2 < 2; r2++)
-                    for (int k = 0; k < 3; k++) GT[r2][k] = G2[r2][0] * T[0][k] + G2[r2][1] * T[1][k];
+                    for (int k = 0; k < 3; k++) V[r2][k] = T[r2][0] * M[0][k] + T[r2][1] * M[1][k] + T[r2][2] * M[2][k];
+                const float s00 = V[0][0] * V[0][0] + V[0][1] * V[0][1] + V[0][2] * V[0][2];
+                const float s11 = V[1][0] * V[1][0] + V[1][1] * V[1][1] + V[1][2] * V[1][2];
+                const float m01 = V[0][0] * V[1][1] - V[0][1] * V[1][0];
+                const float m02 = V[0][0] * V[1][2] - V[0][2] * V[1][0];
+                const float m12 = V[0][1] * V[1][2] - V[0][2] * V[1][1];
+                const float det = m01 * m01 + m02 * m02 + m12 * m12 + rc.dilation * (s00 + s11 + rc.dilation);
+                const float idet = 1.f / det;
+                // conic C = (V V^T + d I)^-1 and dL/dV = -2 C G C V, G = dL/dC (symmetric).  C is applied
+                // through its adjugate, adj(V V^T + d I) = (P V)(P V)^T + d I with P the quarter turn
+                // (P v = (-v_y, v_x)), so (P V)^T v_k holds the 2x2 minors cross(v_i, v_k) of V: every
+                // product keeps its accuracy along both axes of a long thin footprint, where the
+                // entries of C and of dL/dSigma' in image axes would cancel.
+                const float mn[3][3] = {{0.f, m01, m02}, {-m01, 0.f, m12}, {-m02, -m12, 0.f}};
+                const float PV[2][3] = {{-V[1][0], -V[1][1], -V[1][2]}, {V[0][0], V[0][1], V[0][2]}};
+                const float G[2][2] = {{gA, 0.5f * gB}, {0.5f * gB, gC}};
+                float GW[2][3]; // G C v_k
+                for (int k = 0; k < 3; k++) {
+                    float w[2];
+                    for (int r2 = 0; r2 < 2; r2++)
+                        w[r2] = (PV[r2][0] * mn[0][k] + PV[r2][1] * mn[1][k] + PV[r2][2] * mn[2][k] +
+                                 rc.dilation * V[r2][k]) * idet;
+                    for (int r2 = 0; r2 < 2; r2++) GW[r2][k] = G[r2][0] * w[0] + G[r2][1] * w[1];
+                }
+                float gV[2][3];
+                for (int k = 0; k < 3; k++) {
+                    float pv[3];
+                    for (int i2 = 0; i2 < 3; i2++) pv[i2] = PV[0][i2] * GW[0][k] + PV[1][i2] * GW[1][k];
+                    for (int r2 = 0; r2 < 2; r2++)
+                        gV[r2][k] = -2.f * idet *
+                                    (PV[r2][0] * pv[0] + PV[r2][1] * pv[1] + PV[r2][2] * pv[2] + rc.dilation * GW[r2][k]);
+                }
+                // V = T M: dL/dM += T^T dL/dV, dL/dT = dL/dV M^T
                 for (int p = 0; p < 3; p++)
-                    for (int c2 = 0; c2 < 3; c2++) gSsum[p][c2] += T[0][p] * GT[0][c2] + T[1][p] * GT[1][c2];
+                    for (int c2 = 0; c2 < 3; c2++) gM[p][c2] += T[0][p] * gV[0][c2] + T[1][p] * gV[1][c2];
                 float gT[2][3];
                 for (int r2 = 0; r2 < 2; r2++)
                     for (int k = 0; k < 3; k++)
-                        gT[r2][k] = 2.f * (GT[r2][0] * Sg[0][k] + GT[r2][1] * Sg[1][k] + GT[r2][2] * Sg[2][k]);
+                        gT[r2][k] = gV[r2][0] * M[k][0] + gV[r2][1] * M[k][1] + gV[r2][2] * M[k][2];
                 float gJ[2][3];
                 for (int r2 = 0; r2 < 2; r2++)
                     for (int k = 0; k < 3; k++) gJ[r2][k] = gT[r2][0] * W[3 * k] + gT[r2][1] * W[3 * k + 1] + gT[r2][2] * W[3 * k + 2];
@@ -649,14 +703,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, CamTable
                 const float ddot = d[0] * gd[0] + d[1] * gd[1] + d[2] * gd[2];
                 for (int e = 0; e < 3; e++) gm[e] += (gd[e] - d[e] * ddot) * idn;
             }
-            // Sigma = M M^T with M = Q diag(s)
-            float gSs[3][3];
-            for (int p = 0; p < 3; p++)
-                for (int c2 = 0; c2 < 3; c2++) gSs[p][c2] = 0.5f * (gSsum[p][c2] + gSsum[c2][p]);
-            float gM[3][3];
-            for (int p = 0; p < 3; p++)
-                for (int c2 = 0; c2 < 3; c2++)
-                    gM[p][c2] = 2.f * (gSs[p][0] * M[0][c2] + gSs[p][1] * M[1][c2] + gSs[p][2] * M[2][c2]);
+            // M = Q diag(s)
             float gs[3] = {0.f, 0.f, 0.f}, gQ[3][3];
             for (int p = 0; p < 3; p++)
                 for (int c2 = 0; c2 < 3; c2++) { gs[c2] += gM[p][c2] * Q[p][c2]; gQ[p][c2] = gM[p][c2] * s[c2]; }

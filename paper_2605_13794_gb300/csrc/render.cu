@@ -20,9 +20,15 @@ constexpr int kQ = 4;              // pixels per thread
 
 // Thread t owns the quad (qx, qy) = (t % 8, t / 8): warp 0 covers pixel rows
 // 0-7 and warp 1 rows 8-15.  Pixel k of the quad is (2 qx + k % 2, 2 qy + k / 2).
+// Compositing works in tile-local pixel coordinates: pixel centres are exact
+// small floats, and each staged entry's mean is moved to the tile's origin
+// once, from its double-length form u + u_lo, so px - u keeps its full
+// precision however far the tile lies from the image origin.
 struct TileGeom {
     int cam, tx, ty;
-    int px0, py0;              // pixel of quad element 0
+    int px0, py0;              // pixel of quad element 0 (image coordinates)
+    float ox, oy;              // pixel origin of the tile
+    float lx0, ly0;            // centre of quad element 0, tile-local
     const CamInfo *ci;
 };
 
@@ -36,16 +42,31 @@ __device__ __forceinline__ TileGeom tile_geom(const CamTable &ct, int tile)
     t.ty = lt / t.ci->tiles_x;
     t.px0 = t.tx * kTile + 2 * (threadIdx.x & 7);
     t.py0 = t.ty * kTile + 2 * (threadIdx.x >> 3);
+    t.ox = (float)(t.tx * kTile);
+    t.oy = (float)(t.ty * kTile);
+    t.lx0 = (float)(2 * (threadIdx.x & 7)) + 0.5f;
+    t.ly0 = (float)(2 * (threadIdx.x >> 3)) + 0.5f;
     return t;
 }
 
 // ---- packed quad arithmetic (Blackwell FP32x2) ----------------------------------
 // A thread's quad is two rows of two pixels; each row pair is one float2, so
 // the exponent, alpha, transmittance and colour updates are packed FP32x2
-// operations.  The conic is pre-scaled so the exponent is in base 2:
-// G = exp(power) = 2^(log2(e) power).  Every kernel that takes skip decisions
-// (forward, backward, importance) evaluates these same functions.
-constexpr float kLog2e = 1.4426950408889634f;
+// operations.  The exponent is evaluated from the conic's form
+// power = -1/2 (A (dx + k dy)^2 + D dy^2), with A and D pre-scaled at staging so
+// it comes out in base 2: G = exp(power) = 2^(log2(e) power).  Every kernel
+// that takes skip decisions (forward, backward, importance) stages and
+// evaluates through these same functions.
+constexpr float kNegHalfLog2e = -0.72134752044448170f; // -log2(e) / 2
+constexpr float kFromScaled = -1.3862943611198906f;    // -2 ln 2 = 1 / kNegHalfLog2e
+
+// A staged entry: e0 = (u, v) tile-local, A and k; e1.x = D (A, D scaled to base 2)
+__device__ __forceinline__ float4 stage_e0(float4 r0, float4 r2, const TileGeom &tg)
+{
+    return make_float4(__fadd_rn(__fsub_rn(r0.x, tg.ox), r2.y), __fadd_rn(__fsub_rn(r0.y, tg.oy), r2.z),
+                       __fmul_rn(r0.z, kNegHalfLog2e), r0.w);
+}
+__device__ __forceinline__ float stage_D(float4 r1) { return __fmul_rn(r1.x, kNegHalfLog2e); }
 
 __device__ __forceinline__ float ex2_approx(float x)
 {
@@ -60,23 +81,23 @@ struct QuadPow {
     float2 r0, r1; // base-2 exponents of the two row pairs
 };
 
-// e0 = (u, v, A, B), C: conic of the entry; px2 = pixel-centre x of the pair,
-// pya, pyb = the two rows' centre y.
-__device__ __forceinline__ QuadPow quad_power(float4 e0, float C, float2 px2, float pya, float pyb)
+// e0 = staged entry (u, v, A, k), Ds = its scaled D; px2 = the quad's two
+// pixel-centre x, py2 = its two rows' centre y (tile-local).
+__device__ __forceinline__ QuadPow quad_power(float4 e0, float Ds, float2 px2, float2 py2)
 {
-    const float As = __fmul_rn(e0.z, -0.5f * kLog2e), Bs = __fmul_rn(e0.w, -kLog2e), Cs = __fmul_rn(C, -0.5f * kLog2e);
     const float2 dx = __fadd2_rn(px2, f2(-e0.x));
-    const float2 A2 = f2(As);
+    const float2 dy = __fadd2_rn(py2, f2(-e0.y));
+    const float2 kdy = __fmul2_rn(f2(e0.w), dy);
+    const float2 ddy = __fmul2_rn(__fmul2_rn(f2(Ds), dy), dy);
+    const float2 A2 = f2(e0.z);
     QuadPow q;
     {
-        const float dy = __fsub_rn(pya, e0.y);
-        const float bd = __fmul_rn(Bs, dy), cd = __fmul_rn(__fmul_rn(Cs, dy), dy);
-        q.r0 = __ffma2_rn(__ffma2_rn(A2, dx, f2(bd)), dx, f2(cd));
+        const float2 e = __fadd2_rn(dx, f2(kdy.x));
+        q.r0 = __ffma2_rn(A2, __fmul2_rn(e, e), f2(ddy.x));
     }
     {
-        const float dy = __fsub_rn(pyb, e0.y);
-        const float bd = __fmul_rn(Bs, dy), cd = __fmul_rn(__fmul_rn(Cs, dy), dy);
-        q.r1 = __ffma2_rn(__ffma2_rn(A2, dx, f2(bd)), dx, f2(cd));
+        const float2 e = __fadd2_rn(dx, f2(kdy.y));
+        q.r1 = __ffma2_rn(A2, __fmul2_rn(e, e), f2(ddy.y));
     }
     return q;
 }
@@ -112,7 +133,7 @@ __global__ void __launch_bounds__(kRT) render_fwd_kernel(const uint2 *__restrict
                                                          const uint32_t *__restrict__ vals,
                                                          const float4 *__restrict__ rd0,
                                                          const float4 *__restrict__ rd1,
-                                                         const float *__restrict__ rd2, CamTable ct, RenderConsts rc,
+                                                         const float4 *__restrict__ rd2, CamTable ct, RenderConsts rc,
                                                          float *__restrict__ rgb_out, float *__restrict__ T_out,
                                                          float *__restrict__ T_ws, uint32_t *__restrict__ n_contrib)
 {
@@ -124,9 +145,9 @@ __global__ void __launch_bounds__(kRT) render_fwd_kernel(const uint2 *__restrict
     const uint2 rg = ranges[blockIdx.x];
     const int start = (int)rg.x, end = (int)rg.y;
 
-    // pixel pair of row 0 (quad elements 0, 1) and row 1 (2, 3)
-    const float2 px2 = make_float2((float)tg.px0 + 0.5f, (float)tg.px0 + 1.5f);
-    const float pya = (float)tg.py0 + 0.5f, pyb = (float)tg.py0 + 1.5f;
+    // pixel pair of row 0 (quad elements 0, 1) and row 1 (2, 3), tile-local
+    const float2 px2 = make_float2(tg.lx0, tg.lx0 + 1.f);
+    const float2 py2 = make_float2(tg.ly0, tg.ly0 + 1.f);
     float2 T[2] = {f2(1.f), f2(1.f)}, Cr[2] = {f2(0.f), f2(0.f)}, Cg[2] = {f2(0.f), f2(0.f)},
            Cb[2] = {f2(0.f), f2(0.f)};
     uint32_t last[kQ] = {0, 0, 0, 0};
@@ -139,9 +160,10 @@ __global__ void __launch_bounds__(kRT) render_fwd_kernel(const uint2 *__restrict
         const int s = b + threadIdx.x;
         if (s < end) {
             const uint32_t r = vals[s];
-            s0[threadIdx.x] = rd0[r];
-            s1[threadIdx.x] = rd1[r];
-            s2[threadIdx.x] = rd2[r];
+            const float4 r1 = rd1[r], r2 = rd2[r];
+            s0[threadIdx.x] = stage_e0(rd0[r], r2, tg);
+            s1[threadIdx.x] = make_float4(stage_D(r1), r1.y, r1.z, r1.w);
+            s2[threadIdx.x] = r2.x;
         }
         __syncthreads();
         const int cnt = min(kRT, end - b);
@@ -149,7 +171,7 @@ __global__ void __launch_bounds__(kRT) render_fwd_kernel(const uint2 *__restrict
             const float4 p0 = s0[j], p1 = s1[j];
             const float cb = s2[j];
             const uint32_t pos = (uint32_t)(b - start + j + 1);
-            const QuadPow q = quad_power(p0, p1.x, px2, pya, pyb);
+            const QuadPow q = quad_power(p0, p1.x, px2, py2);
 #pragma unroll
             for (int row = 0; row < 2; row++) {
                 float2 G;
@@ -211,8 +233,7 @@ constexpr int kBwdBatch = 32;
 struct BwdRenderArgs {
     const uint2 *ranges;
     const uint32_t *vals;
-    const float4 *rd0, *rd1;
-    const float *rd2;
+    const float4 *rd0, *rd1, *rd2;
     const uint32_t *inst_off;
     const uint2 *rect;
     const float *T_final;
@@ -241,15 +262,15 @@ __global__ void __launch_bounds__(kRT) render_bwd_kernel(BwdRenderArgs a, CamTab
 
     float T[kQ], g0[kQ], g1[kQ], g2[kQ], tgb[kQ], S0[kQ], S1[kQ], S2[kQ], pxf[kQ], pyf[kQ];
     int nc[kQ];
-    const float2 px2 = make_float2((float)tg.px0 + 0.5f, (float)tg.px0 + 1.5f);
-    const float pya = (float)tg.py0 + 0.5f, pyb = (float)tg.py0 + 1.5f;
+    const float2 px2 = make_float2(tg.lx0, tg.lx0 + 1.f);
+    const float2 py2 = make_float2(tg.ly0, tg.ly0 + 1.f);
     int mymax = 0;
     const long long np = (long long)cam.width * cam.height;
     const float *gimg = a.dL_drgb + 3 * cam.pix_base;
 #pragma unroll
     for (int k = 0; k < kQ; k++) {
         const int px = tg.px0 + (k & 1), py = tg.py0 + (k >> 1);
-        pxf[k] = (float)px + 0.5f; pyf[k] = (float)py + 0.5f;
+        pxf[k] = tg.lx0 + (float)(k & 1); pyf[k] = tg.ly0 + (float)(k >> 1);
         T[k] = 1.f; g0[k] = g1[k] = g2[k] = 0.f; nc[k] = 0;
         S0[k] = S1[k] = S2[k] = 0.f;
         if (px < cam.width && py < cam.height) {
@@ -278,9 +299,10 @@ __global__ void __launch_bounds__(kRT) render_bwd_kernel(BwdRenderArgs a, CamTab
         const int cnt = hi - lo;
         if (threadIdx.x < cnt) {
             const uint32_t r = a.vals[lo + threadIdx.x];
-            s0[threadIdx.x] = a.rd0[r];
-            s1[threadIdx.x] = a.rd1[r];
-            s2[threadIdx.x] = a.rd2[r];
+            const float4 r1 = a.rd1[r], r2 = a.rd2[r];
+            s0[threadIdx.x] = stage_e0(a.rd0[r], r2, tg);
+            s1[threadIdx.x] = make_float4(stage_D(r1), r1.y, r1.z, r1.w);
+            s2[threadIdx.x] = r2.x;
             s_slot[threadIdx.x] = slot_of(a.inst_off, a.rect, r, tg.tx, tg.ty);
         }
         __syncthreads();
@@ -289,7 +311,8 @@ __global__ void __launch_bounds__(kRT) render_bwd_kernel(BwdRenderArgs a, CamTab
             const float4 p0 = s0[jj], p1 = s1[jj];
             const float cb = s2[jj];
             // the forward's own exponent and alpha (same functions, same bits)
-            const QuadPow qp = quad_power(p0, p1.x, px2, pya, pyb);
+            const QuadPow qp = quad_power(p0, p1.x, px2, py2);
+            const float Au = p0.z * kFromScaled, Du = p1.x * kFromScaled; // the conic's A and D
             float2 Gr[2], alr[2];
             alr[0] = pair_alpha(qp.r0, p1.y, rc.alpha_max, Gr[0]);
             alr[1] = pair_alpha(qp.r1, p1.y, rc.alpha_max, Gr[1]);
@@ -320,8 +343,10 @@ __global__ void __launch_bounds__(kRT) render_bwd_kernel(BwdRenderArgs a, CamTab
                 if (og < rc.alpha_max) {
                     v[5] = fmaf(G, dalpha, v[5]);
                     const float dpow = G * p1.y * dalpha;
-                    v[0] = fmaf(dpow, p0.z * dx + p0.w * dy, v[0]);
-                    v[1] = fmaf(dpow, p1.x * dy + p0.w * dx, v[1]);
+                    // d power / du = A dx + B dy = A e, d power / dv = B dx + C dy = k A e + D dy
+                    const float Ae = Au * fmaf(p0.w, dy, dx);
+                    v[0] = fmaf(dpow, Ae, v[0]);
+                    v[1] = fmaf(dpow, fmaf(p0.w, Ae, Du * dy), v[1]);
                     v[2] = fmaf(-0.5f * dpow, dx * dx, v[2]);
                     v[3] = fmaf(-dpow, dx * dy, v[3]);
                     v[4] = fmaf(-0.5f * dpow, dy * dy, v[4]);
@@ -362,7 +387,7 @@ cudaError_t launch_render_bwd(gs_workspace *ws, cudaStream_t st, const float *dL
 struct ImpArgs {
     const uint2 *ranges;
     const uint32_t *vals;
-    const float4 *rd0, *rd1;
+    const float4 *rd0, *rd1, *rd2;
     const uint32_t *inst_off;
     const uint2 *rect;
     float *slots; // [I][2]: alpha-weight (float), composited pixels (uint32 bits)
@@ -380,8 +405,8 @@ __global__ void __launch_bounds__(kRT) importance_raster_kernel(ImpArgs a, CamTa
     const uint2 rg = a.ranges[blockIdx.x];
     const int start = (int)rg.x, end = (int)rg.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float2 px2 = make_float2((float)tg.px0 + 0.5f, (float)tg.px0 + 1.5f);
-    const float pya = (float)tg.py0 + 0.5f, pyb = (float)tg.py0 + 1.5f;
+    const float2 px2 = make_float2(tg.lx0, tg.lx0 + 1.f);
+    const float2 py2 = make_float2(tg.ly0, tg.ly0 + 1.f);
     float2 T[2] = {f2(1.f), f2(1.f)};
     bool dn[kQ];
 #pragma unroll
@@ -393,16 +418,16 @@ __global__ void __launch_bounds__(kRT) importance_raster_kernel(ImpArgs a, CamTa
         const int cnt = min(kRT, end - b);
         if (threadIdx.x < cnt) {
             const uint32_t r = a.vals[b + threadIdx.x];
-            s0[threadIdx.x] = a.rd0[r];
             const float4 p1 = a.rd1[r];
-            s1[threadIdx.x] = make_float2(p1.x, p1.y);
+            s0[threadIdx.x] = stage_e0(a.rd0[r], a.rd2[r], tg);
+            s1[threadIdx.x] = make_float2(stage_D(p1), p1.y);
             s_slot[threadIdx.x] = slot_of(a.inst_off, a.rect, r, tg.tx, tg.ty);
         }
         __syncthreads();
         for (int j = 0; j < cnt; j++) {
             const float4 p0 = s0[j];
             const float2 p1 = s1[j];
-            const QuadPow q = quad_power(p0, p1.x, px2, pya, pyb);
+            const QuadPow q = quad_power(p0, p1.x, px2, py2);
             float wv = 0.f;
             uint32_t av = 0;
 #pragma unroll
@@ -446,7 +471,7 @@ cudaError_t launch_importance_raster(gs_workspace *ws, cudaStream_t st)
 {
     if (ws->cams.total_tiles == 0) return cudaSuccess;
     ImpArgs a;
-    a.ranges = ws->ranges; a.vals = ws->tval[ws->tile_buf]; a.rd0 = ws->rd0; a.rd1 = ws->rd1;
+    a.ranges = ws->ranges; a.vals = ws->tval[ws->tile_buf]; a.rd0 = ws->rd0; a.rd1 = ws->rd1; a.rd2 = ws->rd2;
     a.inst_off = ws->inst_off; a.rect = ws->rect; a.slots = ws->slots;
     importance_raster_kernel<<<ws->cams.total_tiles, kRT, 0, st>>>(a, ws->cams, ws->rc);
     note_launch();

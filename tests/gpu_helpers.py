@@ -56,7 +56,7 @@ class GpuRun:
         self.tt = self.ws.read_buffer(B.GS_BUF_REC_TILES, np.uint32, n)
         self.rd0 = self.ws.read_buffer(B.GS_BUF_REC_XY_CONIC, np.float32, n, 4)
         self.rd1 = self.ws.read_buffer(B.GS_BUF_REC_C_OPAC_RG, np.float32, n, 4)
-        self.rd2 = self.ws.read_buffer(B.GS_BUF_REC_B, np.float32, n)
+        self.rd2 = self.ws.read_buffer(B.GS_BUF_REC_B_LO, np.float32, n, 4)
         ntiles = sum(B.tiles_of(cm) for cm in cams)
         self.ranges = self.ws.read_buffer(B.GS_BUF_TILE_RANGES, np.uint32, ntiles, 2)
         self.sorted_vals = self.ws.read_buffer(B.GS_BUF_SORTED_VALUES, np.uint32, self.counts["n_instances"])
@@ -124,3 +124,57 @@ def assert_grad_close(name, g, ref, rtol=1e-3, big=1e-2):
     sel = np.abs(ref) >= big * m
     rel = err[sel] / np.abs(ref[sel])
     assert rel.max() <= rtol, f"{name}: elementwise rel err {rel.max():.3e} (index {np.nonzero(sel)[0][rel.argmax()]})"
+
+
+def assert_param_grad_close(name, g, ref, rtol=1e-3, big=1e-2):
+    """Parameter-gradient parity rule, per Gaussian: with e_i = |g_i - ref_i|
+    and r_i = |ref_i| the Euclidean norms of Gaussian i's gradient for this
+    parameter (its row: 3 for the mean, 48 for the SH coefficients, ...),
+    max e_i <= rtol * max r_i, and e_i <= rtol * r_i wherever r_i >= big * max r_i.
+    A row is compared as a vector because its coordinates are tied to an
+    arbitrary frame (world axes for the mean): a coordinate can be small only
+    because the gradient points along another axis."""
+    g = np.asarray(g, np.float64)
+    ref = np.asarray(ref, np.float64)
+    n = ref.shape[0]
+    e = np.linalg.norm((g - ref).reshape(n, -1), axis=1)
+    r = np.linalg.norm(ref.reshape(n, -1), axis=1)
+    m = r.max() if n else 0.0
+    if m == 0:
+        assert e.max(initial=0.0) == 0, name
+        return
+    assert e.max() <= rtol * m, f"{name}: max err {e.max():.3e} > {rtol} * {m:.3e}"
+    sel = r >= big * m
+    rel = e[sel] / r[sel]
+    assert rel.max() <= rtol, f"{name}: per-Gaussian rel err {rel.max():.3e} (Gaussian {np.nonzero(sel)[0][rel.argmax()]})"
+
+
+def record_mean(rd0, rd2):
+    """Projected mean of GPU records: the float pair u + u_lo, in double."""
+    return rd0[:, :2].astype(np.float64) + rd2[:, 1:3].astype(np.float64)
+
+
+def footprint_power_err(rd0, rd1, rd2, conic, uv):
+    """Largest error of the GPU records' exponent -1/2 (A (dx + k dy)^2 + D dy^2)
+    on the 1-sigma and 3-sigma ellipses of the exact conic (conic rows A, B, C,
+    exact mean uv), where the exact exponent is -1/2 and -9/2."""
+    A, B, C = conic[:, 0], conic[:, 1], conic[:, 2]
+    det = A * C - B * B
+    cov = np.stack([C / det, -B / det, A / det], 1)
+    l00 = np.sqrt(cov[:, 0])
+    l10 = cov[:, 1] / l00
+    l11 = np.sqrt(np.maximum(cov[:, 2] - l10 ** 2, 0.0))
+    mg = record_mean(rd0, rd2)
+    gA, gk, gD = (rd0[:, 2:3].astype(np.float64), rd0[:, 3:4].astype(np.float64), rd1[:, 0:1].astype(np.float64))
+    th = np.linspace(0.0, 2.0 * np.pi, 16, endpoint=False)[None]
+    err = np.zeros(len(A))
+    for r in (1.0, 3.0):
+        dx = l00[:, None] * r * np.cos(th)
+        dy = l10[:, None] * r * np.cos(th) + l11[:, None] * r * np.sin(th)
+        ddx = uv[:, 0:1] + dx - mg[:, 0:1]
+        ddy = uv[:, 1:2] + dy - mg[:, 1:2]
+        e = ddx + gk * ddy
+        pg = -0.5 * (gA * e * e + gD * ddy * ddy)
+        err = np.maximum(err, np.abs(pg + 0.5 * r * r).max(1))
+    return err
+

@@ -180,6 +180,42 @@ def test_two_gaussians_by_hand(oracle_mod):
     assert list(lst[ts[0]:ts[1]]) == [1, 0]
 
 
+def _pixel_case(oracle_mod, frags):
+    """Composites pixel (0, 0) over explicit fragments (offset d from the pixel
+    centre along x, opacity) with a unit isotropic conic: power = -d^2 / 2."""
+    n = len(frags)
+    proj = dict(uv=np.array([[0.5 + d, 0.5] for d, _ in frags]), conic=np.tile([1.0, 0.0, 1.0], (n, 1)),
+                opacity=np.array([o for _, o in frags]), rgb=np.full((n, 3), 0.5))
+    return oracle_mod.render_pixels(proj, [[0, 0]], [list(range(n))], oracle_mod.Params())
+
+
+def _offset_for(alpha, o):
+    return math.sqrt(-2.0 * math.log(alpha / o))
+
+
+def test_threshold_flags(oracle_mod):
+    # a fragment within rounding of a threshold flags its pixel; one a percent away does not
+    O, P = oracle_mod, oracle_mod.Params()
+    # the thresholds as the renderer holds them: FP32
+    amin, amax, tmin = (float(np.float32(x)) for x in (P.alpha_min, P.alpha_max, P.T_min))
+    near = _pixel_case(O, [(_offset_for(amin * (1 + 1e-7), 0.5), 0.5)])
+    assert near["flags"][0] & O.PIX_ALPHA_MIN and near["n_contrib"][0] == 1
+    far = _pixel_case(O, [(_offset_for(amin * 1.01, 0.5), 0.5)])
+    assert far["flags"][0] == 0
+    below = _pixel_case(O, [(_offset_for(amin * (1 - 1e-7), 0.5), 0.5)])
+    assert below["flags"][0] & O.PIX_ALPHA_MIN and below["n_contrib"][0] == 0
+    assert _pixel_case(O, [(0.0, amax * (1 - 1e-7))])["flags"][0] & O.PIX_ALPHA_MAX
+    assert _pixel_case(O, [(0.0, amax * 0.98)])["flags"][0] == 0
+    # T_min: 1 - 0.99 leaves T = 0.01; the second fragment lands T(1 - alpha) next to T_min
+    a2 = 1.0 - tmin * (1 + 1e-7) / (1.0 - amax)
+    t_near = _pixel_case(O, [(0.0, 0.999), (0.0, a2)])
+    assert t_near["flags"][0] & O.PIX_T_MIN and t_near["n_contrib"][0] == 2
+    t_far = _pixel_case(O, [(0.0, 0.999), (0.0, 0.9)])
+    assert t_far["flags"][0] == 0
+    # flags never change what is composited
+    np.testing.assert_allclose(near["T"][0], 1.0 - amin * (1 + 1e-7), rtol=1e-12)
+
+
 def test_equal_depth_ties_by_index(oracle_mod):
     cam = synth.plain_camera(16, 16, 300.0)
     P = oracle_mod.Params()
