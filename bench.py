@@ -57,7 +57,7 @@ LRS = dict(mean=1.6e-4 * 100.0, log_scale=5e-3, quat=1e-3, opacity_logit=5e-2, s
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gsblitz", choices=["gsblitz", "reference"])
     ap.add_argument("--n", type=int, default=N_GAUSS, help="Gaussians (default: the 5M workload)")
@@ -68,29 +68,48 @@ def parse():
 # ---- clocks ---------------------------------------------------------------------
 
 class ClockSampler:
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-              "clocks_event_reasons.sw_power_cap")
+    """nvidia-smi sampling of SM clocks and throttle reasons at 50 ms.  Only
+    samples whose timestamps fall inside the marked load windows count."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device_uuid: str | None):
         self.uuid = device_uuid
         self.proc = None
         self.path = None
+        self.windows = []
 
     def start(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
-        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50"]
         if self.uuid:
             cmd += ["-i", self.uuid]
         try:
             self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        # the timed region starts only once sampling runs
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+            time.sleep(0.02)
+
+    def mark(self, t0: float, t1: float):
+        self.windows.append((t0, t1))
+
+    @staticmethod
+    def _epoch(stamp: str):
+        try:
+            base, _, frac = stamp.strip().partition(".")
+            return time.mktime(time.strptime(base, "%Y/%m/%d %H:%M:%S")) + (float("0." + frac) if frac else 0.0)
+        except ValueError:
+            return None
 
     def stop(self) -> dict:
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -98,12 +117,16 @@ class ClockSampler:
             self.proc.kill()
         rows = [r.split(", ") for r in open(self.path).read().strip().splitlines() if r.strip()]
         os.unlink(self.path)
-        sm = [float(r[0]) for r in rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
+        rows = [r for r in rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        inside = [r for r in rows if (t := self._epoch(r[0])) is not None and
+                  any(a - 0.05 <= t <= b + 0.05 for a, b in self.windows)]
+        use = inside if inside else rows
+        sm = [float(r[1]) for r in use]
+        mx = [float(r[2]) for r in use if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows if len(r) >= 8 for k in range(4) if r[4 + k].strip() == "Active"})
+        reasons = sorted({names[k] for r in use for k in range(4) if r[5 + k].strip() == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(sm)}
+                "reasons": reasons, "samples": len(sm), "in_timed_window": bool(inside)}
 
 
 # ---- workload ---------------------------------------------------------------------
@@ -382,13 +405,14 @@ def main():
     sampler.start()
     launches0 = B.kernel_launches()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0 = time.time()
     start.record(stream)
     for k in range(args.steps):
         step.run(evs[k])
     end.record(stream)
     torch.cuda.synchronize()
+    sampler.mark(w0, time.time())
     launches = B.kernel_launches() - launches0
-    clocks = sampler.stop()
     barrier(world)
     step.ws.sync_status()
     ms = start.elapsed_time(end) / args.steps
@@ -406,6 +430,7 @@ def main():
     barrier(world)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0 = time.time()
     e0.record(stream)
     for _ in range(args.steps):
         step.target.view(-1).copy_(tgt_host.view(-1), non_blocking=True)
@@ -415,10 +440,19 @@ def main():
         cull_host.copy_(step.cull, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
+    sampler.mark(w0, time.time())
+    clocks = sampler.stop()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
 
     P = cam.width * cam.height
     value = world * P / (ms * 1e-3) / 1e6
+    # the render's forward and backward alone (gate and projection, sorts,
+    # compositing, its adjoint and the projection adjoint), without the loss,
+    # Adam and the importance sweep
+    fb_ms = max_over_ranks(sum(stage_ms[k] for k in ("preprocess", "bin_sort", "render_fwd", "render_bwd")), world)
+    fwd_bwd = {"ms": fb_ms, "mpix_per_s": world * P / (fb_ms * 1e-3) / 1e6,
+               "mgaussian_per_s": world * g.n / (fb_ms * 1e-3) / 1e6,
+               "stages": ["preprocess", "bin_sort", "render_fwd", "render_bwd"]}
     gauss = world * g.n / (ms * 1e-3) / 1e6
     counts = step.ws.counts()
     peaks = measured_peaks()
@@ -441,6 +475,7 @@ def main():
                        "lod": True, "cull": True, "importance_pass": True, "optimizer": "adam",
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
             "mgaussian_per_s": gauss,
+            "fwd_bwd": fwd_bwd,
             "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
             "counts": {k: counts[k] for k in ("n_records", "n_instances", "n_visible")},
             "roofline": roof,
