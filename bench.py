@@ -319,15 +319,25 @@ def cpu_baseline(g, cam, target):
 
 # ---- main -------------------------------------------------------------------------------
 
-def dist_setup(args):
+def dist_backend():
+    """NCCL between GPUs; gloo where there is no GPU (the CPU tests of the
+    multi-rank path)."""
+    import torch
+    return "nccl" if torch.cuda.is_available() else "gloo"
+
+
+def dist_setup(args=None):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if dist_backend() == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
     return world, rank, local
 
 
@@ -338,13 +348,21 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """The largest of the ranks' x (each rank's time for the same K steps)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], device="cuda", dtype=torch.float64)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_rate(units_per_rank, ms_max, world):
+    """Whole-job throughput of weak-scaled replicas: every rank processes
+    units_per_rank per step; the job's step time is the slowest rank's."""
+    return world * units_per_rank / (ms_max * 1e-3)
 
 
 def run_reference(args, world, rank):
@@ -445,15 +463,15 @@ def main():
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
 
     P = cam.width * cam.height
-    value = world * P / (ms * 1e-3) / 1e6
+    value = job_rate(P, ms, world) / 1e6
     # the render's forward and backward alone (gate and projection, sorts,
     # compositing, its adjoint and the projection adjoint), without the loss,
     # Adam and the importance sweep
     fb_ms = max_over_ranks(sum(stage_ms[k] for k in ("preprocess", "bin_sort", "render_fwd", "render_bwd")), world)
-    fwd_bwd = {"ms": fb_ms, "mpix_per_s": world * P / (fb_ms * 1e-3) / 1e6,
-               "mgaussian_per_s": world * g.n / (fb_ms * 1e-3) / 1e6,
+    fwd_bwd = {"ms": fb_ms, "mpix_per_s": job_rate(P, fb_ms, world) / 1e6,
+               "mgaussian_per_s": job_rate(g.n, fb_ms, world) / 1e6,
                "stages": ["preprocess", "bin_sort", "render_fwd", "render_bwd"]}
-    gauss = world * g.n / (ms * 1e-3) / 1e6
+    gauss = job_rate(g.n, ms, world) / 1e6
     counts = step.ws.counts()
     peaks = measured_peaks()
     dom = max(stage_ms, key=stage_ms.get)
@@ -479,7 +497,7 @@ def main():
             "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
             "counts": {k: counts[k] for k in ("n_records", "n_instances", "n_visible")},
             "roofline": roof,
-            "e2e": {"value": world * P / (e2e_ms * 1e-3) / 1e6, "unit": "Mpix/s", "ms_per_step": e2e_ms,
+            "e2e": {"value": job_rate(P, e2e_ms, world) / 1e6, "unit": "Mpix/s", "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clocks}
