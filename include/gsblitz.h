@@ -110,7 +110,8 @@ typedef struct {
 
 /* Render parameters; gs_default_params fills the standard values. */
 typedef struct {
-    int32_t tile_size;   /* must be GS_TILE */
+    int32_t tile_w;      /* tile width in pixels; tile_w x tile_h is one of 16x16 (GS_TILE, the */
+    int32_t tile_h;      /* 3DGS tiling), 32x8, 8x32, 32x16 */
     int32_t lod_enable;  /* distance LOD gate of Eq. 1-2 */
     int32_t lod_Lmax;    /* L_max(t) of Eq. 1 */
     int32_t cull_enable; /* per-view Cull column of Eq. 3 */
@@ -183,9 +184,26 @@ int64_t gs_workspace_bytes(const gs_capacity *cap);
  * cameras (host array, <= GS_MAX_CAMERAS).  cull: device bit array
  * [n_cams][ceil(n/32)], bit i%32 of word i/32 set = Gaussian i culled in that
  * view (Eq. 3); may be NULL when params->cull_enable == 0.  The Gaussian
- * arrays must stay unchanged until gs_render_bwd of the same step. */
+ * arrays must stay unchanged until gs_render_bwd of the same step.
+ * Equivalent to gs_upload_cameras followed by gs_preprocess_uploaded. */
 int gs_preprocess(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams, int32_t n_cams,
                   const uint32_t *cull, const gs_render_params *params, gs_stream stream);
+
+/* The two halves of gs_preprocess, for CUDA graphs.  gs_upload_cameras
+ * validates the cameras (host array), lays out their tiles (params->tile_w,
+ * tile_h) and pixels, and copies the table to the workspace's device copy on
+ * the stream; it must not be called while the stream is being captured
+ * (GS_ERR_INVALID_ARG).  Every later kernel reads the cameras from that device
+ * copy, so a graph that captured gs_preprocess_uploaded and the calls after
+ * it renders whatever cameras were uploaded before its launch, provided they
+ * have the widths and heights (hence the tiles and pixels) of the cameras
+ * uploaded when it was captured.  gs_preprocess_uploaded takes the render
+ * parameters of this pass; their tile shape and fov_clamp must be those of
+ * the upload. */
+int gs_upload_cameras(gs_workspace *ws, const gs_camera *cams, int32_t n_cams, const gs_render_params *params,
+                      gs_stream stream);
+int gs_preprocess_uploaded(gs_workspace *ws, const gs_gaussians *g, const uint32_t *cull,
+                           const gs_render_params *params, gs_stream stream);
 
 /* Tile keys, device radix sort by (camera, tile, depth, record), tile ranges. */
 int gs_bin_sort(gs_workspace *ws, gs_stream stream);
@@ -220,7 +238,9 @@ int gs_render_bwd_compact(gs_workspace *ws, const gs_gaussians *g, const float *
  * and second moments in the layout of g; lr: learning rates of mean,
  * log-scale, quat, opacity and SH.  One streaming pass reads and writes the
  * parameters and both moments (24 bytes per parameter) and never a dense
- * gradient array. */
+ * gradient array.  step >= 1 is the step number (and sets the workspace's
+ * device step counter); step == 0 takes one past the device counter and
+ * advances it, so a captured optimizer step counts on every graph replay. */
 int gs_adam_step_compact(gs_workspace *ws, const gs_gaussians *g, const gs_gaussian_grads *m,
                          const gs_gaussian_grads *v, const float lr[5], float beta1, float beta2, float eps,
                          int32_t step, gs_stream stream);

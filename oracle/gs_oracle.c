@@ -55,7 +55,7 @@ typedef struct {
 } or_camera;
 
 typedef struct {
-    int32_t tile;
+    int32_t tile_w, tile_h; /* tile size in pixels (16 x 16 in 3DGS) */
     int32_t lod_enable, lod_Lmax, cull_enable;
     double bg[3];
     double alpha_min, alpha_max, T_min;
@@ -417,11 +417,11 @@ int or_render(const or_camera *cam, const or_params *P, int64_t n, const double 
               int32_t *gcount, const double *ldl32, const double *uv32)
 {
     (void)n;
-    const int W = cam->width, H = cam->height, ts = P->tile;
-    const int tiles_x = (W + ts - 1) / ts;
+    const int W = cam->width, H = cam->height, tw = P->tile_w, th = P->tile_h;
+    const int tiles_x = (W + tw - 1) / tw;
     for (int py = 0; py < H; py++)
         for (int px = 0; px < W; px++) {
-            int64_t t = (int64_t)(py / ts) * tiles_x + px / ts;
+            int64_t t = (int64_t)(py / th) * tiles_x + px / tw;
             pix_t o;
             composite_pixel(P, px + 0.5, py + 0.5, list + tile_start[t], tile_start[t + 1] - tile_start[t],
                             uv, conic, opacity, rgb, &o, w, a, gcount, ldl32, uv32);
@@ -494,14 +494,14 @@ int or_render_bwd(const or_camera *cam, const or_params *P, int64_t n, const dou
                   double *dL_drgb)
 {
     (void)n;
-    const int W = cam->width, H = cam->height, ts = P->tile;
-    const int tiles_x = (W + ts - 1) / ts;
+    const int W = cam->width, H = cam->height, tw = P->tile_w, th = P->tile_h;
+    const int tiles_x = (W + tw - 1) / tw;
     int64_t cap = 0;
     int32_t *frag = NULL;
     double *fa = NULL, *fT = NULL, *fG = NULL, *fog = NULL;
     for (int py = 0; py < H; py++)
         for (int px = 0; px < W; px++) {
-            int64_t t = (int64_t)(py / ts) * tiles_x + px / ts;
+            int64_t t = (int64_t)(py / th) * tiles_x + px / tw;
             const int32_t *ids = list + tile_start[t];
             int64_t len = tile_start[t + 1] - tile_start[t];
             if (len > cap) {

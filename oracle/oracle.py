@@ -58,7 +58,7 @@ class ORCamera(ctypes.Structure):
 
 
 class ORParams(ctypes.Structure):
-    _fields_ = [("tile", ctypes.c_int32), ("lod_enable", ctypes.c_int32), ("lod_Lmax", ctypes.c_int32),
+    _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("lod_enable", ctypes.c_int32), ("lod_Lmax", ctypes.c_int32),
                 ("cull_enable", ctypes.c_int32), ("bg", ctypes.c_double * 3),
                 ("alpha_min", ctypes.c_double), ("alpha_max", ctypes.c_double), ("T_min", ctypes.c_double),
                 ("dilation", ctypes.c_double), ("znear", ctypes.c_double), ("fov_clamp", ctypes.c_double),
@@ -97,7 +97,8 @@ def _p(a):
 class Params:
     """Render parameters (values of the standard 3DGS renderer unless noted)."""
 
-    tile: int = 16
+    tile_w: int = 16
+    tile_h: int = 16
     bg: tuple = (0.0, 0.0, 0.0)
     alpha_min: float = 1.0 / 255.0
     alpha_max: float = 0.99
@@ -119,7 +120,7 @@ class Params:
         # The thresholds are FP32 constants on the GPU; the oracle compares
         # against the same FP32 values so that the two definitions agree.
         f = lambda x: float(np.float32(x))
-        return ORParams(self.tile, int(self.lod_enable), self.lod_Lmax, int(self.cull_enable),
+        return ORParams(self.tile_w, self.tile_h, int(self.lod_enable), self.lod_Lmax, int(self.cull_enable),
                         (ctypes.c_double * 3)(*[f(b) for b in self.bg]), f(self.alpha_min), f(self.alpha_max),
                         f(self.T_min), f(self.dilation), f(self.znear), f(self.fov_clamp), f(self.lod_d0),
                         f(self.lod_f), self.tie_band, self.comp_band)
@@ -171,7 +172,7 @@ def project(g64: dict, cam, params: Params, cull=None) -> dict:
 
 
 def tiles_of(cam, params: Params):
-    return (cam.width + params.tile - 1) // params.tile, (cam.height + params.tile - 1) // params.tile
+    return (cam.width + params.tile_w - 1) // params.tile_w, (cam.height + params.tile_h - 1) // params.tile_h
 
 
 def bin_tiles(proj: dict, cam, params: Params):

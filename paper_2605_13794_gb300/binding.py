@@ -27,7 +27,7 @@ EXPORTS = ("gs_default_params", "gs_last_error", "gs_workspace_create", "gs_work
            "gs_preprocess", "gs_bin_sort", "gs_render_fwd", "gs_render_bwd", "gs_importance", "gs_photometric_loss",
            "gs_adam_step", "gs_sync_status", "gs_workspace_counts", "gs_clear_error", "gs_workspace_buffer",
            "gs_kernel_launches", "gs_render_bwd_adam", "gs_render_bwd_compact", "gs_adam_step_compact",
-           "gs_visible_set_static")
+           "gs_visible_set_static", "gs_upload_cameras", "gs_preprocess_uploaded")
 
 
 class GSError(RuntimeError):
@@ -60,7 +60,7 @@ class GSCamera(ctypes.Structure):
 
 
 class GSRenderParams(ctypes.Structure):
-    _fields_ = [("tile_size", ctypes.c_int32), ("lod_enable", ctypes.c_int32), ("lod_Lmax", ctypes.c_int32),
+    _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("lod_enable", ctypes.c_int32), ("lod_Lmax", ctypes.c_int32),
                 ("cull_enable", ctypes.c_int32), ("bg", ctypes.c_float * 3), ("alpha_min", ctypes.c_float),
                 ("alpha_max", ctypes.c_float), ("T_min", ctypes.c_float), ("dilation", ctypes.c_float),
                 ("znear", ctypes.c_float), ("fov_clamp", ctypes.c_float), ("lod_d0", ctypes.c_float),
@@ -100,6 +100,8 @@ def lib() -> ctypes.CDLL:
         L.gs_kernel_launches.argtypes = []
         L.gs_kernel_launches.restype = i64
         L.gs_preprocess.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+        L.gs_upload_cameras.argtypes = [vp, vp, i32, vp, vp]
+        L.gs_preprocess_uploaded.argtypes = [vp, vp, vp, vp, vp]
         L.gs_bin_sort.argtypes = [vp, vp]
         L.gs_render_fwd.argtypes = [vp, vp, vp, vp]
         L.gs_render_bwd.argtypes = [vp, vp, vp, vp, i32, vp, ctypes.c_float, vp, vp]
@@ -144,6 +146,8 @@ class RenderParams:
     """Mirror of gs_render_params; defaults come from gs_default_params."""
 
     bg: tuple = (0.0, 0.0, 0.0)
+    tile_w: int = GS_TILE
+    tile_h: int = GS_TILE
     alpha_min: float | None = None
     alpha_max: float | None = None
     T_min: float | None = None
@@ -162,6 +166,7 @@ class RenderParams:
         p = GSRenderParams()
         lib().gs_default_params(ctypes.byref(p))
         p.bg = (ctypes.c_float * 3)(*self.bg)
+        p.tile_w, p.tile_h = int(self.tile_w), int(self.tile_h)
         p.lod_enable = int(self.lod_enable)
         p.cull_enable = int(self.cull_enable)
         for name in ("alpha_min", "alpha_max", "T_min", "dilation", "znear", "fov_clamp", "lod_d0", "lod_f",
@@ -174,13 +179,13 @@ class RenderParams:
 
 @dataclasses.dataclass
 class GaussianTensors:
-    """Gaussian parameters as CUDA tensors in the library's SoA layout."""
+    """Gaussian parameters as CUDA tensors in the library's row layout."""
 
-    mean: torch.Tensor          # (3, N) float32
-    log_scale: torch.Tensor     # (3, N)
-    quat: torch.Tensor          # (4, N)
+    mean: torch.Tensor          # (N, 3) float32
+    log_scale: torch.Tensor     # (N, 3)
+    quat: torch.Tensor          # (N, 4) w, x, y, z
     opacity_logit: torch.Tensor # (N,)
-    sh: torch.Tensor            # (16, 3, N)
+    sh: torch.Tensor            # (N, 16, 3)
     lod: torch.Tensor | None    # (N,) uint8
 
     @property
@@ -219,8 +224,8 @@ def camera_c(cam) -> GSCamera:
     return c
 
 
-def tiles_of(cam) -> int:
-    return ((cam.width + GS_TILE - 1) // GS_TILE) * ((cam.height + GS_TILE - 1) // GS_TILE)
+def tiles_of(cam, tile_w: int = GS_TILE, tile_h: int = GS_TILE) -> int:
+    return ((cam.width + tile_w - 1) // tile_w) * ((cam.height + tile_h - 1) // tile_h)
 
 
 class Workspace:
@@ -253,10 +258,27 @@ class Workspace:
     def preprocess(self, g: GaussianTensors, cams, params: RenderParams, cull=None, stream=None):
         arr = (GSCamera * len(cams))(*[camera_c(c) for c in cams])
         self.cams = list(cams)
+        self.tile = (params.tile_w, params.tile_h)
         self._g = g  # keep the parameter tensors alive until the backward
         gc, pc = g.c(), params.c()
         _check(lib().gs_preprocess(self._ws, ctypes.byref(gc), arr, len(cams), _ptr(cull), ctypes.byref(pc),
                                    _stream(stream)))
+
+    def upload_cameras(self, cams, params: RenderParams, stream=None):
+        """Copies the cameras to the workspace's device table (not while the
+        stream is being captured); kernels read them from there."""
+        arr = (GSCamera * len(cams))(*[camera_c(c) for c in cams])
+        self.cams = list(cams)
+        self.tile = (params.tile_w, params.tile_h)
+        pc = params.c()
+        _check(lib().gs_upload_cameras(self._ws, arr, len(cams), ctypes.byref(pc), _stream(stream)))
+
+    def preprocess_uploaded(self, g: GaussianTensors, params: RenderParams, cull=None, stream=None):
+        """gs_preprocess with the cameras of the last upload (graph-capturable)."""
+        self._g = g
+        gc, pc = g.c(), params.c()
+        _check(lib().gs_preprocess_uploaded(self._ws, ctypes.byref(gc), _ptr(cull), ctypes.byref(pc),
+                                            _stream(stream)))
 
     def bin_sort(self, stream=None):
         _check(lib().gs_bin_sort(self._ws, _stream(stream)))

@@ -49,7 +49,7 @@ struct Offsets {
     size_t cand_g, cand_mask, rec_first, cgrad, rec_g, rec_cam, rd0, rd1, rd2, rect, tt, inst_off, clampm, rgrad, dkey0, dkey1, dval0, dval1;
     size_t tkey0, tkey1, tval0, tval1, slots, ranges, n_contrib, T_final, imp_w, imp_a, sel_cum;
     size_t selk0, selk1, selv0, selv1, loss_maps, loss_partial, lb_status, rx_status, rx_hist, rx_off, red_partial,
-        ctr;
+        ctr, d_cams, d_adam_step, d_adam_coef;
     size_t total;
     size_t lb_words, rx_words, red_words, loss_partial_words;
 };
@@ -108,6 +108,9 @@ Offsets plan(const gs_capacity &c)
     o.red_words = k8 > sel ? k8 : sel;
     o.red_partial = L.take<float>(o.red_words);
     o.ctr = L.take<gs::DevCounters>(1);
+    o.d_cams = L.take<gs::CamTable>(1);
+    o.d_adam_step = L.take<int>(1);
+    o.d_adam_coef = L.take<float>(2 * GS_MAX_ADAM_GROUPS);
     o.total = (L.off + 255) & ~(size_t)255;
     return o;
 }
@@ -144,7 +147,8 @@ void gs_default_params(gs_render_params *p)
 {
     if (!p) return;
     memset(p, 0, sizeof(*p));
-    p->tile_size = GS_TILE;
+    p->tile_w = GS_TILE;
+    p->tile_h = GS_TILE;
     p->lod_enable = 0;
     p->lod_Lmax = 5;
     p->cull_enable = 0;
@@ -226,10 +230,19 @@ int gs_workspace_create(const gs_capacity *cap, gs_workspace **out)
     ws->red_partial = (float *)(b + o.red_partial);
     ws->red_words = o.red_words;
     ws->ctr = (gs::DevCounters *)(b + o.ctr);
+    ws->d_cams = (gs::CamTable *)(b + o.d_cams);
+    ws->d_adam_step = (int *)(b + o.d_adam_step);
+    ws->d_adam_coef = (float *)(b + o.d_adam_coef);
     e = cudaMemset(ws->ctr, 0, sizeof(gs::DevCounters));
+    if (e == cudaSuccess) e = cudaMemset(ws->d_cams, 0, sizeof(gs::CamTable));
+    if (e == cudaSuccess) e = cudaMemset(ws->d_adam_step, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&ws->h_stage, gs_workspace::kStageSlots * sizeof(gs::CamTable));
+    for (int k = 0; e == cudaSuccess && k < gs_workspace::kStageSlots; k++) {
+        e = cudaEventCreateWithFlags(&ws->stage_ev[k], cudaEventDisableTiming);
+        if (e != cudaSuccess) ws->stage_ev[k] = nullptr;
+    }
     if (e != cudaSuccess) {
-        cudaFree(ws->base);
-        delete ws;
+        gs_workspace_destroy(ws);
         return cuda_fail(e, "gs_workspace_create");
     }
     *out = ws;
@@ -239,7 +252,11 @@ int gs_workspace_create(const gs_capacity *cap, gs_workspace **out)
 int gs_workspace_destroy(gs_workspace *ws)
 {
     if (!ws) return GS_OK;
-    cudaError_t e = cudaFree(ws->base);
+    cudaError_t e = cudaSuccess, e2;
+    for (int k = 0; k < gs_workspace::kStageSlots; k++)
+        if (ws->stage_ev[k] && (e2 = cudaEventDestroy(ws->stage_ev[k])) != cudaSuccess) e = e2;
+    if (ws->h_stage && (e2 = cudaFreeHost(ws->h_stage)) != cudaSuccess) e = e2;
+    if (ws->base && (e2 = cudaFree(ws->base)) != cudaSuccess) e = e2;
     delete ws;
     if (e != cudaSuccess) return cuda_fail(e, "gs_workspace_destroy");
     return GS_OK;
@@ -247,43 +264,51 @@ int gs_workspace_destroy(gs_workspace *ws)
 
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-int gs_preprocess(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams, int32_t n_cams,
-                  const uint32_t *cull, const gs_render_params *params, gs_stream stream)
+static int check_tile_shape(const gs_render_params *p, const char *who)
 {
-    if (!ws || !g || !cams || !params) return fail(GS_ERR_INVALID_ARG, "gs_preprocess: NULL argument");
+    if (gs::tile_shape_id(p->tile_w, p->tile_h) < 0)
+        return fail(GS_ERR_INVALID_ARG, "%s: tile %dx%d not one of 16x16, 32x8, 8x32, 32x16", who, p->tile_w,
+                    p->tile_h);
+    return GS_OK;
+}
+
+int gs_upload_cameras(gs_workspace *ws, const gs_camera *cams, int32_t n_cams, const gs_render_params *params,
+                      gs_stream stream)
+{
+    if (!ws || !cams || !params) return fail(GS_ERR_INVALID_ARG, "gs_upload_cameras: NULL argument");
     if (n_cams < 1 || n_cams > ws->cap.max_cameras)
-        return fail(GS_ERR_INVALID_ARG, "gs_preprocess: n_cams %d outside [1, %d]", n_cams, ws->cap.max_cameras);
-    if (g->n < 0 || g->n > ws->cap.max_gaussians)
-        return fail(GS_ERR_CAPACITY, "gs_preprocess: n = %lld exceeds max_gaussians %lld", (long long)g->n,
-                    (long long)ws->cap.max_gaussians);
-    if (params->tile_size != GS_TILE) return fail(GS_ERR_INVALID_ARG, "gs_preprocess: tile_size must be %d", GS_TILE);
-    if (g->n > 0 && (!g->mean || !g->log_scale || !g->quat || !g->opacity_logit || !g->sh))
-        return fail(GS_ERR_INVALID_ARG, "gs_preprocess: NULL Gaussian array");
-    if (!aligned16(g->mean) || !aligned16(g->log_scale) || !aligned16(g->quat) || !aligned16(g->opacity_logit) ||
-        !aligned16(g->sh))
-        return fail(GS_ERR_INVALID_ARG, "gs_preprocess: Gaussian arrays must be 16-byte aligned");
-    if (params->cull_enable && !cull) return fail(GS_ERR_INVALID_ARG, "gs_preprocess: cull_enable needs a cull array");
-    if (params->lod_enable && (params->lod_Lmax < 0 || params->lod_Lmax > gs::kMaxLod || !(params->lod_f > 1.f) ||
-                               !(params->lod_d0 > 0.f)))
-        return fail(GS_ERR_INVALID_ARG, "gs_preprocess: LOD gate needs 0 <= lod_Lmax <= %d, lod_f > 1, lod_d0 > 0",
-                    gs::kMaxLod);
+        return fail(GS_ERR_INVALID_ARG, "gs_upload_cameras: n_cams %d outside [1, %d]", n_cams,
+                    ws->cap.max_cameras);
+    int rc = check_tile_shape(params, "gs_upload_cameras");
+    if (rc != GS_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cs), "gs_upload_cameras");
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(GS_ERR_INVALID_ARG, "gs_upload_cameras: upload outside stream capture (the graph reads the "
+                                        "uploaded table; capture gs_preprocess_uploaded instead)");
+    const int tw = params->tile_w, th = params->tile_h;
     gs::CamTable ct;
     memset(&ct, 0, sizeof(ct));
     ct.n = n_cams;
+    ct.tile_w = tw;
+    ct.tile_h = th;
     long long tiles = 0, pix = 0;
     for (int c = 0; c < n_cams; c++) {
         const gs_camera &s = cams[c];
-        if (s.width <= 0 || s.height <= 0 || s.width > 65535 * GS_TILE || s.height > 65535 * GS_TILE)
-            return fail(GS_ERR_INVALID_ARG, "gs_preprocess: camera %d has size %dx%d", c, s.width, s.height);
-        if (!(s.fx > 0.f) || !(s.fy > 0.f)) return fail(GS_ERR_INVALID_ARG, "gs_preprocess: camera %d focal", c);
+        if (s.width <= 0 || s.height <= 0 || s.width > 65535 * 8 || s.height > 65535 * 8)
+            return fail(GS_ERR_INVALID_ARG, "gs_upload_cameras: camera %d has size %dx%d", c, s.width, s.height);
+        if (!(s.fx > 0.f) || !(s.fy > 0.f)) return fail(GS_ERR_INVALID_ARG, "gs_upload_cameras: camera %d focal", c);
         gs::CamInfo &d = ct.c[c];
         memcpy(d.R, s.R, sizeof(d.R));
         memcpy(d.t, s.t, sizeof(d.t));
         d.fx = s.fx; d.fy = s.fy; d.cx = s.cx; d.cy = s.cy;
         memcpy(d.campos, s.campos, sizeof(d.campos));
         d.width = s.width; d.height = s.height;
-        d.tiles_x = (s.width + GS_TILE - 1) / GS_TILE;
-        d.tiles_y = (s.height + GS_TILE - 1) / GS_TILE;
+        d.tiles_x = (s.width + tw - 1) / tw;
+        d.tiles_y = (s.height + th - 1) / th;
+        if (d.tiles_x > 65535 || d.tiles_y > 65535)
+            return fail(GS_ERR_INVALID_ARG, "gs_upload_cameras: camera %d has more than 65535 tiles a side", c);
         d.tile_base = (int)tiles;
         d.pix_base = pix;
         {
@@ -294,9 +319,48 @@ int gs_preprocess(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams
         tiles += (long long)d.tiles_x * d.tiles_y;
         pix += (long long)s.width * s.height;
     }
-    if (tiles > ws->cap.max_tiles) return fail(GS_ERR_CAPACITY, "gs_preprocess: %lld tiles > max_tiles", tiles);
-    if (pix > ws->cap.max_pixels) return fail(GS_ERR_CAPACITY, "gs_preprocess: %lld pixels > max_pixels", pix);
+    if (tiles > ws->cap.max_tiles) return fail(GS_ERR_CAPACITY, "gs_upload_cameras: %lld tiles > max_tiles", tiles);
+    if (pix > ws->cap.max_pixels) return fail(GS_ERR_CAPACITY, "gs_upload_cameras: %lld pixels > max_pixels", pix);
     ct.total_tiles = (int)tiles;
+    // stage in the next pinned slot once the copy that last read it has run
+    const int k = ws->stage_next;
+    if (ws->stage_pending[k]) CK(cudaEventSynchronize(ws->stage_ev[k]), "gs_upload_cameras(stage)");
+    ws->stage_pending[k] = false;
+    memcpy(&ws->h_stage[k], &ct, sizeof(ct));
+    CK(cudaMemcpyAsync(ws->d_cams, &ws->h_stage[k], sizeof(ct), cudaMemcpyHostToDevice, st), "gs_upload_cameras");
+    CK(cudaEventRecord(ws->stage_ev[k], st), "gs_upload_cameras");
+    ws->stage_pending[k] = true;
+    ws->stage_next = (k + 1) % gs_workspace::kStageSlots;
+    ws->cams = ct;
+    ws->up_fov_clamp = params->fov_clamp;
+    ws->have_upload = 1;
+    ws->have_preprocess = 0;
+    ws->have_binning = 0;
+    ws->have_compact = 0;
+    return GS_OK;
+}
+
+int gs_preprocess_uploaded(gs_workspace *ws, const gs_gaussians *g, const uint32_t *cull,
+                           const gs_render_params *params, gs_stream stream)
+{
+    if (!ws || !g || !params) return fail(GS_ERR_INVALID_ARG, "gs_preprocess_uploaded: NULL argument");
+    if (!ws->have_upload) return fail(GS_ERR_INVALID_ARG, "gs_preprocess_uploaded: no gs_upload_cameras yet");
+    if (params->tile_w != ws->cams.tile_w || params->tile_h != ws->cams.tile_h ||
+        params->fov_clamp != ws->up_fov_clamp)
+        return fail(GS_ERR_INVALID_ARG, "gs_preprocess_uploaded: tile shape and fov_clamp must be those of the upload");
+    if (g->n < 0 || g->n > ws->cap.max_gaussians)
+        return fail(GS_ERR_CAPACITY, "gs_preprocess: n = %lld exceeds max_gaussians %lld", (long long)g->n,
+                    (long long)ws->cap.max_gaussians);
+    if (g->n > 0 && (!g->mean || !g->log_scale || !g->quat || !g->opacity_logit || !g->sh))
+        return fail(GS_ERR_INVALID_ARG, "gs_preprocess: NULL Gaussian array");
+    if (!aligned16(g->mean) || !aligned16(g->log_scale) || !aligned16(g->quat) || !aligned16(g->opacity_logit) ||
+        !aligned16(g->sh))
+        return fail(GS_ERR_INVALID_ARG, "gs_preprocess: Gaussian arrays must be 16-byte aligned");
+    if (params->cull_enable && !cull) return fail(GS_ERR_INVALID_ARG, "gs_preprocess: cull_enable needs a cull array");
+    if (params->lod_enable && (params->lod_Lmax < 0 || params->lod_Lmax > gs::kMaxLod || !(params->lod_f > 1.f) ||
+                               !(params->lod_d0 > 0.f)))
+        return fail(GS_ERR_INVALID_ARG, "gs_preprocess: LOD gate needs 0 <= lod_Lmax <= %d, lod_f > 1, lod_d0 > 0",
+                    gs::kMaxLod);
     gs::RenderConsts rc;
     memcpy(rc.bg, params->bg, sizeof(rc.bg));
     rc.alpha_min = params->alpha_min; rc.alpha_max = params->alpha_max; rc.T_min = params->T_min;
@@ -309,7 +373,6 @@ int gs_preprocess(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams
         const double thr = (double)params->lod_d0 * pow((double)params->lod_f, 0.5 - l);
         rc.lod_thr2[l] = l == 0 ? INFINITY : (float)(thr * thr);
     }
-    ws->cams = ct;
     ws->rc = rc;
     ws->g = *g;
     ws->have_preprocess = 1;
@@ -317,6 +380,15 @@ int gs_preprocess(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams
     ws->have_compact = 0;
     CK(gs::launch_preprocess(ws, (cudaStream_t)stream, cull), "gs_preprocess");
     return GS_OK;
+}
+
+int gs_preprocess(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams, int32_t n_cams,
+                  const uint32_t *cull, const gs_render_params *params, gs_stream stream)
+{
+    if (!ws || !g || !cams || !params) return fail(GS_ERR_INVALID_ARG, "gs_preprocess: NULL argument");
+    int rc = gs_upload_cameras(ws, cams, n_cams, params, stream);
+    if (rc != GS_OK) return rc;
+    return gs_preprocess_uploaded(ws, g, cull, params, stream);
 }
 
 int gs_bin_sort(gs_workspace *ws, gs_stream stream)
@@ -397,7 +469,7 @@ int gs_adam_step_compact(gs_workspace *ws, const gs_gaussians *g, const gs_gauss
     if (!ws->have_compact)
         return fail(GS_ERR_INVALID_ARG, "gs_adam_step_compact: no gs_render_bwd_compact since the last preprocess");
     if (g->n != ws->g.n) return fail(GS_ERR_INVALID_ARG, "gs_adam_step_compact: Gaussian count differs from preprocess");
-    if (step < 1) return fail(GS_ERR_INVALID_ARG, "gs_adam_step_compact: step counts from 1");
+    if (step < 0) return fail(GS_ERR_INVALID_ARG, "gs_adam_step_compact: step is >= 1, or 0 for one past the device counter");
     if (g->n > 0 && (!m->mean || !m->log_scale || !m->quat || !m->opacity_logit || !m->sh || !v->mean ||
                      !v->log_scale || !v->quat || !v->opacity_logit || !v->sh))
         return fail(GS_ERR_INVALID_ARG, "gs_adam_step_compact: NULL moment array");

@@ -8,8 +8,6 @@
 
 namespace gs {
 
-constexpr int kTile = GS_TILE;          // 16 x 16 pixel tiles
-constexpr int kTilePix = kTile * kTile; // 256 pixels = one 256-thread block
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;          // keys per thread in a radix pass
 constexpr int kSortTile = kSortThreads * kSortItems;
@@ -48,11 +46,21 @@ struct CamInfo {
     float jbound;         // >= fx^2 (1 + limx^2) + fy^2 (1 + limy^2): bounds |J|_F^2 tz^2
 };
 
+// The cameras of one call and their tiling.  Kernels read it from device
+// memory (the workspace's copy), so a captured CUDA graph replays with
+// whatever cameras were uploaded last.
 struct CamTable {
     int n;
     int total_tiles;
+    int tile_w, tile_h;   // pixels per tile: 16 x 16, 32 x 8, 8 x 32 or 32 x 16
     CamInfo c[GS_MAX_CAMERAS];
 };
+
+// Index of a supported tile shape, -1 if unsupported.
+__host__ __device__ inline int tile_shape_id(int tw, int th)
+{
+    return tw == 16 && th == 16 ? 0 : tw == 32 && th == 8 ? 1 : tw == 8 && th == 32 ? 2 : tw == 32 && th == 16 ? 3 : -1;
+}
 
 // Render-time constants (FP32, as the kernels compare them).
 struct RenderConsts {
@@ -234,8 +242,21 @@ struct gs_workspace {
     float *red_partial;  // [blocks] generic reduction partials
     size_t red_words;
     gs::DevCounters *ctr;
-    // state of the last preprocess
+    gs::CamTable *d_cams;  // device copy of the uploaded cameras, read by every kernel
+    int *d_adam_step;      // device Adam step counter (graph-replayable optimizer step)
+    float *d_adam_coef;    // [2][GS_MAX_ADAM_GROUPS] bias-corrected lr and 1/sqrt(1 - beta2^t)
+    // host staging of camera uploads: a ring of pinned tables, each reused only
+    // after the copy that read it has completed
+    static constexpr int kStageSlots = 8;
+    gs::CamTable *h_stage; // [kStageSlots], pinned
+    cudaEvent_t stage_ev[kStageSlots];
+    bool stage_pending[kStageSlots];
+    int stage_next;
+    // last upload: the host copy of the table (launch sizes) and the parameters it depends on
     gs::CamTable cams;
+    int have_upload;
+    float up_fov_clamp;
+    // state of the last preprocess
     gs::RenderConsts rc;
     gs_gaussians g;
     int have_preprocess;

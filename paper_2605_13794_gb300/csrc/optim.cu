@@ -189,6 +189,20 @@ cudaError_t launch_loss(gs_workspace *ws, cudaStream_t st, const float *img, con
 
 // ---- Adam -------------------------------------------------------------------
 
+// b^t by binary powering: the same IEEE operations in the same order on the
+// host and the device, so both compute bit-identical bias corrections (kept
+// out of line so that no caller fuses its result into a multiply-add).
+__host__ __device__ __noinline__ double powi(double b, int t)
+{
+    double r = 1.0;
+    while (t > 0) {
+        if (t & 1) r *= b;
+        b *= b;
+        t >>= 1;
+    }
+    return r;
+}
+
 struct AdamTable {
     int n;
     unsigned block_start[GS_MAX_ADAM_GROUPS + 1]; // first block of each group
@@ -206,6 +220,7 @@ struct AdamTable {
     int col[GS_MAX_ADAM_GROUPS], per_g[GS_MAX_ADAM_GROUPS];
     float lr_c[GS_MAX_ADAM_GROUPS];   // lr / (1 - beta1^t)
     float ibc2[GS_MAX_ADAM_GROUPS];   // 1 / sqrt(1 - beta2^t)
+    const float *coef;                // device [2][GS_MAX_ADAM_GROUPS]: lr_c, ibc2 (replaces the two above)
     float b1[GS_MAX_ADAM_GROUPS], b2[GS_MAX_ADAM_GROUPS], eps[GS_MAX_ADAM_GROUPS];
 };
 
@@ -266,7 +281,9 @@ template <int PER>
 __device__ __forceinline__ void adam_block(const AdamTable &t, int gi, long long base)
 {
     const long long n = t.count[gi];
-    const float b1 = t.b1[gi], b2 = t.b2[gi], lr_c = t.lr_c[gi], ibc2 = t.ibc2[gi], eps = t.eps[gi];
+    const float b1 = t.b1[gi], b2 = t.b2[gi], eps = t.eps[gi];
+    const float lr_c = t.coef ? t.coef[gi] : t.lr_c[gi];
+    const float ibc2 = t.coef ? t.coef[GS_MAX_ADAM_GROUPS + gi] : t.ibc2[gi];
     float *P = t.p[gi], *M = t.m[gi], *V = t.v[gi];
     const float *G = t.g[gi];
     const uint32_t *rf = t.rec_first[gi];
@@ -351,6 +368,7 @@ cudaError_t launch_adam(const gs_adam_group *groups, int n_groups, int step, cud
     AdamTable t;
     t.n = n_groups;
     t.cgrad = nullptr;
+    t.coef = nullptr;
     t.block_start[0] = 0;
     auto al16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
     for (int k = 0; k < n_groups; k++) {
@@ -360,21 +378,47 @@ cudaError_t launch_adam(const gs_adam_group *groups, int n_groups, int step, cud
         t.count[k] = g.n;
         t.vec[k] = al16(g.param) && al16(g.grad) && al16(g.m) && al16(g.v);
         t.p[k] = g.param; t.g[k] = g.grad; t.m[k] = g.m; t.v[k] = g.v;
-        t.lr_c[k] = (float)(g.lr / (1.0 - pow((double)g.beta1, step)));
-        t.ibc2[k] = (float)(1.0 / sqrt(1.0 - pow((double)g.beta2, step)));
+        t.lr_c[k] = (float)((double)g.lr / (1.0 - powi((double)g.beta1, step)));
+        t.ibc2[k] = (float)(1.0 / sqrt(1.0 - powi((double)g.beta2, step)));
         t.b1[k] = g.beta1; t.b2[k] = g.beta2; t.eps[k] = g.eps;
         t.rec_first[k] = nullptr; t.col[k] = 0; t.per_g[k] = 1;
     }
     return run_adam(t, n_groups, st);
 }
 
+struct AdamCoefArgs {
+    float lr[5];
+    float b1, b2;
+    int step; // > 0: this step; 0: one past the device counter
+};
+
+// Step number and bias-corrected coefficients on the device, so a captured
+// optimizer step advances its own counter on every replay.
+__global__ void adam_coef_kernel(AdamCoefArgs a, int *d_step, float *coef)
+{
+    if (threadIdx.x != 0) return;
+    const int t = a.step > 0 ? a.step : *d_step + 1;
+    *d_step = t;
+    const double c1 = 1.0 - powi((double)a.b1, t), c2 = 1.0 - powi((double)a.b2, t);
+    for (int k = 0; k < 5; k++) {
+        coef[k] = (float)((double)a.lr[k] / c1);
+        coef[GS_MAX_ADAM_GROUPS + k] = (float)(1.0 / sqrt(c2));
+    }
+}
+
 cudaError_t launch_adam_sparse(gs_workspace *ws, cudaStream_t st, const gs_gaussian_grads &param,
                                const gs_gaussian_grads &m, const gs_gaussian_grads &v, long long n,
                                const float lr[5], float beta1, float beta2, float eps, int step)
 {
+    AdamCoefArgs ca;
+    for (int k = 0; k < 5; k++) ca.lr[k] = lr[k];
+    ca.b1 = beta1; ca.b2 = beta2; ca.step = step;
+    adam_coef_kernel<<<1, 32, 0, st>>>(ca, ws->d_adam_step, ws->d_adam_coef);
+    note_launch();
     AdamTable t;
     t.n = 5;
     t.cgrad = ws->cgrad;
+    t.coef = ws->d_adam_coef;
     t.block_start[0] = 0;
     float *P[5] = {param.mean, param.log_scale, param.quat, param.opacity_logit, param.sh};
     float *M[5] = {m.mean, m.log_scale, m.quat, m.opacity_logit, m.sh};
@@ -388,8 +432,7 @@ cudaError_t launch_adam_sparse(gs_workspace *ws, cudaStream_t st, const gs_gauss
         t.vec[k] = al16(P[k]) && al16(M[k]) && al16(V[k]);
         t.p[k] = P[k]; t.g[k] = nullptr; t.m[k] = M[k]; t.v[k] = V[k];
         t.rec_first[k] = ws->rec_first; t.col[k] = col[k]; t.per_g[k] = per[k];
-        t.lr_c[k] = (float)(lr[k] / (1.0 - pow((double)beta1, step)));
-        t.ibc2[k] = (float)(1.0 / sqrt(1.0 - pow((double)beta2, step)));
+        t.lr_c[k] = 0.f; t.ibc2[k] = 0.f;
         t.b1[k] = beta1; t.b2[k] = beta2; t.eps[k] = eps;
     }
     return run_adam(t, 5, st);

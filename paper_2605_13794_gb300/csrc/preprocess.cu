@@ -143,7 +143,7 @@ __device__ __forceinline__ void camera_point_d(const float m[3], const CamInfo &
 // plus sqrt(0.1) for the clamp of the discriminant, with margins for the
 // rounding of this float evaluation (t, e from camera_point).
 __device__ __forceinline__ bool maybe_on_screen(const float t[3], const float e[3], float smax, const CamInfo &cam,
-                                                const RenderConsts &rc)
+                                                int tw, int th, const RenderConsts &rc)
 {
     const float tzl = t[2] - e[2]; // lower bound of the exact depth
     if (!(tzl > 1e-6f)) return true;
@@ -155,8 +155,8 @@ __device__ __forceinline__ bool maybe_on_screen(const float t[3], const float e[
     const float du = 1.01f * cam.fx * (e[0] + fabsf(t[0] * itz) * e[2]) * itzl;
     const float dv = 1.01f * cam.fy * (e[1] + fabsf(t[1] * itz) * e[2]) * itzl;
     const float ru = R + du + 1e-5f * fabsf(u), rv = R + dv + 1e-5f * fabsf(v);
-    return !(u + ru < 0.f || u - ru >= (float)(cam.tiles_x * kTile) || v + rv < 0.f ||
-             v - rv >= (float)(cam.tiles_y * kTile));
+    return !(u + ru < 0.f || u - ru >= (float)(cam.tiles_x * tw) || v + rv < 0.f ||
+             v - rv >= (float)(cam.tiles_y * th));
 }
 
 // Exact projection of one Gaussian into one camera, from the double-precision
@@ -168,7 +168,8 @@ __device__ __forceinline__ bool maybe_on_screen(const float t[3], const float e[
 // minors of V, plus the dilation terms), which is free of the cancellation of
 // a c - b^2.  Returns false when the tile rectangle is empty.
 __device__ __forceinline__ bool project_gaussian(const float ls[3], const float qin[4], const double td[3],
-                                                 const CamInfo &cam, const RenderConsts &rc, Proj &o)
+                                                 const CamInfo &cam, int tile_w, int tile_h, const RenderConsts &rc,
+                                                 Proj &o)
 {
     const float *R = cam.R;
     const float tx = __double2float_rn(td[0]), ty = __double2float_rn(td[1]), tz = __double2float_rn(td[2]);
@@ -233,9 +234,9 @@ __device__ __forceinline__ bool project_gaussian(const float ls[3], const float 
     const double ud = __dadd_rn(__ddiv_rn(__dmul_rn((double)fx, td[0]), td[2]), (double)cam.cx);
     const double vd = __dadd_rn(__ddiv_rn(__dmul_rn((double)fy, td[1]), td[2]), (double)cam.cy);
     float u = __double2float_rn(ud), v = __double2float_rn(vd);
-    float rr = (float)radius, ts = (float)kTile;
-    int x0 = (int)floorf(FDIV(FSUB(u, rr), ts)), y0 = (int)floorf(FDIV(FSUB(v, rr), ts));
-    int x1 = (int)floorf(FDIV(FADD(u, rr), ts)) + 1, y1 = (int)floorf(FDIV(FADD(v, rr), ts)) + 1;
+    float rr = (float)radius, tw = (float)tile_w, th = (float)tile_h;
+    int x0 = (int)floorf(FDIV(FSUB(u, rr), tw)), y0 = (int)floorf(FDIV(FSUB(v, rr), th));
+    int x1 = (int)floorf(FDIV(FADD(u, rr), tw)) + 1, y1 = (int)floorf(FDIV(FADD(v, rr), th)) + 1;
     x0 = min(max(x0, 0), cam.tiles_x); x1 = min(max(x1, 0), cam.tiles_x);
     y0 = min(max(y0, 0), cam.tiles_y); y1 = min(max(y1, 0), cam.tiles_y);
     if (x1 <= x0 || y1 <= y0) return false;
@@ -293,8 +294,10 @@ __device__ __forceinline__ bool cull_bit(const PreOut &o, int c, long long i)
 // rejects most of a city scene -- producing an order-preserving list of
 // candidate Gaussians with a bit per camera that may still be active.
 // Thread t of block b owns Gaussians b*2048 + k*256 + t (k < 8).
-__global__ void __launch_bounds__(256) gate_kernel(GaussPtrs g, PreOut o, CamTable ct, RenderConsts rc)
+__global__ void __launch_bounds__(256) gate_kernel(GaussPtrs g, PreOut o, const CamTable *__restrict__ ctp,
+                                                   RenderConsts rc)
 {
+    const CamTable &ct = *ctp;
     __shared__ unsigned s_bid;
     __shared__ unsigned s_cnt[kGateItems][8];
     __shared__ unsigned s_total;
@@ -332,7 +335,7 @@ __global__ void __launch_bounds__(256) gate_kernel(GaussPtrs g, PreOut o, CamTab
             if (!(t[2] + te[2] > rc.znear)) continue; // the exact near test is the projection's
             if (smax < 0.f)
                 smax = expf(fmaxf(g.log_scale[3 * i], fmaxf(g.log_scale[3 * i + 1], g.log_scale[3 * i + 2])));
-            if (maybe_on_screen(t, te, smax, cam, rc)) mask[k] |= 1ull << c;
+            if (maybe_on_screen(t, te, smax, cam, ct.tile_w, ct.tile_h, rc)) mask[k] |= 1ull << c;
         }
     }
     // order-preserving compaction: item (k, thread) precedes (k', thread') iff
@@ -375,8 +378,10 @@ __global__ void __launch_bounds__(256) gate_kernel(GaussPtrs g, PreOut o, CamTab
 // projection decides which cameras are active; the records are compacted in
 // (Gaussian, camera) order with a look-back scan and written with their
 // conic, colour, opacity, rectangle and depth key.
-__global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, CamTable ct, RenderConsts rc)
+__global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, const CamTable *__restrict__ ctp,
+                                                         RenderConsts rc)
 {
+    const CamTable &ct = *ctp;
     __shared__ unsigned s_bid;
     __shared__ unsigned long long s_warp[8];
     __shared__ unsigned long long s_base;
@@ -401,7 +406,7 @@ __global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, 
             camera_point_d(L.m, ct.c[c], td);
             if (!(__double2float_rn(td[2]) > rc.znear)) continue;
             Proj p;
-            if (project_gaussian(L.ls, L.q, td, ct.c[c], rc, p)) act |= 1ull << c;
+            if (project_gaussian(L.ls, L.q, td, ct.c[c], ct.tile_w, ct.tile_h, rc, p)) act |= 1ull << c;
         }
     }
     const unsigned long long cnt = __popcll(act);
@@ -436,7 +441,7 @@ __global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, 
         double td[3];
         camera_point_d(L.m, cam, td);
         Proj p;
-        project_gaussian(L.ls, L.q, td, cam, rc, p); // same inputs: same (passing) result
+        project_gaussian(L.ls, L.q, td, cam, ct.tile_w, ct.tile_h, rc, p); // same inputs: same (passing) result
         const float dx = L.m[0] - cam.campos[0], dy = L.m[1] - cam.campos[1], dz = L.m[2] - cam.campos[2];
         const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
         float Y[16];
@@ -493,11 +498,11 @@ cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t 
     if ((e = cudaMemsetAsync(ws->rec_first, 0xff, (size_t)n * sizeof(uint32_t), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(ws->lb_status, 0, (gblocks + 1) * sizeof(unsigned long long), st)) != cudaSuccess)
         return e;
-    gate_kernel<<<gblocks, 256, 0, st>>>(gp, o, ws->cams, ws->rc);
+    gate_kernel<<<gblocks, 256, 0, st>>>(gp, o, ws->d_cams, ws->rc);
     note_launch();
     if ((e = cudaMemsetAsync(ws->lb_status, 0, (pblocks + 1) * sizeof(unsigned long long), st)) != cudaSuccess)
         return e;
-    project_kernel<<<pblocks, 256, 0, st>>>(gp, o, ws->cams, ws->rc);
+    project_kernel<<<pblocks, 256, 0, st>>>(gp, o, ws->d_cams, ws->rc);
     note_launch();
     return cudaGetLastError();
 }
@@ -568,8 +573,10 @@ struct BwdArgs {
 
 // Chain rule from the gradients of (u, v, conic A B C, opacity, rgb) of each
 // record to the parameters of its Gaussian, summed over the Gaussian's records.
-__global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, CamTable ct, RenderConsts rc)
+__global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, const CamTable *__restrict__ ctp,
+                                                             RenderConsts rc)
 {
+    const CamTable &ct = *ctp;
     __shared__ float s_red[4];
     // one thread per Gaussian that has records: the thread of its first record
     const unsigned long long rh = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -796,7 +803,7 @@ cudaError_t launch_preprocess_bwd(gs_workspace *ws, cudaStream_t st, const gs_ga
     const bool reduce = beta > 0.f && scale_reg_value && blocks <= ws->red_words;
     a.red_partial = reduce ? ws->red_partial : nullptr;
     a.ctr = ws->ctr;
-    preprocess_bwd_kernel<<<blocks, 128, 0, st>>>(a, ws->cams, ws->rc);
+    preprocess_bwd_kernel<<<blocks, 128, 0, st>>>(a, ws->d_cams, ws->rc);
     note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -15,11 +15,17 @@
 
 namespace gs {
 
-constexpr int kRT = 64;            // threads per 16x16 tile: 2 warps, one 2x2 pixel quad each
-constexpr int kQ = 4;              // pixels per thread
+constexpr int kQ = 4;              // pixels per thread (one 2x2 quad)
 
-// Thread t owns the quad (qx, qy) = (t % 8, t / 8): warp 0 covers pixel rows
-// 0-7 and warp 1 rows 8-15.  Pixel k of the quad is (2 qx + k % 2, 2 qy + k / 2).
+// A block composites one TW x TH tile with TW * TH / 4 threads.  Thread t owns
+// the quad (qx, qy) = (t % (TW/2), t / (TW/2)); pixel k of the quad is
+// (2 qx + k % 2, 2 qy + k / 2).  For 16 x 16: 64 threads, warp 0 rows 0-7.
+template <int TW, int TH> struct TileShape {
+    static constexpr int threads = TW * TH / 4;
+    static constexpr int warps = threads / 32;
+    static constexpr int qx = TW / 2; // quads per tile row
+    static_assert(threads % 32 == 0, "tile must hold whole warps");
+};
 // Compositing works in tile-local pixel coordinates: pixel centres are exact
 // small floats, and each staged entry's mean is moved to the tile's origin
 // once, from its double-length form u + u_lo, so px - u keeps its full
@@ -29,23 +35,29 @@ struct TileGeom {
     int px0, py0;              // pixel of quad element 0 (image coordinates)
     float ox, oy;              // pixel origin of the tile
     float lx0, ly0;            // centre of quad element 0, tile-local
-    const CamInfo *ci;
+    int width, height;         // of the tile's camera
+    long long pix_base;        // first pixel of the camera in the concatenated outputs
 };
 
-__device__ __forceinline__ TileGeom tile_geom(const CamTable &ct, int tile)
+template <int TW, int TH> __device__ __forceinline__ TileGeom tile_geom(const CamTable &ct, int tile)
 {
+    constexpr int QX = TileShape<TW, TH>::qx;
     TileGeom t;
     t.cam = camera_of_tile(ct, tile);
-    t.ci = &ct.c[t.cam];
-    const int lt = tile - t.ci->tile_base;
-    t.tx = lt % t.ci->tiles_x;
-    t.ty = lt / t.ci->tiles_x;
-    t.px0 = t.tx * kTile + 2 * (threadIdx.x & 7);
-    t.py0 = t.ty * kTile + 2 * (threadIdx.x >> 3);
-    t.ox = (float)(t.tx * kTile);
-    t.oy = (float)(t.ty * kTile);
-    t.lx0 = (float)(2 * (threadIdx.x & 7)) + 0.5f;
-    t.ly0 = (float)(2 * (threadIdx.x >> 3)) + 0.5f;
+    const CamInfo &ci = ct.c[t.cam];
+    const int lt = tile - ci.tile_base;
+    t.tx = lt % ci.tiles_x;
+    t.ty = lt / ci.tiles_x;
+    t.width = ci.width;
+    t.height = ci.height;
+    t.pix_base = ci.pix_base;
+    const int qx = (int)threadIdx.x % QX, qy = (int)threadIdx.x / QX;
+    t.px0 = t.tx * TW + 2 * qx;
+    t.py0 = t.ty * TH + 2 * qy;
+    t.ox = (float)(t.tx * TW);
+    t.oy = (float)(t.ty * TH);
+    t.lx0 = (float)(2 * qx) + 0.5f;
+    t.ly0 = (float)(2 * qy) + 0.5f;
     return t;
 }
 
@@ -129,19 +141,21 @@ __device__ __forceinline__ unsigned long long slot_of(const uint32_t *inst_off, 
 
 // ---- forward --------------------------------------------------------------
 
-__global__ void __launch_bounds__(kRT) render_fwd_kernel(const uint2 *__restrict__ ranges,
-                                                         const uint32_t *__restrict__ vals,
-                                                         const float4 *__restrict__ rd0,
-                                                         const float4 *__restrict__ rd1,
-                                                         const float4 *__restrict__ rd2, CamTable ct, RenderConsts rc,
-                                                         float *__restrict__ rgb_out, float *__restrict__ T_out,
-                                                         float *__restrict__ T_ws, uint32_t *__restrict__ n_contrib)
+template <int TW, int TH>
+__global__ void __launch_bounds__(TileShape<TW, TH>::threads, 768 / TileShape<TW, TH>::threads)
+    render_fwd_kernel(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
+                      const float4 *__restrict__ rd0, const float4 *__restrict__ rd1, const float4 *__restrict__ rd2,
+                      const CamTable *__restrict__ ctp, RenderConsts rc, float *__restrict__ rgb_out,
+                      float *__restrict__ T_out, float *__restrict__ T_ws, uint32_t *__restrict__ n_contrib)
 {
+    constexpr int kRT = TileShape<TW, TH>::threads;
     __shared__ float4 s0[kRT];
     __shared__ float4 s1[kRT];
     __shared__ float s2[kRT];
-    const TileGeom tg = tile_geom(ct, blockIdx.x);
-    const CamInfo &cam = *tg.ci;
+    const CamTable &ct = *ctp;
+    if ((int)blockIdx.x >= ct.total_tiles) return;
+    const TileGeom tg = tile_geom<TW, TH>(ct, blockIdx.x);
+    const TileGeom &cam = tg;
     const uint2 rg = ranges[blockIdx.x];
     const int start = (int)rg.x, end = (int)rg.y;
 
@@ -216,12 +230,23 @@ __global__ void __launch_bounds__(kRT) render_fwd_kernel(const uint2 *__restrict
     }
 }
 
+template <int TW, int TH> static void fwd_launch(gs_workspace *ws, cudaStream_t st, float *rgb, float *T_out)
+{
+    render_fwd_kernel<TW, TH><<<ws->cams.total_tiles, TileShape<TW, TH>::threads, 0, st>>>(
+        ws->ranges, ws->tval[ws->tile_buf], ws->rd0, ws->rd1, ws->rd2, ws->d_cams, ws->rc, rgb, T_out, ws->T_final,
+        ws->n_contrib);
+}
+
 cudaError_t launch_render_fwd(gs_workspace *ws, cudaStream_t st, float *rgb, float *T_out)
 {
     if (ws->cams.total_tiles == 0) return cudaSuccess;
-    render_fwd_kernel<<<ws->cams.total_tiles, kRT, 0, st>>>(ws->ranges, ws->tval[ws->tile_buf], ws->rd0, ws->rd1,
-                                                            ws->rd2, ws->cams, ws->rc, rgb, T_out, ws->T_final,
-                                                            ws->n_contrib);
+    switch (tile_shape_id(ws->cams.tile_w, ws->cams.tile_h)) {
+    case 0: fwd_launch<16, 16>(ws, st, rgb, T_out); break;
+    case 1: fwd_launch<32, 8>(ws, st, rgb, T_out); break;
+    case 2: fwd_launch<8, 32>(ws, st, rgb, T_out); break;
+    case 3: fwd_launch<32, 16>(ws, st, rgb, T_out); break;
+    default: return cudaErrorInvalidValue;
+    }
     note_launch();
     return cudaGetLastError();
 }
@@ -246,16 +271,21 @@ struct BwdRenderArgs {
 // T / (1 - alpha) from the final transmittance.  Per entry, each thread sums
 // the gradient over its 4 pixels, each warp reduces over its 32 threads, and
 // the two warp partials are added once per batch into the entry's slot.
-__global__ void __launch_bounds__(kRT) render_bwd_kernel(BwdRenderArgs a, CamTable ct, RenderConsts rc)
+template <int TW, int TH>
+__global__ void __launch_bounds__(TileShape<TW, TH>::threads)
+    render_bwd_kernel(BwdRenderArgs a, const CamTable *__restrict__ ctp, RenderConsts rc)
 {
+    constexpr int kRT = TileShape<TW, TH>::threads, kWarps = TileShape<TW, TH>::warps;
     __shared__ float4 s0[kBwdBatch];
     __shared__ float4 s1[kBwdBatch];
     __shared__ float s2[kBwdBatch];
     __shared__ unsigned long long s_slot[kBwdBatch];
-    __shared__ float s_red[2][kBwdBatch][kSlotFloats];
+    __shared__ float s_red[kWarps][kBwdBatch][kSlotFloats];
     __shared__ int s_max;
-    const TileGeom tg = tile_geom(ct, blockIdx.x);
-    const CamInfo &cam = *tg.ci;
+    const CamTable &ct = *ctp;
+    if ((int)blockIdx.x >= ct.total_tiles) return;
+    const TileGeom tg = tile_geom<TW, TH>(ct, blockIdx.x);
+    const TileGeom &cam = tg;
     const uint2 rg = a.ranges[blockIdx.x];
     const int start = (int)rg.x, end = (int)rg.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -364,7 +394,10 @@ __global__ void __launch_bounds__(kRT) render_bwd_kernel(BwdRenderArgs a, CamTab
         __syncthreads();
         for (int idx = threadIdx.x; idx < cnt * kSlotFloats; idx += kRT) {
             const int jj = idx / kSlotFloats, q = idx - jj * kSlotFloats;
-            a.slots[s_slot[jj] * kSlotFloats + q] = s_red[0][jj][q] + s_red[1][jj][q];
+            float sum = s_red[0][jj][q];
+#pragma unroll
+            for (int w = 1; w < kWarps; w++) sum += s_red[w][jj][q];
+            a.slots[s_slot[jj] * kSlotFloats + q] = sum;
         }
         __syncthreads();
     }
@@ -377,7 +410,14 @@ cudaError_t launch_render_bwd(gs_workspace *ws, cudaStream_t st, const float *dL
     a.ranges = ws->ranges; a.vals = ws->tval[ws->tile_buf]; a.rd0 = ws->rd0; a.rd1 = ws->rd1; a.rd2 = ws->rd2;
     a.inst_off = ws->inst_off; a.rect = ws->rect; a.T_final = ws->T_final; a.n_contrib = ws->n_contrib;
     a.dL_drgb = dL_drgb; a.slots = ws->slots;
-    render_bwd_kernel<<<ws->cams.total_tiles, kRT, 0, st>>>(a, ws->cams, ws->rc);
+    const unsigned grid = (unsigned)ws->cams.total_tiles;
+    switch (tile_shape_id(ws->cams.tile_w, ws->cams.tile_h)) {
+    case 0: render_bwd_kernel<16, 16><<<grid, TileShape<16, 16>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
+    case 1: render_bwd_kernel<32, 8><<<grid, TileShape<32, 8>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
+    case 2: render_bwd_kernel<8, 32><<<grid, TileShape<8, 32>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
+    case 3: render_bwd_kernel<32, 16><<<grid, TileShape<32, 16>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
+    default: return cudaErrorInvalidValue;
+    }
     note_launch();
     return cudaGetLastError();
 }
@@ -393,15 +433,20 @@ struct ImpArgs {
     float *slots; // [I][2]: alpha-weight (float), composited pixels (uint32 bits)
 };
 
-__global__ void __launch_bounds__(kRT) importance_raster_kernel(ImpArgs a, CamTable ct, RenderConsts rc)
+template <int TW, int TH>
+__global__ void __launch_bounds__(TileShape<TW, TH>::threads)
+    importance_raster_kernel(ImpArgs a, const CamTable *__restrict__ ctp, RenderConsts rc)
 {
+    constexpr int kRT = TileShape<TW, TH>::threads, kWarps = TileShape<TW, TH>::warps;
     __shared__ float4 s0[kRT];
     __shared__ float2 s1[kRT];
     __shared__ unsigned long long s_slot[kRT];
-    __shared__ float s_w[2][kRT];
-    __shared__ uint32_t s_a[2][kRT];
-    const TileGeom tg = tile_geom(ct, blockIdx.x);
-    const CamInfo &cam = *tg.ci;
+    __shared__ float s_w[kWarps][kRT];
+    __shared__ uint32_t s_a[kWarps][kRT];
+    const CamTable &ct = *ctp;
+    if ((int)blockIdx.x >= ct.total_tiles) return;
+    const TileGeom tg = tile_geom<TW, TH>(ct, blockIdx.x);
+    const TileGeom &cam = tg;
     const uint2 rg = a.ranges[blockIdx.x];
     const int start = (int)rg.x, end = (int)rg.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -455,9 +500,11 @@ __global__ void __launch_bounds__(kRT) importance_raster_kernel(ImpArgs a, CamTa
         }
         __syncthreads();
         if (threadIdx.x < cnt) {
-            const float2 out = make_float2(s_w[0][threadIdx.x] + s_w[1][threadIdx.x],
-                                           __uint_as_float(s_a[0][threadIdx.x] + s_a[1][threadIdx.x]));
-            reinterpret_cast<float2 *>(a.slots)[s_slot[threadIdx.x]] = out;
+            float wsum = s_w[0][threadIdx.x];
+            uint32_t asum = s_a[0][threadIdx.x];
+#pragma unroll
+            for (int w = 1; w < kWarps; w++) { wsum += s_w[w][threadIdx.x]; asum += s_a[w][threadIdx.x]; }
+            reinterpret_cast<float2 *>(a.slots)[s_slot[threadIdx.x]] = make_float2(wsum, __uint_as_float(asum));
         }
     }
     // entries never reached (every pixel of the tile had stopped)
@@ -473,7 +520,14 @@ cudaError_t launch_importance_raster(gs_workspace *ws, cudaStream_t st)
     ImpArgs a;
     a.ranges = ws->ranges; a.vals = ws->tval[ws->tile_buf]; a.rd0 = ws->rd0; a.rd1 = ws->rd1; a.rd2 = ws->rd2;
     a.inst_off = ws->inst_off; a.rect = ws->rect; a.slots = ws->slots;
-    importance_raster_kernel<<<ws->cams.total_tiles, kRT, 0, st>>>(a, ws->cams, ws->rc);
+    const unsigned grid = (unsigned)ws->cams.total_tiles;
+    switch (tile_shape_id(ws->cams.tile_w, ws->cams.tile_h)) {
+    case 0: importance_raster_kernel<16, 16><<<grid, TileShape<16, 16>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
+    case 1: importance_raster_kernel<32, 8><<<grid, TileShape<32, 8>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
+    case 2: importance_raster_kernel<8, 32><<<grid, TileShape<8, 32>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
+    case 3: importance_raster_kernel<32, 16><<<grid, TileShape<32, 16>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
+    default: return cudaErrorInvalidValue;
+    }
     note_launch();
     return cudaGetLastError();
 }

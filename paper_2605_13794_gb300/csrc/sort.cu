@@ -278,8 +278,9 @@ struct EmitArgs {
     unsigned long long max_instances;
 };
 
-__global__ void __launch_bounds__(256) emit_kernel(EmitArgs a, CamTable ct)
+__global__ void __launch_bounds__(256) emit_kernel(EmitArgs a, const CamTable *__restrict__ ctp)
 {
+    const CamTable &ct = *ctp;
     __shared__ unsigned s_bid;
     __shared__ unsigned long long s_warp[8];
     __shared__ unsigned long long s_base;
@@ -354,7 +355,7 @@ cudaError_t launch_emit(gs_workspace *ws, cudaStream_t st)
     a.tt = ws->tt; a.rect = ws->rect; a.rec_cam = ws->rec_cam; a.inst_off = ws->inst_off;
     a.tkey = ws->tkey[0]; a.tval = ws->tval[0];
     a.lb_status = ws->lb_status; a.ctr = ws->ctr; a.max_instances = (unsigned long long)ws->cap.max_instances;
-    emit_kernel<<<blocks, 256, 0, st>>>(a, ws->cams);
+    emit_kernel<<<blocks, 256, 0, st>>>(a, ws->d_cams);
     note_launch();
     return cudaGetLastError();
 }

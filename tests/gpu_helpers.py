@@ -9,12 +9,8 @@ from paper_2605_13794_gb300 import binding as B
 from paper_2605_13794_gb300 import synth
 
 
-def tiles_xy(cam):
-    return (cam.width + 15) // 16, (cam.height + 15) // 16
-
-
-def capacity_for(n, cams, records=None, instances=None):
-    tiles = sum(B.tiles_of(c) for c in cams)
+def capacity_for(n, cams, records=None, instances=None, tile=(16, 16)):
+    tiles = sum(B.tiles_of(c, *tile) for c in cams)
     pix = sum(c.width * c.height for c in cams)
     return dict(max_gaussians=max(n, 1), max_records=records or max(n * len(cams), 1),
                 max_instances=instances or max(64 * n * len(cams), 1024), max_tiles=tiles, max_pixels=pix,
@@ -23,7 +19,7 @@ def capacity_for(n, cams, records=None, instances=None):
 
 def gpu_params(P, **over):
     """Binding params equal to oracle Params P."""
-    d = dict(bg=tuple(P.bg), alpha_min=P.alpha_min, alpha_max=P.alpha_max, T_min=P.T_min, dilation=P.dilation,
+    d = dict(bg=tuple(P.bg), tile_w=P.tile_w, tile_h=P.tile_h, alpha_min=P.alpha_min, alpha_max=P.alpha_max, T_min=P.T_min, dilation=P.dilation,
              znear=P.znear, fov_clamp=P.fov_clamp, lod_enable=P.lod_enable, lod_d0=P.lod_d0, lod_f=P.lod_f,
              lod_Lmax=P.lod_Lmax, cull_enable=P.cull_enable, eps_score=P.eps_score, vis_mass=P.vis_mass)
     d.update(over)
@@ -35,8 +31,9 @@ class GpuRun:
 
     def __init__(self, g: synth.GaussianSet, cams, P, cull=None, ws=None, cap=None):
         self.cams = cams
+        self.tile = (P.tile_w, P.tile_h)
         self.gt = B.GaussianTensors.from_host(g)
-        self.ws = ws or B.Workspace(**(cap or capacity_for(g.n, cams)))
+        self.ws = ws or B.Workspace(**(cap or capacity_for(g.n, cams, tile=self.tile)))
         self.cull = None if cull is None else torch.from_numpy(np.ascontiguousarray(cull, np.uint32).view(np.int32)).cuda()
         self.ws.preprocess(self.gt, cams, gpu_params(P), self.cull)
         c = self.ws.counts()
@@ -57,7 +54,7 @@ class GpuRun:
         self.rd0 = self.ws.read_buffer(B.GS_BUF_REC_XY_CONIC, np.float32, n, 4)
         self.rd1 = self.ws.read_buffer(B.GS_BUF_REC_C_OPAC_RG, np.float32, n, 4)
         self.rd2 = self.ws.read_buffer(B.GS_BUF_REC_B_LO, np.float32, n, 4)
-        ntiles = sum(B.tiles_of(cm) for cm in cams)
+        ntiles = sum(B.tiles_of(cm, *self.tile) for cm in cams)
         self.ranges = self.ws.read_buffer(B.GS_BUF_TILE_RANGES, np.uint32, ntiles, 2)
         self.sorted_vals = self.ws.read_buffer(B.GS_BUF_SORTED_VALUES, np.uint32, self.counts["n_instances"])
         self.n_contrib = self.ws.read_buffer(B.GS_BUF_N_CONTRIB, np.uint32, self.P)
@@ -67,7 +64,7 @@ class GpuRun:
         return sum(cm.width * cm.height for cm in self.cams[:c])
 
     def tile_base(self, c):
-        return sum(B.tiles_of(cm) for cm in self.cams[:c])
+        return sum(B.tiles_of(cm, *self.tile) for cm in self.cams[:c])
 
     def image(self, c):
         cam = self.cams[c]
@@ -93,7 +90,7 @@ class GpuRun:
         """Per local tile of camera c, the ordered list of Gaussian ids."""
         tb = self.tile_base(c)
         out = []
-        for t in range(B.tiles_of(self.cams[c])):
+        for t in range(B.tiles_of(self.cams[c], *self.tile)):
             s, e = self.ranges[tb + t]
             out.append(self.rec_g[self.sorted_vals[s:e]].astype(np.int64))
         return out

@@ -39,7 +39,7 @@ def test_host_side_argument_checks_without_gpu():
     L = B.lib()
     p = B.GSRenderParams()
     L.gs_default_params(ctypes.byref(p))
-    assert p.tile_size == 16 and abs(p.alpha_min - 1 / 255) < 1e-9 and abs(p.T_min - 1e-4) < 1e-9
+    assert p.tile_w == 16 and p.tile_h == 16 and abs(p.alpha_min - 1 / 255) < 1e-9 and abs(p.T_min - 1e-4) < 1e-9
     bad = B.GSCapacity(10, 10, 1 << 31, 10, 10, 1, 0)
     assert L.gs_workspace_bytes(ctypes.byref(bad)) == -1
     ok = B.GSCapacity(1000, 1000, 10000, 100, 10000, 1, 0)

@@ -85,7 +85,7 @@ def _compare_view(run: GpuRun, c, g64, cam, P, cull=None, check_image=True):
         tx, _ = O.tiles_of(cam, P)
         for i in tied:
             x0, y0, x1, y1 = pr["rect"][i]
-            ok[max(0, y0 - 1) * 16:(y1 + 1) * 16, max(0, x0 - 1) * 16:(x1 + 1) * 16] = False
+            ok[max(0, y0 - 1) * P.tile_h:(y1 + 1) * P.tile_h, max(0, x0 - 1) * P.tile_w:(x1 + 1) * P.tile_w] = False
     assert ok.mean() > 0.99
     img = run.image(c)
     err = np.abs(img - fwd["image"]).max(axis=0)

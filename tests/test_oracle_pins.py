@@ -254,18 +254,43 @@ def test_bg_colour_enters_through_final_transmittance(oracle_mod):
     np.testing.assert_allclose(f1["image"], f0["image"] + bg[:, None, None] * f0["T"][None], atol=1e-12)
 
 
-def test_tiled_equals_untiled_brute_force(oracle_mod):
+TILE_SHAPES = [(16, 16), (32, 8), (8, 32), (32, 16)]
+
+
+@pytest.mark.parametrize("tw,th", TILE_SHAPES)
+def test_tiled_equals_untiled_brute_force(oracle_mod, tw, th):
     # With opacity below alpha_min * e^{4.5} = 0.35 every fragment outside a
     # Gaussian's 3-sigma rectangle has alpha < alpha_min, so compositing all
-    # Gaussians at every pixel (no tiles, no rectangles) must give the same image.
+    # Gaussians at every pixel (no tiles, no rectangles) must give the same
+    # image, whatever the tile shape.
     g = _scene(1500, 23, opacity_max=0.34)
     cam = synth.plain_camera(80, 64, 250.0)
-    P = oracle_mod.Params()
+    P = oracle_mod.Params(tile_w=tw, tile_h=th)
     g64 = oracle_mod.gaussians64(g)
     fwd = oracle_mod.forward_view(g64, cam, P)
     img, T = oracle_mod.render_brute(fwd["proj"], cam, P)
     assert np.array_equal(img, fwd["image"])
     assert np.array_equal(T, fwd["T"])
+
+
+@pytest.mark.parametrize("tw,th", TILE_SHAPES)
+def test_rect_is_the_tiles_meeting_the_3sigma_box(oracle_mod, tw, th):
+    # the rectangle holds exactly the tiles whose pixel span meets
+    # [u - r, u + r] x [v - r, v + r], clipped to the image
+    g = synth.plain_scene(600, 27)
+    cam = synth.plain_camera(100, 70, 250.0)
+    P = oracle_mod.Params(tile_w=tw, tile_h=th)
+    pr = oracle_mod.project(oracle_mod.gaussians64(g), cam, P)
+    tx, ty = oracle_mod.tiles_of(cam, P)
+    act = np.nonzero(pr["status"] == oracle_mod.ACTIVE)[0]
+    assert len(act) > 100
+    for i in act:
+        u, v = pr["uv"][i]
+        r = pr["radius"][i]
+        xs = [x for x in range(tx) if x * tw <= u + r and u - r < (x + 1) * tw]
+        ys = [y for y in range(ty) if y * th <= v + r and v - r < (y + 1) * th]
+        x0, y0, x1, y1 = pr["rect"][i]
+        assert (list(range(x0, x1)), list(range(y0, y1))) == (xs, ys), i
 
 
 def test_binning_brute_force(oracle_mod):
