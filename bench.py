@@ -62,6 +62,14 @@ def parse():
     ap.add_argument("--impl", default="gsblitz", choices=["gsblitz", "reference"])
     ap.add_argument("--n", type=int, default=N_GAUSS, help="Gaussians (default: the 5M workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="city5M", choices=["city5M", "train8-city20M", "batch64-city10M",
+                                                              "serve-city30M"],
+                    help="city5M: the single-view training step (the default line); the others run the "
+                         "multi-view graph-captured training loop, the 64-camera mixed-resolution batched "
+                         "render and the serving loop")
+    ap.add_argument("--tune-cache", default=None, help="autotuner cache file for batch64-city10M")
+    ap.add_argument("--tile", default="16x16", choices=["16x16", "32x8", "8x32", "32x16"],
+                    help="render tile shape of the city5M step")
     return ap.parse_args()
 
 
@@ -142,7 +150,7 @@ def make_host_inputs(n):
 class Step:
     """Device state and the sequence of C-ABI calls of one training step."""
 
-    def __init__(self, g, cam, target):
+    def __init__(self, g, cam, target, tile=(16, 16)):
         import torch
         from paper_2605_13794_gb300 import binding as B
         self.B, self.torch = B, torch
@@ -165,13 +173,14 @@ class Step:
         self.s = torch.zeros(self.n, device="cuda")
         self.crad = torch.zeros(self.n, device="cuda", dtype=torch.int32)
         self.cvis = torch.zeros(self.n, device="cuda", dtype=torch.int32)
-        self.params_train = B.RenderParams(lod_enable=True, cull_enable=True, **LOD)
+        tw, th = tile
+        self.params_train = B.RenderParams(lod_enable=True, cull_enable=True, tile_w=tw, tile_h=th, **LOD)
         # the scoring sweep after density control (the paper's T2 pass) renders with the LOD gate
         # engaged and never applies the Cull mask it recomputes
-        self.params_imp = B.RenderParams(lod_enable=True, cull_enable=False, **LOD)
+        self.params_imp = B.RenderParams(lod_enable=True, cull_enable=False, tile_w=tw, tile_h=th, **LOD)
         self.step_no = 0
         # capacities from a dry run of the importance configuration (no Cull column)
-        tiles = B.tiles_of(cam)
+        tiles = B.tiles_of(cam, tw, th)
         probe = B.Workspace(max_gaussians=self.n, max_records=self.n, max_instances=min((1 << 30) - 1, 32 * self.n),
                             max_tiles=tiles, max_pixels=self.P)
         probe.preprocess(self.gt, [cam], self.params_imp)
@@ -389,18 +398,57 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_workload(args, world, rank, local):
+    """The batched workloads: one JSON line each (device-timed; clocks sampled
+    over the whole run)."""
+    import torch
+    __import__("__graft_entry__").build()
+    from paper_2605_13794_gb300 import workloads as WL
+    torch.cuda.set_device(local)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    w0 = time.time()
+    if args.workload == "train8-city20M":
+        r = WL.train_batch_workload(steps=args.steps, warmup=args.warmup)
+        line = {"metric": "multi-view training step Mpix/s (8 views 1600x1200, 20M city Gaussians, graph-captured)",
+                "value": r["graph_mpix_per_s"], "unit": "Mpix/s", "higher_is_better": True,
+                "ms_per_step": r["graph_ms"], "detail": r}
+    elif args.workload == "batch64-city10M":
+        r = WL.batched_render_workload(reps=args.steps, warmup=args.warmup, tune_cache=args.tune_cache)
+        line = {"metric": "batched render Mpix/s (64 cameras of mixed resolution, 10M city Gaussians, one pass)",
+                "value": r["mpix_per_s"], "unit": "Mpix/s", "higher_is_better": True, "ms_per_step": r["ms"],
+                "detail": r}
+    else:
+        r = WL.serving_workload()
+        line = {"metric": "serving p99 latency ms (Poisson 200 req/s, 60 s, 720p-4K, 30M resident Gaussians)",
+                "value": r["p99_ms"], "unit": "ms", "higher_is_better": False, "detail": r}
+    sampler.mark(w0, time.time())
+    line.update({"workload": args.workload, "n_gpus": world, "dtype": "f32", "data": "synthetic",
+                 "clocks": sampler.stop(), "gpu_launches": None})
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
+    if args.workload != "city5M":
+        run_workload(args, world, rank, local)
+        return
     import torch
     __import__("__graft_entry__").build()
     from paper_2605_13794_gb300 import binding as B
     torch.cuda.set_device(local)
     g, cam, target = make_host_inputs(args.n)
-    step = Step(g, cam, target)
+    step = Step(g, cam, target, tile=tuple(int(x) for x in args.tile.split("x")))
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         step.run()
@@ -489,7 +537,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "gaussians": g.n, "width": W_IMG, "height": H_IMG,
+            "config": {"workload": WORKLOAD, "gaussians": g.n, "width": W_IMG, "height": H_IMG, "tile": args.tile,
                        "lod": True, "cull": True, "importance_pass": True, "optimizer": "adam",
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
             "mgaussian_per_s": gauss,

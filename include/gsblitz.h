@@ -22,10 +22,11 @@
  *     A NULL stream means the legacy default stream.
  *   - Every call returns a gs_status.  Argument errors are reported at once.
  *     Errors found by kernels (capacity overflow, a bounded wait that gave up)
- *     are recorded in the workspace's device error word and returned by the
- *     next gs_sync_status / gs_workspace_counts call; the outputs of the
- *     failing step are then undefined.  The library never aborts, exits or
- *     traps.  gs_last_error() describes the last error of the calling thread.
+ *     are recorded in the workspace's device error word, returned by the next
+ *     gs_sync_status call and reported in gs_counts.error by
+ *     gs_workspace_counts; the outputs of the failing step are then
+ *     undefined.  The library never aborts, exits or traps.  gs_last_error()
+ *     describes the last error of the calling thread.
  *   - Floating point is FP32 throughout.
  */
 #ifndef GSBLITZ_H
@@ -63,8 +64,14 @@ typedef struct {
     int64_t max_tiles;    /* sum over the cameras of one call of tiles_x * tiles_y */
     int64_t max_pixels;   /* sum over the cameras of one call of width * height */
     int32_t max_cameras;  /* <= GS_MAX_CAMERAS */
-    int32_t reserved;
+    int32_t flags;        /* GS_CAP_* bits */
 } gs_capacity;
+
+/* gs_capacity.flags: a workspace for rendering and importance only.  It holds
+ * no gradient storage (36 -> 8 bytes per instance, no per-record gradient
+ * rows, no loss maps); the backward, the loss and the compact Adam step
+ * return GS_ERR_INVALID_ARG on it. */
+#define GS_CAP_FORWARD_ONLY 1
 
 /* Gaussian parameters, one row per Gaussian for each attribute (the layout of
  * PyTorch 3DGS code), FP32:
@@ -179,6 +186,10 @@ int gs_workspace_create(const gs_capacity *cap, gs_workspace **out);
 int gs_workspace_destroy(gs_workspace *ws);
 /* Bytes of device memory a workspace with these capacities holds. */
 int64_t gs_workspace_bytes(const gs_capacity *cap);
+/* Execution tuning that leaves every result unchanged: keys ranked per block
+ * by the radix passes of gs_bin_sort and gs_importance, 2048 or 4096 (the
+ * default).  Applies to the calls made after it. */
+int gs_workspace_set_sort_chunk(gs_workspace *ws, int32_t keys_per_block);
 
 /* View gate, projection and colour of every Gaussian for each of n_cams
  * cameras (host array, <= GS_MAX_CAMERAS).  cull: device bit array

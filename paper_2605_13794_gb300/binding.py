@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libgsblitz.so")
 GS_OK, GS_ERR_INVALID_ARG, GS_ERR_OOM, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_DEVICE = 0, -1, -2, -3, -4, -5, -6
 GS_MAX_CAMERAS = 64
 GS_TILE = 16
+GS_CAP_FORWARD_ONLY = 1
 (GS_BUF_REC_GAUSSIAN, GS_BUF_REC_CAMERA, GS_BUF_REC_RECT, GS_BUF_REC_TILES, GS_BUF_REC_DEPTH, GS_BUF_REC_XY_CONIC,
  GS_BUF_REC_C_OPAC_RG, GS_BUF_REC_B_LO, GS_BUF_SORTED_VALUES, GS_BUF_TILE_RANGES, GS_BUF_N_CONTRIB) = range(11)
 
@@ -27,7 +28,7 @@ EXPORTS = ("gs_default_params", "gs_last_error", "gs_workspace_create", "gs_work
            "gs_preprocess", "gs_bin_sort", "gs_render_fwd", "gs_render_bwd", "gs_importance", "gs_photometric_loss",
            "gs_adam_step", "gs_sync_status", "gs_workspace_counts", "gs_clear_error", "gs_workspace_buffer",
            "gs_kernel_launches", "gs_render_bwd_adam", "gs_render_bwd_compact", "gs_adam_step_compact",
-           "gs_visible_set_static", "gs_upload_cameras", "gs_preprocess_uploaded")
+           "gs_visible_set_static", "gs_upload_cameras", "gs_preprocess_uploaded", "gs_workspace_set_sort_chunk")
 
 
 class GSError(RuntimeError):
@@ -39,7 +40,7 @@ class GSError(RuntimeError):
 class GSCapacity(ctypes.Structure):
     _fields_ = [("max_gaussians", ctypes.c_int64), ("max_records", ctypes.c_int64),
                 ("max_instances", ctypes.c_int64), ("max_tiles", ctypes.c_int64), ("max_pixels", ctypes.c_int64),
-                ("max_cameras", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("max_cameras", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 class GSGaussians(ctypes.Structure):
@@ -101,6 +102,7 @@ def lib() -> ctypes.CDLL:
         L.gs_kernel_launches.restype = i64
         L.gs_preprocess.argtypes = [vp, vp, vp, i32, vp, vp, vp]
         L.gs_upload_cameras.argtypes = [vp, vp, i32, vp, vp]
+        L.gs_workspace_set_sort_chunk.argtypes = [vp, i32]
         L.gs_preprocess_uploaded.argtypes = [vp, vp, vp, vp, vp]
         L.gs_bin_sort.argtypes = [vp, vp]
         L.gs_render_fwd.argtypes = [vp, vp, vp, vp]
@@ -232,8 +234,9 @@ class Workspace:
     """Owns a gs_workspace (all scratch of the render path) on the current device."""
 
     def __init__(self, max_gaussians: int, max_records: int, max_instances: int, max_tiles: int,
-                 max_pixels: int, max_cameras: int = 1):
-        self.cap = GSCapacity(max_gaussians, max_records, max_instances, max_tiles, max_pixels, max_cameras, 0)
+                 max_pixels: int, max_cameras: int = 1, forward_only: bool = False):
+        self.cap = GSCapacity(max_gaussians, max_records, max_instances, max_tiles, max_pixels, max_cameras,
+                              GS_CAP_FORWARD_ONLY if forward_only else 0)
         self._ws = ctypes.c_void_p()
         _check(lib().gs_workspace_create(ctypes.byref(self.cap), ctypes.byref(self._ws)))
         self.cams = []
@@ -241,7 +244,7 @@ class Workspace:
     @staticmethod
     def bytes_for(**cap) -> int:
         c = GSCapacity(cap["max_gaussians"], cap["max_records"], cap["max_instances"], cap["max_tiles"],
-                       cap["max_pixels"], cap.get("max_cameras", 1), 0)
+                       cap["max_pixels"], cap.get("max_cameras", 1), GS_CAP_FORWARD_ONLY if cap.get("forward_only") else 0)
         return int(lib().gs_workspace_bytes(ctypes.byref(c)))
 
     def close(self):
@@ -279,6 +282,11 @@ class Workspace:
         gc, pc = g.c(), params.c()
         _check(lib().gs_preprocess_uploaded(self._ws, ctypes.byref(gc), _ptr(cull), ctypes.byref(pc),
                                             _stream(stream)))
+
+    def set_sort_chunk(self, keys_per_block: int):
+        """Keys per block of the radix passes (2048 or 4096); results are unchanged."""
+        _check(lib().gs_workspace_set_sort_chunk(self._ws, int(keys_per_block)))
+        self.sort_chunk = int(keys_per_block)
 
     def bin_sort(self, stream=None):
         _check(lib().gs_bin_sort(self._ws, _stream(stream)))

@@ -63,7 +63,8 @@ Offsets plan(const gs_capacity &c)
     o.cand_g = L.take<uint32_t>(N);
     o.cand_mask = L.take<unsigned long long>(N);
     o.rec_first = L.take<uint32_t>(N);
-    o.cgrad = L.take<float>(R * gs::kGradRow);
+    const bool fwd_only = (c.flags & GS_CAP_FORWARD_ONLY) != 0;
+    o.cgrad = L.take<float>(fwd_only ? 0 : R * gs::kGradRow);
     o.rec_g = L.take<uint32_t>(R);
     o.rec_cam = L.take<uint16_t>(R);
     o.rd0 = L.take<float4>(R);
@@ -73,7 +74,7 @@ Offsets plan(const gs_capacity &c)
     o.tt = L.take<uint32_t>(R);
     o.inst_off = L.take<uint32_t>(R);
     o.clampm = L.take<uint8_t>(R);
-    o.rgrad = L.take<float>(R * gs::kSlotFloats);
+    o.rgrad = L.take<float>(fwd_only ? 0 : R * gs::kSlotFloats);
     o.dkey0 = L.take<uint32_t>(R);
     o.dkey1 = L.take<uint32_t>(R);
     o.dval0 = L.take<uint32_t>(R);
@@ -82,7 +83,7 @@ Offsets plan(const gs_capacity &c)
     o.tkey1 = L.take<uint32_t>(I);
     o.tval0 = L.take<uint32_t>(I);
     o.tval1 = L.take<uint32_t>(I);
-    o.slots = L.take<float>(I * gs::kSlotFloats);
+    o.slots = L.take<float>(I * (fwd_only ? 2 : gs::kSlotFloats)); // importance needs (w, a) per instance
     o.ranges = L.take<uint2>(T);
     o.n_contrib = L.take<uint32_t>(P);
     o.T_final = L.take<float>(P);
@@ -93,14 +94,14 @@ Offsets plan(const gs_capacity &c)
     o.selk1 = L.take<uint32_t>(R);
     o.selv0 = L.take<uint32_t>(R);
     o.selv1 = L.take<uint32_t>(R);
-    o.loss_maps = L.take<float>(P * 3 * 3);
-    o.loss_partial_words = 2 * 3 * (P / 1024 + 65536);
+    o.loss_maps = L.take<float>(fwd_only ? 0 : P * 3 * 3);
+    o.loss_partial_words = fwd_only ? 0 : 2 * 3 * (P / 1024 + 65536);
     o.loss_partial = L.take<float>(o.loss_partial_words);
     const size_t nb = (N > R ? N : R) / 256 + 2;
     o.lb_words = nb + 1;
     o.lb_status = L.take<unsigned long long>(o.lb_words);
     const size_t items = (R > I ? R : I);
-    o.rx_words = (items / gs::kSortTile + 1) * 256 + 1;
+    o.rx_words = (items / (gs::kSortThreads * 8) + 1) * 256 + 1; // for the smaller (2048-key) blocks
     o.rx_status = L.take<uint32_t>(o.rx_words);
     o.rx_hist = L.take<uint32_t>(4 * 256);
     o.rx_off = L.take<uint32_t>(4 * 256);
@@ -182,6 +183,7 @@ int gs_workspace_create(const gs_capacity *cap, gs_workspace **out)
     gs_workspace *ws = new (std::nothrow) gs_workspace();
     if (!ws) return fail(GS_ERR_OOM, "host allocation failed");
     ws->cap = *cap;
+    ws->sort_items = gs::kSortItems;
     cudaGetDevice(&ws->device);
     cudaError_t e = cudaMalloc(&ws->base, o.total);
     if (e != cudaSuccess) {
@@ -263,6 +265,15 @@ int gs_workspace_destroy(gs_workspace *ws)
 }
 
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+int gs_workspace_set_sort_chunk(gs_workspace *ws, int32_t keys_per_block)
+{
+    if (!ws) return fail(GS_ERR_INVALID_ARG, "gs_workspace_set_sort_chunk: NULL workspace");
+    if (keys_per_block != 2048 && keys_per_block != 4096)
+        return fail(GS_ERR_INVALID_ARG, "gs_workspace_set_sort_chunk: keys_per_block must be 2048 or 4096");
+    ws->sort_items = keys_per_block / gs::kSortThreads;
+    return GS_OK;
+}
 
 static int check_tile_shape(const gs_render_params *p, const char *who)
 {
@@ -430,6 +441,8 @@ int gs_render_fwd(gs_workspace *ws, float *rgb_out, float *T_out, gs_stream stre
 int gs_render_bwd(gs_workspace *ws, const gs_gaussians *g, const float *dL_drgb, const gs_gaussian_grads *grads,
                   int32_t accumulate, float *absgrad, float scale_reg_beta, float *scale_reg_value, gs_stream stream)
 {
+    if (ws && (ws->cap.flags & GS_CAP_FORWARD_ONLY))
+        return fail(GS_ERR_INVALID_ARG, "gs_render_bwd: the workspace was created GS_CAP_FORWARD_ONLY");
     if (!ws || !g || !dL_drgb || !grads) return fail(GS_ERR_INVALID_ARG, "gs_render_bwd: NULL argument");
     if (!ws->have_binning) return fail(GS_ERR_INVALID_ARG, "gs_render_bwd: call gs_bin_sort and gs_render_fwd first");
     if (g->n != ws->g.n) return fail(GS_ERR_INVALID_ARG, "gs_render_bwd: Gaussian count differs from preprocess");
@@ -446,6 +459,8 @@ int gs_render_bwd(gs_workspace *ws, const gs_gaussians *g, const float *dL_drgb,
 int gs_render_bwd_compact(gs_workspace *ws, const gs_gaussians *g, const float *dL_drgb, float *absgrad,
                           float scale_reg_beta, float *scale_reg_value, gs_stream stream)
 {
+    if (ws && (ws->cap.flags & GS_CAP_FORWARD_ONLY))
+        return fail(GS_ERR_INVALID_ARG, "gs_render_bwd_compact: the workspace was created GS_CAP_FORWARD_ONLY");
     if (!ws || !g || !dL_drgb) return fail(GS_ERR_INVALID_ARG, "gs_render_bwd_compact: NULL argument");
     if (!ws->have_binning)
         return fail(GS_ERR_INVALID_ARG, "gs_render_bwd_compact: call gs_bin_sort and gs_render_fwd first");
@@ -465,6 +480,8 @@ int gs_adam_step_compact(gs_workspace *ws, const gs_gaussians *g, const gs_gauss
                          const gs_gaussian_grads *v, const float lr[5], float beta1, float beta2, float eps,
                          int32_t step, gs_stream stream)
 {
+    if (ws && (ws->cap.flags & GS_CAP_FORWARD_ONLY))
+        return fail(GS_ERR_INVALID_ARG, "gs_adam_step_compact: the workspace was created GS_CAP_FORWARD_ONLY");
     if (!ws || !g || !m || !v || !lr) return fail(GS_ERR_INVALID_ARG, "gs_adam_step_compact: NULL argument");
     if (!ws->have_compact)
         return fail(GS_ERR_INVALID_ARG, "gs_adam_step_compact: no gs_render_bwd_compact since the last preprocess");
@@ -506,6 +523,8 @@ int gs_importance(gs_workspace *ws, float *w, uint32_t *a, float *s_accum, uint3
 int gs_photometric_loss(gs_workspace *ws, const float *image, const float *target, int32_t batch, int32_t height,
                         int32_t width, float lambda, float *loss_out, float *dL_dimage, gs_stream stream)
 {
+    if (ws && (ws->cap.flags & GS_CAP_FORWARD_ONLY))
+        return fail(GS_ERR_INVALID_ARG, "gs_photometric_loss: the workspace was created GS_CAP_FORWARD_ONLY");
     if (!ws || !image || !target || !loss_out || !dL_dimage)
         return fail(GS_ERR_INVALID_ARG, "gs_photometric_loss: NULL argument");
     if (batch < 1 || height < 1 || width < 1) return fail(GS_ERR_INVALID_ARG, "gs_photometric_loss: empty batch");

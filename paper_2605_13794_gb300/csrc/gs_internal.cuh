@@ -9,7 +9,7 @@
 namespace gs {
 
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;          // keys per thread in a radix pass
+constexpr int kSortItems = 16;          // keys per thread in a radix pass (default)
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kSlotFloats = 9;          // per (record, tile) gradient slot: du dv dA dB dC do dr dg db
 constexpr int kGradRow = 59;            // parameters per Gaussian: mean 3, log-scale 3, quat 4, opacity 1, SH 48
@@ -243,6 +243,7 @@ struct gs_workspace {
     size_t red_words;
     gs::DevCounters *ctr;
     gs::CamTable *d_cams;  // device copy of the uploaded cameras, read by every kernel
+    int sort_items;        // keys per thread of a radix pass: 16 (4096-key blocks) or 8 (2048)
     int *d_adam_step;      // device Adam step counter (graph-replayable optimizer step)
     float *d_adam_coef;    // [2][GS_MAX_ADAM_GROUPS] bias-corrected lr and 1/sqrt(1 - beta2^t)
     // host staging of camera uploads: a ring of pinned tables, each reused only

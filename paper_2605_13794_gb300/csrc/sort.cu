@@ -12,8 +12,8 @@
 //      the depth order inside each tile: the final order is
 //      (camera, tile, depth bits, Gaussian) without ever sorting 64-bit keys;
 //   4. tile ranges from the sorted tile ids.
-// The radix passes are single-pass ("onesweep"): each 4096-key block ranks its
-// keys in shared memory, publishes per-digit counts and finds its global
+// The radix passes are single-pass ("onesweep"): each block ranks its 2048 or
+// 4096 keys (a tuning of the workspace) in shared memory, publishes per-digit counts and finds its global
 // offsets by a per-digit decoupled look-back, so every pass reads and writes
 // each key once.  Item counts stay on the device, so nothing here needs a
 // host synchronisation.
@@ -70,16 +70,18 @@ __global__ void radix_offsets_kernel(const uint32_t *hist, uint32_t *off, int pa
     }
 }
 
-// One stable LSD pass over digit (key >> shift) & 255.
-template <bool VALS_IDENTITY, bool WRITE_KEYS>
+// One stable LSD pass over digit (key >> shift) & 255; each block ranks
+// 256 * ITEMS keys.
+template <int ITEMS, bool VALS_IDENTITY, bool WRITE_KEYS>
 __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
     uint32_t *__restrict__ vals_out, const unsigned long long *count, unsigned long long cap, int shift,
     const uint32_t *__restrict__ bucket_off, uint32_t *status /* ticket at [0], then [blocks][256] */,
     DevCounters *ctr)
 {
-    __shared__ uint32_t s_keys[kSortTile];
-    __shared__ uint32_t s_vals[kSortTile];
+    constexpr int kTileKeys = kSortThreads * ITEMS;
+    __shared__ uint32_t s_keys[kTileKeys];
+    __shared__ uint32_t s_vals[kTileKeys];
     __shared__ uint32_t s_wcnt[8][256];
     __shared__ uint32_t s_blk[256];
     __shared__ uint32_t s_glob[256];
@@ -92,16 +94,16 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
     __syncthreads();
     const unsigned bid = s_bid;
     const unsigned long long n = clamp_count(count, cap);
-    const unsigned long long base = (unsigned long long)bid * kSortTile;
+    const unsigned long long base = (unsigned long long)bid * kTileKeys;
     if (base >= n) return;
     uint32_t *st = status + 1;
 
     // load in warp-striped order: item j of lane l is base + warp*512 + j*32 + l
-    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+    uint32_t key[ITEMS], val[ITEMS], rank[ITEMS];
     const unsigned lt_mask = (1u << lane) - 1u;
 #pragma unroll
-    for (int j = 0; j < kSortItems; j++) {
-        const unsigned long long idx = base + (unsigned long long)warp * (32 * kSortItems) + j * 32 + lane;
+    for (int j = 0; j < ITEMS; j++) {
+        const unsigned long long idx = base + (unsigned long long)warp * (32 * ITEMS) + j * 32 + lane;
         const bool valid = idx < n;
         key[j] = valid ? keys_in[idx] : 0u;
         val[j] = valid ? (VALS_IDENTITY ? (uint32_t)idx : vals_in[idx]) : 0u;
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
     __syncthreads();
     // scatter into shared memory in block-sorted order
 #pragma unroll
-    for (int j = 0; j < kSortItems; j++) {
+    for (int j = 0; j < ITEMS; j++) {
         if (rank[j] == 0xffffffffu) continue;
         const uint32_t dd = (key[j] >> shift) & 255u;
         const uint32_t pos = s_blk[dd] + s_wcnt[warp][dd] + rank[j];
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
     }
     __syncthreads();
     const unsigned long long rem = n - base;
-    const int nvalid = rem < (unsigned long long)kSortTile ? (int)rem : kSortTile;
+    const int nvalid = rem < (unsigned long long)kTileKeys ? (int)rem : kTileKeys;
     for (int i = tid; i < nvalid; i += kSortThreads) {
         const uint32_t k = s_keys[i];
         const uint32_t dd = (k >> shift) & 255u;
@@ -184,16 +186,41 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
     }
 }
 
+template <int ITEMS>
+static cudaError_t radix_passes(cudaStream_t st, uint32_t *keys[2], uint32_t *vals[2], const unsigned long long *count,
+                                unsigned long long cap, int passes, bool vals_identity, uint32_t *status,
+                                const uint32_t *off, DevCounters *ctr, int &out_buf)
+{
+    const unsigned long long blocks = (cap + kSortThreads * ITEMS - 1) / (kSortThreads * ITEMS);
+    cudaError_t e;
+    int src = 0;
+    for (int p = 0; p < passes; p++) {
+        const int dst = src ^ 1;
+        if ((e = cudaMemsetAsync(status, 0, (blocks * 256 + 1) * sizeof(uint32_t), st)) != cudaSuccess) return e;
+        if (vals_identity && p == 0)
+            radix_pass_kernel<ITEMS, true, true><<<(unsigned)blocks, kSortThreads, 0, st>>>(
+                keys[src], vals[src], keys[dst], vals[dst], count, cap, 8 * p, off + 256 * p, status, ctr);
+        else
+            radix_pass_kernel<ITEMS, false, true><<<(unsigned)blocks, kSortThreads, 0, st>>>(
+                keys[src], vals[src], keys[dst], vals[dst], count, cap, 8 * p, off + 256 * p, status, ctr);
+        note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        src = dst;
+    }
+    out_buf = src;
+    return cudaSuccess;
+}
+
 // LSD radix sort of (key, value) pairs, `bits` significant key bits, count on
 // the device (clamped to cap).  keys[0]/vals[0] hold the input; the sorted
 // result lands in keys[out_buf]/vals[out_buf].  With vals_identity the input
-// values are the item indices and vals[0] is not read.
+// values are the item indices and vals[0] is not read.  Blocks rank
+// ws->sort_items * 256 keys (the workspace's tuning, 2048 or 4096).
 cudaError_t launch_radix_sort(gs_workspace *ws, cudaStream_t st, uint32_t *keys[2], uint32_t *vals[2],
                               const unsigned long long *count, unsigned long long cap, int bits, bool vals_identity,
                               bool /*unused*/, int &out_buf)
 {
     const int passes = bits <= 0 ? 1 : (bits + 7) / 8;
-    const unsigned long long blocks = (cap + kSortTile - 1) / kSortTile;
     cudaError_t e;
     out_buf = 0;
     if (cap == 0) return cudaSuccess;
@@ -204,38 +231,23 @@ cudaError_t launch_radix_sort(gs_workspace *ws, cudaStream_t st, uint32_t *keys[
     note_launch();
     radix_offsets_kernel<<<1, 256, 0, st>>>(ws->rx_hist, ws->rx_off, passes);
     note_launch();
-    int src = 0;
-    for (int p = 0; p < passes; p++) {
-        const int dst = src ^ 1;
-        if ((e = cudaMemsetAsync(ws->rx_status, 0, (blocks * 256 + 1) * sizeof(uint32_t), st)) != cudaSuccess)
-            return e;
-        const bool ident = vals_identity && p == 0;
-        if (ident)
-            radix_pass_kernel<true, true><<<(unsigned)blocks, kSortThreads, 0, st>>>(
-                keys[src], vals[src], keys[dst], vals[dst], count, cap, 8 * p, ws->rx_off + 256 * p, ws->rx_status,
-                ws->ctr);
-        else
-            radix_pass_kernel<false, true><<<(unsigned)blocks, kSortThreads, 0, st>>>(
-                keys[src], vals[src], keys[dst], vals[dst], count, cap, 8 * p, ws->rx_off + 256 * p, ws->rx_status,
-                ws->ctr);
-        note_launch();
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        src = dst;
-    }
-    out_buf = src;
-    return cudaSuccess;
+    if (ws->sort_items == 8)
+        return radix_passes<8>(st, keys, vals, count, cap, passes, vals_identity, ws->rx_status, ws->rx_off, ws->ctr,
+                               out_buf);
+    return radix_passes<kSortItems>(st, keys, vals, count, cap, passes, vals_identity, ws->rx_status, ws->rx_off,
+                                    ws->ctr, out_buf);
 }
 
-// The same LSD sort with every scratch buffer passed in (no workspace):
-// status [ceil(cap / 4096) * 256 + 1] uint32, hist and off [4 * 256] uint32,
-// ctr receives a timeout error.  Used by the entry point without allocation.
+// The same LSD sort with every scratch buffer passed in (no workspace) and
+// 4096-key blocks: status [ceil(cap / 4096) * 256 + 1] uint32, hist and off
+// [4 * 256] uint32, ctr receives a timeout error.  Used by the entry point
+// without allocation.
 cudaError_t launch_radix_sort_scratch(cudaStream_t st, uint32_t *keys[2], uint32_t *vals[2],
                                       const unsigned long long *count, unsigned long long cap, int bits,
                                       bool vals_identity, uint32_t *status, uint32_t *hist, uint32_t *off,
                                       DevCounters *ctr, int &out_buf)
 {
     const int passes = bits <= 0 ? 1 : (bits + 7) / 8;
-    const unsigned long long blocks = (cap + kSortTile - 1) / kSortTile;
     cudaError_t e;
     out_buf = 0;
     if (cap == 0) return cudaSuccess;
@@ -246,22 +258,7 @@ cudaError_t launch_radix_sort_scratch(cudaStream_t st, uint32_t *keys[2], uint32
     note_launch();
     radix_offsets_kernel<<<1, 256, 0, st>>>(hist, off, passes);
     note_launch();
-    int src = 0;
-    for (int p = 0; p < passes; p++) {
-        const int dst = src ^ 1;
-        if ((e = cudaMemsetAsync(status, 0, (blocks * 256 + 1) * sizeof(uint32_t), st)) != cudaSuccess) return e;
-        if (vals_identity && p == 0)
-            radix_pass_kernel<true, true><<<(unsigned)blocks, kSortThreads, 0, st>>>(
-                keys[src], vals[src], keys[dst], vals[dst], count, cap, 8 * p, off + 256 * p, status, ctr);
-        else
-            radix_pass_kernel<false, true><<<(unsigned)blocks, kSortThreads, 0, st>>>(
-                keys[src], vals[src], keys[dst], vals[dst], count, cap, 8 * p, off + 256 * p, status, ctr);
-        note_launch();
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        src = dst;
-    }
-    out_buf = src;
-    return cudaSuccess;
+    return radix_passes<kSortItems>(st, keys, vals, count, cap, passes, vals_identity, status, off, ctr, out_buf);
 }
 
 // ---- emission -------------------------------------------------------------

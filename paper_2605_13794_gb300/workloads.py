@@ -1,0 +1,296 @@
+"""Drivers of the batched workloads beside the single-view training step:
+
+* a multi-view training loop (several equal-size views per step, the whole
+  step captured once as a CUDA graph), against the same steps run eagerly and
+  against the plain per-view path (one view at a time, dense gradients
+  accumulated, then a dense Adam step);
+* one batched render of many cameras of mixed resolution, its tile shape and
+  sort chunk chosen by the autotuner;
+* the serving loop under Poisson arrivals.
+
+Each returns a dict of measured figures; bench.py prints them.  Scenes and
+cameras come from synth (seeded, city-shaped)."""
+from __future__ import annotations
+
+import statistics
+
+import numpy as np
+import torch
+
+from . import binding as B
+from . import synth
+from .autotune import Autotuner, max_tiles
+from .serve import Server, poisson_requests
+from .train import TrainStep
+
+LOD = dict(lod_d0=1600.0, lod_Lmax=5)
+LRS = [1.6e-4 * 100.0, 5e-3, 1e-3, 5e-2, 2.5e-3]
+
+
+def _events():
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _capacity_probe(gt, cams, params):
+    """Records and instances a batch needs, from one preprocess + bin_sort."""
+    n = gt.n
+    probe = B.Workspace(max_gaussians=n, max_records=min(n * len(cams), 1 << 27),
+                        max_instances=(1 << 30) - 1, max_tiles=max_tiles(cams),
+                        max_pixels=sum(c.width * c.height for c in cams), max_cameras=len(cams), forward_only=True)
+    probe.preprocess(gt, cams, params)
+    probe.bin_sort()
+    c = probe.counts()  # *_needed hold the full counts even past the probe's capacity
+    probe.close()
+    if c["records_needed"] > (1 << 27):
+        raise RuntimeError("batch needs more than 2^27 records")
+    return c
+
+
+# ---- multi-view training loop -------------------------------------------------------
+
+def view_pool(n_views: int, seed: int, width: int, height: int):
+    cams = []
+    for k in range(n_views):
+        cams.append(synth.aerial_camera(seed * 1000 + k, width=width, height=height))
+    return cams
+
+
+def train_batch_workload(n: int = 20_000_000, views: int = 8, width: int = 1600, height: int = 1200,
+                         steps: int = 50, warmup: int = 3, pool: int = 64, per_view_steps: int = 5) -> dict:
+    g = synth.city_scene(n, seed=3)
+    target_scene = synth.perturbed_copy(g, seed=4)
+    cams = view_pool(pool, 4, width, height)
+    params = B.RenderParams(lod_enable=True, **LOD)
+    gt_target = B.GaussianTensors.from_host(target_scene)
+    # targets: the perturbed scene rendered through the same path
+    cap = _capacity_probe(gt_target, cams[:views], params)
+    rec = min(n * views, int(cap["records_needed"] * 1.5) + 8192)
+    inst = min((1 << 30) - 1, int(cap["instances_needed"] * 1.5) + 65536)
+    rws = B.Workspace(max_gaussians=n, max_records=rec, max_instances=inst,
+                      max_tiles=views * B.tiles_of(cams[0]), max_pixels=views * width * height, max_cameras=views,
+                      forward_only=True)
+    targets = torch.empty(pool, 3, height, width, device="cuda")
+    for k in range(0, pool, views):
+        rws.preprocess(gt_target, cams[k:k + views], params)
+        rws.bin_sort()
+        rws.render_fwd(targets[k:k + views].view(-1))
+    rws.sync_status()
+    rws.close()
+    del gt_target
+
+    def batch(k):
+        idx = [(k * views + j) % pool for j in range(views)]
+        return [cams[i] for i in idx], targets[idx]
+
+    capd = dict(max_records=rec, max_instances=inst)
+    ga, gb = B.GaussianTensors.from_host(g), B.GaussianTensors.from_host(g)
+    c0, t0 = batch(0)
+    eager = TrainStep(ga, c0, t0, params, LRS, capacity=capd)
+    graph = TrainStep(gb, c0, t0, params, LRS, capacity=capd)
+    eager.run(step=1)
+    graph.run(step=1)
+    graph.capture()
+    for k in range(1, 1 + warmup):
+        cm, tg = batch(k)
+        eager.set_views(cm, tg)
+        eager.run()
+        graph.set_views(cm, tg)
+        graph.replay()
+    torch.cuda.synchronize()
+    # timed: the same steps, eager then replayed (uploads included in both)
+    losses_e, losses_g = [], []
+    e0, e1 = _events()
+    e0.record()
+    for k in range(1 + warmup, 1 + warmup + steps):
+        cm, tg = batch(k)
+        eager.set_views(cm, tg)
+        eager.run()
+        losses_e.append(eager.loss.clone())
+    e1.record()
+    torch.cuda.synchronize()
+    eager_ms = e0.elapsed_time(e1) / steps
+    g0, g1 = _events()
+    g0.record()
+    for k in range(1 + warmup, 1 + warmup + steps):
+        cm, tg = batch(k)
+        graph.set_views(cm, tg)
+        graph.replay()
+        losses_g.append(graph.loss.clone())
+    g1.record()
+    torch.cuda.synchronize()
+    graph_ms = g0.elapsed_time(g1) / steps
+    eager.ws.sync_status()
+    graph.ws.sync_status()
+    le = torch.cat(losses_e).cpu().numpy()
+    lg = torch.cat(losses_g).cpu().numpy()
+    same_params = all(torch.equal(a, b) for a, b in zip(ga.params(), gb.params()))
+    # the plain per-view path: one view at a time, dense gradients, dense Adam
+    per_view = _per_view_path(g, cams, targets, params, views, per_view_steps, capd)
+    pix = views * width * height
+    return {"n": n, "views": views, "width": width, "height": height, "steps": steps,
+            "graph_ms": graph_ms, "eager_ms": eager_ms, "graph_mpix_per_s": pix / graph_ms / 1e3,
+            "eager_mpix_per_s": pix / eager_ms / 1e3, "per_view_ms": per_view["ms"],
+            "per_view_mpix_per_s": pix / per_view["ms"] / 1e3,
+            "graph_equals_eager": bool(np.array_equal(le, lg)) and same_params,
+            "loss_first": float(le[0]), "loss_last": float(le[-1]),
+            "per_view_vs_batched_loss_rel": per_view["loss_rel"]}
+
+
+class _PerViewPath:
+    """The plain per-view path: one view at a time (preprocess, sort, render,
+    loss, dense backward accumulated over the views), then a dense Adam step."""
+
+    def __init__(self, g, cams, targets, params, views, capd):
+        n = g.n
+        self.H, self.W = targets.shape[2], targets.shape[3]
+        self.cams, self.targets, self.params, self.views = cams, targets, params, views
+        self.ws = B.Workspace(max_gaussians=n, max_records=capd["max_records"], max_instances=capd["max_instances"],
+                              max_tiles=B.tiles_of(cams[0]), max_pixels=self.W * self.H)
+        self.rgb = torch.empty(3 * self.H * self.W, device="cuda")
+        self.dL = torch.empty_like(self.rgb)
+        self.l1 = torch.zeros(1, device="cuda")
+        self.loss = torch.zeros(1, device="cuda")
+
+    def step(self, gt, m, v, grads, idx, step_no):
+        ws, H, W, views = self.ws, self.H, self.W, self.views
+        self.loss.zero_()
+        for j, i in enumerate(idx):
+            ws.preprocess(gt, [self.cams[i]], self.params)
+            ws.bin_sort()
+            ws.render_fwd(self.rgb)
+            ws.photometric_loss(self.rgb.view(1, 3, H, W), self.targets[i:i + 1], 0.2, self.l1, self.dL)
+            self.dL.mul_(1.0 / views)  # the batch loss is the mean over its views
+            self.loss.add_(self.l1, alpha=1.0 / views)
+            # Eq. 5 on the last view's visible set only: the per-view path
+            # never sees the batch's visible set as a whole
+            ws.render_bwd(gt, self.dL, grads, accumulate=j > 0, scale_reg_beta=10.0 if j == views - 1 else 0.0)
+        B.adam_step([(p, gr, mm, vv, LRS[q], 0.9, 0.999, 1e-15) for q, (p, gr, mm, vv) in
+                     enumerate(zip(gt.params(), grads.params(), m.params(), v.params()))], step=step_no)
+        return self.loss
+
+
+def _per_view_path(g, cams, targets, params, views, steps, capd):
+    """The first `steps` steps of the batched loop from the same start, one
+    view at a time; returns its ms per step and the largest relative
+    difference of its losses from the batched eager loop's."""
+    path = _PerViewPath(g, cams, targets, params, views, capd)
+    pool = targets.shape[0]
+    # warm-up on scratch state: every kernel of the path is loaded before timing
+    scratch = B.GaussianTensors.from_host(g)
+    path.step(scratch, scratch.zeros_like(), scratch.zeros_like(), scratch.zeros_like(), list(range(views)), 1)
+    torch.cuda.synchronize()
+    del scratch
+    gt = B.GaussianTensors.from_host(g)
+    m, v, grads = gt.zeros_like(), gt.zeros_like(), gt.zeros_like()
+    ref = TrainStep(B.GaussianTensors.from_host(g), cams[:views], targets[:views], params, LRS, capacity=capd)
+    rel, total_ms = 0.0, 0.0
+    for k in range(steps):
+        idx = [(k * views + j) % pool for j in range(views)]
+        e0, e1 = _events()
+        e0.record()
+        loss = path.step(gt, m, v, grads, idx, k + 1)
+        e1.record()
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        ref.set_views([cams[i] for i in idx], targets[idx])
+        ref.run(step=k + 1)
+        torch.cuda.synchronize()
+        rel = max(rel, abs(loss.item() - ref.loss.item()) / abs(ref.loss.item()))
+    path.ws.close()
+    return {"ms": total_ms / steps, "loss_rel": rel}
+
+
+# ---- batched render of many cameras -------------------------------------------------
+
+def batched_render_workload(n: int = 10_000_000, n_cams: int = 64, reps: int = 10, warmup: int = 2,
+                            tune_cache: str | None = None) -> dict:
+    g = synth.city_scene(n, seed=3)
+    cams = synth.mixed_cameras(n_cams, seed=7)
+    gt = B.GaussianTensors.from_host(g)
+    params = B.RenderParams(lod_enable=True, **LOD)
+    cap = _capacity_probe(gt, cams, params)
+    rec = min(n * n_cams, int(cap["records_needed"] * 1.3) + 8192, (1 << 30) - 1)
+    inst = min((1 << 30) - 1, int(cap["instances_needed"] * 1.3) + 65536)
+    pix = sum(c.width * c.height for c in cams)
+    ws = B.Workspace(max_gaussians=n, max_records=rec, max_instances=inst, max_tiles=max_tiles(cams),
+                     max_pixels=pix, max_cameras=n_cams)
+    choice = Autotuner(tune_cache).tune(ws, gt, cams, params, backward=False, reps=2)
+    p = choice.apply(ws, params)
+    rgb = torch.empty(3 * pix, device="cuda")
+    for _ in range(warmup):
+        ws.preprocess(gt, cams, p)
+        ws.bin_sort()
+        ws.render_fwd(rgb)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        e0, e1 = _events()
+        e0.record()
+        ws.preprocess(gt, cams, p)
+        ws.bin_sort()
+        ws.render_fwd(rgb)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    counts = ws.counts()
+    # every view of the batch equals its render alone (checked for a few views)
+    same = True
+    offs = np.cumsum([0] + [c.width * c.height for c in cams])
+    solo = B.Workspace(max_gaussians=n, max_records=min(n, rec), max_instances=inst,
+                       max_tiles=max_tiles(cams[:1] + [max(cams, key=lambda c: c.width * c.height)]),
+                       max_pixels=max(c.width * c.height for c in cams), forward_only=True)
+    solo.set_sort_chunk(choice.sort_chunk)
+    for k in (0, n_cams // 2, n_cams - 1):
+        one = torch.empty(3 * cams[k].width * cams[k].height, device="cuda")
+        solo.preprocess(gt, [cams[k]], p)
+        solo.bin_sort()
+        solo.render_fwd(one)
+        same &= bool(torch.equal(one, rgb[3 * offs[k]:3 * offs[k + 1]]))
+    solo.close()
+    ms = statistics.median(times)
+    return {"n": n, "cameras": n_cams, "pixels": int(pix), "ms": ms, "mpix_per_s": pix / ms / 1e3,
+            "mgaussian_views_per_s": n * n_cams / ms / 1e3, "records": counts["n_records"],
+            "instances": counts["n_instances"], "tile": f"{choice.tile_w}x{choice.tile_h}",
+            "sort_chunk": choice.sort_chunk, "tuning_ms": choice.trials, "views_equal_alone": same,
+            "resolutions": sorted({f"{c.width}x{c.height}" for c in cams})}
+
+
+# ---- serving -------------------------------------------------------------------------
+
+def serving_workload(n: int = 30_000_000, rate: float = 200.0, duration: float = 60.0, seed: int = 5,
+                     key_budget: float = 40e9, max_batch: int = 64) -> dict:
+    g = synth.city_scene(n, seed=3)
+    gt = B.GaussianTensors.from_host(g)
+    sizes = ((1280, 720), (1920, 1080), (2560, 1440), (3840, 2160))
+
+    def camera(rng):
+        w, h = sizes[rng.integers(len(sizes))]
+        return synth.aerial_camera(int(rng.integers(1 << 30)), width=w, height=h)
+
+    params = B.RenderParams(lod_enable=True, **LOD)
+    reqs = poisson_requests(rate, duration, camera, seed=seed)
+    server = Server(gt, params, key_budget_bytes=key_budget, max_batch=max_batch,
+                    max_pixels=16 * 3840 * 2160)
+    # warm-up on a few requests outside the timed run
+    warm = poisson_requests(rate, 0.2, camera, seed=seed + 1)
+    server.run(warm, realtime=False)
+    server.batches.clear()
+    stats = server.run(reqs, realtime=True)
+    # a request alone renders the same image as in its batch
+    probe = Server(gt, params, key_budget_bytes=4e9, max_batch=8, max_pixels=8 * 3840 * 2160, keep_images=True)
+    few = reqs[:6]
+    for r in few:
+        r.done = r.start = None
+    probe.run(few, realtime=False)
+    alone = Server(gt, params, key_budget_bytes=4e9, max_batch=1, max_pixels=3840 * 2160, keep_images=True)
+    solo = [dataclasses_replace(r) for r in few[:3]]
+    alone.run(solo, realtime=False)
+    same = all(torch.equal(a.image, b.image) for a, b in zip(few[:3], solo))
+    stats.update({"n": n, "rate": rate, "duration_s": duration, "key_budget_gb": key_budget / 1e9,
+                  "alone_equals_batched": same})
+    return stats
+
+
+def dataclasses_replace(r):
+    import dataclasses
+    return dataclasses.replace(r, start=None, done=None, image=None, batch=-1)

@@ -9,7 +9,8 @@ import oracle as O
 from paper_2605_13794_gb300 import binding as B
 from paper_2605_13794_gb300 import synth
 from paper_2605_13794_gb300.train import TrainStep
-from tests.gpu_helpers import GpuRun, assert_grad_close, assert_param_grad_close, gpu_params, grads_to_host
+from tests.gpu_helpers import (GpuRun, assert_grad_close, assert_param_grad_close, capacity_for, gpu_params,
+                               grads_to_host)
 from tests.test_gpu_parity import _compare_view
 
 pytestmark = pytest.mark.gpu
@@ -172,3 +173,105 @@ def test_multi_view_train_step_against_oracle():
         big = np.abs(og[name]) > 1e-3 * np.abs(og[name]).max()
         assert big.sum() > 100
         np.testing.assert_allclose(got[big], p_ref[big], rtol=0, atol=1e-6 * max(1.0, np.abs(p0).max()))
+
+
+def test_sort_chunk_leaves_results_unchanged():
+    g = synth.plain_scene(6000, seed=57)
+    cams = _uneven_cameras()
+    P = O.Params()
+    a = GpuRun(g, cams, P)
+    ws = B.Workspace(**capacity_for(g.n, cams))
+    ws.set_sort_chunk(2048)
+    b = GpuRun(g, cams, P, ws=ws)
+    assert np.array_equal(a.sorted_vals, b.sorted_vals) and np.array_equal(a.ranges, b.ranges)
+    assert torch.equal(a.rgb, b.rgb) and np.array_equal(a.n_contrib, b.n_contrib)
+    with pytest.raises(B.GSError):
+        ws.set_sort_chunk(1000)
+
+
+def _mixed_cameras(n, seed, sizes=((64, 48), (128, 72), (192, 108), (256, 144), (384, 216))):
+    rng = np.random.default_rng(seed)
+    cams = []
+    for k in range(n):
+        w, h = sizes[rng.integers(len(sizes))]
+        eye = (rng.uniform(-0.8, 0.8), rng.uniform(-0.8, 0.8), rng.uniform(-1.5, -0.2))
+        cams.append(synth.look_at_camera(eye, (rng.uniform(-0.3, 0.3), rng.uniform(-0.3, 0.3), 4.0),
+                                         (0.0, -1.0, 0.0), w, h, rng.uniform(40.0, 80.0)))
+    return cams
+
+
+def test_each_view_of_a_batch_equals_its_render_alone():
+    # 64 cameras of mixed resolution in one call; every view is bit-identical
+    # to the same camera rendered on its own (per-tile lists keep the same
+    # order: depth bits, then Gaussian index)
+    g = synth.plain_scene(5000, seed=58)
+    cams = _mixed_cameras(64, 59)
+    P = O.Params()
+    batch = GpuRun(g, cams, P)
+    for k in (0, 7, 31, 63):
+        alone = GpuRun(g, [cams[k]], P)
+        assert np.array_equal(batch.image(k), alone.image(0)), k
+        assert np.array_equal(batch.T_final(k), alone.T_final(0)), k
+
+
+def test_autotuner_picks_and_caches(tmp_path):
+    from paper_2605_13794_gb300.autotune import SORT_CHUNKS, TILE_SHAPES, Autotuner, max_tiles
+    g = B.GaussianTensors.from_host(synth.plain_scene(6000, seed=60))
+    cams = _mixed_cameras(8, 61)
+    ws = B.Workspace(max_gaussians=g.n, max_records=g.n * len(cams), max_instances=64 * g.n * len(cams),
+                     max_tiles=max_tiles(cams), max_pixels=sum(c.width * c.height for c in cams),
+                     max_cameras=len(cams))
+    path = str(tmp_path / "tune.json")
+    choice = Autotuner(path).tune(ws, g, cams, B.RenderParams(), reps=2)
+    assert (choice.tile_w, choice.tile_h) in TILE_SHAPES and choice.sort_chunk in SORT_CHUNKS
+    assert len(choice.trials) == len(TILE_SHAPES) * len(SORT_CHUNKS)
+    assert choice.ms == min(choice.trials.values())
+    again = Autotuner(path).tune(ws, g, cams, B.RenderParams())  # from the cache file
+    assert (again.tile_w, again.tile_h, again.sort_chunk) == (choice.tile_w, choice.tile_h, choice.sort_chunk)
+    # the chosen configuration renders what the oracle renders with that tiling
+    P = O.Params(tile_w=choice.tile_w, tile_h=choice.tile_h)
+    run = GpuRun(synth.plain_scene(6000, seed=60), cams[:2], P)
+    g64 = O.gaussians64(synth.plain_scene(6000, seed=60))
+    for c in range(2):
+        _compare_view(run, c, g64, cams[c], P)
+
+
+def _small_request_camera(rng):
+    w, h = [(64, 48), (128, 72), (192, 108), (256, 144)][rng.integers(4)]
+    eye = (rng.uniform(-0.8, 0.8), rng.uniform(-0.8, 0.8), rng.uniform(-1.5, -0.2))
+    return synth.look_at_camera(eye, (0.0, 0.0, 4.0), (0.0, -1.0, 0.0), w, h, 60.0)
+
+
+def test_serving_batches_match_renders_alone():
+    from paper_2605_13794_gb300.serve import Server, poisson_requests
+    g_host = synth.plain_scene(5000, seed=62)
+    g = B.GaussianTensors.from_host(g_host)
+    reqs = poisson_requests(200.0, 1.0, _small_request_camera, seed=5)
+    assert 150 < len(reqs) < 250
+    server = Server(g, B.RenderParams(), key_budget_bytes=2e9, max_batch=16, max_pixels=16 * 256 * 144,
+                    keep_images=True)
+    stats = server.run(reqs, realtime=False)   # all waiting at once: full batches
+    assert stats["requests"] == len(reqs) and stats["batches"] >= len(reqs) // 16
+    assert all(r.done is not None and r.latency >= 0 for r in reqs)
+    assert 0 < stats["p50_ms"] <= stats["p99_ms"]
+    P = O.Params()
+    for r in (reqs[0], reqs[17], reqs[-1]):
+        alone = GpuRun(g_host, [r.cam], P)
+        assert torch.equal(r.image, alone.rgb), r.rid
+
+
+def test_serving_splits_a_batch_that_overflows():
+    from paper_2605_13794_gb300.serve import Server, poisson_requests
+    g = B.GaussianTensors.from_host(synth.plain_scene(5000, seed=63))
+    reqs = poisson_requests(200.0, 0.2, _small_request_camera, seed=6)
+    # a key budget of a few thousand instances with a low initial estimate:
+    # batches overflow, are split and retried
+    server = Server(g, B.RenderParams(), key_budget_bytes=24 * 60_000, max_batch=8, max_pixels=8 * 256 * 144,
+                    inst_per_pixel=0.01, keep_images=True)
+    stats = server.run(reqs, realtime=False)
+    assert stats["requests"] == len(reqs) and all(r.done is not None for r in reqs)
+    assert stats["overflow_retries"] > 0
+    P = O.Params()
+    g_host = synth.plain_scene(5000, seed=63)
+    for r in (reqs[0], reqs[-1]):
+        assert torch.equal(r.image, GpuRun(g_host, [r.cam], P).rgb), r.rid
