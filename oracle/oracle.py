@@ -16,7 +16,11 @@ plain array code:
 * the photometric loss of Eq. 4 (L1 + lambda (1 - SSIM), SSIM with an 11x11
   Gaussian window, sigma 1.5, zero "same" padding) and the scale regulariser of
   Eq. 5, with their gradients;
-* Adam (Kingma and Ba), the optimizer the paper's "standard 3DGS" training uses.
+* Adam (Kingma and Ba), the optimizer the paper's "standard 3DGS" training uses;
+* the model-level operations of Sec. 3.2 and 3.3: the two pruning passes
+  (importance-weighted sampling without replacement, the 99 %-mass cut of s),
+  density control (clone / split) with the phi_i reweighting and the LOD
+  inheritance rule, and order-preserving compaction.
 """
 from __future__ import annotations
 
@@ -412,3 +416,140 @@ def adam_step(p, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-15):
     vhat = v / (1 - beta2 ** step)
     p = p - lr * mhat / (np.sqrt(vhat) + eps)
     return p, m, v
+
+
+# ---- model level: simplification passes and density control --------------------
+#
+# Sec. 3.2: an importance pass yields s_i; Pass 1 keeps a fixed fraction by
+# importance-weighted sampling without replacement, Pass 2 keeps the smallest
+# prefix of Gaussians by descending s carrying 99 % of the total s.  Density
+# control (standard 3DGS adaptive density control, Sec. 3) tests the averaged
+# view-space positional gradient, reweighted by phi_i = c^vis_i / (c^rad_i + eps)
+# (Sec. 3.2), clones small selected Gaussians and splits large ones; the LOD
+# label follows the inheritance rule of Sec. 3.3 (clone keeps the parent's
+# level, split increments it by one).
+
+def prune_mass(s, mass: float = 0.99) -> np.ndarray:
+    """Pass 2: keep mask of the smallest prefix by descending s (ties by lower
+    index) whose summed s reaches `mass` of the total; s = 0 is never kept."""
+    return visible_top_mass(s, mass)
+
+
+def prune_sample(s, expo, k: int) -> np.ndarray:
+    """Pass 1: importance-weighted sampling of k Gaussians without replacement,
+    with probability proportional to s at every draw.  Drawn as exponential
+    clocks: Gaussian i fires at expo_i / s_i (expo_i ~ Exp(1), given), and the
+    k earliest are kept (ties by lower index; s_i = 0 never fires before a
+    Gaussian with s > 0).  The times are taken in FP32, as the device takes them."""
+    s32 = np.asarray(s, np.float32)
+    e32 = np.asarray(expo, np.float32)
+    with np.errstate(divide="ignore"):
+        t = np.where(s32 > 0, e32 / np.where(s32 > 0, s32, np.float32(1)), np.float32(np.inf)).astype(np.float32)
+    order = np.lexsort((np.arange(len(t)), t))
+    keep = np.zeros(len(t), bool)
+    keep[order[:k]] = True
+    return keep
+
+
+def successive_sampling_probs(s, k: int) -> np.ndarray:
+    """Exact inclusion probabilities of drawing k of len(s) items without
+    replacement with probability proportional to s at every draw (enumeration
+    of ordered draws; tiny inputs only)."""
+    s = np.asarray(s, np.float64)
+    n = len(s)
+    incl = np.zeros(n)
+
+    def rec(chosen, p):
+        if len(chosen) == k:
+            for i in chosen:
+                incl[i] += p
+            return
+        rest = [i for i in range(n) if i not in chosen]
+        tot = s[rest].sum()
+        for i in rest:
+            rec(chosen + [i], p * s[i] / tot)
+
+    rec([], 1.0)
+    return incl
+
+
+@dataclasses.dataclass
+class DensifyParams:
+    grad_threshold: float = 0.0002  # on the averaged |dL/d(u,v)| (pixels), after phi reweighting
+    dense_scale: float = 0.01       # largest axis at or below: clone; above: split
+    min_opacity: float = 0.005      # Gaussians below are removed
+    split_shrink: float = 1.6       # a split child's scales are the parent's / 1.6 (two children)
+    n_levels: int = 6               # LOD labels 0..n_levels-1
+    eps: float = 1e-6
+
+
+def densify(g: dict, absgrad, denom, cvis, crad, noise, P: DensifyParams):
+    """One density-control step on per-Gaussian rows (the layout of synth:
+    mean (n,3), log_scale (n,3), quat (n,4), opacity_logit (n,), sh (n,16,3),
+    lod (n,), m and v: dicts of the same rows).  noise: (n, 2, 3) N(0,1)
+    samples, used for the two children of a split parent.
+
+    Output rows in parent order; per parent: removed (opacity < min_opacity):
+    none; kept: itself; clone: itself then its copy; split: its two children
+    mu + R(q) (s * z), log_scale - log(1.6), same q, opacity and SH, level + 1
+    (capped at n_levels - 1).  A kept or cloned parent keeps its Adam moments,
+    every new Gaussian starts from zero moments.  Returns (rows, m, v, kind)
+    with kind per input: 0 removed, 1 kept, 2 cloned, 3 split."""
+    n = len(g["opacity_logit"])
+    absgrad = np.asarray(absgrad, np.float64)
+    denom = np.asarray(denom, np.float64)
+    grad = np.where(denom > 0, absgrad / np.where(denom > 0, denom, 1.0), 0.0)
+    phi = np.asarray(cvis, np.float64) / (np.asarray(crad, np.float64) + P.eps)
+    score = grad * phi
+    opacity = 1.0 / (1.0 + np.exp(-np.asarray(g["opacity_logit"], np.float64)))
+    smax = np.exp(np.asarray(g["log_scale"], np.float64)).max(axis=1)
+    sel = score >= P.grad_threshold
+    kind = np.where(opacity < P.min_opacity, 0, np.where(~sel, 1, np.where(smax <= P.dense_scale, 2, 3)))
+    names = ("mean", "log_scale", "quat", "opacity_logit", "sh")
+    out = []  # (row, m, v) per output Gaussian, in order
+
+    def zeros(row):
+        return {k: np.zeros_like(row[k]) for k in names}
+
+    for i in range(n):
+        if kind[i] == 0:
+            continue
+        row = {k: np.asarray(g[k][i], np.float64) for k in names}
+        row["lod"] = int(g["lod"][i])
+        mi = {k: np.asarray(g["m"][k][i], np.float64) for k in names}
+        vi = {k: np.asarray(g["v"][k][i], np.float64) for k in names}
+        if kind[i] in (1, 2):
+            out.append((row, mi, vi))
+        if kind[i] == 2:
+            out.append((dict(row), zeros(row), zeros(row)))
+        if kind[i] == 3:
+            R = _quat_to_rot(row["quat"] / np.linalg.norm(row["quat"]))
+            s = np.exp(row["log_scale"])
+            for c in range(2):
+                child = dict(row)
+                child["mean"] = row["mean"] + R @ (s * np.asarray(noise[i, c], np.float64))
+                child["log_scale"] = row["log_scale"] - np.log(P.split_shrink)
+                child["lod"] = min(row["lod"] + 1, P.n_levels - 1)
+                out.append((child, zeros(row), zeros(row)))
+
+    def stack(j, key):
+        shape = (0,) + np.shape(g[key])[1:]
+        return np.array([o[j][key] for o in out]) if out else np.zeros(shape)
+
+    rows = {k: stack(0, k) for k in names}
+    rows["lod"] = np.array([o[0]["lod"] for o in out], np.int64)
+    return rows, {k: stack(1, k) for k in names}, {k: stack(2, k) for k in names}, kind
+
+
+def _quat_to_rot(q):
+    """Rotation matrix of the unit quaternion (w, x, y, z)."""
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def compact(rows: dict, keep) -> dict:
+    """The rows whose keep bit is set, in order."""
+    keep = np.asarray(keep, bool)
+    return {k: np.asarray(v)[keep] for k, v in rows.items()}
