@@ -72,6 +72,9 @@ typedef struct {
  * rows, no loss maps); the backward, the loss and the compact Adam step
  * return GS_ERR_INVALID_ARG on it. */
 #define GS_CAP_FORWARD_ONLY 1
+/* gs_capacity.flags: also hold scratch for the model-level calls (pruning,
+ * compaction, densification; about 28 bytes per Gaussian of max_gaussians). */
+#define GS_CAP_MODEL_OPS 2
 
 /* Gaussian parameters, one row per Gaussian for each attribute (the layout of
  * PyTorch 3DGS code), FP32:
@@ -284,6 +287,73 @@ int gs_photometric_loss(gs_workspace *ws, const float *image, const float *targe
 /* One Adam step (Kingma and Ba, bias-corrected) over n_groups (host array,
  * <= GS_MAX_ADAM_GROUPS) parameter groups; step counts from 1. */
 int gs_adam_step(const gs_adam_group *groups, int32_t n_groups, int32_t step, gs_stream stream);
+
+/* ---- model level (Sec. 3.2 simplification passes, density control with the
+ * Sec. 3.3 LOD inheritance).  These calls need a workspace created with
+ * GS_CAP_MODEL_OPS and n <= max_gaussians. */
+
+/* A whole model: parameters in the rows of gs_gaussians plus the Adam moments
+ * (rows of the same shapes; members of m and v may be NULL, then they are not
+ * carried, or read as zero) and the LOD labels (NULL: all level 0). */
+typedef struct {
+    int64_t n;
+    float *mean;
+    float *log_scale;
+    float *quat;
+    float *opacity_logit;
+    float *sh;
+    uint8_t *lod;
+    gs_gaussian_grads m;
+    gs_gaussian_grads v;
+} gs_model;
+
+/* Pass 1 of Sec. 3.2: keeps k of n Gaussians by importance-weighted sampling
+ * without replacement (probability proportional to s at every draw), drawn as
+ * exponential clocks: Gaussian i fires at expo[i] / s[i], expo[i] ~ Exp(1)
+ * supplied by the caller, and the k earliest are kept (equal times by lower
+ * index; s = 0 fires after every s > 0).  keep_bits: [ceil(n/32)] written. */
+int gs_prune_sample(gs_workspace *ws, const float *s, const float *expo, int64_t n, int64_t k, uint32_t *keep_bits,
+                    gs_stream stream);
+
+/* Pass 2 of Sec. 3.2: keeps the smallest prefix of Gaussians by descending s
+ * (equal s by lower index) whose summed s reaches mass (0.99) of the total;
+ * s = 0 is never kept.  The prefix sums are FP64 in a fixed association. */
+int gs_prune_mass(gs_workspace *ws, const float *s, int64_t n, float mass, uint32_t *keep_bits, gs_stream stream);
+
+/* Order-preserving compaction: the rows of src whose keep bit is set, written
+ * to dst (capacity dst_capacity rows; its n is ignored); *n_out (device
+ * int64) receives the count.  src and dst must not overlap. */
+int gs_compact(gs_workspace *ws, const gs_model *src, const uint32_t *keep_bits, gs_model *dst, int64_t dst_capacity,
+               int64_t *n_out, gs_stream stream);
+
+/* Density control (standard 3DGS clone / split) with the phi reweighting of
+ * Sec. 3.2: a Gaussian is selected when (absgrad / denom) * cvis / (crad + eps)
+ * >= grad_threshold (absgrad: summed |dL/d(u,v)| of its records, as
+ * gs_render_bwd accumulates it; denom: views with a record, see
+ * gs_count_views; cvis, crad: gs_importance's accumulators).  Output, in
+ * parent order: a Gaussian with opacity < min_opacity is removed; an
+ * unselected one is kept; a selected one whose largest scale is <= dense_scale
+ * is kept and followed by a copy; a larger one is replaced by two children
+ * mu + R(q) (s * z_c), log-scale - log(split_shrink), the other parameters
+ * copied, LOD level + 1 (capped at n_levels - 1) -- the inheritance rule of
+ * Sec. 3.3 (a clone keeps its parent's level).  noise: [n][2][3] N(0,1)
+ * samples z_c, supplied by the caller.  Kept and cloned parents keep their
+ * Adam moments, new Gaussians start from zero.  dst needs up to 2n rows. */
+typedef struct {
+    float grad_threshold;
+    float dense_scale;
+    float min_opacity;
+    float split_shrink; /* 1.6 */
+    float eps;          /* 1e-6 */
+    int32_t n_levels;   /* LOD labels 0..n_levels-1 */
+} gs_densify_params;
+int gs_densify(gs_workspace *ws, const gs_model *src, const float *absgrad, const uint32_t *denom,
+               const uint32_t *cvis, const uint32_t *crad, const float *noise, const gs_densify_params *params,
+               gs_model *dst, int64_t dst_capacity, int64_t *n_out, gs_stream stream);
+
+/* counts[i] += number of cameras of the last gs_preprocess in which Gaussian i
+ * has a record (the densification denominator of a training step). */
+int gs_count_views(gs_workspace *ws, uint32_t *counts, gs_stream stream);
 
 /* The Cull column of one view (the selection step of gs_importance) without
  * any allocation and without a workspace.  The paper has no counterpart: this

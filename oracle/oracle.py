@@ -26,6 +26,7 @@ from __future__ import annotations
 
 import ctypes
 import dataclasses
+import math
 import os
 import subprocess
 
@@ -496,15 +497,7 @@ def densify(g: dict, absgrad, denom, cvis, crad, noise, P: DensifyParams):
     every new Gaussian starts from zero moments.  Returns (rows, m, v, kind)
     with kind per input: 0 removed, 1 kept, 2 cloned, 3 split."""
     n = len(g["opacity_logit"])
-    absgrad = np.asarray(absgrad, np.float64)
-    denom = np.asarray(denom, np.float64)
-    grad = np.where(denom > 0, absgrad / np.where(denom > 0, denom, 1.0), 0.0)
-    phi = np.asarray(cvis, np.float64) / (np.asarray(crad, np.float64) + P.eps)
-    score = grad * phi
-    opacity = 1.0 / (1.0 + np.exp(-np.asarray(g["opacity_logit"], np.float64)))
-    smax = np.exp(np.asarray(g["log_scale"], np.float64)).max(axis=1)
-    sel = score >= P.grad_threshold
-    kind = np.where(opacity < P.min_opacity, 0, np.where(~sel, 1, np.where(smax <= P.dense_scale, 2, 3)))
+    kind = densify_kinds(g["opacity_logit"], g["log_scale"], absgrad, denom, cvis, crad, P)
     names = ("mean", "log_scale", "quat", "opacity_logit", "sh")
     out = []  # (row, m, v) per output Gaussian, in order
 
@@ -539,6 +532,25 @@ def densify(g: dict, absgrad, denom, cvis, crad, noise, P: DensifyParams):
     rows = {k: stack(0, k) for k in names}
     rows["lod"] = np.array([o[0]["lod"] for o in out], np.int64)
     return rows, {k: stack(1, k) for k in names}, {k: stack(2, k) for k in names}, kind
+
+
+def densify_kinds(opacity_logit, log_scale, absgrad, denom, cvis, crad, P: DensifyParams) -> np.ndarray:
+    """The branch of every Gaussian: 0 removed (opacity < min_opacity), 1 kept,
+    2 cloned, 3 split.  The decisions are taken in FP32, the kernel's
+    precision, on quantities it forms the same way: the averaged gradient
+    absgrad / denom (0 without a view), phi = c^vis / (c^rad + eps), their
+    product against the threshold; opacity < min_opacity as the logit against
+    logit(min_opacity), the largest scale against dense_scale as the largest
+    log-scale against log(dense_scale) (both thresholds from FP64, rounded)."""
+    f = np.float32
+    absgrad, denom = np.asarray(absgrad, f), np.asarray(denom, np.int64)
+    grad = np.where(denom > 0, absgrad / np.where(denom > 0, denom, 1).astype(f), f(0)).astype(f)
+    phi = (np.asarray(cvis, np.int64).astype(f) / (np.asarray(crad, np.int64).astype(f) + f(P.eps))).astype(f)
+    score = (grad * phi).astype(f)
+    sel = score >= f(P.grad_threshold)
+    low = np.asarray(opacity_logit, f) < f(math.log(P.min_opacity / (1.0 - P.min_opacity)))
+    small = np.asarray(log_scale, f).max(axis=1) <= f(math.log(P.dense_scale))
+    return np.where(low, 0, np.where(~sel, 1, np.where(small, 2, 3))).astype(np.int64)
 
 
 def _quat_to_rot(q):

@@ -21,6 +21,7 @@ GS_OK, GS_ERR_INVALID_ARG, GS_ERR_OOM, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_TIME
 GS_MAX_CAMERAS = 64
 GS_TILE = 16
 GS_CAP_FORWARD_ONLY = 1
+GS_CAP_MODEL_OPS = 2
 (GS_BUF_REC_GAUSSIAN, GS_BUF_REC_CAMERA, GS_BUF_REC_RECT, GS_BUF_REC_TILES, GS_BUF_REC_DEPTH, GS_BUF_REC_XY_CONIC,
  GS_BUF_REC_C_OPAC_RG, GS_BUF_REC_B_LO, GS_BUF_SORTED_VALUES, GS_BUF_TILE_RANGES, GS_BUF_N_CONTRIB) = range(11)
 
@@ -28,7 +29,8 @@ EXPORTS = ("gs_default_params", "gs_last_error", "gs_workspace_create", "gs_work
            "gs_preprocess", "gs_bin_sort", "gs_render_fwd", "gs_render_bwd", "gs_importance", "gs_photometric_loss",
            "gs_adam_step", "gs_sync_status", "gs_workspace_counts", "gs_clear_error", "gs_workspace_buffer",
            "gs_kernel_launches", "gs_render_bwd_adam", "gs_render_bwd_compact", "gs_adam_step_compact",
-           "gs_visible_set_static", "gs_upload_cameras", "gs_preprocess_uploaded", "gs_workspace_set_sort_chunk")
+           "gs_visible_set_static", "gs_upload_cameras", "gs_preprocess_uploaded", "gs_workspace_set_sort_chunk",
+           "gs_prune_sample", "gs_prune_mass", "gs_compact", "gs_densify", "gs_count_views")
 
 
 class GSError(RuntimeError):
@@ -52,6 +54,17 @@ class GSGaussians(ctypes.Structure):
 class GSGaussianGrads(ctypes.Structure):
     _fields_ = [("mean", ctypes.c_void_p), ("log_scale", ctypes.c_void_p), ("quat", ctypes.c_void_p),
                 ("opacity_logit", ctypes.c_void_p), ("sh", ctypes.c_void_p)]
+
+
+class GSModel(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("mean", ctypes.c_void_p), ("log_scale", ctypes.c_void_p),
+                ("quat", ctypes.c_void_p), ("opacity_logit", ctypes.c_void_p), ("sh", ctypes.c_void_p),
+                ("lod", ctypes.c_void_p), ("m", GSGaussianGrads), ("v", GSGaussianGrads)]
+
+
+class GSDensifyParams(ctypes.Structure):
+    _fields_ = [("grad_threshold", ctypes.c_float), ("dense_scale", ctypes.c_float), ("min_opacity", ctypes.c_float),
+                ("split_shrink", ctypes.c_float), ("eps", ctypes.c_float), ("n_levels", ctypes.c_int32)]
 
 
 class GSCamera(ctypes.Structure):
@@ -103,6 +116,11 @@ def lib() -> ctypes.CDLL:
         L.gs_preprocess.argtypes = [vp, vp, vp, i32, vp, vp, vp]
         L.gs_upload_cameras.argtypes = [vp, vp, i32, vp, vp]
         L.gs_workspace_set_sort_chunk.argtypes = [vp, i32]
+        L.gs_prune_sample.argtypes = [vp, vp, vp, i64, i64, vp, vp]
+        L.gs_prune_mass.argtypes = [vp, vp, i64, ctypes.c_float, vp, vp]
+        L.gs_compact.argtypes = [vp, vp, vp, vp, i64, vp, vp]
+        L.gs_densify.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, i64, vp, vp]
+        L.gs_count_views.argtypes = [vp, vp, vp]
         L.gs_preprocess_uploaded.argtypes = [vp, vp, vp, vp, vp]
         L.gs_bin_sort.argtypes = [vp, vp]
         L.gs_render_fwd.argtypes = [vp, vp, vp, vp]
@@ -216,6 +234,41 @@ class GaussianTensors:
                                _ptr(self.sh))
 
 
+@dataclasses.dataclass
+class ModelTensors:
+    """A whole model on the device: parameters, Adam moments and LOD labels."""
+
+    g: GaussianTensors
+    m: GaussianTensors | None
+    v: GaussianTensors | None
+
+    @property
+    def n(self) -> int:
+        return self.g.n
+
+    @staticmethod
+    def empty(n: int, with_moments: bool = True, device="cuda") -> "ModelTensors":
+        e = lambda *shape: torch.empty(*shape, device=device)
+        mk = lambda: GaussianTensors(e(n, 3), e(n, 3), e(n, 4), e(n), e(n, 16, 3), None)
+        g = mk()
+        g.lod = torch.empty(n, dtype=torch.uint8, device=device)
+        return ModelTensors(g, mk() if with_moments else None, mk() if with_moments else None)
+
+    def head(self, k: int) -> "ModelTensors":
+        """The first k rows (views, no copy)."""
+        cut = lambda t: None if t is None else GaussianTensors(t.mean[:k], t.log_scale[:k], t.quat[:k],
+                                                              t.opacity_logit[:k], t.sh[:k],
+                                                              None if t.lod is None else t.lod[:k])
+        return ModelTensors(cut(self.g), cut(self.m), cut(self.v))
+
+    def c(self) -> GSModel:
+        g = self.g
+        none = GSGaussianGrads(None, None, None, None, None)
+        return GSModel(g.n, _ptr(g.mean), _ptr(g.log_scale), _ptr(g.quat), _ptr(g.opacity_logit), _ptr(g.sh),
+                       _ptr(g.lod), self.m.c_grads() if self.m is not None else none,
+                       self.v.c_grads() if self.v is not None else none)
+
+
 def camera_c(cam) -> GSCamera:
     c = GSCamera()
     c.R = (ctypes.c_float * 9)(*np.asarray(cam.R, np.float32).ravel())
@@ -234,9 +287,9 @@ class Workspace:
     """Owns a gs_workspace (all scratch of the render path) on the current device."""
 
     def __init__(self, max_gaussians: int, max_records: int, max_instances: int, max_tiles: int,
-                 max_pixels: int, max_cameras: int = 1, forward_only: bool = False):
+                 max_pixels: int, max_cameras: int = 1, forward_only: bool = False, model_ops: bool = False):
         self.cap = GSCapacity(max_gaussians, max_records, max_instances, max_tiles, max_pixels, max_cameras,
-                              GS_CAP_FORWARD_ONLY if forward_only else 0)
+                              (GS_CAP_FORWARD_ONLY if forward_only else 0) | (GS_CAP_MODEL_OPS if model_ops else 0))
         self._ws = ctypes.c_void_p()
         _check(lib().gs_workspace_create(ctypes.byref(self.cap), ctypes.byref(self._ws)))
         self.cams = []
@@ -337,6 +390,34 @@ class Workspace:
         assert C == 3
         _check(lib().gs_photometric_loss(self._ws, _ptr(image), _ptr(target), B, H, W, float(lam), _ptr(loss_out),
                                          _ptr(dL_dimage), _stream(stream)))
+
+    # ---- model level ----------------------------------------------------------------
+    def prune_sample(self, s, expo, k: int, keep_bits, stream=None):
+        """Pass 1: keep k Gaussians, importance-weighted sampling without
+        replacement (exponential clocks expo / s; expo ~ Exp(1))."""
+        _check(lib().gs_prune_sample(self._ws, _ptr(s), _ptr(expo), s.numel(), int(k), _ptr(keep_bits),
+                                     _stream(stream)))
+
+    def prune_mass(self, s, keep_bits, mass: float = 0.99, stream=None):
+        """Pass 2: keep the smallest prefix by descending s carrying `mass` of it."""
+        _check(lib().gs_prune_mass(self._ws, _ptr(s), s.numel(), float(mass), _ptr(keep_bits), _stream(stream)))
+
+    def compact(self, src: "ModelTensors", keep_bits, dst: "ModelTensors", n_out, stream=None):
+        sc, dc = src.c(), dst.c()
+        _check(lib().gs_compact(self._ws, ctypes.byref(sc), _ptr(keep_bits), ctypes.byref(dc), dst.n, _ptr(n_out),
+                                _stream(stream)))
+
+    def densify(self, src: "ModelTensors", absgrad, denom, cvis, crad, noise, dst: "ModelTensors", n_out,
+                grad_threshold=0.0002, dense_scale=0.01, min_opacity=0.005, split_shrink=1.6, eps=1e-6,
+                n_levels=6, stream=None):
+        sc, dc = src.c(), dst.c()
+        p = GSDensifyParams(grad_threshold, dense_scale, min_opacity, split_shrink, eps, n_levels)
+        _check(lib().gs_densify(self._ws, ctypes.byref(sc), _ptr(absgrad), _ptr(denom), _ptr(cvis), _ptr(crad),
+                                _ptr(noise), ctypes.byref(p), ctypes.byref(dc), dst.n, _ptr(n_out),
+                                _stream(stream)))
+
+    def count_views(self, counts, stream=None):
+        _check(lib().gs_count_views(self._ws, _ptr(counts), _stream(stream)))
 
     def counts(self, stream=None) -> dict:
         c = GSCounts()

@@ -50,6 +50,7 @@ struct Offsets {
     size_t tkey0, tkey1, tval0, tval1, slots, ranges, n_contrib, T_final, imp_w, imp_a, sel_cum;
     size_t selk0, selk1, selv0, selv1, loss_maps, loss_partial, lb_status, rx_status, rx_hist, rx_off, red_partial,
         ctr, d_cams, d_adam_step, d_adam_coef;
+    size_t mkey0, mkey1, mval0, mval1, mcum, mbsum, mrx_status, mlb, mhist, moff, mctr;
     size_t total;
     size_t lb_words, rx_words, red_words, loss_partial_words;
 };
@@ -112,6 +113,18 @@ Offsets plan(const gs_capacity &c)
     o.d_cams = L.take<gs::CamTable>(1);
     o.d_adam_step = L.take<int>(1);
     o.d_adam_coef = L.take<float>(2 * GS_MAX_ADAM_GROUPS);
+    const size_t NM = (c.flags & GS_CAP_MODEL_OPS) ? N : 0; // model-level scratch
+    o.mkey0 = L.take<uint32_t>(NM);
+    o.mkey1 = L.take<uint32_t>(NM);
+    o.mval0 = L.take<uint32_t>(NM);
+    o.mval1 = L.take<uint32_t>(NM);
+    o.mcum = L.take<double>(NM);
+    o.mbsum = L.take<double>(NM ? NM / 4096 + 2 : 0);
+    o.mrx_status = L.take<uint32_t>(NM ? (NM / (gs::kSortThreads * 8) + 1) * 256 + 1 : 0);
+    o.mlb = L.take<unsigned long long>(NM ? NM / 256 + 3 : 0);
+    o.mhist = L.take<uint32_t>(4 * 256);
+    o.moff = L.take<uint32_t>(4 * 256);
+    o.mctr = L.take<gs::DevCounters>(1);
     o.total = (L.off + 255) & ~(size_t)255;
     return o;
 }
@@ -235,9 +248,19 @@ int gs_workspace_create(const gs_capacity *cap, gs_workspace **out)
     ws->d_cams = (gs::CamTable *)(b + o.d_cams);
     ws->d_adam_step = (int *)(b + o.d_adam_step);
     ws->d_adam_coef = (float *)(b + o.d_adam_coef);
+    ws->mkey[0] = (uint32_t *)(b + o.mkey0); ws->mkey[1] = (uint32_t *)(b + o.mkey1);
+    ws->mval[0] = (uint32_t *)(b + o.mval0); ws->mval[1] = (uint32_t *)(b + o.mval1);
+    ws->mcum = (double *)(b + o.mcum);
+    ws->mbsum = (double *)(b + o.mbsum);
+    ws->mrx_status = (uint32_t *)(b + o.mrx_status);
+    ws->mlb = (unsigned long long *)(b + o.mlb);
+    ws->mhist = (uint32_t *)(b + o.mhist);
+    ws->moff = (uint32_t *)(b + o.moff);
+    ws->mctr = (gs::DevCounters *)(b + o.mctr);
     e = cudaMemset(ws->ctr, 0, sizeof(gs::DevCounters));
     if (e == cudaSuccess) e = cudaMemset(ws->d_cams, 0, sizeof(gs::CamTable));
     if (e == cudaSuccess) e = cudaMemset(ws->d_adam_step, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ws->mctr, 0, sizeof(gs::DevCounters));
     if (e == cudaSuccess) e = cudaMallocHost(&ws->h_stage, gs_workspace::kStageSlots * sizeof(gs::CamTable));
     for (int k = 0; e == cudaSuccess && k < gs_workspace::kStageSlots; k++) {
         e = cudaEventCreateWithFlags(&ws->stage_ev[k], cudaEventDisableTiming);
@@ -553,11 +576,94 @@ int gs_adam_step(const gs_adam_group *groups, int32_t n_groups, int32_t step, gs
     return GS_OK;
 }
 
+static int model_ops_check(gs_workspace *ws, int64_t n, const char *who)
+{
+    if (!ws) return fail(GS_ERR_INVALID_ARG, "%s: NULL workspace", who);
+    if (!(ws->cap.flags & GS_CAP_MODEL_OPS))
+        return fail(GS_ERR_INVALID_ARG, "%s: the workspace was created without GS_CAP_MODEL_OPS", who);
+    if (n < 0 || n > ws->cap.max_gaussians)
+        return fail(GS_ERR_CAPACITY, "%s: n = %lld outside [0, max_gaussians = %lld]", who, (long long)n,
+                    (long long)ws->cap.max_gaussians);
+    return GS_OK;
+}
+
+static bool model_ok(const gs_model *m)
+{
+    return m && m->mean && m->log_scale && m->quat && m->opacity_logit && m->sh;
+}
+
+int gs_prune_sample(gs_workspace *ws, const float *s, const float *expo, int64_t n, int64_t k, uint32_t *keep_bits,
+                    gs_stream stream)
+{
+    int rc = model_ops_check(ws, n, "gs_prune_sample");
+    if (rc != GS_OK) return rc;
+    if (n > 0 && (!s || !expo || !keep_bits)) return fail(GS_ERR_INVALID_ARG, "gs_prune_sample: NULL argument");
+    if (k < 0) return fail(GS_ERR_INVALID_ARG, "gs_prune_sample: k < 0");
+    if (n == 0) return GS_OK;
+    CK(gs::launch_prune_sample(ws, (cudaStream_t)stream, s, expo, n, k, keep_bits), "gs_prune_sample");
+    return GS_OK;
+}
+
+int gs_prune_mass(gs_workspace *ws, const float *s, int64_t n, float mass, uint32_t *keep_bits, gs_stream stream)
+{
+    int rc = model_ops_check(ws, n, "gs_prune_mass");
+    if (rc != GS_OK) return rc;
+    if (n > 0 && (!s || !keep_bits)) return fail(GS_ERR_INVALID_ARG, "gs_prune_mass: NULL argument");
+    if (!(mass > 0.f) || mass > 1.f) return fail(GS_ERR_INVALID_ARG, "gs_prune_mass: mass must be in (0, 1]");
+    if (n == 0) return GS_OK;
+    CK(gs::launch_prune_mass(ws, (cudaStream_t)stream, s, n, mass, keep_bits), "gs_prune_mass");
+    return GS_OK;
+}
+
+int gs_compact(gs_workspace *ws, const gs_model *src, const uint32_t *keep_bits, gs_model *dst, int64_t dst_capacity,
+               int64_t *n_out, gs_stream stream)
+{
+    if (!src) return fail(GS_ERR_INVALID_ARG, "gs_compact: NULL src");
+    int rc = model_ops_check(ws, src->n, "gs_compact");
+    if (rc != GS_OK) return rc;
+    if (!n_out || !keep_bits || (src->n > 0 && (!model_ok(src) || !model_ok(dst))))
+        return fail(GS_ERR_INVALID_ARG, "gs_compact: NULL argument");
+    if (src->mean == dst->mean) return fail(GS_ERR_INVALID_ARG, "gs_compact: src and dst overlap");
+    CK(gs::launch_compact(ws, (cudaStream_t)stream, *src, keep_bits, *dst, dst_capacity, (long long *)n_out),
+       "gs_compact");
+    return GS_OK;
+}
+
+int gs_densify(gs_workspace *ws, const gs_model *src, const float *absgrad, const uint32_t *denom,
+               const uint32_t *cvis, const uint32_t *crad, const float *noise, const gs_densify_params *params,
+               gs_model *dst, int64_t dst_capacity, int64_t *n_out, gs_stream stream)
+{
+    if (!src || !params) return fail(GS_ERR_INVALID_ARG, "gs_densify: NULL argument");
+    int rc = model_ops_check(ws, src->n, "gs_densify");
+    if (rc != GS_OK) return rc;
+    if (!n_out || (src->n > 0 && (!model_ok(src) || !model_ok(dst) || !absgrad || !denom || !cvis || !crad || !noise)))
+        return fail(GS_ERR_INVALID_ARG, "gs_densify: NULL argument");
+    if (src->mean == dst->mean) return fail(GS_ERR_INVALID_ARG, "gs_densify: src and dst overlap");
+    if (!(params->min_opacity > 0.f && params->min_opacity < 1.f) || !(params->dense_scale > 0.f) ||
+        !(params->split_shrink > 0.f) || params->n_levels < 1 || params->n_levels > 256)
+        return fail(GS_ERR_INVALID_ARG, "gs_densify: parameters out of range");
+    CK(gs::launch_densify(ws, (cudaStream_t)stream, *src, absgrad, denom, cvis, crad, noise, *params, *dst,
+                          dst_capacity, (long long *)n_out),
+       "gs_densify");
+    return GS_OK;
+}
+
+int gs_count_views(gs_workspace *ws, uint32_t *counts, gs_stream stream)
+{
+    if (!ws || !counts) return fail(GS_ERR_INVALID_ARG, "gs_count_views: NULL argument");
+    if (!ws->have_preprocess) return fail(GS_ERR_INVALID_ARG, "gs_count_views: no preprocess on this workspace");
+    CK(gs::launch_count_views(ws, (cudaStream_t)stream, counts), "gs_count_views");
+    return GS_OK;
+}
+
 int gs_sync_status(gs_workspace *ws, gs_stream stream)
 {
     gs_counts c;
     int rc = gs_workspace_counts(ws, &c, stream);
     if (rc != GS_OK) return rc;
+    int merr[2] = {0, 0}; // error word of the model-level calls
+    CK(cudaMemcpy(merr, &ws->mctr->error, sizeof(merr), cudaMemcpyDeviceToHost), "gs_sync_status");
+    if (merr[0]) return fail(merr[0], "device error %d in a model-level call (site %d)", merr[0], merr[1]);
     if (c.error)
         return fail(c.error, "device error %d at site %d (records needed %lld of %lld, instances needed %lld of %lld)",
                     c.error, c.error_site, (long long)c.records_needed, (long long)ws->cap.max_records,
@@ -585,6 +691,7 @@ int gs_clear_error(gs_workspace *ws, gs_stream stream)
 {
     if (!ws) return fail(GS_ERR_INVALID_ARG, "gs_clear_error: NULL workspace");
     CK(cudaMemsetAsync(&ws->ctr->error, 0, 2 * sizeof(int), (cudaStream_t)stream), "gs_clear_error");
+    CK(cudaMemsetAsync(&ws->mctr->error, 0, 2 * sizeof(int), (cudaStream_t)stream), "gs_clear_error");
     return GS_OK;
 }
 

@@ -18,7 +18,7 @@ constexpr int kMaxLod = 15;             // largest supported L_max
 
 // Error sites recorded next to the error word (which kernel gave up).
 enum ErrorSite {
-    kSitePreprocess = 1, kSiteEmit = 2, kSiteRadix = 3, kSiteSelect = 4, kSiteScanF64 = 5,
+    kSitePreprocess = 1, kSiteEmit = 2, kSiteRadix = 3, kSiteSelect = 4, kSiteScanF64 = 5, kSiteModel = 6,
 };
 
 // Device counters of one workspace.
@@ -244,6 +244,14 @@ struct gs_workspace {
     gs::DevCounters *ctr;
     gs::CamTable *d_cams;  // device copy of the uploaded cameras, read by every kernel
     int sort_items;        // keys per thread of a radix pass: 16 (4096-key blocks) or 8 (2048)
+    // model-level scratch (GS_CAP_MODEL_OPS): sorts and scans over all Gaussians
+    uint32_t *mkey[2], *mval[2]; // [N]
+    double *mcum;                // [N]
+    double *mbsum;               // [N / 4096 + 2]
+    uint32_t *mrx_status;        // radix look-back, [(N / 2048 + 1) * 256 + 1]
+    unsigned long long *mlb;     // single-value look-back, [N / 256 + 3]
+    uint32_t *mhist, *moff;      // [4][256]
+    gs::DevCounters *mctr;       // item count (n_records) and errors of the model-level calls
     int *d_adam_step;      // device Adam step counter (graph-replayable optimizer step)
     float *d_adam_coef;    // [2][GS_MAX_ADAM_GROUPS] bias-corrected lr and 1/sqrt(1 - beta2^t)
     // host staging of camera uploads: a ring of pinned tables, each reused only
@@ -295,4 +303,14 @@ cudaError_t launch_importance(gs_workspace *ws, cudaStream_t st, float *w, uint3
 cudaError_t launch_loss(gs_workspace *ws, cudaStream_t st, const float *img, const float *tgt, int B, int H, int W,
                         float lambda, float *loss_out, float *dL);
 cudaError_t launch_adam(const gs_adam_group *groups, int n_groups, int step, cudaStream_t st);
+cudaError_t launch_prune_sample(gs_workspace *ws, cudaStream_t st, const float *s, const float *expo, long long n,
+                                long long k, uint32_t *keep);
+cudaError_t launch_prune_mass(gs_workspace *ws, cudaStream_t st, const float *s, long long n, float mass,
+                              uint32_t *keep);
+cudaError_t launch_count_views(gs_workspace *ws, cudaStream_t st, uint32_t *counts);
+cudaError_t launch_compact(gs_workspace *ws, cudaStream_t st, const gs_model &src, const uint32_t *keep,
+                           const gs_model &dst, long long dst_cap, long long *n_out);
+cudaError_t launch_densify(gs_workspace *ws, cudaStream_t st, const gs_model &src, const float *absgrad,
+                           const uint32_t *denom, const uint32_t *cvis, const uint32_t *crad, const float *noise,
+                           const gs_densify_params &p, const gs_model &dst, long long dst_cap, long long *n_out);
 } // namespace gs
