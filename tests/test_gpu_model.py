@@ -142,18 +142,24 @@ def test_count_views_and_multi_view_sweep():
     acc = O.new_importance(g.n)
     culls = []
     gcount = np.zeros(g.n, np.int64)
+    bound = np.zeros(g.n)  # what undecided fragments can move s by
     for cam in cams:
         f = O.forward_view(g64, cam, P)
+        c, w, a = f["gcount"].astype(np.float64), f["w"], f["a"]
         gcount += f["gcount"]
+        # per flagged pixel a moves by at most 1 and w by at most one fragment's alpha T (< 1e-2)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            hi = np.where(a - c > 0, (w + 1e-2 * c) / (a - c), np.inf) - np.where(a > 0, w / np.maximum(a, 1), 0)
+        bound += np.where(c > 0, hi, 0.0)
         culls.append(O.importance_update(acc, f["w"], f["a"], f["proj"])["cull"])
     assert (sw["crad"].cpu().numpy() != acc["crad"]).sum() <= 3  # projection decisions at a tie may differ
-    # s over Gaussians on no flagged pixel of any view; the others within the
-    # change one undecided fragment can make to w / a
+    # s over Gaussians on no flagged pixel of any view within the gradient
+    # rule; every Gaussian within 1e-3 of its s plus what its undecided
+    # fragments can move
     free = gcount == 0
-    assert free.mean() > 0.8
     s_gpu = sw["s"].double().cpu().numpy()
     assert_grad_close("s", np.where(free, s_gpu, 0.0), np.where(free, acc["s"], 0.0))
-    assert np.all(np.abs(s_gpu - acc["s"])[~free] <= 5e-2 * acc["s"][~free] + 1e-6)
+    assert np.all(np.abs(s_gpu - acc["s"]) <= 1e-3 * acc["s"] + bound + 1e-9)
     cvis = sw["cvis"].cpu().numpy()
     assert np.abs(cvis - acc["cvis"]).max() <= 1 and (cvis != acc["cvis"]).mean() < 1e-2
     cull = sw["cull"].cpu().numpy().view(np.uint32)
