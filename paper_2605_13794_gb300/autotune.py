@@ -1,9 +1,10 @@
 """A small autotuner for the render path: it times every tile shape the
 kernels support (16x16, 32x8, 8x32, 32x16) with both radix-sort chunkings
-(2048 and 4096 keys per block) on the caller's own workload and keeps the
+(1024, 2048 and 4096 keys per block) on the caller's own workload and keeps the
 fastest, cached per workload class (Gaussian count and camera resolutions).
 
-The sort chunk leaves every result unchanged.  The tile shape decides which
+The sort chunk (1024, 2048 or 4096 keys per block) leaves every result
+unchanged.  The tile shape decides which
 Gaussians are listed for which pixels (through the 3-sigma tile rectangle), so
 images from different shapes agree to rounding except where a fragment of
 opacity above 0.35 falls just outside one shape's rectangle."""
@@ -20,7 +21,7 @@ import torch
 from . import binding as B
 
 TILE_SHAPES = ((16, 16), (32, 8), (8, 32), (32, 16))
-SORT_CHUNKS = (2048, 4096)
+SORT_CHUNKS = (1024, 2048, 4096)
 
 
 def max_tiles(cams) -> int:

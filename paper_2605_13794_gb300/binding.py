@@ -337,7 +337,8 @@ class Workspace:
                                             _stream(stream)))
 
     def set_sort_chunk(self, keys_per_block: int):
-        """Keys per block of the radix passes (2048 or 4096); results are unchanged."""
+        """Keys per block of the radix passes (1024, 2048, 4096, or 0 to pick by
+        size); results are unchanged."""
         _check(lib().gs_workspace_set_sort_chunk(self._ws, int(keys_per_block)))
         self.sort_chunk = int(keys_per_block)
 

@@ -46,7 +46,7 @@ struct Layout {
 };
 
 struct Offsets {
-    size_t cand_g, cand_mask, rec_first, cgrad, rec_g, rec_cam, rd0, rd1, rd2, rect, tt, inst_off, clampm, rgrad, dkey0, dkey1, dval0, dval1;
+    size_t cand_g, cand_mask, gate_g, gate_mask, rec_first, cgrad, rec_g, rec_cam, rd0, rd1, rd2, rect, tt, inst_off, clampm, rgrad, dkey0, dkey1, dval0, dval1;
     size_t tkey0, tkey1, tval0, tval1, slots, ranges, n_contrib, T_final, imp_w, imp_a, sel_cum;
     size_t selk0, selk1, selv0, selv1, loss_maps, loss_partial, lb_status, rx_status, rx_hist, rx_off, red_partial,
         ctr, d_cams, d_adam_step, d_adam_coef;
@@ -63,6 +63,8 @@ Offsets plan(const gs_capacity &c)
     const size_t T = (size_t)c.max_tiles, P = (size_t)c.max_pixels;
     o.cand_g = L.take<uint32_t>(N);
     o.cand_mask = L.take<unsigned long long>(N);
+    o.gate_g = L.take<uint32_t>(N);
+    o.gate_mask = L.take<unsigned long long>(N);
     o.rec_first = L.take<uint32_t>(N);
     const bool fwd_only = (c.flags & GS_CAP_FORWARD_ONLY) != 0;
     o.cgrad = L.take<float>(fwd_only ? 0 : R * gs::kGradRow);
@@ -102,7 +104,7 @@ Offsets plan(const gs_capacity &c)
     o.lb_words = nb + 1;
     o.lb_status = L.take<unsigned long long>(o.lb_words);
     const size_t items = (R > I ? R : I);
-    o.rx_words = (items / (gs::kSortThreads * 8) + 1) * 256 + 1; // for the smaller (2048-key) blocks
+    o.rx_words = (items / (gs::kSortThreads * 4) + 1) * 256 + 1; // for the smallest (1024-key) blocks
     o.rx_status = L.take<uint32_t>(o.rx_words);
     o.rx_hist = L.take<uint32_t>(4 * 256);
     o.rx_off = L.take<uint32_t>(4 * 256);
@@ -196,8 +198,11 @@ int gs_workspace_create(const gs_capacity *cap, gs_workspace **out)
     gs_workspace *ws = new (std::nothrow) gs_workspace();
     if (!ws) return fail(GS_ERR_OOM, "host allocation failed");
     ws->cap = *cap;
-    ws->sort_items = gs::kSortItems;
+    ws->sort_items = 0; // by the size of each sort
     cudaGetDevice(&ws->device);
+    if (cudaDeviceGetAttribute(&ws->sm_count, cudaDevAttrMultiProcessorCount, ws->device) != cudaSuccess ||
+        ws->sm_count < 1)
+        ws->sm_count = 152;
     cudaError_t e = cudaMalloc(&ws->base, o.total);
     if (e != cudaSuccess) {
         delete ws;
@@ -208,6 +213,8 @@ int gs_workspace_create(const gs_capacity *cap, gs_workspace **out)
     char *b = (char *)ws->base;
     ws->cand_g = (uint32_t *)(b + o.cand_g);
     ws->cand_mask = (unsigned long long *)(b + o.cand_mask);
+    ws->gate_g = (uint32_t *)(b + o.gate_g);
+    ws->gate_mask = (unsigned long long *)(b + o.gate_mask);
     ws->rec_first = (uint32_t *)(b + o.rec_first);
     ws->cgrad = (float *)(b + o.cgrad);
     ws->rec_g = (uint32_t *)(b + o.rec_g);
@@ -292,8 +299,8 @@ static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 int gs_workspace_set_sort_chunk(gs_workspace *ws, int32_t keys_per_block)
 {
     if (!ws) return fail(GS_ERR_INVALID_ARG, "gs_workspace_set_sort_chunk: NULL workspace");
-    if (keys_per_block != 2048 && keys_per_block != 4096)
-        return fail(GS_ERR_INVALID_ARG, "gs_workspace_set_sort_chunk: keys_per_block must be 2048 or 4096");
+    if (keys_per_block != 0 && keys_per_block != 1024 && keys_per_block != 2048 && keys_per_block != 4096)
+        return fail(GS_ERR_INVALID_ARG, "gs_workspace_set_sort_chunk: keys_per_block must be 0, 1024, 2048 or 4096");
     ws->sort_items = keys_per_block / gs::kSortThreads;
     return GS_OK;
 }

@@ -196,11 +196,14 @@ __device__ __forceinline__ T block_exclusive_scan_256(T v, T *smem_warp /*[8]*/,
 struct gs_workspace {
     gs_capacity cap;
     int device;
+    int sm_count;        // multiprocessors of the device (persistent grids)
     void *base;          // one device allocation, carved into the buffers below
     size_t bytes;
     // per Gaussian (candidates of the gate stage, in index order)
     uint32_t *cand_g;              // [N]
     unsigned long long *cand_mask; // [N] bit per camera
+    uint32_t *gate_g;              // [N] block-strided candidates of the gate's first pass
+    unsigned long long *gate_mask; // [N]
     uint32_t *rec_first;           // [N] first record of each Gaussian, ~0 when none
     float *cgrad;                  // [R][59] compact gradient rows (fused backward + Adam)
     // per record

@@ -11,6 +11,8 @@
 // only touch active work.  The integer decisions (gate, near cull, det sign,
 // radius, rectangle) are computed with explicitly rounded FP32 operations
 // (no contraction) so they are reproducible on any FP32 IEEE implementation.
+#include <algorithm>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -99,13 +101,16 @@ __device__ __forceinline__ float clampf(float x, float lo, float hi) { return x 
 // Distance LOD gate (Sec. 3.3, Eq. 1-2) in its squared-distance form:
 // keep level l iff l == 0, or l <= Lmax and |mu - c|^2 <= (d0 f^(0.5 - l))^2,
 // which is l <= clamp(round(log_f(d0 / d)), 0, Lmax) with half-away rounding.
-__device__ __forceinline__ bool lod_pass(const float m[3], int lod, const CamInfo &cam, const RenderConsts &rc)
+// thr2: the squared-distance thresholds of RenderConsts::lod_thr2 (a copy in
+// shared memory, so the level indexes it without a local-memory copy).
+__device__ __forceinline__ bool lod_pass(const float m[3], int lod, const CamInfo &cam, const RenderConsts &rc,
+                                         const float *thr2)
 {
     if (!rc.lod_enable || lod == 0) return true;
     if (lod > rc.lod_Lmax) return false;
     const float dx = FSUB(m[0], cam.campos[0]), dy = FSUB(m[1], cam.campos[1]), dz = FSUB(m[2], cam.campos[2]);
     const float d2 = FADD(FADD(FMUL(dx, dx), FMUL(dy, dy)), FMUL(dz, dz));
-    return d2 <= rc.lod_thr2[lod];
+    return d2 <= thr2[lod];
 }
 
 // Camera-space mean in float, for the gate only, with a bound on its distance
@@ -145,18 +150,20 @@ __device__ __forceinline__ void camera_point_d(const float m[3], const CamInfo &
 __device__ __forceinline__ bool maybe_on_screen(const float t[3], const float e[3], float smax, const CamInfo &cam,
                                                 int tw, int th, const RenderConsts &rc)
 {
+    // approximate reciprocals and square root (a few ulp): the margins below
+    // (1 % on lambda, 2 px on the radius, 1e-5 |u|) dwarf them
     const float tzl = t[2] - e[2]; // lower bound of the exact depth
-    if (!(tzl > 1e-6f)) return true;
-    const float itz = 1.f / t[2], itzl = 1.f / tzl;
+    const float itz = __fdividef(1.f, t[2]), itzl = __fdividef(1.f, tzl);
     const float u = cam.fx * t[0] * itz + cam.cx, v = cam.fy * t[1] * itz + cam.cy;
     const float lam = 1.01f * (cam.jbound * itzl * itzl * smax * smax + rc.dilation) + 0.33f;
-    const float R = 3.f * sqrtf(lam) + 2.f;
+    const float R = 3.003f * (lam * rsqrtf(lam)) + 2.f;
     // |d(tx / tz)| <= (e_x + |tx / tz| e_z) / tz_low
     const float du = 1.01f * cam.fx * (e[0] + fabsf(t[0] * itz) * e[2]) * itzl;
     const float dv = 1.01f * cam.fy * (e[1] + fabsf(t[1] * itz) * e[2]) * itzl;
     const float ru = R + du + 1e-5f * fabsf(u), rv = R + dv + 1e-5f * fabsf(v);
-    return !(u + ru < 0.f || u - ru >= (float)(cam.tiles_x * tw) || v + rv < 0.f ||
-             v - rv >= (float)(cam.tiles_y * th));
+    const bool off = u + ru < 0.f || u - ru >= (float)(cam.tiles_x * tw) || v + rv < 0.f ||
+                     v - rv >= (float)(cam.tiles_y * th);
+    return !(tzl > 1e-6f) || !off;
 }
 
 // Exact projection of one Gaussian into one camera, from the double-precision
@@ -258,6 +265,8 @@ struct PreOut {
     uint8_t *clampm;
     uint32_t *cand_g;
     unsigned long long *cand_mask;
+    uint32_t *gate_g;              // [N] block-strided candidates of the gate's first pass
+    unsigned long long *gate_mask; // [N]
     uint32_t *rec_first;           // first record of each Gaussian, ~0 when it has none
     unsigned long long *lb_status; // word 0: ticket
     DevCounters *ctr;
@@ -282,33 +291,53 @@ __device__ __forceinline__ void load_shape(const GaussPtrs &g, long long i, Gaus
     L.have_shape = true;
 }
 
-constexpr int kGateItems = 8; // Gaussians per thread of the gate kernel: 2048 per block
+constexpr int kGateItems = 4; // Gaussians per thread of the gate kernel: 1024 per block
+static_assert(kGateItems * 8 == 32, "the gate ranks its (item, warp) counts with one warp");
 
 __device__ __forceinline__ bool cull_bit(const PreOut &o, int c, long long i)
 {
     return o.cull ? ((o.cull[c * o.cull_words + (i >> 5)] >> (i & 31)) & 1u) : false;
 }
 
+// The cameras of the call, copied from the device table into shared memory
+// once per block (every Gaussian reads them).
+__device__ __forceinline__ void stage_cameras(const CamTable &ct, CamInfo *s_cams)
+{
+    const int words = ct.n * (int)(sizeof(CamInfo) / sizeof(int));
+    const int *src = reinterpret_cast<const int *>(ct.c);
+    int *dst = reinterpret_cast<int *>(s_cams);
+    for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+    __syncthreads();
+}
+
 // Stage 1, streaming over all Gaussians: the view gate (LOD, Cull), the near
 // plane and the conservative screen test -- everything that is cheap and
 // rejects most of a city scene -- producing an order-preserving list of
 // candidate Gaussians with a bit per camera that may still be active.
-// Thread t of block b owns Gaussians b*2048 + k*256 + t (k < 8).
-__global__ void __launch_bounds__(256) gate_kernel(GaussPtrs g, PreOut o, const CamTable *__restrict__ ctp,
-                                                   RenderConsts rc)
+// Thread t of block b owns Gaussians b*1024 + k*256 + t (k < 4).  Every load
+// a Gaussian may need (mean, level, log-scale, the Cull word of camera 0) is
+// issued up front, so a thread waits for memory once, not once per test.
+struct GateShared {
+    CamInfo cams[GS_MAX_CAMERAS];
+    float thr2[kMaxLod + 1];
+    unsigned cnt[kGateItems][8];
+    unsigned total;
+};
+
+__device__ __forceinline__ void gate_masks(const GaussPtrs &g, const PreOut &o, const CamTable &ct,
+                                           const RenderConsts &rc, GateShared &sh, long long block0,
+                                           unsigned long long mask[kGateItems])
 {
-    const CamTable &ct = *ctp;
-    __shared__ unsigned s_bid;
-    __shared__ unsigned s_cnt[kGateItems][8];
-    __shared__ unsigned s_total;
-    __shared__ unsigned long long s_base;
-    if (threadIdx.x == 0) s_bid = atomicAdd((unsigned *)o.lb_status, 1u);
-    __syncthreads();
-    const unsigned bid = s_bid;
+    const int ncam = ct.n, tw = ct.tile_w, th = ct.tile_h;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int l = 0; l <= kMaxLod; l++) sh.thr2[l] = rc.lod_thr2[l];
+    }
+    stage_cameras(ct, sh.cams);
     const long long n = g.n;
-    const long long block0 = (long long)bid * 256 * kGateItems;
-    float mx[kGateItems], my[kGateItems], mz[kGateItems];
+    float mx[kGateItems], my[kGateItems], mz[kGateItems], ls[kGateItems][3];
     int lod[kGateItems];
+    uint32_t cw[kGateItems];
 #pragma unroll
     for (int k = 0; k < kGateItems; k++) {
         const long long i = block0 + k * 256 + threadIdx.x;
@@ -316,62 +345,145 @@ __global__ void __launch_bounds__(256) gate_kernel(GaussPtrs g, PreOut o, const 
         mx[k] = ok ? g.mean[3 * i] : 0.f;
         my[k] = ok ? g.mean[3 * i + 1] : 0.f;
         mz[k] = ok ? g.mean[3 * i + 2] : 0.f;
+        ls[k][0] = ok ? g.log_scale[3 * i] : 0.f;
+        ls[k][1] = ok ? g.log_scale[3 * i + 1] : 0.f;
+        ls[k][2] = ok ? g.log_scale[3 * i + 2] : 0.f;
         lod[k] = (ok && rc.lod_enable && g.lod) ? (int)g.lod[i] : 0;
+        cw[k] = (ok && rc.cull_enable && o.cull) ? o.cull[i >> 5] : 0u;
     }
-    unsigned long long mask[kGateItems];
+    if (ncam == 1) {
+        // one camera: every test of every item evaluated without branches, so
+        // the four items' arithmetic interleaves
+        const CamInfo &cam = sh.cams[0];
 #pragma unroll
-    for (int k = 0; k < kGateItems; k++) {
-        mask[k] = 0;
-        const long long i = block0 + k * 256 + threadIdx.x;
-        if (i >= n) continue;
-        const float m[3] = {mx[k], my[k], mz[k]};
-        float smax = -1.f;
-        for (int c = 0; c < ct.n; c++) {
-            const CamInfo &cam = ct.c[c];
-            if (!lod_pass(m, lod[k], cam, rc)) continue;
-            if (rc.cull_enable && cull_bit(o, c, i)) continue;
+        for (int k = 0; k < kGateItems; k++) {
+            const long long i = block0 + k * 256 + threadIdx.x;
+            const float m[3] = {mx[k], my[k], mz[k]};
+            const bool lod_ok = lod_pass(m, lod[k], cam, rc, sh.thr2);
+            const bool culled = rc.cull_enable && ((cw[k] >> (i & 31)) & 1u);
             float t[3], te[3];
             camera_point(m, cam, t, te);
-            if (!(t[2] + te[2] > rc.znear)) continue; // the exact near test is the projection's
-            if (smax < 0.f)
-                smax = expf(fmaxf(g.log_scale[3 * i], fmaxf(g.log_scale[3 * i + 1], g.log_scale[3 * i + 2])));
-            if (maybe_on_screen(t, te, smax, cam, ct.tile_w, ct.tile_h, rc)) mask[k] |= 1ull << c;
+            const bool near_ok = t[2] + te[2] > rc.znear; // the exact near test is the projection's
+            const float smax = 1.0001f * __expf(fmaxf(ls[k][0], fmaxf(ls[k][1], ls[k][2])));
+            const bool on = maybe_on_screen(t, te, smax, cam, tw, th, rc);
+            mask[k] = (i < n && lod_ok && !culled && near_ok && on) ? 1ull : 0ull;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kGateItems; k++) {
+            mask[k] = 0;
+            const long long i = block0 + k * 256 + threadIdx.x;
+            if (i >= n) continue;
+            const float m[3] = {mx[k], my[k], mz[k]};
+            float smax = -1.f;
+            for (int c = 0; c < ncam; c++) {
+                const CamInfo &cam = sh.cams[c];
+                if (!lod_pass(m, lod[k], cam, rc, sh.thr2)) continue;
+                if (rc.cull_enable && (c == 0 ? ((cw[k] >> (i & 31)) & 1u) : cull_bit(o, c, i))) continue;
+                float t[3], te[3];
+                camera_point(m, cam, t, te);
+                if (!(t[2] + te[2] > rc.znear)) continue; // the exact near test is the projection's
+                if (smax < 0.f) smax = 1.0001f * __expf(fmaxf(ls[k][0], fmaxf(ls[k][1], ls[k][2])));
+                if (maybe_on_screen(t, te, smax, cam, tw, th, rc)) mask[k] |= 1ull << c;
+            }
         }
     }
-    // order-preserving compaction: item (k, thread) precedes (k', thread') iff
-    // k < k', or k == k' and thread < thread'
+}
+
+// Block-local order of the candidates: item (k, thread) precedes (k', thread')
+// iff k < k', or k == k' and thread < thread'.  Returns the block's count.
+__device__ __forceinline__ unsigned gate_ranks(const unsigned long long mask[kGateItems], unsigned bal[kGateItems],
+                                               GateShared &sh)
+{
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned bal[kGateItems];
 #pragma unroll
     for (int k = 0; k < kGateItems; k++) {
         bal[k] = __ballot_sync(0xffffffffu, mask[k] != 0);
-        if (lane == 0) s_cnt[k][warp] = __popc(bal[k]);
+        if (lane == 0) sh.cnt[k][warp] = __popc(bal[k]);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned run = 0;
-        for (int k = 0; k < kGateItems; k++)
-            for (int w = 0; w < 8; w++) { const unsigned c = s_cnt[k][w]; s_cnt[k][w] = run; run += c; }
-        s_total = run;
+    if (threadIdx.x < 32) { // warp 0: exclusive scan of the 32 (item, warp) counts in (k, warp) order
+        const unsigned c = sh.cnt[lane >> 3][lane & 7];
+        unsigned x = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        sh.cnt[lane >> 3][lane & 7] = x - c;
+        if (lane == 31) sh.total = x;
     }
     __syncthreads();
-    if (threadIdx.x < 32) {
-        const unsigned long long b = lookback_exclusive(o.lb_status + 1, bid, s_total, o.ctr, kSitePreprocess);
-        if (threadIdx.x == 0) s_base = b;
-    }
-    __syncthreads();
-    const unsigned long long base = s_base;
+    return sh.total;
+}
+
+// The gate runs as count, scan, gather: no block waits on another (an
+// in-order look-back chain makes the blocks of a wave, which all finish their
+// counts together, wait for one another); each block first writes its
+// candidates to its own range, and the gather moves only candidates.
+__global__ void __launch_bounds__(256, 3) gate_count_kernel(GaussPtrs g, PreOut o, const CamTable *__restrict__ ctp,
+                                                            RenderConsts rc, unsigned long long *counts)
+{
+    __shared__ GateShared sh;
+    unsigned long long mask[kGateItems];
+    unsigned bal[kGateItems];
+    const long long block0 = (long long)blockIdx.x * 256 * kGateItems;
+    gate_masks(g, o, *ctp, rc, sh, block0, mask);
+    const unsigned total = gate_ranks(mask, bal, sh);
+    if (threadIdx.x == 0) counts[blockIdx.x] = total;
+    // the block's candidates, in order, at the start of its own range
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
     for (int k = 0; k < kGateItems; k++) {
         if (mask[k]) {
-            const unsigned long long pos = base + s_cnt[k][warp] + __popc(bal[k] & lt);
-            o.cand_g[pos] = (uint32_t)(block0 + k * 256 + threadIdx.x);
-            o.cand_mask[pos] = mask[k];
+            const long long pos = block0 + sh.cnt[k][warp] + __popc(bal[k] & lt);
+            o.gate_g[pos] = (uint32_t)(block0 + k * 256 + threadIdx.x);
+            o.gate_mask[pos] = mask[k];
         }
     }
-    const unsigned long long run = base + s_total;
-    if (bid == gridDim.x - 1 && threadIdx.x == 0) o.ctr->n_candidates = run;
+}
+
+// Exclusive scan of the block counts in place (one block); the total is the
+// candidate count.
+__global__ void __launch_bounds__(1024) gate_scan_kernel(unsigned long long *counts, long long nblocks,
+                                                         DevCounters *ctr)
+{
+    __shared__ unsigned long long s[1024];
+    const long long per = (nblocks + 1023) / 1024;
+    const long long b0 = (long long)threadIdx.x * per;
+    unsigned long long acc = 0;
+    for (long long b = b0; b < b0 + per && b < nblocks; b++) acc += counts[b];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const unsigned long long v = threadIdx.x >= off ? s[threadIdx.x - off] : 0ull;
+        __syncthreads();
+        s[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned long long run = s[threadIdx.x] - acc; // exclusive prefix of this chunk
+    for (long long b = b0; b < b0 + per && b < nblocks; b++) {
+        const unsigned long long c = counts[b];
+        counts[b] = run;
+        run += c;
+    }
+    if (threadIdx.x == 1023) ctr->n_candidates = s[1023];
+}
+
+// Moves each block's candidates from its own range to their place in the
+// ordered list (offsets from gate_scan_kernel).
+__global__ void __launch_bounds__(256) gate_gather_kernel(PreOut o, const unsigned long long *offsets,
+                                                          long long nblocks, const DevCounters *ctr)
+{
+    const long long b = blockIdx.x;
+    const unsigned long long off = offsets[b];
+    const unsigned long long end = b + 1 < nblocks ? offsets[b + 1] : ctr->n_candidates;
+    const long long src = b * 256 * kGateItems;
+    for (unsigned long long t = threadIdx.x; off + t < end; t += 256) {
+        o.cand_g[off + t] = o.gate_g[src + t];
+        o.cand_mask[off + t] = o.gate_mask[src + t];
+    }
 }
 
 // Stage 2, one thread per candidate (converged warps): the exact FP32
@@ -382,13 +494,19 @@ __global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, 
                                                          RenderConsts rc)
 {
     const CamTable &ct = *ctp;
+    __shared__ CamInfo s_cams[GS_MAX_CAMERAS];
     __shared__ unsigned s_bid;
     __shared__ unsigned long long s_warp[8];
     __shared__ unsigned long long s_base;
+    const unsigned long long ncand = o.ctr->n_candidates;
+    const int tw = ct.tile_w, th = ct.tile_h;
+    stage_cameras(ct, s_cams);
+    // persistent blocks: each takes the next 256 candidates (tickets in order,
+    // so every look-back waits only on chunks already being processed)
+    for (;;) {
     if (threadIdx.x == 0) s_bid = atomicAdd((unsigned *)o.lb_status, 1u);
     __syncthreads();
     const unsigned bid = s_bid;
-    const unsigned long long ncand = o.ctr->n_candidates;
     if ((unsigned long long)bid * 256 >= ncand) return;
     const unsigned long long j = (unsigned long long)bid * 256 + threadIdx.x;
     GaussLoad L;
@@ -403,10 +521,10 @@ __global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, 
         for (unsigned long long mm = cm; mm; mm &= mm - 1) {
             const int c = __ffsll((long long)mm) - 1;
             double td[3];
-            camera_point_d(L.m, ct.c[c], td);
+            camera_point_d(L.m, s_cams[c], td);
             if (!(__double2float_rn(td[2]) > rc.znear)) continue;
             Proj p;
-            if (project_gaussian(L.ls, L.q, td, ct.c[c], ct.tile_w, ct.tile_h, rc, p)) act |= 1ull << c;
+            if (project_gaussian(L.ls, L.q, td, s_cams[c], tw, th, rc, p)) act |= 1ull << c;
         }
     }
     const unsigned long long cnt = __popcll(act);
@@ -427,7 +545,7 @@ __global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, 
         o.ctr->records_needed = end;
         o.ctr->n_records = end < (unsigned long long)o.max_records ? end : o.max_records;
     }
-    if (!act) return;
+    if (act) {
     if (base < (unsigned long long)o.max_records) o.rec_first[i] = (uint32_t)base;
     const float op = 1.f / (1.f + expf(-g.opacity_logit[i]));
     unsigned long long r = base;
@@ -437,11 +555,11 @@ __global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, 
             set_error(o.ctr, GS_ERR_CAPACITY, kSitePreprocess);
             break;
         }
-        const CamInfo &cam = ct.c[c];
+        const CamInfo &cam = s_cams[c];
         double td[3];
         camera_point_d(L.m, cam, td);
         Proj p;
-        project_gaussian(L.ls, L.q, td, cam, ct.tile_w, ct.tile_h, rc, p); // same inputs: same (passing) result
+        project_gaussian(L.ls, L.q, td, cam, tw, th, rc, p); // same inputs: same (passing) result
         const float dx = L.m[0] - cam.campos[0], dy = L.m[1] - cam.campos[1], dz = L.m[2] - cam.campos[2];
         const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
         float Y[16];
@@ -475,6 +593,9 @@ __global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, 
         o.dkey[r] = __float_as_uint(p.depth);
         o.clampm[r] = clm;
     }
+    } // act
+    __syncthreads(); // every thread is done with this chunk's shared values
+    } // chunks
 }
 
 cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t *cull)
@@ -491,18 +612,25 @@ cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t 
     o.rec_g = ws->rec_g; o.tt = ws->tt; o.dkey = ws->dkey[0];
     o.rec_cam = ws->rec_cam; o.rd0 = ws->rd0; o.rd1 = ws->rd1; o.rd2 = ws->rd2; o.rect = ws->rect;
     o.clampm = ws->clampm; o.cand_g = ws->cand_g; o.cand_mask = ws->cand_mask; o.rec_first = ws->rec_first;
+    o.gate_g = ws->gate_g; o.gate_mask = ws->gate_mask;
     o.lb_status = ws->lb_status;
     o.ctr = ws->ctr; o.max_records = ws->cap.max_records;
     o.cull = ws->rc.cull_enable ? cull : nullptr;
     o.cull_words = (n + 31) / 32;
     if ((e = cudaMemsetAsync(ws->rec_first, 0xff, (size_t)n * sizeof(uint32_t), st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(ws->lb_status, 0, (gblocks + 1) * sizeof(unsigned long long), st)) != cudaSuccess)
-        return e;
-    gate_kernel<<<gblocks, 256, 0, st>>>(gp, o, ws->d_cams, ws->rc);
+    // gate: per-block counts (in lb_status) and candidates (block-strided), the
+    // scan of the counts, the gather into one ordered list
+    gate_count_kernel<<<gblocks, 256, 0, st>>>(gp, o, ws->d_cams, ws->rc, ws->lb_status);
+    note_launch();
+    gate_scan_kernel<<<1, 1024, 0, st>>>(ws->lb_status, (long long)gblocks, ws->ctr);
+    note_launch();
+    gate_gather_kernel<<<gblocks, 256, 0, st>>>(o, ws->lb_status, (long long)gblocks, ws->ctr);
     note_launch();
     if ((e = cudaMemsetAsync(ws->lb_status, 0, (pblocks + 1) * sizeof(unsigned long long), st)) != cudaSuccess)
         return e;
-    project_kernel<<<pblocks, 256, 0, st>>>(gp, o, ws->d_cams, ws->rc);
+    // projection: two persistent 256-thread blocks per SM
+    const unsigned pgrid = std::min<unsigned>(pblocks, 2u * (unsigned)ws->sm_count);
+    project_kernel<<<pgrid, 256, 0, st>>>(gp, o, ws->d_cams, ws->rc);
     note_launch();
     return cudaGetLastError();
 }
@@ -576,8 +704,9 @@ struct BwdArgs {
 __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, const CamTable *__restrict__ ctp,
                                                              RenderConsts rc)
 {
-    const CamTable &ct = *ctp;
+    __shared__ CamInfo s_cams[GS_MAX_CAMERAS];
     __shared__ float s_red[4];
+    stage_cameras(*ctp, s_cams);
     // one thread per Gaussian that has records: the thread of its first record
     const unsigned long long rh = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned long long nrec = a.ctr->n_records;
@@ -610,7 +739,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, const Ca
             float gM[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}; // dL/dM, M = Q diag(s)
             float absacc = 0.f;
             for (unsigned long long r = r0; r < r1; r++) {
-                const CamInfo &cam = ct.c[a.rec_cam[r]];
+                const CamInfo &cam = s_cams[a.rec_cam[r]];
                 const float *rg = a.rgrad + r * kSlotFloats;
                 const float gu = rg[0], gv = rg[1], gA = rg[2], gB = rg[3], gC = rg[4], go = rg[5];
                 const float grgb[3] = {rg[6], rg[7], rg[8]};

@@ -12,8 +12,8 @@
 //      the depth order inside each tile: the final order is
 //      (camera, tile, depth bits, Gaussian) without ever sorting 64-bit keys;
 //   4. tile ranges from the sorted tile ids.
-// The radix passes are single-pass ("onesweep"): each block ranks its 2048 or
-// 4096 keys (a tuning of the workspace) in shared memory, publishes per-digit counts and finds its global
+// The radix passes are single-pass ("onesweep"): each block ranks its 1024,
+// 2048 or 4096 keys (a tuning of the workspace) in shared memory, publishes per-digit counts and finds its global
 // offsets by a per-digit decoupled look-back, so every pass reads and writes
 // each key once.  Item counts stay on the device, so nothing here needs a
 // host synchronisation.
@@ -144,22 +144,33 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
         s_glob[d] = bucket_off[d];
     } else {
         vst[(unsigned long long)bid * 256 + d] = kRxAgg | dtotal;
+        // walk back 8 predecessors at a time (independent loads in flight):
+        // add aggregates until an inclusive prefix; wait where one is missing
+        constexpr int kWin = 8;
         uint32_t excl = 0;
         long long pred = (long long)bid - 1;
+        unsigned long long spins = 0;
         while (pred >= 0) {
-            uint32_t s;
-            unsigned long long spins = 0;
-            while (((s = vst[(unsigned long long)pred * 256 + d]) >> 30) == 0) {
-                if (++spins > kSpinLimit) {
-                    set_error(ctr, GS_ERR_TIMEOUT, kSiteRadix);
-                    s = kRxInc;
-                    break;
-                }
-                __nanosleep(40);
+            uint32_t sv[kWin];
+#pragma unroll
+            for (int q = 0; q < kWin; q++)
+                sv[q] = pred - q >= 0 ? (uint32_t)vst[(unsigned long long)(pred - q) * 256 + d] : (uint32_t)kRxInc; // block -1: prefix 0
+            int q = 0;
+            bool done = false;
+            for (; q < kWin; q++) {
+                const uint32_t sq = sv[q];
+                if ((sq >> 30) == 0) break; // not published yet
+                excl += sq & kRxVal;
+                if ((sq >> 30) == 2) { done = true; break; }
             }
-            excl += s & kRxVal;
-            if ((s >> 30) == 2) break;
-            pred--;
+            if (done) break;
+            pred -= q;
+            if (q == kWin) continue;
+            if (++spins > kSpinLimit) {
+                set_error(ctr, GS_ERR_TIMEOUT, kSiteRadix);
+                break;
+            }
+            __nanosleep(40);
         }
         vst[(unsigned long long)bid * 256 + d] = kRxInc | (excl + dtotal);
         s_glob[d] = bucket_off[d] + excl;
@@ -215,7 +226,8 @@ static cudaError_t radix_passes(cudaStream_t st, uint32_t *keys[2], uint32_t *va
 // the device (clamped to cap).  keys[0]/vals[0] hold the input; the sorted
 // result lands in keys[out_buf]/vals[out_buf].  With vals_identity the input
 // values are the item indices and vals[0] is not read.  Blocks rank
-// ws->sort_items * 256 keys (the workspace's tuning, 2048 or 4096).
+// ws->sort_items * 256 keys (the workspace's tuning: 1024, 2048 or 4096, or
+// chosen by the size of the sort).
 cudaError_t launch_radix_sort(gs_workspace *ws, cudaStream_t st, uint32_t *keys[2], uint32_t *vals[2],
                               const unsigned long long *count, unsigned long long cap, int bits, bool vals_identity,
                               bool /*unused*/, int &out_buf)
@@ -231,7 +243,14 @@ cudaError_t launch_radix_sort(gs_workspace *ws, cudaStream_t st, uint32_t *keys[
     note_launch();
     radix_offsets_kernel<<<1, 256, 0, st>>>(ws->rx_hist, ws->rx_off, passes);
     note_launch();
-    if (ws->sort_items == 8)
+    // keys per block: the workspace's tuning, or by size (0): small sorts take
+    // small blocks so that enough SMs work on them
+    int items = ws->sort_items;
+    if (items == 0) items = cap <= (4ull << 20) ? 4 : (cap <= (16ull << 20) ? 8 : 16);
+    if (items == 4)
+        return radix_passes<4>(st, keys, vals, count, cap, passes, vals_identity, ws->rx_status, ws->rx_off, ws->ctr,
+                               out_buf);
+    if (items == 8)
         return radix_passes<8>(st, keys, vals, count, cap, passes, vals_identity, ws->rx_status, ws->rx_off, ws->ctr,
                                out_buf);
     return radix_passes<kSortItems>(st, keys, vals, count, cap, passes, vals_identity, ws->rx_status, ws->rx_off,

@@ -181,10 +181,11 @@ def test_sort_chunk_leaves_results_unchanged():
     P = O.Params()
     a = GpuRun(g, cams, P)
     ws = B.Workspace(**capacity_for(g.n, cams))
-    ws.set_sort_chunk(2048)
-    b = GpuRun(g, cams, P, ws=ws)
-    assert np.array_equal(a.sorted_vals, b.sorted_vals) and np.array_equal(a.ranges, b.ranges)
-    assert torch.equal(a.rgb, b.rgb) and np.array_equal(a.n_contrib, b.n_contrib)
+    for chunk in (1024, 2048, 4096):
+        ws.set_sort_chunk(chunk)
+        b = GpuRun(g, cams, P, ws=ws)
+        assert np.array_equal(a.sorted_vals, b.sorted_vals) and np.array_equal(a.ranges, b.ranges), chunk
+        assert torch.equal(a.rgb, b.rgb) and np.array_equal(a.n_contrib, b.n_contrib), chunk
     with pytest.raises(B.GSError):
         ws.set_sort_chunk(1000)
 
