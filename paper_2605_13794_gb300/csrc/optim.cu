@@ -24,13 +24,21 @@ __device__ __forceinline__ float ld_zero(const float *p, int H, int W, int y, in
     return (y >= 0 && y < H && x >= 0 && x < W) ? p[(long long)y * W + x] : 0.f;
 }
 
+// The two 11-tap passes run as sliding windows in registers: a thread
+// produces kHSeg consecutive outputs of a row from kHSeg + 10 inputs (or kVSeg
+// outputs of a column), so each shared-memory value is read once per thread
+// rather than once per tap.
+constexpr int kHSeg = 8;                 // horizontal outputs per thread (42 rows x 4 segments)
+constexpr int kVSeg = 4;                 // vertical outputs per thread (32 columns x 8 segments)
+constexpr int kLTP = kLTH + 1;           // padded row of the staged tile
+
 // grid: (tiles_x, tiles_y, batch * 3)
 __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *img, const float *tgt, int H, int W, Win win,
                                                        float C1, float C2, float *F /*[3][B*3][H][W]*/,
                                                        long long plane_stride_maps, float *partial)
 {
-    __shared__ float sx[kLTH][kLTH], sy[kLTH][kLTH];
-    __shared__ float hb[5][kLTH][kLT];
+    __shared__ float sx[kLTH][kLTP], sy[kLTH][kLTP];
+    __shared__ float hb[5][kLTH][kLT + 1];
     __shared__ float red[2][8];
     const int plane = blockIdx.z;
     const float *x = img + (long long)plane * H * W;
@@ -42,43 +50,70 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *img, const f
         sy[r][c] = ld_zero(y, H, W, oy + r - kHalo, ox + c - kHalo);
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < kLTH * kLT; k += 256) {
-        const int r = k / kLT, c = k % kLT;
-        float a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+    // horizontal blur of x, y, x^2, y^2, xy: 42 rows x (32 / kHSeg) segments
+    for (int wi = threadIdx.x; wi < kLTH * (kLT / kHSeg); wi += 256) {
+        const int r = wi / (kLT / kHSeg), c0 = (wi % (kLT / kHSeg)) * kHSeg;
+        float xv[kHSeg + 10], yv[kHSeg + 10];
 #pragma unroll
-        for (int t = 0; t < 11; t++) {
-            const float xv = sx[r][c + t], yv = sy[r][c + t], wt = win.w[t];
-            a0 += wt * xv; a1 += wt * yv; a2 += wt * xv * xv; a3 += wt * yv * yv; a4 += wt * xv * yv;
+        for (int j = 0; j < kHSeg + 10; j++) { xv[j] = sx[r][c0 + j]; yv[j] = sy[r][c0 + j]; }
+#pragma unroll
+        for (int o = 0; o < kHSeg; o++) {
+            float a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+#pragma unroll
+            for (int t = 0; t < 11; t++) {
+                const float xt = xv[o + t], yt = yv[o + t], wt = win.w[t];
+                a0 += wt * xt; a1 += wt * yt; a2 += wt * xt * xt; a3 += wt * yt * yt; a4 += wt * xt * yt;
+            }
+            hb[0][r][c0 + o] = a0; hb[1][r][c0 + o] = a1; hb[2][r][c0 + o] = a2; hb[3][r][c0 + o] = a3;
+            hb[4][r][c0 + o] = a4;
         }
-        hb[0][r][c] = a0; hb[1][r][c] = a1; hb[2][r][c] = a2; hb[3][r][c] = a3; hb[4][r][c] = a4;
     }
     __syncthreads();
+    // vertical blur and the SSIM terms: 32 columns x (32 / kVSeg) segments
     float ssum = 0.f, l1sum = 0.f;
-    for (int k = threadIdx.x; k < kLT * kLT; k += 256) {
-        const int r = k / kLT, c = k % kLT;
-        const int gy = oy + r, gx = ox + c;
-        if (gy >= H || gx >= W) continue;
-        float mx = 0, my = 0, exx = 0, eyy = 0, exy = 0;
+    {
+        const int c = threadIdx.x % kLT, r0 = (threadIdx.x / kLT) * kVSeg;
+        float m[5][kVSeg];
 #pragma unroll
-        for (int t = 0; t < 11; t++) {
-            const float wt = win.w[t];
-            mx += wt * hb[0][r + t][c]; my += wt * hb[1][r + t][c];
-            exx += wt * hb[2][r + t][c]; eyy += wt * hb[3][r + t][c]; exy += wt * hb[4][r + t][c];
+        for (int q = 0; q < 5; q++)
+#pragma unroll
+            for (int o = 0; o < kVSeg; o++) m[q][o] = 0.f;
+#pragma unroll
+        for (int j = 0; j < kVSeg + 10; j++) {
+            float v[5];
+#pragma unroll
+            for (int q = 0; q < 5; q++) v[q] = hb[q][r0 + j][c];
+#pragma unroll
+            for (int o = 0; o < kVSeg; o++) {
+                const int t = j - o;
+                if (t >= 0 && t < 11) {
+                    const float wt = win.w[t];
+#pragma unroll
+                    for (int q = 0; q < 5; q++) m[q][o] += wt * v[q];
+                }
+            }
         }
-        const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
-        const float A1 = 2.f * mx * my + C1, A2 = 2.f * sxy + C2;
-        const float B1 = mx * mx + my * my + C1, B2 = sxx + syy + C2;
-        const float iB = 1.f / (B1 * B2);
-        const float S = A1 * A2 * iB;
-        const float dmx = 2.f * my * A2 * iB - S * 2.f * mx / B1;
-        const float dsxx = -S / B2;
-        const float dsxy = 2.f * A1 * iB;
-        const long long p = (long long)plane * H * W + (long long)gy * W + gx;
-        F[p] = dmx - 2.f * mx * dsxx - my * dsxy;
-        F[plane_stride_maps + p] = dsxx;
-        F[2 * plane_stride_maps + p] = dsxy;
-        ssum += S;
-        l1sum += fabsf(sx[r + kHalo][c + kHalo] - sy[r + kHalo][c + kHalo]);
+#pragma unroll
+        for (int o = 0; o < kVSeg; o++) {
+            const int r = r0 + o;
+            const int gy = oy + r, gx = ox + c;
+            if (gy >= H || gx >= W) continue;
+            const float mx = m[0][o], my = m[1][o], exx = m[2][o], eyy = m[3][o], exy = m[4][o];
+            const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
+            const float A1 = 2.f * mx * my + C1, A2 = 2.f * sxy + C2;
+            const float B1 = mx * mx + my * my + C1, B2 = sxx + syy + C2;
+            const float iB = 1.f / (B1 * B2);
+            const float S = A1 * A2 * iB;
+            const float dmx = 2.f * my * A2 * iB - S * 2.f * mx / B1;
+            const float dsxx = -S / B2;
+            const float dsxy = 2.f * A1 * iB;
+            const long long p = (long long)plane * H * W + (long long)gy * W + gx;
+            F[p] = dmx - 2.f * mx * dsxx - my * dsxy;
+            F[plane_stride_maps + p] = dsxx;
+            F[2 * plane_stride_maps + p] = dsxy;
+            ssum += S;
+            l1sum += fabsf(sx[r + kHalo][c + kHalo] - sy[r + kHalo][c + kHalo]);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         ssum += __shfl_xor_sync(0xffffffffu, ssum, o);
@@ -99,8 +134,8 @@ __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float *img, const f
                                                        const float *F, long long plane_stride_maps, float lambda,
                                                        int batch, float *dL)
 {
-    __shared__ float sf[3][kLTH][kLTH];
-    __shared__ float hb[3][kLTH][kLT];
+    __shared__ float sf[3][kLTH][kLTP];
+    __shared__ float hb[3][kLTH][kLT + 1];
     const int plane = blockIdx.z;
     const int ox = blockIdx.x * kLT, oy = blockIdx.y * kLT;
     for (int k = threadIdx.x; k < kLTH * kLTH; k += 256) {
@@ -110,31 +145,51 @@ __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float *img, const f
                                   ox + c - kHalo);
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < kLTH * kLT; k += 256) {
-        const int r = k / kLT, c = k % kLT;
-        float a0 = 0, a1 = 0, a2 = 0;
+    for (int wi = threadIdx.x; wi < kLTH * (kLT / kHSeg); wi += 256) {
+        const int r = wi / (kLT / kHSeg), c0 = (wi % (kLT / kHSeg)) * kHSeg;
 #pragma unroll
-        for (int t = 0; t < 11; t++) {
-            const float wt = win.w[t];
-            a0 += wt * sf[0][r][c + t]; a1 += wt * sf[1][r][c + t]; a2 += wt * sf[2][r][c + t];
+        for (int m = 0; m < 3; m++) {
+            float v[kHSeg + 10];
+#pragma unroll
+            for (int j = 0; j < kHSeg + 10; j++) v[j] = sf[m][r][c0 + j];
+#pragma unroll
+            for (int o = 0; o < kHSeg; o++) {
+                float a = 0.f;
+#pragma unroll
+                for (int t = 0; t < 11; t++) a += win.w[t] * v[o + t];
+                hb[m][r][c0 + o] = a;
+            }
         }
-        hb[0][r][c] = a0; hb[1][r][c] = a1; hb[2][r][c] = a2;
     }
     __syncthreads();
     const float npx = 3.f * (float)H * (float)W; // SSIM and L1 are means over channels and pixels
-    for (int k = threadIdx.x; k < kLT * kLT; k += 256) {
-        const int r = k / kLT, c = k % kLT;
-        const int gy = oy + r, gx = ox + c;
-        if (gy >= H || gx >= W) continue;
-        float b0 = 0, b1 = 0, b2 = 0;
+    const int c = threadIdx.x % kLT, r0 = (threadIdx.x / kLT) * kVSeg;
+    float b[3][kVSeg];
 #pragma unroll
-        for (int t = 0; t < 11; t++) {
-            const float wt = win.w[t];
-            b0 += wt * hb[0][r + t][c]; b1 += wt * hb[1][r + t][c]; b2 += wt * hb[2][r + t][c];
+    for (int m = 0; m < 3; m++)
+#pragma unroll
+        for (int o = 0; o < kVSeg; o++) b[m][o] = 0.f;
+#pragma unroll
+    for (int j = 0; j < kVSeg + 10; j++) {
+        float v[3];
+#pragma unroll
+        for (int m = 0; m < 3; m++) v[m] = hb[m][r0 + j][c];
+#pragma unroll
+        for (int o = 0; o < kVSeg; o++) {
+            const int t = j - o;
+            if (t >= 0 && t < 11) {
+#pragma unroll
+                for (int m = 0; m < 3; m++) b[m][o] += win.w[t] * v[m];
+            }
         }
+    }
+#pragma unroll
+    for (int o = 0; o < kVSeg; o++) {
+        const int gy = oy + r0 + o, gx = ox + c;
+        if (gy >= H || gx >= W) continue;
         const long long p = (long long)plane * H * W + (long long)gy * W + gx;
         const float xv = img[p], yv = tgt[p];
-        const float dssim = (b0 + 2.f * xv * b1 + yv * b2) / npx;
+        const float dssim = (b[0][o] + 2.f * xv * b[1][o] + yv * b[2][o]) / npx;
         const float d = xv - yv;
         const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
         dL[p] = ((1.f - lambda) * sgn / npx - lambda * dssim) / (float)batch;

@@ -246,7 +246,7 @@ cudaError_t launch_radix_sort(gs_workspace *ws, cudaStream_t st, uint32_t *keys[
     // keys per block: the workspace's tuning, or by size (0): small sorts take
     // small blocks so that enough SMs work on them
     int items = ws->sort_items;
-    if (items == 0) items = cap <= (4ull << 20) ? 4 : (cap <= (16ull << 20) ? 8 : 16);
+    if (items == 0) items = cap <= (1ull << 20) ? 4 : (cap <= (16ull << 20) ? 8 : 16);
     if (items == 4)
         return radix_passes<4>(st, keys, vals, count, cap, passes, vals_identity, ws->rx_status, ws->rx_off, ws->ctr,
                                out_buf);
