@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--tune-cache", default=None, help="autotuner cache file for batch64-city10M")
     ap.add_argument("--tile", default="16x16", choices=["16x16", "32x8", "8x32", "32x16"],
                     help="render tile shape of the city5M step")
+    ap.add_argument("--dense-adam", action="store_true",
+                    help="update every Gaussian every step instead of deferring zero-gradient steps (same results)")
     return ap.parse_args()
 
 
@@ -150,7 +152,7 @@ def make_host_inputs(n):
 class Step:
     """Device state and the sequence of C-ABI calls of one training step."""
 
-    def __init__(self, g, cam, target, tile=(16, 16)):
+    def __init__(self, g, cam, target, tile=(16, 16), lazy=True):
         import torch
         from paper_2605_13794_gb300 import binding as B
         self.B, self.torch = B, torch
@@ -199,6 +201,17 @@ class Step:
         self.ws.sync_status()
         self.lr = [LRS[k] for k in ("mean", "log_scale", "quat", "opacity_logit", "sh")]
         self.stage_names = ["preprocess", "bin_sort", "render_fwd", "loss", "render_bwd", "adam", "importance"]
+        self.lazy = lazy
+        if lazy:
+            # Adam with deferred zero-gradient steps: bit-identical to dense Adam, touching only the
+            # Gaussians in use; flush() brings every Gaussian to the current step
+            self.last = torch.zeros(self.n, dtype=torch.int32, device="cuda")
+            self.drift = torch.zeros(self.n, 2, device="cuda")
+            self.ws.adam_lazy_enable(self.m, self.v, self.last, self.drift, max_steps=1 << 16)
+
+    def flush(self):
+        if self.lazy:
+            self.ws.adam_flush(self.gt)
 
     def run(self, ev=None):
         """One step; ev, if given, is a list of 8 CUDA events recorded between stages."""
@@ -448,7 +461,7 @@ def main():
     from paper_2605_13794_gb300 import binding as B
     torch.cuda.set_device(local)
     g, cam, target = make_host_inputs(args.n)
-    step = Step(g, cam, target, tile=tuple(int(x) for x in args.tile.split("x")))
+    step = Step(g, cam, target, tile=tuple(int(x) for x in args.tile.split("x")), lazy=not args.dense_adam)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         step.run()
@@ -475,6 +488,11 @@ def main():
     start.record(stream)
     for k in range(args.steps):
         step.run(evs[k])
+    # the deferred Adam steps of every Gaussian not yet brought up to date, inside the timed region
+    fl0, fl1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fl0.record(stream)
+    step.flush()
+    fl1.record(stream)
     end.record(stream)
     torch.cuda.synchronize()
     sampler.mark(w0, time.time())
@@ -485,6 +503,7 @@ def main():
     ms = max_over_ranks(ms, world)
     stage_ms = {name: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
                 for i, name in enumerate(step.stage_names)}
+    stage_ms["adam_flush_per_step"] = fl0.elapsed_time(fl1) / args.steps
 
     # ---- end to end through the public API with host buffers
     tgt_host = torch.from_numpy(target).pin_memory()
@@ -504,6 +523,7 @@ def main():
         step.run()
         loss_host.copy_(step.loss, non_blocking=True)
         cull_host.copy_(step.cull, non_blocking=True)
+    step.flush()
     e1.record(stream)
     torch.cuda.synchronize()
     sampler.mark(w0, time.time())
@@ -538,7 +558,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "gaussians": g.n, "width": W_IMG, "height": H_IMG, "tile": args.tile,
-                       "lod": True, "cull": True, "importance_pass": True, "optimizer": "adam",
+                       "lod": True, "cull": True, "importance_pass": True,
+                       "optimizer": "adam (dense)" if args.dense_adam else "adam, zero-gradient steps deferred (exact)",
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
             "mgaussian_per_s": gauss,
             "fwd_bwd": fwd_bwd,

@@ -260,6 +260,28 @@ int gs_adam_step_compact(gs_workspace *ws, const gs_gaussians *g, const gs_gauss
                          const gs_gaussian_grads *v, const float lr[5], float beta1, float beta2, float eps,
                          int32_t step, gs_stream stream);
 
+/* Deferred zero-gradient Adam steps.  Dense Adam moves every parameter every
+ * step, also those of Gaussians without a gradient.  Once enabled, a
+ * Gaussian's parameters and moments are kept as of the step in last_step[i]
+ * and brought up to date only when it is next used -- by gs_preprocess (its
+ * candidates), by gs_adam_step_compact (before its next gradient step) or by
+ * gs_adam_flush -- by replaying exactly the zero-gradient steps it missed, so
+ * every value equals dense Adam's bit for bit.  Parameters read by anything
+ * else (the caller, the model-level calls, a checkpoint) must be flushed
+ * first.  gs_preprocess then UPDATES the Gaussian arrays it is given.
+ *   m, v: the moments gs_adam_step_compact will be given (same arrays);
+ *   last_step: [n] int32, set by the caller to the current step (0 before the
+ *     first step) when enabling; drift: [n][2] float, zeroed by the caller (per
+ *     Gaussian, bounds on how far its mean and its largest log-scale can still
+ *     move, which widen the view gate);
+ *   max_steps: steps the workspace keeps coefficients for (40 bytes each);
+ *   needs beta1 < sqrt(beta2).  Allocates the step history (once, here). */
+int gs_adam_lazy_enable(gs_workspace *ws, const gs_gaussian_grads *m, const gs_gaussian_grads *v, int32_t *last_step,
+                        float *drift, float beta1, float beta2, float eps, int32_t max_steps);
+int gs_adam_lazy_disable(gs_workspace *ws);
+/* Brings every Gaussian up to the current step (no-op when not enabled). */
+int gs_adam_flush(gs_workspace *ws, const gs_gaussians *g, gs_stream stream);
+
 /* gs_render_bwd_compact followed by gs_adam_step_compact: the backward fused
  * with the optimizer step, no gradient array materialised. */
 int gs_render_bwd_adam(gs_workspace *ws, const gs_gaussians *g, const float *dL_drgb, const gs_gaussian_grads *m,

@@ -30,7 +30,8 @@ EXPORTS = ("gs_default_params", "gs_last_error", "gs_workspace_create", "gs_work
            "gs_adam_step", "gs_sync_status", "gs_workspace_counts", "gs_clear_error", "gs_workspace_buffer",
            "gs_kernel_launches", "gs_render_bwd_adam", "gs_render_bwd_compact", "gs_adam_step_compact",
            "gs_visible_set_static", "gs_upload_cameras", "gs_preprocess_uploaded", "gs_workspace_set_sort_chunk",
-           "gs_prune_sample", "gs_prune_mass", "gs_compact", "gs_densify", "gs_count_views")
+           "gs_prune_sample", "gs_prune_mass", "gs_compact", "gs_densify", "gs_count_views", "gs_adam_lazy_enable",
+           "gs_adam_lazy_disable", "gs_adam_flush")
 
 
 class GSError(RuntimeError):
@@ -121,6 +122,9 @@ def lib() -> ctypes.CDLL:
         L.gs_compact.argtypes = [vp, vp, vp, vp, i64, vp, vp]
         L.gs_densify.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, i64, vp, vp]
         L.gs_count_views.argtypes = [vp, vp, vp]
+        L.gs_adam_lazy_enable.argtypes = [vp, vp, vp, vp, vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, i32]
+        L.gs_adam_lazy_disable.argtypes = [vp]
+        L.gs_adam_flush.argtypes = [vp, vp, vp]
         L.gs_preprocess_uploaded.argtypes = [vp, vp, vp, vp, vp]
         L.gs_bin_sort.argtypes = [vp, vp]
         L.gs_render_fwd.argtypes = [vp, vp, vp, vp]
@@ -416,6 +420,21 @@ class Workspace:
         _check(lib().gs_densify(self._ws, ctypes.byref(sc), _ptr(absgrad), _ptr(denom), _ptr(cvis), _ptr(crad),
                                 _ptr(noise), ctypes.byref(p), ctypes.byref(dc), dst.n, _ptr(n_out),
                                 _stream(stream)))
+
+    def adam_lazy_enable(self, m: GaussianTensors, v: GaussianTensors, last_step, drift, beta1=0.9, beta2=0.999,
+                         eps=1e-15, max_steps=1 << 20):
+        """Deferred zero-gradient Adam steps (see gs_adam_lazy_enable)."""
+        self._lazy = (m, v, last_step, drift)  # keep them alive
+        mc, vc = m.c_grads(), v.c_grads()
+        _check(lib().gs_adam_lazy_enable(self._ws, ctypes.byref(mc), ctypes.byref(vc), _ptr(last_step), _ptr(drift),
+                                         float(beta1), float(beta2), float(eps), int(max_steps)))
+
+    def adam_lazy_disable(self):
+        _check(lib().gs_adam_lazy_disable(self._ws))
+
+    def adam_flush(self, g: GaussianTensors, stream=None):
+        gc = g.c()
+        _check(lib().gs_adam_flush(self._ws, ctypes.byref(gc), _stream(stream)))
 
     def count_views(self, counts, stream=None):
         _check(lib().gs_count_views(self._ws, _ptr(counts), _stream(stream)))

@@ -288,6 +288,7 @@ int gs_workspace_destroy(gs_workspace *ws)
     for (int k = 0; k < gs_workspace::kStageSlots; k++)
         if (ws->stage_ev[k] && (e2 = cudaEventDestroy(ws->stage_ev[k])) != cudaSuccess) e = e2;
     if (ws->h_stage && (e2 = cudaFreeHost(ws->h_stage)) != cudaSuccess) e = e2;
+    if (ws->lazy.hist && (e2 = cudaFree(ws->lazy.hist)) != cudaSuccess) e = e2;
     if (ws->base && (e2 = cudaFree(ws->base)) != cudaSuccess) e = e2;
     delete ws;
     if (e != cudaSuccess) return cuda_fail(e, "gs_workspace_destroy");
@@ -520,6 +521,10 @@ int gs_adam_step_compact(gs_workspace *ws, const gs_gaussians *g, const gs_gauss
     if (g->n > 0 && (!m->mean || !m->log_scale || !m->quat || !m->opacity_logit || !m->sh || !v->mean ||
                      !v->log_scale || !v->quat || !v->opacity_logit || !v->sh))
         return fail(GS_ERR_INVALID_ARG, "gs_adam_step_compact: NULL moment array");
+    if (ws->lazy.enabled &&
+        (m->mean != ws->lazy.m.mean || v->mean != ws->lazy.v.mean || beta1 != ws->lazy.b1 || beta2 != ws->lazy.b2 ||
+         eps != ws->lazy.eps))
+        return fail(GS_ERR_INVALID_ARG, "gs_adam_step_compact: moments and betas must be those of gs_adam_lazy_enable");
     gs_gaussian_grads param;
     param.mean = const_cast<float *>(g->mean);
     param.log_scale = const_cast<float *>(g->log_scale);
@@ -528,6 +533,58 @@ int gs_adam_step_compact(gs_workspace *ws, const gs_gaussians *g, const gs_gauss
     param.sh = const_cast<float *>(g->sh);
     CK(gs::launch_adam_sparse(ws, (cudaStream_t)stream, param, *m, *v, g->n, lr, beta1, beta2, eps, step),
        "gs_adam_step_compact");
+    return GS_OK;
+}
+
+int gs_adam_lazy_enable(gs_workspace *ws, const gs_gaussian_grads *m, const gs_gaussian_grads *v, int32_t *last_step,
+                        float *drift, float beta1, float beta2, float eps, int32_t max_steps)
+{
+    if (!ws || !m || !v || !last_step || !drift) return fail(GS_ERR_INVALID_ARG, "gs_adam_lazy_enable: NULL argument");
+    if (ws->cap.flags & GS_CAP_FORWARD_ONLY)
+        return fail(GS_ERR_INVALID_ARG, "gs_adam_lazy_enable: the workspace was created GS_CAP_FORWARD_ONLY");
+    if (!m->mean || !m->log_scale || !m->quat || !m->opacity_logit || !m->sh || !v->mean || !v->log_scale ||
+        !v->quat || !v->opacity_logit || !v->sh)
+        return fail(GS_ERR_INVALID_ARG, "gs_adam_lazy_enable: NULL moment array");
+    const double r = (double)beta1 / sqrt((double)beta2);
+    if (!(beta1 >= 0.f && beta1 < 1.f && beta2 > 0.f && beta2 < 1.f && r < 1.0))
+        return fail(GS_ERR_INVALID_ARG, "gs_adam_lazy_enable: needs 0 <= beta1 < sqrt(beta2) < 1");
+    if (max_steps < 1) return fail(GS_ERR_INVALID_ARG, "gs_adam_lazy_enable: max_steps < 1");
+    if (ws->lazy.hist) {
+        cudaFree(ws->lazy.hist);
+        ws->lazy.hist = nullptr;
+    }
+    cudaError_t e = cudaMalloc(&ws->lazy.hist, (size_t)(max_steps + 1) * 10 * sizeof(float));
+    if (e != cudaSuccess) {
+        ws->lazy.hist = nullptr;
+        ws->lazy.enabled = 0;
+        cudaGetLastError();
+        return fail(GS_ERR_OOM, "gs_adam_lazy_enable: cudaMalloc of the step history failed");
+    }
+    ws->lazy.max_steps = max_steps;
+    ws->lazy.m = *m;
+    ws->lazy.v = *v;
+    ws->lazy.last = last_step;
+    ws->lazy.drift = drift;
+    ws->lazy.b1 = beta1; ws->lazy.b2 = beta2; ws->lazy.eps = eps;
+    ws->lazy.drift_factor = (float)(1.01 * r / (1.0 - r));
+    ws->lazy.enabled = 1;
+    return GS_OK;
+}
+
+int gs_adam_lazy_disable(gs_workspace *ws)
+{
+    if (!ws) return fail(GS_ERR_INVALID_ARG, "gs_adam_lazy_disable: NULL workspace");
+    if (ws->lazy.hist) cudaFree(ws->lazy.hist);
+    memset(&ws->lazy, 0, sizeof(ws->lazy));
+    return GS_OK;
+}
+
+int gs_adam_flush(gs_workspace *ws, const gs_gaussians *g, gs_stream stream)
+{
+    if (!ws || !g) return fail(GS_ERR_INVALID_ARG, "gs_adam_flush: NULL argument");
+    if (!ws->lazy.enabled) return GS_OK;
+    if (g->n < 0 || g->n > ws->cap.max_gaussians) return fail(GS_ERR_CAPACITY, "gs_adam_flush: n > max_gaussians");
+    CK(gs::launch_lazy_flush(ws, (cudaStream_t)stream, *g), "gs_adam_flush");
     return GS_OK;
 }
 

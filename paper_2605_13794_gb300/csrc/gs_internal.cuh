@@ -256,6 +256,17 @@ struct gs_workspace {
     uint32_t *mhist, *moff;      // [4][256]
     gs::DevCounters *mctr;       // item count (n_records) and errors of the model-level calls
     int *d_adam_step;      // device Adam step counter (graph-replayable optimizer step)
+    // deferred zero-gradient Adam steps (gs_adam_lazy_enable): a Gaussian's p, m,
+    // v are brought to the current step only when it is next used
+    struct {
+        int enabled;
+        int max_steps;
+        float *hist;       // device [max_steps + 1][10]: lr_c of the 5 groups, then 1/sqrt(1 - beta2^t)
+        gs_gaussian_grads m, v;
+        int32_t *last;     // [N] step at which a Gaussian's p, m, v are current
+        float *drift;      // [N][2] bounds on the mean's and the largest log-scale's further drift
+        float b1, b2, eps, drift_factor;
+    } lazy;
     float *d_adam_coef;    // [2][GS_MAX_ADAM_GROUPS] bias-corrected lr and 1/sqrt(1 - beta2^t)
     // host staging of camera uploads: a ring of pinned tables, each reused only
     // after the copy that read it has completed
@@ -311,6 +322,8 @@ cudaError_t launch_prune_sample(gs_workspace *ws, cudaStream_t st, const float *
 cudaError_t launch_prune_mass(gs_workspace *ws, cudaStream_t st, const float *s, long long n, float mass,
                               uint32_t *keep);
 cudaError_t launch_count_views(gs_workspace *ws, cudaStream_t st, uint32_t *counts);
+cudaError_t launch_lazy_catchup(gs_workspace *ws, cudaStream_t st, const gs_gaussians &g);
+cudaError_t launch_lazy_flush(gs_workspace *ws, cudaStream_t st, const gs_gaussians &g);
 cudaError_t launch_compact(gs_workspace *ws, cudaStream_t st, const gs_model &src, const uint32_t *keep,
                            const gs_model &dst, long long dst_cap, long long *n_out);
 cudaError_t launch_densify(gs_workspace *ws, cudaStream_t st, const gs_model &src, const float *absgrad,

@@ -7,6 +7,8 @@
 // gradient needs; pass 2 blurs those maps (the window is symmetric, so the
 // adjoint of the blur is the blur) and assembles dL/dx.  Partial sums are
 // reduced in a fixed order in FP64.
+#include <algorithm>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -448,8 +450,11 @@ struct AdamCoefArgs {
 };
 
 // Step number and bias-corrected coefficients on the device, so a captured
-// optimizer step advances its own counter on every replay.
-__global__ void adam_coef_kernel(AdamCoefArgs a, int *d_step, float *coef)
+// optimizer step advances its own counter on every replay.  With deferred
+// steps enabled the coefficients of every step are also kept (hist), so a
+// Gaussian brought up to date later replays exactly the steps it missed.
+__global__ void adam_coef_kernel(AdamCoefArgs a, int *d_step, float *coef, float *hist, int max_steps,
+                                 DevCounters *ctr)
 {
     if (threadIdx.x != 0) return;
     const int t = a.step > 0 ? a.step : *d_step + 1;
@@ -459,6 +464,193 @@ __global__ void adam_coef_kernel(AdamCoefArgs a, int *d_step, float *coef)
         coef[k] = (float)((double)a.lr[k] / c1);
         coef[GS_MAX_ADAM_GROUPS + k] = (float)(1.0 / sqrt(c2));
     }
+    if (hist) {
+        if (t > max_steps) {
+            set_error(ctr, GS_ERR_CAPACITY, kSiteModel);
+            return;
+        }
+        for (int k = 0; k < 5; k++) {
+            hist[10 * t + k] = coef[k];
+            hist[10 * t + 5 + k] = coef[GS_MAX_ADAM_GROUPS + k];
+        }
+    }
+}
+
+// ---- deferred zero-gradient steps ------------------------------------------------
+//
+// Dense Adam moves every parameter every step, also those without a gradient
+// (m and v decay, p follows the momentum).  With deferred steps a Gaussian's
+// p, m, v are kept as of the step in last[i] and brought up to date only
+// when it is next used: before its projection (preprocess), before its next
+// gradient step, or by a flush.  Bringing it up to date replays exactly the
+// zero-gradient steps it missed, through adam_one with the coefficients of
+// each step, so every value equals dense Adam's bit for bit.  While it waits,
+// drift[i] bounds how far its mean (Euclidean, summed over the axes) and its
+// largest log-scale can still move: every further zero-gradient step moves a
+// parameter by lr_c(t) |m| b1^j / ((sqrt(v) b2^(j/2)) ibc2 + eps) <=
+// lr_c(last) |m| / (sqrt(v) + eps) r^j, r = b1 / sqrt(b2) < 1, so the total is
+// at most lr_c(last) |m| / (sqrt(v) + eps) r / (1 - r) (drift_factor adds 1 %
+// for the approximate square root and reciprocal).  The view gate widens its
+// tests by these bounds, and the projection decides exactly on the
+// up-to-date values.
+
+struct LazyArgs {
+    float *p[5], *m[5], *v[5];
+    int32_t *last;
+    float *drift;
+    const float *hist;
+    const int *d_step;
+    float b1, b2, eps, drift_factor;
+};
+
+// A Gaussian's 59 parameters, one per lane (lane l: parameters l and l + 32):
+// group and element of parameter q of the row (mean 3, log-scale 3, quat 4,
+// opacity 1, SH 48).
+__device__ __forceinline__ void param_slot(int q, int &k, int &e)
+{
+    k = q < 3 ? 0 : q < 6 ? 1 : q < 10 ? 2 : q < 11 ? 3 : 4;
+    e = q - (k == 0 ? 0 : k == 1 ? 3 : k == 2 ? 6 : k == 3 ? 10 : 11);
+}
+
+__device__ __forceinline__ int group_len(int k) { return k == 4 ? 48 : k == 3 ? 1 : k == 2 ? 4 : 3; }
+
+// The drift bounds after Gaussian i was brought to step t (one warp; lanes 0-5
+// hold the mean's and the log-scale's moments in mv, vv).
+__device__ __forceinline__ void lazy_set_drift_warp(const LazyArgs &a, long long i, int t, int lane, float mv,
+                                                    float vv)
+{
+    const float ratio = lane < 6 ? fabsf(mv) / (sqrtf(vv) + a.eps) : 0.f;
+    float dm = lane < 3 ? ratio : 0.f, ds = (lane >= 3 && lane < 6) ? ratio : 0.f;
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+        dm += __shfl_xor_sync(0xffffffffu, dm, o);
+        ds = fmaxf(ds, __shfl_xor_sync(0xffffffffu, ds, o));
+    }
+    if (lane == 0) {
+        a.drift[2 * i] = t > 0 ? a.drift_factor * a.hist[10 * t] * dm : 0.f;
+        a.drift[2 * i + 1] = t > 0 ? a.drift_factor * a.hist[10 * t + 1] * ds : 0.f;
+    }
+}
+
+// One warp brings Gaussian i from step last[i] to step `to` (replaying the
+// zero-gradient steps), then, if grad_row is given, takes the gradient step
+// to + 1 with that compact row.  Every lane computes exactly what the dense
+// kernel computes for its parameters.
+__device__ __forceinline__ void lazy_warp(const LazyArgs &a, long long i, int to, const float *grad_row, int lane)
+{
+    const int from = a.last[i];
+    const int t_end = grad_row ? to + 1 : to;
+    if (from >= t_end) return;
+    float mv_keep = 0.f, vv_keep = 0.f; // lane l < 6: moments of parameter l for the drift bound
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int q = lane + 32 * h;
+        if (q >= kGradRow) break;
+        int k, e;
+        param_slot(q, k, e);
+        const long long idx = i * group_len(k) + e;
+        float pv = a.p[k][idx], mv = a.m[k][idx], vv = a.v[k][idx];
+        for (int s = from + 1; s <= to; s++)
+            adam_one(pv, 0.f, mv, vv, a.b1, a.b2, a.hist[10 * s + k], a.hist[10 * s + 5 + k], a.eps);
+        if (grad_row)
+            adam_one(pv, grad_row[q], mv, vv, a.b1, a.b2, a.hist[10 * t_end + k], a.hist[10 * t_end + 5 + k], a.eps);
+        a.p[k][idx] = pv; a.m[k][idx] = mv; a.v[k][idx] = vv;
+        if (h == 0) { mv_keep = mv; vv_keep = vv; }
+    }
+    __syncwarp();
+    if (lane == 0) a.last[i] = t_end;
+    lazy_set_drift_warp(a, i, t_end, lane, mv_keep, vv_keep);
+}
+
+// The three kernels below run a grid of a few blocks per SM whose warps
+// stride over their items (a warp per item).
+
+// every candidate of the last gate: bring it to the current step
+__global__ void __launch_bounds__(256) lazy_catchup_kernel(LazyArgs a, const uint32_t *cand_g, const DevCounters *ctr)
+{
+    const unsigned long long nc = ctr->n_candidates, nw = (unsigned long long)gridDim.x * 8;
+    const int to = *a.d_step;
+    for (unsigned long long j = ((unsigned long long)blockIdx.x * 256 + threadIdx.x) >> 5; j < nc; j += nw)
+        lazy_warp(a, cand_g[j], to, nullptr, threadIdx.x & 31);
+}
+
+__global__ void __launch_bounds__(256) lazy_flush_kernel(LazyArgs a, long long n)
+{
+    const long long nw = (long long)gridDim.x * 8;
+    const int to = *a.d_step;
+    for (long long i = ((long long)blockIdx.x * 256 + threadIdx.x) >> 5; i < n; i += nw)
+        lazy_warp(a, i, to, nullptr, threadIdx.x & 31);
+}
+
+// every Gaussian with a record: bring it to step t - 1, then take the gradient
+// step t with its compact row; the others wait
+__global__ void __launch_bounds__(256) lazy_adam_kernel(LazyArgs a, const uint32_t *rec_g, const uint32_t *rec_first,
+                                                        const float *cgrad, const DevCounters *ctr)
+{
+    const unsigned long long nrec = ctr->n_records, nw = (unsigned long long)gridDim.x * 8;
+    const int t = *a.d_step;
+    for (unsigned long long r = ((unsigned long long)blockIdx.x * 256 + threadIdx.x) >> 5; r < nrec; r += nw) {
+        if (r > 0 && rec_g[r - 1] == rec_g[r]) continue;
+        const long long i = rec_g[r];
+        lazy_warp(a, i, t - 1, cgrad + (long long)rec_first[i] * kGradRow, threadIdx.x & 31);
+    }
+}
+
+static LazyArgs lazy_args(gs_workspace *ws, const gs_gaussian_grads &param)
+{
+    LazyArgs a;
+    float *P[5] = {param.mean, param.log_scale, param.quat, param.opacity_logit, param.sh};
+    const gs_gaussian_grads &m = ws->lazy.m, &v = ws->lazy.v;
+    float *M[5] = {m.mean, m.log_scale, m.quat, m.opacity_logit, m.sh};
+    float *V[5] = {v.mean, v.log_scale, v.quat, v.opacity_logit, v.sh};
+    for (int k = 0; k < 5; k++) { a.p[k] = P[k]; a.m[k] = M[k]; a.v[k] = V[k]; }
+    a.last = ws->lazy.last;
+    a.drift = ws->lazy.drift;
+    a.hist = ws->lazy.hist;
+    a.d_step = ws->d_adam_step;
+    a.b1 = ws->lazy.b1; a.b2 = ws->lazy.b2; a.eps = ws->lazy.eps; a.drift_factor = ws->lazy.drift_factor;
+    return a;
+}
+
+static gs_gaussian_grads params_of(const gs_gaussians &g)
+{
+    gs_gaussian_grads p;
+    p.mean = const_cast<float *>(g.mean);
+    p.log_scale = const_cast<float *>(g.log_scale);
+    p.quat = const_cast<float *>(g.quat);
+    p.opacity_logit = const_cast<float *>(g.opacity_logit);
+    p.sh = const_cast<float *>(g.sh);
+    return p;
+}
+
+cudaError_t launch_lazy_catchup(gs_workspace *ws, cudaStream_t st, const gs_gaussians &g)
+{
+    const unsigned blocks = (unsigned)std::min<long long>((g.n + 7) / 8, 8ll * ws->sm_count);
+    if (blocks == 0) return cudaSuccess;
+    lazy_catchup_kernel<<<blocks, 256, 0, st>>>(lazy_args(ws, params_of(g)), ws->cand_g, ws->ctr);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lazy_flush(gs_workspace *ws, cudaStream_t st, const gs_gaussians &g)
+{
+    const unsigned blocks = (unsigned)std::min<long long>((g.n + 7) / 8, 8ll * ws->sm_count);
+    if (blocks == 0) return cudaSuccess;
+    lazy_flush_kernel<<<blocks, 256, 0, st>>>(lazy_args(ws, params_of(g)), g.n);
+    note_launch();
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_lazy_adam(gs_workspace *ws, cudaStream_t st, const gs_gaussian_grads &param,
+                                    const gs_gaussian_grads &m, const gs_gaussian_grads &v, float b1, float b2,
+                                    float eps)
+{
+    (void)m; (void)v; (void)b1; (void)b2; (void)eps; // the enabled state's
+    const unsigned blocks = (unsigned)std::min<long long>((ws->cap.max_records + 7) / 8, 8ll * ws->sm_count);
+    if (blocks == 0) return cudaSuccess;
+    lazy_adam_kernel<<<blocks, 256, 0, st>>>(lazy_args(ws, param), ws->rec_g, ws->rec_first, ws->cgrad, ws->ctr);
+    note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_adam_sparse(gs_workspace *ws, cudaStream_t st, const gs_gaussian_grads &param,
@@ -468,8 +660,10 @@ cudaError_t launch_adam_sparse(gs_workspace *ws, cudaStream_t st, const gs_gauss
     AdamCoefArgs ca;
     for (int k = 0; k < 5; k++) ca.lr[k] = lr[k];
     ca.b1 = beta1; ca.b2 = beta2; ca.step = step;
-    adam_coef_kernel<<<1, 32, 0, st>>>(ca, ws->d_adam_step, ws->d_adam_coef);
+    adam_coef_kernel<<<1, 32, 0, st>>>(ca, ws->d_adam_step, ws->d_adam_coef, ws->lazy.hist, ws->lazy.max_steps,
+                                       ws->ctr);
     note_launch();
+    if (ws->lazy.enabled) return launch_lazy_adam(ws, st, param, m, v, beta1, beta2, eps);
     AdamTable t;
     t.n = 5;
     t.cgrad = ws->cgrad;

@@ -113,6 +113,19 @@ __device__ __forceinline__ bool lod_pass(const float m[3], int lod, const CamInf
     return d2 <= thr2[lod];
 }
 
+// lod_pass for a mean that may still move by up to D (deferred Adam steps):
+// passes whenever some point within D of m passes.  D = 0 is lod_pass.
+__device__ __forceinline__ bool lod_pass_margin(const float m[3], int lod, const CamInfo &cam, const RenderConsts &rc,
+                                                const float *thr2, const float *thr, float D)
+{
+    if (D == 0.f) return lod_pass(m, lod, cam, rc, thr2);
+    if (!rc.lod_enable || lod == 0) return true;
+    if (lod > rc.lod_Lmax) return false;
+    const float dx = m[0] - cam.campos[0], dy = m[1] - cam.campos[1], dz = m[2] - cam.campos[2];
+    const float lim = 1.0001f * (thr[lod] + D);
+    return dx * dx + dy * dy + dz * dz <= lim * lim;
+}
+
 // Camera-space mean in float, for the gate only, with a bound on its distance
 // from the double-precision value the projection uses: three additions and
 // the final rounding each err by at most 2^-24 of a partial sum bounded by
@@ -267,6 +280,7 @@ struct PreOut {
     unsigned long long *cand_mask;
     uint32_t *gate_g;              // [N] block-strided candidates of the gate's first pass
     unsigned long long *gate_mask; // [N]
+    const float *drift;            // [N][2] drift bounds of Gaussians with deferred Adam steps, or NULL
     uint32_t *rec_first;           // first record of each Gaussian, ~0 when it has none
     unsigned long long *lb_status; // word 0: ticket
     DevCounters *ctr;
@@ -320,6 +334,7 @@ __device__ __forceinline__ void stage_cameras(const CamTable &ct, CamInfo *s_cam
 struct GateShared {
     CamInfo cams[GS_MAX_CAMERAS];
     float thr2[kMaxLod + 1];
+    float thr[kMaxLod + 1];  // sqrt of thr2, for the drift margin
     unsigned cnt[kGateItems][8];
     unsigned total;
 };
@@ -331,13 +346,17 @@ __device__ __forceinline__ void gate_masks(const GaussPtrs &g, const PreOut &o, 
     const int ncam = ct.n, tw = ct.tile_w, th = ct.tile_h;
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int l = 0; l <= kMaxLod; l++) sh.thr2[l] = rc.lod_thr2[l];
+        for (int l = 0; l <= kMaxLod; l++) {
+            sh.thr2[l] = rc.lod_thr2[l];
+            sh.thr[l] = sqrtf(rc.lod_thr2[l]);
+        }
     }
     stage_cameras(ct, sh.cams);
     const long long n = g.n;
     float mx[kGateItems], my[kGateItems], mz[kGateItems], ls[kGateItems][3];
     int lod[kGateItems];
     uint32_t cw[kGateItems];
+    float dm[kGateItems], dl[kGateItems]; // drift bounds (deferred Adam steps), 0 when up to date
 #pragma unroll
     for (int k = 0; k < kGateItems; k++) {
         const long long i = block0 + k * 256 + threadIdx.x;
@@ -350,6 +369,8 @@ __device__ __forceinline__ void gate_masks(const GaussPtrs &g, const PreOut &o, 
         ls[k][2] = ok ? g.log_scale[3 * i + 2] : 0.f;
         lod[k] = (ok && rc.lod_enable && g.lod) ? (int)g.lod[i] : 0;
         cw[k] = (ok && rc.cull_enable && o.cull) ? o.cull[i >> 5] : 0u;
+        dm[k] = (ok && o.drift) ? o.drift[2 * i] : 0.f;
+        dl[k] = (ok && o.drift) ? o.drift[2 * i + 1] : 0.f;
     }
     if (ncam == 1) {
         // one camera: every test of every item evaluated without branches, so
@@ -359,12 +380,13 @@ __device__ __forceinline__ void gate_masks(const GaussPtrs &g, const PreOut &o, 
         for (int k = 0; k < kGateItems; k++) {
             const long long i = block0 + k * 256 + threadIdx.x;
             const float m[3] = {mx[k], my[k], mz[k]};
-            const bool lod_ok = lod_pass(m, lod[k], cam, rc, sh.thr2);
+            const bool lod_ok = lod_pass_margin(m, lod[k], cam, rc, sh.thr2, sh.thr, dm[k]);
             const bool culled = rc.cull_enable && ((cw[k] >> (i & 31)) & 1u);
             float t[3], te[3];
             camera_point(m, cam, t, te);
+            te[0] += dm[k]; te[1] += dm[k]; te[2] += dm[k];
             const bool near_ok = t[2] + te[2] > rc.znear; // the exact near test is the projection's
-            const float smax = 1.0001f * __expf(fmaxf(ls[k][0], fmaxf(ls[k][1], ls[k][2])));
+            const float smax = 1.0001f * __expf(fmaxf(ls[k][0], fmaxf(ls[k][1], ls[k][2])) + dl[k]);
             const bool on = maybe_on_screen(t, te, smax, cam, tw, th, rc);
             mask[k] = (i < n && lod_ok && !culled && near_ok && on) ? 1ull : 0ull;
         }
@@ -378,12 +400,13 @@ __device__ __forceinline__ void gate_masks(const GaussPtrs &g, const PreOut &o, 
             float smax = -1.f;
             for (int c = 0; c < ncam; c++) {
                 const CamInfo &cam = sh.cams[c];
-                if (!lod_pass(m, lod[k], cam, rc, sh.thr2)) continue;
+                if (!lod_pass_margin(m, lod[k], cam, rc, sh.thr2, sh.thr, dm[k])) continue;
                 if (rc.cull_enable && (c == 0 ? ((cw[k] >> (i & 31)) & 1u) : cull_bit(o, c, i))) continue;
                 float t[3], te[3];
                 camera_point(m, cam, t, te);
+                te[0] += dm[k]; te[1] += dm[k]; te[2] += dm[k];
                 if (!(t[2] + te[2] > rc.znear)) continue; // the exact near test is the projection's
-                if (smax < 0.f) smax = 1.0001f * __expf(fmaxf(ls[k][0], fmaxf(ls[k][1], ls[k][2])));
+                if (smax < 0.f) smax = 1.0001f * __expf(fmaxf(ls[k][0], fmaxf(ls[k][1], ls[k][2])) + dl[k]);
                 if (maybe_on_screen(t, te, smax, cam, tw, th, rc)) mask[k] |= 1ull << c;
             }
         }
@@ -495,11 +518,16 @@ __global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, 
 {
     const CamTable &ct = *ctp;
     __shared__ CamInfo s_cams[GS_MAX_CAMERAS];
+    __shared__ float s_thr2[kMaxLod + 1];
     __shared__ unsigned s_bid;
     __shared__ unsigned long long s_warp[8];
     __shared__ unsigned long long s_base;
     const unsigned long long ncand = o.ctr->n_candidates;
     const int tw = ct.tile_w, th = ct.tile_h;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int l = 0; l <= kMaxLod; l++) s_thr2[l] = rc.lod_thr2[l];
+    }
     stage_cameras(ct, s_cams);
     // persistent blocks: each takes the next 256 candidates (tickets in order,
     // so every look-back waits only on chunks already being processed)
@@ -518,8 +546,11 @@ __global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, 
         const unsigned long long cm = o.cand_mask[j];
         L.m[0] = g.mean[3 * i]; L.m[1] = g.mean[3 * i + 1]; L.m[2] = g.mean[3 * i + 2];
         load_shape(g, i, L);
+        const int lod = (rc.lod_enable && g.lod) ? (int)g.lod[i] : 0;
         for (unsigned long long mm = cm; mm; mm &= mm - 1) {
             const int c = __ffsll((long long)mm) - 1;
+            // the exact LOD decision (the gate's is widened for Gaussians with deferred steps)
+            if (!lod_pass(L.m, lod, s_cams[c], rc, s_thr2)) continue;
             double td[3];
             camera_point_d(L.m, s_cams[c], td);
             if (!(__double2float_rn(td[2]) > rc.znear)) continue;
@@ -613,6 +644,7 @@ cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t 
     o.rec_cam = ws->rec_cam; o.rd0 = ws->rd0; o.rd1 = ws->rd1; o.rd2 = ws->rd2; o.rect = ws->rect;
     o.clampm = ws->clampm; o.cand_g = ws->cand_g; o.cand_mask = ws->cand_mask; o.rec_first = ws->rec_first;
     o.gate_g = ws->gate_g; o.gate_mask = ws->gate_mask;
+    o.drift = ws->lazy.enabled ? ws->lazy.drift : nullptr;
     o.lb_status = ws->lb_status;
     o.ctr = ws->ctr; o.max_records = ws->cap.max_records;
     o.cull = ws->rc.cull_enable ? cull : nullptr;
@@ -628,6 +660,8 @@ cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t 
     note_launch();
     if ((e = cudaMemsetAsync(ws->lb_status, 0, (pblocks + 1) * sizeof(unsigned long long), st)) != cudaSuccess)
         return e;
+    // deferred Adam steps: bring the candidates up to date before projecting them
+    if (ws->lazy.enabled && (e = launch_lazy_catchup(ws, st, ws->g)) != cudaSuccess) return e;
     // projection: two persistent 256-thread blocks per SM
     const unsigned pgrid = std::min<unsigned>(pblocks, 2u * (unsigned)ws->sm_count);
     project_kernel<<<pgrid, 256, 0, st>>>(gp, o, ws->d_cams, ws->rc);

@@ -26,7 +26,7 @@ class TrainStep:
 
     def __init__(self, g: B.GaussianTensors, cams, targets: torch.Tensor, params: B.RenderParams, lr,
                  lam: float = 0.2, beta: float = 10.0, ws: B.Workspace | None = None, cull=None,
-                 capacity: dict | None = None, betas=(0.9, 0.999), eps: float = 1e-15):
+                 capacity: dict | None = None, betas=(0.9, 0.999), eps: float = 1e-15, lazy: bool = False):
         V, C, H, W = targets.shape
         assert C == 3 and len(cams) == V and all(c.width == W and c.height == H for c in cams)
         self.g, self.params, self.lr, self.lam, self.beta = g, params, list(lr), lam, beta
@@ -47,6 +47,12 @@ class TrainStep:
         self.loss = torch.zeros(1, device=targets.device)
         self.reg = torch.zeros(1, device=targets.device)
         self.graph = None
+        self.lazy = lazy
+        if lazy:
+            # deferred zero-gradient steps: exact, but only Gaussians in use are touched
+            self.last = torch.zeros(g.n, dtype=torch.int32, device=targets.device)
+            self.drift = torch.zeros(g.n, 2, device=targets.device)
+            self.ws.adam_lazy_enable(self.m, self.v, self.last, self.drift, betas[0], betas[1], eps)
         self.set_views(cams, targets)
 
     def set_views(self, cams, targets: torch.Tensor | None = None):
@@ -66,6 +72,11 @@ class TrainStep:
         ws.render_bwd_compact(self.g, self.dL, scale_reg_beta=self.beta, scale_reg_value=self.reg)
         ws.adam_step_compact(self.g, self.m, self.v, self.lr, step, beta1=self.betas[0], beta2=self.betas[1],
                              eps=self.eps)
+
+    def flush(self):
+        """Brings every Gaussian up to the current step (deferred steps only)."""
+        if self.lazy:
+            self.ws.adam_flush(self.g)
 
     def run(self, step: int = 0):
         """One eager step; step >= 1 sets the step number, 0 continues the

@@ -1,0 +1,103 @@
+"""Deferred zero-gradient Adam steps: a training run with them equals dense
+Adam bit for bit (every loss on the way, every parameter and moment after a
+flush), with views that move Gaussians in and out of the active set, the LOD
+gate engaged, and the step replayed from a CUDA graph."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2605_13794_gb300 import binding as B
+from paper_2605_13794_gb300 import synth
+from paper_2605_13794_gb300.train import TrainStep
+
+pytestmark = pytest.mark.gpu
+
+LR = [1.6e-3, 5e-3, 1e-3, 5e-2, 2.5e-3]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2605_13794_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def _views(k, n=2, W=96, H=80):
+    # a narrow field of view swinging across the scene: each step sees part of it
+    rng = np.random.default_rng(3000 + k)
+    cams = []
+    for _ in range(n):
+        a = rng.uniform(-0.9, 0.9)
+        eye = (2.0 * np.sin(a), rng.uniform(-0.3, 0.3), 4.0 - 2.0 * np.cos(a))
+        tgt = (rng.uniform(-0.6, 0.6), rng.uniform(-0.6, 0.6), 4.0)
+        cams.append(synth.look_at_camera(eye, tgt, (0.0, -1.0, 0.0), W, H, 35.0))
+    return cams
+
+
+def _targets(cams, seed):
+    return torch.from_numpy(np.stack([synth.noise_target(c.width, c.height, seed=seed + i)
+                                      for i, c in enumerate(cams)]).astype(np.float32)).cuda()
+
+
+def _scene():
+    g = synth.plain_scene(20000, seed=81)
+    g.lod[:] = np.random.default_rng(82).integers(0, 4, g.n).astype(np.uint8)
+    return g
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_deferred_steps_equal_dense_adam(graph):
+    g = _scene()
+    params = B.RenderParams(lod_enable=True, lod_d0=4.0, lod_Lmax=3)
+    gd, gl = B.GaussianTensors.from_host(g), B.GaussianTensors.from_host(g)
+    c0 = _views(0)
+    dense = TrainStep(gd, c0, _targets(c0, 5), params, LR)
+    lazy = TrainStep(gl, c0, _targets(c0, 5), params, LR, lazy=True)
+    dense.run(step=1)
+    lazy.run(step=1)
+    if graph:
+        lazy.capture()
+    behind = 0
+    for k in range(1, 14):
+        cams, tg = _views(k), _targets(_views(k), 5 + 3 * k)
+        dense.set_views(cams, tg)
+        dense.run()
+        lazy.set_views(cams, tg)
+        lazy.replay() if graph else lazy.run()
+        torch.cuda.synchronize()
+        assert torch.equal(dense.loss, lazy.loss), k
+        assert torch.equal(dense.reg, lazy.reg), k
+        behind = max(behind, int((lazy.last < k + 1).sum().item()))
+    dense.ws.sync_status()
+    lazy.ws.sync_status()
+    assert behind > 1000  # deferred steps did happen
+    lazy.flush()
+    torch.cuda.synchronize()
+    assert int((lazy.last == 14).sum().item()) == g.n
+    for a, b in zip(gd.params() + dense.m.params() + dense.v.params(), gl.params() + lazy.m.params() + lazy.v.params()):
+        assert torch.equal(a, b)
+
+
+def test_drift_bounds_hold():
+    # after a run the bounds recorded for waiting Gaussians cover how far a
+    # flush then moves their means and largest log-scales
+    g = _scene()
+    params = B.RenderParams()
+    gl = B.GaussianTensors.from_host(g)
+    c0 = _views(0)
+    lazy = TrainStep(gl, c0, _targets(c0, 9), params, LR, lazy=True)
+    lazy.run(step=1)
+    for k in range(1, 8):
+        cams = _views(k)
+        lazy.set_views(cams, _targets(cams, 9 + k))
+        lazy.run()
+    torch.cuda.synchronize()
+    mean0, ls0, drift = gl.mean.clone(), gl.log_scale.clone(), lazy.drift.clone()
+    waiting = lazy.last < 8
+    lazy.flush()
+    torch.cuda.synchronize()
+    dmean = (gl.mean - mean0).norm(dim=1)
+    dls = (gl.log_scale - ls0).abs().max(dim=1).values
+    assert waiting.sum() > 100
+    assert bool((dmean[waiting] <= drift[waiting, 0] + 1e-7).all())
+    assert bool((dls[waiting] <= drift[waiting, 1] + 1e-7).all())
