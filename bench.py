@@ -242,10 +242,44 @@ class Step:
 
 # ---- roofline bookkeeping --------------------------------------------------------
 
-def adam_bytes(n, n_visible):
-    # per parameter float: read and write p, m, v (24 bytes); per Gaussian the
-    # first-record index (4 bytes); per Gaussian with a record its 59-float row
-    return 59 * n * 24 + 4 * n + 59 * 4 * n_visible
+
+# Algorithmic FP32 operations of the compositing adjoint (App. A's compositing,
+# differentiated), counted per (pixel, list entry) pair of the reverse walk (an
+# FMA is two, a special-function op one).  Every pair re-evaluates the entry's
+# exponent, alpha and the skip test; a pair that composites adds the adjoint.
+BWD_FLOP_EVAL = 13
+BWD_FLOP_COMPOSITE = 59
+# FP32 lanes per SM (FMA pipe) and special-function lanes per SM
+FMA_LANES, SFU_LANES, SMS = 128, 16, 152
+# Algorithmic DRAM bytes of the adjoint: per list entry its sorted index, the
+# staged record (3 x 16 B), the record's slot offset and rectangle and its
+# 9-float slot written back; per pixel dL/dC, T_final and n_contrib.
+BWD_BYTES_ENTRY = 4 + 48 + 4 + 8 + 36
+BWD_BYTES_PIXEL = 12 + 4 + 4
+
+
+def bwd_roofline(fragments, composited, instances, pixels, kernel_ms, sm_mhz, peaks):
+    """Roofline of the compositing adjoint: achieved FP32 rate against the FMA
+    pipe's peak at the maximum SM clock, with the special-function and DRAM
+    fractions beside it."""
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    flops = BWD_FLOP_EVAL * fragments + BWD_FLOP_COMPOSITE * composited
+    sec = kernel_ms * 1e-3
+    achieved = flops / sec / 1e12
+    peak = SMS * FMA_LANES * 2 * max_mhz * 1e6 / 1e12
+    sfu_ops = fragments + composited        # ex2 per pair, reciprocal per composited pair
+    sfu_peak = SMS * SFU_LANES * max_mhz * 1e6
+    nbytes = BWD_BYTES_ENTRY * instances + BWD_BYTES_PIXEL * pixels
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    return {"bound": "alu", "kernel": "render_bwd_kernel", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz (measured max SM clock)",
+            "algorithmic_flops_per_launch": flops, "kernel_ms": kernel_ms,
+            "fragments_per_launch": fragments, "composited_per_launch": composited,
+            "sfu_frac": sfu_ops / sec / sfu_peak,
+            "hbm": {"algorithmic_bytes_per_launch": nbytes, "achieved_gbs": nbytes / sec / 1e9, "peak": hbm,
+                    "frac": nbytes / sec / 1e9 / hbm, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"},
+            "sm_mhz_median": sm_mhz}
 
 
 def measured_peaks():
@@ -255,10 +289,10 @@ def measured_peaks():
         return {}
 
 
-def traffic_from_profile(kernel_file):
-    """Per-launch DRAM bytes of the dominant kernel from the committed ncu
-    summary, if it was taken on the current source of that kernel."""
-    path = os.path.join(ROOT, "profiles", "adam_kernel_city5M.md")
+def traffic_from_profile(profile, kernel_file):
+    """Per-launch DRAM bytes of a kernel from its committed ncu summary, if the
+    summary was taken on the current source of that kernel."""
+    path = os.path.join(ROOT, "profiles", profile)
     src = os.path.join(ROOT, "paper_2605_13794_gb300", "csrc", kernel_file)
     try:
         text = open(path).read()
@@ -467,9 +501,6 @@ def main():
         step.run()
     torch.cuda.synchronize()
     step.ws.sync_status()
-    # Gaussians with a record in the training render (sizes the compact gradient rows)
-    step.ws.preprocess(step.gt, [cam], step.params_train, step.cull)
-    step.nvis_train = step.ws.counts()["n_visible"]
 
     # ---- device-timed region: K whole steps, inputs resident in HBM
     uuid = None
@@ -482,6 +513,9 @@ def main():
     barrier(world)
     torch.cuda.synchronize()
     sampler.start()
+    # per-launch device time of the rasterisers, from event pairs the library
+    # records around each launch on its stream
+    step.ws.kernel_timing(True)
     launches0 = B.kernel_launches()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     w0 = time.time()
@@ -499,6 +533,11 @@ def main():
     launches = B.kernel_launches() - launches0
     barrier(world)
     step.ws.sync_status()
+    kt = {name: step.ws.kernel_time(k) for name, k in (("render_fwd_kernel", B.GS_KT_RENDER_FWD),
+                                                         ("render_bwd_kernel", B.GS_KT_RENDER_BWD),
+                                                         ("importance_raster_kernel", B.GS_KT_IMPORTANCE))}
+    step.ws.kernel_timing(False)
+    kernel_ms = {name: max_over_ranks(t / max(n, 1), world) for name, (t, n) in kt.items()}
     ms = start.elapsed_time(end) / args.steps
     ms = max_over_ranks(ms, world)
     stage_ms = {name: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
@@ -540,20 +579,21 @@ def main():
                "mgaussian_per_s": job_rate(g.n, fb_ms, world) / 1e6,
                "stages": ["preprocess", "bin_sort", "render_fwd", "render_bwd"]}
     gauss = job_rate(g.n, ms, world) / 1e6
-    counts = step.ws.counts()
     peaks = measured_peaks()
     dom = max(stage_ms, key=stage_ms.get)
-    # the roofline is reported for the Adam kernel (one launch per step, its
-    # own stage): algorithmic bytes 24 per parameter float, 59 floats per
-    # Gaussian, plus the index and the compact rows of the visible Gaussians
-    a_ms = stage_ms["adam"]
-    nvis_train = step.nvis_train
-    achieved = adam_bytes(g.n, nvis_train) / (a_ms * 1e-3) / 1e9
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    roof = {"bound": "hbm", "kernel": "adam_kernel", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": traffic_from_profile("optim.cu"),
-            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-            "algorithmic_bytes_per_launch": adam_bytes(g.n, nvis_train), "dominant_stage": dom}
+    # the training render's counts (the last preprocess of a step is the
+    # importance sweep's): one more untimed forward and backward of this view
+    step.ws.preprocess(step.gt, [cam], step.params_train, step.cull)
+    step.ws.bin_sort()
+    step.ws.render_fwd(step.rgb, step.T)
+    step.ws.photometric_loss(step.rgb.view(1, 3, cam.height, cam.width), step.target, LAMBDA, step.loss, step.dL)
+    step.ws.render_bwd_compact(step.gt, step.dL, scale_reg_beta=BETA, scale_reg_value=step.reg)
+    counts = step.ws.counts()
+    # the dominant kernel of the step is the compositing adjoint: FP32-issue bound
+    roof = bwd_roofline(counts["fragments"], counts["composited"], counts["n_instances"], P,
+                        kernel_ms["render_bwd_kernel"], clocks.get("sm_mhz"), peaks)
+    roof["traffic"] = traffic_from_profile("render_bwd_kernel_city5M_1080p.md", "render.cu")
+    roof["dominant_stage"] = dom
     line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -565,6 +605,7 @@ def main():
             "fwd_bwd": fwd_bwd,
             "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
             "counts": {k: counts[k] for k in ("n_records", "n_instances", "n_visible")},
+            "kernel_ms": {k: round(v, 4) for k, v in kernel_ms.items()},
             "roofline": roof,
             "e2e": {"value": job_rate(P, e2e_ms, world) / 1e6, "unit": "Mpix/s", "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -148,6 +148,10 @@ typedef struct {
     int64_t instances_needed; /* equals n_instances unless capacity was exceeded */
     int32_t error;            /* device error word: 0 or a gs_status */
     int32_t error_site;       /* kernel that set it (implementation detail) */
+    int64_t fragments;        /* sum over pixels of the list entries up to and including the pixel's
+                                 last composited one: the (pixel, entry) pairs the backward walks.
+                                 Counted by gs_render_bwd, reset by gs_preprocess */
+    int64_t composited;       /* those of the pairs above that composite (alpha >= alpha_min) */
 } gs_counts;
 
 typedef struct {
@@ -397,6 +401,21 @@ int gs_count_views(gs_workspace *ws, uint32_t *counts, gs_stream stream);
  * bounded and leave the output undefined if one gives up. */
 int gs_visible_set_static(const float *w, int64_t n, float vis_mass, uint32_t *cull_out, uint32_t *cvis_accum,
                           gs_stream stream);
+
+/* Kernel timing, for measurement.  While on, each launch of the timed kernels
+ * below is bracketed by a CUDA event pair recorded on the stream it is launched
+ * on (launches issued under stream capture are not timed).  Turning timing on
+ * discards earlier records; the first 64 launches of each kernel are recorded.
+ * gs_kernel_time synchronises those events and returns the summed device time
+ * (ms) and the number of timed launches of one kernel.  Off by default. */
+enum {
+    GS_KT_RENDER_FWD = 0, /* gs_render_fwd's compositing kernel */
+    GS_KT_RENDER_BWD = 1, /* the compositing adjoint (per (record, tile) slots) */
+    GS_KT_IMPORTANCE = 2, /* the importance sweep's rasteriser */
+    GS_KT_COUNT = 3
+};
+int gs_kernel_timing(gs_workspace *ws, int32_t enable);
+int gs_kernel_time(gs_workspace *ws, int32_t kernel, double *total_ms, int64_t *launches);
 
 /* Synchronises the stream and returns the device error word as a status. */
 int gs_sync_status(gs_workspace *ws, gs_stream stream);

@@ -31,7 +31,10 @@ EXPORTS = ("gs_default_params", "gs_last_error", "gs_workspace_create", "gs_work
            "gs_kernel_launches", "gs_render_bwd_adam", "gs_render_bwd_compact", "gs_adam_step_compact",
            "gs_visible_set_static", "gs_upload_cameras", "gs_preprocess_uploaded", "gs_workspace_set_sort_chunk",
            "gs_prune_sample", "gs_prune_mass", "gs_compact", "gs_densify", "gs_count_views", "gs_adam_lazy_enable",
-           "gs_adam_lazy_disable", "gs_adam_flush")
+           "gs_adam_lazy_disable", "gs_adam_flush", "gs_kernel_timing", "gs_kernel_time")
+
+# kernels gs_kernel_timing brackets with events (include/gsblitz.h)
+GS_KT_RENDER_FWD, GS_KT_RENDER_BWD, GS_KT_IMPORTANCE = range(3)
 
 
 class GSError(RuntimeError):
@@ -85,7 +88,8 @@ class GSRenderParams(ctypes.Structure):
 class GSCounts(ctypes.Structure):
     _fields_ = [("n_records", ctypes.c_int64), ("n_instances", ctypes.c_int64), ("n_visible", ctypes.c_int64),
                 ("records_needed", ctypes.c_int64), ("instances_needed", ctypes.c_int64),
-                ("error", ctypes.c_int32), ("error_site", ctypes.c_int32)]
+                ("error", ctypes.c_int32), ("error_site", ctypes.c_int32), ("fragments", ctypes.c_int64),
+                ("composited", ctypes.c_int64)]
 
 
 class GSAdamGroup(ctypes.Structure):
@@ -141,6 +145,8 @@ def lib() -> ctypes.CDLL:
         L.gs_workspace_counts.argtypes = [vp, vp, vp]
         L.gs_clear_error.argtypes = [vp, vp]
         L.gs_workspace_buffer.argtypes = [vp, i32, vp, vp]
+        L.gs_kernel_timing.argtypes = [vp, i32]
+        L.gs_kernel_time.argtypes = [vp, i32, vp, vp]
         for name in EXPORTS:
             if name not in ("gs_default_params", "gs_last_error", "gs_workspace_bytes", "gs_kernel_launches"):
                 getattr(L, name).restype = ctypes.c_int
@@ -446,6 +452,16 @@ class Workspace:
 
     def sync_status(self, stream=None):
         _check(lib().gs_sync_status(self._ws, _stream(stream)))
+
+    def kernel_timing(self, enable: bool = True):
+        """Turns event timing of the rasterisers' launches on (discarding older records) or off."""
+        _check(lib().gs_kernel_timing(self._ws, int(bool(enable))))
+
+    def kernel_time(self, kernel: int):
+        """(summed device ms, timed launches) of one kernel since timing was turned on."""
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        _check(lib().gs_kernel_time(self._ws, int(kernel), ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
 
     def clear_error(self, stream=None):
         _check(lib().gs_clear_error(self._ws, _stream(stream)))

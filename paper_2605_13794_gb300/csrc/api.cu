@@ -155,6 +155,40 @@ int gs::report_error(int code, const char *msg)
     return fail(code, "%s", msg);
 }
 
+static cudaError_t kt_release(gs_workspace *ws)
+{
+    cudaError_t e = cudaSuccess, e2;
+    for (int k = 0; k < GS_KT_COUNT; k++)
+        for (int i = 0; i < gs_workspace::kTimedPairs; i++)
+            for (int h = 0; h < 2; h++)
+                if (ws->kt.ev[k][i][h]) {
+                    if ((e2 = cudaEventDestroy(ws->kt.ev[k][i][h])) != cudaSuccess) e = e2;
+                    ws->kt.ev[k][i][h] = nullptr;
+                }
+    ws->kt.on = 0;
+    return e;
+}
+
+void gs::kt_begin(gs_workspace *ws, int id, cudaStream_t st)
+{
+    if (!ws->kt.on) return;
+    ws->kt.launches[id]++;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    if (ws->kt.used[id] >= gs_workspace::kTimedPairs) return;
+    cudaEventRecord(ws->kt.ev[id][ws->kt.used[id]][0], st);
+}
+
+void gs::kt_end(gs_workspace *ws, int id, cudaStream_t st)
+{
+    if (!ws->kt.on) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    if (ws->kt.used[id] >= gs_workspace::kTimedPairs) return;
+    cudaEventRecord(ws->kt.ev[id][ws->kt.used[id]][1], st);
+    ws->kt.used[id]++;
+}
+
 extern "C" {
 
 int64_t gs_kernel_launches(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
@@ -281,10 +315,49 @@ int gs_workspace_create(const gs_capacity *cap, gs_workspace **out)
     return GS_OK;
 }
 
+int gs_kernel_timing(gs_workspace *ws, int32_t enable)
+{
+    if (!ws) return fail(GS_ERR_INVALID_ARG, "gs_kernel_timing: null workspace");
+    cudaError_t e = kt_release(ws);
+    if (e != cudaSuccess) return cuda_fail(e, "gs_kernel_timing");
+    for (int k = 0; k < GS_KT_COUNT; k++) {
+        ws->kt.used[k] = 0;
+        ws->kt.launches[k] = 0;
+    }
+    if (!enable) return GS_OK;
+    for (int k = 0; k < GS_KT_COUNT; k++)
+        for (int i = 0; i < gs_workspace::kTimedPairs; i++)
+            for (int h = 0; h < 2; h++)
+                if ((e = cudaEventCreate(&ws->kt.ev[k][i][h])) != cudaSuccess) {
+                    kt_release(ws);
+                    return cuda_fail(e, "gs_kernel_timing");
+                }
+    ws->kt.on = 1;
+    return GS_OK;
+}
+
+int gs_kernel_time(gs_workspace *ws, int32_t kernel, double *total_ms, int64_t *launches)
+{
+    if (!ws || !total_ms || !launches || kernel < 0 || kernel >= GS_KT_COUNT)
+        return fail(GS_ERR_INVALID_ARG, "gs_kernel_time: bad arguments");
+    *total_ms = 0.0;
+    *launches = 0;
+    if (!ws->kt.on) return GS_OK;
+    for (int i = 0; i < ws->kt.used[kernel]; i++) {
+        cudaError_t e = cudaEventSynchronize(ws->kt.ev[kernel][i][1]);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ws->kt.ev[kernel][i][0], ws->kt.ev[kernel][i][1]);
+        if (e != cudaSuccess) return cuda_fail(e, "gs_kernel_time");
+        *total_ms += ms;
+    }
+    *launches = ws->kt.used[kernel];
+    return GS_OK;
+}
+
 int gs_workspace_destroy(gs_workspace *ws)
 {
     if (!ws) return GS_OK;
-    cudaError_t e = cudaSuccess, e2;
+    cudaError_t e = kt_release(ws), e2;
     for (int k = 0; k < gs_workspace::kStageSlots; k++)
         if (ws->stage_ev[k] && (e2 = cudaEventDestroy(ws->stage_ev[k])) != cudaSuccess) e = e2;
     if (ws->h_stage && (e2 = cudaFreeHost(ws->h_stage)) != cudaSuccess) e = e2;
@@ -748,6 +821,8 @@ int gs_workspace_counts(gs_workspace *ws, gs_counts *out, gs_stream stream)
     out->instances_needed = (int64_t)d.instances_needed;
     out->error = d.error;
     out->error_site = d.error_site;
+    out->fragments = (int64_t)d.fragments;
+    out->composited = (int64_t)d.composited;
     return GS_OK;
 }
 

@@ -8,6 +8,21 @@
 
 namespace gs {
 
+// Single-instruction square root and reciprocal (PTX .approx forms).
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;          // keys per thread in a radix pass (default)
 constexpr int kSortTile = kSortThreads * kSortItems;
@@ -32,9 +47,11 @@ struct DevCounters {
     int error;
     int error_site;
     unsigned long long sel_count[GS_MAX_CAMERAS]; // w > 0 entries per camera (importance)
+    unsigned long long fragments;      // sum over pixels of the entries up to the last composited one
+    unsigned long long composited;     // ... of which composited (alpha >= alpha_min)
 };
 
-// Per-camera constants passed by value to the kernels.
+// Per-camera constants (the device camera table).
 struct CamInfo {
     float R[9], t[3];
     float fx, fy, cx, cy;
@@ -287,11 +304,23 @@ struct gs_workspace {
     int have_compact;    // compact gradient rows of the current binning exist
     int depth_buf;       // buffer holding sorted depth order
     int tile_buf;        // buffer holding sorted instances
+    // kernel timing (gs_kernel_timing): event pairs around the rasterisers' launches
+    static constexpr int kTimedPairs = 64;
+    struct {
+        int on;
+        cudaEvent_t ev[GS_KT_COUNT][kTimedPairs][2];
+        int used[GS_KT_COUNT];
+        long long launches[GS_KT_COUNT]; // launches while on, recorded or not
+    } kt;
 };
 
 namespace gs {
 // Counts one kernel launch of this library (process-wide, see gs_kernel_launches).
 void note_launch();
+// Kernel timing: kt_begin/kt_end bracket one launch of kernel id on stream st
+// while timing is on (nothing under stream capture, nothing past kTimedPairs).
+void kt_begin(gs_workspace *ws, int id, cudaStream_t st);
+void kt_end(gs_workspace *ws, int id, cudaStream_t st);
 // Records msg as the calling thread's gs_last_error() and returns code.
 int report_error(int code, const char *msg);
 // Kernel launchers (defined in the .cu files).

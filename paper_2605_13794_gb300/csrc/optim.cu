@@ -284,20 +284,6 @@ struct AdamTable {
 constexpr int kAdamPerThread = 4;  // float4 chunks per thread
 constexpr int kAdamBlockElems = 256 * 4 * kAdamPerThread;
 
-__device__ __forceinline__ float sqrt_approx(float x)
-{
-    float y;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float rcp_approx(float x)
-{
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
 // m <- b1 m + (1 - b1) g;  v <- b2 v + (1 - b2) g^2;  p <- p - lr_c m / (sqrt(v) ibc2 + eps)
 // with lr_c = lr / (1 - b1^t), ibc2 = 1 / sqrt(1 - b2^t) (bias correction folded in).
 __device__ __forceinline__ void adam_one(float &p, float g, float &m, float &v, float b1, float b2, float lr_c,
@@ -541,25 +527,47 @@ __device__ __forceinline__ void lazy_warp(const LazyArgs &a, long long i, int to
     const int from = a.last[i];
     const int t_end = grad_row ? to + 1 : to;
     if (from >= t_end) return;
-    float mv_keep = 0.f, vv_keep = 0.f; // lane l < 6: moments of parameter l for the drift bound
+    long long idx[2];
+    int grp[2];
+    float mv[2] = {0.f, 0.f}, vv[2] = {0.f, 0.f};
+    bool zero = true;
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         const int q = lane + 32 * h;
-        if (q >= kGradRow) break;
-        int k, e;
-        param_slot(q, k, e);
-        const long long idx = i * group_len(k) + e;
-        float pv = a.p[k][idx], mv = a.m[k][idx], vv = a.v[k][idx];
-        for (int s = from + 1; s <= to; s++)
-            adam_one(pv, 0.f, mv, vv, a.b1, a.b2, a.hist[10 * s + k], a.hist[10 * s + 5 + k], a.eps);
-        if (grad_row)
-            adam_one(pv, grad_row[q], mv, vv, a.b1, a.b2, a.hist[10 * t_end + k], a.hist[10 * t_end + 5 + k], a.eps);
-        a.p[k][idx] = pv; a.m[k][idx] = mv; a.v[k][idx] = vv;
-        if (h == 0) { mv_keep = mv; vv_keep = vv; }
+        int e;
+        param_slot(q < kGradRow ? q : 0, grp[h], e);
+        idx[h] = i * group_len(grp[h]) + e;
+        if (q < kGradRow) {
+            mv[h] = a.m[grp[h]][idx[h]];
+            vv[h] = a.v[grp[h]][idx[h]];
+            zero = zero && __float_as_uint(mv[h]) == 0u && __float_as_uint(vv[h]) == 0u;
+        }
+    }
+    // (p, +0, +0) is a fixed point of the zero-gradient step (m and v stay +0,
+    // p moves by (-lr m) / (sqrt(v) ibc2 + eps) = -0), so a Gaussian whose
+    // moments are all +0 -- never given a gradient since they were zeroed --
+    // skips its replay, and without a gradient step is not touched at all
+    zero = __all_sync(0xffffffffu, zero);
+    if (!zero || grad_row) {
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int q = lane + 32 * h;
+            if (q >= kGradRow) break;
+            const int k = grp[h];
+            float pv = a.p[k][idx[h]];
+            if (!zero)
+                for (int s = from + 1; s <= to; s++)
+                    adam_one(pv, 0.f, mv[h], vv[h], a.b1, a.b2, a.hist[10 * s + k], a.hist[10 * s + 5 + k], a.eps);
+            if (grad_row)
+                adam_one(pv, grad_row[q], mv[h], vv[h], a.b1, a.b2, a.hist[10 * t_end + k],
+                         a.hist[10 * t_end + 5 + k], a.eps);
+            a.p[k][idx[h]] = pv; a.m[k][idx[h]] = mv[h]; a.v[k][idx[h]] = vv[h];
+        }
     }
     __syncwarp();
     if (lane == 0) a.last[i] = t_end;
-    lazy_set_drift_warp(a, i, t_end, lane, mv_keep, vv_keep);
+    // lane l < 6: moments of parameter l (mean, log-scale) for the drift bound
+    lazy_set_drift_warp(a, i, t_end, lane, mv[0], vv[0]);
 }
 
 // The three kernels below run a grid of a few blocks per SM whose warps

@@ -122,11 +122,93 @@ __device__ __forceinline__ float2 pair_alpha(float2 p, float o, float amax, floa
     return make_float2(fminf(amax, og.x), fminf(amax, og.y));
 }
 
+// Half-widths of the box around the pixels an entry can composite at:
+// alpha >= alpha_min needs o G >= alpha_min, i.e. the ellipse
+// A (dx + k dy)^2 + D dy^2 <= tau, tau = 2 ln(o / alpha_min), whose bounding box
+// has half-widths sqrt(tau Sx), sqrt(tau Sy) with (Sx, Sy) the diagonal of the
+// inverse of the conic: Sx = 1/A + k^2/D, Sy = 1/D.  Widened (tau by 0.2 % +
+// 2e-3, the widths by 0.1 % + 1/32 px) far beyond the FP32 error of the
+// exponent the kernels evaluate, so no pixel outside the box can reach
+// alpha_min in them; empty (-1e30) when o is below alpha_min.  A warp whose
+// pixels all lie outside an entry's box skips the entry: it composites
+// nowhere in the warp, so skipping it changes nothing.
+__device__ __forceinline__ float2 alpha_box(float A, float k, float D, float o, float alpha_min)
+{
+    float tau = 2.f * logf(o / alpha_min);
+    tau = fmaf(tau, 1.002f, 2e-3f);
+    if (!(tau > 0.f)) return make_float2(-1e30f, -1e30f);
+    const float iD = 1.f / D;
+    return make_float2(fmaf(sqrtf(tau * fmaf(k * k, iD, 1.f / A)), 1.001f, 0.03125f),
+                       fmaf(sqrtf(tau * iD), 1.001f, 0.03125f));
+}
+
+// Tile-local pixel-centre box [x0, x1] x [y0, y1] of warp w's pixels (warp w
+// holds the quads t = 32 w .. 32 w + 31, whole quad rows since 32 is a
+// multiple of the quads per row).
+template <int TW, int TH> struct WarpBox {
+    float x0, x1, y0, y1;
+    __device__ __forceinline__ explicit WarpBox(int w)
+    {
+        constexpr int QX = TileShape<TW, TH>::qx;
+        static_assert(32 % QX == 0, "a warp must hold whole quad rows");
+        x0 = 0.5f;
+        x1 = (float)TW - 0.5f;
+        y0 = 2.f * (float)(32 * w / QX) + 0.5f;
+        y1 = 2.f * (float)((32 * w + 31) / QX) + 1.5f;
+    }
+    // true when the box of half-widths hb around (u, v) misses the warp
+    __device__ __forceinline__ bool misses(float u, float v, float2 hb) const
+    {
+        return u + hb.x < x0 || u - hb.x > x1 || v + hb.y < y0 || v - hb.y > y1;
+    }
+};
+
 __device__ __forceinline__ float warp_sum_f(float v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Sums the 9 slot values over the warp by recursive halving (a reduce-scatter):
+// at each of the first four levels a lane keeps half of its values and trades
+// the other half with its partner, so 5 + 3 + 2 + 1 + 1 = 12 shuffles replace
+// the 45 of nine butterfly sums.  Lane l ends with the full sum of value
+// red9_index(l), valid when red9_owner(l).
+__device__ __forceinline__ float warp_reduce9(const float (&v)[kSlotFloats], int lane)
+{
+    static_assert(kSlotFloats == 9, "the halving schedule is laid out for 9 values");
+    const bool h1 = lane & 16, h2 = lane & 8, h3 = lane & 4, h4 = lane & 2;
+    float a[5], b[3], c[2];
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        const float lo = v[i], hi = i + 5 < 9 ? v[i + 5] : 0.f;
+        a[i] = (h1 ? hi : lo) + __shfl_xor_sync(0xffffffffu, h1 ? lo : hi, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const float lo = a[i], hi = i + 3 < 5 ? a[i + 3] : 0.f;
+        b[i] = (h2 ? hi : lo) + __shfl_xor_sync(0xffffffffu, h2 ? lo : hi, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const float lo = b[i], hi = i + 2 < 3 ? b[i + 2] : 0.f;
+        c[i] = (h3 ? hi : lo) + __shfl_xor_sync(0xffffffffu, h3 ? lo : hi, 4);
+    }
+    const float d = (h4 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, h4 ? c[0] : c[1], 2);
+    return d + __shfl_xor_sync(0xffffffffu, d, 1);
+}
+// value held by lane l after warp_reduce9: lane bit 4 picks 0-4 / 5-8, bits 3, 2
+// and 1 pick within the halves (padding positions hold no value)
+__device__ __forceinline__ int red9_index(int lane)
+{
+    return 5 * ((lane >> 4) & 1) + 3 * ((lane >> 3) & 1) + 2 * ((lane >> 2) & 1) + ((lane >> 1) & 1);
+}
+__device__ __forceinline__ bool red9_owner(int lane)
+{
+    const int h1 = (lane >> 4) & 1, h2 = (lane >> 3) & 1, h3 = (lane >> 2) & 1, h4 = (lane >> 1) & 1;
+    const int ai = 3 * h2 + 2 * h3 + h4;
+    return (lane & 1) == 0 && (h2 ? h3 == 0 : 2 * h3 + h4 <= 2) && ai < (h1 ? 4 : 5);
 }
 
 // Slot of (record r, tile (tx, ty)): first instance of r + position of the
@@ -152,12 +234,14 @@ __global__ void __launch_bounds__(TileShape<TW, TH>::threads, 768 / TileShape<TW
     __shared__ float4 s0[kRT];
     __shared__ float4 s1[kRT];
     __shared__ float s2[kRT];
+    __shared__ float2 s3[kRT];
     const CamTable &ct = *ctp;
     if ((int)blockIdx.x >= ct.total_tiles) return;
     const TileGeom tg = tile_geom<TW, TH>(ct, blockIdx.x);
     const TileGeom &cam = tg;
     const uint2 rg = ranges[blockIdx.x];
     const int start = (int)rg.x, end = (int)rg.y;
+    const WarpBox<TW, TH> wb((int)threadIdx.x >> 5);
 
     // pixel pair of row 0 (quad elements 0, 1) and row 1 (2, 3), tile-local
     const float2 px2 = make_float2(tg.lx0, tg.lx0 + 1.f);
@@ -174,15 +258,18 @@ __global__ void __launch_bounds__(TileShape<TW, TH>::threads, 768 / TileShape<TW
         const int s = b + threadIdx.x;
         if (s < end) {
             const uint32_t r = vals[s];
-            const float4 r1 = rd1[r], r2 = rd2[r];
-            s0[threadIdx.x] = stage_e0(rd0[r], r2, tg);
+            const float4 r0 = rd0[r], r1 = rd1[r], r2 = rd2[r];
+            s0[threadIdx.x] = stage_e0(r0, r2, tg);
             s1[threadIdx.x] = make_float4(stage_D(r1), r1.y, r1.z, r1.w);
             s2[threadIdx.x] = r2.x;
+            s3[threadIdx.x] = alpha_box(r0.z, r0.w, r1.x, r1.y, rc.alpha_min);
         }
         __syncthreads();
         const int cnt = min(kRT, end - b);
         for (int j = 0; j < cnt && !(dn[0] && dn[1] && dn[2] && dn[3]); j++) {
-            const float4 p0 = s0[j], p1 = s1[j];
+            const float4 p0 = s0[j];
+            if (wb.misses(p0.x, p0.y, s3[j])) continue; // warp-uniform
+            const float4 p1 = s1[j];
             const float cb = s2[j];
             const uint32_t pos = (uint32_t)(b - start + j + 1);
             const QuadPow q = quad_power(p0, p1.x, px2, py2);
@@ -240,6 +327,7 @@ template <int TW, int TH> static void fwd_launch(gs_workspace *ws, cudaStream_t 
 cudaError_t launch_render_fwd(gs_workspace *ws, cudaStream_t st, float *rgb, float *T_out)
 {
     if (ws->cams.total_tiles == 0) return cudaSuccess;
+    kt_begin(ws, GS_KT_RENDER_FWD, st);
     switch (tile_shape_id(ws->cams.tile_w, ws->cams.tile_h)) {
     case 0: fwd_launch<16, 16>(ws, st, rgb, T_out); break;
     case 1: fwd_launch<32, 8>(ws, st, rgb, T_out); break;
@@ -247,6 +335,7 @@ cudaError_t launch_render_fwd(gs_workspace *ws, cudaStream_t st, float *rgb, flo
     case 3: fwd_launch<32, 16>(ws, st, rgb, T_out); break;
     default: return cudaErrorInvalidValue;
     }
+    kt_end(ws, GS_KT_RENDER_FWD, st);
     note_launch();
     return cudaGetLastError();
 }
@@ -265,7 +354,10 @@ struct BwdRenderArgs {
     const uint32_t *n_contrib;
     const float *dL_drgb;
     float *slots;
+    unsigned long long *fragments; // += sum of the tile's n_contrib; [1] += composited pairs
 };
+static_assert(offsetof(DevCounters, composited) == offsetof(DevCounters, fragments) + sizeof(unsigned long long),
+              "the backward adds to the two adjacent counters through one pointer");
 
 // Reverse traversal from each pixel's last composited entry, recovering T by
 // T / (1 - alpha) from the final transmittance.  Per entry, each thread sums
@@ -279,6 +371,7 @@ __global__ void __launch_bounds__(TileShape<TW, TH>::threads)
     __shared__ float4 s0[kBwdBatch];
     __shared__ float4 s1[kBwdBatch];
     __shared__ float s2[kBwdBatch];
+    __shared__ float2 s3[kBwdBatch];
     __shared__ unsigned long long s_slot[kBwdBatch];
     __shared__ float s_red[kWarps][kBwdBatch][kSlotFloats];
     __shared__ int s_max;
@@ -289,29 +382,48 @@ __global__ void __launch_bounds__(TileShape<TW, TH>::threads)
     const uint2 rg = a.ranges[blockIdx.x];
     const int start = (int)rg.x, end = (int)rg.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool red_own = red9_owner(lane);
+    const int red_q = red9_index(lane);
+    const WarpBox<TW, TH> wb(warp);
 
-    float T[kQ], g0[kQ], g1[kQ], g2[kQ], tgb[kQ], S0[kQ], S1[kQ], S2[kQ], pxf[kQ], pyf[kQ];
+    // per-pixel state, as row pairs (element x: left pixel, y: right pixel)
+    float2 T[2], g0[2], g1[2], g2[2], tgb[2], S0[2], S1[2], S2[2];
     int nc[kQ];
     const float2 px2 = make_float2(tg.lx0, tg.lx0 + 1.f);
     const float2 py2 = make_float2(tg.ly0, tg.ly0 + 1.f);
-    int mymax = 0;
+    int mymax = 0, ncomp = 0;
     const long long np = (long long)cam.width * cam.height;
     const float *gimg = a.dL_drgb + 3 * cam.pix_base;
 #pragma unroll
-    for (int k = 0; k < kQ; k++) {
-        const int px = tg.px0 + (k & 1), py = tg.py0 + (k >> 1);
-        pxf[k] = tg.lx0 + (float)(k & 1); pyf[k] = tg.ly0 + (float)(k >> 1);
-        T[k] = 1.f; g0[k] = g1[k] = g2[k] = 0.f; nc[k] = 0;
-        S0[k] = S1[k] = S2[k] = 0.f;
-        if (px < cam.width && py < cam.height) {
-            const long long pix = (long long)py * cam.width + px;
-            g0[k] = gimg[pix]; g1[k] = gimg[np + pix]; g2[k] = gimg[2 * np + pix];
-            T[k] = a.T_final[cam.pix_base + pix];
-            nc[k] = (int)a.n_contrib[cam.pix_base + pix];
+    for (int row = 0; row < 2; row++) {
+        float t[2] = {1.f, 1.f}, c0[2] = {0.f, 0.f}, c1[2] = {0.f, 0.f}, c2[2] = {0.f, 0.f};
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int k = 2 * row + h;
+            const int px = tg.px0 + h, py = tg.py0 + row;
+            nc[k] = 0;
+            if (px < cam.width && py < cam.height) {
+                const long long pix = (long long)py * cam.width + px;
+                c0[h] = gimg[pix]; c1[h] = gimg[np + pix]; c2[h] = gimg[2 * np + pix];
+                t[h] = a.T_final[cam.pix_base + pix];
+                nc[k] = (int)a.n_contrib[cam.pix_base + pix];
+            }
+            mymax = max(mymax, nc[k]);
         }
+        T[row] = make_float2(t[0], t[1]);
+        g0[row] = make_float2(c0[0], c0[1]);
+        g1[row] = make_float2(c1[0], c1[1]);
+        g2[row] = make_float2(c2[0], c2[1]);
+        S0[row] = S1[row] = S2[row] = f2(0.f);
         // d/dalpha of the background term: -T_final (g . bg) / (1 - alpha)
-        tgb[k] = T[k] * (g0[k] * rc.bg[0] + g1[k] * rc.bg[1] + g2[k] * rc.bg[2]);
-        mymax = max(mymax, nc[k]);
+        tgb[row] = __fmul2_rn(T[row], __ffma2_rn(g2[row], f2(rc.bg[2]), __ffma2_rn(g1[row], f2(rc.bg[1]),
+                                                                                  __fmul2_rn(g0[row], f2(rc.bg[0])))));
+    }
+    {
+        unsigned long long f = (unsigned long long)nc[0] + nc[1] + nc[2] + nc[3];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+        if (lane == 0 && f) atomicAdd(a.fragments, f);
     }
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
@@ -329,67 +441,80 @@ __global__ void __launch_bounds__(TileShape<TW, TH>::threads)
         const int cnt = hi - lo;
         if (threadIdx.x < cnt) {
             const uint32_t r = a.vals[lo + threadIdx.x];
-            const float4 r1 = a.rd1[r], r2 = a.rd2[r];
-            s0[threadIdx.x] = stage_e0(a.rd0[r], r2, tg);
+            const float4 r0 = a.rd0[r], r1 = a.rd1[r], r2 = a.rd2[r];
+            s0[threadIdx.x] = stage_e0(r0, r2, tg);
             s1[threadIdx.x] = make_float4(stage_D(r1), r1.y, r1.z, r1.w);
             s2[threadIdx.x] = r2.x;
+            s3[threadIdx.x] = alpha_box(r0.z, r0.w, r1.x, r1.y, rc.alpha_min);
             s_slot[threadIdx.x] = slot_of(a.inst_off, a.rect, r, tg.tx, tg.ty);
         }
         __syncthreads();
         for (int jj = cnt - 1; jj >= 0; jj--) {
             const int j = lo + jj - start; // position in the tile list
-            const float4 p0 = s0[jj], p1 = s1[jj];
+            const float4 p0 = s0[jj];
+            if (wb.misses(p0.x, p0.y, s3[jj])) { // warp-uniform: nothing to add
+                if (red_own) s_red[warp][jj][red_q] = 0.f;
+                continue;
+            }
+            const float4 p1 = s1[jj];
             const float cb = s2[jj];
             // the forward's own exponent and alpha (same functions, same bits)
             const QuadPow qp = quad_power(p0, p1.x, px2, py2);
             const float Au = p0.z * kFromScaled, Du = p1.x * kFromScaled; // the conic's A and D
-            float2 Gr[2], alr[2];
-            alr[0] = pair_alpha(qp.r0, p1.y, rc.alpha_max, Gr[0]);
-            alr[1] = pair_alpha(qp.r1, p1.y, rc.alpha_max, Gr[1]);
-            float v[kSlotFloats];
+            float2 acc[kSlotFloats];
 #pragma unroll
-            for (int q = 0; q < kSlotFloats; q++) v[q] = 0.f;
+            for (int q = 0; q < kSlotFloats; q++) acc[q] = f2(0.f);
             bool act = false;
 #pragma unroll
-            for (int k = 0; k < kQ; k++) {
-                const float alpha = (k & 1) ? alr[k >> 1].y : alr[k >> 1].x;
-                if (j >= nc[k] || alpha < rc.alpha_min) continue;
-                const float G = (k & 1) ? Gr[k >> 1].y : Gr[k >> 1].x;
-                const float og = p1.y * G;
-                const float dx = pxf[k] - p0.x, dy = pyf[k] - p0.y;
+            for (int row = 0; row < 2; row++) {
+                float2 G;
+                const float2 al = pair_alpha(row ? qp.r1 : qp.r0, p1.y, rc.alpha_max, G);
+                // composited pixels: in front of the pixel's last contribution, alpha >= alpha_min
+                const bool m0 = j < nc[2 * row] && al.x >= rc.alpha_min;
+                const bool m1 = j < nc[2 * row + 1] && al.y >= rc.alpha_min;
+                if (!(m0 || m1)) continue;
                 act = true;
-                const float inv = 1.f / (1.f - alpha);
-                const float Tj = T[k] * inv; // transmittance in front of this fragment
-                const float aT = alpha * Tj;
-                v[6] = fmaf(aT, g0[k], v[6]);
-                v[7] = fmaf(aT, g1[k], v[7]);
-                v[8] = fmaf(aT, g2[k], v[8]);
-                const float dalpha = g0[k] * (Tj * p1.z - S0[k] * inv) + g1[k] * (Tj * p1.w - S1[k] * inv) +
-                                     g2[k] * (Tj * cb - S2[k] * inv) - tgb[k] * inv;
-                S0[k] = fmaf(aT, p1.z, S0[k]);
-                S1[k] = fmaf(aT, p1.w, S1[k]);
-                S2[k] = fmaf(aT, cb, S2[k]);
-                T[k] = Tj;
-                if (og < rc.alpha_max) {
-                    v[5] = fmaf(G, dalpha, v[5]);
-                    const float dpow = G * p1.y * dalpha;
-                    // d power / du = A dx + B dy = A e, d power / dv = B dx + C dy = k A e + D dy
-                    const float Ae = Au * fmaf(p0.w, dy, dx);
-                    v[0] = fmaf(dpow, Ae, v[0]);
-                    v[1] = fmaf(dpow, fmaf(p0.w, Ae, Du * dy), v[1]);
-                    v[2] = fmaf(-0.5f * dpow, dx * dx, v[2]);
-                    v[3] = fmaf(-dpow, dx * dy, v[3]);
-                    v[4] = fmaf(-0.5f * dpow, dy * dy, v[4]);
-                }
+                ncomp += (int)m0 + (int)m1;
+                const float2 inv = make_float2(rcp_approx(1.f - al.x), rcp_approx(1.f - al.y));
+                const float2 Tj = __fmul2_rn(T[row], inv); // transmittance in front of this fragment
+                const float2 aTf = __fmul2_rn(al, Tj);
+                const float2 aT = make_float2(m0 ? aTf.x : 0.f, m1 ? aTf.y : 0.f);
+                acc[6] = __ffma2_rn(aT, g0[row], acc[6]);
+                acc[7] = __ffma2_rn(aT, g1[row], acc[7]);
+                acc[8] = __ffma2_rn(aT, g2[row], acc[8]);
+                // dL/dalpha = Tj (g . c) - (g . S + T_final g . bg) / (1 - alpha), S the
+                // colour composited behind this fragment
+                const float2 gc = __ffma2_rn(g2[row], f2(cb), __ffma2_rn(g1[row], f2(p1.w), __fmul2_rn(g0[row], f2(p1.z))));
+                const float2 gS = __ffma2_rn(g2[row], S2[row], __ffma2_rn(g1[row], S1[row],
+                                                                          __ffma2_rn(g0[row], S0[row], tgb[row])));
+                const float2 dal = __ffma2_rn(make_float2(-inv.x, -inv.y), gS, __fmul2_rn(Tj, gc));
+                S0[row] = __ffma2_rn(aT, f2(p1.z), S0[row]);
+                S1[row] = __ffma2_rn(aT, f2(p1.w), S1[row]);
+                S2[row] = __ffma2_rn(aT, f2(cb), S2[row]);
+                T[row] = make_float2(m0 ? Tj.x : T[row].x, m1 ? Tj.y : T[row].y);
+                // opacity, mean and conic: only where alpha is not clamped at alpha_max
+                const float2 dGf = __fmul2_rn(G, dal);
+                const float2 dG = make_float2(m0 && al.x < rc.alpha_max ? dGf.x : 0.f,
+                                              m1 && al.y < rc.alpha_max ? dGf.y : 0.f);
+                acc[5] = __fadd2_rn(acc[5], dG);
+                const float2 dpow = __fmul2_rn(dG, f2(p1.y));
+                const float2 dx = __fadd2_rn(px2, f2(-p0.x));
+                const float dy = (row ? py2.y : py2.x) - p0.y;
+                // d power / du = A dx + B dy = A e, d power / dv = B dx + C dy = k A e + D dy
+                const float2 Ae = __fmul2_rn(f2(Au), __fadd2_rn(dx, f2(p0.w * dy)));
+                acc[0] = __ffma2_rn(dpow, Ae, acc[0]);
+                acc[1] = __ffma2_rn(dpow, __ffma2_rn(f2(p0.w), Ae, f2(Du * dy)), acc[1]);
+                const float2 hd = __fmul2_rn(f2(-0.5f), dpow);
+                acc[2] = __ffma2_rn(hd, __fmul2_rn(dx, dx), acc[2]);
+                acc[3] = __ffma2_rn(__fmul2_rn(dpow, f2(-dy)), dx, acc[3]);
+                acc[4] = __ffma2_rn(hd, f2(dy * dy), acc[4]);
             }
-            if (__any_sync(0xffffffffu, act)) {
+            float v[kSlotFloats];
 #pragma unroll
-                for (int q = 0; q < kSlotFloats; q++) v[q] = warp_sum_f(v[q]);
-            }
-            if (lane == 0) {
-#pragma unroll
-                for (int q = 0; q < kSlotFloats; q++) s_red[warp][jj][q] = v[q];
-            }
+            for (int q = 0; q < kSlotFloats; q++) v[q] = acc[q].x + acc[q].y;
+            float r = 0.f;
+            if (__any_sync(0xffffffffu, act)) r = warp_reduce9(v, lane);
+            if (red_own) s_red[warp][jj][red_q] = r;
         }
         __syncthreads();
         for (int idx = threadIdx.x; idx < cnt * kSlotFloats; idx += kRT) {
@@ -401,6 +526,10 @@ __global__ void __launch_bounds__(TileShape<TW, TH>::threads)
         }
         __syncthreads();
     }
+    unsigned long long f = (unsigned long long)ncomp;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+    if (lane == 0 && f) atomicAdd(a.fragments + 1, f);
 }
 
 cudaError_t launch_render_bwd(gs_workspace *ws, cudaStream_t st, const float *dL_drgb)
@@ -409,8 +538,9 @@ cudaError_t launch_render_bwd(gs_workspace *ws, cudaStream_t st, const float *dL
     BwdRenderArgs a;
     a.ranges = ws->ranges; a.vals = ws->tval[ws->tile_buf]; a.rd0 = ws->rd0; a.rd1 = ws->rd1; a.rd2 = ws->rd2;
     a.inst_off = ws->inst_off; a.rect = ws->rect; a.T_final = ws->T_final; a.n_contrib = ws->n_contrib;
-    a.dL_drgb = dL_drgb; a.slots = ws->slots;
+    a.dL_drgb = dL_drgb; a.slots = ws->slots; a.fragments = &ws->ctr->fragments;
     const unsigned grid = (unsigned)ws->cams.total_tiles;
+    kt_begin(ws, GS_KT_RENDER_BWD, st);
     switch (tile_shape_id(ws->cams.tile_w, ws->cams.tile_h)) {
     case 0: render_bwd_kernel<16, 16><<<grid, TileShape<16, 16>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
     case 1: render_bwd_kernel<32, 8><<<grid, TileShape<32, 8>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
@@ -418,6 +548,7 @@ cudaError_t launch_render_bwd(gs_workspace *ws, cudaStream_t st, const float *dL
     case 3: render_bwd_kernel<32, 16><<<grid, TileShape<32, 16>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
     default: return cudaErrorInvalidValue;
     }
+    kt_end(ws, GS_KT_RENDER_BWD, st);
     note_launch();
     return cudaGetLastError();
 }
@@ -440,6 +571,7 @@ __global__ void __launch_bounds__(TileShape<TW, TH>::threads)
     constexpr int kRT = TileShape<TW, TH>::threads, kWarps = TileShape<TW, TH>::warps;
     __shared__ float4 s0[kRT];
     __shared__ float2 s1[kRT];
+    __shared__ float2 s3[kRT];
     __shared__ unsigned long long s_slot[kRT];
     __shared__ float s_w[kWarps][kRT];
     __shared__ uint32_t s_a[kWarps][kRT];
@@ -450,6 +582,7 @@ __global__ void __launch_bounds__(TileShape<TW, TH>::threads)
     const uint2 rg = a.ranges[blockIdx.x];
     const int start = (int)rg.x, end = (int)rg.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const WarpBox<TW, TH> wb(warp);
     const float2 px2 = make_float2(tg.lx0, tg.lx0 + 1.f);
     const float2 py2 = make_float2(tg.ly0, tg.ly0 + 1.f);
     float2 T[2] = {f2(1.f), f2(1.f)};
@@ -463,14 +596,19 @@ __global__ void __launch_bounds__(TileShape<TW, TH>::threads)
         const int cnt = min(kRT, end - b);
         if (threadIdx.x < cnt) {
             const uint32_t r = a.vals[b + threadIdx.x];
-            const float4 p1 = a.rd1[r];
-            s0[threadIdx.x] = stage_e0(a.rd0[r], a.rd2[r], tg);
+            const float4 p0 = a.rd0[r], p1 = a.rd1[r];
+            s0[threadIdx.x] = stage_e0(p0, a.rd2[r], tg);
             s1[threadIdx.x] = make_float2(stage_D(p1), p1.y);
+            s3[threadIdx.x] = alpha_box(p0.z, p0.w, p1.x, p1.y, rc.alpha_min);
             s_slot[threadIdx.x] = slot_of(a.inst_off, a.rect, r, tg.tx, tg.ty);
         }
         __syncthreads();
         for (int j = 0; j < cnt; j++) {
             const float4 p0 = s0[j];
+            if (wb.misses(p0.x, p0.y, s3[j])) { // warp-uniform: nothing to add
+                if (lane == 0) { s_w[warp][j] = 0.f; s_a[warp][j] = 0u; }
+                continue;
+            }
             const float2 p1 = s1[j];
             const QuadPow q = quad_power(p0, p1.x, px2, py2);
             float wv = 0.f;
@@ -521,6 +659,7 @@ cudaError_t launch_importance_raster(gs_workspace *ws, cudaStream_t st)
     a.ranges = ws->ranges; a.vals = ws->tval[ws->tile_buf]; a.rd0 = ws->rd0; a.rd1 = ws->rd1; a.rd2 = ws->rd2;
     a.inst_off = ws->inst_off; a.rect = ws->rect; a.slots = ws->slots;
     const unsigned grid = (unsigned)ws->cams.total_tiles;
+    kt_begin(ws, GS_KT_IMPORTANCE, st);
     switch (tile_shape_id(ws->cams.tile_w, ws->cams.tile_h)) {
     case 0: importance_raster_kernel<16, 16><<<grid, TileShape<16, 16>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
     case 1: importance_raster_kernel<32, 8><<<grid, TileShape<32, 8>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
@@ -528,6 +667,7 @@ cudaError_t launch_importance_raster(gs_workspace *ws, cudaStream_t st)
     case 3: importance_raster_kernel<32, 16><<<grid, TileShape<32, 16>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
     default: return cudaErrorInvalidValue;
     }
+    kt_end(ws, GS_KT_IMPORTANCE, st);
     note_launch();
     return cudaGetLastError();
 }

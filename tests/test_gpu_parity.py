@@ -185,6 +185,37 @@ def test_backward_parity(seed):
         assert_param_grad_close(k, gg[k], og[k])
 
 
+def test_backward_fragment_counts_and_kernel_timing():
+    """The backward's work counters: fragments is the sum of n_contrib (integer,
+    exact); composited is the number of composited (pixel, Gaussian) pairs, the
+    sum of the oracle's per-Gaussian pixel counts a (Sec. 3.2) up to the pairs of
+    flagged pixels.  Timing brackets exactly the timed launches."""
+    g = synth.plain_scene(3000, seed=25)
+    cam = synth.plain_camera(144, 104, 160.0)
+    P = O.Params()
+    run = GpuRun(g, [cam], P)
+    fwd = O.forward_view(O.gaussians64(g), cam, P)
+    dL = np.random.default_rng(26).standard_normal((3, cam.height, cam.width))
+    assert run.ws.kernel_time(B.GS_KT_RENDER_BWD) == (0.0, 0)
+    run.ws.kernel_timing(True)
+    _backward(run, dL)
+    _backward(run, dL)
+    ms, n = run.ws.kernel_time(B.GS_KT_RENDER_BWD)
+    assert n == 2 and ms > 0.0
+    assert run.ws.kernel_time(B.GS_KT_RENDER_FWD) == (0.0, 0)
+    run.ws.kernel_timing(False)
+    assert run.ws.kernel_time(B.GS_KT_RENDER_BWD) == (0.0, 0)
+    c = run.ws.counts()
+    # two backward launches since the preprocess
+    assert c["fragments"] == 2 * int(run.n_contrib.astype(np.int64).sum())
+    comp = c["composited"] // 2
+    assert c["composited"] % 2 == 0
+    assert comp <= c["fragments"] // 2
+    ref = int(round(fwd["a"].sum()))
+    assert abs(comp - ref) <= int(fwd["gcount"].sum()) + 0, (comp, ref)
+    assert comp > 0
+
+
 def test_backward_multi_camera_accumulates():
     g = synth.plain_scene(3000, seed=23)
     cams = [synth.plain_camera(128, 128, 160.0), synth.plain_camera(96, 80, 120.0)]
