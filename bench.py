@@ -7,13 +7,14 @@ Gaussians over 2 km x 2 km (ground plane + 200 buildings), degree-3 SH, one
 and the importance cull column enabled.  One step runs every stage of the hot
 path through the C ABI on resident device data:
 
-  preprocess (gate + cull + projection + SH) -> bin_sort -> render_fwd
+  preprocess (gate + projection + SH; Gaussians culled in the view are kept
+  and marked) -> bin_sort -> render_fwd (marked records composite nowhere)
   -> L1 + 0.2 D-SSIM loss against a target -> render backward (+ scale
      regulariser) into compact per-Gaussian gradient rows -> Adam over all 59
-     parameters of all Gaussians (fused with the gradient rows, no dense
-     gradient array) -> importance sweep (preprocess with the LOD gate but
-     without the Cull column it recomputes, bin_sort, importance: w, a, s,
-     c^rad, c^vis and the next Cull column).
+     parameters of all Gaussians (zero-gradient steps deferred and replayed
+     exactly) -> importance sweep on the same binning, which scores every
+     record as without the Cull column it recomputes (w, a, s, c^rad, c^vis
+     and the next Cull column).
 
 value = rendered pixels per second of whole steps (Mpix/s); the line also
 carries Mgaussian/s.  All inputs (1.2 GB of parameters, Adam state, the
@@ -176,7 +177,10 @@ class Step:
         self.crad = torch.zeros(self.n, device="cuda", dtype=torch.int32)
         self.cvis = torch.zeros(self.n, device="cuda", dtype=torch.int32)
         tw, th = tile
-        self.params_train = B.RenderParams(lod_enable=True, cull_enable=True, tile_w=tw, tile_h=th, **LOD)
+        # one binning per step: culled Gaussians stay in the lists, marked, so the training render
+        # skips them and the importance sweep of the same view scores them
+        self.params_train = B.RenderParams(lod_enable=True, cull_enable=B.GS_CULL_MARK, tile_w=tw, tile_h=th,
+                                           **LOD)
         # the scoring sweep after density control (the paper's T2 pass) renders with the LOD gate
         # engaged and never applies the Cull mask it recomputes
         self.params_imp = B.RenderParams(lod_enable=True, cull_enable=False, tile_w=tw, tile_h=th, **LOD)
@@ -233,9 +237,7 @@ class Step:
         # Adam on all Gaussians with the compact gradients (zero for Gaussians without a record)
         ws.adam_step_compact(self.gt, self.m, self.v, self.lr, self.step_no)
         rec(6)
-        # importance sweep of the updated model; its Cull column gates the next step
-        ws.preprocess(self.gt, [self.cam], self.params_imp)
-        ws.bin_sort()
+        # importance sweep of the view on the step's binning; its Cull column gates the next step
         ws.importance(s_accum=self.s, crad=self.crad, cvis=self.cvis, cull_out=self.cull)
         rec(7)
 
@@ -581,8 +583,7 @@ def main():
     gauss = job_rate(g.n, ms, world) / 1e6
     peaks = measured_peaks()
     dom = max(stage_ms, key=stage_ms.get)
-    # the training render's counts (the last preprocess of a step is the
-    # importance sweep's): one more untimed forward and backward of this view
+    # the counts of one more untimed forward and backward of this view
     step.ws.preprocess(step.gt, [cam], step.params_train, step.cull)
     step.ws.bin_sort()
     step.ws.render_fwd(step.rgb, step.T)

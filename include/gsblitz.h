@@ -118,13 +118,22 @@ typedef struct {
     int32_t width, height;
 } gs_camera;
 
+/* Cull modes (gs_render_params.cull_enable).  GS_CULL_DROP removes a culled
+ * Gaussian from the view at the gate.  GS_CULL_MARK keeps it and marks its
+ * record: gs_render_fwd and the backward treat a marked record as absent (the
+ * same images and gradients as GS_CULL_DROP; its gradient is zero and it is
+ * not in the visible set of Eq. 5), while gs_importance scores every record
+ * as with GS_CULL_OFF -- so one preprocess and one gs_bin_sort serve both the
+ * masked training render and the unmasked importance sweep of a view. */
+enum { GS_CULL_OFF = 0, GS_CULL_DROP = 1, GS_CULL_MARK = 2 };
+
 /* Render parameters; gs_default_params fills the standard values. */
 typedef struct {
     int32_t tile_w;      /* tile width in pixels; tile_w x tile_h is one of 16x16 (GS_TILE, the */
     int32_t tile_h;      /* 3DGS tiling), 32x8, 8x32, 32x16 */
     int32_t lod_enable;  /* distance LOD gate of Eq. 1-2 */
     int32_t lod_Lmax;    /* L_max(t) of Eq. 1 */
-    int32_t cull_enable; /* per-view Cull column of Eq. 3 */
+    int32_t cull_enable; /* per-view Cull column of Eq. 3: GS_CULL_OFF, GS_CULL_DROP or GS_CULL_MARK */
     float bg[3];         /* background colour, added as T_final * bg */
     float alpha_min;     /* 1/255: fragments with alpha below are skipped */
     float alpha_max;     /* 0.99: alpha = min(alpha_max, o G') */
@@ -143,7 +152,7 @@ typedef struct {
 typedef struct {
     int64_t n_records;        /* active (Gaussian, camera) pairs */
     int64_t n_instances;      /* (record, tile) pairs */
-    int64_t n_visible;        /* Gaussians with at least one record */
+    int64_t n_visible;        /* Gaussians with at least one record (not marked culled) */
     int64_t records_needed;   /* equals n_records unless capacity was exceeded */
     int64_t instances_needed; /* equals n_instances unless capacity was exceeded */
     int32_t error;            /* device error word: 0 or a gs_status */
@@ -379,7 +388,8 @@ int gs_densify(gs_workspace *ws, const gs_model *src, const float *absgrad, cons
                gs_model *dst, int64_t dst_capacity, int64_t *n_out, gs_stream stream);
 
 /* counts[i] += number of cameras of the last gs_preprocess in which Gaussian i
- * has a record (the densification denominator of a training step). */
+ * has a record not marked culled (the densification denominator of a training
+ * step). */
 int gs_count_views(gs_workspace *ws, uint32_t *counts, gs_stream stream);
 
 /* The Cull column of one view (the selection step of gs_importance) without

@@ -33,6 +33,9 @@ EXPORTS = ("gs_default_params", "gs_last_error", "gs_workspace_create", "gs_work
            "gs_prune_sample", "gs_prune_mass", "gs_compact", "gs_densify", "gs_count_views", "gs_adam_lazy_enable",
            "gs_adam_lazy_disable", "gs_adam_flush", "gs_kernel_timing", "gs_kernel_time")
 
+# Cull modes of RenderParams.cull_enable (include/gsblitz.h)
+GS_CULL_OFF, GS_CULL_DROP, GS_CULL_MARK = 0, 1, 2
+
 # kernels gs_kernel_timing brackets with events (include/gsblitz.h)
 GS_KT_RENDER_FWD, GS_KT_RENDER_BWD, GS_KT_IMPORTANCE = range(3)
 
@@ -188,7 +191,7 @@ class RenderParams:
     lod_d0: float | None = None
     lod_f: float | None = None
     lod_Lmax: int | None = None
-    cull_enable: bool = False
+    cull_enable: int = 0  # GS_CULL_OFF / GS_CULL_DROP (or True) / GS_CULL_MARK
     eps_score: float | None = None
     vis_mass: float | None = None
 

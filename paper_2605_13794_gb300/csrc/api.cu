@@ -471,6 +471,8 @@ int gs_preprocess_uploaded(gs_workspace *ws, const gs_gaussians *g, const uint32
     if (!aligned16(g->mean) || !aligned16(g->log_scale) || !aligned16(g->quat) || !aligned16(g->opacity_logit) ||
         !aligned16(g->sh))
         return fail(GS_ERR_INVALID_ARG, "gs_preprocess: Gaussian arrays must be 16-byte aligned");
+    if (params->cull_enable < GS_CULL_OFF || params->cull_enable > GS_CULL_MARK)
+        return fail(GS_ERR_INVALID_ARG, "gs_preprocess: cull_enable must be GS_CULL_OFF, GS_CULL_DROP or GS_CULL_MARK");
     if (params->cull_enable && !cull) return fail(GS_ERR_INVALID_ARG, "gs_preprocess: cull_enable needs a cull array");
     if (params->lod_enable && (params->lod_Lmax < 0 || params->lod_Lmax > gs::kMaxLod || !(params->lod_f > 1.f) ||
                                !(params->lod_d0 > 0.f)))

@@ -195,14 +195,15 @@ __global__ void __launch_bounds__(256) model_scatter_kernel(ScatterArgs a)
 
 // Views in which each Gaussian has a record (+= per Gaussian; records of a
 // Gaussian are contiguous).
-__global__ void count_views_kernel(const uint32_t *rec_g, const DevCounters *ctr, uint32_t *counts)
+__global__ void count_views_kernel(const uint32_t *rec_g, const float4 *rd2, const DevCounters *ctr, uint32_t *counts)
 {
     const unsigned long long r = (unsigned long long)blockIdx.x * 256 + threadIdx.x;
     const unsigned long long nrec = ctr->n_records;
     if (r >= nrec || (r > 0 && rec_g[r - 1] == rec_g[r])) return;
-    unsigned long long e = r + 1;
-    while (e < nrec && rec_g[e] == rec_g[r]) e++;
-    counts[rec_g[r]] += (uint32_t)(e - r);
+    uint32_t views = 0;
+    for (unsigned long long e = r; e < nrec && rec_g[e] == rec_g[r]; e++)
+        views += rd2[e].w != 0.f ? 0u : 1u; // records marked culled (GS_CULL_MARK) are not rendered
+    counts[rec_g[r]] += views;
 }
 
 // ---- launchers ------------------------------------------------------------------------
@@ -316,7 +317,7 @@ cudaError_t launch_count_views(gs_workspace *ws, cudaStream_t st, uint32_t *coun
 {
     const unsigned blocks = (unsigned)((ws->cap.max_records + 255) / 256);
     if (blocks == 0) return cudaSuccess;
-    count_views_kernel<<<blocks, 256, 0, st>>>(ws->rec_g, ws->ctr, counts);
+    count_views_kernel<<<blocks, 256, 0, st>>>(ws->rec_g, ws->rd2, ws->ctr, counts);
     note_launch();
     return cudaGetLastError();
 }

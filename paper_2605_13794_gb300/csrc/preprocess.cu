@@ -368,7 +368,7 @@ __device__ __forceinline__ void gate_masks(const GaussPtrs &g, const PreOut &o, 
         ls[k][1] = ok ? g.log_scale[3 * i + 1] : 0.f;
         ls[k][2] = ok ? g.log_scale[3 * i + 2] : 0.f;
         lod[k] = (ok && rc.lod_enable && g.lod) ? (int)g.lod[i] : 0;
-        cw[k] = (ok && rc.cull_enable && o.cull) ? o.cull[i >> 5] : 0u;
+        cw[k] = (ok && rc.cull_enable == GS_CULL_DROP && o.cull) ? o.cull[i >> 5] : 0u;
         dm[k] = (ok && o.drift) ? o.drift[2 * i] : 0.f;
         dl[k] = (ok && o.drift) ? o.drift[2 * i + 1] : 0.f;
     }
@@ -381,7 +381,7 @@ __device__ __forceinline__ void gate_masks(const GaussPtrs &g, const PreOut &o, 
             const long long i = block0 + k * 256 + threadIdx.x;
             const float m[3] = {mx[k], my[k], mz[k]};
             const bool lod_ok = lod_pass_margin(m, lod[k], cam, rc, sh.thr2, sh.thr, dm[k]);
-            const bool culled = rc.cull_enable && ((cw[k] >> (i & 31)) & 1u);
+            const bool culled = rc.cull_enable == GS_CULL_DROP && ((cw[k] >> (i & 31)) & 1u);
             float t[3], te[3];
             camera_point(m, cam, t, te);
             te[0] += dm[k]; te[1] += dm[k]; te[2] += dm[k];
@@ -401,7 +401,8 @@ __device__ __forceinline__ void gate_masks(const GaussPtrs &g, const PreOut &o, 
             for (int c = 0; c < ncam; c++) {
                 const CamInfo &cam = sh.cams[c];
                 if (!lod_pass_margin(m, lod[k], cam, rc, sh.thr2, sh.thr, dm[k])) continue;
-                if (rc.cull_enable && (c == 0 ? ((cw[k] >> (i & 31)) & 1u) : cull_bit(o, c, i))) continue;
+                if (rc.cull_enable == GS_CULL_DROP && (c == 0 ? ((cw[k] >> (i & 31)) & 1u) : cull_bit(o, c, i)))
+                    continue;
                 float t[3], te[3];
                 camera_point(m, cam, t, te);
                 te[0] += dm[k]; te[1] += dm[k]; te[2] += dm[k];
@@ -559,9 +560,16 @@ __global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, 
         }
     }
     const unsigned long long cnt = __popcll(act);
+    // GS_CULL_MARK: records of the cameras whose Cull bit is set are kept and marked
+    unsigned long long marked = 0;
+    if (rc.cull_enable == GS_CULL_MARK)
+        for (unsigned long long mm = act; mm; mm &= mm - 1) {
+            const int c = __ffsll((long long)mm) - 1;
+            if (cull_bit(o, c, i)) marked |= 1ull << c;
+        }
     unsigned long long total, tvis;
     const unsigned long long excl = block_exclusive_scan_256<unsigned long long>(cnt, s_warp, total);
-    block_exclusive_scan_256<unsigned long long>((unsigned long long)(cnt > 0), s_warp, tvis);
+    block_exclusive_scan_256<unsigned long long>((unsigned long long)((act & ~marked) != 0), s_warp, tvis);
     if (threadIdx.x < 32) {
         const unsigned long long b = lookback_exclusive(o.lb_status + 1, bid, total, o.ctr, kSitePreprocess);
         if (threadIdx.x == 0) {
@@ -618,7 +626,7 @@ __global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, 
         o.rec_cam[r] = (uint16_t)c;
         o.rd0[r] = make_float4(p.u, p.v, p.A, p.k);
         o.rd1[r] = make_float4(p.D, op, col[0], col[1]);
-        o.rd2[r] = make_float4(col[2], p.u_lo, p.v_lo, 0.f);
+        o.rd2[r] = make_float4(col[2], p.u_lo, p.v_lo, ((marked >> c) & 1ull) ? 1.f : 0.f);
         o.rect[r] = make_uint2((uint32_t)p.x0 | ((uint32_t)p.y0 << 16), (uint32_t)p.x1 | ((uint32_t)p.y1 << 16));
         o.tt[r] = (uint32_t)((p.x1 - p.x0) * (p.y1 - p.y0));
         o.dkey[r] = __float_as_uint(p.depth);
@@ -724,6 +732,7 @@ struct BwdArgs {
     const uint32_t *rec_g;
     const uint16_t *rec_cam;
     const uint8_t *clampm;
+    const float4 *rd2;  // .w != 0: record marked culled (GS_CULL_MARK), no gradient
     const float *rgrad;
     float *cgrad;      // non-NULL: write each Gaussian's gradient row here (at its first record) instead
     float *absgrad;
@@ -751,6 +760,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, const Ca
         unsigned long long r0 = rh, r1 = rh + 1; // a Gaussian's records are contiguous
         while (r1 < nrec && a.rec_g[r1] == (uint32_t)i) r1++;
         float gm[3] = {0, 0, 0}, gls[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gop = 0.f;
+        bool vis = false; // an unmarked record (the visible set of Eq. 5)
         float gsh[48];
 #pragma unroll
         for (int k = 0; k < 48; k++) gsh[k] = 0.f;
@@ -773,6 +783,8 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, const Ca
             float gM[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}; // dL/dM, M = Q diag(s)
             float absacc = 0.f;
             for (unsigned long long r = r0; r < r1; r++) {
+                if (a.rd2[r].w != 0.f) continue; // marked culled: composited nowhere
+                vis = true;
                 const CamInfo &cam = s_cams[a.rec_cam[r]];
                 const float *rg = a.rgrad + r * kSlotFloats;
                 const float gu = rg[0], gv = rg[1], gA = rg[2], gB = rg[3], gC = rg[4], go = rg[5];
@@ -887,7 +899,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, const Ca
             for (int k = 0; k < 4; k++) gq[k] = (gq[k] - q[k] * qdot) / qn;
             if (a.absgrad) a.absgrad[i] += absacc;
             // scale regulariser (Eq. 5): beta / |V| * min_j s_j on the first smallest axis
-            if (a.beta > 0.f) {
+            if (a.beta > 0.f && vis) {
                 int jm = 0;
                 if (s[1] < s[jm]) jm = 1;
                 if (s[2] < s[jm]) jm = 2;
@@ -959,7 +971,7 @@ cudaError_t launch_preprocess_bwd(gs_workspace *ws, cudaStream_t st, const gs_ga
     BwdArgs a;
     a.g = GaussPtrs{g.mean, g.log_scale, g.quat, g.opacity_logit, g.sh, g.lod, n};
     a.gmean = gr.mean; a.gls = gr.log_scale; a.gquat = gr.quat; a.gop = gr.opacity_logit; a.gsh = gr.sh;
-    a.rec_g = ws->rec_g; a.rec_cam = ws->rec_cam; a.clampm = ws->clampm;
+    a.rec_g = ws->rec_g; a.rec_cam = ws->rec_cam; a.clampm = ws->clampm; a.rd2 = ws->rd2;
     a.rgrad = ws->rgrad;
     a.cgrad = cgrad;
     a.absgrad = absgrad; a.accumulate = accumulate; a.beta = beta;

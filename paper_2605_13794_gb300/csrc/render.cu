@@ -259,10 +259,11 @@ __global__ void __launch_bounds__(TileShape<TW, TH>::threads, 768 / TileShape<TW
         if (s < end) {
             const uint32_t r = vals[s];
             const float4 r0 = rd0[r], r1 = rd1[r], r2 = rd2[r];
+            const float op = r2.w != 0.f ? 0.f : r1.y; // a record marked culled composites nowhere
             s0[threadIdx.x] = stage_e0(r0, r2, tg);
-            s1[threadIdx.x] = make_float4(stage_D(r1), r1.y, r1.z, r1.w);
+            s1[threadIdx.x] = make_float4(stage_D(r1), op, r1.z, r1.w);
             s2[threadIdx.x] = r2.x;
-            s3[threadIdx.x] = alpha_box(r0.z, r0.w, r1.x, r1.y, rc.alpha_min);
+            s3[threadIdx.x] = alpha_box(r0.z, r0.w, r1.x, op, rc.alpha_min);
         }
         __syncthreads();
         const int cnt = min(kRT, end - b);
@@ -442,10 +443,11 @@ __global__ void __launch_bounds__(TileShape<TW, TH>::threads)
         if (threadIdx.x < cnt) {
             const uint32_t r = a.vals[lo + threadIdx.x];
             const float4 r0 = a.rd0[r], r1 = a.rd1[r], r2 = a.rd2[r];
+            const float op = r2.w != 0.f ? 0.f : r1.y; // a record marked culled composites nowhere
             s0[threadIdx.x] = stage_e0(r0, r2, tg);
-            s1[threadIdx.x] = make_float4(stage_D(r1), r1.y, r1.z, r1.w);
+            s1[threadIdx.x] = make_float4(stage_D(r1), op, r1.z, r1.w);
             s2[threadIdx.x] = r2.x;
-            s3[threadIdx.x] = alpha_box(r0.z, r0.w, r1.x, r1.y, rc.alpha_min);
+            s3[threadIdx.x] = alpha_box(r0.z, r0.w, r1.x, op, rc.alpha_min);
             s_slot[threadIdx.x] = slot_of(a.inst_off, a.rect, r, tg.tx, tg.ty);
         }
         __syncthreads();

@@ -139,6 +139,68 @@ def test_lod_gate_and_cull_mask_parity():
     assert (st == O.GATED_LOD).sum() > 1000 and (st == O.GATED_CULL).sum() > 1000
 
 
+def test_cull_mark_equals_drop_for_training_and_off_for_importance():
+    """GS_CULL_MARK keeps culled Gaussians in the lists, marked: the training
+    render and its gradients are those of GS_CULL_DROP bit for bit, and the
+    importance sweep on the same binning is that of GS_CULL_OFF bit for bit."""
+    g = synth.plain_scene(4000, seed=31)
+    cams = [synth.plain_camera(128, 112, 160.0), synth.plain_camera(96, 80, 120.0)]
+    n, words = g.n, (g.n + 31) // 32
+    rng = np.random.default_rng(32)
+    cull = (rng.integers(0, 1 << 32, size=(2, words), dtype=np.uint64) &
+            rng.integers(0, 1 << 32, size=(2, words), dtype=np.uint64)).astype(np.uint32) # ~25 % culled
+    cull_t = torch.from_numpy(cull.view(np.int32).ravel()).cuda()
+    P = O.Params(bg=(0.1, 0.2, 0.3))
+    gt = B.GaussianTensors.from_host(g)
+    npix = sum(c.width * c.height for c in cams)
+    dL = torch.from_numpy(rng.standard_normal(3 * npix).astype(np.float32)).cuda()
+
+    def run(mode):
+        ws = B.Workspace(**capacity_for(n, cams))
+        ws.preprocess(gt, cams, gpu_params(P, cull_enable=mode), cull_t if mode else None)
+        ws.bin_sort()
+        rgb, T = torch.empty(3 * npix, device="cuda"), torch.empty(npix, device="cuda")
+        ws.render_fwd(rgb, T)
+        out = dict(rgb=rgb.cpu().numpy(), T=T.cpu().numpy(), counts=ws.counts())
+        grads, absg, reg = gt.zeros_like(), torch.zeros(n, device="cuda"), torch.zeros(1, device="cuda")
+        ws.render_bwd(gt, dL, grads, accumulate=False, absgrad=absg, scale_reg_beta=10.0, scale_reg_value=reg)
+        views = torch.zeros(n, device="cuda", dtype=torch.int32)
+        ws.count_views(views)
+        out.update(grads=grads_to_host(grads), absg=absg.cpu().numpy(), reg=reg.item(), views=views.cpu().numpy())
+        out["imp"] = _importance(GpuRunLike(ws), n, len(cams))
+        return out
+
+    drop, mark, off = run(B.GS_CULL_DROP), run(B.GS_CULL_MARK), run(B.GS_CULL_OFF)
+    assert mark["counts"]["n_records"] == off["counts"]["n_records"] > drop["counts"]["n_records"]
+    assert mark["counts"]["n_visible"] == drop["counts"]["n_visible"]
+    for k in ("rgb", "T", "absg", "views"):
+        assert np.array_equal(mark[k], drop[k]), k
+    assert mark["reg"] == drop["reg"]
+    for k in mark["grads"]:
+        assert np.array_equal(mark["grads"][k], drop["grads"][k]), k
+    for k in off["imp"]:
+        assert np.array_equal(mark["imp"][k], off["imp"][k]), k
+    # and the marked render is the oracle's culled render
+    g64 = O.gaussians64(g)
+    Pc = O.Params(bg=(0.1, 0.2, 0.3), cull_enable=True)
+    base = 0
+    for c, cam in enumerate(cams):
+        fwd = O.forward_view(g64, cam, Pc, cull[c])
+        hw = cam.width * cam.height
+        img = mark["rgb"][3 * base:3 * (base + hw)].reshape(3, cam.height, cam.width)
+        ok = fwd["flags"] == 0
+        assert ok.mean() > 0.99
+        assert np.abs(img - fwd["image"]).max(axis=0)[ok].max() <= 1e-4
+        base += hw
+
+
+class GpuRunLike:
+    """The one attribute _importance needs from a GpuRun."""
+
+    def __init__(self, ws):
+        self.ws = ws
+
+
 def test_empty_and_fully_gated_scenes():
     cam = synth.plain_camera(64, 48, 100.0)
     P = O.Params()
