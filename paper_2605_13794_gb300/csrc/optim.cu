@@ -29,18 +29,23 @@ __device__ __forceinline__ float ld_zero(const float *p, int H, int W, int y, in
 // The two 11-tap passes run as sliding windows in registers: a thread
 // produces kHSeg consecutive outputs of a row from kHSeg + 10 inputs (or kVSeg
 // outputs of a column), so each shared-memory value is read once per thread
-// rather than once per tap.
+// rather than once per tap.  Maps travel in pairs as FP32x2 values -- (x, y),
+// (x^2, y^2) in the forward, (F0, F1) in the backward -- so one packed FMA
+// advances two maps.
 constexpr int kHSeg = 8;                 // horizontal outputs per thread (42 rows x 4 segments)
 constexpr int kVSeg = 4;                 // vertical outputs per thread (32 columns x 8 segments)
 constexpr int kLTP = kLTH + 1;           // padded row of the staged tile
 
-// grid: (tiles_x, tiles_y, batch * 3)
+__device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
+
+// grid: (tiles_x, tiles_y, batch * 3).  F: per pixel of each plane the three
+// coefficient maps of the SSIM gradient, (F0, F1, F2, 0).
 __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *img, const float *tgt, int H, int W, Win win,
-                                                       float C1, float C2, float *F /*[3][B*3][H][W]*/,
-                                                       long long plane_stride_maps, float *partial)
+                                                       float C1, float C2, float4 *F, float *partial)
 {
-    __shared__ float sx[kLTH][kLTP], sy[kLTH][kLTP];
-    __shared__ float hb[5][kLTH][kLT + 1];
+    __shared__ float2 sxy[kLTH][kLTP];
+    __shared__ float2 hb01[kLTH][kLT + 1], hb23[kLTH][kLT + 1];
+    __shared__ float hb4[kLTH][kLT + 1];
     __shared__ float red[2][8];
     const int plane = blockIdx.z;
     const float *x = img + (long long)plane * H * W;
@@ -48,26 +53,29 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *img, const f
     const int ox = blockIdx.x * kLT, oy = blockIdx.y * kLT;
     for (int k = threadIdx.x; k < kLTH * kLTH; k += 256) {
         const int r = k / kLTH, c = k % kLTH;
-        sx[r][c] = ld_zero(x, H, W, oy + r - kHalo, ox + c - kHalo);
-        sy[r][c] = ld_zero(y, H, W, oy + r - kHalo, ox + c - kHalo);
+        sxy[r][c] = make_float2(ld_zero(x, H, W, oy + r - kHalo, ox + c - kHalo),
+                                ld_zero(y, H, W, oy + r - kHalo, ox + c - kHalo));
     }
     __syncthreads();
-    // horizontal blur of x, y, x^2, y^2, xy: 42 rows x (32 / kHSeg) segments
+    // horizontal blur of (x, y), (x^2, y^2) and xy: 42 rows x (32 / kHSeg) segments
     for (int wi = threadIdx.x; wi < kLTH * (kLT / kHSeg); wi += 256) {
         const int r = wi / (kLT / kHSeg), c0 = (wi % (kLT / kHSeg)) * kHSeg;
-        float xv[kHSeg + 10], yv[kHSeg + 10];
+        float2 v[kHSeg + 10];
 #pragma unroll
-        for (int j = 0; j < kHSeg + 10; j++) { xv[j] = sx[r][c0 + j]; yv[j] = sy[r][c0 + j]; }
+        for (int j = 0; j < kHSeg + 10; j++) v[j] = sxy[r][c0 + j];
 #pragma unroll
         for (int o = 0; o < kHSeg; o++) {
-            float a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+            float2 a01 = f2s(0.f), a23 = f2s(0.f);
+            float a4 = 0.f;
 #pragma unroll
             for (int t = 0; t < 11; t++) {
-                const float xt = xv[o + t], yt = yv[o + t], wt = win.w[t];
-                a0 += wt * xt; a1 += wt * yt; a2 += wt * xt * xt; a3 += wt * yt * yt; a4 += wt * xt * yt;
+                const float2 wt = f2s(win.w[t]), vt = v[o + t];
+                const float2 p = __fmul2_rn(wt, vt);
+                a01 = __ffma2_rn(wt, vt, a01);
+                a23 = __ffma2_rn(p, vt, a23);
+                a4 = fmaf(p.x, vt.y, a4);
             }
-            hb[0][r][c0 + o] = a0; hb[1][r][c0 + o] = a1; hb[2][r][c0 + o] = a2; hb[3][r][c0 + o] = a3;
-            hb[4][r][c0 + o] = a4;
+            hb01[r][c0 + o] = a01; hb23[r][c0 + o] = a23; hb4[r][c0 + o] = a4;
         }
     }
     __syncthreads();
@@ -75,23 +83,22 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *img, const f
     float ssum = 0.f, l1sum = 0.f;
     {
         const int c = threadIdx.x % kLT, r0 = (threadIdx.x / kLT) * kVSeg;
-        float m[5][kVSeg];
+        float2 m01[kVSeg], m23[kVSeg];
+        float m4[kVSeg];
 #pragma unroll
-        for (int q = 0; q < 5; q++)
-#pragma unroll
-            for (int o = 0; o < kVSeg; o++) m[q][o] = 0.f;
+        for (int o = 0; o < kVSeg; o++) { m01[o] = f2s(0.f); m23[o] = f2s(0.f); m4[o] = 0.f; }
 #pragma unroll
         for (int j = 0; j < kVSeg + 10; j++) {
-            float v[5];
-#pragma unroll
-            for (int q = 0; q < 5; q++) v[q] = hb[q][r0 + j][c];
+            const float2 v01 = hb01[r0 + j][c], v23 = hb23[r0 + j][c];
+            const float v4 = hb4[r0 + j][c];
 #pragma unroll
             for (int o = 0; o < kVSeg; o++) {
                 const int t = j - o;
                 if (t >= 0 && t < 11) {
-                    const float wt = win.w[t];
-#pragma unroll
-                    for (int q = 0; q < 5; q++) m[q][o] += wt * v[q];
+                    const float2 wt = f2s(win.w[t]);
+                    m01[o] = __ffma2_rn(wt, v01, m01[o]);
+                    m23[o] = __ffma2_rn(wt, v23, m23[o]);
+                    m4[o] = fmaf(wt.x, v4, m4[o]);
                 }
             }
         }
@@ -100,9 +107,9 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *img, const f
             const int r = r0 + o;
             const int gy = oy + r, gx = ox + c;
             if (gy >= H || gx >= W) continue;
-            const float mx = m[0][o], my = m[1][o], exx = m[2][o], eyy = m[3][o], exy = m[4][o];
-            const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
-            const float A1 = 2.f * mx * my + C1, A2 = 2.f * sxy + C2;
+            const float mx = m01[o].x, my = m01[o].y, exx = m23[o].x, eyy = m23[o].y, exy = m4[o];
+            const float sxx = exx - mx * mx, syy = eyy - my * my, sxy_ = exy - mx * my;
+            const float A1 = 2.f * mx * my + C1, A2 = 2.f * sxy_ + C2;
             const float B1 = mx * mx + my * my + C1, B2 = sxx + syy + C2;
             const float iB = 1.f / (B1 * B2);
             const float S = A1 * A2 * iB;
@@ -110,11 +117,10 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *img, const f
             const float dsxx = -S / B2;
             const float dsxy = 2.f * A1 * iB;
             const long long p = (long long)plane * H * W + (long long)gy * W + gx;
-            F[p] = dmx - 2.f * mx * dsxx - my * dsxy;
-            F[plane_stride_maps + p] = dsxx;
-            F[2 * plane_stride_maps + p] = dsxy;
+            F[p] = make_float4(dmx - 2.f * mx * dsxx - my * dsxy, dsxx, dsxy, 0.f);
             ssum += S;
-            l1sum += fabsf(sx[r + kHalo][c + kHalo] - sy[r + kHalo][c + kHalo]);
+            const float2 px = sxy[r + kHalo][c + kHalo];
+            l1sum += fabsf(px.x - px.y);
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -133,55 +139,60 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *img, const f
 }
 
 __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float *img, const float *tgt, int H, int W, Win win,
-                                                       const float *F, long long plane_stride_maps, float lambda,
-                                                       int batch, float *dL)
+                                                       const float4 *F, float lambda, int batch, float *dL)
 {
-    __shared__ float sf[3][kLTH][kLTP];
-    __shared__ float hb[3][kLTH][kLT + 1];
+    __shared__ float2 sf01[kLTH][kLTP];
+    __shared__ float sf2[kLTH][kLTP];
+    __shared__ float2 hb01[kLTH][kLT + 1];
+    __shared__ float hb2[kLTH][kLT + 1];
     const int plane = blockIdx.z;
     const int ox = blockIdx.x * kLT, oy = blockIdx.y * kLT;
+    const float4 *Fp = F + (long long)plane * H * W;
     for (int k = threadIdx.x; k < kLTH * kLTH; k += 256) {
         const int r = k / kLTH, c = k % kLTH;
-        for (int m = 0; m < 3; m++)
-            sf[m][r][c] = ld_zero(F + m * plane_stride_maps + (long long)plane * H * W, H, W, oy + r - kHalo,
-                                  ox + c - kHalo);
+        const int gy = oy + r - kHalo, gx = ox + c - kHalo;
+        const float4 f = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? Fp[(long long)gy * W + gx]
+                                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+        sf01[r][c] = make_float2(f.x, f.y);
+        sf2[r][c] = f.z;
     }
     __syncthreads();
     for (int wi = threadIdx.x; wi < kLTH * (kLT / kHSeg); wi += 256) {
         const int r = wi / (kLT / kHSeg), c0 = (wi % (kLT / kHSeg)) * kHSeg;
+        float2 v01[kHSeg + 10];
+        float v2[kHSeg + 10];
 #pragma unroll
-        for (int m = 0; m < 3; m++) {
-            float v[kHSeg + 10];
+        for (int j = 0; j < kHSeg + 10; j++) { v01[j] = sf01[r][c0 + j]; v2[j] = sf2[r][c0 + j]; }
 #pragma unroll
-            for (int j = 0; j < kHSeg + 10; j++) v[j] = sf[m][r][c0 + j];
+        for (int o = 0; o < kHSeg; o++) {
+            float2 a01 = f2s(0.f);
+            float a2 = 0.f;
 #pragma unroll
-            for (int o = 0; o < kHSeg; o++) {
-                float a = 0.f;
-#pragma unroll
-                for (int t = 0; t < 11; t++) a += win.w[t] * v[o + t];
-                hb[m][r][c0 + o] = a;
+            for (int t = 0; t < 11; t++) {
+                a01 = __ffma2_rn(f2s(win.w[t]), v01[o + t], a01);
+                a2 = fmaf(win.w[t], v2[o + t], a2);
             }
+            hb01[r][c0 + o] = a01;
+            hb2[r][c0 + o] = a2;
         }
     }
     __syncthreads();
     const float npx = 3.f * (float)H * (float)W; // SSIM and L1 are means over channels and pixels
     const int c = threadIdx.x % kLT, r0 = (threadIdx.x / kLT) * kVSeg;
-    float b[3][kVSeg];
+    float2 b01[kVSeg];
+    float b2[kVSeg];
 #pragma unroll
-    for (int m = 0; m < 3; m++)
-#pragma unroll
-        for (int o = 0; o < kVSeg; o++) b[m][o] = 0.f;
+    for (int o = 0; o < kVSeg; o++) { b01[o] = f2s(0.f); b2[o] = 0.f; }
 #pragma unroll
     for (int j = 0; j < kVSeg + 10; j++) {
-        float v[3];
-#pragma unroll
-        for (int m = 0; m < 3; m++) v[m] = hb[m][r0 + j][c];
+        const float2 v01 = hb01[r0 + j][c];
+        const float v2 = hb2[r0 + j][c];
 #pragma unroll
         for (int o = 0; o < kVSeg; o++) {
             const int t = j - o;
             if (t >= 0 && t < 11) {
-#pragma unroll
-                for (int m = 0; m < 3; m++) b[m][o] += win.w[t] * v[m];
+                b01[o] = __ffma2_rn(f2s(win.w[t]), v01, b01[o]);
+                b2[o] = fmaf(win.w[t], v2, b2[o]);
             }
         }
     }
@@ -191,7 +202,7 @@ __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float *img, const f
         if (gy >= H || gx >= W) continue;
         const long long p = (long long)plane * H * W + (long long)gy * W + gx;
         const float xv = img[p], yv = tgt[p];
-        const float dssim = (b[0][o] + 2.f * xv * b[1][o] + yv * b[2][o]) / npx;
+        const float dssim = (b01[o].x + 2.f * xv * b01[o].y + yv * b2[o]) / npx;
         const float d = xv - yv;
         const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
         dL[p] = ((1.f - lambda) * sgn / npx - lambda * dssim) / (float)batch;
@@ -232,11 +243,10 @@ cudaError_t launch_loss(gs_workspace *ws, cudaStream_t st, const float *img, con
     for (int k = 0; k < 11; k++) { g[k] = exp(-((k - 5) * (k - 5)) / (2.0 * 1.5 * 1.5)); sum += g[k]; }
     for (int k = 0; k < 11; k++) win.w[k] = (float)(g[k] / sum);
     const dim3 grid((W + kLT - 1) / kLT, (H + kLT - 1) / kLT, B * 3);
-    const long long stride = (long long)B * 3 * H * W;
-    ssim_fwd_kernel<<<grid, 256, 0, st>>>(img, tgt, H, W, win, 0.01f * 0.01f, 0.03f * 0.03f, ws->loss_maps, stride,
-                                          ws->loss_partial);
+    float4 *maps = reinterpret_cast<float4 *>(ws->loss_maps);
+    ssim_fwd_kernel<<<grid, 256, 0, st>>>(img, tgt, H, W, win, 0.01f * 0.01f, 0.03f * 0.03f, maps, ws->loss_partial);
     note_launch();
-    ssim_bwd_kernel<<<grid, 256, 0, st>>>(img, tgt, H, W, win, ws->loss_maps, stride, lambda, B, dL);
+    ssim_bwd_kernel<<<grid, 256, 0, st>>>(img, tgt, H, W, win, maps, lambda, B, dL);
     note_launch();
     const int bpv = (int)(grid.x * grid.y * 3);
     loss_finalize_kernel<<<1, 256, 0, st>>>(ws->loss_partial, bpv, B, H, W, lambda, loss_out);
@@ -500,107 +510,137 @@ __device__ __forceinline__ void param_slot(int q, int &k, int &e)
 
 __device__ __forceinline__ int group_len(int k) { return k == 4 ? 48 : k == 3 ? 1 : k == 2 ? 4 : 3; }
 
-// The drift bounds after Gaussian i was brought to step t (one warp; lanes 0-5
-// hold the mean's and the log-scale's moments in mv, vv).
-__device__ __forceinline__ void lazy_set_drift_warp(const LazyArgs &a, long long i, int t, int lane, float mv,
-                                                    float vv)
+// The deferred steps run element-parallel.  A first kernel gives each
+// (Gaussian, parameter) pair one thread, which replays that parameter's missed
+// zero-gradient steps (and takes the gradient step): it reads last[i] and
+// never writes it, so the threads of one Gaussian need no ordering.  A second
+// kernel, one thread per Gaussian, then moves last[i] to the current step and
+// recomputes the drift bounds from the moments now stored.  Items: every
+// Gaussian (flush), the gate's candidates (catch-up, before projecting them) or
+// the Gaussians with a record (the gradient step).  A parameter whose m and v
+// are both +0 is a fixed point of the zero-gradient step (m and v stay +0, p
+// moves by (-lr m) / (sqrt(v) ibc2 + eps) = -0), so its replay is skipped and,
+// without a gradient step, it is not written at all.
+enum LazyMode { kLazyAll = 0, kLazyCandidates = 1, kLazyGrad = 2 };
+
+struct LazyItems {
+    const uint32_t *cand_g;    // kLazyCandidates: candidate Gaussians of the last gate
+    const uint32_t *rec_g;     // kLazyGrad: Gaussian of each record (a Gaussian's records contiguous)
+    const uint32_t *rec_first; // kLazyGrad: first record of each Gaussian
+    const float *cgrad;        // kLazyGrad: compact gradient rows at the first record
+    const DevCounters *ctr;    // sizes of the device lists
+    long long n;               // kLazyAll: Gaussians
+};
+
+template <int MODE> __device__ __forceinline__ unsigned long long lazy_count(const LazyItems &it)
 {
-    const float ratio = lane < 6 ? fabsf(mv) / (sqrtf(vv) + a.eps) : 0.f;
-    float dm = lane < 3 ? ratio : 0.f, ds = (lane >= 3 && lane < 6) ? ratio : 0.f;
+    return MODE == kLazyAll ? (unsigned long long)it.n
+                            : MODE == kLazyCandidates ? it.ctr->n_candidates : it.ctr->n_records;
+}
+
+// item j -> Gaussian i; false for a record that is not its Gaussian's first
+template <int MODE> __device__ __forceinline__ bool lazy_item(const LazyItems &it, unsigned long long j, long long &i)
+{
+    if (MODE == kLazyAll) { i = (long long)j; return true; }
+    if (MODE == kLazyCandidates) { i = it.cand_g[j]; return true; }
+    const uint32_t gi = it.rec_g[j];
+    if (j > 0 && it.rec_g[j - 1] == gi) return false;
+    i = gi;
+    return true;
+}
+
+// Parameter element idx of group k of Gaussian i: from its step `from` to step
+// t (kLazyGrad: the zero-gradient steps to t - 1, then the gradient step t).
+template <int MODE>
+__device__ __forceinline__ void lazy_param(const LazyArgs &a, int k, long long idx, int from, int t, float grad)
+{
+    const int to = MODE == kLazyGrad ? t - 1 : t;
+    float mv = a.m[k][idx], vv = a.v[k][idx];
+    const bool zero = (__float_as_uint(mv) | __float_as_uint(vv)) == 0u;
+    if (zero && MODE != kLazyGrad) return;
+    float pv = a.p[k][idx];
+    if (!zero)
+        for (int s = from + 1; s <= to; s++)
+            adam_one(pv, 0.f, mv, vv, a.b1, a.b2, a.hist[10 * s + k], a.hist[10 * s + 5 + k], a.eps);
+    if (MODE == kLazyGrad) adam_one(pv, grad, mv, vv, a.b1, a.b2, a.hist[10 * t + k], a.hist[10 * t + 5 + k], a.eps);
+    a.p[k][idx] = pv; a.m[k][idx] = mv; a.v[k][idx] = vv;
+}
+
+// every Gaussian, group by group: consecutive threads, consecutive elements.
+// Each thread takes kAllUnroll elements a grid stride apart per pass and
+// issues all their loads before any arithmetic.
+constexpr int kAllUnroll = 4;
+__global__ void __launch_bounds__(256) lazy_all_elem_kernel(LazyArgs a, long long n)
+{
+    const int t = *a.d_step;
+    const unsigned long long total = (unsigned long long)n * kGradRow, stride = gridDim.x * 256ull;
+    // groups laid end to end: mean 3n, log-scale 3n, quat 4n, opacity n, SH 48n
+    const unsigned long long b1 = 3ull * n, b2 = 6ull * n, b3 = 10ull * n, b4 = 11ull * n;
+    for (unsigned long long e0 = blockIdx.x * 256ull + threadIdx.x; e0 < total; e0 += kAllUnroll * stride) {
+        int k[kAllUnroll], from[kAllUnroll];
+        long long idx[kAllUnroll];
+        float mv[kAllUnroll], vv[kAllUnroll];
 #pragma unroll
-    for (int o = 4; o > 0; o >>= 1) {
-        dm += __shfl_xor_sync(0xffffffffu, dm, o);
-        ds = fmaxf(ds, __shfl_xor_sync(0xffffffffu, ds, o));
+        for (int u = 0; u < kAllUnroll; u++) {
+            const unsigned long long e = e0 + u * stride;
+            from[u] = t;
+            if (e >= total) continue;
+            k[u] = e < b1 ? 0 : e < b2 ? 1 : e < b3 ? 2 : e < b4 ? 3 : 4;
+            idx[u] = (long long)(e - (k[u] == 0 ? 0 : k[u] == 1 ? b1 : k[u] == 2 ? b2 : k[u] == 3 ? b3 : b4));
+            const unsigned long long x = (unsigned long long)idx[u];
+            const long long i = (long long)(k[u] == 4 ? x / 48 : k[u] == 3 ? x : k[u] == 2 ? x >> 2 : x / 3);
+            from[u] = a.last[i];
+            mv[u] = a.m[k[u]][idx[u]];
+            vv[u] = a.v[k[u]][idx[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < kAllUnroll; u++) {
+            if (from[u] >= t || (__float_as_uint(mv[u]) | __float_as_uint(vv[u])) == 0u) continue;
+            float pv = a.p[k[u]][idx[u]];
+            for (int s = from[u] + 1; s <= t; s++)
+                adam_one(pv, 0.f, mv[u], vv[u], a.b1, a.b2, a.hist[10 * s + k[u]], a.hist[10 * s + 5 + k[u]], a.eps);
+            a.p[k[u]][idx[u]] = pv; a.m[k[u]][idx[u]] = mv[u]; a.v[k[u]][idx[u]] = vv[u];
+        }
     }
-    if (lane == 0) {
+}
+
+// the Gaussians of a device list, 59 consecutive threads per Gaussian
+template <int MODE> __global__ void __launch_bounds__(256) lazy_list_elem_kernel(LazyArgs a, LazyItems it)
+{
+    const int t = *a.d_step;
+    const unsigned long long total = lazy_count<MODE>(it) * kGradRow;
+    for (unsigned long long e = blockIdx.x * 256ull + threadIdx.x; e < total; e += gridDim.x * 256ull) {
+        const unsigned long long j = e / kGradRow;
+        const int q = (int)(e - j * kGradRow);
+        long long i;
+        if (!lazy_item<MODE>(it, j, i)) continue;
+        const int from = a.last[i];
+        if (from >= t) continue;
+        int k, el;
+        param_slot(q, k, el);
+        const float grad = MODE == kLazyGrad ? it.cgrad[(long long)it.rec_first[i] * kGradRow + q] : 0.f;
+        lazy_param<MODE>(a, k, i * group_len(k) + el, from, t, grad);
+    }
+}
+
+// last[i] = t and the drift bounds of Gaussian i from its current moments
+template <int MODE> __global__ void __launch_bounds__(256) lazy_fin_kernel(LazyArgs a, LazyItems it)
+{
+    const int t = *a.d_step;
+    const unsigned long long cnt = lazy_count<MODE>(it);
+    for (unsigned long long j = blockIdx.x * 256ull + threadIdx.x; j < cnt; j += gridDim.x * 256ull) {
+        long long i;
+        if (!lazy_item<MODE>(it, j, i)) continue;
+        if (a.last[i] >= t) continue;
+        a.last[i] = t;
+        float dm = 0.f, ds = 0.f;
+#pragma unroll
+        for (int l = 0; l < 3; l++) {
+            dm += fabsf(a.m[0][3 * i + l]) / (sqrtf(a.v[0][3 * i + l]) + a.eps);
+            ds = fmaxf(ds, fabsf(a.m[1][3 * i + l]) / (sqrtf(a.v[1][3 * i + l]) + a.eps));
+        }
         a.drift[2 * i] = t > 0 ? a.drift_factor * a.hist[10 * t] * dm : 0.f;
         a.drift[2 * i + 1] = t > 0 ? a.drift_factor * a.hist[10 * t + 1] * ds : 0.f;
-    }
-}
-
-// One warp brings Gaussian i from step last[i] to step `to` (replaying the
-// zero-gradient steps), then, if grad_row is given, takes the gradient step
-// to + 1 with that compact row.  Every lane computes exactly what the dense
-// kernel computes for its parameters.
-__device__ __forceinline__ void lazy_warp(const LazyArgs &a, long long i, int to, const float *grad_row, int lane)
-{
-    const int from = a.last[i];
-    const int t_end = grad_row ? to + 1 : to;
-    if (from >= t_end) return;
-    long long idx[2];
-    int grp[2];
-    float mv[2] = {0.f, 0.f}, vv[2] = {0.f, 0.f};
-    bool zero = true;
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-        const int q = lane + 32 * h;
-        int e;
-        param_slot(q < kGradRow ? q : 0, grp[h], e);
-        idx[h] = i * group_len(grp[h]) + e;
-        if (q < kGradRow) {
-            mv[h] = a.m[grp[h]][idx[h]];
-            vv[h] = a.v[grp[h]][idx[h]];
-            zero = zero && __float_as_uint(mv[h]) == 0u && __float_as_uint(vv[h]) == 0u;
-        }
-    }
-    // (p, +0, +0) is a fixed point of the zero-gradient step (m and v stay +0,
-    // p moves by (-lr m) / (sqrt(v) ibc2 + eps) = -0), so a Gaussian whose
-    // moments are all +0 -- never given a gradient since they were zeroed --
-    // skips its replay, and without a gradient step is not touched at all
-    zero = __all_sync(0xffffffffu, zero);
-    if (!zero || grad_row) {
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int q = lane + 32 * h;
-            if (q >= kGradRow) break;
-            const int k = grp[h];
-            float pv = a.p[k][idx[h]];
-            if (!zero)
-                for (int s = from + 1; s <= to; s++)
-                    adam_one(pv, 0.f, mv[h], vv[h], a.b1, a.b2, a.hist[10 * s + k], a.hist[10 * s + 5 + k], a.eps);
-            if (grad_row)
-                adam_one(pv, grad_row[q], mv[h], vv[h], a.b1, a.b2, a.hist[10 * t_end + k],
-                         a.hist[10 * t_end + 5 + k], a.eps);
-            a.p[k][idx[h]] = pv; a.m[k][idx[h]] = mv[h]; a.v[k][idx[h]] = vv[h];
-        }
-    }
-    __syncwarp();
-    if (lane == 0) a.last[i] = t_end;
-    // lane l < 6: moments of parameter l (mean, log-scale) for the drift bound
-    lazy_set_drift_warp(a, i, t_end, lane, mv[0], vv[0]);
-}
-
-// The three kernels below run a grid of a few blocks per SM whose warps
-// stride over their items (a warp per item).
-
-// every candidate of the last gate: bring it to the current step
-__global__ void __launch_bounds__(256) lazy_catchup_kernel(LazyArgs a, const uint32_t *cand_g, const DevCounters *ctr)
-{
-    const unsigned long long nc = ctr->n_candidates, nw = (unsigned long long)gridDim.x * 8;
-    const int to = *a.d_step;
-    for (unsigned long long j = ((unsigned long long)blockIdx.x * 256 + threadIdx.x) >> 5; j < nc; j += nw)
-        lazy_warp(a, cand_g[j], to, nullptr, threadIdx.x & 31);
-}
-
-__global__ void __launch_bounds__(256) lazy_flush_kernel(LazyArgs a, long long n)
-{
-    const long long nw = (long long)gridDim.x * 8;
-    const int to = *a.d_step;
-    for (long long i = ((long long)blockIdx.x * 256 + threadIdx.x) >> 5; i < n; i += nw)
-        lazy_warp(a, i, to, nullptr, threadIdx.x & 31);
-}
-
-// every Gaussian with a record: bring it to step t - 1, then take the gradient
-// step t with its compact row; the others wait
-__global__ void __launch_bounds__(256) lazy_adam_kernel(LazyArgs a, const uint32_t *rec_g, const uint32_t *rec_first,
-                                                        const float *cgrad, const DevCounters *ctr)
-{
-    const unsigned long long nrec = ctr->n_records, nw = (unsigned long long)gridDim.x * 8;
-    const int t = *a.d_step;
-    for (unsigned long long r = ((unsigned long long)blockIdx.x * 256 + threadIdx.x) >> 5; r < nrec; r += nw) {
-        if (r > 0 && rec_g[r - 1] == rec_g[r]) continue;
-        const long long i = rec_g[r];
-        lazy_warp(a, i, t - 1, cgrad + (long long)rec_first[i] * kGradRow, threadIdx.x & 31);
     }
 }
 
@@ -631,34 +671,53 @@ static gs_gaussian_grads params_of(const gs_gaussians &g)
     return p;
 }
 
-cudaError_t launch_lazy_catchup(gs_workspace *ws, cudaStream_t st, const gs_gaussians &g)
+static LazyItems lazy_items(gs_workspace *ws, long long n)
 {
-    const unsigned blocks = (unsigned)std::min<long long>((g.n + 7) / 8, 8ll * ws->sm_count);
-    if (blocks == 0) return cudaSuccess;
-    lazy_catchup_kernel<<<blocks, 256, 0, st>>>(lazy_args(ws, params_of(g)), ws->cand_g, ws->ctr);
+    LazyItems it;
+    it.cand_g = ws->cand_g; it.rec_g = ws->rec_g; it.rec_first = ws->rec_first; it.cgrad = ws->cgrad;
+    it.ctr = ws->ctr; it.n = n;
+    return it;
+}
+
+// grid of up to 8 resident 256-thread blocks per SM, striding over `work` items
+static unsigned lazy_grid(gs_workspace *ws, unsigned long long work)
+{
+    return (unsigned)std::max<unsigned long long>(1, std::min<unsigned long long>((work + 255) / 256,
+                                                                                   8ull * ws->sm_count));
+}
+
+template <int MODE>
+static cudaError_t launch_lazy_list(gs_workspace *ws, cudaStream_t st, const LazyArgs &a, unsigned long long cap)
+{
+    const LazyItems it = lazy_items(ws, 0);
+    lazy_list_elem_kernel<MODE><<<lazy_grid(ws, cap * kGradRow), 256, 0, st>>>(a, it);
+    note_launch();
+    lazy_fin_kernel<MODE><<<lazy_grid(ws, cap), 256, 0, st>>>(a, it);
     note_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_lazy_catchup(gs_workspace *ws, cudaStream_t st, const gs_gaussians &g)
+{
+    if (g.n == 0) return cudaSuccess;
+    return launch_lazy_list<kLazyCandidates>(ws, st, lazy_args(ws, params_of(g)), (unsigned long long)g.n);
 }
 
 cudaError_t launch_lazy_flush(gs_workspace *ws, cudaStream_t st, const gs_gaussians &g)
 {
-    const unsigned blocks = (unsigned)std::min<long long>((g.n + 7) / 8, 8ll * ws->sm_count);
-    if (blocks == 0) return cudaSuccess;
-    lazy_flush_kernel<<<blocks, 256, 0, st>>>(lazy_args(ws, params_of(g)), g.n);
+    if (g.n == 0) return cudaSuccess;
+    const LazyArgs a = lazy_args(ws, params_of(g));
+    lazy_all_elem_kernel<<<lazy_grid(ws, (unsigned long long)g.n * kGradRow), 256, 0, st>>>(a, g.n);
+    note_launch();
+    lazy_fin_kernel<kLazyAll><<<lazy_grid(ws, (unsigned long long)g.n), 256, 0, st>>>(a, lazy_items(ws, g.n));
     note_launch();
     return cudaGetLastError();
 }
 
-static cudaError_t launch_lazy_adam(gs_workspace *ws, cudaStream_t st, const gs_gaussian_grads &param,
-                                    const gs_gaussian_grads &m, const gs_gaussian_grads &v, float b1, float b2,
-                                    float eps)
+static cudaError_t launch_lazy_adam(gs_workspace *ws, cudaStream_t st, const gs_gaussian_grads &param)
 {
-    (void)m; (void)v; (void)b1; (void)b2; (void)eps; // the enabled state's
-    const unsigned blocks = (unsigned)std::min<long long>((ws->cap.max_records + 7) / 8, 8ll * ws->sm_count);
-    if (blocks == 0) return cudaSuccess;
-    lazy_adam_kernel<<<blocks, 256, 0, st>>>(lazy_args(ws, param), ws->rec_g, ws->rec_first, ws->cgrad, ws->ctr);
-    note_launch();
-    return cudaGetLastError();
+    if (ws->cap.max_records == 0) return cudaSuccess;
+    return launch_lazy_list<kLazyGrad>(ws, st, lazy_args(ws, param), (unsigned long long)ws->cap.max_records);
 }
 
 cudaError_t launch_adam_sparse(gs_workspace *ws, cudaStream_t st, const gs_gaussian_grads &param,
@@ -671,7 +730,7 @@ cudaError_t launch_adam_sparse(gs_workspace *ws, cudaStream_t st, const gs_gauss
     adam_coef_kernel<<<1, 32, 0, st>>>(ca, ws->d_adam_step, ws->d_adam_coef, ws->lazy.hist, ws->lazy.max_steps,
                                        ws->ctr);
     note_launch();
-    if (ws->lazy.enabled) return launch_lazy_adam(ws, st, param, m, v, beta1, beta2, eps);
+    if (ws->lazy.enabled) return launch_lazy_adam(ws, st, param);
     AdamTable t;
     t.n = 5;
     t.cgrad = ws->cgrad;

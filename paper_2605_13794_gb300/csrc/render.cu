@@ -343,7 +343,7 @@ cudaError_t launch_render_fwd(gs_workspace *ws, cudaStream_t st, float *rgb, flo
 
 // ---- backward ---------------------------------------------------------------
 
-constexpr int kBwdBatch = 32;
+constexpr int kBwdBatch = 64; // entries staged per batch of the reverse walk (<= threads of every tile shape)
 
 struct BwdRenderArgs {
     const uint2 *ranges;
@@ -369,6 +369,7 @@ __global__ void __launch_bounds__(TileShape<TW, TH>::threads)
     render_bwd_kernel(BwdRenderArgs a, const CamTable *__restrict__ ctp, RenderConsts rc)
 {
     constexpr int kRT = TileShape<TW, TH>::threads, kWarps = TileShape<TW, TH>::warps;
+    static_assert(kBwdBatch <= kRT, "one staging thread per entry of a batch");
     __shared__ float4 s0[kBwdBatch];
     __shared__ float4 s1[kBwdBatch];
     __shared__ float s2[kBwdBatch];
