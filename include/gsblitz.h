@@ -288,6 +288,7 @@ int gs_adam_step_compact(gs_workspace *ws, const gs_gaussians *g, const gs_gauss
  *     Gaussian, bounds on how far its mean and its largest log-scale can still
  *     move, which widen the view gate);
  *   max_steps: steps the workspace keeps coefficients for (40 bytes each);
+ *   every moment array 16-byte aligned (as the parameter arrays);
  *   needs beta1 < sqrt(beta2).  Allocates the step history (once, here). */
 int gs_adam_lazy_enable(gs_workspace *ws, const gs_gaussian_grads *m, const gs_gaussian_grads *v, int32_t *last_step,
                         float *drift, float beta1, float beta2, float eps, int32_t max_steps);

@@ -620,6 +620,10 @@ int gs_adam_lazy_enable(gs_workspace *ws, const gs_gaussian_grads *m, const gs_g
     if (!m->mean || !m->log_scale || !m->quat || !m->opacity_logit || !m->sh || !v->mean || !v->log_scale ||
         !v->quat || !v->opacity_logit || !v->sh)
         return fail(GS_ERR_INVALID_ARG, "gs_adam_lazy_enable: NULL moment array");
+    if (!aligned16(m->mean) || !aligned16(m->log_scale) || !aligned16(m->quat) || !aligned16(m->opacity_logit) ||
+        !aligned16(m->sh) || !aligned16(v->mean) || !aligned16(v->log_scale) || !aligned16(v->quat) ||
+        !aligned16(v->opacity_logit) || !aligned16(v->sh))
+        return fail(GS_ERR_INVALID_ARG, "gs_adam_lazy_enable: moment arrays must be 16-byte aligned");
     const double r = (double)beta1 / sqrt((double)beta2);
     if (!(beta1 >= 0.f && beta1 < 1.f && beta2 > 0.f && beta2 < 1.f && r < 1.0))
         return fail(GS_ERR_INVALID_ARG, "gs_adam_lazy_enable: needs 0 <= beta1 < sqrt(beta2) < 1");
@@ -659,6 +663,9 @@ int gs_adam_flush(gs_workspace *ws, const gs_gaussians *g, gs_stream stream)
     if (!ws || !g) return fail(GS_ERR_INVALID_ARG, "gs_adam_flush: NULL argument");
     if (!ws->lazy.enabled) return GS_OK;
     if (g->n < 0 || g->n > ws->cap.max_gaussians) return fail(GS_ERR_CAPACITY, "gs_adam_flush: n > max_gaussians");
+    if (!aligned16(g->mean) || !aligned16(g->log_scale) || !aligned16(g->quat) || !aligned16(g->opacity_logit) ||
+        !aligned16(g->sh))
+        return fail(GS_ERR_INVALID_ARG, "gs_adam_flush: parameter arrays must be 16-byte aligned");
     CK(gs::launch_lazy_flush(ws, (cudaStream_t)stream, *g), "gs_adam_flush");
     return GS_OK;
 }

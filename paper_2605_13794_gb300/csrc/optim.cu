@@ -35,6 +35,7 @@ __device__ __forceinline__ float ld_zero(const float *p, int H, int W, int y, in
 constexpr int kHSeg = 8;                 // horizontal outputs per thread (42 rows x 4 segments)
 constexpr int kVSeg = 4;                 // vertical outputs per thread (32 columns x 8 segments)
 constexpr int kLTP = kLTH + 1;           // padded row of the staged tile
+constexpr int kStageIters = (kLTH * kLTH + 255) / 256; // staged values per thread
 
 __device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
 
@@ -51,15 +52,28 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *img, const f
     const float *x = img + (long long)plane * H * W;
     const float *y = tgt + (long long)plane * H * W;
     const int ox = blockIdx.x * kLT, oy = blockIdx.y * kLT;
-    for (int k = threadIdx.x; k < kLTH * kLTH; k += 256) {
-        const int r = k / kLTH, c = k % kLTH;
-        sxy[r][c] = make_float2(ld_zero(x, H, W, oy + r - kHalo, ox + c - kHalo),
-                                ld_zero(y, H, W, oy + r - kHalo, ox + c - kHalo));
+    {
+        // every load of the thread issued before the first store
+        float2 buf[kStageIters];
+#pragma unroll
+        for (int u = 0; u < kStageIters; u++) {
+            const int k = threadIdx.x + 256 * u;
+            const int r = k / kLTH, c = k % kLTH;
+            buf[u] = k < kLTH * kLTH ? make_float2(ld_zero(x, H, W, oy + r - kHalo, ox + c - kHalo),
+                                                   ld_zero(y, H, W, oy + r - kHalo, ox + c - kHalo))
+                                     : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < kStageIters; u++) {
+            const int k = threadIdx.x + 256 * u;
+            if (k < kLTH * kLTH) sxy[k / kLTH][k % kLTH] = buf[u];
+        }
     }
     __syncthreads();
-    // horizontal blur of (x, y), (x^2, y^2) and xy: 42 rows x (32 / kHSeg) segments
+    // horizontal blur of (x, y), (x^2, y^2) and xy: 42 rows x (32 / kHSeg) segments,
+    // consecutive threads on consecutive rows (no bank conflicts)
     for (int wi = threadIdx.x; wi < kLTH * (kLT / kHSeg); wi += 256) {
-        const int r = wi / (kLT / kHSeg), c0 = (wi % (kLT / kHSeg)) * kHSeg;
+        const int r = wi % kLTH, c0 = (wi / kLTH) * kHSeg;
         float2 v[kHSeg + 10];
 #pragma unroll
         for (int j = 0; j < kHSeg + 10; j++) v[j] = sxy[r][c0 + j];
@@ -148,17 +162,28 @@ __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float *img, const f
     const int plane = blockIdx.z;
     const int ox = blockIdx.x * kLT, oy = blockIdx.y * kLT;
     const float4 *Fp = F + (long long)plane * H * W;
-    for (int k = threadIdx.x; k < kLTH * kLTH; k += 256) {
-        const int r = k / kLTH, c = k % kLTH;
-        const int gy = oy + r - kHalo, gx = ox + c - kHalo;
-        const float4 f = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? Fp[(long long)gy * W + gx]
-                                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
-        sf01[r][c] = make_float2(f.x, f.y);
-        sf2[r][c] = f.z;
+    {
+        float4 buf[kStageIters];
+#pragma unroll
+        for (int u = 0; u < kStageIters; u++) {
+            const int k = threadIdx.x + 256 * u;
+            const int r = k / kLTH, c = k % kLTH;
+            const int gy = oy + r - kHalo, gx = ox + c - kHalo;
+            buf[u] = (k < kLTH * kLTH && gy >= 0 && gy < H && gx >= 0 && gx < W) ? Fp[(long long)gy * W + gx]
+                                                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < kStageIters; u++) {
+            const int k = threadIdx.x + 256 * u;
+            if (k < kLTH * kLTH) {
+                sf01[k / kLTH][k % kLTH] = make_float2(buf[u].x, buf[u].y);
+                sf2[k / kLTH][k % kLTH] = buf[u].z;
+            }
+        }
     }
     __syncthreads();
     for (int wi = threadIdx.x; wi < kLTH * (kLT / kHSeg); wi += 256) {
-        const int r = wi / (kLT / kHSeg), c0 = (wi % (kLT / kHSeg)) * kHSeg;
+        const int r = wi % kLTH, c0 = (wi / kLTH) * kHSeg;
         float2 v01[kHSeg + 10];
         float v2[kHSeg + 10];
 #pragma unroll
@@ -566,42 +591,57 @@ __device__ __forceinline__ void lazy_param(const LazyArgs &a, int k, long long i
     a.p[k][idx] = pv; a.m[k][idx] = mv; a.v[k][idx] = vv;
 }
 
-// every Gaussian, group by group: consecutive threads, consecutive elements.
-// Each thread takes kAllUnroll elements a grid stride apart per pass and
-// issues all their loads before any arithmetic.
-constexpr int kAllUnroll = 4;
+// every Gaussian: each group's array of n * LEN floats (16-byte aligned) in
+// float4 chunks, consecutive threads on consecutive chunks.  A chunk whose m
+// and v are all +0 needs nothing, not even its Gaussians' steps.
+template <int LEN>
+__device__ __forceinline__ void lazy_all_group(const LazyArgs &a, int k, long long n, int t)
+{
+    const unsigned long long total = (unsigned long long)n * LEN, chunks = total / 4;
+    const unsigned long long stride = gridDim.x * 256ull;
+    float *P = a.p[k], *M = a.m[k], *V = a.v[k];
+    for (unsigned long long c = blockIdx.x * 256ull + threadIdx.x; c < chunks; c += stride) {
+        float4 m4 = reinterpret_cast<const float4 *>(M)[c], v4 = reinterpret_cast<const float4 *>(V)[c];
+        float mv[4] = {m4.x, m4.y, m4.z, m4.w}, vv[4] = {v4.x, v4.y, v4.z, v4.w};
+        unsigned nz = 0;
+#pragma unroll
+        for (int u = 0; u < 4; u++) nz |= (__float_as_uint(mv[u]) | __float_as_uint(vv[u])) != 0u ? 1u << u : 0u;
+        if (!nz) continue;
+        int from[4];
+        bool any = false;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            from[u] = a.last[(4 * c + u) / LEN];
+            any = any || ((nz >> u) & 1u && from[u] < t);
+        }
+        if (!any) continue;
+        const float4 p4 = reinterpret_cast<const float4 *>(P)[c];
+        float pv[4] = {p4.x, p4.y, p4.z, p4.w};
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (!((nz >> u) & 1u)) continue;
+            for (int s = from[u] + 1; s <= t; s++)
+                adam_one(pv[u], 0.f, mv[u], vv[u], a.b1, a.b2, a.hist[10 * s + k], a.hist[10 * s + 5 + k], a.eps);
+        }
+        reinterpret_cast<float4 *>(P)[c] = make_float4(pv[0], pv[1], pv[2], pv[3]);
+        reinterpret_cast<float4 *>(M)[c] = make_float4(mv[0], mv[1], mv[2], mv[3]);
+        reinterpret_cast<float4 *>(V)[c] = make_float4(vv[0], vv[1], vv[2], vv[3]);
+    }
+    // the last total % 4 elements
+    for (unsigned long long e = chunks * 4 + blockIdx.x * 256ull + threadIdx.x; e < total; e += stride) {
+        const int from = a.last[e / LEN];
+        if (from < t) lazy_param<kLazyAll>(a, k, (long long)e, from, t, 0.f);
+    }
+}
+
 __global__ void __launch_bounds__(256) lazy_all_elem_kernel(LazyArgs a, long long n)
 {
     const int t = *a.d_step;
-    const unsigned long long total = (unsigned long long)n * kGradRow, stride = gridDim.x * 256ull;
-    // groups laid end to end: mean 3n, log-scale 3n, quat 4n, opacity n, SH 48n
-    const unsigned long long b1 = 3ull * n, b2 = 6ull * n, b3 = 10ull * n, b4 = 11ull * n;
-    for (unsigned long long e0 = blockIdx.x * 256ull + threadIdx.x; e0 < total; e0 += kAllUnroll * stride) {
-        int k[kAllUnroll], from[kAllUnroll];
-        long long idx[kAllUnroll];
-        float mv[kAllUnroll], vv[kAllUnroll];
-#pragma unroll
-        for (int u = 0; u < kAllUnroll; u++) {
-            const unsigned long long e = e0 + u * stride;
-            from[u] = t;
-            if (e >= total) continue;
-            k[u] = e < b1 ? 0 : e < b2 ? 1 : e < b3 ? 2 : e < b4 ? 3 : 4;
-            idx[u] = (long long)(e - (k[u] == 0 ? 0 : k[u] == 1 ? b1 : k[u] == 2 ? b2 : k[u] == 3 ? b3 : b4));
-            const unsigned long long x = (unsigned long long)idx[u];
-            const long long i = (long long)(k[u] == 4 ? x / 48 : k[u] == 3 ? x : k[u] == 2 ? x >> 2 : x / 3);
-            from[u] = a.last[i];
-            mv[u] = a.m[k[u]][idx[u]];
-            vv[u] = a.v[k[u]][idx[u]];
-        }
-#pragma unroll
-        for (int u = 0; u < kAllUnroll; u++) {
-            if (from[u] >= t || (__float_as_uint(mv[u]) | __float_as_uint(vv[u])) == 0u) continue;
-            float pv = a.p[k[u]][idx[u]];
-            for (int s = from[u] + 1; s <= t; s++)
-                adam_one(pv, 0.f, mv[u], vv[u], a.b1, a.b2, a.hist[10 * s + k[u]], a.hist[10 * s + 5 + k[u]], a.eps);
-            a.p[k[u]][idx[u]] = pv; a.m[k[u]][idx[u]] = mv[u]; a.v[k[u]][idx[u]] = vv[u];
-        }
-    }
+    lazy_all_group<3>(a, 0, n, t);   // mean
+    lazy_all_group<3>(a, 1, n, t);   // log-scale
+    lazy_all_group<4>(a, 2, n, t);   // quaternion
+    lazy_all_group<1>(a, 3, n, t);   // opacity
+    lazy_all_group<48>(a, 4, n, t);  // SH
 }
 
 // the Gaussians of a device list, 59 consecutive threads per Gaussian
