@@ -16,6 +16,11 @@ path through the C ABI on resident device data:
      record as without the Cull column it recomputes (w, a, s, c^rad, c^vis
      and the next Cull column).
 
+The timed steps are replays of one CUDA graph of the whole step (captured
+after eager warm-up steps; cameras from the workspace's device table, the Adam
+step number from its device counter), followed by the flush of the deferred
+Adam steps.
+
 value = rendered pixels per second of whole steps (Mpix/s); the line also
 carries Mgaussian/s.  All inputs (1.2 GB of parameters, Adam state, the
 workspace) exceed the 129 MB L2, so no flush is needed between steps.
@@ -184,7 +189,7 @@ class Step:
         # the scoring sweep after density control (the paper's T2 pass) renders with the LOD gate
         # engaged and never applies the Cull mask it recomputes
         self.params_imp = B.RenderParams(lod_enable=True, cull_enable=False, tile_w=tw, tile_h=th, **LOD)
-        self.step_no = 0
+        self.graph = None
         # capacities from a dry run of the importance configuration (no Cull column)
         tiles = B.tiles_of(cam, tw, th)
         probe = B.Workspace(max_gaussians=self.n, max_records=self.n, max_instances=min((1 << 30) - 1, 32 * self.n),
@@ -218,12 +223,34 @@ class Step:
             self.ws.adam_flush(self.gt)
 
     def run(self, ev=None):
-        """One step; ev, if given, is a list of 8 CUDA events recorded between stages."""
+        """One eager step; ev, if given, is a list of 8 CUDA events recorded between stages."""
+        self._body(ev)
+
+    def capture(self):
+        """The step as a CUDA graph (cameras in the workspace's device table,
+        the Adam step number from its device counter); returns the number of
+        kernels of this library in it."""
+        torch = self.torch
+        self.ws.upload_cameras([self.cam], self.params_train)
+        torch.cuda.synchronize()
+        n0 = self.B.kernel_launches()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._body(None, uploaded=True)
+        torch.cuda.synchronize()
+        return self.B.kernel_launches() - n0
+
+    def replay(self):
+        self.graph.replay()
+
+    def _body(self, ev, uploaded=False):
         B, ws, torch = self.B, self.ws, self.torch
         rec = (lambda k: ev[k].record()) if ev is not None else (lambda k: None)
-        self.step_no += 1
         rec(0)
-        ws.preprocess(self.gt, [self.cam], self.params_train, self.cull)
+        if uploaded:
+            ws.preprocess_uploaded(self.gt, self.params_train, self.cull)
+        else:
+            ws.preprocess(self.gt, [self.cam], self.params_train, self.cull)
         rec(1)
         ws.bin_sort()
         rec(2)
@@ -234,8 +261,9 @@ class Step:
         rec(4)
         ws.render_bwd_compact(self.gt, self.dL, scale_reg_beta=BETA, scale_reg_value=self.reg)
         rec(5)
-        # Adam on all Gaussians with the compact gradients (zero for Gaussians without a record)
-        ws.adam_step_compact(self.gt, self.m, self.v, self.lr, self.step_no)
+        # Adam on all Gaussians with the compact gradients (zero for Gaussians without a
+        # record); step 0: one past the workspace's device step counter
+        ws.adam_step_compact(self.gt, self.m, self.v, self.lr, 0)
         rec(6)
         # importance sweep of the view on the step's binning; its Cull column gates the next step
         ws.importance(s_accum=self.s, crad=self.crad, cvis=self.cvis, cull_out=self.cull)
@@ -503,6 +531,14 @@ def main():
         step.run()
     torch.cuda.synchronize()
     step.ws.sync_status()
+    # per-launch device time of the rasterisers: the library brackets each launch
+    # with events on its stream, as event nodes inside the captured step
+    step.ws.kernel_timing(True)
+    launches_per_step = step.capture()
+    for _ in range(args.warmup):
+        step.replay()
+    torch.cuda.synchronize()
+    step.ws.sync_status()
 
     # ---- device-timed region: K whole steps, inputs resident in HBM
     uuid = None
@@ -511,19 +547,15 @@ def main():
     except Exception:
         pass
     sampler = ClockSampler(uuid)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(args.steps)]
     barrier(world)
     torch.cuda.synchronize()
     sampler.start()
-    # per-launch device time of the rasterisers, from event pairs the library
-    # records around each launch on its stream
-    step.ws.kernel_timing(True)
     launches0 = B.kernel_launches()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     w0 = time.time()
     start.record(stream)
     for k in range(args.steps):
-        step.run(evs[k])
+        step.replay()
     # the deferred Adam steps of every Gaussian not yet brought up to date, inside the timed region
     fl0, fl1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     fl0.record(stream)
@@ -532,9 +564,11 @@ def main():
     end.record(stream)
     torch.cuda.synchronize()
     sampler.mark(w0, time.time())
-    launches = B.kernel_launches() - launches0
+    # graph replays launch the captured kernels without host calls
+    launches = launches_per_step * args.steps + (B.kernel_launches() - launches0)
     barrier(world)
     step.ws.sync_status()
+    # the captured event nodes hold the last timed replay's kernel durations
     kt = {name: step.ws.kernel_time(k) for name, k in (("render_fwd_kernel", B.GS_KT_RENDER_FWD),
                                                          ("render_bwd_kernel", B.GS_KT_RENDER_BWD),
                                                          ("importance_raster_kernel", B.GS_KT_IMPORTANCE))}
@@ -542,9 +576,6 @@ def main():
     kernel_ms = {name: max_over_ranks(t / max(n, 1), world) for name, (t, n) in kt.items()}
     ms = start.elapsed_time(end) / args.steps
     ms = max_over_ranks(ms, world)
-    stage_ms = {name: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
-                for i, name in enumerate(step.stage_names)}
-    stage_ms["adam_flush_per_step"] = fl0.elapsed_time(fl1) / args.steps
 
     # ---- end to end through the public API with host buffers
     tgt_host = torch.from_numpy(target).pin_memory()
@@ -561,7 +592,7 @@ def main():
     for _ in range(args.steps):
         step.target.view(-1).copy_(tgt_host.view(-1), non_blocking=True)
         step.cull.copy_(cull_host, non_blocking=True)
-        step.run()
+        step.replay()
         loss_host.copy_(step.loss, non_blocking=True)
         cull_host.copy_(step.cull, non_blocking=True)
     step.flush()
@@ -570,6 +601,17 @@ def main():
     sampler.mark(w0, time.time())
     clocks = sampler.stop()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+
+    # stage breakdown (diagnostic, outside the timed regions): eager steps with
+    # events between the stages
+    diag = max(1, min(args.steps, 10))
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(diag)]
+    for k in range(diag):
+        step.run(evs[k])
+    torch.cuda.synchronize()
+    stage_ms = {name: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(diag))
+                for i, name in enumerate(step.stage_names)}
+    stage_ms["adam_flush_per_step"] = fl0.elapsed_time(fl1) / args.steps
 
     P = cam.width * cam.height
     value = job_rate(P, ms, world) / 1e6
@@ -601,10 +643,12 @@ def main():
             "config": {"workload": WORKLOAD, "gaussians": g.n, "width": W_IMG, "height": H_IMG, "tile": args.tile,
                        "lod": True, "cull": True, "importance_pass": True,
                        "optimizer": "adam (dense)" if args.dense_adam else "adam, zero-gradient steps deferred (exact)",
-                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
+                       "l2": "inputs larger than L2 (no flush)", "execution": "CUDA graph of the whole step",
+                       "parallelism": f"replicas{world}"},
             "mgaussian_per_s": gauss,
             "fwd_bwd": fwd_bwd,
             "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+            "stage_ms_source": "eager steps with events between stages, outside the timed region",
             "counts": {k: counts[k] for k in ("n_records", "n_instances", "n_visible")},
             "kernel_ms": {k: round(v, 4) for k, v in kernel_ms.items()},
             "roofline": roof,
@@ -616,6 +660,9 @@ def main():
         line["cpu_baseline"] = cpu_baseline(g, cam, target)
     if rank == 0:
         print(json.dumps(line), flush=True)
+    # the graph names the workspace's buffers and events: release it first
+    step.graph = None
+    torch.cuda.synchronize()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -415,10 +415,15 @@ int gs_visible_set_static(const float *w, int64_t n, float vis_mass, uint32_t *c
 
 /* Kernel timing, for measurement.  While on, each launch of the timed kernels
  * below is bracketed by a CUDA event pair recorded on the stream it is launched
- * on (launches issued under stream capture are not timed).  Turning timing on
- * discards earlier records; the first 64 launches of each kernel are recorded.
- * gs_kernel_time synchronises those events and returns the summed device time
- * (ms) and the number of timed launches of one kernel.  Off by default. */
+ * on; a launch issued under stream capture gets a pair of event nodes in the
+ * graph, which each replay records again (so they hold the last replay's
+ * time).  Turning timing on discards earlier records; the first 64 launches of
+ * each kernel are recorded.  gs_kernel_time synchronises those events and
+ * returns the summed device time (ms) and the number of timed launches of one
+ * kernel (of a captured launch: after at least one replay).  Off by default.
+ * The events belong to the workspace (created on first use, destroyed with
+ * it), so a captured graph stays valid while timing is turned off and on; the
+ * pairs are numbered again from the first each time timing is turned on. */
 enum {
     GS_KT_RENDER_FWD = 0, /* gs_render_fwd's compositing kernel */
     GS_KT_RENDER_BWD = 1, /* the compositing adjoint (per (record, tile) slots) */

@@ -169,23 +169,31 @@ static cudaError_t kt_release(gs_workspace *ws)
     return e;
 }
 
+// Records one event of a timed launch: an ordinary record on an eager stream,
+// an event node (cudaEventRecordExternal) under stream capture, which every
+// replay of the graph records again.
+static void kt_record(cudaEvent_t ev, cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return;
+    if (cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+    else if (cs == cudaStreamCaptureStatusNone)
+        cudaEventRecord(ev, st);
+}
+
 void gs::kt_begin(gs_workspace *ws, int id, cudaStream_t st)
 {
     if (!ws->kt.on) return;
     ws->kt.launches[id]++;
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     if (ws->kt.used[id] >= gs_workspace::kTimedPairs) return;
-    cudaEventRecord(ws->kt.ev[id][ws->kt.used[id]][0], st);
+    kt_record(ws->kt.ev[id][ws->kt.used[id]][0], st);
 }
 
 void gs::kt_end(gs_workspace *ws, int id, cudaStream_t st)
 {
-    if (!ws->kt.on) return;
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
-    if (ws->kt.used[id] >= gs_workspace::kTimedPairs) return;
-    cudaEventRecord(ws->kt.ev[id][ws->kt.used[id]][1], st);
+    if (!ws->kt.on || ws->kt.used[id] >= gs_workspace::kTimedPairs) return;
+    kt_record(ws->kt.ev[id][ws->kt.used[id]][1], st);
     ws->kt.used[id]++;
 }
 
@@ -318,21 +326,24 @@ int gs_workspace_create(const gs_capacity *cap, gs_workspace **out)
 int gs_kernel_timing(gs_workspace *ws, int32_t enable)
 {
     if (!ws) return fail(GS_ERR_INVALID_ARG, "gs_kernel_timing: null workspace");
-    cudaError_t e = kt_release(ws);
-    if (e != cudaSuccess) return cuda_fail(e, "gs_kernel_timing");
+    // the events live as long as the workspace: a graph captured with timing on
+    // holds event nodes that name them
+    if (enable && !ws->kt.ev[0][0][0]) {
+        for (int k = 0; k < GS_KT_COUNT; k++)
+            for (int i = 0; i < gs_workspace::kTimedPairs; i++)
+                for (int h = 0; h < 2; h++) {
+                    const cudaError_t e = cudaEventCreate(&ws->kt.ev[k][i][h]);
+                    if (e != cudaSuccess) {
+                        kt_release(ws);
+                        return cuda_fail(e, "gs_kernel_timing");
+                    }
+                }
+    }
     for (int k = 0; k < GS_KT_COUNT; k++) {
         ws->kt.used[k] = 0;
         ws->kt.launches[k] = 0;
     }
-    if (!enable) return GS_OK;
-    for (int k = 0; k < GS_KT_COUNT; k++)
-        for (int i = 0; i < gs_workspace::kTimedPairs; i++)
-            for (int h = 0; h < 2; h++)
-                if ((e = cudaEventCreate(&ws->kt.ev[k][i][h])) != cudaSuccess) {
-                    kt_release(ws);
-                    return cuda_fail(e, "gs_kernel_timing");
-                }
-    ws->kt.on = 1;
+    ws->kt.on = enable ? 1 : 0;
     return GS_OK;
 }
 
