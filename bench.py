@@ -215,7 +215,7 @@ class Step:
             # Adam with deferred zero-gradient steps: bit-identical to dense Adam, touching only the
             # Gaussians in use; flush() brings every Gaussian to the current step
             self.last = torch.zeros(self.n, dtype=torch.int32, device="cuda")
-            self.drift = torch.zeros(self.n, 2, device="cuda")
+            self.drift = torch.zeros(2, self.n, device="cuda")
             self.ws.adam_lazy_enable(self.m, self.v, self.last, self.drift, max_steps=1 << 16)
 
     def flush(self):

@@ -284,7 +284,7 @@ int gs_adam_step_compact(gs_workspace *ws, const gs_gaussians *g, const gs_gauss
  * first.  gs_preprocess then UPDATES the Gaussian arrays it is given.
  *   m, v: the moments gs_adam_step_compact will be given (same arrays);
  *   last_step: [n] int32, set by the caller to the current step (0 before the
- *     first step) when enabling; drift: [n][2] float, zeroed by the caller (per
+ *     first step) when enabling; drift: [2][n] float, zeroed by the caller (per
  *     Gaussian, bounds on how far its mean and its largest log-scale can still
  *     move, which widen the view gate);
  *   max_steps: steps the workspace keeps coefficients for (40 bytes each);

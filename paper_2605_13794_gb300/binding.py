@@ -432,7 +432,9 @@ class Workspace:
 
     def adam_lazy_enable(self, m: GaussianTensors, v: GaussianTensors, last_step, drift, beta1=0.9, beta2=0.999,
                          eps=1e-15, max_steps=1 << 20):
-        """Deferred zero-gradient Adam steps (see gs_adam_lazy_enable)."""
+        """Deferred zero-gradient Adam steps (see gs_adam_lazy_enable).  last_step: (n,)
+        int32; drift: (2, n) float32, zeroed (mean and log-scale drift bounds)."""
+        assert drift.numel() == 2 * last_step.numel(), "drift must hold 2 * n floats"
         self._lazy = (m, v, last_step, drift)  # keep them alive
         mc, vc = m.c_grads(), v.c_grads()
         _check(lib().gs_adam_lazy_enable(self._ws, ctypes.byref(mc), ctypes.byref(vc), _ptr(last_step), _ptr(drift),

@@ -518,13 +518,14 @@ __global__ void adam_coef_kernel(AdamCoefArgs a, int *d_step, float *coef, float
 struct LazyArgs {
     float *p[5], *m[5], *v[5];
     int32_t *last;
-    float *drift;
+    float *drift;      // [2][n]: bounds on the further drift of the mean and of the largest log-scale
+    long long n;       // Gaussians
     const float *hist;
     const int *d_step;
     float b1, b2, eps, drift_factor;
 };
 
-// A Gaussian's 59 parameters, one per lane (lane l: parameters l and l + 32):
+// A Gaussian's 59 parameters in row order:
 // group and element of parameter q of the row (mean 3, log-scale 3, quat 4,
 // opacity 1, SH 48).
 __device__ __forceinline__ void param_slot(int q, int &k, int &e)
@@ -679,14 +680,15 @@ template <int MODE> __global__ void __launch_bounds__(256) lazy_fin_kernel(LazyA
             dm += fabsf(a.m[0][3 * i + l]) / (sqrtf(a.v[0][3 * i + l]) + a.eps);
             ds = fmaxf(ds, fabsf(a.m[1][3 * i + l]) / (sqrtf(a.v[1][3 * i + l]) + a.eps));
         }
-        a.drift[2 * i] = t > 0 ? a.drift_factor * a.hist[10 * t] * dm : 0.f;
-        a.drift[2 * i + 1] = t > 0 ? a.drift_factor * a.hist[10 * t + 1] * ds : 0.f;
+        a.drift[i] = t > 0 ? a.drift_factor * a.hist[10 * t] * dm : 0.f;
+        a.drift[a.n + i] = t > 0 ? a.drift_factor * a.hist[10 * t + 1] * ds : 0.f;
     }
 }
 
-static LazyArgs lazy_args(gs_workspace *ws, const gs_gaussian_grads &param)
+static LazyArgs lazy_args(gs_workspace *ws, const gs_gaussian_grads &param, long long n)
 {
     LazyArgs a;
+    a.n = n;
     float *P[5] = {param.mean, param.log_scale, param.quat, param.opacity_logit, param.sh};
     const gs_gaussian_grads &m = ws->lazy.m, &v = ws->lazy.v;
     float *M[5] = {m.mean, m.log_scale, m.quat, m.opacity_logit, m.sh};
@@ -740,13 +742,13 @@ static cudaError_t launch_lazy_list(gs_workspace *ws, cudaStream_t st, const Laz
 cudaError_t launch_lazy_catchup(gs_workspace *ws, cudaStream_t st, const gs_gaussians &g)
 {
     if (g.n == 0) return cudaSuccess;
-    return launch_lazy_list<kLazyCandidates>(ws, st, lazy_args(ws, params_of(g)), (unsigned long long)g.n);
+    return launch_lazy_list<kLazyCandidates>(ws, st, lazy_args(ws, params_of(g), g.n), (unsigned long long)g.n);
 }
 
 cudaError_t launch_lazy_flush(gs_workspace *ws, cudaStream_t st, const gs_gaussians &g)
 {
     if (g.n == 0) return cudaSuccess;
-    const LazyArgs a = lazy_args(ws, params_of(g));
+    const LazyArgs a = lazy_args(ws, params_of(g), g.n);
     lazy_all_elem_kernel<<<lazy_grid(ws, (unsigned long long)g.n * kGradRow), 256, 0, st>>>(a, g.n);
     note_launch();
     lazy_fin_kernel<kLazyAll><<<lazy_grid(ws, (unsigned long long)g.n), 256, 0, st>>>(a, lazy_items(ws, g.n));
@@ -754,10 +756,10 @@ cudaError_t launch_lazy_flush(gs_workspace *ws, cudaStream_t st, const gs_gaussi
     return cudaGetLastError();
 }
 
-static cudaError_t launch_lazy_adam(gs_workspace *ws, cudaStream_t st, const gs_gaussian_grads &param)
+static cudaError_t launch_lazy_adam(gs_workspace *ws, cudaStream_t st, const gs_gaussian_grads &param, long long n)
 {
     if (ws->cap.max_records == 0) return cudaSuccess;
-    return launch_lazy_list<kLazyGrad>(ws, st, lazy_args(ws, param), (unsigned long long)ws->cap.max_records);
+    return launch_lazy_list<kLazyGrad>(ws, st, lazy_args(ws, param, n), (unsigned long long)ws->cap.max_records);
 }
 
 cudaError_t launch_adam_sparse(gs_workspace *ws, cudaStream_t st, const gs_gaussian_grads &param,
@@ -770,7 +772,7 @@ cudaError_t launch_adam_sparse(gs_workspace *ws, cudaStream_t st, const gs_gauss
     adam_coef_kernel<<<1, 32, 0, st>>>(ca, ws->d_adam_step, ws->d_adam_coef, ws->lazy.hist, ws->lazy.max_steps,
                                        ws->ctr);
     note_launch();
-    if (ws->lazy.enabled) return launch_lazy_adam(ws, st, param);
+    if (ws->lazy.enabled) return launch_lazy_adam(ws, st, param, n);
     AdamTable t;
     t.n = 5;
     t.cgrad = ws->cgrad;

@@ -30,7 +30,7 @@ struct GaussPtrs {
 };
 
 // One projected (Gaussian, camera) pair.  The mean is kept to about 48 bits
-// as u + u_lo (u = the float nearest the double-precision mean): pixel
+// as u + u_lo (u = the float nearest the double-float mean): pixel
 // coordinates near 2000 carry only 1e-4 px in one float, and at the edge of a
 // small footprint that is a relative 1e-3 of alpha.  The conic is held as
 // A (x + k y)^2 + D y^2, whose terms stay accurate for long thin footprints at
@@ -127,7 +127,7 @@ __device__ __forceinline__ bool lod_pass_margin(const float m[3], int lod, const
 }
 
 // Camera-space mean in float, for the gate only, with a bound on its distance
-// from the double-precision value the projection uses: three additions and
+// from the double-float value the projection uses: three additions and
 // the final rounding each err by at most 2^-24 of a partial sum bounded by
 // sum_k |R_jk m_k| + |t_j|.
 __device__ __forceinline__ void camera_point(const float m[3], const CamInfo &cam, float t[3], float err[3])
@@ -142,17 +142,61 @@ __device__ __forceinline__ void camera_point(const float m[3], const CamInfo &ca
     }
 }
 
-// Camera-space mean in double: x_cam = R x + t.  float * float is exact in
-// double, so only the three additions round.
-__device__ __forceinline__ void camera_point_d(const float m[3], const CamInfo &cam, double t[3])
+// Double-float arithmetic: a value carried as hi + lo, two floats (~48
+// significant bits).  A product of floats splits exactly with an FMA
+// (Dekker's product), a sum exactly with Knuth's two-sum; every operation is
+// an explicitly rounded IEEE one, never contracted.  On GB300 the FP32 pipes
+// run these many times faster than the FP64 unit runs doubles.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF two_prod(float a, float b)
+{
+    const float p = FMUL(a, b);
+    return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ DF two_sum(float a, float b)
+{
+    const float s = FADD(a, b), bb = FSUB(s, a);
+    return {s, FADD(FSUB(a, FSUB(s, bb)), FSUB(b, bb))};
+}
+// |a| >= |b| (or a == 0)
+__device__ __forceinline__ DF fast_two_sum(float a, float b)
+{
+    const float s = FADD(a, b);
+    return {s, FSUB(b, FSUB(s, a))};
+}
+
+// Camera-space mean x_cam = R x + t in double-float: the three products
+// exactly, the three sums by two-sum, their error terms gathered in float
+// and folded in once (relative error ~2^-46 of the largest term).
+__device__ __forceinline__ void camera_point_df(const float m[3], const CamInfo &cam, DF t[3])
 {
     const float *R = cam.R;
 #pragma unroll
-    for (int j = 0; j < 3; j++)
-        t[j] = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn((double)R[3 * j], (double)m[0]),
-                                             __dmul_rn((double)R[3 * j + 1], (double)m[1])),
-                                   __dmul_rn((double)R[3 * j + 2], (double)m[2])),
-                         (double)cam.t[j]);
+    for (int j = 0; j < 3; j++) {
+        const DF p0 = two_prod(R[3 * j], m[0]), p1 = two_prod(R[3 * j + 1], m[1]), p2 = two_prod(R[3 * j + 2], m[2]);
+        const DF s1 = two_sum(p0.hi, p1.hi);
+        const DF s2 = two_sum(s1.hi, p2.hi);
+        const DF s3 = two_sum(s2.hi, cam.t[j]);
+        const float lo = FADD(FADD(FADD(FADD(FADD(p0.lo, p1.lo), s1.lo), p2.lo), s2.lo), s3.lo);
+        t[j] = fast_two_sum(s3.hi, lo);
+    }
+}
+
+// f * x / z + c in double-float (x, z double-float, f, c float): the quotient
+// x.hi / z.hi corrected by the exactly formed remainder, then the product and
+// the sum split exactly; returns the normalised pair (hi = the float nearest).
+__device__ __forceinline__ DF df_project(float f, DF x, DF z, float c)
+{
+    const float iz = 1.f / z.hi;
+    const float q = FMUL(x.hi, iz);
+    const DF qz = two_prod(q, z.hi);
+    const float r = FSUB(FADD(FSUB(FSUB(x.hi, qz.hi), qz.lo), x.lo), FMUL(q, z.lo)); // x - q z
+    const float ql = FMUL(r, iz);
+    const DF a = two_prod(f, q);
+    const DF b = two_sum(a.hi, c);
+    return fast_two_sum(b.hi, FADD(FADD(a.lo, FMUL(f, ql)), b.lo));
 }
 
 // Conservative screen test run before the exact covariance: false only when
@@ -179,7 +223,7 @@ __device__ __forceinline__ bool maybe_on_screen(const float t[3], const float e[
     return !(tzl > 1e-6f) || !off;
 }
 
-// Exact projection of one Gaussian into one camera, from the double-precision
+// Exact projection of one Gaussian into one camera, from the double-float
 // camera-space mean td (the near plane already passed).  Every float
 // operation is one explicitly rounded IEEE operation in a fixed order, so the
 // integer results (radius, rectangle, depth key) are reproducible bit for bit.
@@ -187,12 +231,12 @@ __device__ __forceinline__ bool maybe_on_screen(const float t[3], const float e[
 // determinant comes from the Cauchy-Binet identity (sum of the squared 2x2
 // minors of V, plus the dilation terms), which is free of the cancellation of
 // a c - b^2.  Returns false when the tile rectangle is empty.
-__device__ __forceinline__ bool project_gaussian(const float ls[3], const float qin[4], const double td[3],
+__device__ __forceinline__ bool project_gaussian(const float ls[3], const float qin[4], const DF td[3],
                                                  const CamInfo &cam, int tile_w, int tile_h, const RenderConsts &rc,
                                                  Proj &o)
 {
     const float *R = cam.R;
-    const float tx = __double2float_rn(td[0]), ty = __double2float_rn(td[1]), tz = __double2float_rn(td[2]);
+    const float tx = td[0].hi, ty = td[1].hi, tz = td[2].hi;
     float qw = qin[0], qx = qin[1], qy = qin[2], qz = qin[3];
     float qn = FSQRT(FADD(FADD(FADD(FMUL(qw, qw), FMUL(qx, qx)), FMUL(qy, qy)), FMUL(qz, qz)));
     qw = FDIV(qw, qn); qx = FDIV(qx, qn); qy = FDIV(qy, qn); qz = FDIV(qz, qn);
@@ -251,9 +295,8 @@ __device__ __forceinline__ bool project_gaussian(const float ls[3], const float 
     float lam = FADD(mid, FSQRT(disc));
     float ext = FMUL(3.f, FSQRT(lam));
     int radius = (int)ceilf(ext);
-    const double ud = __dadd_rn(__ddiv_rn(__dmul_rn((double)fx, td[0]), td[2]), (double)cam.cx);
-    const double vd = __dadd_rn(__ddiv_rn(__dmul_rn((double)fy, td[1]), td[2]), (double)cam.cy);
-    float u = __double2float_rn(ud), v = __double2float_rn(vd);
+    const DF ud = df_project(fx, td[0], td[2], cam.cx), vd = df_project(fy, td[1], td[2], cam.cy);
+    float u = ud.hi, v = vd.hi;
     float rr = (float)radius, tw = (float)tile_w, th = (float)tile_h;
     int x0 = (int)floorf(FDIV(FSUB(u, rr), tw)), y0 = (int)floorf(FDIV(FSUB(v, rr), th));
     int x1 = (int)floorf(FDIV(FADD(u, rr), tw)) + 1, y1 = (int)floorf(FDIV(FADD(v, rr), th)) + 1;
@@ -261,8 +304,8 @@ __device__ __forceinline__ bool project_gaussian(const float ls[3], const float 
     y0 = min(max(y0, 0), cam.tiles_y); y1 = min(max(y1, 0), cam.tiles_y);
     if (x1 <= x0 || y1 <= y0) return false;
     o.u = u; o.v = v;
-    o.u_lo = __double2float_rn(__dsub_rn(ud, (double)u));
-    o.v_lo = __double2float_rn(__dsub_rn(vd, (double)v));
+    o.u_lo = ud.lo;
+    o.v_lo = vd.lo;
     o.A = FDIV(c, det); o.k = FDIV(-b, c); o.D = FDIV(1.f, c);
     o.depth = tz;
     o.radius = radius;
@@ -280,7 +323,7 @@ struct PreOut {
     unsigned long long *cand_mask;
     uint32_t *gate_g;              // [N] block-strided candidates of the gate's first pass
     unsigned long long *gate_mask; // [N]
-    const float *drift;            // [N][2] drift bounds of Gaussians with deferred Adam steps, or NULL
+    const float *drift;            // [2][N] drift bounds (mean, log-scale) of deferred Adam steps, or NULL
     uint32_t *rec_first;           // first record of each Gaussian, ~0 when it has none
     unsigned long long *lb_status; // word 0: ticket
     DevCounters *ctr;
@@ -353,10 +396,11 @@ __device__ __forceinline__ void gate_masks(const GaussPtrs &g, const PreOut &o, 
     }
     stage_cameras(ct, sh.cams);
     const long long n = g.n;
-    float mx[kGateItems], my[kGateItems], mz[kGateItems], ls[kGateItems][3];
+    // first the loads every test needs (mean, level, Cull word, mean drift) ...
+    float mx[kGateItems], my[kGateItems], mz[kGateItems];
     int lod[kGateItems];
     uint32_t cw[kGateItems];
-    float dm[kGateItems], dl[kGateItems]; // drift bounds (deferred Adam steps), 0 when up to date
+    float dm[kGateItems]; // drift bound of the mean (deferred Adam steps), 0 when up to date
 #pragma unroll
     for (int k = 0; k < kGateItems; k++) {
         const long long i = block0 + k * 256 + threadIdx.x;
@@ -364,18 +408,16 @@ __device__ __forceinline__ void gate_masks(const GaussPtrs &g, const PreOut &o, 
         mx[k] = ok ? g.mean[3 * i] : 0.f;
         my[k] = ok ? g.mean[3 * i + 1] : 0.f;
         mz[k] = ok ? g.mean[3 * i + 2] : 0.f;
-        ls[k][0] = ok ? g.log_scale[3 * i] : 0.f;
-        ls[k][1] = ok ? g.log_scale[3 * i + 1] : 0.f;
-        ls[k][2] = ok ? g.log_scale[3 * i + 2] : 0.f;
         lod[k] = (ok && rc.lod_enable && g.lod) ? (int)g.lod[i] : 0;
         cw[k] = (ok && rc.cull_enable == GS_CULL_DROP && o.cull) ? o.cull[i >> 5] : 0u;
-        dm[k] = (ok && o.drift) ? o.drift[2 * i] : 0.f;
-        dl[k] = (ok && o.drift) ? o.drift[2 * i + 1] : 0.f;
+        dm[k] = (ok && o.drift) ? o.drift[i] : 0.f;
     }
     if (ncam == 1) {
-        // one camera: every test of every item evaluated without branches, so
-        // the four items' arithmetic interleaves
+        // one camera: the LOD, Cull and near tests of every item, then the
+        // shape (log-scales, their drift) of the items still in, then the
+        // screen test
         const CamInfo &cam = sh.cams[0];
+        bool in[kGateItems];
 #pragma unroll
         for (int k = 0; k < kGateItems; k++) {
             const long long i = block0 + k * 256 + threadIdx.x;
@@ -384,11 +426,29 @@ __device__ __forceinline__ void gate_masks(const GaussPtrs &g, const PreOut &o, 
             const bool culled = rc.cull_enable == GS_CULL_DROP && ((cw[k] >> (i & 31)) & 1u);
             float t[3], te[3];
             camera_point(m, cam, t, te);
+            const bool near_ok = t[2] + te[2] + dm[k] > rc.znear; // the exact near test is the projection's
+            in[k] = i < n && lod_ok && !culled && near_ok;
+        }
+        float lsmax[kGateItems];
+#pragma unroll
+        for (int k = 0; k < kGateItems; k++) {
+            const long long i = block0 + k * 256 + threadIdx.x;
+            lsmax[k] = 0.f;
+            if (in[k]) {
+                const float dl = o.drift ? o.drift[n + i] : 0.f;
+                lsmax[k] = fmaxf(g.log_scale[3 * i], fmaxf(g.log_scale[3 * i + 1], g.log_scale[3 * i + 2])) + dl;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kGateItems; k++) {
+            mask[k] = 0;
+            if (!in[k]) continue;
+            const float m[3] = {mx[k], my[k], mz[k]};
+            float t[3], te[3];
+            camera_point(m, cam, t, te);
             te[0] += dm[k]; te[1] += dm[k]; te[2] += dm[k];
-            const bool near_ok = t[2] + te[2] > rc.znear; // the exact near test is the projection's
-            const float smax = 1.0001f * __expf(fmaxf(ls[k][0], fmaxf(ls[k][1], ls[k][2])) + dl[k]);
-            const bool on = maybe_on_screen(t, te, smax, cam, tw, th, rc);
-            mask[k] = (i < n && lod_ok && !culled && near_ok && on) ? 1ull : 0ull;
+            const float smax = 1.0001f * __expf(lsmax[k]);
+            mask[k] = maybe_on_screen(t, te, smax, cam, tw, th, rc) ? 1ull : 0ull;
         }
     } else {
 #pragma unroll
@@ -407,7 +467,11 @@ __device__ __forceinline__ void gate_masks(const GaussPtrs &g, const PreOut &o, 
                 camera_point(m, cam, t, te);
                 te[0] += dm[k]; te[1] += dm[k]; te[2] += dm[k];
                 if (!(t[2] + te[2] > rc.znear)) continue; // the exact near test is the projection's
-                if (smax < 0.f) smax = 1.0001f * __expf(fmaxf(ls[k][0], fmaxf(ls[k][1], ls[k][2])) + dl[k]);
+                if (smax < 0.f) {
+                    const float dl = o.drift ? o.drift[n + i] : 0.f;
+                    smax = 1.0001f * __expf(fmaxf(g.log_scale[3 * i], fmaxf(g.log_scale[3 * i + 1],
+                                                                            g.log_scale[3 * i + 2])) + dl);
+                }
                 if (maybe_on_screen(t, te, smax, cam, tw, th, rc)) mask[k] |= 1ull << c;
             }
         }
@@ -552,9 +616,9 @@ __global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, 
             const int c = __ffsll((long long)mm) - 1;
             // the exact LOD decision (the gate's is widened for Gaussians with deferred steps)
             if (!lod_pass(L.m, lod, s_cams[c], rc, s_thr2)) continue;
-            double td[3];
-            camera_point_d(L.m, s_cams[c], td);
-            if (!(__double2float_rn(td[2]) > rc.znear)) continue;
+            DF td[3];
+            camera_point_df(L.m, s_cams[c], td);
+            if (!(td[2].hi > rc.znear)) continue;
             Proj p;
             if (project_gaussian(L.ls, L.q, td, s_cams[c], tw, th, rc, p)) act |= 1ull << c;
         }
@@ -595,8 +659,8 @@ __global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, 
             break;
         }
         const CamInfo &cam = s_cams[c];
-        double td[3];
-        camera_point_d(L.m, cam, td);
+        DF td[3];
+        camera_point_df(L.m, cam, td);
         Proj p;
         project_gaussian(L.ls, L.q, td, cam, tw, th, rc, p); // same inputs: same (passing) result
         const float dx = L.m[0] - cam.campos[0], dy = L.m[1] - cam.campos[1], dz = L.m[2] - cam.campos[2];
@@ -791,9 +855,9 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, const Ca
                 const float grgb[3] = {rg[6], rg[7], rg[8]};
                 absacc += sqrtf(gu * gu + gv * gv);
                 const float *W = cam.R;
-                double td[3];
-                camera_point_d(m, cam, td); // the camera-space mean the forward projected
-                const float t[3] = {__double2float_rn(td[0]), __double2float_rn(td[1]), __double2float_rn(td[2])};
+                DF td[3];
+                camera_point_df(m, cam, td); // the camera-space mean the forward projected
+                const float t[3] = {td[0].hi, td[1].hi, td[2].hi};
                 const float fx = cam.fx, fy = cam.fy;
                 const float limx = rc.fov_clamp * ((float)cam.width / (2.f * fx));
                 const float limy = rc.fov_clamp * ((float)cam.height / (2.f * fy));

@@ -343,7 +343,7 @@ cudaError_t launch_render_fwd(gs_workspace *ws, cudaStream_t st, float *rgb, flo
 
 // ---- backward ---------------------------------------------------------------
 
-constexpr int kBwdBatch = 64; // entries staged per batch of the reverse walk (<= threads of every tile shape)
+constexpr int kBwdBatch = 64; // entries staged per batch of the reverse walk
 
 struct BwdRenderArgs {
     const uint2 *ranges;
@@ -369,7 +369,6 @@ __global__ void __launch_bounds__(TileShape<TW, TH>::threads)
     render_bwd_kernel(BwdRenderArgs a, const CamTable *__restrict__ ctp, RenderConsts rc)
 {
     constexpr int kRT = TileShape<TW, TH>::threads, kWarps = TileShape<TW, TH>::warps;
-    static_assert(kBwdBatch <= kRT, "one staging thread per entry of a batch");
     __shared__ float4 s0[kBwdBatch];
     __shared__ float4 s1[kBwdBatch];
     __shared__ float s2[kBwdBatch];
@@ -441,15 +440,15 @@ __global__ void __launch_bounds__(TileShape<TW, TH>::threads)
     for (int hi = last; hi > start; hi -= kBwdBatch) {
         const int lo = max(start, hi - kBwdBatch);
         const int cnt = hi - lo;
-        if (threadIdx.x < cnt) {
-            const uint32_t r = a.vals[lo + threadIdx.x];
+        for (int e = threadIdx.x; e < cnt; e += kRT) {
+            const uint32_t r = a.vals[lo + e];
             const float4 r0 = a.rd0[r], r1 = a.rd1[r], r2 = a.rd2[r];
             const float op = r2.w != 0.f ? 0.f : r1.y; // a record marked culled composites nowhere
-            s0[threadIdx.x] = stage_e0(r0, r2, tg);
-            s1[threadIdx.x] = make_float4(stage_D(r1), op, r1.z, r1.w);
-            s2[threadIdx.x] = r2.x;
-            s3[threadIdx.x] = alpha_box(r0.z, r0.w, r1.x, op, rc.alpha_min);
-            s_slot[threadIdx.x] = slot_of(a.inst_off, a.rect, r, tg.tx, tg.ty);
+            s0[e] = stage_e0(r0, r2, tg);
+            s1[e] = make_float4(stage_D(r1), op, r1.z, r1.w);
+            s2[e] = r2.x;
+            s3[e] = alpha_box(r0.z, r0.w, r1.x, op, rc.alpha_min);
+            s_slot[e] = slot_of(a.inst_off, a.rect, r, tg.tx, tg.ty);
         }
         __syncthreads();
         for (int jj = cnt - 1; jj >= 0; jj--) {

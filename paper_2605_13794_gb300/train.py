@@ -51,7 +51,7 @@ class TrainStep:
         if lazy:
             # deferred zero-gradient steps: exact, but only Gaussians in use are touched
             self.last = torch.zeros(g.n, dtype=torch.int32, device=targets.device)
-            self.drift = torch.zeros(g.n, 2, device=targets.device)
+            self.drift = torch.zeros(2, g.n, device=targets.device)
             self.ws.adam_lazy_enable(self.m, self.v, self.last, self.drift, betas[0], betas[1], eps)
         self.set_views(cams, targets)
 

@@ -99,5 +99,5 @@ def test_drift_bounds_hold():
     dmean = (gl.mean - mean0).norm(dim=1)
     dls = (gl.log_scale - ls0).abs().max(dim=1).values
     assert waiting.sum() > 100
-    assert bool((dmean[waiting] <= drift[waiting, 0] + 1e-7).all())
-    assert bool((dls[waiting] <= drift[waiting, 1] + 1e-7).all())
+    assert bool((dmean[waiting] <= drift[0, waiting] + 1e-7).all())
+    assert bool((dls[waiting] <= drift[1, waiting] + 1e-7).all())
