@@ -645,7 +645,8 @@ __global__ void __launch_bounds__(256) lazy_all_elem_kernel(LazyArgs a, long lon
     lazy_all_group<48>(a, 4, n, t);  // SH
 }
 
-// the Gaussians of a device list, 59 consecutive threads per Gaussian
+// the Gaussians of a device list, 59 consecutive threads per Gaussian (a
+// record head j is its Gaussian's first record: its compact gradient row is row j)
 template <int MODE> __global__ void __launch_bounds__(256) lazy_list_elem_kernel(LazyArgs a, LazyItems it)
 {
     const int t = *a.d_step;
@@ -659,7 +660,7 @@ template <int MODE> __global__ void __launch_bounds__(256) lazy_list_elem_kernel
         if (from >= t) continue;
         int k, el;
         param_slot(q, k, el);
-        const float grad = MODE == kLazyGrad ? it.cgrad[(long long)it.rec_first[i] * kGradRow + q] : 0.f;
+        const float grad = MODE == kLazyGrad ? it.cgrad[j * kGradRow + q] : 0.f;
         lazy_param<MODE>(a, k, i * group_len(k) + el, from, t, grad);
     }
 }

@@ -126,6 +126,15 @@ __device__ __forceinline__ bool lod_pass_margin(const float m[3], int lod, const
     return dx * dx + dy * dy + dz * dz <= lim * lim;
 }
 
+// Depth row of camera_point alone (the near-plane test).
+__device__ __forceinline__ void camera_z(const float m[3], const CamInfo &cam, float &tz, float &ez)
+{
+    const float *R = cam.R;
+    tz = FADD(FADD(FADD(FMUL(R[6], m[0]), FMUL(R[7], m[1])), FMUL(R[8], m[2])), cam.t[2]);
+    const float mag = fabsf(R[6] * m[0]) + fabsf(R[7] * m[1]) + fabsf(R[8] * m[2]) + fabsf(cam.t[2]);
+    ez = 8.f * 5.9604645e-8f * mag + 1e-30f;
+}
+
 // Camera-space mean in float, for the gate only, with a bound on its distance
 // from the double-float value the projection uses: three additions and
 // the final rounding each err by at most 2^-24 of a partial sum bounded by
@@ -349,7 +358,7 @@ __device__ __forceinline__ void load_shape(const GaussPtrs &g, long long i, Gaus
 }
 
 constexpr int kGateItems = 4; // Gaussians per thread of the gate kernel: 1024 per block
-static_assert(kGateItems * 8 == 32, "the gate ranks its (item, warp) counts with one warp");
+static_assert((kGateItems * 8) % 32 == 0, "the gate ranks its (item, warp) counts with one warp");
 
 __device__ __forceinline__ bool cull_bit(const PreOut &o, int c, long long i)
 {
@@ -371,7 +380,7 @@ __device__ __forceinline__ void stage_cameras(const CamTable &ct, CamInfo *s_cam
 // plane and the conservative screen test -- everything that is cheap and
 // rejects most of a city scene -- producing an order-preserving list of
 // candidate Gaussians with a bit per camera that may still be active.
-// Thread t of block b owns Gaussians b*1024 + k*256 + t (k < 4).  Every load
+// Thread t of block b owns Gaussians b*256*kGateItems + k*256 + t.  Every load
 // a Gaussian may need (mean, level, log-scale, the Cull word of camera 0) is
 // issued up front, so a thread waits for memory once, not once per test.
 struct GateShared {
@@ -387,14 +396,6 @@ __device__ __forceinline__ void gate_masks(const GaussPtrs &g, const PreOut &o, 
                                            unsigned long long mask[kGateItems])
 {
     const int ncam = ct.n, tw = ct.tile_w, th = ct.tile_h;
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int l = 0; l <= kMaxLod; l++) {
-            sh.thr2[l] = rc.lod_thr2[l];
-            sh.thr[l] = sqrtf(rc.lod_thr2[l]);
-        }
-    }
-    stage_cameras(ct, sh.cams);
     const long long n = g.n;
     // first the loads every test needs (mean, level, Cull word, mean drift) ...
     float mx[kGateItems], my[kGateItems], mz[kGateItems];
@@ -412,6 +413,15 @@ __device__ __forceinline__ void gate_masks(const GaussPtrs &g, const PreOut &o, 
         cw[k] = (ok && rc.cull_enable == GS_CULL_DROP && o.cull) ? o.cull[i >> 5] : 0u;
         dm[k] = (ok && o.drift) ? o.drift[i] : 0.f;
     }
+    // ... in flight while the cameras and LOD thresholds are staged
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int l = 0; l <= kMaxLod; l++) {
+            sh.thr2[l] = rc.lod_thr2[l];
+            sh.thr[l] = sqrtf(rc.lod_thr2[l]);
+        }
+    }
+    stage_cameras(ct, sh.cams);
     if (ncam == 1) {
         // one camera: the LOD, Cull and near tests of every item, then the
         // shape (log-scales, their drift) of the items still in, then the
@@ -424,9 +434,9 @@ __device__ __forceinline__ void gate_masks(const GaussPtrs &g, const PreOut &o, 
             const float m[3] = {mx[k], my[k], mz[k]};
             const bool lod_ok = lod_pass_margin(m, lod[k], cam, rc, sh.thr2, sh.thr, dm[k]);
             const bool culled = rc.cull_enable == GS_CULL_DROP && ((cw[k] >> (i & 31)) & 1u);
-            float t[3], te[3];
-            camera_point(m, cam, t, te);
-            const bool near_ok = t[2] + te[2] + dm[k] > rc.znear; // the exact near test is the projection's
+            float tz, ez;
+            camera_z(m, cam, tz, ez);
+            const bool near_ok = tz + ez + dm[k] > rc.znear; // the exact near test is the projection's
             in[k] = i < n && lod_ok && !culled && near_ok;
         }
         float lsmax[kGateItems];
@@ -490,15 +500,28 @@ __device__ __forceinline__ unsigned gate_ranks(const unsigned long long mask[kGa
         if (lane == 0) sh.cnt[k][warp] = __popc(bal[k]);
     }
     __syncthreads();
-    if (threadIdx.x < 32) { // warp 0: exclusive scan of the 32 (item, warp) counts in (k, warp) order
-        const unsigned c = sh.cnt[lane >> 3][lane & 7];
-        unsigned x = c;
+    if (threadIdx.x < 32) { // warp 0: exclusive scan of the (item, warp) counts in (k, warp) order
+        constexpr int kPer = kGateItems * 8 / 32; // consecutive counts per lane
+        unsigned c[kPer], sum = 0;
+#pragma unroll
+        for (int p = 0; p < kPer; p++) {
+            const int e = lane * kPer + p;
+            c[p] = sh.cnt[e >> 3][e & 7];
+            sum += c[p];
+        }
+        unsigned x = sum;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const unsigned y = __shfl_up_sync(0xffffffffu, x, d);
             if (lane >= d) x += y;
         }
-        sh.cnt[lane >> 3][lane & 7] = x - c;
+        unsigned run = x - sum;
+#pragma unroll
+        for (int p = 0; p < kPer; p++) {
+            const int e = lane * kPer + p;
+            sh.cnt[e >> 3][e & 7] = run;
+            run += c[p];
+        }
         if (lane == 31) sh.total = x;
     }
     __syncthreads();
@@ -746,10 +769,11 @@ cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t 
 // Sum of the per-(record, tile) gradient slots of each record.  One warp per
 // record (records in depth order, whose slots are contiguous): lanes read the
 // slots strided by 32, then a fixed shuffle tree adds the lanes, so the sum is
-// the same on every run and no record's size serialises a thread.
+// the same on every run and no record's size serialises a thread.  Records
+// marked culled are skipped: the projection adjoint never reads them.
 __global__ void __launch_bounds__(256) reduce_slots_kernel(const uint32_t *drec, const uint32_t *inst_off,
-                                                           const uint32_t *tt, const float *slots, float *rgrad,
-                                                           const DevCounters *ctr)
+                                                           const uint32_t *tt, const float4 *rd2, const float *slots,
+                                                           float *rgrad, const DevCounters *ctr)
 {
     const unsigned long long nrec = ctr->n_records, ninst = ctr->n_instances;
     const int lane = threadIdx.x & 31;
@@ -757,7 +781,7 @@ __global__ void __launch_bounds__(256) reduce_slots_kernel(const uint32_t *drec,
     for (unsigned long long k = (unsigned long long)blockIdx.x * 8 + (threadIdx.x >> 5); k < nrec; k += nwarps) {
         const uint32_t r = drec[k];
         const unsigned long long off = inst_off[r], cnt = tt[r];
-        if (off + cnt > ninst) continue; // capacity error already recorded
+        if (off + cnt > ninst || rd2[r].w != 0.f) continue; // capacity error already recorded; marked
         float acc[kSlotFloats];
 #pragma unroll
         for (int j = 0; j < kSlotFloats; j++) acc[j] = 0.f;
@@ -784,7 +808,7 @@ cudaError_t launch_reduce_slots(gs_workspace *ws, cudaStream_t st)
     long long blocks = (cap + 7) / 8;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    reduce_slots_kernel<<<(unsigned)blocks, 256, 0, st>>>(ws->dval[ws->depth_buf], ws->inst_off, ws->tt, ws->slots,
+    reduce_slots_kernel<<<(unsigned)blocks, 256, 0, st>>>(ws->dval[ws->depth_buf], ws->inst_off, ws->tt, ws->rd2, ws->slots,
                                                          ws->rgrad, ws->ctr);
     note_launch();
     return cudaGetLastError();

@@ -122,22 +122,37 @@ __global__ void __launch_bounds__(256) sel_block_sum_kernel(const uint32_t *vals
     if (threadIdx.x == 0) bsum[blockIdx.x] = s[0];
 }
 
-// Exclusive scan of the block sums, one block, sequential chunks per thread.
-__global__ void sel_block_scan_kernel(double *bsum, int nblocks)
+// Exclusive scan of the block sums in one block of 1024 threads: each thread
+// a contiguous chunk, then a shuffle scan of the chunk sums per warp and one
+// over the 32 warp totals (a fixed association).
+constexpr int kBScanThreads = 1024;
+__global__ void __launch_bounds__(kBScanThreads) sel_block_scan_kernel(double *bsum, int nblocks)
 {
-    __shared__ double s[256];
-    const int per = (nblocks + 255) / 256;
+    __shared__ double s_w[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int per = (nblocks + kBScanThreads - 1) / kBScanThreads;
     const int b0 = threadIdx.x * per;
     double acc = 0.0;
     for (int b = b0; b < b0 + per && b < nblocks; b++) acc += bsum[b];
-    s[threadIdx.x] = acc;
+    double x = acc; // inclusive scan over the warp
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double run = 0.0;
-        for (int t = 0; t < 256; t++) { const double v = s[t]; s[t] = run; run += v; }
+    if (warp == 0) {
+        double t = s_w[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const double y = __shfl_up_sync(0xffffffffu, t, d);
+            if (lane >= d) t += y;
+        }
+        s_w[lane] = t - s_w[lane]; // exclusive over the warps
     }
     __syncthreads();
-    double run = s[threadIdx.x];
+    double run = s_w[warp] + (x - acc);
     for (int b = b0; b < b0 + per && b < nblocks; b++) { const double v = bsum[b]; bsum[b] = run; run += v; }
 }
 
@@ -194,7 +209,7 @@ cudaError_t launch_mass_scan(cudaStream_t st, const uint32_t *sorted, const floa
     if (sblocks == 0) return cudaSuccess;
     sel_block_sum_kernel<<<sblocks, 256, 0, st>>>(sorted, w, bsum, ctr);
     note_launch();
-    sel_block_scan_kernel<<<1, 256, 0, st>>>(bsum, (int)sblocks);
+    sel_block_scan_kernel<<<1, kBScanThreads, 0, st>>>(bsum, (int)sblocks);
     note_launch();
     sel_scan_kernel<<<sblocks, 256, 0, st>>>(sorted, w, bsum, cum, ctr);
     note_launch();
@@ -299,7 +314,7 @@ cudaError_t launch_importance(gs_workspace *ws, cudaStream_t st, float *w, uint3
     double *bsum = reinterpret_cast<double *>(ws->red_partial);
     sel_block_sum_kernel<<<sblocks, 256, 0, st>>>(sorted, ws->imp_w, bsum, ws->ctr);
     note_launch();
-    sel_block_scan_kernel<<<1, 256, 0, st>>>(bsum, (int)sblocks);
+    sel_block_scan_kernel<<<1, kBScanThreads, 0, st>>>(bsum, (int)sblocks);
     note_launch();
     sel_scan_kernel<<<sblocks, 256, 0, st>>>(sorted, ws->imp_w, bsum, ws->sel_cum, ws->ctr);
     note_launch();
