@@ -85,8 +85,9 @@ def train_batch_workload(n: int = 20_000_000, views: int = 8, width: int = 1600,
     capd = dict(max_records=rec, max_instances=inst)
     ga, gb = B.GaussianTensors.from_host(g), B.GaussianTensors.from_host(g)
     c0, t0 = batch(0)
-    eager = TrainStep(ga, c0, t0, params, LRS, capacity=capd)
-    graph = TrainStep(gb, c0, t0, params, LRS, capacity=capd)
+    # Adam with deferred zero-gradient steps (exact): each timed region ends with the flush
+    eager = TrainStep(ga, c0, t0, params, LRS, capacity=capd, lazy=True)
+    graph = TrainStep(gb, c0, t0, params, LRS, capacity=capd, lazy=True)
     eager.run(step=1)
     graph.run(step=1)
     graph.capture()
@@ -106,6 +107,7 @@ def train_batch_workload(n: int = 20_000_000, views: int = 8, width: int = 1600,
         eager.set_views(cm, tg)
         eager.run()
         losses_e.append(eager.loss.clone())
+    eager.flush()
     e1.record()
     torch.cuda.synchronize()
     eager_ms = e0.elapsed_time(e1) / steps
@@ -116,6 +118,7 @@ def train_batch_workload(n: int = 20_000_000, views: int = 8, width: int = 1600,
         graph.set_views(cm, tg)
         graph.replay()
         losses_g.append(graph.loss.clone())
+    graph.flush()
     g1.record()
     torch.cuda.synchronize()
     graph_ms = g0.elapsed_time(g1) / steps
