@@ -241,6 +241,15 @@ int gs_bin_sort(gs_workspace *ws, gs_stream stream);
  * transmittance [sum of H*W], same camera order; may be NULL. */
 int gs_render_fwd(gs_workspace *ws, float *rgb_out, float *T_out, gs_stream stream);
 
+/* gs_render_fwd and the importance sweep's raster in one walk of the lists:
+ * the image, T_final and n_contrib of gs_render_fwd, and each record's w and a
+ * (the raster and per-record sums of gs_importance, Sec. 3.2), bit for bit
+ * both.  With GS_CULL_MARK the image skips the marked records while the
+ * scores take every record.  The next gs_importance on the same binning then
+ * only selects (it skips its raster); a gs_preprocess or gs_bin_sort clears
+ * this.  The scores survive gs_render_bwd of the same binning. */
+int gs_render_fwd_importance(gs_workspace *ws, float *rgb_out, float *T_out, gs_stream stream);
+
 /* Adjoint of preprocess + compositing for dL_drgb (layout of rgb_out).
  * g must be the arrays given to gs_preprocess.  grads: written (accumulate=0,
  * every Gaussian, zeros where no record) or added to (accumulate=1).

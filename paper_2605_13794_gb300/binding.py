@@ -31,7 +31,8 @@ EXPORTS = ("gs_default_params", "gs_last_error", "gs_workspace_create", "gs_work
            "gs_kernel_launches", "gs_render_bwd_adam", "gs_render_bwd_compact", "gs_adam_step_compact",
            "gs_visible_set_static", "gs_upload_cameras", "gs_preprocess_uploaded", "gs_workspace_set_sort_chunk",
            "gs_prune_sample", "gs_prune_mass", "gs_compact", "gs_densify", "gs_count_views", "gs_adam_lazy_enable",
-           "gs_adam_lazy_disable", "gs_adam_flush", "gs_kernel_timing", "gs_kernel_time")
+           "gs_adam_lazy_disable", "gs_adam_flush", "gs_kernel_timing", "gs_kernel_time",
+           "gs_render_fwd_importance")
 
 # Cull modes of RenderParams.cull_enable (include/gsblitz.h)
 GS_CULL_OFF, GS_CULL_DROP, GS_CULL_MARK = 0, 1, 2
@@ -135,6 +136,7 @@ def lib() -> ctypes.CDLL:
         L.gs_preprocess_uploaded.argtypes = [vp, vp, vp, vp, vp]
         L.gs_bin_sort.argtypes = [vp, vp]
         L.gs_render_fwd.argtypes = [vp, vp, vp, vp]
+        L.gs_render_fwd_importance.argtypes = [vp, vp, vp, vp]
         L.gs_render_bwd.argtypes = [vp, vp, vp, vp, i32, vp, ctypes.c_float, vp, vp]
         f32 = ctypes.c_float
         L.gs_render_bwd_adam.argtypes = [vp, vp, vp, vp, vp, vp, f32, f32, f32, i32, vp, f32, vp, vp]
@@ -364,6 +366,10 @@ class Workspace:
 
     def render_fwd(self, rgb_out, T_out=None, stream=None):
         _check(lib().gs_render_fwd(self._ws, _ptr(rgb_out), _ptr(T_out), _stream(stream)))
+
+    def render_fwd_importance(self, rgb_out, T_out=None, stream=None):
+        """render_fwd and the importance raster in one pass; the next importance() only selects."""
+        _check(lib().gs_render_fwd_importance(self._ws, _ptr(rgb_out), _ptr(T_out), _stream(stream)))
 
     def render_bwd(self, g: GaussianTensors, dL_drgb, grads: GaussianTensors, accumulate=False, absgrad=None,
                    scale_reg_beta=0.0, scale_reg_value=None, stream=None):

@@ -463,6 +463,7 @@ int gs_upload_cameras(gs_workspace *ws, const gs_camera *cams, int32_t n_cams, c
     ws->have_preprocess = 0;
     ws->have_binning = 0;
     ws->have_compact = 0;
+    ws->imp_ready = 0;
     return GS_OK;
 }
 
@@ -506,6 +507,7 @@ int gs_preprocess_uploaded(gs_workspace *ws, const gs_gaussians *g, const uint32
     ws->have_preprocess = 1;
     ws->have_binning = 0;
     ws->have_compact = 0;
+    ws->imp_ready = 0;
     CK(gs::launch_preprocess(ws, (cudaStream_t)stream, cull), "gs_preprocess");
     return GS_OK;
 }
@@ -544,6 +546,7 @@ int gs_bin_sort(gs_workspace *ws, gs_stream stream)
     // 4. tile ranges
     CK(gs::launch_ranges(ws, st), "gs_bin_sort(ranges)");
     ws->have_binning = 1;
+    ws->imp_ready = 0;
     return GS_OK;
 }
 
@@ -552,6 +555,16 @@ int gs_render_fwd(gs_workspace *ws, float *rgb_out, float *T_out, gs_stream stre
     if (!ws || !rgb_out) return fail(GS_ERR_INVALID_ARG, "gs_render_fwd: NULL argument");
     if (!ws->have_binning) return fail(GS_ERR_INVALID_ARG, "gs_render_fwd: call gs_bin_sort first");
     CK(gs::launch_render_fwd(ws, (cudaStream_t)stream, rgb_out, T_out), "gs_render_fwd");
+    return GS_OK;
+}
+
+int gs_render_fwd_importance(gs_workspace *ws, float *rgb_out, float *T_out, gs_stream stream)
+{
+    if (!ws || !rgb_out) return fail(GS_ERR_INVALID_ARG, "gs_render_fwd_importance: NULL argument");
+    if (!ws->have_binning) return fail(GS_ERR_INVALID_ARG, "gs_render_fwd_importance: call gs_bin_sort first");
+    CK(gs::launch_render_fwd_importance(ws, (cudaStream_t)stream, rgb_out, T_out), "gs_render_fwd_importance");
+    CK(gs::launch_importance_reduce(ws, (cudaStream_t)stream), "gs_render_fwd_importance(reduce)");
+    ws->imp_ready = 1;
     return GS_OK;
 }
 

@@ -302,6 +302,7 @@ struct gs_workspace {
     int have_preprocess;
     int have_binning;
     int have_compact;    // compact gradient rows of the current binning exist
+    int imp_ready;       // the importance w, a of the current binning exist (gs_render_fwd_importance)
     int depth_buf;       // buffer holding sorted depth order
     int tile_buf;        // buffer holding sorted instances
     // kernel timing (gs_kernel_timing): event pairs around the rasterisers' launches
@@ -325,6 +326,8 @@ void kt_end(gs_workspace *ws, int id, cudaStream_t st);
 int report_error(int code, const char *msg);
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t *cull);
+cudaError_t launch_render_fwd_importance(gs_workspace *ws, cudaStream_t st, float *rgb, float *T_out);
+cudaError_t launch_importance_reduce(gs_workspace *ws, cudaStream_t st);
 cudaError_t launch_radix_sort(gs_workspace *ws, cudaStream_t st, uint32_t *keys[2], uint32_t *vals[2],
                               const unsigned long long *count, unsigned long long cap, int bits, bool vals_identity,
                               bool descending_keys_in_place, int &out_buf);

@@ -341,6 +341,189 @@ cudaError_t launch_render_fwd(gs_workspace *ws, cudaStream_t st, float *rgb, flo
     return cudaGetLastError();
 }
 
+// ---- forward fused with the importance raster ----------------------------------
+//
+// One walk over the view's lists computes both the training image (records
+// marked culled composite nowhere) and the importance slots (every record
+// with its own opacity, as the importance sweep renders).  Each entry's
+// exponent and alpha are evaluated once; each pixel carries two
+// transmittances and two stop flags.  Both outputs are those of
+// render_fwd_kernel and importance_raster_kernel bit for bit.
+struct FwdImpArgs {
+    const uint2 *ranges;
+    const uint32_t *vals;
+    const float4 *rd0, *rd1, *rd2;
+    const uint32_t *inst_off;
+    const uint2 *rect;
+    float *rgb_out, *T_out, *T_ws;
+    uint32_t *n_contrib;
+    float *slots; // [I][2]: importance alpha-weight, composited pixels (uint32 bits)
+};
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TileShape<TW, TH>::threads, 768 / TileShape<TW, TH>::threads)
+    render_fwd_imp_kernel(FwdImpArgs a, const CamTable *__restrict__ ctp, RenderConsts rc)
+{
+    constexpr int kRT = TileShape<TW, TH>::threads, kWarps = TileShape<TW, TH>::warps;
+    __shared__ float4 s0[kRT];
+    __shared__ float4 s1[kRT]; // (D, training opacity (0 when marked), r, g)
+    __shared__ float s2[kRT];
+    __shared__ float2 s3[kRT]; // alpha box of the record's own opacity
+    __shared__ float s4[kRT];  // the record's own opacity
+    __shared__ unsigned long long s_slot[kRT];
+    __shared__ float s_w[kWarps][kRT];
+    __shared__ uint32_t s_a[kWarps][kRT];
+    const CamTable &ct = *ctp;
+    if ((int)blockIdx.x >= ct.total_tiles) return;
+    const TileGeom tg = tile_geom<TW, TH>(ct, blockIdx.x);
+    const TileGeom &cam = tg;
+    const uint2 rg = a.ranges[blockIdx.x];
+    const int start = (int)rg.x, end = (int)rg.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const WarpBox<TW, TH> wb(warp);
+
+    const float2 px2 = make_float2(tg.lx0, tg.lx0 + 1.f);
+    const float2 py2 = make_float2(tg.ly0, tg.ly0 + 1.f);
+    float2 T[2] = {f2(1.f), f2(1.f)}, Cr[2] = {f2(0.f), f2(0.f)}, Cg[2] = {f2(0.f), f2(0.f)},
+           Cb[2] = {f2(0.f), f2(0.f)};
+    float2 Ti[2] = {f2(1.f), f2(1.f)}; // importance transmittance
+    uint32_t last[kQ] = {0, 0, 0, 0};
+    bool dn[kQ], di[kQ];
+#pragma unroll
+    for (int k = 0; k < kQ; k++) {
+        dn[k] = tg.px0 + (k & 1) >= cam.width || tg.py0 + (k >> 1) >= cam.height;
+        di[k] = dn[k];
+    }
+    int b = start;
+    for (; b < end; b += kRT) {
+        if (__syncthreads_count(dn[0] && dn[1] && dn[2] && dn[3] && di[0] && di[1] && di[2] && di[3]) == kRT)
+            break;
+        const int cnt = min(kRT, end - b);
+        if (threadIdx.x < cnt) {
+            const uint32_t r = a.vals[b + threadIdx.x];
+            const float4 r0 = a.rd0[r], r1 = a.rd1[r], r2 = a.rd2[r];
+            s0[threadIdx.x] = stage_e0(r0, r2, tg);
+            s1[threadIdx.x] = make_float4(stage_D(r1), r2.w != 0.f ? 0.f : r1.y, r1.z, r1.w);
+            s2[threadIdx.x] = r2.x;
+            s3[threadIdx.x] = alpha_box(r0.z, r0.w, r1.x, r1.y, rc.alpha_min);
+            s4[threadIdx.x] = r1.y;
+            s_slot[threadIdx.x] = slot_of(a.inst_off, a.rect, r, tg.tx, tg.ty);
+        }
+        __syncthreads();
+        bool wdone = false;
+        for (int j = 0; j < cnt; j++) {
+            const float4 p0 = s0[j];
+            if (!wdone)
+                wdone = __all_sync(0xffffffffu, dn[0] && dn[1] && dn[2] && dn[3] && di[0] && di[1] && di[2] && di[3]);
+            if (wdone || wb.misses(p0.x, p0.y, s3[j])) { // warp-uniform: nothing to add
+                if (lane == 0) { s_w[warp][j] = 0.f; s_a[warp][j] = 0u; }
+                continue;
+            }
+            const float4 p1 = s1[j];
+            const float cb = s2[j], oi = s4[j];
+            const bool train = p1.y != 0.f; // not marked culled
+            const uint32_t pos = (uint32_t)(b - start + j + 1);
+            const QuadPow q = quad_power(p0, p1.x, px2, py2);
+            float wv = 0.f;
+            uint32_t av = 0;
+#pragma unroll
+            for (int row = 0; row < 2; row++) {
+                float2 G;
+                const float2 al = pair_alpha(row ? q.r1 : q.r0, oi, rc.alpha_max, G);
+                const int k0 = 2 * row, k1 = 2 * row + 1;
+                if (train) { // the training image: render_fwd_kernel's update
+                    const float2 tT = __ffma2_rn(make_float2(-T[row].x, -T[row].y), al, T[row]);
+                    const bool ok0 = !dn[k0] && al.x >= rc.alpha_min, ok1 = !dn[k1] && al.y >= rc.alpha_min;
+                    const bool st0 = ok0 && tT.x < rc.T_min, st1 = ok1 && tT.y < rc.T_min;
+                    const bool c0 = ok0 && !st0, c1 = ok1 && !st1;
+                    dn[k0] = dn[k0] || st0;
+                    dn[k1] = dn[k1] || st1;
+                    const float2 ae = make_float2(c0 ? al.x : 0.f, c1 ? al.y : 0.f);
+                    const float2 w = __fmul2_rn(ae, T[row]);
+                    Cr[row] = __ffma2_rn(w, f2(p1.z), Cr[row]);
+                    Cg[row] = __ffma2_rn(w, f2(p1.w), Cg[row]);
+                    Cb[row] = __ffma2_rn(w, f2(cb), Cb[row]);
+                    T[row] = __ffma2_rn(make_float2(-T[row].x, -T[row].y), ae, T[row]);
+                    last[k0] = c0 ? pos : last[k0];
+                    last[k1] = c1 ? pos : last[k1];
+                }
+                { // the importance sweep: importance_raster_kernel's update
+                    const float2 tT = __ffma2_rn(make_float2(-Ti[row].x, -Ti[row].y), al, Ti[row]);
+                    const bool ok0 = !di[k0] && al.x >= rc.alpha_min, ok1 = !di[k1] && al.y >= rc.alpha_min;
+                    const bool st0 = ok0 && tT.x < rc.T_min, st1 = ok1 && tT.y < rc.T_min;
+                    const bool c0 = ok0 && !st0, c1 = ok1 && !st1;
+                    di[k0] = di[k0] || st0;
+                    di[k1] = di[k1] || st1;
+                    const float2 ae = make_float2(c0 ? al.x : 0.f, c1 ? al.y : 0.f);
+                    const float2 w = __fmul2_rn(ae, Ti[row]);
+                    wv += w.x + w.y;
+                    av += (uint32_t)c0 + (uint32_t)c1;
+                    Ti[row] = __ffma2_rn(make_float2(-Ti[row].x, -Ti[row].y), ae, Ti[row]);
+                }
+            }
+            if (__any_sync(0xffffffffu, av != 0)) {
+                wv = warp_sum_f(wv);
+                av = __reduce_add_sync(0xffffffffu, av);
+            }
+            if (lane == 0) { s_w[warp][j] = wv; s_a[warp][j] = av; }
+        }
+        __syncthreads();
+        if (threadIdx.x < cnt) {
+            float wsum = s_w[0][threadIdx.x];
+            uint32_t asum = s_a[0][threadIdx.x];
+#pragma unroll
+            for (int w = 1; w < kWarps; w++) { wsum += s_w[w][threadIdx.x]; asum += s_a[w][threadIdx.x]; }
+            reinterpret_cast<float2 *>(a.slots)[s_slot[threadIdx.x]] = make_float2(wsum, __uint_as_float(asum));
+        }
+    }
+    // entries never reached (every pixel of the tile had stopped in both walks)
+    for (int s = b + threadIdx.x; s < end; s += kRT) {
+        const unsigned long long slot = slot_of(a.inst_off, a.rect, a.vals[s], tg.tx, tg.ty);
+        reinterpret_cast<float2 *>(a.slots)[slot] = make_float2(0.f, 0.f);
+    }
+    const long long np = (long long)cam.width * cam.height;
+    float *img = a.rgb_out + 3 * cam.pix_base;
+#pragma unroll
+    for (int k = 0; k < kQ; k++) {
+        const int px = tg.px0 + (k & 1), py = tg.py0 + (k >> 1);
+        if (px >= cam.width || py >= cam.height) continue;
+        const int row = k >> 1;
+        const float Tk = (k & 1) ? T[row].y : T[row].x;
+        const float cr = (k & 1) ? Cr[row].y : Cr[row].x;
+        const float cg = (k & 1) ? Cg[row].y : Cg[row].x;
+        const float cbk = (k & 1) ? Cb[row].y : Cb[row].x;
+        const long long pix = (long long)py * cam.width + px;
+        img[pix] = cr + Tk * rc.bg[0];
+        img[np + pix] = cg + Tk * rc.bg[1];
+        img[2 * np + pix] = cbk + Tk * rc.bg[2];
+        const long long gp = cam.pix_base + pix;
+        if (a.T_out) a.T_out[gp] = Tk;
+        a.T_ws[gp] = Tk;
+        a.n_contrib[gp] = last[k];
+    }
+}
+
+cudaError_t launch_render_fwd_importance(gs_workspace *ws, cudaStream_t st, float *rgb, float *T_out)
+{
+    if (ws->cams.total_tiles == 0) return cudaSuccess;
+    FwdImpArgs a;
+    a.ranges = ws->ranges; a.vals = ws->tval[ws->tile_buf]; a.rd0 = ws->rd0; a.rd1 = ws->rd1; a.rd2 = ws->rd2;
+    a.inst_off = ws->inst_off; a.rect = ws->rect; a.rgb_out = rgb; a.T_out = T_out; a.T_ws = ws->T_final;
+    a.n_contrib = ws->n_contrib; a.slots = ws->slots;
+    const unsigned grid = (unsigned)ws->cams.total_tiles;
+    kt_begin(ws, GS_KT_RENDER_FWD, st);
+    switch (tile_shape_id(ws->cams.tile_w, ws->cams.tile_h)) {
+    case 0: render_fwd_imp_kernel<16, 16><<<grid, TileShape<16, 16>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
+    case 1: render_fwd_imp_kernel<32, 8><<<grid, TileShape<32, 8>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
+    case 2: render_fwd_imp_kernel<8, 32><<<grid, TileShape<8, 32>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
+    case 3: render_fwd_imp_kernel<32, 16><<<grid, TileShape<32, 16>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
+    default: return cudaErrorInvalidValue;
+    }
+    kt_end(ws, GS_KT_RENDER_FWD, st);
+    note_launch();
+    return cudaGetLastError();
+}
+
 // ---- backward ---------------------------------------------------------------
 
 constexpr int kBwdBatch = 64; // entries staged per batch of the reverse walk

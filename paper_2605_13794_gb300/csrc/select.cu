@@ -262,6 +262,19 @@ __global__ void cull_init_kernel(uint32_t *cull, long long words, long long n, i
     }
 }
 
+// w and a of every record from the importance slots of the current binning
+cudaError_t launch_importance_reduce(gs_workspace *ws, cudaStream_t st)
+{
+    const unsigned long long rcap = (unsigned long long)ws->cap.max_records;
+    const unsigned blocks = (unsigned)std::max<unsigned long long>(1, std::min<unsigned long long>((rcap + 7) / 8,
+                                                                                                    16ull * ws->sm_count));
+    imp_reduce_kernel<<<blocks, 256, 0, st>>>(ws->dval[ws->depth_buf], ws->inst_off, ws->tt,
+                                              reinterpret_cast<const float2 *>(ws->slots), ws->imp_w, ws->imp_a,
+                                              ws->ctr);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_importance(gs_workspace *ws, cudaStream_t st, float *w, uint32_t *a, float *s_accum,
                               uint32_t *crad, uint32_t *cvis, uint32_t *cull_out)
 {
@@ -270,12 +283,11 @@ cudaError_t launch_importance(gs_workspace *ws, cudaStream_t st, float *w, uint3
     const int ncam = ws->cams.n;
     const unsigned long long rcap = (unsigned long long)ws->cap.max_records;
     const unsigned rblocks = (unsigned)((rcap + 255) / 256);
-    if ((e = launch_importance_raster(ws, st)) != cudaSuccess) return e;
-    imp_reduce_kernel<<<(unsigned)std::max<unsigned long long>(1, std::min<unsigned long long>((rcap + 7) / 8, 152 * 16)), 256, 0, st>>>(
-        ws->dval[ws->depth_buf], ws->inst_off, ws->tt,
-                                                reinterpret_cast<const float2 *>(ws->slots), ws->imp_w, ws->imp_a,
-                                                ws->ctr);
-    note_launch();
+    // w and a per record: from the raster here, unless gs_render_fwd_importance took them already
+    if (!ws->imp_ready) {
+        if ((e = launch_importance_raster(ws, st)) != cudaSuccess) return e;
+        if ((e = launch_importance_reduce(ws, st)) != cudaSuccess) return e;
+    }
     if (w && (e = cudaMemsetAsync(w, 0, (size_t)ncam * n * sizeof(float), st)) != cudaSuccess) return e;
     if (a && (e = cudaMemsetAsync(a, 0, (size_t)ncam * n * sizeof(uint32_t), st)) != cudaSuccess) return e;
     if (n > 0) {

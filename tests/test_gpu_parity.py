@@ -194,6 +194,44 @@ def test_cull_mark_equals_drop_for_training_and_off_for_importance():
         base += hw
 
 
+@pytest.mark.parametrize("mode", [B.GS_CULL_MARK, B.GS_CULL_OFF])
+def test_fused_forward_importance_matches_separate(mode):
+    """gs_render_fwd_importance: the image, T_final and n_contrib of gs_render_fwd
+    and the importance outputs of gs_importance's own raster, bit for bit, on a
+    two-camera scene with a Cull column; the backward after it is unchanged."""
+    g = synth.plain_scene(4000, seed=33)
+    cams = [synth.plain_camera(128, 112, 160.0), synth.plain_camera(96, 80, 120.0)]
+    n, words = g.n, (g.n + 31) // 32
+    rng = np.random.default_rng(34)
+    cull = (rng.integers(0, 1 << 32, size=(2, words), dtype=np.uint64) &
+            rng.integers(0, 1 << 32, size=(2, words), dtype=np.uint64)).astype(np.uint32)
+    cull_t = torch.from_numpy(cull.view(np.int32).ravel()).cuda()
+    P = O.Params(bg=(0.1, 0.2, 0.3))
+    gt = B.GaussianTensors.from_host(g)
+    npix = sum(c.width * c.height for c in cams)
+    dL = torch.from_numpy(rng.standard_normal(3 * npix).astype(np.float32)).cuda()
+
+    def run(fused):
+        ws = B.Workspace(**capacity_for(n, cams))
+        ws.preprocess(gt, cams, gpu_params(P, cull_enable=mode), cull_t if mode else None)
+        ws.bin_sort()
+        rgb, T = torch.empty(3 * npix, device="cuda"), torch.empty(npix, device="cuda")
+        (ws.render_fwd_importance if fused else ws.render_fwd)(rgb, T)
+        nc = ws.read_buffer(B.GS_BUF_N_CONTRIB, np.uint32, npix)
+        grads = gt.zeros_like()
+        ws.render_bwd(gt, dL, grads, accumulate=False)
+        imp = _importance(GpuRunLike(ws), n, len(cams))
+        return rgb.cpu().numpy(), T.cpu().numpy(), nc, grads_to_host(grads), imp
+
+    sep, fus = run(False), run(True)
+    for k in range(3):
+        assert np.array_equal(sep[k], fus[k])
+    for k in sep[3]:
+        assert np.array_equal(sep[3][k], fus[3][k]), k
+    for k in sep[4]:
+        assert np.array_equal(sep[4][k], fus[4][k]), k
+
+
 class GpuRunLike:
     """The one attribute _importance needs from a GpuRun."""
 
