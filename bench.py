@@ -577,30 +577,59 @@ def main():
     ms = start.elapsed_time(end) / args.steps
     ms = max_over_ranks(ms, world)
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers: every step's
+    # target image comes from pinned host memory, and its loss and new Cull
+    # column go back to pinned host memory.  The copies run on their own
+    # streams through double-buffered device staging, overlapped with the
+    # neighbouring steps; the timed region ends when the last read-back lands.
+    K = args.steps
     tgt_host = torch.from_numpy(target).pin_memory()
-    cull_host = torch.empty(step.cull.numel(), dtype=torch.int32).pin_memory()
-    loss_host = torch.empty(1).pin_memory()
-    h2d = tgt_host.numel() * 4 + cull_host.numel() * 4
-    d2h = loss_host.numel() * 4 + cull_host.numel() * 4
-    cull_host.copy_(step.cull.cpu())
+    loss_host = torch.empty(K).pin_memory()
+    cull_host = torch.empty((K, step.cull.numel()), dtype=torch.int32).pin_memory()
+    h2d = tgt_host.numel() * 4
+    d2h = 4 + step.cull.numel() * 4
+    h2d_stream, d2h_stream = torch.cuda.Stream(), torch.cuda.Stream()
+    stage_t = [torch.empty_like(step.target) for _ in range(2)]
+    stage_o = [(torch.empty(1, device="cuda"), torch.empty_like(step.cull)) for _ in range(2)]
+    t_ready, t_free = [torch.cuda.Event() for _ in range(2)], [torch.cuda.Event() for _ in range(2)]
+    o_ready, o_free = [torch.cuda.Event() for _ in range(2)], [torch.cuda.Event() for _ in range(2)]
     barrier(world)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     w0 = time.time()
     e0.record(stream)
-    for _ in range(args.steps):
-        step.target.view(-1).copy_(tgt_host.view(-1), non_blocking=True)
-        step.cull.copy_(cull_host, non_blocking=True)
+    h2d_stream.wait_event(e0)
+    with torch.cuda.stream(h2d_stream):
+        stage_t[0].copy_(tgt_host, non_blocking=True)
+        t_ready[0].record(h2d_stream)
+    for k in range(K):
+        b, nb = k % 2, (k + 1) % 2
+        stream.wait_event(t_ready[b])
+        step.target.copy_(stage_t[b])
+        t_free[b].record(stream)
+        if k + 1 < K:  # the next step's target, while this step runs
+            h2d_stream.wait_event(t_free[nb])
+            with torch.cuda.stream(h2d_stream):
+                stage_t[nb].copy_(tgt_host, non_blocking=True)
+                t_ready[nb].record(h2d_stream)
         step.replay()
-        loss_host.copy_(step.loss, non_blocking=True)
-        cull_host.copy_(step.cull, non_blocking=True)
+        stream.wait_event(o_free[b])
+        stage_o[b][0].copy_(step.loss)
+        stage_o[b][1].copy_(step.cull)
+        o_ready[b].record(stream)
+        d2h_stream.wait_event(o_ready[b])
+        with torch.cuda.stream(d2h_stream):
+            loss_host[k:k + 1].copy_(stage_o[b][0], non_blocking=True)
+            cull_host[k].copy_(stage_o[b][1], non_blocking=True)
+            o_free[b].record(d2h_stream)
     step.flush()
+    stream.wait_stream(d2h_stream)
     e1.record(stream)
     torch.cuda.synchronize()
     sampler.mark(w0, time.time())
     clocks = sampler.stop()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+    assert bool(torch.isfinite(loss_host).all()), "non-finite loss read back"
 
     # stage breakdown (diagnostic, outside the timed regions): eager steps with
     # events between the stages
