@@ -8,6 +8,31 @@
 
 namespace gs {
 
+// Programmatic dependent launch.  Every kernel of this library is launched
+// with launch_pdl, which lets it be scheduled while the previous kernel on
+// the stream drains, and begins with griddep_wait, which blocks until that
+// kernel has completed and its writes are visible (a no-op when launched
+// without the attribute).  Kernel-to-kernel gaps of a step shrink; inside a
+// CUDA graph the launches become programmatic dependency edges.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Single-instruction square root and reciprocal (PTX .approx forms).
 __device__ __forceinline__ float sqrt_approx(float x)
 {

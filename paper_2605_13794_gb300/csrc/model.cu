@@ -33,6 +33,7 @@ cudaError_t launch_mass_scan(cudaStream_t st, const uint32_t *sorted, const floa
 // values); s_i = 0 gives +inf and fires after every Gaussian with s > 0.
 __global__ void sample_keys_kernel(const float *s, const float *expo, long long n, uint32_t *keys, DevCounters *ctr)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
     if (i == 0) {
         ctr->n_records = (unsigned long long)n;
@@ -47,6 +48,7 @@ __global__ void sample_keys_kernel(const float *s, const float *expo, long long 
 // keys are descending s and s = 0 sorts last.
 __global__ void mass_keys_kernel(const float *s, long long n, uint32_t *keys, DevCounters *ctr)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
     if (i == 0) {
         ctr->n_records = (unsigned long long)n;
@@ -57,12 +59,14 @@ __global__ void mass_keys_kernel(const float *s, long long n, uint32_t *keys, De
 
 __global__ void clear_bits_kernel(uint32_t *bits, long long words)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const long long k = (long long)blockIdx.x * 256 + threadIdx.x;
     if (k < words) bits[k] = 0u;
 }
 
 __global__ void keep_first_kernel(const uint32_t *sorted, long long n, long long k, uint32_t *keep)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const long long j = (long long)blockIdx.x * 256 + threadIdx.x;
     if (j >= n || j >= k) return;
     const uint32_t g = sorted[j];
@@ -72,6 +76,7 @@ __global__ void keep_first_kernel(const uint32_t *sorted, long long n, long long
 __global__ void keep_mass_kernel(const uint32_t *sorted, const float *s, const double *cum, long long n, float mass,
                                  uint32_t *keep)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const long long j = (long long)blockIdx.x * 256 + threadIdx.x;
     if (j >= n) return;
     const uint32_t g = sorted[j];
@@ -158,6 +163,7 @@ __device__ __forceinline__ void write_child(const ScatterArgs &a, long long i, l
 // finds its offset by decoupled look-back and writes them in parent order.
 __global__ void __launch_bounds__(256) model_scatter_kernel(ScatterArgs a)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     __shared__ unsigned s_bid;
     __shared__ unsigned long long s_warp[8];
     __shared__ unsigned long long s_base;
@@ -197,6 +203,7 @@ __global__ void __launch_bounds__(256) model_scatter_kernel(ScatterArgs a)
 // Gaussian are contiguous).
 __global__ void count_views_kernel(const uint32_t *rec_g, const float4 *rd2, const DevCounters *ctr, uint32_t *counts)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const unsigned long long r = (unsigned long long)blockIdx.x * 256 + threadIdx.x;
     const unsigned long long nrec = ctr->n_records;
     if (r >= nrec || (r > 0 && rec_g[r - 1] == rec_g[r])) return;
@@ -219,14 +226,14 @@ cudaError_t launch_prune_sample(gs_workspace *ws, cudaStream_t st, const float *
 {
     const unsigned blocks = (unsigned)((n + 255) / 256);
     const long long words = (n + 31) / 32;
-    sample_keys_kernel<<<blocks, 256, 0, st>>>(s, expo, n, ws->mkey[0], ws->mctr);
+    launch_pdl(sample_keys_kernel, blocks, 256, 0, st, s, expo, n, ws->mkey[0], ws->mctr);
     note_launch();
-    clear_bits_kernel<<<(unsigned)((words + 255) / 256), 256, 0, st>>>(keep, words);
+    launch_pdl(clear_bits_kernel, (unsigned)((words + 255) / 256), 256, 0, st, keep, words);
     note_launch();
     int ob = 0;
     cudaError_t e = sort_model_keys(ws, st, n, ob);
     if (e != cudaSuccess) return e;
-    keep_first_kernel<<<blocks, 256, 0, st>>>(ws->mval[ob], n, k, keep);
+    launch_pdl(keep_first_kernel, blocks, 256, 0, st, ws->mval[ob], n, k, keep);
     note_launch();
     return cudaGetLastError();
 }
@@ -236,9 +243,9 @@ cudaError_t launch_prune_mass(gs_workspace *ws, cudaStream_t st, const float *s,
 {
     const unsigned blocks = (unsigned)((n + 255) / 256);
     const long long words = (n + 31) / 32;
-    mass_keys_kernel<<<blocks, 256, 0, st>>>(s, n, ws->mkey[0], ws->mctr);
+    launch_pdl(mass_keys_kernel, blocks, 256, 0, st, s, n, ws->mkey[0], ws->mctr);
     note_launch();
-    clear_bits_kernel<<<(unsigned)((words + 255) / 256), 256, 0, st>>>(keep, words);
+    launch_pdl(clear_bits_kernel, (unsigned)((words + 255) / 256), 256, 0, st, keep, words);
     note_launch();
     int ob = 0;
     cudaError_t e = sort_model_keys(ws, st, n, ob);
@@ -246,7 +253,7 @@ cudaError_t launch_prune_mass(gs_workspace *ws, cudaStream_t st, const float *s,
     if ((e = launch_mass_scan(st, ws->mval[ob], s, ws->mbsum, ws->mcum, ws->mctr, (unsigned long long)n)) !=
         cudaSuccess)
         return e;
-    keep_mass_kernel<<<blocks, 256, 0, st>>>(ws->mval[ob], s, ws->mcum, n, mass, keep);
+    launch_pdl(keep_mass_kernel, blocks, 256, 0, st, ws->mval[ob], s, ws->mcum, n, mass, keep);
     note_launch();
     return cudaGetLastError();
 }
@@ -260,7 +267,7 @@ cudaError_t launch_model_scatter(gs_workspace *ws, cudaStream_t st, ScatterArgs 
     a.lb_status = ws->mlb;
     a.ctr = ws->mctr;
     if (blocks == 0) return cudaSuccess;
-    model_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(a);
+    launch_pdl(model_scatter_kernel, (unsigned)blocks, 256, 0, st, a);
     note_launch();
     return cudaGetLastError();
 }
@@ -317,7 +324,7 @@ cudaError_t launch_count_views(gs_workspace *ws, cudaStream_t st, uint32_t *coun
 {
     const unsigned blocks = (unsigned)((ws->cap.max_records + 255) / 256);
     if (blocks == 0) return cudaSuccess;
-    count_views_kernel<<<blocks, 256, 0, st>>>(ws->rec_g, ws->rd2, ws->ctr, counts);
+    launch_pdl(count_views_kernel, blocks, 256, 0, st, ws->rec_g, ws->rd2, ws->ctr, counts);
     note_launch();
     return cudaGetLastError();
 }

@@ -53,6 +53,7 @@ static __device__ __align__(256) unsigned char g_vis_scratch[kVisScratchBytes];
 
 __global__ void vis_init_kernel(const float *w, long long n, unsigned char *scratch)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     DevCounters *ctr = reinterpret_cast<DevCounters *>(scratch + kOffCtr);
     uint32_t *keys = reinterpret_cast<uint32_t *>(scratch + kOffKey0);
     const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
@@ -66,6 +67,7 @@ __global__ void vis_init_kernel(const float *w, long long n, unsigned char *scra
 
 __global__ void vis_cull_init_kernel(uint32_t *cull, long long words, long long n)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const long long k = (long long)blockIdx.x * 256 + threadIdx.x;
     if (k >= words) return;
     const long long bits = n - k * 32;
@@ -75,6 +77,7 @@ __global__ void vis_cull_init_kernel(uint32_t *cull, long long words, long long 
 __global__ void vis_apply_kernel(const float *w, long long n, const uint32_t *sorted, const double *cum,
                                  float vis_mass, uint32_t *cull, uint32_t *cvis)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const long long k = (long long)blockIdx.x * 256 + threadIdx.x;
     if (k >= n) return;
     const uint32_t g = sorted[k];
@@ -148,16 +151,16 @@ int gs_visible_set_static(const float *w, int64_t n, float vis_mass, uint32_t *c
     uint32_t *off = reinterpret_cast<uint32_t *>(scratch + kOffOff);
     const unsigned blocks = (unsigned)((n + 255) / 256);
     const long long words = (n + 31) / 32;
-    vis_init_kernel<<<blocks, 256, 0, st>>>(w, n, scratch);
+    launch_pdl(vis_init_kernel, blocks, 256, 0, st, w, n, scratch);
     note_launch();
-    vis_cull_init_kernel<<<(unsigned)((words + 255) / 256), 256, 0, st>>>(cull_out, words, n);
+    launch_pdl(vis_cull_init_kernel, (unsigned)((words + 255) / 256), 256, 0, st, cull_out, words, n);
     note_launch();
     int ob = 0;
     if ((e = launch_radix_sort_scratch(st, keys, vals, &ctr->n_records, (unsigned long long)n, 32, true, status, hist,
                                        off, ctr, ob)) != cudaSuccess ||
         (e = launch_mass_scan(st, vals[ob], w, bsum, cum, ctr, (unsigned long long)n)) != cudaSuccess)
         return vis_fail(GS_ERR_CUDA, "gs_visible_set_static: a kernel launch failed");
-    vis_apply_kernel<<<blocks, 256, 0, st>>>(w, n, vals[ob], cum, vis_mass, cull_out, cvis_accum);
+    launch_pdl(vis_apply_kernel, blocks, 256, 0, st, w, n, vals[ob], cum, vis_mass, cull_out, cvis_accum);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess)
         return vis_fail(GS_ERR_CUDA, "gs_visible_set_static: a kernel launch failed");

@@ -44,6 +44,7 @@ __device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
 __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *img, const float *tgt, int H, int W, Win win,
                                                        float C1, float C2, float4 *F, float *partial)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     __shared__ float2 sxy[kLTH][kLTP];
     __shared__ float2 hb01[kLTH][kLT + 1], hb23[kLTH][kLT + 1];
     __shared__ float hb4[kLTH][kLT + 1];
@@ -155,6 +156,7 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *img, const f
 __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float *img, const float *tgt, int H, int W, Win win,
                                                        const float4 *F, float lambda, int batch, float *dL)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     __shared__ float2 sf01[kLTH][kLTP];
     __shared__ float sf2[kLTH][kLTP];
     __shared__ float2 hb01[kLTH][kLT + 1];
@@ -237,6 +239,7 @@ __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float *img, const f
 __global__ void loss_finalize_kernel(const float *partial, int blocks_per_view, int batch, int H, int W, float lambda,
                                      float *loss_out)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     __shared__ double s_s[256], s_l[256];
     double loss = 0.0;
     for (int b = 0; b < batch; b++) {
@@ -269,12 +272,12 @@ cudaError_t launch_loss(gs_workspace *ws, cudaStream_t st, const float *img, con
     for (int k = 0; k < 11; k++) win.w[k] = (float)(g[k] / sum);
     const dim3 grid((W + kLT - 1) / kLT, (H + kLT - 1) / kLT, B * 3);
     float4 *maps = reinterpret_cast<float4 *>(ws->loss_maps);
-    ssim_fwd_kernel<<<grid, 256, 0, st>>>(img, tgt, H, W, win, 0.01f * 0.01f, 0.03f * 0.03f, maps, ws->loss_partial);
+    launch_pdl(ssim_fwd_kernel, grid, 256, 0, st, img, tgt, H, W, win, 0.01f * 0.01f, 0.03f * 0.03f, maps, ws->loss_partial);
     note_launch();
-    ssim_bwd_kernel<<<grid, 256, 0, st>>>(img, tgt, H, W, win, maps, lambda, B, dL);
+    launch_pdl(ssim_bwd_kernel, grid, 256, 0, st, img, tgt, H, W, win, maps, lambda, B, dL);
     note_launch();
     const int bpv = (int)(grid.x * grid.y * 3);
-    loss_finalize_kernel<<<1, 256, 0, st>>>(ws->loss_partial, bpv, B, H, W, lambda, loss_out);
+    launch_pdl(loss_finalize_kernel, 1, 256, 0, st, ws->loss_partial, bpv, B, H, W, lambda, loss_out);
     note_launch();
     return cudaGetLastError();
 }
@@ -420,6 +423,7 @@ __device__ __forceinline__ void adam_block(const AdamTable &t, int gi, long long
 // gradient, 24 with the compact rows.
 __global__ void __launch_bounds__(256) adam_kernel(AdamTable t)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     int gi = 0;
     while (blockIdx.x >= t.block_start[gi + 1]) gi++;
     const long long base = (long long)(blockIdx.x - t.block_start[gi]) * kAdamBlockElems;
@@ -436,7 +440,7 @@ static cudaError_t run_adam(AdamTable &t, int n_groups, cudaStream_t st)
 {
     for (int k = n_groups; k < GS_MAX_ADAM_GROUPS; k++) t.block_start[k + 1] = t.block_start[k];
     if (t.block_start[n_groups] == 0) return cudaSuccess;
-    adam_kernel<<<t.block_start[n_groups], 256, 0, st>>>(t);
+    launch_pdl(adam_kernel, t.block_start[n_groups], 256, 0, st, t);
     note_launch();
     return cudaGetLastError();
 }
@@ -477,6 +481,7 @@ struct AdamCoefArgs {
 __global__ void adam_coef_kernel(AdamCoefArgs a, int *d_step, float *coef, float *hist, int max_steps,
                                  DevCounters *ctr)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     if (threadIdx.x != 0) return;
     const int t = a.step > 0 ? a.step : *d_step + 1;
     *d_step = t;
@@ -637,6 +642,7 @@ __device__ __forceinline__ void lazy_all_group(const LazyArgs &a, int k, long lo
 
 __global__ void __launch_bounds__(256) lazy_all_elem_kernel(LazyArgs a, long long n)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const int t = *a.d_step;
     lazy_all_group<3>(a, 0, n, t);   // mean
     lazy_all_group<3>(a, 1, n, t);   // log-scale
@@ -649,6 +655,7 @@ __global__ void __launch_bounds__(256) lazy_all_elem_kernel(LazyArgs a, long lon
 // record head j is its Gaussian's first record: its compact gradient row is row j)
 template <int MODE> __global__ void __launch_bounds__(256) lazy_list_elem_kernel(LazyArgs a, LazyItems it)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const int t = *a.d_step;
     const unsigned long long total = lazy_count<MODE>(it) * kGradRow;
     for (unsigned long long e = blockIdx.x * 256ull + threadIdx.x; e < total; e += gridDim.x * 256ull) {
@@ -668,6 +675,7 @@ template <int MODE> __global__ void __launch_bounds__(256) lazy_list_elem_kernel
 // last[i] = t and the drift bounds of Gaussian i from its current moments
 template <int MODE> __global__ void __launch_bounds__(256) lazy_fin_kernel(LazyArgs a, LazyItems it)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const int t = *a.d_step;
     const unsigned long long cnt = lazy_count<MODE>(it);
     for (unsigned long long j = blockIdx.x * 256ull + threadIdx.x; j < cnt; j += gridDim.x * 256ull) {
@@ -733,9 +741,9 @@ template <int MODE>
 static cudaError_t launch_lazy_list(gs_workspace *ws, cudaStream_t st, const LazyArgs &a, unsigned long long cap)
 {
     const LazyItems it = lazy_items(ws, 0);
-    lazy_list_elem_kernel<MODE><<<lazy_grid(ws, cap * kGradRow), 256, 0, st>>>(a, it);
+    launch_pdl(lazy_list_elem_kernel<MODE>, lazy_grid(ws, cap * kGradRow), 256, 0, st, a, it);
     note_launch();
-    lazy_fin_kernel<MODE><<<lazy_grid(ws, cap), 256, 0, st>>>(a, it);
+    launch_pdl(lazy_fin_kernel<MODE>, lazy_grid(ws, cap), 256, 0, st, a, it);
     note_launch();
     return cudaGetLastError();
 }
@@ -750,9 +758,9 @@ cudaError_t launch_lazy_flush(gs_workspace *ws, cudaStream_t st, const gs_gaussi
 {
     if (g.n == 0) return cudaSuccess;
     const LazyArgs a = lazy_args(ws, params_of(g), g.n);
-    lazy_all_elem_kernel<<<lazy_grid(ws, (unsigned long long)g.n * kGradRow), 256, 0, st>>>(a, g.n);
+    launch_pdl(lazy_all_elem_kernel, lazy_grid(ws, (unsigned long long)g.n * kGradRow), 256, 0, st, a, g.n);
     note_launch();
-    lazy_fin_kernel<kLazyAll><<<lazy_grid(ws, (unsigned long long)g.n), 256, 0, st>>>(a, lazy_items(ws, g.n));
+    launch_pdl(lazy_fin_kernel<kLazyAll>, lazy_grid(ws, (unsigned long long)g.n), 256, 0, st, a, lazy_items(ws, g.n));
     note_launch();
     return cudaGetLastError();
 }
@@ -770,7 +778,7 @@ cudaError_t launch_adam_sparse(gs_workspace *ws, cudaStream_t st, const gs_gauss
     AdamCoefArgs ca;
     for (int k = 0; k < 5; k++) ca.lr[k] = lr[k];
     ca.b1 = beta1; ca.b2 = beta2; ca.step = step;
-    adam_coef_kernel<<<1, 32, 0, st>>>(ca, ws->d_adam_step, ws->d_adam_coef, ws->lazy.hist, ws->lazy.max_steps,
+    launch_pdl(adam_coef_kernel, 1, 32, 0, st, ca, ws->d_adam_step, ws->d_adam_coef, ws->lazy.hist, ws->lazy.max_steps,
                                        ws->ctr);
     note_launch();
     if (ws->lazy.enabled) return launch_lazy_adam(ws, st, param, n);

@@ -535,6 +535,7 @@ __device__ __forceinline__ unsigned gate_ranks(const unsigned long long mask[kGa
 __global__ void __launch_bounds__(256, 3) gate_count_kernel(GaussPtrs g, PreOut o, const CamTable *__restrict__ ctp,
                                                             RenderConsts rc, unsigned long long *counts)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     __shared__ GateShared sh;
     unsigned long long mask[kGateItems];
     unsigned bal[kGateItems];
@@ -560,6 +561,7 @@ __global__ void __launch_bounds__(256, 3) gate_count_kernel(GaussPtrs g, PreOut 
 __global__ void __launch_bounds__(1024) gate_scan_kernel(unsigned long long *counts, long long nblocks,
                                                          DevCounters *ctr)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     __shared__ unsigned long long s[1024];
     const long long per = (nblocks + 1023) / 1024;
     const long long b0 = (long long)threadIdx.x * per;
@@ -587,6 +589,7 @@ __global__ void __launch_bounds__(1024) gate_scan_kernel(unsigned long long *cou
 __global__ void __launch_bounds__(256) gate_gather_kernel(PreOut o, const unsigned long long *offsets,
                                                           long long nblocks, const DevCounters *ctr)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const long long b = blockIdx.x;
     const unsigned long long off = offsets[b];
     const unsigned long long end = b + 1 < nblocks ? offsets[b + 1] : ctr->n_candidates;
@@ -604,6 +607,7 @@ __global__ void __launch_bounds__(256) gate_gather_kernel(PreOut o, const unsign
 __global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, const CamTable *__restrict__ ctp,
                                                          RenderConsts rc)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const CamTable &ct = *ctp;
     __shared__ CamInfo s_cams[GS_MAX_CAMERAS];
     __shared__ float s_thr2[kMaxLod + 1];
@@ -747,11 +751,11 @@ cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t 
     if ((e = cudaMemsetAsync(ws->rec_first, 0xff, (size_t)n * sizeof(uint32_t), st)) != cudaSuccess) return e;
     // gate: per-block counts (in lb_status) and candidates (block-strided), the
     // scan of the counts, the gather into one ordered list
-    gate_count_kernel<<<gblocks, 256, 0, st>>>(gp, o, ws->d_cams, ws->rc, ws->lb_status);
+    launch_pdl(gate_count_kernel, gblocks, 256, 0, st, gp, o, ws->d_cams, ws->rc, ws->lb_status);
     note_launch();
-    gate_scan_kernel<<<1, 1024, 0, st>>>(ws->lb_status, (long long)gblocks, ws->ctr);
+    launch_pdl(gate_scan_kernel, 1, 1024, 0, st, ws->lb_status, (long long)gblocks, ws->ctr);
     note_launch();
-    gate_gather_kernel<<<gblocks, 256, 0, st>>>(o, ws->lb_status, (long long)gblocks, ws->ctr);
+    launch_pdl(gate_gather_kernel, gblocks, 256, 0, st, o, ws->lb_status, (long long)gblocks, ws->ctr);
     note_launch();
     if ((e = cudaMemsetAsync(ws->lb_status, 0, (pblocks + 1) * sizeof(unsigned long long), st)) != cudaSuccess)
         return e;
@@ -759,7 +763,7 @@ cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t 
     if (ws->lazy.enabled && (e = launch_lazy_catchup(ws, st, ws->g)) != cudaSuccess) return e;
     // projection: two persistent 256-thread blocks per SM
     const unsigned pgrid = std::min<unsigned>(pblocks, 2u * (unsigned)ws->sm_count);
-    project_kernel<<<pgrid, 256, 0, st>>>(gp, o, ws->d_cams, ws->rc);
+    launch_pdl(project_kernel, pgrid, 256, 0, st, gp, o, ws->d_cams, ws->rc);
     note_launch();
     return cudaGetLastError();
 }
@@ -775,6 +779,7 @@ __global__ void __launch_bounds__(256) reduce_slots_kernel(const uint32_t *drec,
                                                            const uint32_t *tt, const float4 *rd2, const float *slots,
                                                            float *rgrad, const DevCounters *ctr)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const unsigned long long nrec = ctr->n_records, ninst = ctr->n_instances;
     const int lane = threadIdx.x & 31;
     const unsigned long long nwarps = (unsigned long long)gridDim.x * 8;
@@ -808,7 +813,7 @@ cudaError_t launch_reduce_slots(gs_workspace *ws, cudaStream_t st)
     long long blocks = (cap + 7) / 8;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    reduce_slots_kernel<<<(unsigned)blocks, 256, 0, st>>>(ws->dval[ws->depth_buf], ws->inst_off, ws->tt, ws->rd2, ws->slots,
+    launch_pdl(reduce_slots_kernel, (unsigned)blocks, 256, 0, st, ws->dval[ws->depth_buf], ws->inst_off, ws->tt, ws->rd2, ws->slots,
                                                          ws->rgrad, ws->ctr);
     note_launch();
     return cudaGetLastError();
@@ -835,6 +840,7 @@ struct BwdArgs {
 __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, const CamTable *__restrict__ ctp,
                                                              RenderConsts rc)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     __shared__ CamInfo s_cams[GS_MAX_CAMERAS];
     __shared__ float s_red[4];
     stage_cameras(*ctp, s_cams);
@@ -1026,6 +1032,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, const Ca
 __global__ void scale_reg_finalize_kernel(const float *partial, int nblocks, float beta, const DevCounters *ctr,
                                           float *out)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     __shared__ double s[256];
     double acc = 0.0;
     for (int b = threadIdx.x; b < nblocks; b += 256) acc += (double)partial[b];
@@ -1066,12 +1073,12 @@ cudaError_t launch_preprocess_bwd(gs_workspace *ws, cudaStream_t st, const gs_ga
     const bool reduce = beta > 0.f && scale_reg_value && blocks <= ws->red_words;
     a.red_partial = reduce ? ws->red_partial : nullptr;
     a.ctr = ws->ctr;
-    preprocess_bwd_kernel<<<blocks, 128, 0, st>>>(a, ws->d_cams, ws->rc);
+    launch_pdl(preprocess_bwd_kernel, blocks, 128, 0, st, a, ws->d_cams, ws->rc);
     note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (reduce) {
-        scale_reg_finalize_kernel<<<1, 256, 0, st>>>(ws->red_partial, (int)blocks, beta, ws->ctr, scale_reg_value);
+        launch_pdl(scale_reg_finalize_kernel, 1, 256, 0, st, ws->red_partial, (int)blocks, beta, ws->ctr, scale_reg_value);
         note_launch();
         e = cudaGetLastError();
     }

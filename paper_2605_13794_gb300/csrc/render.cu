@@ -230,6 +230,7 @@ __global__ void __launch_bounds__(TileShape<TW, TH>::threads, 768 / TileShape<TW
                       const CamTable *__restrict__ ctp, RenderConsts rc, float *__restrict__ rgb_out,
                       float *__restrict__ T_out, float *__restrict__ T_ws, uint32_t *__restrict__ n_contrib)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     constexpr int kRT = TileShape<TW, TH>::threads;
     __shared__ float4 s0[kRT];
     __shared__ float4 s1[kRT];
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(TileShape<TW, TH>::threads, 768 / TileShape<TW
 
 template <int TW, int TH> static void fwd_launch(gs_workspace *ws, cudaStream_t st, float *rgb, float *T_out)
 {
-    render_fwd_kernel<TW, TH><<<ws->cams.total_tiles, TileShape<TW, TH>::threads, 0, st>>>(
+    launch_pdl(render_fwd_kernel<TW, TH>, ws->cams.total_tiles, TileShape<TW, TH>::threads, 0, st,
         ws->ranges, ws->tval[ws->tile_buf], ws->rd0, ws->rd1, ws->rd2, ws->d_cams, ws->rc, rgb, T_out, ws->T_final,
         ws->n_contrib);
 }
@@ -364,6 +365,7 @@ template <int TW, int TH>
 __global__ void __launch_bounds__(TileShape<TW, TH>::threads, 768 / TileShape<TW, TH>::threads)
     render_fwd_imp_kernel(FwdImpArgs a, const CamTable *__restrict__ ctp, RenderConsts rc)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     constexpr int kRT = TileShape<TW, TH>::threads, kWarps = TileShape<TW, TH>::warps;
     __shared__ float4 s0[kRT];
     __shared__ float4 s1[kRT]; // (D, training opacity (0 when marked), r, g)
@@ -513,10 +515,10 @@ cudaError_t launch_render_fwd_importance(gs_workspace *ws, cudaStream_t st, floa
     const unsigned grid = (unsigned)ws->cams.total_tiles;
     kt_begin(ws, GS_KT_RENDER_FWD, st);
     switch (tile_shape_id(ws->cams.tile_w, ws->cams.tile_h)) {
-    case 0: render_fwd_imp_kernel<16, 16><<<grid, TileShape<16, 16>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
-    case 1: render_fwd_imp_kernel<32, 8><<<grid, TileShape<32, 8>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
-    case 2: render_fwd_imp_kernel<8, 32><<<grid, TileShape<8, 32>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
-    case 3: render_fwd_imp_kernel<32, 16><<<grid, TileShape<32, 16>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
+    case 0: launch_pdl(render_fwd_imp_kernel<16, 16>, grid, TileShape<16, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 1: launch_pdl(render_fwd_imp_kernel<32, 8>, grid, TileShape<32, 8>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 2: launch_pdl(render_fwd_imp_kernel<8, 32>, grid, TileShape<8, 32>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 3: launch_pdl(render_fwd_imp_kernel<32, 16>, grid, TileShape<32, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
     default: return cudaErrorInvalidValue;
     }
     kt_end(ws, GS_KT_RENDER_FWD, st);
@@ -551,6 +553,7 @@ template <int TW, int TH>
 __global__ void __launch_bounds__(TileShape<TW, TH>::threads)
     render_bwd_kernel(BwdRenderArgs a, const CamTable *__restrict__ ctp, RenderConsts rc)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     constexpr int kRT = TileShape<TW, TH>::threads, kWarps = TileShape<TW, TH>::warps;
     __shared__ float4 s0[kBwdBatch];
     __shared__ float4 s1[kBwdBatch];
@@ -727,10 +730,10 @@ cudaError_t launch_render_bwd(gs_workspace *ws, cudaStream_t st, const float *dL
     const unsigned grid = (unsigned)ws->cams.total_tiles;
     kt_begin(ws, GS_KT_RENDER_BWD, st);
     switch (tile_shape_id(ws->cams.tile_w, ws->cams.tile_h)) {
-    case 0: render_bwd_kernel<16, 16><<<grid, TileShape<16, 16>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
-    case 1: render_bwd_kernel<32, 8><<<grid, TileShape<32, 8>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
-    case 2: render_bwd_kernel<8, 32><<<grid, TileShape<8, 32>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
-    case 3: render_bwd_kernel<32, 16><<<grid, TileShape<32, 16>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
+    case 0: launch_pdl(render_bwd_kernel<16, 16>, grid, TileShape<16, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 1: launch_pdl(render_bwd_kernel<32, 8>, grid, TileShape<32, 8>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 2: launch_pdl(render_bwd_kernel<8, 32>, grid, TileShape<8, 32>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 3: launch_pdl(render_bwd_kernel<32, 16>, grid, TileShape<32, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
     default: return cudaErrorInvalidValue;
     }
     kt_end(ws, GS_KT_RENDER_BWD, st);
@@ -753,6 +756,7 @@ template <int TW, int TH>
 __global__ void __launch_bounds__(TileShape<TW, TH>::threads)
     importance_raster_kernel(ImpArgs a, const CamTable *__restrict__ ctp, RenderConsts rc)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     constexpr int kRT = TileShape<TW, TH>::threads, kWarps = TileShape<TW, TH>::warps;
     __shared__ float4 s0[kRT];
     __shared__ float2 s1[kRT];
@@ -846,10 +850,10 @@ cudaError_t launch_importance_raster(gs_workspace *ws, cudaStream_t st)
     const unsigned grid = (unsigned)ws->cams.total_tiles;
     kt_begin(ws, GS_KT_IMPORTANCE, st);
     switch (tile_shape_id(ws->cams.tile_w, ws->cams.tile_h)) {
-    case 0: importance_raster_kernel<16, 16><<<grid, TileShape<16, 16>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
-    case 1: importance_raster_kernel<32, 8><<<grid, TileShape<32, 8>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
-    case 2: importance_raster_kernel<8, 32><<<grid, TileShape<8, 32>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
-    case 3: importance_raster_kernel<32, 16><<<grid, TileShape<32, 16>::threads, 0, st>>>(a, ws->d_cams, ws->rc); break;
+    case 0: launch_pdl(importance_raster_kernel<16, 16>, grid, TileShape<16, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 1: launch_pdl(importance_raster_kernel<32, 8>, grid, TileShape<32, 8>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 2: launch_pdl(importance_raster_kernel<8, 32>, grid, TileShape<8, 32>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 3: launch_pdl(importance_raster_kernel<32, 16>, grid, TileShape<32, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
     default: return cudaErrorInvalidValue;
     }
     kt_end(ws, GS_KT_IMPORTANCE, st);

@@ -22,6 +22,7 @@ __global__ void __launch_bounds__(256) imp_reduce_kernel(const uint32_t *drec, c
                                                          const uint32_t *tt, const float2 *slots, float *imp_w,
                                                          uint32_t *imp_a, const DevCounters *ctr)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const unsigned long long nrec = ctr->n_records, ninst = ctr->n_instances;
     const int lane = threadIdx.x & 31;
     const unsigned long long nwarps = (unsigned long long)gridDim.x * 8;
@@ -64,6 +65,7 @@ struct ImpGaussArgs {
 // Gaussian's records are contiguous).
 __global__ void __launch_bounds__(256) imp_gauss_kernel(ImpGaussArgs a)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const unsigned long long rh = (unsigned long long)blockIdx.x * 256 + threadIdx.x;
     const unsigned long long nrec = a.ctr->n_records;
     if (rh >= nrec || (rh > 0 && a.rec_g[rh - 1] == a.rec_g[rh])) return;
@@ -86,6 +88,7 @@ __global__ void __launch_bounds__(256) imp_gauss_kernel(ImpGaussArgs a)
 // descending w and w = 0 sorts last.
 __global__ void sel_keys_kernel(const float *imp_w, uint32_t *keys, const DevCounters *ctr)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const unsigned long long r = (unsigned long long)blockIdx.x * 256 + threadIdx.x;
     if (r < ctr->n_records) keys[r] = ~__float_as_uint(imp_w[r]);
 }
@@ -93,6 +96,7 @@ __global__ void sel_keys_kernel(const float *imp_w, uint32_t *keys, const DevCou
 __global__ void sel_camkeys_kernel(const uint32_t *vals, const uint16_t *rec_cam, uint32_t *keys,
                                    const DevCounters *ctr)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const unsigned long long k = (unsigned long long)blockIdx.x * 256 + threadIdx.x;
     if (k < ctr->n_records) keys[k] = rec_cam[vals[k]];
 }
@@ -103,6 +107,7 @@ constexpr int kScanTile = 4096;
 __global__ void __launch_bounds__(256) sel_block_sum_kernel(const uint32_t *vals, const float *imp_w, double *bsum,
                                                             const DevCounters *ctr)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     __shared__ double s[256];
     const unsigned long long n = ctr->n_records;
     const unsigned long long base = (unsigned long long)blockIdx.x * kScanTile;
@@ -128,6 +133,7 @@ __global__ void __launch_bounds__(256) sel_block_sum_kernel(const uint32_t *vals
 constexpr int kBScanThreads = 1024;
 __global__ void __launch_bounds__(kBScanThreads) sel_block_scan_kernel(double *bsum, int nblocks)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     __shared__ double s_w[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int per = (nblocks + kBScanThreads - 1) / kBScanThreads;
@@ -160,6 +166,7 @@ __global__ void __launch_bounds__(kBScanThreads) sel_block_scan_kernel(double *b
 __global__ void __launch_bounds__(256) sel_scan_kernel(const uint32_t *vals, const float *imp_w, const double *boff,
                                                        double *cum, const DevCounters *ctr)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     __shared__ double s[256];
     const unsigned long long n = ctr->n_records;
     const unsigned long long base = (unsigned long long)blockIdx.x * kScanTile;
@@ -190,6 +197,7 @@ __global__ void __launch_bounds__(256) sel_scan_kernel(const uint32_t *vals, con
 // Camera segments of the cam-major sorted order.
 __global__ void sel_segments_kernel(const uint32_t *vals, const uint16_t *rec_cam, uint2 *seg, const DevCounters *ctr)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const unsigned long long n = ctr->n_records;
     for (unsigned long long k = (unsigned long long)blockIdx.x * 256 + threadIdx.x; k < n;
          k += (unsigned long long)gridDim.x * 256) {
@@ -207,11 +215,11 @@ cudaError_t launch_mass_scan(cudaStream_t st, const uint32_t *sorted, const floa
 {
     const unsigned sblocks = (unsigned)((cap + kScanTile - 1) / kScanTile);
     if (sblocks == 0) return cudaSuccess;
-    sel_block_sum_kernel<<<sblocks, 256, 0, st>>>(sorted, w, bsum, ctr);
+    launch_pdl(sel_block_sum_kernel, sblocks, 256, 0, st, sorted, w, bsum, ctr);
     note_launch();
-    sel_block_scan_kernel<<<1, kBScanThreads, 0, st>>>(bsum, (int)sblocks);
+    launch_pdl(sel_block_scan_kernel, 1, kBScanThreads, 0, st, bsum, (int)sblocks);
     note_launch();
-    sel_scan_kernel<<<sblocks, 256, 0, st>>>(sorted, w, bsum, cum, ctr);
+    launch_pdl(sel_scan_kernel, sblocks, 256, 0, st, sorted, w, bsum, cum, ctr);
     note_launch();
     return cudaGetLastError();
 }
@@ -232,6 +240,7 @@ struct SelApplyArgs {
 
 __global__ void sel_apply_kernel(SelApplyArgs a)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const unsigned long long n = a.ctr->n_records;
     for (unsigned long long k = (unsigned long long)blockIdx.x * 256 + threadIdx.x; k < n;
          k += (unsigned long long)gridDim.x * 256) {
@@ -254,6 +263,7 @@ __global__ void sel_apply_kernel(SelApplyArgs a)
 // Cull words start at "culled" for every valid bit.
 __global__ void cull_init_kernel(uint32_t *cull, long long words, long long n, int n_cams)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const long long total = words * n_cams;
     for (long long k = (long long)blockIdx.x * 256 + threadIdx.x; k < total; k += (long long)gridDim.x * 256) {
         const long long wi = k % words;
@@ -268,7 +278,7 @@ cudaError_t launch_importance_reduce(gs_workspace *ws, cudaStream_t st)
     const unsigned long long rcap = (unsigned long long)ws->cap.max_records;
     const unsigned blocks = (unsigned)std::max<unsigned long long>(1, std::min<unsigned long long>((rcap + 7) / 8,
                                                                                                     16ull * ws->sm_count));
-    imp_reduce_kernel<<<blocks, 256, 0, st>>>(ws->dval[ws->depth_buf], ws->inst_off, ws->tt,
+    launch_pdl(imp_reduce_kernel, blocks, 256, 0, st, ws->dval[ws->depth_buf], ws->inst_off, ws->tt,
                                               reinterpret_cast<const float2 *>(ws->slots), ws->imp_w, ws->imp_a,
                                               ws->ctr);
     note_launch();
@@ -293,21 +303,21 @@ cudaError_t launch_importance(gs_workspace *ws, cudaStream_t st, float *w, uint3
     if (n > 0) {
         ImpGaussArgs ga{ws->rec_g, ws->rec_cam, ws->imp_w, ws->imp_a, w, a, s_accum, crad, n, ws->rc.eps_score,
                         ws->ctr};
-        imp_gauss_kernel<<<rblocks, 256, 0, st>>>(ga);
+        launch_pdl(imp_gauss_kernel, rblocks, 256, 0, st, ga);
         note_launch();
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (!cull_out && !cvis) return cudaSuccess;
     const long long words = (n + 31) / 32;
     if (cull_out && words > 0) {
-        cull_init_kernel<<<1216, 256, 0, st>>>(cull_out, words, n, ncam);
+        launch_pdl(cull_init_kernel, 1216, 256, 0, st, cull_out, words, n, ncam);
         note_launch();
     }
     // sort records by w descending (stable), then by camera (stable); own
     // buffers, so the depth order stays valid for a later backward
     uint32_t *sk[2] = {ws->selk[0], ws->selk[1]};
     uint32_t *sv[2] = {ws->selv[0], ws->selv[1]};
-    sel_keys_kernel<<<rblocks, 256, 0, st>>>(ws->imp_w, sk[0], ws->ctr);
+    launch_pdl(sel_keys_kernel, rblocks, 256, 0, st, ws->imp_w, sk[0], ws->ctr);
     note_launch();
     int ob = 0;
     const unsigned long long *cnt = &ws->ctr->n_records;
@@ -316,7 +326,7 @@ cudaError_t launch_importance(gs_workspace *ws, cudaStream_t st, float *w, uint3
     if (ncam > 1) {
         uint32_t *k2[2] = {sk[ob ^ 1], sk[ob]};
         uint32_t *v2[2] = {sv[ob], sv[ob ^ 1]};
-        sel_camkeys_kernel<<<rblocks, 256, 0, st>>>(v2[0], ws->rec_cam, k2[0], ws->ctr);
+        launch_pdl(sel_camkeys_kernel, rblocks, 256, 0, st, v2[0], ws->rec_cam, k2[0], ws->ctr);
         note_launch();
         int ob2 = 0;
         if ((e = launch_radix_sort(ws, st, k2, v2, cnt, rcap, 8, false, false, ob2)) != cudaSuccess) return e;
@@ -324,19 +334,19 @@ cudaError_t launch_importance(gs_workspace *ws, cudaStream_t st, float *w, uint3
     }
     const unsigned sblocks = (unsigned)((rcap + kScanTile - 1) / kScanTile);
     double *bsum = reinterpret_cast<double *>(ws->red_partial);
-    sel_block_sum_kernel<<<sblocks, 256, 0, st>>>(sorted, ws->imp_w, bsum, ws->ctr);
+    launch_pdl(sel_block_sum_kernel, sblocks, 256, 0, st, sorted, ws->imp_w, bsum, ws->ctr);
     note_launch();
-    sel_block_scan_kernel<<<1, kBScanThreads, 0, st>>>(bsum, (int)sblocks);
+    launch_pdl(sel_block_scan_kernel, 1, kBScanThreads, 0, st, bsum, (int)sblocks);
     note_launch();
-    sel_scan_kernel<<<sblocks, 256, 0, st>>>(sorted, ws->imp_w, bsum, ws->sel_cum, ws->ctr);
+    launch_pdl(sel_scan_kernel, sblocks, 256, 0, st, sorted, ws->imp_w, bsum, ws->sel_cum, ws->ctr);
     note_launch();
     uint2 *seg = reinterpret_cast<uint2 *>(ws->rx_hist); // 64 uint2 fit in the histogram scratch
     if ((e = cudaMemsetAsync(seg, 0, GS_MAX_CAMERAS * sizeof(uint2), st)) != cudaSuccess) return e;
-    sel_segments_kernel<<<1216, 256, 0, st>>>(sorted, ws->rec_cam, seg, ws->ctr);
+    launch_pdl(sel_segments_kernel, 1216, 256, 0, st, sorted, ws->rec_cam, seg, ws->ctr);
     note_launch();
     SelApplyArgs sa{sorted, ws->rec_g, ws->rec_cam, ws->imp_w, ws->sel_cum, seg, cull_out, cvis, words,
                     ws->rc.vis_mass, ws->ctr};
-    sel_apply_kernel<<<1216, 256, 0, st>>>(sa);
+    launch_pdl(sel_apply_kernel, 1216, 256, 0, st, sa);
     note_launch();
     return cudaGetLastError();
 }

@@ -35,6 +35,7 @@ __device__ __forceinline__ unsigned long long clamp_count(const unsigned long lo
 __global__ void __launch_bounds__(256) radix_hist_kernel(const uint32_t *keys, const unsigned long long *count,
                                                          unsigned long long cap, int passes, uint32_t *hist)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     __shared__ uint32_t h[4][256];
     for (int k = threadIdx.x; k < 4 * 256; k += 256) (&h[0][0])[k] = 0;
     __syncthreads();
@@ -54,6 +55,7 @@ __global__ void __launch_bounds__(256) radix_hist_kernel(const uint32_t *keys, c
 // Exclusive scan of each pass's 256-bucket histogram.
 __global__ void radix_offsets_kernel(const uint32_t *hist, uint32_t *off, int passes)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     __shared__ uint32_t s[256];
     for (int p = 0; p < passes; p++) {
         uint32_t v = hist[p * 256 + threadIdx.x];
@@ -79,6 +81,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
     const uint32_t *__restrict__ bucket_off, uint32_t *status /* ticket at [0], then [blocks][256] */,
     DevCounters *ctr)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     constexpr int kTileKeys = kSortThreads * ITEMS;
     __shared__ uint32_t s_keys[kTileKeys];
     __shared__ uint32_t s_vals[kTileKeys];
@@ -209,10 +212,10 @@ static cudaError_t radix_passes(cudaStream_t st, uint32_t *keys[2], uint32_t *va
         const int dst = src ^ 1;
         if ((e = cudaMemsetAsync(status, 0, (blocks * 256 + 1) * sizeof(uint32_t), st)) != cudaSuccess) return e;
         if (vals_identity && p == 0)
-            radix_pass_kernel<ITEMS, true, true><<<(unsigned)blocks, kSortThreads, 0, st>>>(
+            launch_pdl(radix_pass_kernel<ITEMS, true, true>, (unsigned)blocks, kSortThreads, 0, st,
                 keys[src], vals[src], keys[dst], vals[dst], count, cap, 8 * p, off + 256 * p, status, ctr);
         else
-            radix_pass_kernel<ITEMS, false, true><<<(unsigned)blocks, kSortThreads, 0, st>>>(
+            launch_pdl(radix_pass_kernel<ITEMS, false, true>, (unsigned)blocks, kSortThreads, 0, st,
                 keys[src], vals[src], keys[dst], vals[dst], count, cap, 8 * p, off + 256 * p, status, ctr);
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -239,9 +242,9 @@ cudaError_t launch_radix_sort(gs_workspace *ws, cudaStream_t st, uint32_t *keys[
     if ((e = cudaMemsetAsync(ws->rx_hist, 0, 4 * 256 * sizeof(uint32_t), st)) != cudaSuccess) return e;
     unsigned hblocks = (unsigned)((cap + 255) / 256);
     if (hblocks > 1216) hblocks = 1216;
-    radix_hist_kernel<<<hblocks, 256, 0, st>>>(keys[0], count, cap, passes, ws->rx_hist);
+    launch_pdl(radix_hist_kernel, hblocks, 256, 0, st, keys[0], count, cap, passes, ws->rx_hist);
     note_launch();
-    radix_offsets_kernel<<<1, 256, 0, st>>>(ws->rx_hist, ws->rx_off, passes);
+    launch_pdl(radix_offsets_kernel, 1, 256, 0, st, ws->rx_hist, ws->rx_off, passes);
     note_launch();
     // keys per block: the workspace's tuning, or by size (0): small sorts take
     // small blocks so that enough SMs work on them
@@ -273,9 +276,9 @@ cudaError_t launch_radix_sort_scratch(cudaStream_t st, uint32_t *keys[2], uint32
     if ((e = cudaMemsetAsync(hist, 0, 4 * 256 * sizeof(uint32_t), st)) != cudaSuccess) return e;
     unsigned hblocks = (unsigned)((cap + 255) / 256);
     if (hblocks > 1216) hblocks = 1216;
-    radix_hist_kernel<<<hblocks, 256, 0, st>>>(keys[0], count, cap, passes, hist);
+    launch_pdl(radix_hist_kernel, hblocks, 256, 0, st, keys[0], count, cap, passes, hist);
     note_launch();
-    radix_offsets_kernel<<<1, 256, 0, st>>>(hist, off, passes);
+    launch_pdl(radix_offsets_kernel, 1, 256, 0, st, hist, off, passes);
     note_launch();
     return radix_passes<kSortItems>(st, keys, vals, count, cap, passes, vals_identity, status, off, ctr, out_buf);
 }
@@ -296,6 +299,7 @@ struct EmitArgs {
 
 __global__ void __launch_bounds__(256) emit_kernel(EmitArgs a, const CamTable *__restrict__ ctp)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const CamTable &ct = *ctp;
     __shared__ unsigned s_bid;
     __shared__ unsigned long long s_warp[8];
@@ -371,7 +375,7 @@ cudaError_t launch_emit(gs_workspace *ws, cudaStream_t st)
     a.tt = ws->tt; a.rect = ws->rect; a.rec_cam = ws->rec_cam; a.inst_off = ws->inst_off;
     a.tkey = ws->tkey[0]; a.tval = ws->tval[0];
     a.lb_status = ws->lb_status; a.ctr = ws->ctr; a.max_instances = (unsigned long long)ws->cap.max_instances;
-    emit_kernel<<<blocks, 256, 0, st>>>(a, ws->d_cams);
+    launch_pdl(emit_kernel, blocks, 256, 0, st, a, ws->d_cams);
     note_launch();
     return cudaGetLastError();
 }
@@ -380,6 +384,7 @@ cudaError_t launch_emit(gs_workspace *ws, cudaStream_t st)
 
 __global__ void __launch_bounds__(256) ranges_kernel(const uint32_t *keys, const DevCounters *ctr, uint2 *ranges)
 {
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const unsigned long long n = ctr->n_instances;
     for (unsigned long long s = (unsigned long long)blockIdx.x * 256 + threadIdx.x; s < n;
          s += (unsigned long long)gridDim.x * 256) {
@@ -394,7 +399,7 @@ cudaError_t launch_ranges(gs_workspace *ws, cudaStream_t st)
     cudaError_t e;
     if ((e = cudaMemsetAsync(ws->ranges, 0, (size_t)ws->cams.total_tiles * sizeof(uint2), st)) != cudaSuccess)
         return e;
-    ranges_kernel<<<152 * 8, 256, 0, st>>>(ws->tkey[ws->tile_buf], ws->ctr, ws->ranges);
+    launch_pdl(ranges_kernel, 152 * 8, 256, 0, st, ws->tkey[ws->tile_buf], ws->ctr, ws->ranges);
     note_launch();
     return cudaGetLastError();
 }
