@@ -6,8 +6,9 @@
 //   c^vis_{i,v}: the smallest set of largest w carrying vis_mass of the view's
 //   total w, ties toward the lower Gaussian index; Cull = 1 - c^vis.
 // The selection sorts each view's records by w (descending, stable), takes an
-// FP64 inclusive scan in a fixed (reduce-then-scan) association, and marks
-// every entry whose exclusive prefix is still below vis_mass * total.
+// inclusive scan of w in 64-bit fixed point (32 fractional bits: exact, so
+// the same in any association), and marks every entry whose exclusive prefix
+// is still below vis_mass * total.
 #include <algorithm>
 
 #include "gs_internal.cuh"
@@ -103,19 +104,30 @@ __global__ void sel_camkeys_kernel(const uint32_t *vals, const uint16_t *rec_cam
 
 constexpr int kScanTile = 4096;
 
-// Per-block FP64 sums of w in sorted order (fixed association).
-__global__ void __launch_bounds__(256) sel_block_sum_kernel(const uint32_t *vals, const float *imp_w, double *bsum,
+// The mass of a record in the prefix sums: FP64, or 64-bit fixed point with 32
+// fractional bits (exact and associative; a view's total alpha weight is at
+// most its pixel count, so 64 bits hold every prefix of up to 64 views).
+template <typename M> __device__ __forceinline__ M mass_of(float w);
+template <> __device__ __forceinline__ double mass_of<double>(float w) { return (double)w; }
+template <> __device__ __forceinline__ unsigned long long mass_of<unsigned long long>(float w)
+{
+    return __double2ull_rn((double)w * 4294967296.0);
+}
+
+// Per-block sums of w in sorted order (fixed association).
+template <typename M>
+__global__ void __launch_bounds__(256) sel_block_sum_kernel(const uint32_t *vals, const float *imp_w, M *bsum,
                                                             const DevCounters *ctr)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
-    __shared__ double s[256];
+    __shared__ M s[256];
     const unsigned long long n = ctr->n_records;
     const unsigned long long base = (unsigned long long)blockIdx.x * kScanTile;
-    double acc = 0.0;
+    M acc = 0;
     if (base < n) {
         for (int j = 0; j < kScanTile / 256; j++) {
             const unsigned long long k = base + (unsigned long long)threadIdx.x * (kScanTile / 256) + j;
-            if (k < n) acc += (double)imp_w[vals[k]];
+            if (k < n) acc += mass_of<M>(imp_w[vals[k]]);
         }
     }
     s[threadIdx.x] = acc;
@@ -127,66 +139,67 @@ __global__ void __launch_bounds__(256) sel_block_sum_kernel(const uint32_t *vals
     if (threadIdx.x == 0) bsum[blockIdx.x] = s[0];
 }
 
-// Exclusive scan of the block sums in one block of 1024 threads: each thread
-// a contiguous chunk, then a shuffle scan of the chunk sums per warp and one
-// over the 32 warp totals (a fixed association).
-constexpr int kBScanThreads = 1024;
-__global__ void __launch_bounds__(kBScanThreads) sel_block_scan_kernel(double *bsum, int nblocks)
+// Inclusive scan of x over the block (blockDim.x a multiple of 32, <= 1024):
+// shuffles within the warps, then over the warp totals.  Returns the
+// block-inclusive value; s_w holds 32 scratch entries.
+template <typename M> __device__ __forceinline__ M block_inclusive_scan(M x, M *s_w)
 {
-    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
-    __shared__ double s_w[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int per = (nblocks + kBScanThreads - 1) / kBScanThreads;
-    const int b0 = threadIdx.x * per;
-    double acc = 0.0;
-    for (int b = b0; b < b0 + per && b < nblocks; b++) acc += bsum[b];
-    double x = acc; // inclusive scan over the warp
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const double y = __shfl_up_sync(0xffffffffu, x, d);
+        const M y = __shfl_up_sync(0xffffffffu, x, d);
         if (lane >= d) x += y;
     }
     if (lane == 31) s_w[warp] = x;
     __syncthreads();
     if (warp == 0) {
-        double t = s_w[lane];
+        M t = lane < nw ? s_w[lane] : M(0);
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const double y = __shfl_up_sync(0xffffffffu, t, d);
+            const M y = __shfl_up_sync(0xffffffffu, t, d);
             if (lane >= d) t += y;
         }
-        s_w[lane] = t - s_w[lane]; // exclusive over the warps
+        if (lane < nw) s_w[lane] = t - s_w[lane]; // exclusive over the warps
     }
     __syncthreads();
-    double run = s_w[warp] + (x - acc);
-    for (int b = b0; b < b0 + per && b < nblocks; b++) { const double v = bsum[b]; bsum[b] = run; run += v; }
+    return s_w[warp] + x;
+}
+
+// Exclusive scan of the block sums in one block of 1024 threads: each thread
+// a contiguous chunk, then a shuffle scan of the chunk sums (a fixed
+// association).
+constexpr int kBScanThreads = 1024;
+template <typename M> __global__ void __launch_bounds__(kBScanThreads) sel_block_scan_kernel(M *bsum, int nblocks)
+{
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
+    __shared__ M s_w[32];
+    const int per = (nblocks + kBScanThreads - 1) / kBScanThreads;
+    const int b0 = threadIdx.x * per;
+    M acc = 0;
+    for (int b = b0; b < b0 + per && b < nblocks; b++) acc += bsum[b];
+    M run = block_inclusive_scan<M>(acc, s_w) - acc;
+    for (int b = b0; b < b0 + per && b < nblocks; b++) { const M v = bsum[b]; bsum[b] = run; run += v; }
 }
 
 // Inclusive prefix of w in sorted order: cum[k].
-__global__ void __launch_bounds__(256) sel_scan_kernel(const uint32_t *vals, const float *imp_w, const double *boff,
-                                                       double *cum, const DevCounters *ctr)
+template <typename M>
+__global__ void __launch_bounds__(256) sel_scan_kernel(const uint32_t *vals, const float *imp_w, const M *boff,
+                                                       M *cum, const DevCounters *ctr)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
-    __shared__ double s[256];
+    __shared__ M s_w[32];
     const unsigned long long n = ctr->n_records;
     const unsigned long long base = (unsigned long long)blockIdx.x * kScanTile;
     if (base >= n) return;
     constexpr int per = kScanTile / 256;
-    double v[per];
-    double acc = 0.0;
+    M v[per];
+    M acc = 0;
     for (int j = 0; j < per; j++) {
         const unsigned long long k = base + (unsigned long long)threadIdx.x * per + j;
-        v[j] = k < n ? (double)imp_w[vals[k]] : 0.0;
+        v[j] = k < n ? mass_of<M>(imp_w[vals[k]]) : M(0);
         acc += v[j];
     }
-    s[threadIdx.x] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double run = boff[blockIdx.x];
-        for (int t = 0; t < 256; t++) { const double x = s[t]; s[t] = run; run += x; }
-    }
-    __syncthreads();
-    double run = s[threadIdx.x];
+    M run = boff[blockIdx.x] + block_inclusive_scan<M>(acc, s_w) - acc;
     for (int j = 0; j < per; j++) {
         const unsigned long long k = base + (unsigned long long)threadIdx.x * per + j;
         run += v[j];
@@ -215,11 +228,11 @@ cudaError_t launch_mass_scan(cudaStream_t st, const uint32_t *sorted, const floa
 {
     const unsigned sblocks = (unsigned)((cap + kScanTile - 1) / kScanTile);
     if (sblocks == 0) return cudaSuccess;
-    launch_pdl(sel_block_sum_kernel, sblocks, 256, 0, st, sorted, w, bsum, ctr);
+    launch_pdl(sel_block_sum_kernel<double>, sblocks, 256, 0, st, sorted, w, bsum, ctr);
     note_launch();
-    launch_pdl(sel_block_scan_kernel, 1, kBScanThreads, 0, st, bsum, (int)sblocks);
+    launch_pdl(sel_block_scan_kernel<double>, 1, kBScanThreads, 0, st, bsum, (int)sblocks);
     note_launch();
-    launch_pdl(sel_scan_kernel, sblocks, 256, 0, st, sorted, w, bsum, cum, ctr);
+    launch_pdl(sel_scan_kernel<double>, sblocks, 256, 0, st, sorted, w, bsum, cum, ctr);
     note_launch();
     return cudaGetLastError();
 }
@@ -229,7 +242,7 @@ struct SelApplyArgs {
     const uint32_t *rec_g;
     const uint16_t *rec_cam;
     const float *imp_w;
-    const double *cum;
+    const unsigned long long *cum; // fixed-point inclusive prefix of w (mass_of)
     const uint2 *seg;
     uint32_t *cull_out;
     uint32_t *cvis;
@@ -249,10 +262,10 @@ __global__ void sel_apply_kernel(SelApplyArgs a)
         if (!(w > 0.f)) continue;
         const int c = a.rec_cam[r];
         const uint2 sg = a.seg[c];
-        const double before = sg.x > 0 ? a.cum[sg.x - 1] : 0.0;
-        const double total = a.cum[sg.y - 1] - before;
-        const double excl = (k > 0 ? a.cum[k - 1] : 0.0) - before;
-        if (excl < (double)a.vis_mass * total) {
+        const unsigned long long before = sg.x > 0 ? a.cum[sg.x - 1] : 0ull;
+        const unsigned long long total = a.cum[sg.y - 1] - before;
+        const unsigned long long excl = (k > 0 ? a.cum[k - 1] : 0ull) - before;
+        if ((double)excl < (double)a.vis_mass * (double)total) {
             const uint32_t g = a.rec_g[r];
             if (a.cull_out) atomicAnd(&a.cull_out[(long long)c * a.words + (g >> 5)], ~(1u << (g & 31)));
             if (a.cvis) atomicAdd(&a.cvis[g], 1u);
@@ -333,18 +346,20 @@ cudaError_t launch_importance(gs_workspace *ws, cudaStream_t st, float *w, uint3
         sorted = v2[ob2];
     }
     const unsigned sblocks = (unsigned)((rcap + kScanTile - 1) / kScanTile);
-    double *bsum = reinterpret_cast<double *>(ws->red_partial);
-    launch_pdl(sel_block_sum_kernel, sblocks, 256, 0, st, sorted, ws->imp_w, bsum, ws->ctr);
+    // fixed-point masses: exact sums in any association
+    unsigned long long *bsum = reinterpret_cast<unsigned long long *>(ws->red_partial);
+    unsigned long long *cum = reinterpret_cast<unsigned long long *>(ws->sel_cum);
+    launch_pdl(sel_block_sum_kernel<unsigned long long>, sblocks, 256, 0, st, sorted, ws->imp_w, bsum, ws->ctr);
     note_launch();
-    launch_pdl(sel_block_scan_kernel, 1, kBScanThreads, 0, st, bsum, (int)sblocks);
+    launch_pdl(sel_block_scan_kernel<unsigned long long>, 1, kBScanThreads, 0, st, bsum, (int)sblocks);
     note_launch();
-    launch_pdl(sel_scan_kernel, sblocks, 256, 0, st, sorted, ws->imp_w, bsum, ws->sel_cum, ws->ctr);
+    launch_pdl(sel_scan_kernel<unsigned long long>, sblocks, 256, 0, st, sorted, ws->imp_w, bsum, cum, ws->ctr);
     note_launch();
     uint2 *seg = reinterpret_cast<uint2 *>(ws->rx_hist); // 64 uint2 fit in the histogram scratch
     if ((e = cudaMemsetAsync(seg, 0, GS_MAX_CAMERAS * sizeof(uint2), st)) != cudaSuccess) return e;
     launch_pdl(sel_segments_kernel, 1216, 256, 0, st, sorted, ws->rec_cam, seg, ws->ctr);
     note_launch();
-    SelApplyArgs sa{sorted, ws->rec_g, ws->rec_cam, ws->imp_w, ws->sel_cum, seg, cull_out, cvis, words,
+    SelApplyArgs sa{sorted, ws->rec_g, ws->rec_cam, ws->imp_w, cum, seg, cull_out, cvis, words,
                     ws->rc.vis_mass, ws->ctr};
     launch_pdl(sel_apply_kernel, 1216, 256, 0, st, sa);
     note_launch();
