@@ -74,7 +74,7 @@ def parse():
                          "multi-view graph-captured training loop, the 64-camera mixed-resolution batched "
                          "render and the serving loop")
     ap.add_argument("--tune-cache", default=None, help="autotuner cache file for batch64-city10M")
-    ap.add_argument("--tile", default="16x16", choices=["16x16", "32x8", "8x32", "32x16"],
+    ap.add_argument("--tile", default="16x16", choices=["16x16", "32x8", "8x32", "32x16", "16x8", "8x16"],
                     help="render tile shape of the city5M step")
     ap.add_argument("--dense-adam", action="store_true",
                     help="update every Gaussian every step instead of deferring zero-gradient steps (same results)")

@@ -130,7 +130,7 @@ enum { GS_CULL_OFF = 0, GS_CULL_DROP = 1, GS_CULL_MARK = 2 };
 /* Render parameters; gs_default_params fills the standard values. */
 typedef struct {
     int32_t tile_w;      /* tile width in pixels; tile_w x tile_h is one of 16x16 (GS_TILE, the */
-    int32_t tile_h;      /* 3DGS tiling), 32x8, 8x32, 32x16 */
+    int32_t tile_h;      /* 3DGS tiling), 32x8, 8x32, 32x16, 16x8, 8x16 */
     int32_t lod_enable;  /* distance LOD gate of Eq. 1-2 */
     int32_t lod_Lmax;    /* L_max(t) of Eq. 1 */
     int32_t cull_enable; /* per-view Cull column of Eq. 3: GS_CULL_OFF, GS_CULL_DROP or GS_CULL_MARK */

@@ -1,5 +1,5 @@
 """A small autotuner for the render path: it times every tile shape the
-kernels support (16x16, 32x8, 8x32, 32x16) with both radix-sort chunkings
+kernels support (16x16, 32x8, 8x32, 32x16, 16x8, 8x16) with the radix-sort chunkings
 (1024, 2048 and 4096 keys per block) on the caller's own workload and keeps the
 fastest, cached per workload class (Gaussian count and camera resolutions).
 
@@ -20,7 +20,7 @@ import torch
 
 from . import binding as B
 
-TILE_SHAPES = ((16, 16), (32, 8), (8, 32), (32, 16))
+TILE_SHAPES = ((16, 16), (32, 8), (8, 32), (32, 16), (16, 8), (8, 16))
 SORT_CHUNKS = (1024, 2048, 4096)
 
 

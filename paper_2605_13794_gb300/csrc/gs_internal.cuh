@@ -101,7 +101,8 @@ struct CamTable {
 // Index of a supported tile shape, -1 if unsupported.
 __host__ __device__ inline int tile_shape_id(int tw, int th)
 {
-    return tw == 16 && th == 16 ? 0 : tw == 32 && th == 8 ? 1 : tw == 8 && th == 32 ? 2 : tw == 32 && th == 16 ? 3 : -1;
+    return tw == 16 && th == 16 ? 0 : tw == 32 && th == 8 ? 1 : tw == 8 && th == 32 ? 2 : tw == 32 && th == 16 ? 3
+         : tw == 16 && th == 8 ? 4 : tw == 8 && th == 16 ? 5 : -1;
 }
 
 // Render-time constants (FP32, as the kernels compare them).

@@ -335,6 +335,8 @@ cudaError_t launch_render_fwd(gs_workspace *ws, cudaStream_t st, float *rgb, flo
     case 1: fwd_launch<32, 8>(ws, st, rgb, T_out); break;
     case 2: fwd_launch<8, 32>(ws, st, rgb, T_out); break;
     case 3: fwd_launch<32, 16>(ws, st, rgb, T_out); break;
+    case 4: fwd_launch<16, 8>(ws, st, rgb, T_out); break;
+    case 5: fwd_launch<8, 16>(ws, st, rgb, T_out); break;
     default: return cudaErrorInvalidValue;
     }
     kt_end(ws, GS_KT_RENDER_FWD, st);
@@ -519,6 +521,8 @@ cudaError_t launch_render_fwd_importance(gs_workspace *ws, cudaStream_t st, floa
     case 1: launch_pdl(render_fwd_imp_kernel<32, 8>, grid, TileShape<32, 8>::threads, 0, st, a, ws->d_cams, ws->rc); break;
     case 2: launch_pdl(render_fwd_imp_kernel<8, 32>, grid, TileShape<8, 32>::threads, 0, st, a, ws->d_cams, ws->rc); break;
     case 3: launch_pdl(render_fwd_imp_kernel<32, 16>, grid, TileShape<32, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 4: launch_pdl(render_fwd_imp_kernel<16, 8>, grid, TileShape<16, 8>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 5: launch_pdl(render_fwd_imp_kernel<8, 16>, grid, TileShape<8, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
     default: return cudaErrorInvalidValue;
     }
     kt_end(ws, GS_KT_RENDER_FWD, st);
@@ -734,6 +738,8 @@ cudaError_t launch_render_bwd(gs_workspace *ws, cudaStream_t st, const float *dL
     case 1: launch_pdl(render_bwd_kernel<32, 8>, grid, TileShape<32, 8>::threads, 0, st, a, ws->d_cams, ws->rc); break;
     case 2: launch_pdl(render_bwd_kernel<8, 32>, grid, TileShape<8, 32>::threads, 0, st, a, ws->d_cams, ws->rc); break;
     case 3: launch_pdl(render_bwd_kernel<32, 16>, grid, TileShape<32, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 4: launch_pdl(render_bwd_kernel<16, 8>, grid, TileShape<16, 8>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 5: launch_pdl(render_bwd_kernel<8, 16>, grid, TileShape<8, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
     default: return cudaErrorInvalidValue;
     }
     kt_end(ws, GS_KT_RENDER_BWD, st);
@@ -854,6 +860,8 @@ cudaError_t launch_importance_raster(gs_workspace *ws, cudaStream_t st)
     case 1: launch_pdl(importance_raster_kernel<32, 8>, grid, TileShape<32, 8>::threads, 0, st, a, ws->d_cams, ws->rc); break;
     case 2: launch_pdl(importance_raster_kernel<8, 32>, grid, TileShape<8, 32>::threads, 0, st, a, ws->d_cams, ws->rc); break;
     case 3: launch_pdl(importance_raster_kernel<32, 16>, grid, TileShape<32, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 4: launch_pdl(importance_raster_kernel<16, 8>, grid, TileShape<16, 8>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 5: launch_pdl(importance_raster_kernel<8, 16>, grid, TileShape<8, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
     default: return cudaErrorInvalidValue;
     }
     kt_end(ws, GS_KT_IMPORTANCE, st);

@@ -23,7 +23,7 @@ def _built():
     O.build()
     assert torch.cuda.is_available()
 
-TILE_SHAPES = [(16, 16), (32, 8), (8, 32), (32, 16)]
+TILE_SHAPES = [(16, 16), (32, 8), (8, 32), (32, 16), (16, 8), (8, 16)]
 
 
 def _uneven_cameras():

@@ -254,7 +254,7 @@ def test_bg_colour_enters_through_final_transmittance(oracle_mod):
     np.testing.assert_allclose(f1["image"], f0["image"] + bg[:, None, None] * f0["T"][None], atol=1e-12)
 
 
-TILE_SHAPES = [(16, 16), (32, 8), (8, 32), (32, 16)]
+TILE_SHAPES = [(16, 16), (32, 8), (8, 32), (32, 16), (16, 8), (8, 16)]
 
 
 @pytest.mark.parametrize("tw,th", TILE_SHAPES)
