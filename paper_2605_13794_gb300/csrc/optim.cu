@@ -5,8 +5,9 @@
 // C2 = 0.03^2 and zero padding.  Pass 1 blurs x, y, x^2, y^2, xy over a tile
 // with a 5-pixel halo, forms the SSIM map and the three coefficient maps its
 // gradient needs; pass 2 blurs those maps (the window is symmetric, so the
-// adjoint of the blur is the blur) and assembles dL/dx.  Partial sums are
-// reduced in a fixed order in FP64.
+// adjoint of the blur is the blur) and assembles dL/dx.  The per-tile sums of
+// SSIM and |x - y| are added in 64-bit fixed point (exact, so independent of
+// the order of the blocks).
 #include <algorithm>
 
 #include "gs_internal.cuh"
@@ -42,7 +43,7 @@ __device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
 // grid: (tiles_x, tiles_y, batch * 3).  F: per pixel of each plane the three
 // coefficient maps of the SSIM gradient, (F0, F1, F2, 0).
 __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *img, const float *tgt, int H, int W, Win win,
-                                                       float C1, float C2, float4 *F, float *partial)
+                                                       float C1, float C2, float4 *F, unsigned long long *acc)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     __shared__ float2 sxy[kLTH][kLTP];
@@ -147,9 +148,11 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *img, const f
     if (threadIdx.x == 0) {
         float a = 0.f, b = 0.f;
         for (int w = 0; w < 8; w++) { a += red[0][w]; b += red[1][w]; }
-        const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-        partial[2 * blk] = a;
-        partial[2 * blk + 1] = b;
+        // the view's sums in 64-bit fixed point (24 fractional bits): integer
+        // atomics add exactly, so the totals do not depend on block order
+        const int view = blockIdx.z / 3;
+        atomicAdd(&acc[2 * view], (unsigned long long)__float2ll_rn(a * 16777216.f));
+        atomicAdd(&acc[2 * view + 1], (unsigned long long)__float2ll_rn(b * 16777216.f));
     }
 }
 
@@ -236,31 +239,19 @@ __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float *img, const f
     }
 }
 
-__global__ void loss_finalize_kernel(const float *partial, int blocks_per_view, int batch, int H, int W, float lambda,
-                                     float *loss_out)
+// The loss from the views' fixed-point sums (SSIM, L1), zeroed before the
+// SSIM kernel of the same call.
+__global__ void loss_finalize_kernel(const unsigned long long *acc, int batch, int H, int W, float lambda, float *loss_out)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
-    __shared__ double s_s[256], s_l[256];
+    if (threadIdx.x != 0) return;
+    const double npx = 3.0 * H * W, unit = 1.0 / 16777216.0;
     double loss = 0.0;
     for (int b = 0; b < batch; b++) {
-        double as = 0.0, al = 0.0;
-        for (int k = threadIdx.x; k < blocks_per_view; k += 256) {
-            const long long blk = (long long)b * blocks_per_view + k;
-            as += (double)partial[2 * blk];
-            al += (double)partial[2 * blk + 1];
-        }
-        s_s[threadIdx.x] = as;
-        s_l[threadIdx.x] = al;
-        __syncthreads();
-        for (int o = 128; o > 0; o >>= 1) {
-            if (threadIdx.x < o) { s_s[threadIdx.x] += s_s[threadIdx.x + o]; s_l[threadIdx.x] += s_l[threadIdx.x + o]; }
-            __syncthreads();
-        }
-        const double npx = 3.0 * H * W;
-        loss += ((1.0 - lambda) * s_l[0] / npx + lambda * (1.0 - s_s[0] / npx)) / batch;
-        __syncthreads();
+        const double ssim = (double)(long long)acc[2 * b] * unit, l1 = (double)(long long)acc[2 * b + 1] * unit;
+        loss += ((1.0 - lambda) * l1 / npx + lambda * (1.0 - ssim / npx)) / batch;
     }
-    if (threadIdx.x == 0) *loss_out = (float)loss;
+    *loss_out = (float)loss;
 }
 
 cudaError_t launch_loss(gs_workspace *ws, cudaStream_t st, const float *img, const float *tgt, int B, int H, int W,
@@ -272,12 +263,14 @@ cudaError_t launch_loss(gs_workspace *ws, cudaStream_t st, const float *img, con
     for (int k = 0; k < 11; k++) win.w[k] = (float)(g[k] / sum);
     const dim3 grid((W + kLT - 1) / kLT, (H + kLT - 1) / kLT, B * 3);
     float4 *maps = reinterpret_cast<float4 *>(ws->loss_maps);
-    launch_pdl(ssim_fwd_kernel, grid, 256, 0, st, img, tgt, H, W, win, 0.01f * 0.01f, 0.03f * 0.03f, maps, ws->loss_partial);
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(ws->loss_partial); // [B][2]
+    cudaError_t e = cudaMemsetAsync(acc, 0, 2 * (size_t)B * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    launch_pdl(ssim_fwd_kernel, grid, 256, 0, st, img, tgt, H, W, win, 0.01f * 0.01f, 0.03f * 0.03f, maps, acc);
     note_launch();
     launch_pdl(ssim_bwd_kernel, grid, 256, 0, st, img, tgt, H, W, win, maps, lambda, B, dL);
     note_launch();
-    const int bpv = (int)(grid.x * grid.y * 3);
-    launch_pdl(loss_finalize_kernel, 1, 256, 0, st, ws->loss_partial, bpv, B, H, W, lambda, loss_out);
+    launch_pdl(loss_finalize_kernel, 1, 32, 0, st, acc, B, H, W, lambda, loss_out);
     note_launch();
     return cudaGetLastError();
 }
