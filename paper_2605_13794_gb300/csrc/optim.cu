@@ -523,14 +523,6 @@ struct LazyArgs {
     float b1, b2, eps, drift_factor;
 };
 
-// A Gaussian's 59 parameters in row order:
-// group and element of parameter q of the row (mean 3, log-scale 3, quat 4,
-// opacity 1, SH 48).
-__device__ __forceinline__ void param_slot(int q, int &k, int &e)
-{
-    k = q < 3 ? 0 : q < 6 ? 1 : q < 10 ? 2 : q < 11 ? 3 : 4;
-    e = q - (k == 0 ? 0 : k == 1 ? 3 : k == 2 ? 6 : k == 3 ? 10 : 11);
-}
 
 __device__ __forceinline__ int group_len(int k) { return k == 4 ? 48 : k == 3 ? 1 : k == 2 ? 4 : 3; }
 
@@ -644,24 +636,67 @@ __global__ void __launch_bounds__(256) lazy_all_elem_kernel(LazyArgs a, long lon
     lazy_all_group<48>(a, 4, n, t);  // SH
 }
 
-// the Gaussians of a device list, 59 consecutive threads per Gaussian (a
-// record head j is its Gaussian's first record: its compact gradient row is row j)
-template <int MODE> __global__ void __launch_bounds__(256) lazy_list_elem_kernel(LazyArgs a, LazyItems it)
+// The Gaussians of a device list, 20 consecutive threads per Gaussian, one
+// per unit of its row: the 48 SH coefficients as 12 float4, the quaternion as
+// one float4 (both 16-byte aligned rows), and the 3 + 3 + 1 scalars of mean,
+// log-scale and opacity.  Every component takes exactly lazy_param's steps.
+// A record head j is its Gaussian's first record: its compact gradient row
+// is row j.
+constexpr int kLazyUnits = 20;
+__device__ __forceinline__ void lazy_unit(int u, int &k, int &el, int &row)
+{
+    if (u < 12) { k = 4; el = 4 * u; row = 11 + el; }            // SH, float4
+    else if (u == 12) { k = 2; el = 0; row = 6; }                  // quaternion, float4
+    else if (u < 16) { k = 0; el = u - 13; row = el; }             // mean
+    else if (u < 19) { k = 1; el = u - 16; row = 3 + el; }         // log-scale
+    else { k = 3; el = 0; row = 10; }                              // opacity
+}
+
+template <int MODE> __global__ void __launch_bounds__(256) lazy_list_vec_kernel(LazyArgs a, LazyItems it)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const int t = *a.d_step;
-    const unsigned long long total = lazy_count<MODE>(it) * kGradRow;
+    const unsigned long long total = lazy_count<MODE>(it) * kLazyUnits;
     for (unsigned long long e = blockIdx.x * 256ull + threadIdx.x; e < total; e += gridDim.x * 256ull) {
-        const unsigned long long j = e / kGradRow;
-        const int q = (int)(e - j * kGradRow);
+        const unsigned long long j = e / kLazyUnits;
+        const int u = (int)(e - j * kLazyUnits);
         long long i;
         if (!lazy_item<MODE>(it, j, i)) continue;
         const int from = a.last[i];
         if (from >= t) continue;
-        int k, el;
-        param_slot(q, k, el);
-        const float grad = MODE == kLazyGrad ? it.cgrad[j * kGradRow + q] : 0.f;
-        lazy_param<MODE>(a, k, i * group_len(k) + el, from, t, grad);
+        int k, el, row;
+        lazy_unit(u, k, el, row);
+        const long long idx = i * group_len(k) + el;
+        if (u > 12) { // a scalar
+            const float grad = MODE == kLazyGrad ? it.cgrad[j * kGradRow + row] : 0.f;
+            lazy_param<MODE>(a, k, idx, from, t, grad);
+            continue;
+        }
+        const float4 m4 = *reinterpret_cast<const float4 *>(a.m[k] + idx);
+        const float4 v4 = *reinterpret_cast<const float4 *>(a.v[k] + idx);
+        float mv[4] = {m4.x, m4.y, m4.z, m4.w}, vv[4] = {v4.x, v4.y, v4.z, v4.w};
+        bool zero[4], any = MODE == kLazyGrad;
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            zero[c] = (__float_as_uint(mv[c]) | __float_as_uint(vv[c])) == 0u;
+            any = any || !zero[c];
+        }
+        if (!any) continue; // every component a fixed point
+        const float4 p4 = *reinterpret_cast<const float4 *>(a.p[k] + idx);
+        float pv[4] = {p4.x, p4.y, p4.z, p4.w};
+        const int to = MODE == kLazyGrad ? t - 1 : t;
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            if (!zero[c])
+                for (int s2 = from + 1; s2 <= to; s2++)
+                    adam_one(pv[c], 0.f, mv[c], vv[c], a.b1, a.b2, a.hist[10 * s2 + k], a.hist[10 * s2 + 5 + k], a.eps);
+            if (MODE == kLazyGrad)
+                adam_one(pv[c], it.cgrad[j * kGradRow + row + c], mv[c], vv[c], a.b1, a.b2, a.hist[10 * t + k],
+                         a.hist[10 * t + 5 + k], a.eps);
+        }
+        *reinterpret_cast<float4 *>(a.p[k] + idx) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+        *reinterpret_cast<float4 *>(a.m[k] + idx) = make_float4(mv[0], mv[1], mv[2], mv[3]);
+        *reinterpret_cast<float4 *>(a.v[k] + idx) = make_float4(vv[0], vv[1], vv[2], vv[3]);
     }
 }
 
@@ -734,7 +769,7 @@ template <int MODE>
 static cudaError_t launch_lazy_list(gs_workspace *ws, cudaStream_t st, const LazyArgs &a, unsigned long long cap)
 {
     const LazyItems it = lazy_items(ws, 0);
-    launch_pdl(lazy_list_elem_kernel<MODE>, lazy_grid(ws, cap * kGradRow), 256, 0, st, a, it);
+    launch_pdl(lazy_list_vec_kernel<MODE>, lazy_grid(ws, cap * kLazyUnits), 256, 0, st, a, it);
     note_launch();
     launch_pdl(lazy_fin_kernel<MODE>, lazy_grid(ws, cap), 256, 0, st, a, it);
     note_launch();
