@@ -272,7 +272,7 @@ struct gs_workspace {
     // importance
     float *imp_w;        // [R] per-record alpha-weight
     uint32_t *imp_a;     // [R]
-    double *sel_cum;     // [R] scratch for the FP64 mass scan
+    double *sel_cum;     // [R] scratch for the mass scans (FP64, or fixed point for the selection)
     uint32_t *selk[2], *selv[2]; // [R] selection sort pairs
     // loss scratch: 3 maps of [P][3]
     float *loss_maps;

@@ -2,11 +2,13 @@
 // adjoint, and the instrumented colourless sweep of the importance pass
 // (Sec. 3.2, Fig. 2).
 //
-// One 64-thread block per 16x16 tile; each thread owns a 2x2 pixel quad.  The
-// tile's depth-ordered list is staged through shared memory in batches; every
-// pixel walks the same entry at the same time, so per-Gaussian quantities are
-// block reductions (thread over its quad, warp shuffles, then two warp
-// partials) rather than per-pixel global atomics.  The backward and
+// One block per tile (64 threads for 16x16); each thread owns a 2x2 pixel
+// quad.  The tile's depth-ordered list is staged through shared memory in
+// batches; every pixel walks the same entry at the same time, and a warp skips
+// an entry whose alpha box misses all its pixels.  Per-Gaussian quantities are
+// block reductions (thread over its quad, warp shuffles -- recursive halving
+// for the adjoint's nine values -- then the warps' partials) rather than
+// per-pixel global atomics.  The backward and
 // the importance sweep write one gradient/score slot per (record, tile) --
 // slot index = the record's first instance + the tile's position inside the
 // record's rectangle -- and a later per-record pass sums a record's slots in
