@@ -11,7 +11,15 @@
  *   gs_importance  the instrumented colourless sweep of Sec. 3.2 / Fig. 2:
  *                  w = sum_p alpha T, a = qualifying pixels, s, c^rad, c^vis, Cull
  *   gs_photometric_loss  L1 + lambda (1 - SSIM) of Eq. 4
- *   gs_adam_step   the optimizer step of "standard 3DGS" training
+ *   gs_adam_step   the optimizer step of "standard 3DGS" training (also fused
+ *                  with compact gradient rows, and with deferred zero-gradient
+ *                  steps: gs_adam_lazy_enable / gs_adam_flush)
+ *   gs_render_fwd_importance  the forward and the importance raster in one pass
+ *   gs_prune_sample, gs_prune_mass, gs_compact, gs_densify, gs_count_views
+ *                  the model-level passes of Sec. 3.2-3.3 (pruning Pass 1 and 2,
+ *                  density control with the phi reweighting, LOD inheritance)
+ *   gs_visible_set_static  a view's Cull column without any allocation
+ *   gs_kernel_timing, gs_kernel_time  event timing of the rasterisers
  *
  * Conventions for every call:
  *   - Every pointer argument that names an array is a DEVICE pointer unless the
@@ -27,7 +35,9 @@
  *     gs_workspace_counts; the outputs of the failing step are then
  *     undefined.  The library never aborts, exits or traps.  gs_last_error()
  *     describes the last error of the calling thread.
- *   - Floating point is FP32 throughout.
+ *   - Floating point is FP32: the projected mean is carried as a pair of
+ *     floats (double-float), and the few scalar reductions (loss, importance
+ *     masses) are exact fixed-point or FP64 sums.
  */
 #ifndef GSBLITZ_H
 #define GSBLITZ_H
