@@ -96,6 +96,21 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float d
     dY[15][0] = -C3a * (3.f * xx - 3.f * yy); dY[15][1] = C3a * 6.f * x * y; dY[15][2] = 0.f;
 }
 
+// g = sum_k c_k grad Y_k(x, y, z): the gradients of sh_basis_grad weighted
+// and summed, without materialising the 16 x 3 table.
+__device__ __forceinline__ void sh_grad_dot(float x, float y, float z, const float c[16], float g[3])
+{
+    float dY[16][3];
+    sh_basis_grad(x, y, z, dY);
+    g[0] = g[1] = g[2] = 0.f;
+#pragma unroll
+    for (int k = 1; k < 16; k++) {
+        g[0] = fmaf(c[k], dY[k][0], g[0]);
+        g[1] = fmaf(c[k], dY[k][1], g[1]);
+        g[2] = fmaf(c[k], dY[k][2], g[2]);
+    }
+}
+
 __device__ __forceinline__ float clampf(float x, float lo, float hi) { return x < lo ? lo : (x > hi ? hi : x); }
 
 // Distance LOD gate (Sec. 3.3, Eq. 1-2) in its squared-distance form:
@@ -960,22 +975,29 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, const Ca
                 const float dn = sqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
                 const float idn = 1.f / dn;
                 const float d[3] = {dv[0] * idn, dv[1] * idn, dv[2] * idn};
-                float Y[16], dY[16][3];
+                float Y[16];
                 sh_basis(d[0], d[1], d[2], Y);
-                sh_basis_grad(d[0], d[1], d[2], dY);
                 const uint8_t cm = a.clampm[r];
-                float gd[3] = {0.f, 0.f, 0.f};
-                for (int ch = 0; ch < 3; ch++) {
-                    if (cm & (1u << ch)) continue;
-                    const float gr = grgb[ch];
-                    for (int k = 0; k < 16; k++) {
-                        const float coef = a.g.sh[48 * i + 3 * k + ch];
-                        gsh[3 * k + ch] += gr * Y[k];
-                        gd[0] += gr * coef * dY[k][0];
-                        gd[1] += gr * coef * dY[k][1];
-                        gd[2] += gr * coef * dY[k][2];
+                // dL/dd = sum_k c_k grad Y_k(d) with c_k = sum over unclamped channels of
+                // dL/drgb_ch * sh_k,ch: the 16 weights first, then one gradient sum
+                float ck[16];
+#pragma unroll
+                for (int k = 0; k < 16; k++) ck[k] = 0.f;
+                const float4 *shv = reinterpret_cast<const float4 *>(a.g.sh + 48 * i); // [16][3]
+#pragma unroll
+                for (int v4 = 0; v4 < 12; v4++) {
+                    const float4 c4 = shv[v4];
+                    const float cc[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+                    for (int e2 = 0; e2 < 4; e2++) {
+                        const int flat = 4 * v4 + e2, k = flat / 3, ch = flat % 3;
+                        if (cm & (1u << ch)) continue;
+                        gsh[flat] += grgb[ch] * Y[k];
+                        ck[k] += grgb[ch] * cc[e2];
                     }
                 }
+                float gd[3];
+                sh_grad_dot(d[0], d[1], d[2], ck, gd);
                 const float ddot = d[0] * gd[0] + d[1] * gd[1] + d[2] * gd[2];
                 for (int e = 0; e < 3; e++) gm[e] += (gd[e] - d[e] * ddot) * idn;
             }
