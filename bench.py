@@ -12,9 +12,10 @@ path through the C ABI on resident device data:
   -> L1 + 0.2 D-SSIM loss against a target -> render backward (+ scale
      regulariser) into compact per-Gaussian gradient rows -> Adam over all 59
      parameters of all Gaussians (zero-gradient steps deferred and replayed
-     exactly) -> importance sweep on the same binning, which scores every
-     record as without the Cull column it recomputes (w, a, s, c^rad, c^vis
-     and the next Cull column).
+     exactly); beside them, on a second stream forked after bin_sort, the
+     importance sweep on the same binning, which scores every record as
+     without the Cull column it recomputes (w, a, s, c^rad, c^vis and the next
+     Cull column); the step ends when both streams have.
 
 The timed steps are replays of one CUDA graph of the whole step (captured
 after eager warm-up steps; cameras from the workspace's device table, the Adam
@@ -78,6 +79,9 @@ def parse():
                     help="render tile shape of the city5M step")
     ap.add_argument("--dense-adam", action="store_true",
                     help="update every Gaussian every step instead of deferring zero-gradient steps (same results)")
+    ap.add_argument("--overlap", default="step", choices=["fwd", "step", "late", "off"],
+                    help="city5M: the importance sweep on a second stream beside the forward and loss (fwd), "
+                         "beside the whole training pass (step), or on the one stream (off)")
     return ap.parse_args()
 
 
@@ -158,7 +162,7 @@ def make_host_inputs(n):
 class Step:
     """Device state and the sequence of C-ABI calls of one training step."""
 
-    def __init__(self, g, cam, target, tile=(16, 16), lazy=True):
+    def __init__(self, g, cam, target, tile=(16, 16), lazy=True, overlap="fwd"):
         import torch
         from paper_2605_13794_gb300 import binding as B
         self.B, self.torch = B, torch
@@ -190,6 +194,14 @@ class Step:
         # engaged and never applies the Cull mask it recomputes
         self.params_imp = B.RenderParams(lod_enable=True, cull_enable=False, tile_w=tw, tile_h=th, **LOD)
         self.graph = None
+        # the captured step runs the importance sweep on a second stream, forked after the
+        # binning: "fwd" joins it before the adjoint, "step" at the end of the step, "off"
+        # keeps the single stream (the sweep shares no scratch with the training pass)
+        self.overlap = overlap
+        # both streams at the same priority: a higher one for the training pass was
+        # measured slower (the sweep's raster then runs into the adjoint)
+        self.cap_stream = torch.cuda.Stream()
+        self.side = torch.cuda.Stream() if overlap != "off" else None
         # capacities from a dry run of the importance configuration (no Cull column)
         tiles = B.tiles_of(cam, tw, th)
         probe = B.Workspace(max_gaussians=self.n, max_records=self.n, max_instances=min((1 << 30) - 1, 32 * self.n),
@@ -234,18 +246,25 @@ class Step:
         self.ws.upload_cameras([self.cam], self.params_train)
         torch.cuda.synchronize()
         n0 = self.B.kernel_launches()
-        self.graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.graph):
+        self.graph = self.B.Graph()
+        with self.graph.capture(self.cap_stream):
             self._body(None, uploaded=True)
         torch.cuda.synchronize()
         return self.B.kernel_launches() - n0
 
     def replay(self):
-        self.graph.replay()
+        self.graph.launch()
+
+    def _importance(self, stream=None):
+        # importance sweep of the view on the step's binning; its Cull column gates the next step
+        self.ws.importance(s_accum=self.s, crad=self.crad, cvis=self.cvis, cull_out=self.cull, stream=stream)
 
     def _body(self, ev, uploaded=False):
         B, ws, torch = self.B, self.ws, self.torch
         rec = (lambda k: ev[k].record()) if ev is not None else (lambda k: None)
+        # the eager diagnostic steps (stage events) keep one stream
+        side = self.side if ev is None else None
+        main = torch.cuda.current_stream()
         rec(0)
         if uploaded:
             ws.preprocess_uploaded(self.gt, self.params_train, self.cull)
@@ -254,19 +273,29 @@ class Step:
         rec(1)
         ws.bin_sort()
         rec(2)
+        if side is not None and self.overlap != "late":
+            side.wait_stream(main)
+            self._importance(stream=side)
         ws.render_fwd(self.rgb, self.T)
         rec(3)
+        if side is not None and self.overlap == "late":
+            side.wait_stream(main)
+            self._importance(stream=side)
         ws.photometric_loss(self.rgb.view(1, 3, self.cam.height, self.cam.width), self.target, LAMBDA, self.loss,
                             self.dL)
         rec(4)
+        if side is not None and self.overlap == "fwd":
+            main.wait_stream(side)
         ws.render_bwd_compact(self.gt, self.dL, scale_reg_beta=BETA, scale_reg_value=self.reg)
         rec(5)
         # Adam on all Gaussians with the compact gradients (zero for Gaussians without a
         # record); step 0: one past the workspace's device step counter
         ws.adam_step_compact(self.gt, self.m, self.v, self.lr, 0)
         rec(6)
-        # importance sweep of the view on the step's binning; its Cull column gates the next step
-        ws.importance(s_accum=self.s, crad=self.crad, cvis=self.cvis, cull_out=self.cull)
+        if side is None:
+            self._importance()
+        elif self.overlap in ("step", "late"):
+            main.wait_stream(side)
         rec(7)
 
 
@@ -542,7 +571,8 @@ def main():
     from paper_2605_13794_gb300 import binding as B
     torch.cuda.set_device(local)
     g, cam, target = make_host_inputs(args.n)
-    step = Step(g, cam, target, tile=tuple(int(x) for x in args.tile.split("x")), lazy=not args.dense_adam)
+    step = Step(g, cam, target, tile=tuple(int(x) for x in args.tile.split("x")), lazy=not args.dense_adam,
+                overlap=args.overlap)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         step.run()
@@ -690,6 +720,10 @@ def main():
                        "lod": True, "cull": True, "importance_pass": True,
                        "optimizer": "adam (dense)" if args.dense_adam else "adam, zero-gradient steps deferred (exact)",
                        "l2": "inputs larger than L2 (no flush)", "execution": "CUDA graph of the whole step",
+                       "importance_stream": {"fwd": "second stream beside forward and loss",
+                                             "step": "second stream beside the training pass",
+                                             "late": "second stream beside loss and adjoint",
+                                             "off": "one stream"}[args.overlap],
                        "parallelism": f"replicas{world}"},
             "mgaussian_per_s": gauss,
             "fwd_bwd": fwd_bwd,
@@ -707,6 +741,7 @@ def main():
     if rank == 0:
         print(json.dumps(line), flush=True)
     # the graph names the workspace's buffers and events: release it first
+    step.graph.close()
     step.graph = None
     torch.cuda.synchronize()
     if world > 1:

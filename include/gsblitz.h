@@ -20,6 +20,7 @@
  *                  density control with the phi reweighting, LOD inheritance)
  *   gs_visible_set_static  a view's Cull column without any allocation
  *   gs_kernel_timing, gs_kernel_time  event timing of the rasterisers
+ *   gs_graph_*     capture and replay of a sequence of calls as a CUDA graph
  *
  * Conventions for every call:
  *   - Every pointer argument that names an array is a DEVICE pointer unless the
@@ -328,7 +329,14 @@ int gs_render_bwd_adam(gs_workspace *ws, const gs_gaussians *g, const float *dL_
  * crad_accum[i] += 1 when the Gaussian has a record (in frustum, radius > 0),
  * cvis_accum[i] += 1 when w lies in the view's top vis_mass of w mass.
  * cull_out: [n_cams][ceil(n/32)] written, bit = 1 - c^vis.  Any of the
- * accumulators may be NULL. */
+ * accumulators may be NULL.
+ * Concurrency: gs_importance reads only the binning and the records, and its
+ * scratch (importance slots, selection sort and scans) is its own, so it may
+ * run on a second stream, ordered after gs_bin_sort by an event, while
+ * gs_render_fwd, gs_photometric_loss, gs_render_bwd(_compact),
+ * gs_adam_step(_compact) and gs_render_bwd_adam run on the first.  The next
+ * gs_preprocess, gs_bin_sort or gs_render_fwd_importance on the workspace
+ * must be ordered after it, and cull_out must not be read meanwhile. */
 int gs_importance(gs_workspace *ws, float *w, uint32_t *a, float *s_accum, uint32_t *crad_accum,
                   uint32_t *cvis_accum, uint32_t *cull_out, gs_stream stream);
 
@@ -451,6 +459,24 @@ enum {
 };
 int gs_kernel_timing(gs_workspace *ws, int32_t enable);
 int gs_kernel_time(gs_workspace *ws, int32_t kernel, double *total_ms, int64_t *launches);
+
+/* CUDA graph of a sequence of calls, with per-kernel priorities.
+ * gs_graph_capture_begin starts a thread-local capture on stream (not the
+ * legacy NULL stream); the calls that follow on it, and on streams that join it
+ * through events, are recorded, not run.  gs_graph_capture_end ends the capture
+ * (every joined stream must have been joined back), instantiates the graph and
+ * returns it in *out (host handle owned by the caller; NULL on error).  Every
+ * kernel of this library carries the priority of the stream it was launched
+ * on, and the graph runs each kernel at that priority whatever stream it is
+ * launched into: a step captured on a high-priority stream, with a side sweep
+ * on a low-priority stream, keeps the side sweep out of the critical path's
+ * way.  gs_graph_launch enqueues one run on stream; gs_graph_destroy frees the
+ * graph (NULL is ignored) once its runs have completed. */
+typedef struct gs_graph gs_graph;
+int gs_graph_capture_begin(gs_stream stream);
+int gs_graph_capture_end(gs_stream stream, gs_graph **out);
+int gs_graph_launch(gs_graph *graph, gs_stream stream);
+int gs_graph_destroy(gs_graph *graph);
 
 /* Synchronises the stream and returns the device error word as a status. */
 int gs_sync_status(gs_workspace *ws, gs_stream stream);

@@ -7,6 +7,7 @@ fails loudly: there is no fallback implementation.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import dataclasses
 import os
@@ -32,7 +33,8 @@ EXPORTS = ("gs_default_params", "gs_last_error", "gs_workspace_create", "gs_work
            "gs_visible_set_static", "gs_upload_cameras", "gs_preprocess_uploaded", "gs_workspace_set_sort_chunk",
            "gs_prune_sample", "gs_prune_mass", "gs_compact", "gs_densify", "gs_count_views", "gs_adam_lazy_enable",
            "gs_adam_lazy_disable", "gs_adam_flush", "gs_kernel_timing", "gs_kernel_time",
-           "gs_render_fwd_importance")
+           "gs_render_fwd_importance", "gs_graph_capture_begin", "gs_graph_capture_end", "gs_graph_launch",
+           "gs_graph_destroy")
 
 # Cull modes of RenderParams.cull_enable (include/gsblitz.h)
 GS_CULL_OFF, GS_CULL_DROP, GS_CULL_MARK = 0, 1, 2
@@ -152,6 +154,10 @@ def lib() -> ctypes.CDLL:
         L.gs_workspace_buffer.argtypes = [vp, i32, vp, vp]
         L.gs_kernel_timing.argtypes = [vp, i32]
         L.gs_kernel_time.argtypes = [vp, i32, vp, vp]
+        L.gs_graph_capture_begin.argtypes = [vp]
+        L.gs_graph_capture_end.argtypes = [vp, vp]
+        L.gs_graph_launch.argtypes = [vp, vp]
+        L.gs_graph_destroy.argtypes = [vp]
         for name in EXPORTS:
             if name not in ("gs_default_params", "gs_last_error", "gs_workspace_bytes", "gs_kernel_launches"):
                 getattr(L, name).restype = ctypes.c_int
@@ -513,6 +519,52 @@ def visible_set_static(w, vis_mass, cull_out, cvis_accum=None, stream=None):
     (fixed library scratch, n <= 2^20; see gs_visible_set_static)."""
     _check(lib().gs_visible_set_static(_ptr(w), int(w.numel()), float(vis_mass), _ptr(cull_out), _ptr(cvis_accum),
                                        _stream(stream)))
+
+
+class Graph:
+    """A CUDA graph of library calls (gs_graph_*): kernels keep the priority of
+    the stream they were captured from.
+
+        g = Graph()
+        with g.capture(stream):      # a non-default torch stream
+            ...calls on stream, and on streams that join it...
+        g.launch()
+    """
+
+    def __init__(self):
+        self._g = ctypes.c_void_p(0)
+
+    @contextlib.contextmanager
+    def capture(self, stream):
+        assert stream.cuda_stream != 0, "capture needs a non-default stream"
+        self.close()
+        with torch.cuda.stream(stream):
+            _check(lib().gs_graph_capture_begin(_stream(stream)))
+            ok = False
+            try:
+                yield self
+                ok = True
+            finally:
+                g = ctypes.c_void_p(0)
+                rc = lib().gs_graph_capture_end(_stream(stream), ctypes.byref(g))
+                if ok:
+                    _check(rc)
+                self._g = g
+
+    def launch(self, stream=None):
+        assert self._g.value, "no captured graph"
+        _check(lib().gs_graph_launch(self._g, _stream(stream)))
+
+    def close(self):
+        if self._g.value:
+            _check(lib().gs_graph_destroy(self._g))
+            self._g = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def kernel_launches() -> int:

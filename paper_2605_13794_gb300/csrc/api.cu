@@ -47,7 +47,7 @@ struct Layout {
 
 struct Offsets {
     size_t cand_g, cand_mask, gate_g, gate_mask, rec_first, cgrad, rec_g, rec_cam, rd0, rd1, rd2, rect, tt, inst_off, clampm, rgrad, dkey0, dkey1, dval0, dval1;
-    size_t tkey0, tkey1, tval0, tval1, slots, ranges, n_contrib, T_final, imp_w, imp_a, sel_cum;
+    size_t tkey0, tkey1, tval0, tval1, slots, imp_slots, ranges, n_contrib, T_final, imp_w, imp_a, sel_cum, sel_bsum;
     size_t selk0, selk1, selv0, selv1, loss_maps, loss_partial, lb_status, rx_status, rx_hist, rx_off, red_partial,
         ctr, d_cams, d_adam_step, d_adam_coef;
     size_t mkey0, mkey1, mval0, mval1, mcum, mbsum, mrx_status, mlb, mhist, moff, mctr;
@@ -86,13 +86,15 @@ Offsets plan(const gs_capacity &c)
     o.tkey1 = L.take<uint32_t>(I);
     o.tval0 = L.take<uint32_t>(I);
     o.tval1 = L.take<uint32_t>(I);
-    o.slots = L.take<float>(I * (fwd_only ? 2 : gs::kSlotFloats)); // importance needs (w, a) per instance
+    o.slots = L.take<float>(fwd_only ? 0 : I * gs::kSlotFloats);
+    o.imp_slots = L.take<float2>(I); // importance (w, a) per instance
     o.ranges = L.take<uint2>(T);
     o.n_contrib = L.take<uint32_t>(P);
     o.T_final = L.take<float>(P);
     o.imp_w = L.take<float>(R);
     o.imp_a = L.take<uint32_t>(R);
     o.sel_cum = L.take<double>(R);
+    o.sel_bsum = L.take<unsigned long long>(R / 4096 + 2);
     o.selk0 = L.take<uint32_t>(R);
     o.selk1 = L.take<uint32_t>(R);
     o.selv0 = L.take<uint32_t>(R);
@@ -108,8 +110,7 @@ Offsets plan(const gs_capacity &c)
     o.rx_status = L.take<uint32_t>(o.rx_words);
     o.rx_hist = L.take<uint32_t>(4 * 256);
     o.rx_off = L.take<uint32_t>(4 * 256);
-    const size_t k8 = R / 128 + 2, sel = 2 * (R / 4096 + 2);
-    o.red_words = k8 > sel ? k8 : sel;
+    o.red_words = R / 128 + 2;
     o.red_partial = L.take<float>(o.red_words);
     o.ctr = L.take<gs::DevCounters>(1);
     o.d_cams = L.take<gs::CamTable>(1);
@@ -197,6 +198,11 @@ void gs::kt_end(gs_workspace *ws, int id, cudaStream_t st)
     ws->kt.used[id]++;
 }
 
+struct gs_graph {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
 extern "C" {
 
 int64_t gs_kernel_launches(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
@@ -274,12 +280,14 @@ int gs_workspace_create(const gs_capacity *cap, gs_workspace **out)
     ws->tkey[0] = (uint32_t *)(b + o.tkey0); ws->tkey[1] = (uint32_t *)(b + o.tkey1);
     ws->tval[0] = (uint32_t *)(b + o.tval0); ws->tval[1] = (uint32_t *)(b + o.tval1);
     ws->slots = (float *)(b + o.slots);
+    ws->imp_slots = (float2 *)(b + o.imp_slots);
     ws->ranges = (uint2 *)(b + o.ranges);
     ws->n_contrib = (uint32_t *)(b + o.n_contrib);
     ws->T_final = (float *)(b + o.T_final);
     ws->imp_w = (float *)(b + o.imp_w);
     ws->imp_a = (uint32_t *)(b + o.imp_a);
     ws->sel_cum = (double *)(b + o.sel_cum);
+    ws->sel_bsum = (unsigned long long *)(b + o.sel_bsum);
     ws->selk[0] = (uint32_t *)(b + o.selk0); ws->selk[1] = (uint32_t *)(b + o.selk1);
     ws->selv[0] = (uint32_t *)(b + o.selv0); ws->selv[1] = (uint32_t *)(b + o.selv1);
     ws->loss_maps = (float *)(b + o.loss_maps);
@@ -823,6 +831,54 @@ int gs_count_views(gs_workspace *ws, uint32_t *counts, gs_stream stream)
     if (!ws || !counts) return fail(GS_ERR_INVALID_ARG, "gs_count_views: NULL argument");
     if (!ws->have_preprocess) return fail(GS_ERR_INVALID_ARG, "gs_count_views: no preprocess on this workspace");
     CK(gs::launch_count_views(ws, (cudaStream_t)stream, counts), "gs_count_views");
+    return GS_OK;
+}
+
+int gs_graph_capture_begin(gs_stream stream)
+{
+    if (!stream) return fail(GS_ERR_INVALID_ARG, "gs_graph_capture_begin: the legacy NULL stream cannot be captured");
+    CK(cudaStreamBeginCapture((cudaStream_t)stream, cudaStreamCaptureModeThreadLocal), "gs_graph_capture_begin");
+    return GS_OK;
+}
+
+int gs_graph_capture_end(gs_stream stream, gs_graph **out)
+{
+    if (!out) return fail(GS_ERR_INVALID_ARG, "gs_graph_capture_end: out is NULL");
+    *out = nullptr;
+    if (!stream) return fail(GS_ERR_INVALID_ARG, "gs_graph_capture_end: the legacy NULL stream cannot be captured");
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamEndCapture((cudaStream_t)stream, &g), "gs_graph_capture_end");
+    cudaGraphExec_t x = nullptr;
+    // per-node priorities: each kernel keeps the priority of the stream it was captured from
+    cudaError_t e = cudaGraphInstantiateWithFlags(&x, g, cudaGraphInstantiateFlagUseNodePriority);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(e, "gs_graph_capture_end(instantiate)");
+    }
+    gs_graph *h = new (std::nothrow) gs_graph{g, x};
+    if (!h) {
+        cudaGraphExecDestroy(x);
+        cudaGraphDestroy(g);
+        return fail(GS_ERR_OOM, "host allocation failed");
+    }
+    *out = h;
+    return GS_OK;
+}
+
+int gs_graph_launch(gs_graph *graph, gs_stream stream)
+{
+    if (!graph) return fail(GS_ERR_INVALID_ARG, "gs_graph_launch: NULL graph");
+    CK(cudaGraphLaunch(graph->exec, (cudaStream_t)stream), "gs_graph_launch");
+    return GS_OK;
+}
+
+int gs_graph_destroy(gs_graph *graph)
+{
+    if (!graph) return GS_OK;
+    cudaError_t e1 = cudaGraphExecDestroy(graph->exec), e2 = cudaGraphDestroy(graph->graph);
+    delete graph;
+    CK(e1, "gs_graph_destroy");
+    CK(e2, "gs_graph_destroy");
     return GS_OK;
 }
 

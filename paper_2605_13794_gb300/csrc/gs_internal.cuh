@@ -25,11 +25,19 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute attr;
-    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr.val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = &attr;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
     cfg.numAttrs = 1;
+    // the stream's priority, carried explicitly so that a kernel node captured
+    // from the stream keeps it (graphs instantiated with per-node priorities)
+    int prio = 0;
+    if (cudaStreamGetPriority(st, &prio) == cudaSuccess && prio != 0) {
+        attr[1].id = cudaLaunchAttributePriority;
+        attr[1].val.priority = prio;
+        cfg.numAttrs = 2;
+    }
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
@@ -263,7 +271,9 @@ struct gs_workspace {
     uint32_t *dkey[2], *dval[2];
     // per instance
     uint32_t *tkey[2], *tval[2];
-    float *slots;        // [I][9]
+    float *slots;        // [I][9] adjoint slots (training workspaces only)
+    float2 *imp_slots;   // [I] importance slots (alpha-weight, composited pixels as uint32 bits); a buffer
+                         // of their own, so the importance sweep shares no scratch with the training pass
     // per tile
     uint2 *ranges;       // [T]
     // per pixel
@@ -273,6 +283,7 @@ struct gs_workspace {
     float *imp_w;        // [R] per-record alpha-weight
     uint32_t *imp_a;     // [R]
     double *sel_cum;     // [R] scratch for the mass scans (FP64, or fixed point for the selection)
+    unsigned long long *sel_bsum; // [R / 4096 + 2] block masses of the selection scan
     uint32_t *selk[2], *selv[2]; // [R] selection sort pairs
     // loss scratch: 3 maps of [P][3]
     float *loss_maps;
@@ -285,7 +296,7 @@ struct gs_workspace {
     size_t rx_words;
     uint32_t *rx_hist;   // [4][256]
     uint32_t *rx_off;    // [4][256]
-    float *red_partial;  // [blocks] generic reduction partials
+    float *red_partial;  // [blocks] reduction partials of the adjoint (scale regulariser)
     size_t red_words;
     gs::DevCounters *ctr;
     gs::CamTable *d_cams;  // device copy of the uploaded cameras, read by every kernel

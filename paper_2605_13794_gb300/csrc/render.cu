@@ -362,7 +362,7 @@ struct FwdImpArgs {
     const uint2 *rect;
     float *rgb_out, *T_out, *T_ws;
     uint32_t *n_contrib;
-    float *slots; // [I][2]: importance alpha-weight, composited pixels (uint32 bits)
+    float2 *slots; // [I]: importance alpha-weight, composited pixels (uint32 bits)
 };
 
 template <int TW, int TH>
@@ -479,13 +479,13 @@ __global__ void __launch_bounds__(TileShape<TW, TH>::threads, 768 / TileShape<TW
             uint32_t asum = s_a[0][threadIdx.x];
 #pragma unroll
             for (int w = 1; w < kWarps; w++) { wsum += s_w[w][threadIdx.x]; asum += s_a[w][threadIdx.x]; }
-            reinterpret_cast<float2 *>(a.slots)[s_slot[threadIdx.x]] = make_float2(wsum, __uint_as_float(asum));
+            a.slots[s_slot[threadIdx.x]] = make_float2(wsum, __uint_as_float(asum));
         }
     }
     // entries never reached (every pixel of the tile had stopped in both walks)
     for (int s = b + threadIdx.x; s < end; s += kRT) {
         const unsigned long long slot = slot_of(a.inst_off, a.rect, a.vals[s], tg.tx, tg.ty);
-        reinterpret_cast<float2 *>(a.slots)[slot] = make_float2(0.f, 0.f);
+        a.slots[slot] = make_float2(0.f, 0.f);
     }
     const long long np = (long long)cam.width * cam.height;
     float *img = a.rgb_out + 3 * cam.pix_base;
@@ -515,7 +515,7 @@ cudaError_t launch_render_fwd_importance(gs_workspace *ws, cudaStream_t st, floa
     FwdImpArgs a;
     a.ranges = ws->ranges; a.vals = ws->tval[ws->tile_buf]; a.rd0 = ws->rd0; a.rd1 = ws->rd1; a.rd2 = ws->rd2;
     a.inst_off = ws->inst_off; a.rect = ws->rect; a.rgb_out = rgb; a.T_out = T_out; a.T_ws = ws->T_final;
-    a.n_contrib = ws->n_contrib; a.slots = ws->slots;
+    a.n_contrib = ws->n_contrib; a.slots = ws->imp_slots;
     const unsigned grid = (unsigned)ws->cams.total_tiles;
     kt_begin(ws, GS_KT_RENDER_FWD, st);
     switch (tile_shape_id(ws->cams.tile_w, ws->cams.tile_h)) {
@@ -757,7 +757,7 @@ struct ImpArgs {
     const float4 *rd0, *rd1, *rd2;
     const uint32_t *inst_off;
     const uint2 *rect;
-    float *slots; // [I][2]: alpha-weight (float), composited pixels (uint32 bits)
+    float2 *slots; // [I]: alpha-weight (float), composited pixels (uint32 bits)
 };
 
 template <int TW, int TH>
@@ -839,13 +839,13 @@ __global__ void __launch_bounds__(TileShape<TW, TH>::threads)
             uint32_t asum = s_a[0][threadIdx.x];
 #pragma unroll
             for (int w = 1; w < kWarps; w++) { wsum += s_w[w][threadIdx.x]; asum += s_a[w][threadIdx.x]; }
-            reinterpret_cast<float2 *>(a.slots)[s_slot[threadIdx.x]] = make_float2(wsum, __uint_as_float(asum));
+            a.slots[s_slot[threadIdx.x]] = make_float2(wsum, __uint_as_float(asum));
         }
     }
     // entries never reached (every pixel of the tile had stopped)
     for (int s = b + threadIdx.x; s < end; s += kRT) {
         const unsigned long long slot = slot_of(a.inst_off, a.rect, a.vals[s], tg.tx, tg.ty);
-        reinterpret_cast<float2 *>(a.slots)[slot] = make_float2(0.f, 0.f);
+        a.slots[slot] = make_float2(0.f, 0.f);
     }
 }
 
@@ -854,7 +854,7 @@ cudaError_t launch_importance_raster(gs_workspace *ws, cudaStream_t st)
     if (ws->cams.total_tiles == 0) return cudaSuccess;
     ImpArgs a;
     a.ranges = ws->ranges; a.vals = ws->tval[ws->tile_buf]; a.rd0 = ws->rd0; a.rd1 = ws->rd1; a.rd2 = ws->rd2;
-    a.inst_off = ws->inst_off; a.rect = ws->rect; a.slots = ws->slots;
+    a.inst_off = ws->inst_off; a.rect = ws->rect; a.slots = ws->imp_slots;
     const unsigned grid = (unsigned)ws->cams.total_tiles;
     kt_begin(ws, GS_KT_IMPORTANCE, st);
     switch (tile_shape_id(ws->cams.tile_w, ws->cams.tile_h)) {

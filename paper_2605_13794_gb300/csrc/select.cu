@@ -292,7 +292,7 @@ cudaError_t launch_importance_reduce(gs_workspace *ws, cudaStream_t st)
     const unsigned blocks = (unsigned)std::max<unsigned long long>(1, std::min<unsigned long long>((rcap + 7) / 8,
                                                                                                     16ull * ws->sm_count));
     launch_pdl(imp_reduce_kernel, blocks, 256, 0, st, ws->dval[ws->depth_buf], ws->inst_off, ws->tt,
-                                              reinterpret_cast<const float2 *>(ws->slots), ws->imp_w, ws->imp_a,
+                                              ws->imp_slots, ws->imp_w, ws->imp_a,
                                               ws->ctr);
     note_launch();
     return cudaGetLastError();
@@ -347,7 +347,7 @@ cudaError_t launch_importance(gs_workspace *ws, cudaStream_t st, float *w, uint3
     }
     const unsigned sblocks = (unsigned)((rcap + kScanTile - 1) / kScanTile);
     // fixed-point masses: exact sums in any association
-    unsigned long long *bsum = reinterpret_cast<unsigned long long *>(ws->red_partial);
+    unsigned long long *bsum = ws->sel_bsum;
     unsigned long long *cum = reinterpret_cast<unsigned long long *>(ws->sel_cum);
     launch_pdl(sel_block_sum_kernel<unsigned long long>, sblocks, 256, 0, st, sorted, ws->imp_w, bsum, ws->ctr);
     note_launch();

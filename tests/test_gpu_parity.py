@@ -232,6 +232,95 @@ def test_fused_forward_importance_matches_separate(mode):
         assert np.array_equal(sep[4][k], fus[4][k]), k
 
 
+def test_importance_on_a_second_stream_matches_one_stream():
+    """gs_importance shares no scratch with the training pass: forked onto a
+    second stream after gs_bin_sort, beside gs_render_fwd, gs_photometric_loss,
+    gs_render_bwd_compact and gs_adam_step_compact of the same binning, and
+    captured with them as one graph (torch's, and the library's with per-kernel
+    priorities), three steps (each gated by the previous step's Cull column)
+    give the one-stream results bit for bit."""
+    g = synth.plain_scene(20000, seed=35)
+    cams = [synth.plain_camera(320, 240, 300.0)]
+    cam = cams[0]
+    n, words, npix = g.n, (g.n + 31) // 32, cam.width * cam.height
+    rng = np.random.default_rng(36)
+    target = torch.from_numpy(rng.random((1, 3, cam.height, cam.width), dtype=np.float32)).cuda()
+    P = O.Params(bg=(0.1, 0.2, 0.3))
+    lr = [1e-3, 5e-3, 1e-3, 5e-2, 2.5e-3]
+
+    def run(mode):
+        gt = B.GaussianTensors.from_host(g)
+        m, v = gt.zeros_like(), gt.zeros_like()
+        ws = B.Workspace(**capacity_for(n, cams))
+        side = torch.cuda.Stream() if mode != "one" else None
+        rgb, T, dL = (torch.empty(3 * npix, device="cuda"), torch.empty(npix, device="cuda"),
+                      torch.empty(3 * npix, device="cuda"))
+        loss, reg = torch.zeros(1, device="cuda"), torch.zeros(1, device="cuda")
+        s = torch.zeros(n, device="cuda")
+        crad, cvis = (torch.zeros(n, device="cuda", dtype=torch.int32) for _ in range(2))
+        cull = torch.zeros(words, device="cuda", dtype=torch.int32)
+        ws.preprocess(gt, cams, gpu_params(P), None)
+        ws.bin_sort()
+        ws.importance(cull_out=cull)
+        ws.upload_cameras(cams, gpu_params(P, cull_enable=B.GS_CULL_MARK))
+        losses = []
+
+        def body():
+            main = torch.cuda.current_stream() # the capture stream inside the graph capture
+            ws.preprocess_uploaded(gt, gpu_params(P, cull_enable=B.GS_CULL_MARK), cull)
+            ws.bin_sort()
+            if side is not None:
+                side.wait_stream(main)
+                ws.importance(s_accum=s, crad=crad, cvis=cvis, cull_out=cull, stream=side)
+            ws.render_fwd(rgb, T)
+            ws.photometric_loss(rgb.view(1, 3, cam.height, cam.width), target, 0.2, loss, dL)
+            ws.render_bwd_compact(gt, dL, scale_reg_beta=10.0, scale_reg_value=reg)
+            ws.adam_step_compact(gt, m, v, lr, 0)
+            if side is None:
+                ws.importance(s_accum=s, crad=crad, cvis=cvis, cull_out=cull)
+            else:
+                main.wait_stream(side)
+
+        if mode == "graph":
+            torch.cuda.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                body()
+            torch.cuda.synchronize()
+        elif mode == "gs_graph": # the library's graph, the step on a high-priority stream
+            torch.cuda.synchronize()
+            graph = B.Graph()
+            with graph.capture(torch.cuda.Stream(priority=-1)):
+                body()
+            torch.cuda.synchronize()
+        for _ in range(3):
+            if mode == "graph":
+                graph.replay()
+            elif mode == "gs_graph":
+                graph.launch()
+            else:
+                body()
+            losses.append(loss.clone())
+        torch.cuda.synchronize()
+        ws.sync_status()
+        if mode == "gs_graph":
+            graph.close()
+        out = {f"p_{k}": t.cpu().numpy() for k, t in zip(("mean", "log_scale", "quat", "opacity_logit", "sh"),
+                                                          gt.params())}
+        out.update({f"m_{k}": t for k, t in grads_to_host(m).items()})
+        out.update(rgb=rgb.cpu().numpy(), loss=torch.cat(losses).cpu().numpy(), reg=reg.cpu().numpy(),
+                   s=s.cpu().numpy(), crad=crad.cpu().numpy(), cvis=cvis.cpu().numpy(), cull=cull.cpu().numpy())
+        ws.close()
+        return out
+
+    one = run("one")
+    assert one["crad"].sum() > 0 and one["cvis"].sum() > 0
+    for mode in ("two", "graph", "gs_graph"):
+        other = run(mode)
+        for k in one:
+            assert np.array_equal(one[k], other[k]), (mode, k)
+
+
 class GpuRunLike:
     """The one attribute _importance needs from a GpuRun."""
 
