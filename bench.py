@@ -246,11 +246,20 @@ class Step:
         self.ws.upload_cameras([self.cam], self.params_train)
         torch.cuda.synchronize()
         n0 = self.B.kernel_launches()
-        self.graph = self.B.Graph()
-        with self.graph.capture(self.cap_stream):
-            self._body(None, uploaded=True)
+        self.graph = self.capture_with(self.target)
         torch.cuda.synchronize()
         return self.B.kernel_launches() - n0
+
+    def capture_with(self, target):
+        """A graph of the step whose loss reads the target image from `target`."""
+        saved, self.target = self.target, target
+        graph = self.B.Graph()
+        try:
+            with graph.capture(self.cap_stream):
+                self._body(None, uploaded=True)
+        finally:
+            self.target = saved
+        return graph
 
     def replay(self):
         self.graph.launch()
@@ -640,6 +649,8 @@ def main():
     stage_o = [(torch.empty(1, device="cuda"), torch.empty_like(step.cull)) for _ in range(2)]
     t_ready, t_free = [torch.cuda.Event() for _ in range(2)], [torch.cuda.Event() for _ in range(2)]
     o_ready, o_free = [torch.cuda.Event() for _ in range(2)], [torch.cuda.Event() for _ in range(2)]
+    # one graph of the step per staging buffer: each upload lands where its step reads it
+    e2e_graphs = [step.capture_with(stage_t[b]) for b in range(2)]
     barrier(world)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -651,15 +662,14 @@ def main():
         t_ready[0].record(h2d_stream)
     for k in range(K):
         b, nb = k % 2, (k + 1) % 2
-        stream.wait_event(t_ready[b])
-        step.target.copy_(stage_t[b])
-        t_free[b].record(stream)
-        if k + 1 < K:  # the next step's target, while this step runs
+        if k + 1 < K:  # the next step's target, into the buffer the previous step read
             h2d_stream.wait_event(t_free[nb])
             with torch.cuda.stream(h2d_stream):
                 stage_t[nb].copy_(tgt_host, non_blocking=True)
                 t_ready[nb].record(h2d_stream)
-        step.replay()
+        stream.wait_event(t_ready[b])
+        e2e_graphs[b].launch(stream)
+        t_free[b].record(stream)
         stream.wait_event(o_free[b])
         stage_o[b][0].copy_(step.loss)
         stage_o[b][1].copy_(step.cull)
@@ -740,7 +750,9 @@ def main():
         line["cpu_baseline"] = cpu_baseline(g, cam, target)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    # the graph names the workspace's buffers and events: release it first
+    # the graphs name the workspace's buffers and events: release them first
+    for gr in e2e_graphs:
+        gr.close()
     step.graph.close()
     step.graph = None
     torch.cuda.synchronize()
