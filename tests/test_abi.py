@@ -47,3 +47,18 @@ def test_host_side_argument_checks_without_gpu():
     ws = ctypes.c_void_p()
     assert L.gs_workspace_create(ctypes.byref(bad), ctypes.byref(ws)) == B.GS_ERR_INVALID_ARG
     assert b"2^30" in L.gs_last_error()
+
+
+def test_graph_entry_points_reject_bad_arguments_without_gpu():
+    # the legacy NULL stream cannot be captured; NULL graphs are rejected or ignored
+    from paper_2605_13794_gb300 import binding as B
+    L = B.lib()
+    null = ctypes.c_void_p(0)
+    assert L.gs_graph_capture_begin(null) == B.GS_ERR_INVALID_ARG
+    assert b"legacy NULL stream" in L.gs_last_error()
+    out = ctypes.c_void_p(1)
+    assert L.gs_graph_capture_end(null, ctypes.byref(out)) == B.GS_ERR_INVALID_ARG
+    assert out.value is None
+    assert L.gs_graph_capture_end(null, null) == B.GS_ERR_INVALID_ARG
+    assert L.gs_graph_launch(null, null) == B.GS_ERR_INVALID_ARG
+    assert L.gs_graph_destroy(null) == B.GS_OK
