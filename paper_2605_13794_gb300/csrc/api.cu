@@ -401,7 +401,7 @@ int gs_workspace_set_sort_chunk(gs_workspace *ws, int32_t keys_per_block)
 static int check_tile_shape(const gs_render_params *p, const char *who)
 {
     if (gs::tile_shape_id(p->tile_w, p->tile_h) < 0)
-        return fail(GS_ERR_INVALID_ARG, "%s: tile %dx%d not one of 16x16, 32x8, 8x32, 32x16", who, p->tile_w,
+        return fail(GS_ERR_INVALID_ARG, "%s: tile %dx%d not one of 16x16, 32x8, 8x32, 32x16, 16x8, 8x16", who, p->tile_w,
                     p->tile_h);
     return GS_OK;
 }
