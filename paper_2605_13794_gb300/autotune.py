@@ -65,7 +65,10 @@ class Autotuner:
              backward: bool = True, reps: int = 3) -> Choice:
         """The fastest (tile shape, sort chunk) for preprocess + bin_sort +
         render_fwd (+ the compact backward) of this workload; `ws` must hold
-        max_tiles(cams) tiles.  A cached choice is returned without timing."""
+        max_tiles(cams) tiles.  A shape whose binning needs more records or
+        instances than `ws` holds is skipped (its capacity error cleared), so
+        the choice fits the workspace.  A cached choice is returned without
+        timing."""
         key = workload_key(g.n, cams) + f";bwd={int(backward)}"
         if key in self.cache:
             c = self.cache[key]
@@ -73,9 +76,20 @@ class Autotuner:
         npix = sum(c.width * c.height for c in cams)
         rgb = torch.empty(3 * npix, device="cuda")
         dL = torch.full_like(rgb, 1e-3)
-        trials = {}
+        trials, skipped = {}, []
         for tw, th in TILE_SHAPES:
             p = dataclasses.replace(params, tile_w=tw, tile_h=th)
+            # the binning of this shape must fit the workspace (the sort chunk changes no count)
+            ws.preprocess(g, cams, p, cull)
+            ws.bin_sort()
+            try:
+                ws.sync_status()
+            except B.GSError as e:
+                if e.code != B.GS_ERR_CAPACITY:
+                    raise
+                ws.clear_error()
+                skipped.append(f"{tw}x{th}")
+                continue
             for chunk in SORT_CHUNKS:
                 ws.set_sort_chunk(chunk)
                 times = []
@@ -93,10 +107,12 @@ class Autotuner:
                         times.append(e0.elapsed_time(e1))
                 ws.sync_status()
                 trials[f"{tw}x{th}/{chunk}"] = statistics.median(times)
+        if not trials:
+            raise RuntimeError("autotune: no tile shape fits the workspace's capacity")
         best = min(trials, key=trials.get)
         shape, chunk = best.split("/")
         tw, th = (int(x) for x in shape.split("x"))
-        choice = Choice(tw, th, int(chunk), trials[best], trials)
+        choice = Choice(tw, th, int(chunk), trials[best], dict(trials, skipped=skipped) if skipped else trials)
         self.cache[key] = dataclasses.asdict(choice)
         self._save()
         ws.set_sort_chunk(choice.sort_chunk)
