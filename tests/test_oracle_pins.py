@@ -434,3 +434,56 @@ def test_adam_first_step_closed_form(oracle_mod):
     np.testing.assert_allclose(p1, p - 0.01 * g / (np.abs(g) + 1e-15), rtol=0, atol=1e-15)
     np.testing.assert_allclose(m1, 0.1 * g)
     np.testing.assert_allclose(v1, 0.001 * g * g)
+
+
+def test_ssim_value_against_library_gaussian_filter(oracle_mod):
+    # the local statistics from scipy's Gaussian filter (sigma 1.5, radius 5, zero
+    # padding, one image plane at a time) put into the SSIM index of Wang et al.
+    # (2004); pins the oracle's window, its normalisation and its padding
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(54)
+    x = rng.uniform(0, 1, (3, 19, 23))
+    y = np.clip(x + rng.normal(0, 0.2, x.shape), 0, 1)
+
+    def blur(a):
+        return ndimage.gaussian_filter(a, sigma=(0, 1.5, 1.5), truncate=5 / 1.5, mode="constant", cval=0.0)
+
+    C1, C2 = 0.01 ** 2, 0.03 ** 2
+    mx, my = blur(x), blur(y)
+    vx, vy, cxy = blur(x * x) - mx ** 2, blur(y * y) - my ** 2, blur(x * y) - mx * my
+    ref = ((2 * mx * my + C1) * (2 * cxy + C2) / ((mx ** 2 + my ** 2 + C1) * (vx + vy + C2))).mean()
+    s, _ = oracle_mod.ssim_and_grad(x, y)
+    assert abs(s - ref) < 1e-12
+    assert s < 0.9  # a real difference, not the identity
+
+
+def test_adam_constant_gradient_closed_form(oracle_mod):
+    # with a constant gradient from zero moments the bias-corrected moments are
+    # g and g^2 at every step, so each step moves p by lr * g / (|g| + eps)
+    rng = np.random.default_rng(55)
+    p0 = rng.standard_normal(64)
+    g = rng.standard_normal(64)
+    b1, b2, lr, eps = 0.9, 0.999, 0.01, 1e-15
+    p, m, v = p0, np.zeros(64), np.zeros(64)
+    for t in range(1, 51):
+        p, m, v = oracle_mod.adam_step(p, g, m, v, step=t, lr=lr, beta1=b1, beta2=b2, eps=eps)
+        np.testing.assert_allclose(m, (1 - b1 ** t) * g, rtol=1e-12, atol=0)
+        np.testing.assert_allclose(v, (1 - b2 ** t) * g * g, rtol=1e-12, atol=0)
+        np.testing.assert_allclose(p, p0 - t * lr * g / (np.abs(g) + eps), rtol=0, atol=1e-12)
+
+
+def test_adam_zero_gradient_step_closed_form(oracle_mod):
+    # a gradient step then a zero-gradient step (the step a deferred Gaussian
+    # replays): m = b1 (1 - b1) g, v = b2 (1 - b2) g^2, and the bias-corrected
+    # ratio is (b1 / (1 + b1)) g / sqrt(b2 / (1 + b2)) |g|
+    rng = np.random.default_rng(56)
+    p0 = rng.standard_normal(64)
+    g = rng.standard_normal(64)
+    b1, b2, lr, eps = 0.9, 0.999, 0.01, 1e-15
+    z = np.zeros(64)
+    p1, m1, v1 = oracle_mod.adam_step(p0, g, z, z, step=1, lr=lr, beta1=b1, beta2=b2, eps=eps)
+    p2, m2, v2 = oracle_mod.adam_step(p1, z, m1, v1, step=2, lr=lr, beta1=b1, beta2=b2, eps=eps)
+    np.testing.assert_allclose(m2, b1 * (1 - b1) * g, rtol=1e-12, atol=0)
+    np.testing.assert_allclose(v2, b2 * (1 - b2) * g * g, rtol=1e-12, atol=0)
+    step2 = lr * (b1 / (1 + b1)) * g / (np.sqrt(b2 / (1 + b2)) * np.abs(g) + eps)
+    np.testing.assert_allclose(p2, p1 - step2, rtol=0, atol=1e-12)
