@@ -487,3 +487,20 @@ def test_adam_zero_gradient_step_closed_form(oracle_mod):
     np.testing.assert_allclose(v2, b2 * (1 - b2) * g * g, rtol=1e-12, atol=0)
     step2 = lr * (b1 / (1 + b1)) * g / (np.sqrt(b2 / (1 + b2)) * np.abs(g) + eps)
     np.testing.assert_allclose(p2, p1 - step2, rtol=0, atol=1e-12)
+
+
+def test_photometric_loss_weights_eq4(oracle_mod):
+    # Eq. 4 with lambda = 0.2 on a target offset by a constant c: the L1 term is |c|
+    # exactly, the D-SSIM term is 1 - SSIM; a batch of two copies of the view has
+    # the loss of one view (mean over views)
+    rng = np.random.default_rng(57)
+    x = rng.uniform(0.2, 0.8, (3, 17, 21))
+    c = 0.05
+    y = x + c
+    s, _ = oracle_mod.ssim_and_grad(x, y)
+    L1, _ = oracle_mod.photometric_loss(x[None], y[None], lam=0.2)
+    assert abs(L1 - (0.8 * c + 0.2 * (1.0 - s))) < 1e-12
+    L2, g2 = oracle_mod.photometric_loss(np.stack([x, x]), np.stack([y, y]), lam=0.2)
+    _, g1 = oracle_mod.photometric_loss(x[None], y[None], lam=0.2)
+    assert abs(L2 - L1) < 1e-12
+    np.testing.assert_allclose(g2[0], g1[0] / 2, rtol=1e-12, atol=1e-18)
