@@ -448,6 +448,10 @@ int gs_visible_set_static(const float *w, int64_t n, float vis_mass, uint32_t *c
  * each kernel are recorded.  gs_kernel_time synchronises those events and
  * returns the summed device time (ms) and the number of timed launches of one
  * kernel (of a captured launch: after at least one replay).  Off by default.
+ * gs_kernel_timing's `kernels` selects what is timed: 0 turns timing off,
+ * otherwise a mask of (1 << GS_KT_*) bits (GS_KT_ALL: every kernel); each
+ * event pair between kernels of a captured graph costs the launch overlap of
+ * programmatic dependent launch there, so time only what is read.
  * The events belong to the workspace (created on first use, destroyed with
  * it), so a captured graph stays valid while timing is turned off and on; the
  * pairs are numbered again from the first each time timing is turned on. */
@@ -455,9 +459,10 @@ enum {
     GS_KT_RENDER_FWD = 0, /* gs_render_fwd's compositing kernel */
     GS_KT_RENDER_BWD = 1, /* the compositing adjoint (per (record, tile) slots) */
     GS_KT_IMPORTANCE = 2, /* the importance sweep's rasteriser */
-    GS_KT_COUNT = 3
+    GS_KT_COUNT = 3,
+    GS_KT_ALL = (1 << 3) - 1 /* mask of every timed kernel */
 };
-int gs_kernel_timing(gs_workspace *ws, int32_t enable);
+int gs_kernel_timing(gs_workspace *ws, int32_t kernels);
 int gs_kernel_time(gs_workspace *ws, int32_t kernel, double *total_ms, int64_t *launches);
 
 /* CUDA graph of a sequence of calls, with per-kernel priorities.

@@ -41,6 +41,7 @@ GS_CULL_OFF, GS_CULL_DROP, GS_CULL_MARK = 0, 1, 2
 
 # kernels gs_kernel_timing brackets with events (include/gsblitz.h)
 GS_KT_RENDER_FWD, GS_KT_RENDER_BWD, GS_KT_IMPORTANCE = range(3)
+GS_KT_ALL = (1 << 3) - 1
 
 
 class GSError(RuntimeError):
@@ -470,9 +471,13 @@ class Workspace:
     def sync_status(self, stream=None):
         _check(lib().gs_sync_status(self._ws, _stream(stream)))
 
-    def kernel_timing(self, enable: bool = True):
-        """Turns event timing of the rasterisers' launches on (discarding older records) or off."""
-        _check(lib().gs_kernel_timing(self._ws, int(bool(enable))))
+    def kernel_timing(self, enable: bool = True, kernels=None):
+        """Turns event timing of the rasterisers' launches on (discarding older
+        records) or off; kernels: the GS_KT_* ids to time (default: all)."""
+        mask = 0
+        if enable:
+            mask = GS_KT_ALL if kernels is None else sum(1 << int(k) for k in set(kernels))
+        _check(lib().gs_kernel_timing(self._ws, mask))
 
     def kernel_time(self, kernel: int):
         """(summed device ms, timed launches) of one kernel since timing was turned on."""

@@ -185,7 +185,7 @@ static void kt_record(cudaEvent_t ev, cudaStream_t st)
 
 void gs::kt_begin(gs_workspace *ws, int id, cudaStream_t st)
 {
-    if (!ws->kt.on) return;
+    if (!ws->kt.on || !((ws->kt.mask >> id) & 1u)) return;
     ws->kt.launches[id]++;
     if (ws->kt.used[id] >= gs_workspace::kTimedPairs) return;
     kt_record(ws->kt.ev[id][ws->kt.used[id]][0], st);
@@ -193,7 +193,7 @@ void gs::kt_begin(gs_workspace *ws, int id, cudaStream_t st)
 
 void gs::kt_end(gs_workspace *ws, int id, cudaStream_t st)
 {
-    if (!ws->kt.on || ws->kt.used[id] >= gs_workspace::kTimedPairs) return;
+    if (!ws->kt.on || !((ws->kt.mask >> id) & 1u) || ws->kt.used[id] >= gs_workspace::kTimedPairs) return;
     kt_record(ws->kt.ev[id][ws->kt.used[id]][1], st);
     ws->kt.used[id]++;
 }
@@ -331,9 +331,11 @@ int gs_workspace_create(const gs_capacity *cap, gs_workspace **out)
     return GS_OK;
 }
 
-int gs_kernel_timing(gs_workspace *ws, int32_t enable)
+int gs_kernel_timing(gs_workspace *ws, int32_t kernels)
 {
     if (!ws) return fail(GS_ERR_INVALID_ARG, "gs_kernel_timing: null workspace");
+    if (kernels & ~GS_KT_ALL) return fail(GS_ERR_INVALID_ARG, "gs_kernel_timing: unknown kernel bits 0x%x", kernels);
+    const int enable = kernels != 0;
     // the events live as long as the workspace: a graph captured with timing on
     // holds event nodes that name them
     if (enable && !ws->kt.ev[0][0][0]) {
@@ -351,7 +353,8 @@ int gs_kernel_timing(gs_workspace *ws, int32_t enable)
         ws->kt.used[k] = 0;
         ws->kt.launches[k] = 0;
     }
-    ws->kt.on = enable ? 1 : 0;
+    ws->kt.on = enable;
+    ws->kt.mask = (unsigned)kernels;
     return GS_OK;
 }
 

@@ -346,6 +346,7 @@ struct gs_workspace {
     static constexpr int kTimedPairs = 64;
     struct {
         int on;
+        unsigned mask; // (1 << GS_KT_*) bits of the kernels timed while on
         cudaEvent_t ev[GS_KT_COUNT][kTimedPairs][2];
         int used[GS_KT_COUNT];
         long long launches[GS_KT_COUNT]; // launches while on, recorded or not

@@ -399,6 +399,14 @@ def test_backward_fragment_counts_and_kernel_timing():
     assert c["fragments"] == 2 * int(run.n_contrib.astype(np.int64).sum())
     comp = c["composited"] // 2
     assert c["composited"] % 2 == 0
+    # a selection of kernels: the backward is not timed when only the forward is
+    run.ws.kernel_timing(True, kernels=[B.GS_KT_RENDER_FWD])
+    _backward(run, dL)
+    assert run.ws.kernel_time(B.GS_KT_RENDER_BWD) == (0.0, 0)
+    run.ws.kernel_timing(True, kernels=[B.GS_KT_RENDER_BWD])
+    _backward(run, dL)
+    assert run.ws.kernel_time(B.GS_KT_RENDER_BWD)[1] == 1
+    run.ws.kernel_timing(False)
     assert comp <= c["fragments"] // 2
     ref = int(round(fwd["a"].sum()))
     assert abs(comp - ref) <= int(fwd["gcount"].sum()) + 0, (comp, ref)
