@@ -29,6 +29,9 @@
  *   - Calls are asynchronous on the given stream and allocate nothing: all
  *     scratch lives in a gs_workspace created once by gs_workspace_create.
  *     A NULL stream means the legacy default stream.
+ *   - A workspace is not thread-safe on the host: the calls on one workspace
+ *     are issued from one thread at a time (their GPU work may still overlap
+ *     where a call says so, as gs_importance on a second stream).
  *   - Every call returns a gs_status.  Argument errors are reported at once.
  *     Errors found by kernels (capacity overflow, a bounded wait that gave up)
  *     are recorded in the workspace's device error word, returned by the next
