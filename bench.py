@@ -212,7 +212,8 @@ class Step:
         probe.close()
         del probe
         # headroom for the training itself: the Gaussians' footprints drift over the steps
-        # (measured: 1.25x the initial instances after ~200 steps against the noise target)
+        # (measured against the noise target: 1.25x the initial instances after ~210 steps,
+        # 1.66x after ~420)
         self.inst_cap = min((1 << 30) - 1, int(c["instances_needed"] * 2.5) + 4096)
         self.rec_cap = min(self.n, int(c["records_needed"] * 1.5) + 4096)
         self.ws = B.Workspace(max_gaussians=self.n, max_records=self.rec_cap, max_instances=self.inst_cap,
