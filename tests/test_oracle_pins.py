@@ -504,3 +504,24 @@ def test_photometric_loss_weights_eq4(oracle_mod):
     _, g1 = oracle_mod.photometric_loss(x[None], y[None], lam=0.2)
     assert abs(L2 - L1) < 1e-12
     np.testing.assert_allclose(g2[0], g1[0] / 2, rtol=1e-12, atol=1e-18)
+
+
+def test_importance_accumulation_by_hand(oracle_mod):
+    # Sec. 3.2 over two views of four Gaussians, worked by hand: s += w / (a + eps)
+    # where a > 0, c^rad counts the views in which the Gaussian has a record, and
+    # c^vis the views in whose top 99 % of w mass it lies
+    O = oracle_mod
+    acc = O.new_importance(4)
+    st = lambda *v: {"status": np.array(v)}
+    # view 1: w = (6, 3, 1, 0), masses 6, 9, 10 of 10: the 99 % cut needs all three
+    v1 = O.importance_update(acc, [6.0, 3.0, 1.0, 0.0], [3, 2, 1, 0],
+                             st(O.ACTIVE, O.ACTIVE, O.ACTIVE, O.GATED_LOD), eps=0.0)
+    # view 2: w = (0, 200, 1, 0.5): 200 of 201.5 is 99.26 % >= 99 %, so only Gaussian 1
+    v2 = O.importance_update(acc, [0.0, 200.0, 1.0, 0.5], [0, 8, 2, 1],
+                             st(O.NEAR, O.ACTIVE, O.ACTIVE, O.ACTIVE), eps=0.0)
+    np.testing.assert_array_equal(v1["cvis"], [True, True, True, False])
+    np.testing.assert_array_equal(v2["cvis"], [False, True, False, False])
+    np.testing.assert_array_equal(v2["cull"], [True, False, True, True])
+    np.testing.assert_allclose(acc["s"], [6 / 3, 3 / 2 + 200 / 8, 1 / 1 + 1 / 2, 0.5 / 1], rtol=1e-15)
+    np.testing.assert_array_equal(acc["crad"], [1, 2, 2, 1])
+    np.testing.assert_array_equal(acc["cvis"], [1, 2, 1, 0])
