@@ -525,3 +525,33 @@ def test_importance_accumulation_by_hand(oracle_mod):
     np.testing.assert_allclose(acc["s"], [6 / 3, 3 / 2 + 200 / 8, 1 / 1 + 1 / 2, 0.5 / 1], rtol=1e-15)
     np.testing.assert_array_equal(acc["crad"], [1, 2, 2, 1])
     np.testing.assert_array_equal(acc["cvis"], [1, 2, 1, 0])
+
+
+def test_rotated_anisotropic_on_axis_closed_form(oracle_mod):
+    # a needle rotated by 40 degrees about the optical axis, on the axis: the
+    # screen covariance is (f/z)^2 R2 diag(s1^2, s2^2) R2^T + 0.3 I with R2 the
+    # in-plane rotation, whose angle comes from the quaternion's half-angle
+    # identities; its major axis turns from +u toward +v, so the covariance of
+    # (u, v) is positive and the conic's B negative
+    cam = synth.plain_camera(64, 64, 300.0)
+    P = oracle_mod.Params()
+    z = 3.0
+    half = math.radians(20.0)
+    q = [math.cos(half), 0.0, 0.0, math.sin(half)]
+    ls = [math.log(0.02), math.log(0.005), math.log(0.001)]
+    g = _one([0.0, 0.0, z], ls, q, 0.8)
+    pr = oracle_mod.project(oracle_mod.gaussians64(g), cam, P)
+    qf = np.array(q, np.float32).astype(np.float64)
+    qf /= np.linalg.norm(qf)
+    c, s = qf[0] ** 2 - qf[3] ** 2, 2.0 * qf[0] * qf[3]
+    s1, s2 = (math.exp(float(np.float32(v))) for v in ls[:2])
+    k = (float(np.float32(300.0)) / z) ** 2
+    dil = float(np.float32(0.3))
+    a = k * (s1 * s1 * c * c + s2 * s2 * s * s) + dil
+    b = k * (s1 * s1 - s2 * s2) * s * c
+    cc = k * (s1 * s1 * s * s + s2 * s2 * c * c) + dil
+    det = a * cc - b * b
+    assert pr["status"][0] == oracle_mod.ACTIVE
+    np.testing.assert_allclose(pr["conic"][0], [cc / det, -b / det, a / det], rtol=1e-10, atol=0)
+    assert b > 0 and pr["conic"][0][1] < 0
+    np.testing.assert_allclose(pr["uv"][0], [32.0, 32.0])
