@@ -555,3 +555,23 @@ def test_rotated_anisotropic_on_axis_closed_form(oracle_mod):
     np.testing.assert_allclose(pr["conic"][0], [cc / det, -b / det, a / det], rtol=1e-10, atol=0)
     assert b > 0 and pr["conic"][0][1] < 0
     np.testing.assert_allclose(pr["uv"][0], [32.0, 32.0])
+
+
+def test_isotropic_off_axis_jacobian_term(oracle_mod):
+    # an isotropic Gaussian off the axis at (x, 0, z), inside the Jacobian's
+    # clamp: J = (f/z) [[1, 0, -x/z], [0, 1, 0]] stretches the u variance by
+    # 1 + (x/z)^2 and leaves v and the covariance as they are
+    cam = synth.plain_camera(64, 64, 300.0)
+    P = oracle_mod.Params()
+    sigma = 0.02
+    g = _one([0.3, 0.0, 3.0], [math.log(sigma)] * 3, [1.0, 0.0, 0.0, 0.0], 0.8)
+    pr = oracle_mod.project(oracle_mod.gaussians64(g), cam, P)
+    x, z = float(np.float32(0.3)), 3.0
+    f = float(np.float32(300.0))
+    s = math.exp(float(np.float32(math.log(sigma))))
+    dil = float(np.float32(0.3))
+    a = (f * s / z) ** 2 * (1.0 + (x / z) ** 2) + dil
+    c = (f * s / z) ** 2 + dil
+    assert pr["status"][0] == oracle_mod.ACTIVE
+    np.testing.assert_allclose(pr["conic"][0], [1.0 / a, 0.0, 1.0 / c], rtol=1e-10, atol=1e-15)
+    np.testing.assert_allclose(pr["uv"][0], [f * x / z + 32.0, 32.0], rtol=1e-12)
