@@ -575,3 +575,22 @@ def test_isotropic_off_axis_jacobian_term(oracle_mod):
     assert pr["status"][0] == oracle_mod.ACTIVE
     np.testing.assert_allclose(pr["conic"][0], [1.0 / a, 0.0, 1.0 / c], rtol=1e-10, atol=1e-15)
     np.testing.assert_allclose(pr["uv"][0], [f * x / z + 32.0, 32.0], rtol=1e-12)
+
+
+def test_jacobian_clamp_beyond_the_field_of_view(oracle_mod):
+    # past 1.3 tan(fov/2) the Jacobian takes the clamped ratio (the mean does
+    # not): a wide Gaussian at x/z = 0.2 whose footprint reaches back into a
+    # 64-pixel image with f = 300 (limit 1.3 * 32 / 300)
+    cam = synth.plain_camera(64, 64, 300.0)
+    P = oracle_mod.Params()
+    sigma = 0.2
+    g = _one([0.6, 0.0, 3.0], [math.log(sigma)] * 3, [1.0, 0.0, 0.0, 0.0], 0.8)
+    pr = oracle_mod.project(oracle_mod.gaussians64(g), cam, P)
+    f = float(np.float32(300.0))
+    s = math.exp(float(np.float32(math.log(sigma))))
+    lim = 1.3 * 32.0 / f
+    a = (f * s / 3.0) ** 2 * (1.0 + lim * lim) + 0.3
+    c = (f * s / 3.0) ** 2 + 0.3
+    assert pr["status"][0] == oracle_mod.ACTIVE
+    np.testing.assert_allclose(pr["conic"][0], [1.0 / a, 0.0, 1.0 / c], rtol=1e-6, atol=1e-12)
+    assert pr["uv"][0][0] > 64.0  # the mean itself is off the image
