@@ -594,3 +594,15 @@ def test_jacobian_clamp_beyond_the_field_of_view(oracle_mod):
     assert pr["status"][0] == oracle_mod.ACTIVE
     np.testing.assert_allclose(pr["conic"][0], [1.0 / a, 0.0, 1.0 / c], rtol=1e-6, atol=1e-12)
     assert pr["uv"][0][0] > 64.0  # the mean itself is off the image
+
+
+def test_stop_before_the_fragment_that_would_pass_t_min(oracle_mod):
+    # four layers of alpha 0.95 at the pixel centre: T runs 1, 0.05, 0.0025,
+    # 1.25e-4; the fourth would leave 6.25e-6 < 1e-4, so the pixel stops before
+    # it: three fragments composited, C = 0.5 (1 - T_final) with unit-half colours
+    res = oracle_mod.render_pixels(
+        dict(uv=np.full((4, 2), 0.5), conic=np.tile([1.0, 0.0, 1.0], (4, 1)), opacity=np.full(4, 0.95),
+             rgb=np.full((4, 3), 0.5)), [[0, 0]], [[0, 1, 2, 3]], oracle_mod.Params())
+    assert res["n_contrib"][0] == 3 and res["flags"][0] == 0
+    assert abs(res["T"][0] - 0.05 ** 3) < 1e-15
+    np.testing.assert_allclose(res["C"][0], 0.5 * (1.0 - 0.05 ** 3), rtol=1e-12)
