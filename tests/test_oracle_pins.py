@@ -606,3 +606,20 @@ def test_stop_before_the_fragment_that_would_pass_t_min(oracle_mod):
     assert res["n_contrib"][0] == 3 and res["flags"][0] == 0
     assert abs(res["T"][0] - 0.05 ** 3) < 1e-15
     np.testing.assert_allclose(res["C"][0], 0.5 * (1.0 - 0.05 ** 3), rtol=1e-12)
+
+
+def test_sh_colour_clamp_blocks_its_gradient(oracle_mod):
+    # rgb = max(SH + 0.5, 0): a channel whose DC term drives it below zero is
+    # black in the image and passes no gradient to any of its 16 coefficients
+    cam = synth.plain_camera(32, 32, 300.0)
+    P = oracle_mod.Params()
+    g = _one([0.0, 0.0, 3.0], [math.log(0.01)] * 3, [1.0, 0.0, 0.0, 0.0], 0.8, (0.3, -3.0, 0.0))
+    g64 = oracle_mod.gaussians64(g)
+    fwd = oracle_mod.forward_view(g64, cam, P)
+    assert fwd["image"][0].max() > 0.1 and fwd["image"][1].max() == 0.0
+    np.testing.assert_allclose(fwd["image"][2].max() / fwd["image"][0].max(),
+                               0.5 / (0.28209479177387814 * float(np.float32(0.3)) + 0.5), rtol=1e-12)
+    grads = oracle_mod.backward_view(g64, fwd, cam, P, np.ones((3, cam.height, cam.width)))
+    sh = grads["sh"].reshape(16, 3) if grads["sh"].size == 48 else grads["sh"][0]
+    assert np.all(sh[:, 1] == 0.0)
+    assert sh[0, 0] > 0.0 and sh[0, 2] > 0.0
