@@ -623,3 +623,14 @@ def test_sh_colour_clamp_blocks_its_gradient(oracle_mod):
     sh = grads["sh"].reshape(16, 3) if grads["sh"].size == 48 else grads["sh"][0]
     assert np.all(sh[:, 1] == 0.0)
     assert sh[0, 0] > 0.0 and sh[0, 2] > 0.0
+
+
+def test_visible_set_breaks_ties_by_lower_index(oracle_mod):
+    # w = (2, 3, 3, 1): the descending order with ties by index is 1, 2, 0, 3
+    # (masses 3, 6, 8, 9 of 9); a cut at 30 % takes Gaussian 1 alone, at 60 %
+    # Gaussians 1 and 2, at 85 % all but 3; zero mass makes nothing visible
+    w = [2.0, 3.0, 3.0, 1.0]
+    np.testing.assert_array_equal(oracle_mod.visible_top_mass(w, 0.3), [False, True, False, False])
+    np.testing.assert_array_equal(oracle_mod.visible_top_mass(w, 0.6), [False, True, True, False])
+    np.testing.assert_array_equal(oracle_mod.visible_top_mass(w, 0.85), [True, True, True, False])
+    np.testing.assert_array_equal(oracle_mod.visible_top_mass([0.0, 0.0], 0.99), [False, False])
