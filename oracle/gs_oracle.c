@@ -13,10 +13,22 @@
  *   - Sec. 3.2 and Fig. 2: per-(Gaussian, view) alpha-weight w = sum_p alpha T
  *     and qualifying-pixel count a, accumulated during compositing.
  *   - The exact adjoint (reverse-mode derivative) of all of the above.
- * Continuous values are FP64; integer decisions of the projection are taken in
- * FP32 (project.inc compiled with REAL = float); compositing thresholds are
- * compared in FP64 and pixels where a fragment lies within tie_band of a
- * threshold are flagged, so callers can exclude them from exact comparisons.
+ * Everything is computed in FP64 from the FP32 inputs, decisions included.
+ * A renderer that computes in FP32 can take a decision the other way only
+ * where the FP64 value lies within its rounding error of the boundary: each
+ * such decision is flagged (tie bits per Gaussian, flag bits per pixel) from
+ * a stated FP32 error bound, so callers can exclude exactly those cases from
+ * exact comparisons.  The bounds are:
+ *   - projection decisions (LOD level, near plane, radius): a running
+ *     forward-error bound of an FP32 evaluation of the same formulas
+ *     (Wilkinson's running error analysis; Higham, "Accuracy and Stability
+ *     of Numerical Algorithms", ch. 3), valid in any association order;
+ *   - tile rectangle: the FP32 projected mean (the float nearest a mean held
+ *     to at least 2^-38 relative), the rectangle's arithmetic being exact;
+ *   - compositing thresholds: a renderer whose per-Gaussian exponent form
+ *     A (x + k y)^2 + D y^2 carries at most prec_conic relative error in A, D
+ *     and prec_conic (|k| + sqrt(D / A)) in k, and whose mean carries at most
+ *     prec_mean pixels, evaluating the exponent in FP32.
  *
  * The SH basis is built from its definition: associated Legendre functions
  * from Rodrigues' formula, normalisation sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!),
@@ -40,6 +52,7 @@
 #define OR_TIE_RADIUS 8u
 #define OR_TIE_RECT 16u
 #define OR_TIE_CLAMP 32u
+#define OR_TIE_DEPTH 64u
 
 /* pixel flags */
 #define OR_PIX_ALPHA_MIN 1u  /* some fragment's alpha within band of alpha_min */
@@ -61,36 +74,331 @@ typedef struct {
     double alpha_min, alpha_max, T_min;
     double dilation, znear, fov_clamp;
     double lod_d0, lod_f;
-    double tie_band;       /* relative band for projection decisions */
-    double comp_band;      /* relative band for compositing thresholds */
+    double prec_mean;      /* renderer's projected-mean error bound, pixels */
+    double prec_conic;     /* renderer's exponent-form coefficient error bound (relative) */
+    double comp_band;      /* extra log-space band for compositing thresholds */
 } or_params;
 
-/* ---- projection, two precisions ---------------------------------------- */
-#define REAL double
-#define PFN(x) x##_f64
-#define SQRT sqrt
-#define EXP exp
-#define LOG2 log2
-#define FLOOR floor
-#define CEIL ceil
-#include "project.inc"
-#undef REAL
-#undef PFN
-#undef SQRT
-#undef EXP
-#undef LOG2
-#undef FLOOR
-#undef CEIL
-#define REAL float
-#define PFN(x) x##_f32
-#define SQRT sqrtf
-#define EXP expf
-#define LOG2 log2f
-#define FLOOR floorf
-#define CEIL ceilf
-#include "project.inc"
-#undef REAL
-#undef PFN
+/* ---- FP32 forward-error bounds -------------------------------------------
+ * Each quantity v of a formula is carried with a bound e such that an FP32
+ * evaluation of the same formula, whatever the association order of its sums,
+ * is within e of v: every FP32 operation adds one rounding of at most
+ * U32 = 2^-24 of its result, and errors of the operands propagate to first
+ * order plus the product of the two errors.  Sums of n terms take
+ * gamma_{n-1} = (n - 1) U32 of the sum of their magnitudes (Higham, Eq. 3.5);
+ * library exp is taken as at most 2 ulp, sqrt and division as correctly
+ * rounded. */
+#define U32 5.9604644775390625e-08
+
+typedef struct { double v, e; } eb_t;
+
+static eb_t eb(double v, double e) { eb_t r; r.v = v; r.e = e; return r; }
+static eb_t eb_round(double v, double e) { return eb(v, e + U32 * (fabs(v) + e)); }
+static eb_t eb_add(eb_t a, eb_t b) { return eb_round(a.v + b.v, a.e + b.e); }
+static eb_t eb_sub(eb_t a, eb_t b) { return eb_round(a.v - b.v, a.e + b.e); }
+static eb_t eb_neg(eb_t a) { return eb(-a.v, a.e); }
+static eb_t eb_scale(eb_t a, double k) { return eb(k * a.v, fabs(k) * a.e); } /* k a power of two: exact */
+static eb_t eb_mul(eb_t a, eb_t b)
+{
+    return eb_round(a.v * b.v, fabs(a.v) * b.e + fabs(b.v) * a.e + a.e * b.e);
+}
+static eb_t eb_div(eb_t a, eb_t b)
+{
+    const double v = a.v / b.v, den = fabs(b.v) - b.e;
+    return eb_round(v, den > 0.0 ? (a.e + fabs(v) * b.e) / den : INFINITY);
+}
+static eb_t eb_sqrt(eb_t a)
+{
+    const double v = sqrt(a.v > 0.0 ? a.v : 0.0);
+    const double hi = sqrt(a.v + a.e), lo = sqrt(a.v - a.e > 0.0 ? a.v - a.e : 0.0);
+    return eb_round(v, fmax(hi - v, v - lo));
+}
+static eb_t eb_exp(eb_t a)
+{
+    const double v = exp(a.v), e = v * expm1(a.e);
+    return eb(v, e + 4.0 * U32 * (v + e));
+}
+/* sum of n terms in any order */
+static eb_t eb_sum(const eb_t *t, int n)
+{
+    double v = 0.0, mag = 0.0, e = 0.0;
+    for (int i = 0; i < n; i++) { v += t[i].v; mag += fabs(t[i].v) + t[i].e; e += t[i].e; }
+    return eb(v, e + (double)n * U32 * mag); /* gamma_{n-1} of the terms plus the final rounding */
+}
+/* clamp to [-lim, lim]: 1-Lipschitz in x and in lim */
+static eb_t eb_clamp(eb_t x, eb_t lim)
+{
+    const double v = x.v < -lim.v ? -lim.v : (x.v > lim.v ? lim.v : x.v);
+    return eb(v, fmax(x.e, lim.e));
+}
+static eb_t eb_in(double v) { return eb(v, 0.0); } /* an FP32 input, exact */
+
+/* ---- projection (App. A; view gate Eq. 1-3) -------------------------------
+ * Steps, all in FP64:
+ *   1. LOD gate L = clamp(round(log_f(d0 / d)), 0, Lmax), keep lod <= L (Eq. 1, 2)
+ *   2. cull mask column (Eq. 3)
+ *   3. camera transform, near-plane cull
+ *   4. Sigma = R(q) diag(exp(2 log s)) R(q)^T
+ *   5. Sigma' = J W Sigma W^T J^T + dilation I     (EWA splatting, 3DGS)
+ *   6. conic = inverse of Sigma' (det = a c - b^2), radius = ceil(3 sqrt(lambda_max)),
+ *      tile rectangle covering [u - r, u + r] x [v - r, v + r].
+ * Tie bits mark the decisions an FP32 renderer may take the other way. */
+typedef struct {
+    int status;            /* OR_ACTIVE or the first failed test */
+    unsigned tie;          /* OR_TIE_* bits */
+    double tx, ty, tz;     /* camera-space mean */
+    double u, v;           /* projected mean, pixels */
+    double a, b, c, det;   /* Sigma' (with dilation) and its determinant */
+    double conA, conB, conC;
+    double extent, extent_err; /* 3 sqrt(lambda_max) and its FP32 error bound */
+    int radius;
+    int rect[4];           /* x0, y0, x1, y1 in tiles, half-open */
+} proj_t;
+
+static double ulp32(double x)
+{
+    const double ax = fabs(x);
+    if (ax < 1.1754943508222875e-38) return 1.401298464324817e-45;
+    int ex;
+    frexp(ax, &ex); /* ax = m 2^ex, 0.5 <= m < 1 */
+    return ldexp(1.0, ex - 24);
+}
+
+/* frac distance of x to the nearest integer */
+static double dist_int(double x) { return fabs(x - floor(x + 0.5)); }
+
+/* The rotation of a quaternion (w, x, y, z), normalised, with its FP32 error bounds. */
+static void quat_rot_eb(const double q4[4], eb_t Q[3][3])
+{
+    eb_t sq[4];
+    for (int k = 0; k < 4; k++) sq[k] = eb_mul(eb_in(q4[k]), eb_in(q4[k]));
+    const eb_t qn = eb_sqrt(eb_sum(sq, 4));
+    const eb_t w = eb_div(eb_in(q4[0]), qn), x = eb_div(eb_in(q4[1]), qn);
+    const eb_t y = eb_div(eb_in(q4[2]), qn), z = eb_div(eb_in(q4[3]), qn);
+    const eb_t one = eb_in(1.0);
+    Q[0][0] = eb_sub(one, eb_scale(eb_add(eb_mul(y, y), eb_mul(z, z)), 2.0));
+    Q[0][1] = eb_scale(eb_sub(eb_mul(x, y), eb_mul(w, z)), 2.0);
+    Q[0][2] = eb_scale(eb_add(eb_mul(x, z), eb_mul(w, y)), 2.0);
+    Q[1][0] = eb_scale(eb_add(eb_mul(x, y), eb_mul(w, z)), 2.0);
+    Q[1][1] = eb_sub(one, eb_scale(eb_add(eb_mul(x, x), eb_mul(z, z)), 2.0));
+    Q[1][2] = eb_scale(eb_sub(eb_mul(y, z), eb_mul(w, x)), 2.0);
+    Q[2][0] = eb_scale(eb_sub(eb_mul(x, z), eb_mul(w, y)), 2.0);
+    Q[2][1] = eb_scale(eb_add(eb_mul(y, z), eb_mul(w, x)), 2.0);
+    Q[2][2] = eb_sub(one, eb_scale(eb_add(eb_mul(x, x), eb_mul(y, y)), 2.0));
+}
+
+/* lambda_max of Sigma' = [[a, b], [b, c]]: mid + sqrt(max(0.1, mid^2 - det)) */
+static eb_t lambda_max_eb(eb_t a, eb_t c, eb_t det)
+{
+    const eb_t mid = eb_scale(eb_add(a, c), 0.5);
+    eb_t disc = eb_sub(eb_mul(mid, mid), det);
+    if (disc.v < 0.1) disc.v = 0.1; /* max(0.1, .) is 1-Lipschitz: the bound stays */
+    return eb_add(mid, eb_sqrt(disc));
+}
+
+static void project_one(const double *mean3, const double *ls3, const double *q4, int lod, int culled,
+                        const or_camera *cam, const or_params *P, proj_t *o)
+{
+    memset(o, 0, sizeof(*o));
+    o->status = OR_ACTIVE;
+    const double mx = mean3[0], my = mean3[1], mz = mean3[2];
+
+    /* 1. distance-based LOD gate (Eq. 1 and Eq. 2).  An FP32 renderer forms
+     * d^2 from the float coordinates with relative error <= 7 U32; the level
+     * log_f(d0 / d) then moves by <= 3.5 U32 / ln f, and a threshold rounded
+     * to float adds U32 / ln f: flagged within twice that of a half-integer. */
+    if (P->lod_enable) {
+        const double dx = mx - cam->campos[0], dy = my - cam->campos[1], dz = mz - cam->campos[2];
+        const double d = sqrt(dx * dx + dy * dy + dz * dz);
+        int L;
+        if (d > 0.0) {
+            const double x = log(P->lod_d0 / d) / log(P->lod_f);
+            const double r = x >= 0.0 ? floor(x + 0.5) : -floor(-x + 0.5); /* half away from zero */
+            L = (int)r;
+            if (dist_int(x + 0.5) <= 2.0 * 4.5 * U32 / log(P->lod_f)) o->tie |= OR_TIE_LOD;
+        } else {
+            L = P->lod_Lmax;
+        }
+        if (L < 0) L = 0;
+        if (L > P->lod_Lmax) L = P->lod_Lmax;
+        if (lod > L) {
+            o->status = OR_GATED_LOD;
+            if (!(o->tie & OR_TIE_LOD)) return; /* a tied gate: the values below are still wanted */
+        }
+    }
+    /* 2. importance-based per-view cull (Eq. 3) */
+    if (P->cull_enable && culled) { o->status = OR_GATED_CULL; return; }
+
+    /* 3. camera transform, t = W mu + t0 (W row-major) */
+    const double *W = cam->R;
+    const double tx = W[0] * mx + W[1] * my + W[2] * mz + cam->t[0];
+    const double ty = W[3] * mx + W[4] * my + W[5] * mz + cam->t[1];
+    const double tz = W[6] * mx + W[7] * my + W[8] * mz + cam->t[2];
+    o->tx = tx; o->ty = ty; o->tz = tz;
+    /* the renderer compares its float depth (nearest to a mean held to 2^-38) with znear */
+    const double zmag = fabs(W[6] * mx) + fabs(W[7] * my) + fabs(W[8] * mz) + fabs(cam->t[2]);
+    if (fabs(tz - P->znear) <= ulp32(P->znear) + 0x1p-38 * zmag) o->tie |= OR_TIE_NEAR;
+    if (!(tz > P->znear) && o->status == OR_ACTIVE) {
+        o->status = OR_NEAR;
+        if (!(o->tie & OR_TIE_NEAR)) return;
+    }
+    if (!(tz > 0.0)) { if (o->status == OR_ACTIVE) o->status = OR_NEAR; return; }
+    /* the depth key is the float nearest the depth: flagged where a depth held
+     * to 2^-38 could round to the neighbouring float */
+    {
+        const double d32 = (double)(float)tz, half = 0.5 * ulp32(d32);
+        if (fabs(half - fabs(tz - d32)) <= 0x1p-38 * zmag) o->tie |= OR_TIE_DEPTH;
+    }
+
+    /* 4. 3D covariance from the normalised quaternion and the scales */
+    double qn = sqrt(q4[0] * q4[0] + q4[1] * q4[1] + q4[2] * q4[2] + q4[3] * q4[3]);
+    const double w = q4[0] / qn, x = q4[1] / qn, y = q4[2] / qn, z = q4[3] / qn;
+    const double Q[3][3] = {{1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)},
+                            {2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)},
+                            {2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)}};
+    const double sc[3] = {exp(ls3[0]), exp(ls3[1]), exp(ls3[2])};
+    double Sg[3][3];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; k++) acc += Q[i][k] * sc[k] * sc[k] * Q[j][k];
+            Sg[i][j] = acc;
+        }
+
+    /* 5. EWA: Jacobian of the perspective map at the (clamped) mean */
+    const double fx = cam->fx, fy = cam->fy;
+    const double limx = P->fov_clamp * (cam->width / (2.0 * fx));
+    const double limy = P->fov_clamp * (cam->height / (2.0 * fy));
+    const double xr = tx / tz, yr = ty / tz;
+    const double xc = xr < -limx ? -limx : (xr > limx ? limx : xr);
+    const double yc = yr < -limy ? -limy : (yr > limy ? limy : yr);
+    const double J[2][3] = {{fx / tz, 0.0, -fx * xc / tz}, {0.0, fy / tz, -fy * yc / tz}};
+    double T[2][3];
+    for (int r = 0; r < 2; r++)
+        for (int k = 0; k < 3; k++) T[r][k] = J[r][0] * W[k] + J[r][1] * W[3 + k] + J[r][2] * W[6 + k];
+    double S2[2][2];
+    for (int r = 0; r < 2; r++)
+        for (int c = 0; c < 2; c++) {
+            double acc = 0.0;
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++) acc += T[r][i] * Sg[i][j] * T[c][j];
+            S2[r][c] = acc;
+        }
+    const double a = S2[0][0] + P->dilation, b = S2[0][1], c = S2[1][1] + P->dilation;
+    o->a = a; o->b = b; o->c = c;
+
+    /* 6. conic, extent, footprint */
+    const double det = a * c - b * b;
+    o->det = det;
+
+    /* FP32 error bounds of det and of the extent, for the two standard ways of
+     * forming Sigma': as V V^T with V = J W R diag(s) (det by the Cauchy-Binet
+     * identity), and as J W Sigma W^T J^T with Sigma formed first (det as
+     * a c - b^2).  The larger bound of the two is taken. */
+    double det_err, ext_err;
+    {
+        eb_t Qe[3][3];
+        quat_rot_eb(q4, Qe);
+        eb_t se[3];
+        for (int k = 0; k < 3; k++) se[k] = eb_exp(eb_in(ls3[k]));
+        eb_t M[3][3];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) M[i][j] = eb_mul(Qe[i][j], se[j]);
+        /* the renderer's float camera-space mean: nearest float to a value held to 2^-38 */
+        const double tmag[3] = {fabs(W[0] * mx) + fabs(W[1] * my) + fabs(W[2] * mz) + fabs(cam->t[0]),
+                                fabs(W[3] * mx) + fabs(W[4] * my) + fabs(W[5] * mz) + fabs(cam->t[1]), zmag};
+        const eb_t te[3] = {eb(tx, 0.5 * ulp32(tx) + 0x1p-38 * tmag[0]), eb(ty, 0.5 * ulp32(ty) + 0x1p-38 * tmag[1]),
+                            eb(tz, 0.5 * ulp32(tz) + 0x1p-38 * tmag[2])};
+        const eb_t fxe = eb_in(fx), fye = eb_in(fy), fc = eb_in(P->fov_clamp);
+        const eb_t lx = eb_mul(fc, eb_div(eb_in(cam->width), eb_scale(fxe, 2.0)));
+        const eb_t ly = eb_mul(fc, eb_div(eb_in(cam->height), eb_scale(fye, 2.0)));
+        const eb_t xce = eb_clamp(eb_div(te[0], te[2]), lx), yce = eb_clamp(eb_div(te[1], te[2]), ly);
+        const eb_t tz2 = eb_mul(te[2], te[2]);
+        const eb_t j00 = eb_div(fxe, te[2]), j02 = eb_neg(eb_div(eb_mul(fxe, eb_mul(xce, te[2])), tz2));
+        const eb_t j11 = eb_div(fye, te[2]), j12 = eb_neg(eb_div(eb_mul(fye, eb_mul(yce, te[2])), tz2));
+        eb_t Te[2][3];
+        for (int k = 0; k < 3; k++) {
+            Te[0][k] = eb_add(eb_mul(j00, eb_in(W[k])), eb_mul(j02, eb_in(W[6 + k])));
+            Te[1][k] = eb_add(eb_mul(j11, eb_in(W[3 + k])), eb_mul(j12, eb_in(W[6 + k])));
+        }
+        const eb_t dil = eb_in(P->dilation);
+        /* (i) V = T M, Sigma' = V V^T + dil I, det by Cauchy-Binet */
+        eb_t V[2][3];
+        for (int r = 0; r < 2; r++)
+            for (int k = 0; k < 3; k++) {
+                eb_t t3[3] = {eb_mul(Te[r][0], M[0][k]), eb_mul(Te[r][1], M[1][k]), eb_mul(Te[r][2], M[2][k])};
+                V[r][k] = eb_sum(t3, 3);
+            }
+        eb_t t00[3], t11[3];
+        for (int k = 0; k < 3; k++) { t00[k] = eb_mul(V[0][k], V[0][k]); t11[k] = eb_mul(V[1][k], V[1][k]); }
+        const eb_t s00 = eb_sum(t00, 3), s11 = eb_sum(t11, 3);
+        const eb_t av = eb_add(s00, dil), cv = eb_add(s11, dil);
+        const eb_t m01 = eb_sub(eb_mul(V[0][0], V[1][1]), eb_mul(V[0][1], V[1][0]));
+        const eb_t m02 = eb_sub(eb_mul(V[0][0], V[1][2]), eb_mul(V[0][2], V[1][0]));
+        const eb_t m12 = eb_sub(eb_mul(V[0][1], V[1][2]), eb_mul(V[0][2], V[1][1]));
+        const eb_t dterms[5] = {eb_mul(m01, m01), eb_mul(m02, m02), eb_mul(m12, m12),
+                                eb_mul(dil, eb_add(s00, s11)), eb_mul(dil, dil)};
+        const eb_t detv = eb_sum(dterms, 5);
+        const eb_t lamv = lambda_max_eb(av, cv, detv);
+        /* (ii) Sigma = M M^T, Sigma' = T Sigma T^T + dil I, det = a c - b^2 */
+        eb_t Se[3][3];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                eb_t t3[3] = {eb_mul(M[i][0], M[j][0]), eb_mul(M[i][1], M[j][1]), eb_mul(M[i][2], M[j][2])};
+                Se[i][j] = eb_sum(t3, 3);
+            }
+        eb_t S2e[2][2];
+        for (int r = 0; r < 2; r++)
+            for (int cc = 0; cc < 2; cc++) {
+                eb_t t9[9];
+                for (int i = 0; i < 3; i++)
+                    for (int j = 0; j < 3; j++) t9[3 * i + j] = eb_mul(eb_mul(Te[r][i], Se[i][j]), Te[cc][j]);
+                S2e[r][cc] = eb_sum(t9, 9);
+            }
+        const eb_t as = eb_add(S2e[0][0], dil), bs = S2e[0][1], cs = eb_add(S2e[1][1], dil);
+        const eb_t dets = eb_sub(eb_mul(as, cs), eb_mul(bs, bs));
+        const eb_t lams = lambda_max_eb(as, cs, dets);
+        /* ext = 3 sqrt(lambda): its bound from each lambda bound */
+        const eb_t e1 = eb_mul(eb_in(3.0), eb_sqrt(lamv)), e2 = eb_mul(eb_in(3.0), eb_sqrt(lams));
+        det_err = fmax(detv.e, dets.e);
+        ext_err = fmax(e1.e, e2.e);
+    }
+    if (fabs(det) <= 2.0 * det_err) o->tie |= OR_TIE_DET;
+    if (!(det > 0.0)) { if (o->status == OR_ACTIVE) o->status = OR_DEGENERATE; return; }
+    o->conA = c / det; o->conB = -b / det; o->conC = a / det;
+    const double mid = 0.5 * (a + c);
+    double disc = mid * mid - det;
+    if (disc < 0.1) disc = 0.1;
+    const double lam = mid + sqrt(disc);
+    const double ext = 3.0 * sqrt(lam);
+    o->extent = ext;
+    o->extent_err = ext_err;
+    /* ceil(ext) changes where ext crosses an integer */
+    if (dist_int(ext) <= 2.0 * ext_err) o->tie |= OR_TIE_RADIUS;
+    o->radius = (int)ceil(ext);
+    const double u = fx * tx / tz + cam->cx;
+    const double v = fy * ty / tz + cam->cy;
+    o->u = u; o->v = v;
+    const int r = o->radius, tw = P->tile_w, th = P->tile_h;
+    const int tiles_x = (cam->width + tw - 1) / tw;
+    const int tiles_y = (cam->height + th - 1) / th;
+    /* the rectangle from the renderer's float mean (within 1/2 ulp + 2^-38 of
+     * the exact one) and the integer radius is exact arithmetic: an edge can
+     * move only where (u +- r) lies within that of a tile boundary */
+    const double bu = 0.5 * ulp32(u) + 0x1p-38 * fabs(u) + 1e-300, bv = 0.5 * ulp32(v) + 0x1p-38 * fabs(v) + 1e-300;
+    const double e[4] = {(u - r) / tw, (v - r) / th, (u + r) / tw, (v + r) / th};
+    const double be[4] = {2.0 * bu / tw, 2.0 * bv / th, 2.0 * bu / tw, 2.0 * bv / th};
+    for (int k = 0; k < 4; k++)
+        if (dist_int(e[k]) <= be[k]) o->tie |= OR_TIE_RECT;
+    int x0 = (int)floor(e[0]), y0 = (int)floor(e[1]);
+    int x1 = (int)floor(e[2]) + 1, y1 = (int)floor(e[3]) + 1;
+    x0 = x0 < 0 ? 0 : (x0 > tiles_x ? tiles_x : x0);
+    x1 = x1 < 0 ? 0 : (x1 > tiles_x ? tiles_x : x1);
+    y0 = y0 < 0 ? 0 : (y0 > tiles_y ? tiles_y : y0);
+    y1 = y1 < 0 ? 0 : (y1 > tiles_y ? tiles_y : y1);
+    o->rect[0] = x0; o->rect[1] = y0; o->rect[2] = x1; o->rect[3] = y1;
+    if ((x1 <= x0 || y1 <= y0) && o->status == OR_ACTIVE) o->status = OR_EMPTY;
+}
 
 /* ---- spherical harmonics from the definition ---------------------------- */
 static double factorial(int k)
@@ -191,8 +499,7 @@ typedef struct {
     int32_t *radius;    /* n */
     int32_t *rect;      /* 4n */
     int32_t *tiles;     /* n */
-    double *ldl32;      /* 3n: (A, k, D) of the FP32 instance's conic, NULL if not wanted */
-    double *uv32;       /* 2n: projected mean in double, before the FP32 instance rounds it */
+    double *extent;     /* 2n: 3 sqrt(lambda_max) and the FP32 error bound of it */
 } or_proj_out;
 
 static int cull_bit(const uint32_t *cull, int64_t i)
@@ -210,29 +517,21 @@ int or_project(int64_t n, const double *mean, const double *log_scale, const dou
         double q4[4] = {quat[i], quat[n + i], quat[2 * n + i], quat[3 * n + i]};
         int l = lod ? lod[i] : 0;
         int cb = cull_bit(cull, i);
-        proj_t_f32 d32;
-        proj_t_f64 d64;
-        project_one_f32(m3, s3, q4, l, cb, cam, P, &d32);
-        project_one_f64(m3, s3, q4, l, cb, cam, P, &d64);
-        out->status[i] = (int8_t)d32.status;
-        out->tie[i] = (uint8_t)(d32.tie | d64.tie);
-        out->depth32[i] = d32.tz;
-        out->depth[i] = d64.tz;
-        out->radius[i] = d32.radius;
-        for (int k = 0; k < 4; k++) out->rect[4 * i + k] = d32.rect[k];
-        out->tiles[i] = d32.status == OR_ACTIVE ? (d32.rect[2] - d32.rect[0]) * (d32.rect[3] - d32.rect[1]) : 0;
-        out->uv[2 * i] = d64.u;
-        out->uv[2 * i + 1] = d64.v;
-        if (out->ldl32) {
-            out->ldl32[3 * i] = d32.ldlA;
-            out->ldl32[3 * i + 1] = d32.ldlK;
-            out->ldl32[3 * i + 2] = d32.ldlD;
-            out->uv32[2 * i] = d32.ud;
-            out->uv32[2 * i + 1] = d32.vd;
-        }
-        out->conic[3 * i] = d64.conA;
-        out->conic[3 * i + 1] = d64.conB;
-        out->conic[3 * i + 2] = d64.conC;
+        proj_t pj;
+        project_one(m3, s3, q4, l, cb, cam, P, &pj);
+        out->status[i] = (int8_t)pj.status;
+        out->tie[i] = (uint8_t)pj.tie;
+        out->depth32[i] = (float)pj.tz; /* the depth key: the FP32 value of the exact depth */
+        out->depth[i] = pj.tz;
+        out->radius[i] = pj.radius;
+        for (int k = 0; k < 4; k++) out->rect[4 * i + k] = pj.rect[k];
+        out->tiles[i] = pj.status == OR_ACTIVE ? (pj.rect[2] - pj.rect[0]) * (pj.rect[3] - pj.rect[1]) : 0;
+        out->uv[2 * i] = pj.u;
+        out->uv[2 * i + 1] = pj.v;
+        if (out->extent) { out->extent[2 * i] = pj.extent; out->extent[2 * i + 1] = pj.extent_err; }
+        out->conic[3 * i] = pj.conA;
+        out->conic[3 * i + 1] = pj.conB;
+        out->conic[3 * i + 2] = pj.conC;
         out->opacity[i] = 1.0 / (1.0 + exp(-opacity_logit[i]));
         /* view-dependent colour, degree-3 SH, +0.5 offset, clamped at 0 */
         double d[3] = {m3[0] - cam->campos[0], m3[1] - cam->campos[1], m3[2] - cam->campos[2]};
@@ -329,37 +628,40 @@ static int near_log(double x, double thr, double band)
 }
 
 /* How far an FP32 renderer's exponent for this fragment can be from the exact
- * one.  An FP32 renderer composites with the FP32 instance's conic, held as
- * A (x + k y)^2 + D y^2 (ldl32), and a mean kept to double precision (uv32).
- * The exponent these give, evaluated exactly, differs from the exact exponent
- * by the projection's own rounding; evaluating that form in FP32 adds, per
- * operation, a relative 2^-24 of the terms it combines, and 2^x in FP32 a few
- * more units.  A fragment whose alpha lies within this of a threshold may be
- * decided the other way by a correct FP32 renderer. */
-static double fp32_power_err(const double *ldl32, const double *uv32, int32_t g, double px, double py,
+ * one, for a renderer that holds each Gaussian's exponent as
+ * A (x + k y)^2 + D y^2 (k = B / A, D = C - B^2 / A) with |dA| <= pc A,
+ * |dD| <= pc D, |dk| <= pc (|k| + sqrt(D / A)) (pc = prec_conic) and its mean
+ * within pm = prec_mean pixels, and evaluates the form, the exponential and
+ * o G in FP32.  With e = dx + k dy:
+ *   |de|  <= pm (1 + |k|) + |dy| pc (|k| + sqrt(D / A)) + 2 U32 (|dx| + 2 |k dy|)
+ *   |dp|  <= pc |p| + A |e| |de| + A |de|^2 / 2 + D |dy| pm + 4 U32 |p|
+ * plus 2^-21 for the exponential and 8 U32 for the opacity.  Returned
+ * doubled: a fragment whose alpha lies within this (in log space) of a
+ * threshold may be decided the other way by such a renderer. */
+static double fp32_power_err(const or_params *P, const double *conic, int32_t g, double dx, double dy,
                              double power)
 {
-    const double eps32 = 5.9604644775390625e-08; /* 2^-24 */
-    if (!ldl32) return 16.0 * eps32 * (fabs(power) + 1.0);
-    const double A = ldl32[3 * g], k = ldl32[3 * g + 1], D = ldl32[3 * g + 2];
-    const double dx = px - uv32[2 * g], dy = py - uv32[2 * g + 1];
+    const double A = conic[3 * g], B = conic[3 * g + 1], C = conic[3 * g + 2];
+    const double k = B / A, D = C - B * k;
+    const double pm = P->prec_mean, pc = P->prec_conic;
     const double e = dx + k * dy;
-    const double p32 = -0.5 * (A * e * e + D * dy * dy);
-    const double de = 2.0 * eps32 * (fabs(dx) + 2.0 * fabs(k * dy));
-    const double eval = 0.5 * A * (2.0 * fabs(e) * de + de * de) + 4.0 * eps32 * (fabs(p32) + 1.0);
-    return 2.0 * (fabs(p32 - power) + eval);
+    const double de = pm * (1.0 + fabs(k)) + fabs(dy) * pc * (fabs(k) + sqrt(fabs(D / A)))
+                    + 2.0 * U32 * (fabs(dx) + 2.0 * fabs(k * dy));
+    const double dp = pc * fabs(power) + A * fabs(e) * de + 0.5 * A * de * de + fabs(D * dy) * pm
+                    + 4.0 * U32 * fabs(power);
+    return 2.0 * (dp + 0x1p-21 + 8.0 * U32);
 }
 
 /* Composites the ordered Gaussians ids[0..len) at pixel centre (px, py).
  * Optional w/a accumulate the importance alpha-weight and pixel count.
- * Flags: a fragment within tie band (comp_band, widened by its own FP32 error
- * bound) of the alpha_min or T_min threshold, or at the exponent's maximum 0.
+ * Flags: a fragment within comp_band plus its own FP32 error bound (log
+ * space) of the alpha_min, alpha_max or T_min threshold, or at the
+ * exponent's maximum 0.
  * When the pixel is flagged and gcount is given, every Gaussian the pixel
  * composited or nearly composited has its count of such pixels raised. */
 static void composite_pixel(const or_params *P, double px, double py, const int32_t *ids, int64_t len,
                             const double *uv, const double *conic, const double *opacity,
-                            const double *rgb, pix_t *o, double *w, double *a, int32_t *gcount,
-                            const double *ldl32, const double *uv32)
+                            const double *rgb, pix_t *o, double *w, double *a, int32_t *gcount)
 {
     double T = 1.0, C[3] = {0, 0, 0};
     double T_relerr = 0.0; /* bound on the relative error of T in FP32 */
@@ -371,7 +673,7 @@ static void composite_pixel(const or_params *P, double px, double py, const int3
         double dx = px - uv[2 * g], dy = py - uv[2 * g + 1];
         double A = conic[3 * g], B = conic[3 * g + 1], Cc = conic[3 * g + 2];
         double power = -0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy;
-        const double perr = fp32_power_err(ldl32, uv32, g, px, py, power);
+        const double perr = fp32_power_err(P, conic, g, dx, dy, power);
         if (power > 0.0) { fl |= OR_PIX_POWER; continue; } /* only from rounding at the centre */
         double G = exp(power);
         double og = opacity[g] * G;
@@ -407,14 +709,11 @@ static void composite_pixel(const or_params *P, double px, double py, const int3
 
 /* Tiled render: image (3,H,W) planar, T_final (H,W), n_contrib (H,W), flags
  * (H,W); w, a (n) accumulate the importance signals when non-NULL; gcount (n)
- * counts, per Gaussian, the flagged pixels it takes part in, when non-NULL.
- * ldl32 (3n) and uv32 (2n), from the projection's FP32 instance, widen the
- * flag bands by how far an FP32 renderer's exponents can be from the exact
- * ones; NULL leaves only the fixed bands. */
+ * counts, per Gaussian, the flagged pixels it takes part in, when non-NULL. */
 int or_render(const or_camera *cam, const or_params *P, int64_t n, const double *uv, const double *conic,
               const double *opacity, const double *rgb, const int64_t *tile_start, const int32_t *list,
               double *image, double *T_final, int32_t *n_contrib, uint8_t *flags, double *w, double *a,
-              int32_t *gcount, const double *ldl32, const double *uv32)
+              int32_t *gcount)
 {
     (void)n;
     const int W = cam->width, H = cam->height, tw = P->tile_w, th = P->tile_h;
@@ -424,7 +723,7 @@ int or_render(const or_camera *cam, const or_params *P, int64_t n, const double 
             int64_t t = (int64_t)(py / th) * tiles_x + px / tw;
             pix_t o;
             composite_pixel(P, px + 0.5, py + 0.5, list + tile_start[t], tile_start[t + 1] - tile_start[t],
-                            uv, conic, opacity, rgb, &o, w, a, gcount, ldl32, uv32);
+                            uv, conic, opacity, rgb, &o, w, a, gcount);
             int64_t p = (int64_t)py * W + px;
             for (int c = 0; c < 3; c++) image[(int64_t)c * W * H + p] = o.C[c];
             T_final[p] = o.T;
@@ -451,7 +750,7 @@ int or_render_brute(const or_camera *cam, const or_params *P, int64_t n, const i
     for (int py = 0; py < H; py++)
         for (int px = 0; px < W; px++) {
             pix_t o;
-            composite_pixel(P, px + 0.5, py + 0.5, ids, m, uv, conic, opacity, rgb, &o, NULL, NULL, NULL, NULL, NULL);
+            composite_pixel(P, px + 0.5, py + 0.5, ids, m, uv, conic, opacity, rgb, &o, NULL, NULL, NULL);
             int64_t p = (int64_t)py * W + px;
             for (int c = 0; c < 3; c++) image[(int64_t)c * W * H + p] = o.C[c];
             T_final[p] = o.T;
@@ -470,8 +769,7 @@ int or_render_pixels(const or_params *P, int64_t npix, const int32_t *pxy, const
     for (int64_t k = 0; k < npix; k++) {
         pix_t o;
         composite_pixel(P, pxy[2 * k] + 0.5, pxy[2 * k + 1] + 0.5, lists + list_start[k],
-                        list_start[k + 1] - list_start[k], uv, conic, opacity, rgb, &o, NULL, NULL, NULL, NULL,
-                        NULL);
+                        list_start[k + 1] - list_start[k], uv, conic, opacity, rgb, &o, NULL, NULL, NULL);
         for (int c = 0; c < 3; c++) C[3 * k + c] = o.C[c];
         T[k] = o.T;
         n_contrib[k] = o.n_contrib;
@@ -491,7 +789,7 @@ int or_render_pixels(const or_params *P, int64_t npix, const int32_t *pxy, const
 int or_render_bwd(const or_camera *cam, const or_params *P, int64_t n, const double *uv, const double *conic,
                   const double *opacity, const double *rgb, const int64_t *tile_start, const int32_t *list,
                   const double *dL_dimage, double *dL_duv, double *dL_dconic, double *dL_dopacity,
-                  double *dL_drgb)
+                  double *dL_drgb, double *dL_dconic_abs)
 {
     (void)n;
     const int W = cam->width, H = cam->height, tw = P->tile_w, th = P->tile_h;
@@ -557,6 +855,11 @@ int or_render_bwd(const or_camera *cam, const or_params *P, int64_t n, const dou
                 dL_dconic[3 * g] += dpower * (-0.5 * dx * dx);
                 dL_dconic[3 * g + 1] += dpower * (-dx * dy);
                 dL_dconic[3 * g + 2] += dpower * (-0.5 * dy * dy);
+                if (dL_dconic_abs) { /* magnitudes of the pixel terms, for FP32 error bounds */
+                    dL_dconic_abs[3 * g] += fabs(dpower * 0.5 * dx * dx);
+                    dL_dconic_abs[3 * g + 1] += fabs(dpower * dx * dy);
+                    dL_dconic_abs[3 * g + 2] += fabs(dpower * 0.5 * dy * dy);
+                }
             }
         }
     free(frag); free(fa); free(fT); free(fG); free(fog);
@@ -722,6 +1025,81 @@ int or_project_bwd(int64_t n, const double *mean, const double *log_scale, const
         double ddot = d[0] * gd[0] + d[1] * gd[1] + d[2] * gd[2];
         for (int e = 0; e < 3; e++) gm[e] += (gd[e] - d[e] * ddot) / dn;
         for (int k = 0; k < 3; k++) g_mean[(int64_t)k * n + i] += gm[k];
+    }
+    return 0;
+}
+
+/* ---- FP32 error bounds of the scale and rotation gradients ----------------
+ * With V = J W R(q) diag(s) and C = (V V^T + dilation I)^-1, w_k = C v_k (v_k the
+ * columns of V) and G = dL/dconic = [[gA, gB/2], [gB/2, gC]]:
+ *   dL/dlog s_k = -2 w_k^T G w_k,
+ *   the rotation gradient (body frame) theta_i = -2 w_a^T G w_b (s_a/s_b - s_b/s_a)
+ *   for (i, a, b) = (0, 1, 2), (1, 2, 0), (2, 0, 1), and dL/dq = (2/|q|) q (x) (0, theta).
+ * Each pixel adds dpow (w_a . d)(w_b . d) to w_a^T G w_b: a short axis of a long
+ * thin footprint sees pixel terms of gA, gB, gC that nearly cancel.  An FP32
+ * renderer holds the summed G to within eps_sum of the sums of the magnitudes of
+ * its pixel terms (dL_dconic_abs) and w_k to within prec_conic; the bound below
+ * propagates both through the bilinear forms (first order, magnitudes):
+ *   |d(w_a^T G w_b)| <= (eps_sum + 2 prec_conic) S_ab,
+ *   S_ab = |w_a0 w_b0| SA + (|w_a0 w_b1| + |w_a1 w_b0|) SB / 2 + |w_a1 w_b1| SC.
+ * Accumulates (+=) into ls_err (3n) and q_err (4n) for every ACTIVE Gaussian. */
+int or_grad_bounds(int64_t n, const double *mean, const double *log_scale, const double *quat, const int8_t *status,
+                   const or_camera *cam, const or_params *P, const double *dL_dconic_abs, double eps_sum,
+                   double *ls_err, double *q_err)
+{
+    const double *Wc = cam->R;
+    for (int64_t i = 0; i < n; i++) {
+        if (status[i] != OR_ACTIVE) continue;
+        double m3[3] = {mean[i], mean[n + i], mean[2 * n + i]};
+        double t[3];
+        for (int r = 0; r < 3; r++) t[r] = Wc[3 * r] * m3[0] + Wc[3 * r + 1] * m3[1] + Wc[3 * r + 2] * m3[2] + cam->t[r];
+        double qr[4] = {quat[i], quat[n + i], quat[2 * n + i], quat[3 * n + i]};
+        const double qn = sqrt(qr[0] * qr[0] + qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]);
+        const double q[4] = {qr[0] / qn, qr[1] / qn, qr[2] / qn, qr[3] / qn};
+        double Q[3][3];
+        quat_rot(q, Q);
+        const double s[3] = {exp(log_scale[i]), exp(log_scale[n + i]), exp(log_scale[2 * n + i])};
+        const double limx = P->fov_clamp * (cam->width / (2.0 * cam->fx));
+        const double limy = P->fov_clamp * (cam->height / (2.0 * cam->fy));
+        const double xr = t[0] / t[2], yr = t[1] / t[2];
+        const double xc = xr < -limx ? -limx : (xr > limx ? limx : xr);
+        const double yc = yr < -limy ? -limy : (yr > limy ? limy : yr);
+        const double J[2][3] = {{cam->fx / t[2], 0.0, -cam->fx * xc / t[2]}, {0.0, cam->fy / t[2], -cam->fy * yc / t[2]}};
+        double V[2][3];
+        for (int r = 0; r < 2; r++)
+            for (int k = 0; k < 3; k++) {
+                double acc = 0.0;
+                for (int a = 0; a < 3; a++) {
+                    double ta = J[r][0] * Wc[a] + J[r][1] * Wc[3 + a] + J[r][2] * Wc[6 + a];
+                    acc += ta * Q[a][k] * s[k];
+                }
+                V[r][k] = acc;
+            }
+        const double a = V[0][0] * V[0][0] + V[0][1] * V[0][1] + V[0][2] * V[0][2] + P->dilation;
+        const double b = V[0][0] * V[1][0] + V[0][1] * V[1][1] + V[0][2] * V[1][2];
+        const double c = V[1][0] * V[1][0] + V[1][1] * V[1][1] + V[1][2] * V[1][2] + P->dilation;
+        const double det = a * c - b * b;
+        const double C00 = c / det, C01 = -b / det, C11 = a / det;
+        double w[3][2];
+        for (int k = 0; k < 3; k++) {
+            w[k][0] = C00 * V[0][k] + C01 * V[1][k];
+            w[k][1] = C01 * V[0][k] + C11 * V[1][k];
+        }
+        const double SA = dL_dconic_abs[3 * i], SB = dL_dconic_abs[3 * i + 1], SC = dL_dconic_abs[3 * i + 2];
+        const double f = eps_sum + 2.0 * P->prec_conic;
+#define S_AB(x, y) (fabs(w[x][0] * w[y][0]) * SA + 0.5 * (fabs(w[x][0] * w[y][1]) + fabs(w[x][1] * w[y][0])) * SB + \
+                    fabs(w[x][1] * w[y][1]) * SC)
+        for (int k = 0; k < 3; k++) ls_err[(int64_t)k * n + i] += 2.0 * f * S_AB(k, k);
+        const double th[3] = {2.0 * f * S_AB(1, 2) * fabs(s[1] / s[2] - s[2] / s[1]),
+                              2.0 * f * S_AB(2, 0) * fabs(s[2] / s[0] - s[0] / s[2]),
+                              2.0 * f * S_AB(0, 1) * fabs(s[0] / s[1] - s[1] / s[0])};
+#undef S_AB
+        const double aw = fabs(q[0]), ax = fabs(q[1]), ay = fabs(q[2]), az = fabs(q[3]);
+        const double iq = 2.0 / qn;
+        q_err[i] += iq * (ax * th[0] + ay * th[1] + az * th[2]);
+        q_err[n + i] += iq * (aw * th[0] + ay * th[2] + az * th[1]);
+        q_err[2 * n + i] += iq * (aw * th[1] + az * th[0] + ax * th[2]);
+        q_err[3 * n + i] += iq * (aw * th[2] + ax * th[1] + ay * th[0]);
     }
     return 0;
 }

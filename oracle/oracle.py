@@ -34,16 +34,16 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "_gs_oracle.so")
-_SRC = [os.path.join(_HERE, "gs_oracle.c"), os.path.join(_HERE, "project.inc")]
+_SRC = [os.path.join(_HERE, "gs_oracle.c")]
 
 ACTIVE, GATED_LOD, GATED_CULL, NEAR, DEGENERATE, EMPTY = range(6)
-TIE_LOD, TIE_NEAR, TIE_DET, TIE_RADIUS, TIE_RECT, TIE_CLAMP = 1, 2, 4, 8, 16, 32
+TIE_LOD, TIE_NEAR, TIE_DET, TIE_RADIUS, TIE_RECT, TIE_CLAMP, TIE_DEPTH = 1, 2, 4, 8, 16, 32, 64
 PIX_ALPHA_MIN, PIX_T_MIN, PIX_ALPHA_MAX, PIX_POWER = 1, 2, 4, 8
 
 
 def build(force: bool = False) -> str:
-    """Compile the C oracle (plain C, -ffp-contract=off so FP32 decisions are
-    one IEEE operation each on every host)."""
+    """Compile the C oracle (plain C; -ffp-contract=off keeps every FP64
+    operation one IEEE operation on every host)."""
     if not force and os.path.exists(_SO) and all(os.path.getmtime(_SO) >= os.path.getmtime(s) for s in _SRC):
         return _SO
     cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fno-fast-math",
@@ -68,13 +68,13 @@ class ORParams(ctypes.Structure):
                 ("alpha_min", ctypes.c_double), ("alpha_max", ctypes.c_double), ("T_min", ctypes.c_double),
                 ("dilation", ctypes.c_double), ("znear", ctypes.c_double), ("fov_clamp", ctypes.c_double),
                 ("lod_d0", ctypes.c_double), ("lod_f", ctypes.c_double),
-                ("tie_band", ctypes.c_double), ("comp_band", ctypes.c_double)]
+                ("prec_mean", ctypes.c_double), ("prec_conic", ctypes.c_double), ("comp_band", ctypes.c_double)]
 
 
 class ORProjOut(ctypes.Structure):
     _fields_ = [(name, ctypes.c_void_p) for name in
                 ("status", "tie", "uv", "depth", "depth32", "conic", "opacity", "rgb", "clamp", "radius", "rect", "tiles",
-                 "ldl32", "uv32")]
+                 "extent")]
 
 
 def lib():
@@ -85,10 +85,11 @@ def lib():
         _lib.or_project.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         _lib.or_bin.argtypes = [i64, vp, vp, vp, i32, i32, vp, vp, i64]
         _lib.or_bin.restype = i64
-        _lib.or_render.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        _lib.or_render.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         _lib.or_render_brute.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
         _lib.or_render_pixels.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
-        _lib.or_render_bwd.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        _lib.or_render_bwd.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        _lib.or_grad_bounds.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, ctypes.c_double, vp, vp]
         _lib.or_project_bwd.argtypes = [i64] + [vp] * 18
         _lib.or_sh_basis.argtypes = [vp, i64, vp, vp]
     return _lib
@@ -116,8 +117,14 @@ class Params:
     lod_f: float = 2.0
     lod_Lmax: int = 5
     cull_enable: bool = False
-    tie_band: float = 1e-6
-    comp_band: float = 1e-4
+    # Precision of the renderer the decision flags allow for (compositing): its
+    # projected mean within prec_mean pixels, the coefficients of its exponent
+    # form A (x + k y)^2 + D y^2 within prec_conic (relative; k relative to
+    # |k| + sqrt(D / A)).  The GPU parity tests check the CUDA records against
+    # both bounds.  comp_band is a further log-space margin on every threshold.
+    prec_mean: float = 1e-6
+    prec_conic: float = 8e-6
+    comp_band: float = 2e-6
     eps_score: float = 1e-6
     vis_mass: float = 0.99
 
@@ -128,7 +135,7 @@ class Params:
         return ORParams(self.tile_w, self.tile_h, int(self.lod_enable), self.lod_Lmax, int(self.cull_enable),
                         (ctypes.c_double * 3)(*[f(b) for b in self.bg]), f(self.alpha_min), f(self.alpha_max),
                         f(self.T_min), f(self.dilation), f(self.znear), f(self.fov_clamp), f(self.lod_d0),
-                        f(self.lod_f), self.tie_band, self.comp_band)
+                        f(self.lod_f), self.prec_mean, self.prec_conic, self.comp_band)
 
 
 def camera_c(cam) -> ORCamera:
@@ -154,9 +161,13 @@ def gaussians64(g) -> dict:
 
 def grads_per_gaussian(grads: dict) -> dict:
     """The oracle's attribute-major gradients in the per-Gaussian row layout
-    of the inputs: mean (n, 3), log_scale (n, 3), quat (n, 4), sh (n, 16, 3)."""
-    return dict(mean=grads["mean"].T, log_scale=grads["log_scale"].T, quat=grads["quat"].T,
-                opacity_logit=grads["opacity_logit"], sh=grads["sh"].transpose(2, 0, 1))
+    of the inputs: mean (n, 3), log_scale (n, 3), quat (n, 4), sh (n, 16, 3);
+    with "bounds" (the same layout) where backward_view computed them."""
+    out = dict(mean=grads["mean"].T, log_scale=grads["log_scale"].T, quat=grads["quat"].T,
+               opacity_logit=grads["opacity_logit"], sh=grads["sh"].transpose(2, 0, 1))
+    if "_bounds" in grads:
+        out["bounds"] = dict(log_scale=grads["_bounds"]["log_scale"].T, quat=grads["_bounds"]["quat"].T)
+    return out
 
 
 def project(g64: dict, cam, params: Params, cull=None) -> dict:
@@ -166,7 +177,7 @@ def project(g64: dict, cam, params: Params, cull=None) -> dict:
                depth=np.zeros(n), depth32=np.zeros(n, np.float32), conic=np.zeros((n, 3)),
                opacity=np.zeros(n), rgb=np.zeros((n, 3)), clamp=np.zeros(n, np.uint8),
                radius=np.zeros(n, np.int32), rect=np.zeros((n, 4), np.int32), tiles=np.zeros(n, np.int32),
-               ldl32=np.zeros((n, 3)), uv32=np.zeros((n, 2)))
+               extent=np.zeros((n, 2)))
     po = ORProjOut(*[out[f[0]].ctypes.data for f in ORProjOut._fields_])
     cull_arr = None if cull is None else np.ascontiguousarray(cull, np.uint32)
     cam_c, par_c = camera_c(cam), params.c()
@@ -202,8 +213,7 @@ def render(proj: dict, bins, cam, params: Params) -> dict:
     lst = np.ascontiguousarray(lst, np.int32) if lst.size else np.zeros(1, np.int32)
     lib().or_render(ctypes.byref(camera_c(cam)), ctypes.byref(params.c()), n, _p(proj["uv"]), _p(proj["conic"]),
                     _p(proj["opacity"]), _p(proj["rgb"]), _p(tile_start), _p(lst), _p(out["image"]), _p(out["T"]),
-                    _p(out["n_contrib"]), _p(out["flags"]), _p(out["w"]), _p(out["a"]), _p(out["gcount"]),
-                    _p(proj.get("ldl32")), _p(proj.get("uv32")))
+                    _p(out["n_contrib"]), _p(out["flags"]), _p(out["w"]), _p(out["a"]), _p(out["gcount"]))
     return out
 
 
@@ -236,14 +246,37 @@ def render_pixels(proj: dict, pixels, lists, params: Params) -> dict:
 
 
 def render_bwd(proj: dict, bins, cam, params: Params, dL_dimage) -> dict:
+    """Gradients of the projected quantities; conic_abs holds, per Gaussian, the
+    sums of the magnitudes of the pixel terms of dL/dconic."""
     tile_start, lst = bins
     n = proj["status"].shape[0]
-    out = dict(uv=np.zeros((n, 2)), conic=np.zeros((n, 3)), opacity=np.zeros(n), rgb=np.zeros((n, 3)))
+    out = dict(uv=np.zeros((n, 2)), conic=np.zeros((n, 3)), opacity=np.zeros(n), rgb=np.zeros((n, 3)),
+               conic_abs=np.zeros((n, 3)))
     lst = np.ascontiguousarray(lst, np.int32) if lst.size else np.zeros(1, np.int32)
     lib().or_render_bwd(ctypes.byref(camera_c(cam)), ctypes.byref(params.c()), n, _p(proj["uv"]),
                         _p(proj["conic"]), _p(proj["opacity"]), _p(proj["rgb"]), _p(tile_start), _p(lst),
-                        _p(_d(dL_dimage)), _p(out["uv"]), _p(out["conic"]), _p(out["opacity"]), _p(out["rgb"]))
+                        _p(_d(dL_dimage)), _p(out["uv"]), _p(out["conic"]), _p(out["opacity"]), _p(out["rgb"]),
+                        _p(out["conic_abs"]))
     return out
+
+
+# FP32 error of a renderer's summed conic gradient, relative to the sum of the
+# magnitudes of its pixel terms: a budget of 64 roundings (the per-pixel chain
+# through alpha, T and dL/dalpha, and the tree sums over the pixels)
+EPS_CONIC_SUM = 64 * 2.0 ** -24
+
+
+def grad_bounds(g64: dict, proj: dict, cam, params: Params, pgrad: dict, bounds=None) -> dict:
+    """Accumulates, per Gaussian, how far an FP32 renderer's log-scale and
+    quaternion gradients can be from the exact ones through the conditioning of
+    the bilinear forms they are (see or_grad_bounds in gs_oracle.c)."""
+    n = g64["opacity_logit"].shape[0]
+    if bounds is None:
+        bounds = dict(log_scale=np.zeros((3, n)), quat=np.zeros((4, n)))
+    lib().or_grad_bounds(n, _p(g64["mean"]), _p(g64["log_scale"]), _p(g64["quat"]), _p(proj["status"]),
+                         ctypes.byref(camera_c(cam)), ctypes.byref(params.c()), _p(pgrad["conic_abs"]),
+                         EPS_CONIC_SUM, _p(bounds["log_scale"]), _p(bounds["quat"]))
+    return bounds
 
 
 def zero_grads(n: int) -> dict:
@@ -287,6 +320,7 @@ def backward_view(g64: dict, fwd: dict, cam, params: Params, dL_dimage, grads=No
     pg = render_bwd(fwd["proj"], fwd["bins"], cam, params, dL_dimage)
     project_bwd(g64, fwd["proj"], cam, params, pg, grads)
     grads["_projected"] = pg
+    grads["_bounds"] = grad_bounds(g64, fwd["proj"], cam, params, pg, grads.get("_bounds"))
     return grads
 
 
@@ -436,20 +470,36 @@ def prune_mass(s, mass: float = 0.99) -> np.ndarray:
     return visible_top_mass(s, mass)
 
 
-def prune_sample(s, expo, k: int) -> np.ndarray:
+def prune_sample(s, expo, k: int, with_ties: bool = False):
     """Pass 1: importance-weighted sampling of k Gaussians without replacement,
     with probability proportional to s at every draw.  Drawn as exponential
     clocks: Gaussian i fires at expo_i / s_i (expo_i ~ Exp(1), given), and the
     k earliest are kept (ties by lower index; s_i = 0 never fires before a
-    Gaussian with s > 0).  The times are taken in FP32, as the device takes them."""
-    s32 = np.asarray(s, np.float32)
-    e32 = np.asarray(expo, np.float32)
+    Gaussian with s > 0).  The times are exact quotients (FP64 of the FP32
+    inputs).
+
+    with_ties: also returns the Gaussians a renderer forming the times in FP32
+    may put on the other side of the cut: an FP32 quotient is within 2^-24 of
+    the exact one, so two times less than 2^-22 apart (relative) may swap; the
+    flagged set is every time within that of the k-th or (k+1)-th smallest when
+    those two are that close."""
+    s64 = np.asarray(s, np.float32).astype(np.float64)
+    e64 = np.asarray(expo, np.float32).astype(np.float64)
     with np.errstate(divide="ignore"):
-        t = np.where(s32 > 0, e32 / np.where(s32 > 0, s32, np.float32(1)), np.float32(np.inf)).astype(np.float32)
-    order = np.lexsort((np.arange(len(t)), t))
-    keep = np.zeros(len(t), bool)
+        t = np.where(s64 > 0, e64 / np.where(s64 > 0, s64, 1.0), np.inf)
+    n = len(t)
+    order = np.lexsort((np.arange(n), t))
+    keep = np.zeros(n, bool)
     keep[order[:k]] = True
-    return keep
+    if not with_ties:
+        return keep
+    tie = np.zeros(n, bool)
+    if 0 < k < n:
+        lo, hi = t[order[k - 1]], t[order[k]]
+        band = 2.0 ** -22
+        if np.isfinite(hi) and hi <= lo * (1 + 2 * band):
+            tie = (t >= lo * (1 - band)) & (t <= hi * (1 + band))
+    return keep, tie
 
 
 def successive_sampling_probs(s, k: int) -> np.ndarray:
@@ -534,23 +584,43 @@ def densify(g: dict, absgrad, denom, cvis, crad, noise, P: DensifyParams):
     return rows, {k: stack(1, k) for k in names}, {k: stack(2, k) for k in names}, kind
 
 
-def densify_kinds(opacity_logit, log_scale, absgrad, denom, cvis, crad, P: DensifyParams) -> np.ndarray:
+def densify_kinds(opacity_logit, log_scale, absgrad, denom, cvis, crad, P: DensifyParams, with_ties: bool = False):
     """The branch of every Gaussian: 0 removed (opacity < min_opacity), 1 kept,
-    2 cloned, 3 split.  The decisions are taken in FP32, the kernel's
-    precision, on quantities it forms the same way: the averaged gradient
-    absgrad / denom (0 without a view), phi = c^vis / (c^rad + eps), their
-    product against the threshold; opacity < min_opacity as the logit against
-    logit(min_opacity), the largest scale against dense_scale as the largest
-    log-scale against log(dense_scale) (both thresholds from FP64, rounded)."""
-    f = np.float32
-    absgrad, denom = np.asarray(absgrad, f), np.asarray(denom, np.int64)
-    grad = np.where(denom > 0, absgrad / np.where(denom > 0, denom, 1).astype(f), f(0)).astype(f)
-    phi = (np.asarray(cvis, np.int64).astype(f) / (np.asarray(crad, np.int64).astype(f) + f(P.eps))).astype(f)
-    score = (grad * phi).astype(f)
-    sel = score >= f(P.grad_threshold)
-    low = np.asarray(opacity_logit, f) < f(math.log(P.min_opacity / (1.0 - P.min_opacity)))
-    small = np.asarray(log_scale, f).max(axis=1) <= f(math.log(P.dense_scale))
-    return np.where(low, 0, np.where(~sel, 1, np.where(small, 2, 3))).astype(np.int64)
+    2 cloned, 3 split, decided in FP64 on the FP32 inputs: the averaged
+    gradient absgrad / denom (0 without a view) times phi = c^vis / (c^rad + eps)
+    against the threshold (Sec. 3.2); opacity below min_opacity, as the logit
+    against logit(min_opacity); the largest scale against dense_scale, as the
+    largest log-scale against log(dense_scale).
+
+    with_ties: also returns the Gaussians whose decision an FP32 renderer may
+    take the other way: a score within 10 x 2^-24 (relative) of the threshold
+    (its FP32 evaluation -- two quotients, a sum and a product -- is within
+    5 x 2^-24), a logit or largest log-scale within one float spacing of its
+    threshold (the thresholds held as floats)."""
+    f32 = lambda x: float(np.float32(x))
+    absgrad = np.asarray(absgrad, np.float32).astype(np.float64)
+    denom = np.asarray(denom, np.int64)
+    grad = np.where(denom > 0, absgrad / np.where(denom > 0, denom, 1), 0.0)
+    eps = f32(P.eps)
+    phi = np.asarray(cvis, np.int64) / (np.asarray(crad, np.int64) + eps)
+    score = grad * phi
+    thr = f32(P.grad_threshold)
+    sel = score >= thr
+    logit = np.asarray(opacity_logit, np.float32).astype(np.float64)
+    lthr = math.log(P.min_opacity / (1.0 - P.min_opacity))
+    low = logit < lthr
+    mls = np.asarray(log_scale, np.float32).astype(np.float64).max(axis=1)
+    sthr = math.log(P.dense_scale)
+    small = mls <= sthr
+    kind = np.where(low, 0, np.where(~sel, 1, np.where(small, 2, 3))).astype(np.int64)
+    if not with_ties:
+        return kind
+    u = 2.0 ** -24
+    sp = lambda x: float(np.spacing(np.float32(abs(x))))
+    tie = (np.abs(score - thr) <= 10 * u * thr) & ~low
+    tie |= np.abs(logit - lthr) <= sp(lthr)
+    tie |= (np.abs(mls - sthr) <= sp(sthr)) & sel & ~low
+    return kind, tie
 
 
 def _quat_to_rot(q):

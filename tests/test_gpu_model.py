@@ -33,7 +33,7 @@ def _bits_to_bool(bits, n):
 
 
 @pytest.mark.parametrize("n", [1, 31, 4097, 100_003])
-def test_prune_sample_matches_oracle_exactly(n):
+def test_prune_sample_matches_oracle(n):
     rng = np.random.default_rng(70 + n % 7)
     s = rng.gamma(0.5, 1.0, n).astype(np.float32)
     s[rng.uniform(size=n) < 0.1] = 0.0
@@ -43,7 +43,11 @@ def test_prune_sample_matches_oracle_exactly(n):
     keep = torch.zeros((n + 31) // 32, dtype=torch.int32, device="cuda")
     ws.prune_sample(torch.from_numpy(s).cuda(), torch.from_numpy(e).cuda(), k, keep)
     ws.sync_status()
-    assert np.array_equal(_bits_to_bool(keep, n), O.prune_sample(s, e, k))
+    got = _bits_to_bool(keep, n)
+    ref, tie = O.prune_sample(s, e, k, with_ties=True)
+    # exact outside the Gaussians whose FP32 firing time may cross the cut
+    assert got.sum() == k and tie.sum() <= 4
+    assert np.array_equal(got[~tie], ref[~tie])
 
 
 @pytest.mark.parametrize("n", [17, 5000, 300_001])
@@ -114,6 +118,10 @@ def test_densify_matches_oracle():
                 m={k: getattr(model.m, k).cpu().numpy() for k in NAMES},
                 v={k: getattr(model.v, k).cpu().numpy() for k in NAMES})
     ref, rm, rv, kind = O.densify(rows, absgrad, denom, cvis, crad, noise, P)
+    # the seeded inputs put no decision within an FP32 renderer's error of its
+    # threshold, so every branch must agree
+    _, tie = O.densify_kinds(g.opacity_logit, g.log_scale, absgrad, denom, cvis, crad, P, with_ties=True)
+    assert not tie.any(), np.nonzero(tie)[0][:10]
     assert all((kind == c).sum() > 100 for c in range(4)), np.bincount(kind)
     out = dst.head(int(n_out.item()))
     assert out.n == len(ref["opacity_logit"])

@@ -1,10 +1,12 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
 Bars: bit-exact for integer work (active records, tile rectangles and counts,
-sorted per-tile lists, n_contrib); images within 1e-4 max-abs; gradients and
-importance scores within 1e-3 relative.  Decisions that the oracle flags as
-lying within its tie band of a threshold are excluded from exact comparison
-and must stay rare.
+depth keys, sorted per-tile lists, n_contrib); images within 1e-4 max-abs;
+gradients and importance scores within 1e-3 relative.  The oracle takes every
+decision in FP64 and flags those within an FP32 renderer's error bound of
+their boundary: a flagged projection decision must be one of the outcomes the
+flag allows and is then taken into the oracle's projection; a flagged
+compositing decision excludes its pixel.  Both stay rare.
 """
 import math
 
@@ -15,12 +17,11 @@ import torch
 import oracle as O
 from paper_2605_13794_gb300 import binding as B
 from paper_2605_13794_gb300 import synth
-from tests.gpu_helpers import (GpuRun, assert_grad_close, assert_param_grad_close, capacity_for, footprint_power_err,
-                               gpu_params, grads_to_host, record_mean, unpack_rect)
+from tests.gpu_helpers import (GpuRun, assert_grad_close, assert_gaussian_grads_close, assert_param_grad_close, assert_record_precision,
+                               capacity_for, footprint_power_err, gpu_params, grads_to_host, oracle_view_matched,
+                               unpack_rect)
 
 pytestmark = pytest.mark.gpu
-
-GEOM_TIES = O.TIE_LOD | O.TIE_NEAR | O.TIE_DET | O.TIE_RADIUS | O.TIE_RECT
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -32,60 +33,50 @@ def _built():
 
 
 def _compare_view(run: GpuRun, c, g64, cam, P, cull=None, check_image=True):
-    """Compares one camera of a GPU run with the oracle; returns the oracle forward."""
-    fwd = O.forward_view(g64, cam, P, cull)
+    """Compares one camera of a GPU run with the oracle; returns the oracle forward.
+
+    Projection decisions (active set, rectangles, tile counts, depth keys) are
+    exact outside the oracle's tie flags; a flagged decision must be one the
+    flag allows and is then taken into the oracle's projection, so binning,
+    image and everything downstream compare exactly or within tolerance."""
+    fwd = oracle_view_matched(O, run, c, g64, cam, P, cull)
     pr = fwd["proj"]
-    n = g64["opacity_logit"].shape[0]
-    tie = (pr["tie"] & GEOM_TIES) != 0
-    ora_active = pr["status"] == O.ACTIVE
     recs = run.records_of(c)
-    gpu_active = np.zeros(n, bool)
-    gpu_active[list(recs.keys())] = True
-    mism = np.nonzero(gpu_active != ora_active)[0]
-    assert tie[mism].all(), f"active-set mismatch outside tie bands: {mism[~tie[mism]][:10]}"
-    assert tie.sum() <= max(3, 1e-3 * n)
-    # a tie-band Gaussian whose decisions still agree is compared like any other
-    agree = gpu_active & ora_active
-    tie_both = np.nonzero(agree & tie)[0]
-    if len(tie_both):
-        tr = np.array([recs[i] for i in tie_both], np.int64)
-        same = (unpack_rect(run.rect[tr]) == pr["rect"][tie_both]).all(1)
-        tie[tie_both[same]] = False
-    tie[np.nonzero(~gpu_active & ~ora_active)[0]] = False
-    both = np.nonzero(gpu_active & ora_active & ~tie)[0]
+    both = np.nonzero(pr["status"] == O.ACTIVE)[0]
+    assert sorted(recs.keys()) == both.tolist()
     ridx = np.array([recs[i] for i in both], np.int64)
-    # integer parity: rectangles, tiles touched, depth key bits
-    assert np.array_equal(unpack_rect(run.rect[ridx]), pr["rect"][both])
     assert np.array_equal(run.tt[ridx].astype(np.int64), pr["tiles"][both].astype(np.int64))
-    assert np.array_equal(run.depth_bits[ridx], pr["depth32"][both].view(np.uint32))
     # continuous projected values: the mean is held to about 48 bits (u + u_lo);
-    # the conic, as A (dx + k dy)^2 + D dy^2, is checked through the exponent it
-    # gives on each footprint's 1- and 3-sigma ellipses
-    np.testing.assert_allclose(record_mean(run.rd0[ridx], run.rd2[ridx]), pr["uv"][both], rtol=0, atol=1e-6)
+    # the conic as A (dx + k dy)^2 + D dy^2 within the precision the compositing
+    # flags allow for, and through the exponent it gives on each footprint's
+    # 1- and 3-sigma ellipses
+    assert_record_precision(run, ridx, pr, both, P)
     perr = footprint_power_err(run.rd0[ridx], run.rd1[ridx], run.rd2[ridx], pr["conic"][both], pr["uv"][both])
-    assert perr.max() <= 2e-4, perr.max()
+    assert perr.max(initial=0.0) <= 2e-4, perr.max()
     np.testing.assert_allclose(run.rd1[ridx, 1], pr["opacity"][both], rtol=1e-6, atol=1e-7)
     rgb = np.concatenate([run.rd1[ridx, 2:4], run.rd2[ridx, :1]], 1)
     np.testing.assert_allclose(rgb, pr["rgb"][both], rtol=0, atol=2e-5)
-    # sorted per-tile lists (ties removed from both sides)
+    # sorted per-tile lists: bit-exact, against the oracle's binning of its own
+    # decisions and against its binning of the GPU's own FP32 records
+    # (rectangle and depth key as the GPU computed them)
     ts, lst = fwd["bins"]
     glists = run.tile_lists(c)
-    tied = set(np.nonzero(tie)[0].tolist())
     for t, gl in enumerate(glists):
-        ol = lst[ts[t]:ts[t + 1]]
-        if tied:
-            gl = [x for x in gl.tolist() if x not in tied]
-            ol = [x for x in ol.tolist() if x not in tied]
-        assert np.array_equal(np.asarray(gl, np.int64), np.asarray(ol, np.int64)), f"tile {t} list differs"
+        assert np.array_equal(gl, lst[ts[t]:ts[t + 1]].astype(np.int64)), f"tile {t} list differs"
+    n = pr["status"].shape[0]
+    own = dict(status=np.full(n, O.EMPTY, np.int8), rect=np.zeros((n, 4), np.int32),
+               depth32=np.zeros(n, np.float32), tiles=np.zeros(n, np.int32))
+    own["status"][both] = O.ACTIVE
+    own["rect"][both] = unpack_rect(run.rect[ridx])
+    own["depth32"][both] = run.depth_bits[ridx].view(np.float32)
+    own["tiles"][both] = run.tt[ridx]
+    ts2, lst2 = O.bin_tiles(own, cam, P)
+    for t, gl in enumerate(glists):
+        assert np.array_equal(gl, lst2[ts2[t]:ts2[t + 1]].astype(np.int64)), f"tile {t}: GPU binning of its own records"
     if not check_image:
         return fwd
-    # image: 1e-4 max-abs outside flagged pixels and outside tiles of tied Gaussians
+    # image: 1e-4 max-abs outside flagged pixels
     ok = fwd["flags"] == 0
-    if tied:
-        tx, _ = O.tiles_of(cam, P)
-        for i in tied:
-            x0, y0, x1, y1 = pr["rect"][i]
-            ok[max(0, y0 - 1) * P.tile_h:(y1 + 1) * P.tile_h, max(0, x0 - 1) * P.tile_w:(x1 + 1) * P.tile_w] = False
     assert ok.mean() > 0.99
     img = run.image(c)
     err = np.abs(img - fwd["image"]).max(axis=0)
@@ -370,8 +361,7 @@ def test_backward_parity(seed):
     dL = np.random.default_rng(seed + 100).standard_normal((3, cam.height, cam.width))
     gg = _backward(run, dL)
     og = O.grads_per_gaussian(O.backward_view(g64, fwd, cam, P, dL))
-    for k in ("mean", "log_scale", "quat", "opacity_logit", "sh"):
-        assert_param_grad_close(k, gg[k], og[k])
+    assert_gaussian_grads_close(gg, og)
 
 
 def test_backward_fragment_counts_and_kernel_timing():
@@ -427,8 +417,7 @@ def test_backward_multi_camera_accumulates():
         fwd = _compare_view(run, c, g64, cam, P)
         O.backward_view(g64, fwd, cam, P, dLs[c], og)
     og = O.grads_per_gaussian(og)
-    for k in ("mean", "log_scale", "quat", "opacity_logit", "sh"):
-        assert_param_grad_close(k, gg[k], og[k])
+    assert_gaussian_grads_close(gg, og)
 
 
 def test_deterministic_reruns():
@@ -475,7 +464,27 @@ def _check_visible_set(vis_gpu, w_ref, vis_mass):
     assert not np.any(vis_gpu & (w_ref == 0))
 
 
+def _check_cull_against_own_w(vis_gpu, w_gpu, vis_mass):
+    """The Cull column is the 99 %-mass selection of the GPU's own w: the GPU's
+    fixed-point prefix sums and the oracle's FP64 ones may put the cut one
+    place apart, never more."""
+    w64 = np.asarray(w_gpu, np.float64)
+    mine = O.visible_top_mass(w64, vis_mass)
+    pos = np.nonzero(w64 > 0)[0]
+    order = pos[np.lexsort((pos, -w64[pos]))]
+    k = int(mine.sum())
+    diff = set(np.nonzero(vis_gpu != mine)[0].tolist())
+    if len(order):
+        assert diff <= {int(order[k - 1]), int(order[min(k, len(order) - 1)])} and len(diff) <= 1, sorted(diff)[:10]
+    else:
+        assert not diff
+
+
 def test_importance_parity():
+    """w and a per view, s, c^rad, c^vis and the Cull columns against the
+    oracle.  A Gaussian on no flagged pixel (gcount 0) has w within the
+    gradient rule and a exact; on a flagged pixel an undecided fragment may
+    move a by one and w by one fragment's alpha T (< 1e-2), per such pixel."""
     g = synth.plain_scene(6000, seed=31)
     cams = [synth.plain_camera(), synth.plain_camera(160, 200, 200.0)]
     P = O.Params()
@@ -484,26 +493,31 @@ def test_importance_parity():
     imp = _importance(run, g.n, len(cams))
     acc = O.new_importance(g.n)
     vm = float(np.float32(P.vis_mass))
-    view_a = []
+    gcount = np.zeros(g.n, np.int64)
+    bound = np.zeros(g.n)
     for c, cam in enumerate(cams):
         fwd = _compare_view(run, c, g64, cam, P, check_image=False)
-        view_a.append(fwd["a"])
-        view = O.importance_update(acc, fwd["w"], fwd["a"], fwd["proj"], vm, float(np.float32(P.eps_score)))
-        # Gaussians with a flagged pixel in their footprint may differ by one fragment
-        assert_grad_close(f"w[{c}]", imp["w"][c], fwd["w"])
-        a_diff = np.nonzero(imp["a"][c] != fwd["a"].astype(np.int64))[0]
-        assert len(a_diff) <= max(2, int(2e-3 * g.n)), a_diff[:10]
+        O.importance_update(acc, fwd["w"], fwd["a"], fwd["proj"], vm, float(np.float32(P.eps_score)))
+        cnt = fwd["gcount"].astype(np.int64)
+        gcount += cnt
+        free = cnt == 0
+        wg, ag, ao = imp["w"][c], imp["a"][c].astype(np.int64), fwd["a"].astype(np.int64)
+        assert_grad_close(f"w[{c}]", np.where(free, wg, 0.0), np.where(free, fwd["w"], 0.0))
+        assert np.array_equal(ag[free], ao[free])
+        assert np.all(np.abs(ag - ao) <= cnt)
+        assert np.all(np.abs(wg - fwd["w"]) <= 1e-3 * np.abs(fwd["w"]) + 1e-2 * cnt + 1e-9)
+        # what the undecided fragments of this view can move s_i = sum w / (a + eps) by
+        cf = cnt.astype(np.float64)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            hi = np.where(ao - cnt > 0, (fwd["w"] + 1e-2 * cf) / (ao - cnt), np.inf) - np.where(ao > 0, fwd["w"] / np.maximum(ao, 1), 0)
+        bound += np.where(cnt > 0, hi, 0.0)
         vis_gpu = ~synth.unpack_bits(imp["cull"][c], g.n)
         _check_visible_set(vis_gpu, fwd["w"], vm)
-        # with identical w the sets would be identical; FP32 w moves only near-cut entries
-        assert (vis_gpu != view["cvis"]).sum() <= 2
-    # s_i = sum w/(a+eps): a Gaussian whose pixel count moved at a flagged alpha_min
-    # decision changes by ~1/a, so it is compared only where every view's a agrees
-    a_ok = np.ones(g.n, bool)
-    for c, cam in enumerate(cams):
-        a_ok &= imp["a"][c] == np.rint(view_a[c]).astype(np.int64)
-    assert (~a_ok).sum() <= max(2, int(4e-3 * g.n))
-    assert_grad_close("s", imp["s"][a_ok], acc["s"][a_ok])
+        _check_cull_against_own_w(vis_gpu, wg, vm)
+    free = gcount == 0
+    assert free.sum() > 0.75 * (acc["crad"] > 0).sum()
+    assert_grad_close("s", np.where(free, imp["s"], 0.0), np.where(free, acc["s"], 0.0))
+    assert np.all(np.abs(imp["s"] - acc["s"]) <= 1e-3 * acc["s"] + bound + 1e-9)
     assert np.array_equal(imp["crad"], acc["crad"])
     assert np.abs(imp["cvis"] - acc["cvis"]).max() <= 1
 
@@ -557,7 +571,7 @@ def test_scale_regulariser_parity():
     vis = pr["status"] == O.ACTIVE
     ref_val, ref_g = O.scale_regulariser(g.log_scale.T.astype(np.float64), vis, beta=10.0)
     assert abs(val.item() - ref_val) <= 1e-5 * ref_val
-    assert_param_grad_close("log_scale", grads.log_scale.double().cpu().numpy(), ref_g.T)
+    assert_grad_close("log_scale", grads.log_scale.double().cpu().numpy(), ref_g.T)
 
 
 def test_fused_backward_adam_matches_unfused():
