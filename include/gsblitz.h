@@ -28,6 +28,9 @@
  *     frees or retains them beyond the call.
  *   - Calls are asynchronous on the given stream and allocate nothing: all
  *     scratch lives in a gs_workspace created once by gs_workspace_create.
+ *     The one exception is gs_visible_set_static, which takes no workspace:
+ *     its scratch is a fixed device array of the library, and its kernel
+ *     errors come back through its own error_out word, not gs_sync_status.
  *     A NULL stream means the legacy default stream.
  *   - A workspace is not thread-safe on the host: the calls on one workspace
  *     are issued from one thread at a time (their GPU work may still overlap
@@ -432,16 +435,38 @@ int gs_count_views(gs_workspace *ws, uint32_t *counts, gs_stream stream);
  *   w        [n] device: the view's per-Gaussian alpha-weights (gs_importance's w)
  *   cull_out [ceil(n/32)] device, written: bit = 1 - c^vis (top vis_mass of the w mass)
  *   cvis_accum [n] device, += 1 where visible; may be NULL
+ *   error_out [1] device, may be NULL: written with the call's device error,
+ *            a gs_status cast to uint32_t (0 = GS_OK; GS_ERR_TIMEOUT if a
+ *            bounded wait of the sort gave up, and then every Gaussian is
+ *            left culled)
+ * The selection is gs_importance's own (the same stable sort and exact
+ * fixed-point prefix sums), so the column equals gs_importance's bit for bit.
  * n <= 2^20: the scratch (about 24.6 MB) is one fixed device array of the
  * library, which every GPU that loads its module keeps until the process
  * exits; larger n is rejected with GS_ERR_CAPACITY.  The first call on a
  * device looks the array's device address up (cudaGetSymbolAddress, with that
  * device current), so make that first call before any stream capture.  All
  * calls share the array: calls whose work overlaps on the GPU race and must be
- * serialised by the caller.  Asynchronous on stream; kernel-side waits are
- * bounded and leave the output undefined if one gives up. */
+ * serialised by the caller.  Asynchronous on stream. */
 int gs_visible_set_static(const float *w, int64_t n, float vis_mass, uint32_t *cull_out, uint32_t *cvis_accum,
-                          gs_stream stream);
+                          uint32_t *error_out, gs_stream stream);
+
+/* Measured throughput of the arithmetic pipes the compositing kernels are
+ * bound by, for roofline fractions.  The paper has no counterpart: this is a
+ * measurement utility.  Runs three short kernels (FP32 FMA chains, the same
+ * as packed FP32x2 FMA, and ex2.approx) on every SM of the current device,
+ * times each with CUDA events on `stream` and synchronises with it.
+ *   fp32_fma_flops    FLOP/s of scalar FFMA (2 per FMA)
+ *   fp32x2_fma_flops  FLOP/s of packed FP32x2 FMA (4 per instruction)
+ *   ex2_per_s         ex2.approx results per second (special-function unit)
+ *   sms               the device's multiprocessor count */
+typedef struct {
+    double fp32_fma_flops;
+    double fp32x2_fma_flops;
+    double ex2_per_s;
+    int32_t sms;
+} gs_alu_peak;
+int gs_alu_peaks(gs_alu_peak *out, gs_stream stream);
 
 /* Kernel timing, for measurement.  While on, each launch of the timed kernels
  * below is bracketed by a CUDA event pair recorded on the stream it is launched

@@ -34,7 +34,7 @@ EXPORTS = ("gs_default_params", "gs_last_error", "gs_workspace_create", "gs_work
            "gs_prune_sample", "gs_prune_mass", "gs_compact", "gs_densify", "gs_count_views", "gs_adam_lazy_enable",
            "gs_adam_lazy_disable", "gs_adam_flush", "gs_kernel_timing", "gs_kernel_time",
            "gs_render_fwd_importance", "gs_graph_capture_begin", "gs_graph_capture_end", "gs_graph_launch",
-           "gs_graph_destroy")
+           "gs_graph_destroy", "gs_alu_peaks")
 
 # Cull modes of RenderParams.cull_enable (include/gsblitz.h)
 GS_CULL_OFF, GS_CULL_DROP, GS_CULL_MARK = 0, 1, 2
@@ -99,6 +99,11 @@ class GSCounts(ctypes.Structure):
                 ("composited", ctypes.c_int64)]
 
 
+class GSAluPeak(ctypes.Structure):
+    _fields_ = [("fp32_fma_flops", ctypes.c_double), ("fp32x2_fma_flops", ctypes.c_double),
+                ("ex2_per_s", ctypes.c_double), ("sms", ctypes.c_int32)]
+
+
 class GSAdamGroup(ctypes.Structure):
     _fields_ = [("param", ctypes.c_void_p), ("grad", ctypes.c_void_p), ("m", ctypes.c_void_p),
                 ("v", ctypes.c_void_p), ("n", ctypes.c_int64), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
@@ -145,7 +150,8 @@ def lib() -> ctypes.CDLL:
         L.gs_render_bwd_adam.argtypes = [vp, vp, vp, vp, vp, vp, f32, f32, f32, i32, vp, f32, vp, vp]
         L.gs_render_bwd_compact.argtypes = [vp, vp, vp, vp, f32, vp, vp]
         L.gs_adam_step_compact.argtypes = [vp, vp, vp, vp, vp, f32, f32, f32, i32, vp]
-        L.gs_visible_set_static.argtypes = [vp, i64, f32, vp, vp, vp]
+        L.gs_visible_set_static.argtypes = [vp, i64, f32, vp, vp, vp, vp]
+        L.gs_alu_peaks.argtypes = [vp, vp]
         L.gs_importance.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
         L.gs_photometric_loss.argtypes = [vp, vp, vp, i32, i32, i32, ctypes.c_float, vp, vp, vp]
         L.gs_adam_step.argtypes = [vp, i32, i32, vp]
@@ -315,6 +321,9 @@ class Workspace:
         self._ws = ctypes.c_void_p()
         _check(lib().gs_workspace_create(ctypes.byref(self.cap), ctypes.byref(self._ws)))
         self.cams = []
+        # forwards started on this workspace; a differentiable render remembers
+        # the one its backward belongs to
+        self.generation = 0
 
     @staticmethod
     def bytes_for(**cap) -> int:
@@ -339,6 +348,7 @@ class Workspace:
         self.tile = (params.tile_w, params.tile_h)
         self._g = g  # keep the parameter tensors alive until the backward
         gc, pc = g.c(), params.c()
+        self.generation += 1
         _check(lib().gs_preprocess(self._ws, ctypes.byref(gc), arr, len(cams), _ptr(cull), ctypes.byref(pc),
                                    _stream(stream)))
 
@@ -355,6 +365,7 @@ class Workspace:
         """gs_preprocess with the cameras of the last upload (graph-capturable)."""
         self._g = g
         gc, pc = g.c(), params.c()
+        self.generation += 1
         _check(lib().gs_preprocess_uploaded(self._ws, ctypes.byref(gc), _ptr(cull), ctypes.byref(pc),
                                             _stream(stream)))
 
@@ -519,11 +530,12 @@ def _memcpy_d2h(dst: int, src: int, nbytes: int):
         raise RuntimeError(f"cudaMemcpy failed with {rc}")
 
 
-def visible_set_static(w, vis_mass, cull_out, cvis_accum=None, stream=None):
+def visible_set_static(w, vis_mass, cull_out, cvis_accum=None, error_out=None, stream=None):
     """Cull column of one view from its per-Gaussian w without any allocation
-    (fixed library scratch, n <= 2^20; see gs_visible_set_static)."""
+    (fixed library scratch, n <= 2^20; see gs_visible_set_static).  error_out:
+    an int32 device tensor of one element receiving the device error code."""
     _check(lib().gs_visible_set_static(_ptr(w), int(w.numel()), float(vis_mass), _ptr(cull_out), _ptr(cvis_accum),
-                                       _stream(stream)))
+                                       _ptr(error_out), _stream(stream)))
 
 
 class Graph:
@@ -572,6 +584,14 @@ class Graph:
             pass
 
 
+def alu_peaks(stream=None) -> dict:
+    """Measured FP32 FMA (scalar, FP32x2) FLOP/s and ex2 results/s of the
+    current device (gs_alu_peaks; synchronises)."""
+    out = GSAluPeak()
+    _check(lib().gs_alu_peaks(ctypes.byref(out), _stream(stream)))
+    return {f[0]: getattr(out, f[0]) for f in GSAluPeak._fields_}
+
+
 def kernel_launches() -> int:
     """Kernels the library has launched so far in this process."""
     return int(lib().gs_kernel_launches())
@@ -587,7 +607,12 @@ def adam_step(groups, step: int, stream=None):
 
 class RenderFunction(torch.autograd.Function):
     """Differentiable render through the library: forward = preprocess +
-    bin_sort + render_fwd, backward = render_bwd (the hand-written adjoint)."""
+    bin_sort + render_fwd, backward = render_bwd (the hand-written adjoint).
+
+    The backward reads the binning, T_final and n_contrib the forward left in
+    the workspace; a later forward on the same workspace replaces them, so the
+    backward checks the workspace's forward generation and raises if another
+    forward ran in between."""
 
     @staticmethod
     def forward(ctx, ws, cams, params, cull, lod, mean, log_scale, quat, opacity_logit, sh):
@@ -599,12 +624,15 @@ class RenderFunction(torch.autograd.Function):
         rgb = torch.empty(3 * P, device=mean.device, dtype=torch.float32)
         T = torch.empty(P, device=mean.device, dtype=torch.float32)
         ws.render_fwd(rgb, T)
-        ctx.ws, ctx.g = ws, g
+        ctx.ws, ctx.g, ctx.generation = ws, g, ws.generation
         ctx.mark_non_differentiable(T)
         return rgb, T
 
     @staticmethod
     def backward(ctx, dL_drgb, dL_dT):
+        if ctx.ws.generation != ctx.generation:
+            raise RuntimeError("render backward: the workspace has run another forward since this render's; "
+                               "its binning and per-pixel state are gone (use one workspace per pending backward)")
         g = ctx.g
         grads = g.zeros_like()
         ctx.ws.render_bwd(g, dL_drgb.contiguous(), grads, accumulate=False)

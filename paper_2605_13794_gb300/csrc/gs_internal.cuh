@@ -59,6 +59,7 @@ __device__ __forceinline__ float rcp_approx(float x)
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;          // keys per thread in a radix pass (default)
 constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kScanTile = 4096;         // items per block of the selection's prefix sums
 constexpr int kSlotFloats = 9;          // per (record, tile) gradient slot: du dv dA dB dC do dr dg db
 constexpr int kGradRow = 59;            // parameters per Gaussian: mean 3, log-scale 3, quat 4, opacity 1, SH 48
 constexpr unsigned long long kSpinLimit = 1ull << 22;
@@ -67,6 +68,7 @@ constexpr int kMaxLod = 15;             // largest supported L_max
 // Error sites recorded next to the error word (which kernel gave up).
 enum ErrorSite {
     kSitePreprocess = 1, kSiteEmit = 2, kSiteRadix = 3, kSiteSelect = 4, kSiteScanF64 = 5, kSiteModel = 6,
+    kSiteRender = 7,
 };
 
 // Device counters of one workspace.

@@ -18,6 +18,11 @@
 // any stream capture.  All calls share the array: calls whose work overlaps on
 // the GPU (other streams, other threads) race and must be serialised by the
 // caller.  Every value the selection reads is written earlier in the same call.
+// The selection is gs_importance's, operation for operation: the same stable
+// sort of w descending (ties toward the lower index) and the same exact 64-bit
+// fixed-point prefix sums, so the two give the same Cull column bit for bit.
+// A device-side failure (a bounded wait of the sort that gave up) leaves every
+// Gaussian culled and is reported through the caller's error word.
 #include <mutex>
 #include <stdio.h>
 #include <string.h>
@@ -30,12 +35,15 @@ cudaError_t launch_radix_sort_scratch(cudaStream_t st, uint32_t *keys[2], uint32
                                       const unsigned long long *count, unsigned long long cap, int bits,
                                       bool vals_identity, uint32_t *status, uint32_t *hist, uint32_t *off,
                                       DevCounters *ctr, int &out_buf);
-cudaError_t launch_mass_scan(cudaStream_t st, const uint32_t *sorted, const float *w, double *bsum, double *cum,
-                             const DevCounters *ctr, unsigned long long cap);
+cudaError_t launch_mass_scan_fixed(cudaStream_t st, const uint32_t *sorted, const float *w, unsigned long long *bsum,
+                                   unsigned long long *cum, const DevCounters *ctr, unsigned long long cap);
 
 constexpr long long kVisMaxGaussians = 1ll << 20;
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-constexpr size_t kVisBlocks = (size_t)(kVisMaxGaussians + kSortTile - 1) / kSortTile;
+// the sort's look-back status words are sized by its key blocks, the scan's block
+// sums by its item blocks: each from its own constant
+constexpr size_t kVisSortBlocks = (size_t)(kVisMaxGaussians + kSortTile - 1) / kSortTile;
+constexpr size_t kVisScanBlocks = (size_t)(kVisMaxGaussians + kScanTile - 1) / kScanTile;
 // layout of the scratch array
 constexpr size_t kOffCtr = 0;
 constexpr size_t kOffKey0 = align256(kOffCtr + sizeof(DevCounters));
@@ -44,8 +52,8 @@ constexpr size_t kOffVal0 = align256(kOffKey1 + 4 * (size_t)kVisMaxGaussians);
 constexpr size_t kOffVal1 = align256(kOffVal0 + 4 * (size_t)kVisMaxGaussians);
 constexpr size_t kOffCum = align256(kOffVal1 + 4 * (size_t)kVisMaxGaussians);
 constexpr size_t kOffBsum = align256(kOffCum + 8 * (size_t)kVisMaxGaussians);
-constexpr size_t kOffStatus = align256(kOffBsum + 8 * (kVisBlocks + 1));
-constexpr size_t kOffHist = align256(kOffStatus + 4 * (kVisBlocks * 256 + 1));
+constexpr size_t kOffStatus = align256(kOffBsum + 8 * (kVisScanBlocks + 1));
+constexpr size_t kOffHist = align256(kOffStatus + 4 * (kVisSortBlocks * 256 + 1));
 constexpr size_t kOffOff = align256(kOffHist + 4 * 1024);
 constexpr size_t kVisScratchBytes = align256(kOffOff + 4 * 1024);
 
@@ -74,20 +82,27 @@ __global__ void vis_cull_init_kernel(uint32_t *cull, long long words, long long 
     cull[k] = bits >= 32 ? 0xffffffffu : ((1u << bits) - 1u);
 }
 
-__global__ void vis_apply_kernel(const float *w, long long n, const uint32_t *sorted, const double *cum,
-                                 float vis_mass, uint32_t *cull, uint32_t *cvis)
+__global__ void vis_apply_kernel(const float *w, long long n, const uint32_t *sorted, const unsigned long long *cum,
+                                 float vis_mass, uint32_t *cull, uint32_t *cvis, const DevCounters *ctr)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const long long k = (long long)blockIdx.x * 256 + threadIdx.x;
-    if (k >= n) return;
+    if (k >= n || ctr->error != 0) return; // a failed sort: every Gaussian stays culled
     const uint32_t g = sorted[k];
     if (!(w[g] > 0.f)) return;
-    const double total = cum[n - 1];
-    const double excl = k > 0 ? cum[k - 1] : 0.0;
-    if (excl < (double)vis_mass * total) {
+    const unsigned long long total = cum[n - 1];
+    const unsigned long long excl = k > 0 ? cum[k - 1] : 0ull;
+    if ((double)excl < (double)vis_mass * (double)total) {
         atomicAnd(&cull[g >> 5], ~(1u << (g & 31)));
         if (cvis) atomicAdd(&cvis[g], 1u);
     }
+}
+
+// The call's device error word (0: none) for the caller.
+__global__ void vis_status_kernel(const DevCounters *ctr, uint32_t *error_out)
+{
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
+    if (threadIdx.x == 0) *error_out = (uint32_t)ctr->error;
 }
 
 namespace {
@@ -107,7 +122,7 @@ int vis_fail(int code, const char *fmt, long long a = 0, long long b = 0)
 extern "C" {
 
 int gs_visible_set_static(const float *w, int64_t n, float vis_mass, uint32_t *cull_out, uint32_t *cvis_accum,
-                          gs_stream stream)
+                          uint32_t *error_out, gs_stream stream)
 {
     using namespace gs;
     if (!w || !cull_out) return vis_fail(GS_ERR_INVALID_ARG, "gs_visible_set_static: NULL w or cull_out");
@@ -118,7 +133,11 @@ int gs_visible_set_static(const float *w, int64_t n, float vis_mass, uint32_t *c
                         (long long)n, kVisMaxGaussians);
     if (!(vis_mass > 0.f) || vis_mass > 1.f)
         return vis_fail(GS_ERR_INVALID_ARG, "gs_visible_set_static: vis_mass must be in (0, 1]");
-    if (n == 0) return GS_OK;
+    if (n == 0) {
+        if (error_out && cudaMemsetAsync(error_out, 0, sizeof(uint32_t), (cudaStream_t)stream) != cudaSuccess)
+            return vis_fail(GS_ERR_CUDA, "gs_visible_set_static: clearing error_out failed");
+        return GS_OK;
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= 256)
@@ -144,8 +163,8 @@ int gs_visible_set_static(const float *w, int64_t n, float vis_mass, uint32_t *c
                          reinterpret_cast<uint32_t *>(scratch + kOffKey1)};
     uint32_t *vals[2] = {reinterpret_cast<uint32_t *>(scratch + kOffVal0),
                          reinterpret_cast<uint32_t *>(scratch + kOffVal1)};
-    double *cum = reinterpret_cast<double *>(scratch + kOffCum);
-    double *bsum = reinterpret_cast<double *>(scratch + kOffBsum);
+    unsigned long long *cum = reinterpret_cast<unsigned long long *>(scratch + kOffCum);
+    unsigned long long *bsum = reinterpret_cast<unsigned long long *>(scratch + kOffBsum);
     uint32_t *status = reinterpret_cast<uint32_t *>(scratch + kOffStatus);
     uint32_t *hist = reinterpret_cast<uint32_t *>(scratch + kOffHist);
     uint32_t *off = reinterpret_cast<uint32_t *>(scratch + kOffOff);
@@ -158,10 +177,15 @@ int gs_visible_set_static(const float *w, int64_t n, float vis_mass, uint32_t *c
     int ob = 0;
     if ((e = launch_radix_sort_scratch(st, keys, vals, &ctr->n_records, (unsigned long long)n, 32, true, status, hist,
                                        off, ctr, ob)) != cudaSuccess ||
-        (e = launch_mass_scan(st, vals[ob], w, bsum, cum, ctr, (unsigned long long)n)) != cudaSuccess)
+        (e = launch_mass_scan_fixed(st, vals[ob], w, bsum, cum, ctr, (unsigned long long)n)) != cudaSuccess)
         return vis_fail(GS_ERR_CUDA, "gs_visible_set_static: a kernel launch failed");
-    launch_pdl(vis_apply_kernel, blocks, 256, 0, st, w, n, vals[ob], cum, vis_mass, cull_out, cvis_accum);
+    launch_pdl(vis_apply_kernel, blocks, 256, 0, st, w, n, vals[ob], cum, vis_mass, cull_out, cvis_accum,
+               (const DevCounters *)ctr);
     note_launch();
+    if (error_out) {
+        launch_pdl(vis_status_kernel, 1, 32, 0, st, (const DevCounters *)ctr, error_out);
+        note_launch();
+    }
     if ((e = cudaGetLastError()) != cudaSuccess)
         return vis_fail(GS_ERR_CUDA, "gs_visible_set_static: a kernel launch failed");
     return GS_OK;

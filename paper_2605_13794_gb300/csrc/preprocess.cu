@@ -889,7 +889,9 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, const Ca
             for (int p = 0; p < 3; p++)
                 for (int c = 0; c < 3; c++) M[p][c] = Q[p][c] * s[c];
             const float o = 1.f / (1.f + expf(-a.g.opacity_logit[i]));
-            float gM[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}; // dL/dM, M = Q diag(s)
+            // H[a][b] = w_a^T G w_b summed over the records, w_k = C v_k: the scale and
+            // rotation gradients below are these bilinear forms (see after the loop)
+            float H00 = 0.f, H11 = 0.f, H22 = 0.f, H01 = 0.f, H02 = 0.f, H12 = 0.f;
             float absacc = 0.f;
             for (unsigned long long r = r0; r < r1; r++) {
                 if (a.rd2[r].w != 0.f) continue; // marked culled: composited nowhere
@@ -933,14 +935,22 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, const Ca
                 const float mn[3][3] = {{0.f, m01, m02}, {-m01, 0.f, m12}, {-m02, -m12, 0.f}};
                 const float PV[2][3] = {{-V[1][0], -V[1][1], -V[1][2]}, {V[0][0], V[0][1], V[0][2]}};
                 const float G[2][2] = {{gA, 0.5f * gB}, {0.5f * gB, gC}};
+                float Wk[2][3]; // w_k = C v_k
                 float GW[2][3]; // G C v_k
                 for (int k = 0; k < 3; k++) {
                     float w[2];
                     for (int r2 = 0; r2 < 2; r2++)
                         w[r2] = (PV[r2][0] * mn[0][k] + PV[r2][1] * mn[1][k] + PV[r2][2] * mn[2][k] +
                                  rc.dilation * V[r2][k]) * idet;
+                    Wk[0][k] = w[0]; Wk[1][k] = w[1];
                     for (int r2 = 0; r2 < 2; r2++) GW[r2][k] = G[r2][0] * w[0] + G[r2][1] * w[1];
                 }
+                H00 += Wk[0][0] * GW[0][0] + Wk[1][0] * GW[1][0];
+                H11 += Wk[0][1] * GW[0][1] + Wk[1][1] * GW[1][1];
+                H22 += Wk[0][2] * GW[0][2] + Wk[1][2] * GW[1][2];
+                H01 += Wk[0][0] * GW[0][1] + Wk[1][0] * GW[1][1];
+                H02 += Wk[0][0] * GW[0][2] + Wk[1][0] * GW[1][2];
+                H12 += Wk[0][1] * GW[0][2] + Wk[1][1] * GW[1][2];
                 float gV[2][3];
                 for (int k = 0; k < 3; k++) {
                     float pv[3];
@@ -949,9 +959,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, const Ca
                         gV[r2][k] = -2.f * idet *
                                     (PV[r2][0] * pv[0] + PV[r2][1] * pv[1] + PV[r2][2] * pv[2] + rc.dilation * GW[r2][k]);
                 }
-                // V = T M: dL/dM += T^T dL/dV, dL/dT = dL/dV M^T
-                for (int p = 0; p < 3; p++)
-                    for (int c2 = 0; c2 < 3; c2++) gM[p][c2] += T[0][p] * gV[0][c2] + T[1][p] * gV[1][c2];
+                // V = T M: dL/dT = dL/dV M^T (dL/dM enters through H)
                 float gT[2][3];
                 for (int r2 = 0; r2 < 2; r2++)
                     for (int k = 0; k < 3; k++)
@@ -1001,18 +1009,25 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, const Ca
                 const float ddot = d[0] * gd[0] + d[1] * gd[1] + d[2] * gd[2];
                 for (int e = 0; e < 3; e++) gm[e] += (gd[e] - d[e] * ddot) * idn;
             }
-            // M = Q diag(s)
-            float gs[3] = {0.f, 0.f, 0.f}, gQ[3][3];
-            for (int p = 0; p < 3; p++)
-                for (int c2 = 0; c2 < 3; c2++) { gs[c2] += gM[p][c2] * Q[p][c2]; gQ[p][c2] = gM[p][c2] * s[c2]; }
-            for (int k = 0; k < 3; k++) gls[k] = gs[k] * s[k];
-            // rotation matrix of the unit quaternion
-            gq[0] = 2.f * (-z * gQ[0][1] + y * gQ[0][2] + z * gQ[1][0] - x * gQ[1][2] - y * gQ[2][0] + x * gQ[2][1]);
-            gq[1] = 2.f * (y * gQ[0][1] + z * gQ[0][2] + y * gQ[1][0] - 2.f * x * gQ[1][1] - w * gQ[1][2] + z * gQ[2][0] + w * gQ[2][1] - 2.f * x * gQ[2][2]);
-            gq[2] = 2.f * (-2.f * y * gQ[0][0] + x * gQ[0][1] + w * gQ[0][2] + x * gQ[1][0] + z * gQ[1][2] - w * gQ[2][0] + z * gQ[2][1] - 2.f * y * gQ[2][2]);
-            gq[3] = 2.f * (-2.f * z * gQ[0][0] - w * gQ[0][1] + x * gQ[0][2] + w * gQ[1][0] - 2.f * z * gQ[1][1] + y * gQ[1][2] + x * gQ[2][0] + y * gQ[2][1]);
-            const float qdot = q[0] * gq[0] + q[1] * gq[1] + q[2] * gq[2] + q[3] * gq[3];
-            for (int k = 0; k < 4; k++) gq[k] = (gq[k] - q[k] * qdot) / qn;
+            // Scale and rotation.  With V = T R diag(s) and dL/dV = -2 C G C V (C the
+            // conic, G = dL/dC), Omega = R^T dL/dR = diag(1/s) V^T dL/dV diag(s) has
+            // entries -2 (s_b / s_a) H[a][b], H[a][b] = w_a^T G w_b.  The log-scale
+            // gradient is its diagonal, -2 H[k][k]; the rotation gradient is its
+            // antisymmetric part, dL/dtheta = (O21 - O12, O02 - O20, O10 - O01) for
+            // R(q) R(I + [theta]x).  Forming them from H instead of through T^T dL/dV
+            // and R's columns avoids the cancellation of a long thin footprint, whose
+            // short axis projects to a short V column although T and R are large.
+            gls[0] = -2.f * H00; gls[1] = -2.f * H11; gls[2] = -2.f * H22;
+            const float th0 = -2.f * H12 * (s[1] / s[2] - s[2] / s[1]);
+            const float th1 = -2.f * H02 * (s[2] / s[0] - s[0] / s[2]);
+            const float th2 = -2.f * H01 * (s[0] / s[1] - s[1] / s[0]);
+            // unit quaternion: dL/dq = 2 q (x) (0, dL/dtheta), tangent to the sphere;
+            // the stored one is q |q_raw|, so dL/dq_raw = dL/dq / |q_raw|
+            const float iq = 2.f / qn;
+            gq[0] = iq * (-(x * th0 + y * th1 + z * th2));
+            gq[1] = iq * (w * th0 + (y * th2 - z * th1));
+            gq[2] = iq * (w * th1 + (z * th0 - x * th2));
+            gq[3] = iq * (w * th2 + (x * th1 - y * th0));
             if (a.absgrad) a.absgrad[i] += absacc;
             // scale regulariser (Eq. 5): beta / |V| * min_j s_j on the first smallest axis
             if (a.beta > 0.f && vis) {

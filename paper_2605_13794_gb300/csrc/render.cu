@@ -75,10 +75,14 @@ constexpr float kNegHalfLog2e = -0.72134752044448170f; // -log2(e) / 2
 constexpr float kFromScaled = -1.3862943611198906f;    // -2 ln 2 = 1 / kNegHalfLog2e
 
 // A staged entry: e0 = (u, v) tile-local, A and k; e1.x = D (A, D scaled to base 2)
+__device__ __forceinline__ float4 stage_e0_at(float4 r0, float4 r2, float ox, float oy)
+{
+    return make_float4(__fadd_rn(__fsub_rn(r0.x, ox), r2.y), __fadd_rn(__fsub_rn(r0.y, oy), r2.z),
+                       __fmul_rn(r0.z, kNegHalfLog2e), r0.w);
+}
 __device__ __forceinline__ float4 stage_e0(float4 r0, float4 r2, const TileGeom &tg)
 {
-    return make_float4(__fadd_rn(__fsub_rn(r0.x, tg.ox), r2.y), __fadd_rn(__fsub_rn(r0.y, tg.oy), r2.z),
-                       __fmul_rn(r0.z, kNegHalfLog2e), r0.w);
+    return stage_e0_at(r0, r2, tg.ox, tg.oy);
 }
 __device__ __forceinline__ float stage_D(float4 r1) { return __fmul_rn(r1.x, kNegHalfLog2e); }
 
@@ -533,8 +537,30 @@ cudaError_t launch_render_fwd_importance(gs_workspace *ws, cudaStream_t st, floa
 }
 
 // ---- backward ---------------------------------------------------------------
+//
+// Each warp owns an 8 x 8 pixel square of the tile -- lane l the horizontal
+// pixel pair (2 (l % 4), l / 4) of it, packed as FP32x2 -- and walks the
+// tile's list back to front on its own, from the last entry any of its pixels
+// composited, recovering T by T / (1 - alpha) from the final transmittance.
+// It stages each batch of 32 entries itself (one per lane), so no block-wide
+// barrier holds it while another warp of the tile has more to do; the staging
+// lane also tests its entry's alpha box against the warp's square, and one
+// ballot gives the batch's entries the warp must visit.  Per visited entry the
+// warp's gradient is one warp reduction; the warps' partials of a batch are
+// summed in warp order by the warp that finishes that batch last
+// (shared-memory arrival counters) and written to the entries' slots.  A warp may run up to
+// kBwdBufs - 1 batches ahead of the slowest warp of its tile; its wait for a
+// partial buffer is bounded.
 
-constexpr int kBwdBatch = 64; // entries staged per batch of the reverse walk
+constexpr int kBwdBatch = 32; // entries staged per batch of the reverse walk (one per lane)
+constexpr int kBwdBufs = 3;   // partial buffers: batches a warp may run ahead, plus one
+
+template <int TW, int TH> struct BwdShape {
+    static_assert(TW % 8 == 0 && TH % 8 == 0, "the adjoint walks 8 x 8 pixel squares");
+    static constexpr int wx = TW / 8;
+    static constexpr int warps = (TW / 8) * (TH / 8);
+    static constexpr int threads = 32 * warps;
+};
 
 struct BwdRenderArgs {
     const uint2 *ranges;
@@ -546,184 +572,212 @@ struct BwdRenderArgs {
     const uint32_t *n_contrib;
     const float *dL_drgb;
     float *slots;
-    unsigned long long *fragments; // += sum of the tile's n_contrib; [1] += composited pairs
+    DevCounters *ctr; // fragments += sum of the tile's n_contrib; composited += composited pairs
 };
-static_assert(offsetof(DevCounters, composited) == offsetof(DevCounters, fragments) + sizeof(unsigned long long),
-              "the backward adds to the two adjacent counters through one pointer");
 
-// Reverse traversal from each pixel's last composited entry, recovering T by
-// T / (1 - alpha) from the final transmittance.  Per entry, each thread sums
-// the gradient over its 4 pixels, each warp reduces over its 32 threads, and
-// the two warp partials are added once per batch into the entry's slot.
 template <int TW, int TH>
-__global__ void __launch_bounds__(TileShape<TW, TH>::threads)
+__global__ void __launch_bounds__(BwdShape<TW, TH>::threads)
     render_bwd_kernel(BwdRenderArgs a, const CamTable *__restrict__ ctp, RenderConsts rc)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
-    constexpr int kRT = TileShape<TW, TH>::threads, kWarps = TileShape<TW, TH>::warps;
-    __shared__ float4 s0[kBwdBatch];
-    __shared__ float4 s1[kBwdBatch];
-    __shared__ float s2[kBwdBatch];
-    __shared__ float2 s3[kBwdBatch];
-    __shared__ unsigned long long s_slot[kBwdBatch];
-    __shared__ float s_red[kWarps][kBwdBatch][kSlotFloats];
+    constexpr int kWarps = BwdShape<TW, TH>::warps, kRT = BwdShape<TW, TH>::threads;
+    __shared__ float4 s0[kWarps][kBwdBatch];
+    __shared__ float4 s1[kWarps][kBwdBatch];
+    __shared__ float s2[kWarps][kBwdBatch];
+    __shared__ unsigned long long s_slot[kWarps][kBwdBatch];
+    __shared__ float s_part[kBwdBufs][kWarps][kBwdBatch][kSlotFloats];
+    __shared__ unsigned s_mask[kBwdBufs][kWarps]; // entries of the batch each warp visited
+    __shared__ int s_arrive[kBwdBufs], s_done[kBwdBufs];
     __shared__ int s_max;
     const CamTable &ct = *ctp;
     if ((int)blockIdx.x >= ct.total_tiles) return;
-    const TileGeom tg = tile_geom<TW, TH>(ct, blockIdx.x);
-    const TileGeom &cam = tg;
+    const int tile = blockIdx.x;
+    const CamInfo &ci = ct.c[camera_of_tile(ct, tile)];
+    const int lt = tile - ci.tile_base;
+    const int tx = lt % ci.tiles_x, ty = lt / ci.tiles_x;
+    const float ox = (float)(tx * TW), oy = (float)(ty * TH);
     const uint2 rg = a.ranges[blockIdx.x];
     const int start = (int)rg.x, end = (int)rg.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool red_own = red9_owner(lane);
     const int red_q = red9_index(lane);
-    const WarpBox<TW, TH> wb(warp);
+    // the warp's square and the lane's pixel pair (tile-local)
+    const int sx = 8 * (warp % BwdShape<TW, TH>::wx), sy = 8 * (warp / BwdShape<TW, TH>::wx);
+    const int lx = sx + 2 * (lane & 3), ly = sy + (lane >> 2);
+    const float2 pxc = make_float2((float)lx + 0.5f, (float)lx + 1.5f);
+    const float pyc = (float)ly + 0.5f;
+    const float bx0 = (float)sx + 0.5f, bx1 = (float)sx + 7.5f, by0 = (float)sy + 0.5f, by1 = (float)sy + 7.5f;
 
-    // per-pixel state, as row pairs (element x: left pixel, y: right pixel)
-    float2 T[2], g0[2], g1[2], g2[2], tgb[2], S0[2], S1[2], S2[2];
-    int nc[kQ];
-    const float2 px2 = make_float2(tg.lx0, tg.lx0 + 1.f);
-    const float2 py2 = make_float2(tg.ly0, tg.ly0 + 1.f);
-    int mymax = 0, ncomp = 0;
-    const long long np = (long long)cam.width * cam.height;
-    const float *gimg = a.dL_drgb + 3 * cam.pix_base;
-#pragma unroll
-    for (int row = 0; row < 2; row++) {
+    // per-pixel state of the pair: dL/dC (g), T (from T_final back to each
+    // fragment's own), S = colour composited behind the current fragment plus
+    // the background seen through T_final
+    float2 T = f2(1.f), g0 = f2(0.f), g1 = f2(0.f), g2 = f2(0.f);
+    int nc0 = 0, nc1 = 0;
+    {
+        const long long np = (long long)ci.width * ci.height;
+        const float *gimg = a.dL_drgb + 3 * ci.pix_base;
+        const int px = tx * TW + lx, py = ty * TH + ly;
         float t[2] = {1.f, 1.f}, c0[2] = {0.f, 0.f}, c1[2] = {0.f, 0.f}, c2[2] = {0.f, 0.f};
+        int n[2] = {0, 0};
 #pragma unroll
         for (int h = 0; h < 2; h++) {
-            const int k = 2 * row + h;
-            const int px = tg.px0 + h, py = tg.py0 + row;
-            nc[k] = 0;
-            if (px < cam.width && py < cam.height) {
-                const long long pix = (long long)py * cam.width + px;
+            if (px + h < ci.width && py < ci.height) {
+                const long long pix = (long long)py * ci.width + px + h;
                 c0[h] = gimg[pix]; c1[h] = gimg[np + pix]; c2[h] = gimg[2 * np + pix];
-                t[h] = a.T_final[cam.pix_base + pix];
-                nc[k] = (int)a.n_contrib[cam.pix_base + pix];
+                t[h] = a.T_final[ci.pix_base + pix];
+                n[h] = (int)a.n_contrib[ci.pix_base + pix];
             }
-            mymax = max(mymax, nc[k]);
         }
-        T[row] = make_float2(t[0], t[1]);
-        g0[row] = make_float2(c0[0], c0[1]);
-        g1[row] = make_float2(c1[0], c1[1]);
-        g2[row] = make_float2(c2[0], c2[1]);
-        S0[row] = S1[row] = S2[row] = f2(0.f);
-        // d/dalpha of the background term: -T_final (g . bg) / (1 - alpha)
-        tgb[row] = __fmul2_rn(T[row], __ffma2_rn(g2[row], f2(rc.bg[2]), __ffma2_rn(g1[row], f2(rc.bg[1]),
-                                                                                  __fmul2_rn(g0[row], f2(rc.bg[0])))));
+        T = make_float2(t[0], t[1]);
+        g0 = make_float2(c0[0], c0[1]); g1 = make_float2(c1[0], c1[1]); g2 = make_float2(c2[0], c2[1]);
+        nc0 = n[0]; nc1 = n[1];
     }
+    float2 S0 = __fmul2_rn(T, f2(rc.bg[0])), S1 = __fmul2_rn(T, f2(rc.bg[1])), S2 = __fmul2_rn(T, f2(rc.bg[2]));
+    const int wmax = __reduce_max_sync(0xffffffffu, max(nc0, nc1));
     {
-        unsigned long long f = (unsigned long long)nc[0] + nc[1] + nc[2] + nc[3];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
-        if (lane == 0 && f) atomicAdd(a.fragments, f);
+        const unsigned f = __reduce_add_sync(0xffffffffu, (unsigned)(nc0 + nc1));
+        if (lane == 0 && f) atomicAdd(&a.ctr->fragments, (unsigned long long)f);
     }
     if (threadIdx.x == 0) s_max = 0;
+    if (threadIdx.x < kBwdBufs) { s_arrive[threadIdx.x] = 0; s_done[threadIdx.x] = 0; }
     __syncthreads();
-    atomicMax(&s_max, mymax);
+    if (lane == 0) atomicMax(&s_max, wmax);
     __syncthreads();
     const int last = start + s_max;
     // entries after the last contribution of every pixel carry zero gradient
     for (int s = last + threadIdx.x; s < end; s += kRT) {
-        float *dst = a.slots + slot_of(a.inst_off, a.rect, a.vals[s], tg.tx, tg.ty) * kSlotFloats;
+        float *dst = a.slots + slot_of(a.inst_off, a.rect, a.vals[s], tx, ty) * kSlotFloats;
 #pragma unroll
         for (int k = 0; k < kSlotFloats; k++) dst[k] = 0.f;
     }
-    for (int hi = last; hi > start; hi -= kBwdBatch) {
+    int ncomp = 0;
+    int b = 0;
+    for (int hi = last; hi > start; hi -= kBwdBatch, b++) {
         const int lo = max(start, hi - kBwdBatch);
         const int cnt = hi - lo;
-        for (int e = threadIdx.x; e < cnt; e += kRT) {
-            const uint32_t r = a.vals[lo + e];
+        const int buf = b % kBwdBufs;
+        bool visit = false;
+        if (lane < cnt) {
+            const uint32_t r = a.vals[lo + lane];
             const float4 r0 = a.rd0[r], r1 = a.rd1[r], r2 = a.rd2[r];
             const float op = r2.w != 0.f ? 0.f : r1.y; // a record marked culled composites nowhere
-            s0[e] = stage_e0(r0, r2, tg);
-            s1[e] = make_float4(stage_D(r1), op, r1.z, r1.w);
-            s2[e] = r2.x;
-            s3[e] = alpha_box(r0.z, r0.w, r1.x, op, rc.alpha_min);
-            s_slot[e] = slot_of(a.inst_off, a.rect, r, tg.tx, tg.ty);
+            const float4 e0 = stage_e0_at(r0, r2, ox, oy);
+            s0[warp][lane] = e0;
+            s1[warp][lane] = make_float4(stage_D(r1), op, r1.z, r1.w);
+            s2[warp][lane] = r2.x;
+            s_slot[warp][lane] = slot_of(a.inst_off, a.rect, r, tx, ty);
+            // visited: in front of the warp's last contribution, alpha box meeting the square
+            const float2 hb = alpha_box(r0.z, r0.w, r1.x, op, rc.alpha_min);
+            visit = lo + lane - start < wmax && !(e0.x + hb.x < bx0 || e0.x - hb.x > bx1 || e0.y + hb.y < by0 ||
+                                                  e0.y - hb.y > by1);
         }
-        __syncthreads();
-        for (int jj = cnt - 1; jj >= 0; jj--) {
-            const int j = lo + jj - start; // position in the tile list
-            const float4 p0 = s0[jj];
-            if (wb.misses(p0.x, p0.y, s3[jj])) { // warp-uniform: nothing to add
-                if (red_own) s_red[warp][jj][red_q] = 0.f;
-                continue;
+        const unsigned vmask = __ballot_sync(0xffffffffu, visit);
+        // the partial buffer of this batch is free once batch b - kBwdBufs has been summed
+        if (b >= kBwdBufs) {
+            const int want = b / kBwdBufs;
+            unsigned long long spins = 0;
+            bool gave_up = false;
+            while (*(volatile int *)&s_done[buf] < want) {
+                if (++spins > kSpinLimit) { gave_up = true; break; }
+                __nanosleep(32);
             }
-            const float4 p1 = s1[jj];
-            const float cb = s2[jj];
-            // the forward's own exponent and alpha (same functions, same bits)
-            const QuadPow qp = quad_power(p0, p1.x, px2, py2);
-            const float Au = p0.z * kFromScaled, Du = p1.x * kFromScaled; // the conic's A and D
-            float2 acc[kSlotFloats];
+            if (__any_sync(0xffffffffu, gave_up)) {
+                if (lane == 0) set_error(a.ctr, GS_ERR_TIMEOUT, kSiteRender);
+                return;
+            }
+            __threadfence_block();
+        }
+        __syncwarp();
+        float (*part)[kSlotFloats] = s_part[buf][warp];
+        if (lane == 0) s_mask[buf][warp] = vmask;
+        for (unsigned m = vmask; m != 0u;) {
+            const int jj = 31 - __clz(m); // back to front
+            m ^= 1u << jj;
+            const int j = lo + jj - start; // position in the tile list
+            const float4 p0 = s0[warp][jj];
+            const float4 p1 = s1[warp][jj];
+            // the forward's own exponent and alpha (the same operations, the same bits)
+            const float2 dx = __fadd2_rn(pxc, f2(-p0.x));
+            const float dy = __fadd_rn(pyc, -p0.y);
+            const float kdy = __fmul_rn(p0.w, dy);
+            const float ddy = __fmul_rn(__fmul_rn(p1.x, dy), dy);
+            const float2 e = __fadd2_rn(dx, f2(kdy));
+            const float2 pw = __ffma2_rn(f2(p0.z), __fmul2_rn(e, e), f2(ddy));
+            float2 G;
+            const float2 al = pair_alpha(pw, p1.y, rc.alpha_max, G);
+            // composited pixels: in front of the pixel's last contribution, alpha >= alpha_min
+            const bool m0 = j < nc0 && al.x >= rc.alpha_min;
+            const bool m1 = j < nc1 && al.y >= rc.alpha_min;
+            const bool act = m0 || m1;
+            float v[kSlotFloats];
 #pragma unroll
-            for (int q = 0; q < kSlotFloats; q++) acc[q] = f2(0.f);
-            bool act = false;
-#pragma unroll
-            for (int row = 0; row < 2; row++) {
-                float2 G;
-                const float2 al = pair_alpha(row ? qp.r1 : qp.r0, p1.y, rc.alpha_max, G);
-                // composited pixels: in front of the pixel's last contribution, alpha >= alpha_min
-                const bool m0 = j < nc[2 * row] && al.x >= rc.alpha_min;
-                const bool m1 = j < nc[2 * row + 1] && al.y >= rc.alpha_min;
-                if (!(m0 || m1)) continue;
-                act = true;
+            for (int q = 0; q < kSlotFloats; q++) v[q] = 0.f;
+            if (act) {
                 ncomp += (int)m0 + (int)m1;
+                const float cb = s2[warp][jj];
                 const float2 inv = make_float2(rcp_approx(1.f - al.x), rcp_approx(1.f - al.y));
-                const float2 Tj = __fmul2_rn(T[row], inv); // transmittance in front of this fragment
+                const float2 Tj = __fmul2_rn(T, inv); // transmittance in front of this fragment
                 const float2 aTf = __fmul2_rn(al, Tj);
                 const float2 aT = make_float2(m0 ? aTf.x : 0.f, m1 ? aTf.y : 0.f);
-                acc[6] = __ffma2_rn(aT, g0[row], acc[6]);
-                acc[7] = __ffma2_rn(aT, g1[row], acc[7]);
-                acc[8] = __ffma2_rn(aT, g2[row], acc[8]);
-                // dL/dalpha = Tj (g . c) - (g . S + T_final g . bg) / (1 - alpha), S the
-                // colour composited behind this fragment
-                const float2 gc = __ffma2_rn(g2[row], f2(cb), __ffma2_rn(g1[row], f2(p1.w), __fmul2_rn(g0[row], f2(p1.z))));
-                const float2 gS = __ffma2_rn(g2[row], S2[row], __ffma2_rn(g1[row], S1[row],
-                                                                          __ffma2_rn(g0[row], S0[row], tgb[row])));
+                const float2 dr = __fmul2_rn(aT, g0), dg = __fmul2_rn(aT, g1), db = __fmul2_rn(aT, g2);
+                // dL/dalpha = Tj (g . c) - (g . S) / (1 - alpha)
+                const float2 gc = __ffma2_rn(g2, f2(cb), __ffma2_rn(g1, f2(p1.w), __fmul2_rn(g0, f2(p1.z))));
+                const float2 gS = __ffma2_rn(g2, S2, __ffma2_rn(g1, S1, __fmul2_rn(g0, S0)));
                 const float2 dal = __ffma2_rn(make_float2(-inv.x, -inv.y), gS, __fmul2_rn(Tj, gc));
-                S0[row] = __ffma2_rn(aT, f2(p1.z), S0[row]);
-                S1[row] = __ffma2_rn(aT, f2(p1.w), S1[row]);
-                S2[row] = __ffma2_rn(aT, f2(cb), S2[row]);
-                T[row] = make_float2(m0 ? Tj.x : T[row].x, m1 ? Tj.y : T[row].y);
+                S0 = __ffma2_rn(aT, f2(p1.z), S0);
+                S1 = __ffma2_rn(aT, f2(p1.w), S1);
+                S2 = __ffma2_rn(aT, f2(cb), S2);
+                T = make_float2(m0 ? Tj.x : T.x, m1 ? Tj.y : T.y);
                 // opacity, mean and conic: only where alpha is not clamped at alpha_max
                 const float2 dGf = __fmul2_rn(G, dal);
                 const float2 dG = make_float2(m0 && al.x < rc.alpha_max ? dGf.x : 0.f,
                                               m1 && al.y < rc.alpha_max ? dGf.y : 0.f);
-                acc[5] = __fadd2_rn(acc[5], dG);
                 const float2 dpow = __fmul2_rn(dG, f2(p1.y));
-                const float2 dx = __fadd2_rn(px2, f2(-p0.x));
-                const float dy = (row ? py2.y : py2.x) - p0.y;
-                // d power / du = A dx + B dy = A e, d power / dv = B dx + C dy = k A e + D dy
-                const float2 Ae = __fmul2_rn(f2(Au), __fadd2_rn(dx, f2(p0.w * dy)));
-                acc[0] = __ffma2_rn(dpow, Ae, acc[0]);
-                acc[1] = __ffma2_rn(dpow, __ffma2_rn(f2(p0.w), Ae, f2(Du * dy)), acc[1]);
+                // d power / du = A e, d power / dv = k A e + D dy, e = dx + k dy
+                const float Au = p0.z * kFromScaled, Du = p1.x * kFromScaled; // the conic's A and D
+                const float2 Ae = __fmul2_rn(f2(Au), e);
+                const float2 du = __fmul2_rn(dpow, Ae);
+                const float2 dv = __fmul2_rn(dpow, __ffma2_rn(f2(p0.w), Ae, f2(Du * dy)));
                 const float2 hd = __fmul2_rn(f2(-0.5f), dpow);
-                acc[2] = __ffma2_rn(hd, __fmul2_rn(dx, dx), acc[2]);
-                acc[3] = __ffma2_rn(__fmul2_rn(dpow, f2(-dy)), dx, acc[3]);
-                acc[4] = __ffma2_rn(hd, f2(dy * dy), acc[4]);
+                const float2 dA = __fmul2_rn(hd, __fmul2_rn(dx, dx));
+                const float2 dB = __fmul2_rn(__fmul2_rn(dpow, f2(-dy)), dx);
+                const float2 dC = __fmul2_rn(hd, f2(dy * dy));
+                v[0] = du.x + du.y; v[1] = dv.x + dv.y; v[2] = dA.x + dA.y; v[3] = dB.x + dB.y;
+                v[4] = dC.x + dC.y; v[5] = dG.x + dG.y; v[6] = dr.x + dr.y; v[7] = dg.x + dg.y;
+                v[8] = db.x + db.y;
             }
-            float v[kSlotFloats];
-#pragma unroll
-            for (int q = 0; q < kSlotFloats; q++) v[q] = acc[q].x + acc[q].y;
             float r = 0.f;
             if (__any_sync(0xffffffffu, act)) r = warp_reduce9(v, lane);
-            if (red_own) s_red[warp][jj][red_q] = r;
+            if (red_own) part[jj][red_q] = r;
         }
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < cnt * kSlotFloats; idx += kRT) {
-            const int jj = idx / kSlotFloats, q = idx - jj * kSlotFloats;
-            float sum = s_red[0][jj][q];
+        // arrive; the last warp of the tile to finish this batch sums it
+        __syncwarp();
+        int arrived = 0;
+        if (lane == 0) {
+            __threadfence_block();
+            arrived = atomicAdd(&s_arrive[buf], 1);
+        }
+        arrived = __shfl_sync(0xffffffffu, arrived, 0);
+        if (arrived == kWarps - 1) {
+            __threadfence_block();
+            for (int idx = lane; idx < cnt * kSlotFloats; idx += 32) {
+                const int jj = idx / kSlotFloats, q = idx - jj * kSlotFloats;
+                float sum = 0.f; // the warps that visited the entry, in warp order
 #pragma unroll
-            for (int w = 1; w < kWarps; w++) sum += s_red[w][jj][q];
-            a.slots[s_slot[jj] * kSlotFloats + q] = sum;
+                for (int w = 0; w < kWarps; w++)
+                    if ((s_mask[buf][w] >> jj) & 1u) sum += s_part[buf][w][jj][q];
+                a.slots[s_slot[warp][jj] * kSlotFloats + q] = sum;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                s_arrive[buf] = 0;
+                __threadfence_block();
+                *(volatile int *)&s_done[buf] = b / kBwdBufs + 1;
+            }
         }
-        __syncthreads();
     }
-    unsigned long long f = (unsigned long long)ncomp;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
-    if (lane == 0 && f) atomicAdd(a.fragments + 1, f);
+    const unsigned f = __reduce_add_sync(0xffffffffu, (unsigned)ncomp);
+    if (lane == 0 && f) atomicAdd(&a.ctr->composited, (unsigned long long)f);
 }
 
 cudaError_t launch_render_bwd(gs_workspace *ws, cudaStream_t st, const float *dL_drgb)
@@ -732,16 +786,16 @@ cudaError_t launch_render_bwd(gs_workspace *ws, cudaStream_t st, const float *dL
     BwdRenderArgs a;
     a.ranges = ws->ranges; a.vals = ws->tval[ws->tile_buf]; a.rd0 = ws->rd0; a.rd1 = ws->rd1; a.rd2 = ws->rd2;
     a.inst_off = ws->inst_off; a.rect = ws->rect; a.T_final = ws->T_final; a.n_contrib = ws->n_contrib;
-    a.dL_drgb = dL_drgb; a.slots = ws->slots; a.fragments = &ws->ctr->fragments;
+    a.dL_drgb = dL_drgb; a.slots = ws->slots; a.ctr = ws->ctr;
     const unsigned grid = (unsigned)ws->cams.total_tiles;
     kt_begin(ws, GS_KT_RENDER_BWD, st);
     switch (tile_shape_id(ws->cams.tile_w, ws->cams.tile_h)) {
-    case 0: launch_pdl(render_bwd_kernel<16, 16>, grid, TileShape<16, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
-    case 1: launch_pdl(render_bwd_kernel<32, 8>, grid, TileShape<32, 8>::threads, 0, st, a, ws->d_cams, ws->rc); break;
-    case 2: launch_pdl(render_bwd_kernel<8, 32>, grid, TileShape<8, 32>::threads, 0, st, a, ws->d_cams, ws->rc); break;
-    case 3: launch_pdl(render_bwd_kernel<32, 16>, grid, TileShape<32, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
-    case 4: launch_pdl(render_bwd_kernel<16, 8>, grid, TileShape<16, 8>::threads, 0, st, a, ws->d_cams, ws->rc); break;
-    case 5: launch_pdl(render_bwd_kernel<8, 16>, grid, TileShape<8, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 0: launch_pdl(render_bwd_kernel<16, 16>, grid, BwdShape<16, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 1: launch_pdl(render_bwd_kernel<32, 8>, grid, BwdShape<32, 8>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 2: launch_pdl(render_bwd_kernel<8, 32>, grid, BwdShape<8, 32>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 3: launch_pdl(render_bwd_kernel<32, 16>, grid, BwdShape<32, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 4: launch_pdl(render_bwd_kernel<16, 8>, grid, BwdShape<16, 8>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 5: launch_pdl(render_bwd_kernel<8, 16>, grid, BwdShape<8, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
     default: return cudaErrorInvalidValue;
     }
     kt_end(ws, GS_KT_RENDER_BWD, st);

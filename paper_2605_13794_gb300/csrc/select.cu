@@ -102,7 +102,6 @@ __global__ void sel_camkeys_kernel(const uint32_t *vals, const uint16_t *rec_cam
     if (k < ctr->n_records) keys[k] = rec_cam[vals[k]];
 }
 
-constexpr int kScanTile = 4096;
 
 // The mass of a record in the prefix sums: FP64, or 64-bit fixed point with 32
 // fractional bits (exact and associative; a view's total alpha weight is at
@@ -233,6 +232,22 @@ cudaError_t launch_mass_scan(cudaStream_t st, const uint32_t *sorted, const floa
     launch_pdl(sel_block_scan_kernel<double>, 1, kBScanThreads, 0, st, bsum, (int)sblocks);
     note_launch();
     launch_pdl(sel_scan_kernel<double>, sblocks, 256, 0, st, sorted, w, bsum, cum, ctr);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// The same prefix in 64-bit fixed point (32 fractional bits), the arithmetic
+// of gs_importance's selection: exact, so identical in any association.
+cudaError_t launch_mass_scan_fixed(cudaStream_t st, const uint32_t *sorted, const float *w, unsigned long long *bsum,
+                                   unsigned long long *cum, const DevCounters *ctr, unsigned long long cap)
+{
+    const unsigned sblocks = (unsigned)((cap + kScanTile - 1) / kScanTile);
+    if (sblocks == 0) return cudaSuccess;
+    launch_pdl(sel_block_sum_kernel<unsigned long long>, sblocks, 256, 0, st, sorted, w, bsum, ctr);
+    note_launch();
+    launch_pdl(sel_block_scan_kernel<unsigned long long>, 1, kBScanThreads, 0, st, bsum, (int)sblocks);
+    note_launch();
+    launch_pdl(sel_scan_kernel<unsigned long long>, sblocks, 256, 0, st, sorted, w, bsum, cum, ctr);
     note_launch();
     return cudaGetLastError();
 }
