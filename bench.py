@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--impl", default="gsblitz", choices=["gsblitz", "reference"])
     ap.add_argument("--n", type=int, default=N_GAUSS, help="Gaussians (default: the 5M workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the short serving run of the default line")
     ap.add_argument("--workload", default="city5M", choices=["city5M", "train8-city20M", "batch64-city10M",
                                                               "serve-city30M"],
                     help="city5M: the single-view training step (the default line); the others run the "
@@ -320,8 +321,13 @@ class Step:
 # exponent, alpha and the skip test; a pair that composites adds the adjoint.
 BWD_FLOP_EVAL = 13
 BWD_FLOP_COMPOSITE = 59
-# FP32 lanes per SM (FMA pipe) and special-function lanes per SM
-FMA_LANES, SFU_LANES, SMS = 128, 16, 152
+# Algorithmic FP32 operations of the forward compositing and of the colourless
+# importance walk per (pixel, entry) pair: the same 13 to evaluate the entry's
+# alpha, then per composited pair the forward's T (1 - alpha), alpha T, three
+# colour FMAs and the T update (11), the importance walk's T (1 - alpha),
+# alpha T, the w and a sums and the T update (8).
+FWD_FLOP_COMPOSITE = 11
+IMP_FLOP_COMPOSITE = 8
 # Algorithmic DRAM bytes of the adjoint: per list entry its sorted index, the
 # staged record (3 x 16 B), the record's slot offset and rectangle and its
 # 9-float slot written back; per pixel dL/dC, T_final and n_contrib.
@@ -329,28 +335,36 @@ BWD_BYTES_ENTRY = 4 + 48 + 4 + 8 + 36
 BWD_BYTES_PIXEL = 12 + 4 + 4
 
 
-def bwd_roofline(fragments, composited, instances, pixels, kernel_ms, sm_mhz, peaks):
-    """Roofline of the compositing adjoint: achieved FP32 rate against the FMA
-    pipe's peak at the maximum SM clock, with the special-function and DRAM
-    fractions beside it."""
-    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    flops = BWD_FLOP_EVAL * fragments + BWD_FLOP_COMPOSITE * composited
+def alu_roofline(kernel, flops, sfu_ops, kernel_ms, alu, peaks, sm_mhz):
+    """FP32 roofline of one compositing kernel: achieved FLOP/s against the
+    measured FP32 FMA peak of this GPU (gs_alu_peaks), with the
+    special-function fraction beside it."""
     sec = kernel_ms * 1e-3
     achieved = flops / sec / 1e12
-    peak = SMS * FMA_LANES * 2 * max_mhz * 1e6 / 1e12
+    peak = max(alu["fp32_fma_flops"], alu["fp32x2_fma_flops"]) / 1e12
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_source": "measured on this GPU (gs_alu_peaks: FP32 FMA chains on all %d SMs, best of scalar "
+                           "and FP32x2)" % alu["sms"],
+            "algorithmic_flops_per_launch": flops, "kernel_ms": kernel_ms,
+            "sfu_frac": sfu_ops / sec / alu["ex2_per_s"], "sm_mhz_median": sm_mhz}
+
+
+def bwd_roofline(fragments, composited, instances, pixels, kernel_ms, sm_mhz, peaks, alu):
+    """Roofline of the compositing adjoint: achieved FP32 rate against the
+    measured FP32 FMA peak, with the special-function and DRAM fractions
+    beside it."""
+    flops = BWD_FLOP_EVAL * fragments + BWD_FLOP_COMPOSITE * composited
     sfu_ops = fragments + composited        # ex2 per pair, reciprocal per composited pair
-    sfu_peak = SMS * SFU_LANES * max_mhz * 1e6
+    r = alu_roofline("render_bwd_kernel", flops, sfu_ops, kernel_ms, alu, peaks, sm_mhz)
+    sec = kernel_ms * 1e-3
     nbytes = BWD_BYTES_ENTRY * instances + BWD_BYTES_PIXEL * pixels
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    return {"bound": "alu", "kernel": "render_bwd_kernel", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
-            "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz (measured max SM clock)",
-            "algorithmic_flops_per_launch": flops, "kernel_ms": kernel_ms,
-            "fragments_per_launch": fragments, "composited_per_launch": composited,
-            "sfu_frac": sfu_ops / sec / sfu_peak,
-            "hbm": {"algorithmic_bytes_per_launch": nbytes, "achieved_gbs": nbytes / sec / 1e9, "peak": hbm,
-                    "frac": nbytes / sec / 1e9 / hbm, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"},
-            "sm_mhz_median": sm_mhz}
+    r.update({"fragments_per_launch": fragments, "composited_per_launch": composited,
+              "hbm": {"algorithmic_bytes_per_launch": nbytes, "achieved_gbs": nbytes / sec / 1e9, "peak": hbm,
+                      "frac": nbytes / sec / 1e9 / hbm,
+                      "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}})
+    return r
 
 
 def measured_peaks():
@@ -377,6 +391,64 @@ def traffic_from_profile(profile, kernel_file):
         return float(vals["dram_bytes_per_launch"].strip())
     except (KeyError, ValueError):
         return None
+
+
+# ---- latency ------------------------------------------------------------------------
+
+LATENCY_VIEWS = 40
+
+
+def render_latency(step, g, B, torch):
+    """Forward-only render of single 1920x1080 views of the resident scene
+    (preprocess with the LOD gate, bin_sort, render_fwd), LATENCY_VIEWS random
+    aerial poses one after another: per view the device time between events
+    around the three calls, and the host time from the first call to the
+    image being complete."""
+    from paper_2605_13794_gb300 import synth
+    cams = [synth.aerial_camera(seed=1000 + k, width=W_IMG, height=H_IMG) for k in range(LATENCY_VIEWS)]
+    params = B.RenderParams(lod_enable=True, **LOD)
+    ws = B.Workspace(max_gaussians=step.n, max_records=min(step.n, 1 << 21), max_instances=1 << 25,
+                     max_tiles=B.tiles_of(cams[0]), max_pixels=W_IMG * H_IMG, forward_only=True)
+    rgb = torch.empty(3 * W_IMG * H_IMG, device="cuda")
+    dev, host = [], []
+    for k in range(-3, LATENCY_VIEWS):  # three warm-up views
+        cam = cams[k % LATENCY_VIEWS]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        h0 = time.perf_counter()
+        e0.record()
+        ws.preprocess(step.gt, [cam], params)
+        ws.bin_sort()
+        ws.render_fwd(rgb)
+        e1.record()
+        e1.synchronize()
+        h1 = time.perf_counter()
+        if k >= 0:
+            dev.append(e0.elapsed_time(e1))
+            host.append((h1 - h0) * 1e3)
+    ws.sync_status()
+    ws.close()
+    q = lambda a, f: float(np.quantile(np.asarray(a), f))
+    return {"views": LATENCY_VIEWS, "resolution": f"{W_IMG}x{H_IMG}", "gaussians": step.n,
+            "p50_ms": q(dev, 0.5), "p99_ms": q(dev, 0.99), "host_p50_ms": q(host, 0.5), "host_p99_ms": q(host, 0.99),
+            "what": "forward-only render of one view: preprocess (LOD gate) + bin_sort + render_fwd"}
+
+
+SERVE_RATE, SERVE_SECONDS = 200.0, 3.0
+
+
+def serving_short(step, torch):
+    """A short run of the serving loop (continuous batching, three batches in
+    flight at most) against the resident scene: Poisson arrivals at
+    SERVE_RATE per second for SERVE_SECONDS, resolutions 720p-4K."""
+    from paper_2605_13794_gb300 import workloads as WL
+    r = WL.serve_run(step.gt, SERVE_RATE, SERVE_SECONDS, seed=5, key_budget=12e9, slots=3, check_alone=False)
+    keep = ("requests", "p50_ms", "p99_ms", "max_ms", "req_per_s", "mpix_per_s", "mean_batch", "mean_in_flight",
+            "overlap_frac", "max_in_flight", "slots", "rate", "duration_s")
+    out = {k: r[k] for k in keep}
+    out["what"] = (f"serving loop against the {step.n // 1_000_000}M-Gaussian scene: Poisson {SERVE_RATE:.0f} req/s "
+                   f"for {SERVE_SECONDS:.0f} s, 720p-4K, latency from arrival to the image complete on the device")
+    return out
 
 
 # ---- CPU oracle on a bounded sample ------------------------------------------------
@@ -583,6 +655,8 @@ def main():
     from paper_2605_13794_gb300 import binding as B
     torch.cuda.set_device(local)
     g, cam, target = make_host_inputs(args.n)
+    # measured FP32 FMA and special-function throughput of this GPU: the roofline peaks
+    alu = B.alu_peaks()
     step = Step(g, cam, target, tile=tuple(int(x) for x in args.tile.split("x")), lazy=not args.dense_adam,
                 overlap=args.overlap)
     stream = torch.cuda.current_stream()
@@ -614,6 +688,7 @@ def main():
     launches0 = B.kernel_launches()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     w0 = time.time()
+    torch.cuda.nvtx.range_push("timed_region")  # lets a profiler select the timed launches
     start.record(stream)
     for k in range(args.steps):
         step.replay()
@@ -623,6 +698,7 @@ def main():
     step.flush()
     fl1.record(stream)
     end.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     sampler.mark(w0, time.time())
     # graph replays launch the captured kernels without host calls
@@ -695,9 +771,16 @@ def main():
     # events between the stages
     diag = max(1, min(args.steps, 10))
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(diag)]
+    # and the per-launch device time of the forward and the importance raster in
+    # these one-stream steps (event pairs around each launch)
+    step.ws.kernel_timing(True, kernels=[B.GS_KT_RENDER_FWD, B.GS_KT_IMPORTANCE])
     for k in range(diag):
         step.run(evs[k])
     torch.cuda.synchronize()
+    for name, kid in (("render_fwd_kernel", B.GS_KT_RENDER_FWD), ("importance_raster_kernel", B.GS_KT_IMPORTANCE)):
+        t, n_l = step.ws.kernel_time(kid)
+        kernel_ms[name] = max_over_ranks(t / max(n_l, 1), world)
+    step.ws.kernel_timing(False)
     stage_ms = {name: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(diag))
                 for i, name in enumerate(step.stage_names)}
     stage_ms["adam_flush_per_step"] = fl0.elapsed_time(fl1) / args.steps
@@ -721,11 +804,27 @@ def main():
     step.ws.photometric_loss(step.rgb.view(1, 3, cam.height, cam.width), step.target, LAMBDA, step.loss, step.dL)
     step.ws.render_bwd_compact(step.gt, step.dL, scale_reg_beta=BETA, scale_reg_value=step.reg)
     counts = step.ws.counts()
+    # the importance walk's composited pairs: the sum of its per-Gaussian a
+    a_imp = torch.zeros(g.n, device="cuda", dtype=torch.int32)
+    step.ws.importance(a=a_imp)
+    imp_composited = int(a_imp.sum().item())
     # the dominant kernel of the step is the compositing adjoint: FP32-issue bound
+    sm_mhz = clocks.get("sm_mhz")
     roof = bwd_roofline(counts["fragments"], counts["composited"], counts["n_instances"], P,
-                        kernel_ms["render_bwd_kernel"], clocks.get("sm_mhz"), peaks)
+                        kernel_ms["render_bwd_kernel"], sm_mhz, peaks, alu)
     roof["traffic"] = traffic_from_profile("render_bwd_kernel_city5M_1080p.md", "render.cu")
     roof["dominant_stage"] = dom
+    # the forward and the importance raster against the same peak; their pairs are
+    # counted as the adjoint's (the entries up to each pixel's last composited one, a
+    # lower bound of the pairs they evaluate)
+    frag = counts["fragments"]
+    roof_fwd = alu_roofline("render_fwd_kernel", BWD_FLOP_EVAL * frag + FWD_FLOP_COMPOSITE * counts["composited"],
+                            frag, kernel_ms["render_fwd_kernel"], alu, peaks, sm_mhz)
+    roof_imp = alu_roofline("importance_raster_kernel", BWD_FLOP_EVAL * frag + IMP_FLOP_COMPOSITE * imp_composited,
+                            frag, kernel_ms["importance_raster_kernel"], alu, peaks, sm_mhz)
+    roof_imp["composited_per_launch"] = imp_composited
+    latency = render_latency(step, g, B, torch)
+    serving = serving_short(step, torch) if not args.no_serving else None
     line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -745,6 +844,11 @@ def main():
             "counts": {k: counts[k] for k in ("n_records", "n_instances", "n_visible")},
             "kernel_ms": {k: round(v, 4) for k, v in kernel_ms.items()},
             "roofline": roof,
+            "roofline_other": {"render_fwd_kernel": roof_fwd, "importance_raster_kernel": roof_imp},
+            "alu_peaks": {k: (round(v / 1e12, 3) if k != "sms" else v) for k, v in alu.items()},
+            "alu_peaks_unit": "TFLOP/s (FMA) and T results/s (ex2)",
+            "render_latency": latency,
+            "serving": serving,
             "e2e": {"value": job_rate(P, e2e_ms, world) / 1e6, "unit": "Mpix/s", "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,

@@ -260,37 +260,57 @@ def batched_render_workload(n: int = 10_000_000, n_cams: int = 64, reps: int = 1
 
 # ---- serving -------------------------------------------------------------------------
 
+SERVE_SIZES = ((1280, 720), (1920, 1080), (2560, 1440), (3840, 2160))
+
+
+def serve_camera(rng):
+    """A serving request's view: a random aerial pose at 720p, 1080p, 1440p or 4K."""
+    w, h = SERVE_SIZES[rng.integers(len(SERVE_SIZES))]
+    return synth.aerial_camera(int(rng.integers(1 << 30)), width=w, height=h)
+
+
+def serve_run(gt, rate: float, duration: float, seed: int = 5, key_budget: float = 40e9, max_batch: int = 64,
+              slots: int = 3, check_alone: bool = True) -> dict:
+    """Poisson arrivals at `rate` for `duration` seconds against resident
+    Gaussians gt, with `slots` batches in flight at most (1: one batch at a
+    time, the control without overlap)."""
+    params = B.RenderParams(lod_enable=True, **LOD)
+    reqs = poisson_requests(rate, duration, serve_camera, seed=seed)
+    server = Server(gt, params, key_budget_bytes=key_budget, max_batch=max_batch,
+                    max_pixels=16 * 3840 * 2160, slots=slots)
+    # warm-up on a few requests outside the timed run
+    warm = poisson_requests(rate, 0.2, serve_camera, seed=seed + 1)
+    server.run(warm, realtime=False)
+    server.batches.clear()
+    stats = server.run(reqs, realtime=True)
+    server.close()
+    stats.update({"rate": rate, "duration_s": duration, "key_budget_gb": key_budget / 1e9})
+    if check_alone:
+        # a request renders the same image in an overlapped mix of batches as alone
+        mix = Server(gt, params, key_budget_bytes=8e9, max_batch=4, max_pixels=4 * 3840 * 2160, keep_images=True,
+                     slots=3)
+        few = [dataclasses_replace(r) for r in reqs[:12]]
+        mstats = mix.run(few, realtime=False)
+        mix.close()
+        alone = Server(gt, params, key_budget_bytes=4e9, max_batch=1, max_pixels=3840 * 2160, keep_images=True,
+                       slots=1)
+        solo = [dataclasses_replace(r) for r in few[:4]]
+        alone.run(solo, realtime=False)
+        alone.close()
+        stats["alone_equals_in_mix"] = all(torch.equal(a.image, b.image) for a, b in zip(few[:4], solo))
+        stats["mix_max_in_flight"] = mstats["max_in_flight"]
+    return stats
+
+
 def serving_workload(n: int = 30_000_000, rate: float = 200.0, duration: float = 60.0, seed: int = 5,
                      key_budget: float = 40e9, max_batch: int = 64) -> dict:
     g = synth.city_scene(n, seed=3)
     gt = B.GaussianTensors.from_host(g)
-    sizes = ((1280, 720), (1920, 1080), (2560, 1440), (3840, 2160))
-
-    def camera(rng):
-        w, h = sizes[rng.integers(len(sizes))]
-        return synth.aerial_camera(int(rng.integers(1 << 30)), width=w, height=h)
-
-    params = B.RenderParams(lod_enable=True, **LOD)
-    reqs = poisson_requests(rate, duration, camera, seed=seed)
-    server = Server(gt, params, key_budget_bytes=key_budget, max_batch=max_batch,
-                    max_pixels=16 * 3840 * 2160)
-    # warm-up on a few requests outside the timed run
-    warm = poisson_requests(rate, 0.2, camera, seed=seed + 1)
-    server.run(warm, realtime=False)
-    server.batches.clear()
-    stats = server.run(reqs, realtime=True)
-    # a request alone renders the same image as in its batch
-    probe = Server(gt, params, key_budget_bytes=4e9, max_batch=8, max_pixels=8 * 3840 * 2160, keep_images=True)
-    few = reqs[:6]
-    for r in few:
-        r.done = r.start = None
-    probe.run(few, realtime=False)
-    alone = Server(gt, params, key_budget_bytes=4e9, max_batch=1, max_pixels=3840 * 2160, keep_images=True)
-    solo = [dataclasses_replace(r) for r in few[:3]]
-    alone.run(solo, realtime=False)
-    same = all(torch.equal(a.image, b.image) for a, b in zip(few[:3], solo))
-    stats.update({"n": n, "rate": rate, "duration_s": duration, "key_budget_gb": key_budget / 1e9,
-                  "alone_equals_batched": same})
+    stats = serve_run(gt, rate, duration, seed, key_budget, max_batch, slots=3)
+    # the control: one batch at a time
+    off = serve_run(gt, rate, duration, seed, key_budget, max_batch, slots=1, check_alone=False)
+    stats.update({"n": n, "overlap_off": {k: off[k] for k in ("p50_ms", "p99_ms", "mean_batch", "req_per_s",
+                                                              "mean_in_flight")}})
     return stats
 
 
