@@ -468,6 +468,18 @@ typedef struct {
 } gs_alu_peak;
 int gs_alu_peaks(gs_alu_peak *out, gs_stream stream);
 
+/* Bound on the waits of gs_importance's selection sorts: each wait of a
+ * block on its predecessors in a sort pass gives up after `spins` polls
+ * (0 restores the default, 2^22) and sets GS_ERR_TIMEOUT (reported by
+ * gs_sync_status).  The sort's output order is then wrong but every write
+ * stays inside its buffers, and the selection's later kernels skip their
+ * work, so the Cull column comes out with every Gaussian culled.  The next
+ * call after gs_clear_error runs normally.  Host-side setting, read when a
+ * call is issued (a captured graph keeps the value it was captured with).
+ * The paper has no counterpart: it exists so that the bounded waits can be
+ * exercised. */
+int gs_workspace_set_spin_limit(gs_workspace *ws, uint64_t spins);
+
 /* Kernel timing, for measurement.  While on, each launch of the timed kernels
  * below is bracketed by a CUDA event pair recorded on the stream it is launched
  * on; a launch issued under stream capture gets a pair of event nodes in the

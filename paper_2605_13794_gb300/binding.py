@@ -34,7 +34,7 @@ EXPORTS = ("gs_default_params", "gs_last_error", "gs_workspace_create", "gs_work
            "gs_prune_sample", "gs_prune_mass", "gs_compact", "gs_densify", "gs_count_views", "gs_adam_lazy_enable",
            "gs_adam_lazy_disable", "gs_adam_flush", "gs_kernel_timing", "gs_kernel_time",
            "gs_render_fwd_importance", "gs_graph_capture_begin", "gs_graph_capture_end", "gs_graph_launch",
-           "gs_graph_destroy", "gs_alu_peaks")
+           "gs_graph_destroy", "gs_alu_peaks", "gs_workspace_set_spin_limit")
 
 # Cull modes of RenderParams.cull_enable (include/gsblitz.h)
 GS_CULL_OFF, GS_CULL_DROP, GS_CULL_MARK = 0, 1, 2
@@ -152,6 +152,7 @@ def lib() -> ctypes.CDLL:
         L.gs_adam_step_compact.argtypes = [vp, vp, vp, vp, vp, f32, f32, f32, i32, vp]
         L.gs_visible_set_static.argtypes = [vp, i64, f32, vp, vp, vp, vp]
         L.gs_alu_peaks.argtypes = [vp, vp]
+        L.gs_workspace_set_spin_limit.argtypes = [vp, ctypes.c_uint64]
         L.gs_importance.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
         L.gs_photometric_loss.argtypes = [vp, vp, vp, i32, i32, i32, ctypes.c_float, vp, vp, vp]
         L.gs_adam_step.argtypes = [vp, i32, i32, vp]
@@ -374,6 +375,11 @@ class Workspace:
         size); results are unchanged."""
         _check(lib().gs_workspace_set_sort_chunk(self._ws, int(keys_per_block)))
         self.sort_chunk = int(keys_per_block)
+
+    def set_spin_limit(self, spins: int):
+        """Bound on the look-back waits of importance()'s selection sorts (0:
+        the default); see gs_workspace_set_spin_limit."""
+        _check(lib().gs_workspace_set_spin_limit(self._ws, int(spins)))
 
     def bin_sort(self, stream=None):
         _check(lib().gs_bin_sort(self._ws, _stream(stream)))

@@ -247,6 +247,7 @@ int gs_workspace_create(const gs_capacity *cap, gs_workspace **out)
     if (!ws) return fail(GS_ERR_OOM, "host allocation failed");
     ws->cap = *cap;
     ws->sort_items = 0; // by the size of each sort
+    ws->sel_spin_limit = gs::kSpinLimit;
     cudaGetDevice(&ws->device);
     if (cudaDeviceGetAttribute(&ws->sm_count, cudaDevAttrMultiProcessorCount, ws->device) != cudaSuccess ||
         ws->sm_count < 1)
@@ -398,6 +399,13 @@ int gs_workspace_set_sort_chunk(gs_workspace *ws, int32_t keys_per_block)
     if (keys_per_block != 0 && keys_per_block != 1024 && keys_per_block != 2048 && keys_per_block != 4096)
         return fail(GS_ERR_INVALID_ARG, "gs_workspace_set_sort_chunk: keys_per_block must be 0, 1024, 2048 or 4096");
     ws->sort_items = keys_per_block / gs::kSortThreads;
+    return GS_OK;
+}
+
+int gs_workspace_set_spin_limit(gs_workspace *ws, uint64_t spins)
+{
+    if (!ws) return fail(GS_ERR_INVALID_ARG, "gs_workspace_set_spin_limit: NULL workspace");
+    ws->sel_spin_limit = spins == 0 ? gs::kSpinLimit : (unsigned long long)spins;
     return GS_OK;
 }
 

@@ -133,6 +133,17 @@ __device__ __forceinline__ void set_error(DevCounters *ctr, int code, int site)
     if (atomicCAS(&ctr->error, 0, code) == 0) ctr->error_site = site;
 }
 
+// Whether the error word was set before this block started, read by one thread
+// so that the whole block takes the same branch (the kernels calling it use
+// block barriers).
+__device__ __forceinline__ bool block_error(const DevCounters *ctr)
+{
+    __shared__ int s_err;
+    if (threadIdx.x == 0) s_err = *(volatile const int *)&ctr->error;
+    __syncthreads();
+    return s_err != 0;
+}
+
 // Camera of a global tile id (binary search over tile bases).
 __device__ __forceinline__ int camera_of_tile(const CamTable &ct, int tile)
 {
@@ -248,6 +259,7 @@ __device__ __forceinline__ T block_exclusive_scan_256(T v, T *smem_warp /*[8]*/,
 // ---- workspace (host struct, device buffers) -------------------------------
 struct gs_workspace {
     gs_capacity cap;
+    unsigned long long sel_spin_limit; // bound on the look-back waits of gs_importance's selection sorts
     int device;
     int sm_count;        // multiprocessors of the device (persistent grids)
     void *base;          // one device allocation, carved into the buffers below
@@ -370,7 +382,7 @@ cudaError_t launch_render_fwd_importance(gs_workspace *ws, cudaStream_t st, floa
 cudaError_t launch_importance_reduce(gs_workspace *ws, cudaStream_t st);
 cudaError_t launch_radix_sort(gs_workspace *ws, cudaStream_t st, uint32_t *keys[2], uint32_t *vals[2],
                               const unsigned long long *count, unsigned long long cap, int bits, bool vals_identity,
-                              bool descending_keys_in_place, int &out_buf);
+                              bool descending_keys_in_place, int &out_buf, unsigned long long spin_limit = kSpinLimit);
 cudaError_t launch_emit(gs_workspace *ws, cudaStream_t st);
 cudaError_t launch_ranges(gs_workspace *ws, cudaStream_t st);
 cudaError_t launch_render_fwd(gs_workspace *ws, cudaStream_t st, float *rgb, float *T_out);

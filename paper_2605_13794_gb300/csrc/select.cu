@@ -98,6 +98,7 @@ __global__ void sel_camkeys_kernel(const uint32_t *vals, const uint16_t *rec_cam
                                    const DevCounters *ctr)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
+    if (ctr->error != 0) return; // a sort that gave up: its order is not a permutation
     const unsigned long long k = (unsigned long long)blockIdx.x * 256 + threadIdx.x;
     if (k < ctr->n_records) keys[k] = rec_cam[vals[k]];
 }
@@ -120,6 +121,7 @@ __global__ void __launch_bounds__(256) sel_block_sum_kernel(const uint32_t *vals
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     __shared__ M s[256];
+    if (block_error(ctr)) return; // a sort that gave up: its order is not a permutation
     const unsigned long long n = ctr->n_records;
     const unsigned long long base = (unsigned long long)blockIdx.x * kScanTile;
     M acc = 0;
@@ -187,6 +189,7 @@ __global__ void __launch_bounds__(256) sel_scan_kernel(const uint32_t *vals, con
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     __shared__ M s_w[32];
+    if (block_error(ctr)) return; // a sort that gave up: its order is not a permutation
     const unsigned long long n = ctr->n_records;
     const unsigned long long base = (unsigned long long)blockIdx.x * kScanTile;
     if (base >= n) return;
@@ -210,6 +213,7 @@ __global__ void __launch_bounds__(256) sel_scan_kernel(const uint32_t *vals, con
 __global__ void sel_segments_kernel(const uint32_t *vals, const uint16_t *rec_cam, uint2 *seg, const DevCounters *ctr)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
+    if (ctr->error != 0) return; // a sort that gave up: its order is not a permutation
     const unsigned long long n = ctr->n_records;
     for (unsigned long long k = (unsigned long long)blockIdx.x * 256 + threadIdx.x; k < n;
          k += (unsigned long long)gridDim.x * 256) {
@@ -269,6 +273,7 @@ struct SelApplyArgs {
 __global__ void sel_apply_kernel(SelApplyArgs a)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
+    if (a.ctr->error != 0) return; // a sort that gave up: every Gaussian stays culled
     const unsigned long long n = a.ctr->n_records;
     for (unsigned long long k = (unsigned long long)blockIdx.x * 256 + threadIdx.x; k < n;
          k += (unsigned long long)gridDim.x * 256) {
@@ -349,7 +354,8 @@ cudaError_t launch_importance(gs_workspace *ws, cudaStream_t st, float *w, uint3
     note_launch();
     int ob = 0;
     const unsigned long long *cnt = &ws->ctr->n_records;
-    if ((e = launch_radix_sort(ws, st, sk, sv, cnt, rcap, 32, true, false, ob)) != cudaSuccess) return e;
+    if ((e = launch_radix_sort(ws, st, sk, sv, cnt, rcap, 32, true, false, ob, ws->sel_spin_limit)) != cudaSuccess)
+        return e;
     uint32_t *sorted = sv[ob];
     if (ncam > 1) {
         uint32_t *k2[2] = {sk[ob ^ 1], sk[ob]};
@@ -357,7 +363,9 @@ cudaError_t launch_importance(gs_workspace *ws, cudaStream_t st, float *w, uint3
         launch_pdl(sel_camkeys_kernel, rblocks, 256, 0, st, v2[0], ws->rec_cam, k2[0], ws->ctr);
         note_launch();
         int ob2 = 0;
-        if ((e = launch_radix_sort(ws, st, k2, v2, cnt, rcap, 8, false, false, ob2)) != cudaSuccess) return e;
+        if ((e = launch_radix_sort(ws, st, k2, v2, cnt, rcap, 8, false, false, ob2, ws->sel_spin_limit)) !=
+            cudaSuccess)
+            return e;
         sorted = v2[ob2];
     }
     const unsigned sblocks = (unsigned)((rcap + kScanTile - 1) / kScanTile);

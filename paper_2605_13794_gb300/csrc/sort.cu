@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
     uint32_t *__restrict__ vals_out, const unsigned long long *count, unsigned long long cap, int shift,
     const uint32_t *__restrict__ bucket_off, uint32_t *status /* ticket at [0], then [blocks][256] */,
-    DevCounters *ctr)
+    DevCounters *ctr, unsigned long long spin_limit)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     constexpr int kTileKeys = kSortThreads * ITEMS;
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
             if (done) break;
             pred -= q;
             if (q == kWin) continue;
-            if (++spins > kSpinLimit) {
+            if (++spins > spin_limit) {
                 set_error(ctr, GS_ERR_TIMEOUT, kSiteRadix);
                 break;
             }
@@ -195,6 +195,9 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
         const uint32_t k = s_keys[i];
         const uint32_t dd = (k >> shift) & 255u;
         const unsigned long long out = (unsigned long long)s_glob[dd] + (uint32_t)(i - (int)s_blk[dd]);
+        // always below n for a complete look-back; after one gave up (or a pass that
+        // follows it) the offsets are wrong but never beyond the output
+        if (out >= n) continue;
         if (WRITE_KEYS) keys_out[out] = k;
         vals_out[out] = s_vals[i];
     }
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
 template <int ITEMS>
 static cudaError_t radix_passes(cudaStream_t st, uint32_t *keys[2], uint32_t *vals[2], const unsigned long long *count,
                                 unsigned long long cap, int passes, bool vals_identity, uint32_t *status,
-                                const uint32_t *off, DevCounters *ctr, int &out_buf)
+                                const uint32_t *off, DevCounters *ctr, int &out_buf, unsigned long long spin_limit)
 {
     const unsigned long long blocks = (cap + kSortThreads * ITEMS - 1) / (kSortThreads * ITEMS);
     cudaError_t e;
@@ -213,10 +216,10 @@ static cudaError_t radix_passes(cudaStream_t st, uint32_t *keys[2], uint32_t *va
         if ((e = cudaMemsetAsync(status, 0, (blocks * 256 + 1) * sizeof(uint32_t), st)) != cudaSuccess) return e;
         if (vals_identity && p == 0)
             launch_pdl(radix_pass_kernel<ITEMS, true, true>, (unsigned)blocks, kSortThreads, 0, st,
-                keys[src], vals[src], keys[dst], vals[dst], count, cap, 8 * p, off + 256 * p, status, ctr);
+                keys[src], vals[src], keys[dst], vals[dst], count, cap, 8 * p, off + 256 * p, status, ctr, spin_limit);
         else
             launch_pdl(radix_pass_kernel<ITEMS, false, true>, (unsigned)blocks, kSortThreads, 0, st,
-                keys[src], vals[src], keys[dst], vals[dst], count, cap, 8 * p, off + 256 * p, status, ctr);
+                keys[src], vals[src], keys[dst], vals[dst], count, cap, 8 * p, off + 256 * p, status, ctr, spin_limit);
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         src = dst;
@@ -233,7 +236,7 @@ static cudaError_t radix_passes(cudaStream_t st, uint32_t *keys[2], uint32_t *va
 // chosen by the size of the sort).
 cudaError_t launch_radix_sort(gs_workspace *ws, cudaStream_t st, uint32_t *keys[2], uint32_t *vals[2],
                               const unsigned long long *count, unsigned long long cap, int bits, bool vals_identity,
-                              bool /*unused*/, int &out_buf)
+                              bool /*unused*/, int &out_buf, unsigned long long spin_limit)
 {
     const int passes = bits <= 0 ? 1 : (bits + 7) / 8;
     cudaError_t e;
@@ -252,12 +255,12 @@ cudaError_t launch_radix_sort(gs_workspace *ws, cudaStream_t st, uint32_t *keys[
     if (items == 0) items = cap <= (1ull << 20) ? 4 : (cap <= (16ull << 20) ? 8 : 16);
     if (items == 4)
         return radix_passes<4>(st, keys, vals, count, cap, passes, vals_identity, ws->rx_status, ws->rx_off, ws->ctr,
-                               out_buf);
+                               out_buf, spin_limit);
     if (items == 8)
         return radix_passes<8>(st, keys, vals, count, cap, passes, vals_identity, ws->rx_status, ws->rx_off, ws->ctr,
-                               out_buf);
+                               out_buf, spin_limit);
     return radix_passes<kSortItems>(st, keys, vals, count, cap, passes, vals_identity, ws->rx_status, ws->rx_off,
-                                    ws->ctr, out_buf);
+                                    ws->ctr, out_buf, spin_limit);
 }
 
 // The same LSD sort with every scratch buffer passed in (no workspace) and
@@ -280,7 +283,8 @@ cudaError_t launch_radix_sort_scratch(cudaStream_t st, uint32_t *keys[2], uint32
     note_launch();
     launch_pdl(radix_offsets_kernel, 1, 256, 0, st, hist, off, passes);
     note_launch();
-    return radix_passes<kSortItems>(st, keys, vals, count, cap, passes, vals_identity, status, off, ctr, out_buf);
+    return radix_passes<kSortItems>(st, keys, vals, count, cap, passes, vals_identity, status, off, ctr, out_buf,
+                                    kSpinLimit);
 }
 
 // ---- emission -------------------------------------------------------------
