@@ -227,107 +227,160 @@ __device__ __forceinline__ unsigned long long slot_of(const uint32_t *inst_off, 
     return (unsigned long long)inst_off[r] + (unsigned long long)((ty - y0) * (x1 - x0) + (tx - x0));
 }
 
+// ---- warp squares ------------------------------------------------------------
+//
+// The forward and the adjoint give each warp an 8 x 8 pixel square of the
+// tile: lane l holds the horizontal pixel pair (2 (l % 4), l / 4) of it, as
+// FP32x2, and the warp walks the tile's list on its own.  The warp stages each
+// batch of 32 entries itself (lane i the i-th), the staging lane tests its
+// entry's alpha box against the square, and one ballot gives the entries the
+// warp visits; an entry whose box misses the square composites nowhere in it.
+
+template <int TW, int TH> struct SquareShape {
+    static_assert(TW % 8 == 0 && TH % 8 == 0, "the tile splits into 8 x 8 pixel squares");
+    static constexpr int wx = TW / 8;
+    static constexpr int warps = (TW / 8) * (TH / 8);
+    static constexpr int threads = 32 * warps;
+};
+
+// Tile, camera and pixel geometry of one warp square.
+struct SquareGeom {
+    const CamInfo *ci;
+    int tx, ty;            // tile coordinates in its camera
+    float ox, oy;          // pixel origin of the tile
+    int lx, ly;            // tile-local pixel of the lane's pair (left pixel)
+    float2 pxc;            // its two pixel-centre x, tile-local
+    float pyc;             // its pixel-centre y, tile-local
+    float bx0, bx1, by0, by1; // the square's pixel-centre box, tile-local
+};
+
+template <int TW, int TH> __device__ __forceinline__ SquareGeom square_geom(const CamTable &ct, int tile, int warp,
+                                                                            int lane)
+{
+    SquareGeom q;
+    q.ci = &ct.c[camera_of_tile(ct, tile)];
+    const int lt = tile - q.ci->tile_base;
+    q.tx = lt % q.ci->tiles_x;
+    q.ty = lt / q.ci->tiles_x;
+    q.ox = (float)(q.tx * TW);
+    q.oy = (float)(q.ty * TH);
+    const int sx = 8 * (warp % SquareShape<TW, TH>::wx), sy = 8 * (warp / SquareShape<TW, TH>::wx);
+    q.lx = sx + 2 * (lane & 3);
+    q.ly = sy + (lane >> 2);
+    q.pxc = make_float2((float)q.lx + 0.5f, (float)q.lx + 1.5f);
+    q.pyc = (float)q.ly + 0.5f;
+    q.bx0 = (float)sx + 0.5f; q.bx1 = (float)sx + 7.5f;
+    q.by0 = (float)sy + 0.5f; q.by1 = (float)sy + 7.5f;
+    return q;
+}
+
+// Base-2 exponent of a staged entry (e0 = (u, v, A, k), Ds = scaled D) at the
+// lane's pixel pair: the same operations per pixel as quad_power, so every
+// kernel takes the same decisions.  e returns dx + k dy.
+__device__ __forceinline__ float2 pair_power(float4 e0, float Ds, float2 pxc, float pyc, float2 &dx, float &dy,
+                                             float2 &e)
+{
+    dx = __fadd2_rn(pxc, f2(-e0.x));
+    dy = __fadd_rn(pyc, -e0.y);
+    const float kdy = __fmul_rn(e0.w, dy);
+    const float ddy = __fmul_rn(__fmul_rn(Ds, dy), dy);
+    e = __fadd2_rn(dx, f2(kdy));
+    return __ffma2_rn(f2(e0.z), __fmul2_rn(e, e), f2(ddy));
+}
+
 // ---- forward --------------------------------------------------------------
+//
+// Front to back over the visited entries of each batch; a warp stops once all
+// of its pixels have (T would drop below T_min), with no block barrier.
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(TileShape<TW, TH>::threads, 768 / TileShape<TW, TH>::threads)
+__global__ void __launch_bounds__(SquareShape<TW, TH>::threads)
     render_fwd_kernel(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
                       const float4 *__restrict__ rd0, const float4 *__restrict__ rd1, const float4 *__restrict__ rd2,
                       const CamTable *__restrict__ ctp, RenderConsts rc, float *__restrict__ rgb_out,
                       float *__restrict__ T_out, float *__restrict__ T_ws, uint32_t *__restrict__ n_contrib)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
-    constexpr int kRT = TileShape<TW, TH>::threads;
-    __shared__ float4 s0[kRT];
-    __shared__ float4 s1[kRT];
-    __shared__ float s2[kRT];
-    __shared__ float2 s3[kRT];
+    constexpr int kWarps = SquareShape<TW, TH>::warps;
+    __shared__ float4 s0[kWarps][32];
+    __shared__ float4 s1[kWarps][32];
+    __shared__ float s2[kWarps][32];
     const CamTable &ct = *ctp;
     if ((int)blockIdx.x >= ct.total_tiles) return;
-    const TileGeom tg = tile_geom<TW, TH>(ct, blockIdx.x);
-    const TileGeom &cam = tg;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const SquareGeom q = square_geom<TW, TH>(ct, blockIdx.x, warp, lane);
+    const CamInfo &cam = *q.ci;
     const uint2 rg = ranges[blockIdx.x];
     const int start = (int)rg.x, end = (int)rg.y;
-    const WarpBox<TW, TH> wb((int)threadIdx.x >> 5);
-
-    // pixel pair of row 0 (quad elements 0, 1) and row 1 (2, 3), tile-local
-    const float2 px2 = make_float2(tg.lx0, tg.lx0 + 1.f);
-    const float2 py2 = make_float2(tg.ly0, tg.ly0 + 1.f);
-    float2 T[2] = {f2(1.f), f2(1.f)}, Cr[2] = {f2(0.f), f2(0.f)}, Cg[2] = {f2(0.f), f2(0.f)},
-           Cb[2] = {f2(0.f), f2(0.f)};
-    uint32_t last[kQ] = {0, 0, 0, 0};
-    bool dn[kQ];
-#pragma unroll
-    for (int k = 0; k < kQ; k++)
-        dn[k] = tg.px0 + (k & 1) >= cam.width || tg.py0 + (k >> 1) >= cam.height;
-    for (int b = start; b < end; b += kRT) {
-        if (__syncthreads_count(dn[0] && dn[1] && dn[2] && dn[3]) == kRT) break;
-        const int s = b + threadIdx.x;
-        if (s < end) {
-            const uint32_t r = vals[s];
+    const int px = q.tx * TW + q.lx, py = q.ty * TH + q.ly;
+    float2 T = f2(1.f), Cr = f2(0.f), Cg = f2(0.f), Cb = f2(0.f);
+    uint32_t last0 = 0, last1 = 0;
+    bool dn0 = px >= cam.width || py >= cam.height, dn1 = px + 1 >= cam.width || py >= cam.height;
+    for (int b = start; b < end && !__all_sync(0xffffffffu, dn0 && dn1); b += 32) {
+        const int cnt = min(32, end - b);
+        bool visit = false;
+        if (lane < cnt) {
+            const uint32_t r = vals[b + lane];
             const float4 r0 = rd0[r], r1 = rd1[r], r2 = rd2[r];
             const float op = r2.w != 0.f ? 0.f : r1.y; // a record marked culled composites nowhere
-            s0[threadIdx.x] = stage_e0(r0, r2, tg);
-            s1[threadIdx.x] = make_float4(stage_D(r1), op, r1.z, r1.w);
-            s2[threadIdx.x] = r2.x;
-            s3[threadIdx.x] = alpha_box(r0.z, r0.w, r1.x, op, rc.alpha_min);
+            const float4 e0 = stage_e0_at(r0, r2, q.ox, q.oy);
+            s0[warp][lane] = e0;
+            s1[warp][lane] = make_float4(stage_D(r1), op, r1.z, r1.w);
+            s2[warp][lane] = r2.x;
+            const float2 hb = alpha_box(r0.z, r0.w, r1.x, op, rc.alpha_min);
+            visit = !(e0.x + hb.x < q.bx0 || e0.x - hb.x > q.bx1 || e0.y + hb.y < q.by0 || e0.y - hb.y > q.by1);
         }
-        __syncthreads();
-        const int cnt = min(kRT, end - b);
-        for (int j = 0; j < cnt && !(dn[0] && dn[1] && dn[2] && dn[3]); j++) {
-            const float4 p0 = s0[j];
-            if (wb.misses(p0.x, p0.y, s3[j])) continue; // warp-uniform
-            const float4 p1 = s1[j];
-            const float cb = s2[j];
-            const uint32_t pos = (uint32_t)(b - start + j + 1);
-            const QuadPow q = quad_power(p0, p1.x, px2, py2);
-#pragma unroll
-            for (int row = 0; row < 2; row++) {
-                float2 G;
-                const float2 al = pair_alpha(row ? q.r1 : q.r0, p1.y, rc.alpha_max, G);
-                const float2 tT = __ffma2_rn(make_float2(-T[row].x, -T[row].y), al, T[row]); // T (1 - alpha)
-                const int k0 = 2 * row, k1 = 2 * row + 1;
-                const bool ok0 = !dn[k0] && al.x >= rc.alpha_min, ok1 = !dn[k1] && al.y >= rc.alpha_min;
-                const bool st0 = ok0 && tT.x < rc.T_min, st1 = ok1 && tT.y < rc.T_min;
-                const bool c0 = ok0 && !st0, c1 = ok1 && !st1;
-                dn[k0] = dn[k0] || st0;
-                dn[k1] = dn[k1] || st1;
-                const float2 ae = make_float2(c0 ? al.x : 0.f, c1 ? al.y : 0.f); // skipped fragments add nothing
-                const float2 w = __fmul2_rn(ae, T[row]);
-                Cr[row] = __ffma2_rn(w, f2(p1.z), Cr[row]);
-                Cg[row] = __ffma2_rn(w, f2(p1.w), Cg[row]);
-                Cb[row] = __ffma2_rn(w, f2(cb), Cb[row]);
-                T[row] = __ffma2_rn(make_float2(-T[row].x, -T[row].y), ae, T[row]);
-                last[k0] = c0 ? pos : last[k0];
-                last[k1] = c1 ? pos : last[k1];
-            }
+        unsigned m = __ballot_sync(0xffffffffu, visit);
+        __syncwarp();
+        while (m != 0u) {
+            const int jj = __ffs(m) - 1; // front to back
+            m &= m - 1u;
+            const float4 p0 = s0[warp][jj];
+            const float4 p1 = s1[warp][jj];
+            const uint32_t pos = (uint32_t)(b - start + jj + 1);
+            float2 dx, e;
+            float dy;
+            const float2 pw = pair_power(p0, p1.x, q.pxc, q.pyc, dx, dy, e);
+            float2 G;
+            const float2 al = pair_alpha(pw, p1.y, rc.alpha_max, G);
+            const float2 tT = __ffma2_rn(make_float2(-T.x, -T.y), al, T); // T (1 - alpha)
+            const bool ok0 = !dn0 && al.x >= rc.alpha_min, ok1 = !dn1 && al.y >= rc.alpha_min;
+            const bool st0 = ok0 && tT.x < rc.T_min, st1 = ok1 && tT.y < rc.T_min;
+            const bool c0 = ok0 && !st0, c1 = ok1 && !st1;
+            dn0 = dn0 || st0;
+            dn1 = dn1 || st1;
+            const float2 ae = make_float2(c0 ? al.x : 0.f, c1 ? al.y : 0.f); // skipped fragments add nothing
+            const float2 w = __fmul2_rn(ae, T);
+            Cr = __ffma2_rn(w, f2(p1.z), Cr);
+            Cg = __ffma2_rn(w, f2(p1.w), Cg);
+            Cb = __ffma2_rn(w, f2(s2[warp][jj]), Cb);
+            T = __ffma2_rn(make_float2(-T.x, -T.y), ae, T);
+            last0 = c0 ? pos : last0;
+            last1 = c1 ? pos : last1;
+            if (__all_sync(0xffffffffu, dn0 && dn1)) break;
         }
+        __syncwarp();
     }
     const long long np = (long long)cam.width * cam.height;
     float *img = rgb_out + 3 * cam.pix_base;
 #pragma unroll
-    for (int k = 0; k < kQ; k++) {
-        const int px = tg.px0 + (k & 1), py = tg.py0 + (k >> 1);
-        if (px >= cam.width || py >= cam.height) continue;
-        const int row = k >> 1;
-        const float Tk = (k & 1) ? T[row].y : T[row].x;
-        const float cr = (k & 1) ? Cr[row].y : Cr[row].x;
-        const float cg = (k & 1) ? Cg[row].y : Cg[row].x;
-        const float cbk = (k & 1) ? Cb[row].y : Cb[row].x;
-        const long long pix = (long long)py * cam.width + px;
-        img[pix] = cr + Tk * rc.bg[0];
-        img[np + pix] = cg + Tk * rc.bg[1];
-        img[2 * np + pix] = cbk + Tk * rc.bg[2];
+    for (int h = 0; h < 2; h++) {
+        if (px + h >= cam.width || py >= cam.height) continue;
+        const float Tk = h ? T.y : T.x;
+        const long long pix = (long long)py * cam.width + px + h;
+        img[pix] = (h ? Cr.y : Cr.x) + Tk * rc.bg[0];
+        img[np + pix] = (h ? Cg.y : Cg.x) + Tk * rc.bg[1];
+        img[2 * np + pix] = (h ? Cb.y : Cb.x) + Tk * rc.bg[2];
         const long long gp = cam.pix_base + pix;
         if (T_out) T_out[gp] = Tk;
         T_ws[gp] = Tk;
-        n_contrib[gp] = last[k];
+        n_contrib[gp] = h ? last1 : last0;
     }
 }
 
 template <int TW, int TH> static void fwd_launch(gs_workspace *ws, cudaStream_t st, float *rgb, float *T_out)
 {
-    launch_pdl(render_fwd_kernel<TW, TH>, ws->cams.total_tiles, TileShape<TW, TH>::threads, 0, st,
+    launch_pdl(render_fwd_kernel<TW, TH>, ws->cams.total_tiles, SquareShape<TW, TH>::threads, 0, st,
         ws->ranges, ws->tval[ws->tile_buf], ws->rd0, ws->rd1, ws->rd2, ws->d_cams, ws->rc, rgb, T_out, ws->T_final,
         ws->n_contrib);
 }
@@ -555,12 +608,6 @@ cudaError_t launch_render_fwd_importance(gs_workspace *ws, cudaStream_t st, floa
 constexpr int kBwdBatch = 32; // entries staged per batch of the reverse walk (one per lane)
 constexpr int kBwdBufs = 3;   // partial buffers: batches a warp may run ahead, plus one
 
-template <int TW, int TH> struct BwdShape {
-    static_assert(TW % 8 == 0 && TH % 8 == 0, "the adjoint walks 8 x 8 pixel squares");
-    static constexpr int wx = TW / 8;
-    static constexpr int warps = (TW / 8) * (TH / 8);
-    static constexpr int threads = 32 * warps;
-};
 
 struct BwdRenderArgs {
     const uint2 *ranges;
@@ -576,11 +623,11 @@ struct BwdRenderArgs {
 };
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(BwdShape<TW, TH>::threads)
+__global__ void __launch_bounds__(SquareShape<TW, TH>::threads)
     render_bwd_kernel(BwdRenderArgs a, const CamTable *__restrict__ ctp, RenderConsts rc)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
-    constexpr int kWarps = BwdShape<TW, TH>::warps, kRT = BwdShape<TW, TH>::threads;
+    constexpr int kWarps = SquareShape<TW, TH>::warps, kRT = SquareShape<TW, TH>::threads;
     __shared__ float4 s0[kWarps][kBwdBatch];
     __shared__ float4 s1[kWarps][kBwdBatch];
     __shared__ float s2[kWarps][kBwdBatch];
@@ -602,7 +649,7 @@ __global__ void __launch_bounds__(BwdShape<TW, TH>::threads)
     const bool red_own = red9_owner(lane);
     const int red_q = red9_index(lane);
     // the warp's square and the lane's pixel pair (tile-local)
-    const int sx = 8 * (warp % BwdShape<TW, TH>::wx), sy = 8 * (warp / BwdShape<TW, TH>::wx);
+    const int sx = 8 * (warp % SquareShape<TW, TH>::wx), sy = 8 * (warp / SquareShape<TW, TH>::wx);
     const int lx = sx + 2 * (lane & 3), ly = sy + (lane >> 2);
     const float2 pxc = make_float2((float)lx + 0.5f, (float)lx + 1.5f);
     const float pyc = (float)ly + 0.5f;
@@ -697,12 +744,9 @@ __global__ void __launch_bounds__(BwdShape<TW, TH>::threads)
             const float4 p0 = s0[warp][jj];
             const float4 p1 = s1[warp][jj];
             // the forward's own exponent and alpha (the same operations, the same bits)
-            const float2 dx = __fadd2_rn(pxc, f2(-p0.x));
-            const float dy = __fadd_rn(pyc, -p0.y);
-            const float kdy = __fmul_rn(p0.w, dy);
-            const float ddy = __fmul_rn(__fmul_rn(p1.x, dy), dy);
-            const float2 e = __fadd2_rn(dx, f2(kdy));
-            const float2 pw = __ffma2_rn(f2(p0.z), __fmul2_rn(e, e), f2(ddy));
+            float2 dx, e;
+            float dy;
+            const float2 pw = pair_power(p0, p1.x, pxc, pyc, dx, dy, e);
             float2 G;
             const float2 al = pair_alpha(pw, p1.y, rc.alpha_max, G);
             // composited pixels: in front of the pixel's last contribution, alpha >= alpha_min
@@ -790,12 +834,12 @@ cudaError_t launch_render_bwd(gs_workspace *ws, cudaStream_t st, const float *dL
     const unsigned grid = (unsigned)ws->cams.total_tiles;
     kt_begin(ws, GS_KT_RENDER_BWD, st);
     switch (tile_shape_id(ws->cams.tile_w, ws->cams.tile_h)) {
-    case 0: launch_pdl(render_bwd_kernel<16, 16>, grid, BwdShape<16, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
-    case 1: launch_pdl(render_bwd_kernel<32, 8>, grid, BwdShape<32, 8>::threads, 0, st, a, ws->d_cams, ws->rc); break;
-    case 2: launch_pdl(render_bwd_kernel<8, 32>, grid, BwdShape<8, 32>::threads, 0, st, a, ws->d_cams, ws->rc); break;
-    case 3: launch_pdl(render_bwd_kernel<32, 16>, grid, BwdShape<32, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
-    case 4: launch_pdl(render_bwd_kernel<16, 8>, grid, BwdShape<16, 8>::threads, 0, st, a, ws->d_cams, ws->rc); break;
-    case 5: launch_pdl(render_bwd_kernel<8, 16>, grid, BwdShape<8, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 0: launch_pdl(render_bwd_kernel<16, 16>, grid, SquareShape<16, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 1: launch_pdl(render_bwd_kernel<32, 8>, grid, SquareShape<32, 8>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 2: launch_pdl(render_bwd_kernel<8, 32>, grid, SquareShape<8, 32>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 3: launch_pdl(render_bwd_kernel<32, 16>, grid, SquareShape<32, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 4: launch_pdl(render_bwd_kernel<16, 8>, grid, SquareShape<16, 8>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 5: launch_pdl(render_bwd_kernel<8, 16>, grid, SquareShape<8, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
     default: return cudaErrorInvalidValue;
     }
     kt_end(ws, GS_KT_RENDER_BWD, st);
