@@ -2,71 +2,29 @@
 // adjoint, and the instrumented colourless sweep of the importance pass
 // (Sec. 3.2, Fig. 2).
 //
-// One block per tile (64 threads for 16x16); each thread owns a 2x2 pixel
-// quad.  The tile's depth-ordered list is staged through shared memory in
-// batches; every pixel walks the same entry at the same time, and a warp skips
-// an entry whose alpha box misses all its pixels.  Per-Gaussian quantities are
-// block reductions (thread over its quad, warp shuffles -- recursive halving
-// for the adjoint's nine values -- then the warps' partials) rather than
-// per-pixel global atomics.  The backward and
-// the importance sweep write one gradient/score slot per (record, tile) --
-// slot index = the record's first instance + the tile's position inside the
-// record's rectangle -- and a later per-record pass sums a record's slots in
-// a fixed order, so results are bit-reproducible run to run.
+// One block per tile; each warp owns an 8 x 8 pixel square of it (lane l the
+// horizontal pixel pair (2 (l % 4), l / 4), packed FP32x2) and walks the
+// tile's depth-ordered list on its own, staging each batch of 32 entries
+// itself and visiting only the entries whose alpha box meets its square.
+// Per-Gaussian quantities are warp reductions (recursive halving for the
+// adjoint's nine values), then the warps' partials summed in warp order,
+// rather than per-pixel global atomics.  The backward and the importance
+// sweep write one gradient/score slot per (record, tile) -- slot index = the
+// record's first instance + the tile's position inside the record's rectangle
+// -- and a later per-record pass sums a record's slots in a fixed order, so
+// results are bit-reproducible run to run.
 #include "gs_internal.cuh"
 
 namespace gs {
 
-constexpr int kQ = 4;              // pixels per thread (one 2x2 quad)
-
-// A block composites one TW x TH tile with TW * TH / 4 threads.  Thread t owns
-// the quad (qx, qy) = (t % (TW/2), t / (TW/2)); pixel k of the quad is
-// (2 qx + k % 2, 2 qy + k / 2).  For 16 x 16: 64 threads, warp 0 rows 0-7.
-template <int TW, int TH> struct TileShape {
-    static constexpr int threads = TW * TH / 4;
-    static constexpr int warps = threads / 32;
-    static constexpr int qx = TW / 2; // quads per tile row
-    static_assert(threads % 32 == 0, "tile must hold whole warps");
-};
 // Compositing works in tile-local pixel coordinates: pixel centres are exact
 // small floats, and each staged entry's mean is moved to the tile's origin
 // once, from its double-length form u + u_lo, so px - u keeps its full
 // precision however far the tile lies from the image origin.
-struct TileGeom {
-    int cam, tx, ty;
-    int px0, py0;              // pixel of quad element 0 (image coordinates)
-    float ox, oy;              // pixel origin of the tile
-    float lx0, ly0;            // centre of quad element 0, tile-local
-    int width, height;         // of the tile's camera
-    long long pix_base;        // first pixel of the camera in the concatenated outputs
-};
 
-template <int TW, int TH> __device__ __forceinline__ TileGeom tile_geom(const CamTable &ct, int tile)
-{
-    constexpr int QX = TileShape<TW, TH>::qx;
-    TileGeom t;
-    t.cam = camera_of_tile(ct, tile);
-    const CamInfo &ci = ct.c[t.cam];
-    const int lt = tile - ci.tile_base;
-    t.tx = lt % ci.tiles_x;
-    t.ty = lt / ci.tiles_x;
-    t.width = ci.width;
-    t.height = ci.height;
-    t.pix_base = ci.pix_base;
-    const int qx = (int)threadIdx.x % QX, qy = (int)threadIdx.x / QX;
-    t.px0 = t.tx * TW + 2 * qx;
-    t.py0 = t.ty * TH + 2 * qy;
-    t.ox = (float)(t.tx * TW);
-    t.oy = (float)(t.ty * TH);
-    t.lx0 = (float)(2 * qx) + 0.5f;
-    t.ly0 = (float)(2 * qy) + 0.5f;
-    return t;
-}
-
-// ---- packed quad arithmetic (Blackwell FP32x2) ----------------------------------
-// A thread's quad is two rows of two pixels; each row pair is one float2, so
-// the exponent, alpha, transmittance and colour updates are packed FP32x2
-// operations.  The exponent is evaluated from the conic's form
+// ---- packed pair arithmetic (Blackwell FP32x2) ----------------------------------
+// A lane's two pixels are one float2, so the exponent, alpha, transmittance
+// and colour updates are packed FP32x2 operations.  The exponent is evaluated from the conic's form
 // power = -1/2 (A (dx + k dy)^2 + D dy^2), with A and D pre-scaled at staging so
 // it comes out in base 2: G = exp(power) = 2^(log2(e) power).  Every kernel
 // that takes skip decisions (forward, backward, importance) stages and
@@ -80,10 +38,6 @@ __device__ __forceinline__ float4 stage_e0_at(float4 r0, float4 r2, float ox, fl
     return make_float4(__fadd_rn(__fsub_rn(r0.x, ox), r2.y), __fadd_rn(__fsub_rn(r0.y, oy), r2.z),
                        __fmul_rn(r0.z, kNegHalfLog2e), r0.w);
 }
-__device__ __forceinline__ float4 stage_e0(float4 r0, float4 r2, const TileGeom &tg)
-{
-    return stage_e0_at(r0, r2, tg.ox, tg.oy);
-}
 __device__ __forceinline__ float stage_D(float4 r1) { return __fmul_rn(r1.x, kNegHalfLog2e); }
 
 __device__ __forceinline__ float ex2_approx(float x)
@@ -94,31 +48,6 @@ __device__ __forceinline__ float ex2_approx(float x)
 }
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-
-struct QuadPow {
-    float2 r0, r1; // base-2 exponents of the two row pairs
-};
-
-// e0 = staged entry (u, v, A, k), Ds = its scaled D; px2 = the quad's two
-// pixel-centre x, py2 = its two rows' centre y (tile-local).
-__device__ __forceinline__ QuadPow quad_power(float4 e0, float Ds, float2 px2, float2 py2)
-{
-    const float2 dx = __fadd2_rn(px2, f2(-e0.x));
-    const float2 dy = __fadd2_rn(py2, f2(-e0.y));
-    const float2 kdy = __fmul2_rn(f2(e0.w), dy);
-    const float2 ddy = __fmul2_rn(__fmul2_rn(f2(Ds), dy), dy);
-    const float2 A2 = f2(e0.z);
-    QuadPow q;
-    {
-        const float2 e = __fadd2_rn(dx, f2(kdy.x));
-        q.r0 = __ffma2_rn(A2, __fmul2_rn(e, e), f2(ddy.x));
-    }
-    {
-        const float2 e = __fadd2_rn(dx, f2(kdy.y));
-        q.r1 = __ffma2_rn(A2, __fmul2_rn(e, e), f2(ddy.y));
-    }
-    return q;
-}
 
 // alpha = min(alpha_max, o 2^p) of a pixel pair
 __device__ __forceinline__ float2 pair_alpha(float2 p, float o, float amax, float2 &G)
@@ -147,27 +76,6 @@ __device__ __forceinline__ float2 alpha_box(float A, float k, float D, float o, 
     return make_float2(fmaf(sqrtf(tau * fmaf(k * k, iD, 1.f / A)), 1.001f, 0.03125f),
                        fmaf(sqrtf(tau * iD), 1.001f, 0.03125f));
 }
-
-// Tile-local pixel-centre box [x0, x1] x [y0, y1] of warp w's pixels (warp w
-// holds the quads t = 32 w .. 32 w + 31, whole quad rows since 32 is a
-// multiple of the quads per row).
-template <int TW, int TH> struct WarpBox {
-    float x0, x1, y0, y1;
-    __device__ __forceinline__ explicit WarpBox(int w)
-    {
-        constexpr int QX = TileShape<TW, TH>::qx;
-        static_assert(32 % QX == 0, "a warp must hold whole quad rows");
-        x0 = 0.5f;
-        x1 = (float)TW - 0.5f;
-        y0 = 2.f * (float)(32 * w / QX) + 0.5f;
-        y1 = 2.f * (float)((32 * w + 31) / QX) + 1.5f;
-    }
-    // true when the box of half-widths hb around (u, v) misses the warp
-    __device__ __forceinline__ bool misses(float u, float v, float2 hb) const
-    {
-        return u + hb.x < x0 || u - hb.x > x1 || v + hb.y < y0 || v - hb.y > y1;
-    }
-};
 
 __device__ __forceinline__ float warp_sum_f(float v)
 {
@@ -275,8 +183,8 @@ template <int TW, int TH> __device__ __forceinline__ SquareGeom square_geom(cons
 }
 
 // Base-2 exponent of a staged entry (e0 = (u, v, A, k), Ds = scaled D) at the
-// lane's pixel pair: the same operations per pixel as quad_power, so every
-// kernel takes the same decisions.  e returns dx + k dy.
+// lane's pixel pair; every kernel evaluates it through this function, so all
+// take the same decisions.  e returns dx + k dy.
 __device__ __forceinline__ float2 pair_power(float4 e0, float Ds, float2 pxc, float pyc, float2 &dx, float &dy,
                                              float2 &e)
 {
@@ -396,192 +304,6 @@ cudaError_t launch_render_fwd(gs_workspace *ws, cudaStream_t st, float *rgb, flo
     case 3: fwd_launch<32, 16>(ws, st, rgb, T_out); break;
     case 4: fwd_launch<16, 8>(ws, st, rgb, T_out); break;
     case 5: fwd_launch<8, 16>(ws, st, rgb, T_out); break;
-    default: return cudaErrorInvalidValue;
-    }
-    kt_end(ws, GS_KT_RENDER_FWD, st);
-    note_launch();
-    return cudaGetLastError();
-}
-
-// ---- forward fused with the importance raster ----------------------------------
-//
-// One walk over the view's lists computes both the training image (records
-// marked culled composite nowhere) and the importance slots (every record
-// with its own opacity, as the importance sweep renders).  Each entry's
-// exponent and alpha are evaluated once; each pixel carries two
-// transmittances and two stop flags.  Both outputs are those of
-// render_fwd_kernel and importance_raster_kernel bit for bit.
-struct FwdImpArgs {
-    const uint2 *ranges;
-    const uint32_t *vals;
-    const float4 *rd0, *rd1, *rd2;
-    const uint32_t *inst_off;
-    const uint2 *rect;
-    float *rgb_out, *T_out, *T_ws;
-    uint32_t *n_contrib;
-    float2 *slots; // [I]: importance alpha-weight, composited pixels (uint32 bits)
-};
-
-template <int TW, int TH>
-__global__ void __launch_bounds__(TileShape<TW, TH>::threads, 768 / TileShape<TW, TH>::threads)
-    render_fwd_imp_kernel(FwdImpArgs a, const CamTable *__restrict__ ctp, RenderConsts rc)
-{
-    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
-    constexpr int kRT = TileShape<TW, TH>::threads, kWarps = TileShape<TW, TH>::warps;
-    __shared__ float4 s0[kRT];
-    __shared__ float4 s1[kRT]; // (D, training opacity (0 when marked), r, g)
-    __shared__ float s2[kRT];
-    __shared__ float2 s3[kRT]; // alpha box of the record's own opacity
-    __shared__ float s4[kRT];  // the record's own opacity
-    __shared__ unsigned long long s_slot[kRT];
-    __shared__ float s_w[kWarps][kRT];
-    __shared__ uint32_t s_a[kWarps][kRT];
-    const CamTable &ct = *ctp;
-    if ((int)blockIdx.x >= ct.total_tiles) return;
-    const TileGeom tg = tile_geom<TW, TH>(ct, blockIdx.x);
-    const TileGeom &cam = tg;
-    const uint2 rg = a.ranges[blockIdx.x];
-    const int start = (int)rg.x, end = (int)rg.y;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const WarpBox<TW, TH> wb(warp);
-
-    const float2 px2 = make_float2(tg.lx0, tg.lx0 + 1.f);
-    const float2 py2 = make_float2(tg.ly0, tg.ly0 + 1.f);
-    float2 T[2] = {f2(1.f), f2(1.f)}, Cr[2] = {f2(0.f), f2(0.f)}, Cg[2] = {f2(0.f), f2(0.f)},
-           Cb[2] = {f2(0.f), f2(0.f)};
-    float2 Ti[2] = {f2(1.f), f2(1.f)}; // importance transmittance
-    uint32_t last[kQ] = {0, 0, 0, 0};
-    bool dn[kQ], di[kQ];
-#pragma unroll
-    for (int k = 0; k < kQ; k++) {
-        dn[k] = tg.px0 + (k & 1) >= cam.width || tg.py0 + (k >> 1) >= cam.height;
-        di[k] = dn[k];
-    }
-    int b = start;
-    for (; b < end; b += kRT) {
-        if (__syncthreads_count(dn[0] && dn[1] && dn[2] && dn[3] && di[0] && di[1] && di[2] && di[3]) == kRT)
-            break;
-        const int cnt = min(kRT, end - b);
-        if (threadIdx.x < cnt) {
-            const uint32_t r = a.vals[b + threadIdx.x];
-            const float4 r0 = a.rd0[r], r1 = a.rd1[r], r2 = a.rd2[r];
-            s0[threadIdx.x] = stage_e0(r0, r2, tg);
-            s1[threadIdx.x] = make_float4(stage_D(r1), r2.w != 0.f ? 0.f : r1.y, r1.z, r1.w);
-            s2[threadIdx.x] = r2.x;
-            s3[threadIdx.x] = alpha_box(r0.z, r0.w, r1.x, r1.y, rc.alpha_min);
-            s4[threadIdx.x] = r1.y;
-            s_slot[threadIdx.x] = slot_of(a.inst_off, a.rect, r, tg.tx, tg.ty);
-        }
-        __syncthreads();
-        bool wdone = false;
-        for (int j = 0; j < cnt; j++) {
-            const float4 p0 = s0[j];
-            if (!wdone)
-                wdone = __all_sync(0xffffffffu, dn[0] && dn[1] && dn[2] && dn[3] && di[0] && di[1] && di[2] && di[3]);
-            if (wdone || wb.misses(p0.x, p0.y, s3[j])) { // warp-uniform: nothing to add
-                if (lane == 0) { s_w[warp][j] = 0.f; s_a[warp][j] = 0u; }
-                continue;
-            }
-            const float4 p1 = s1[j];
-            const float cb = s2[j], oi = s4[j];
-            const bool train = p1.y != 0.f; // not marked culled
-            const uint32_t pos = (uint32_t)(b - start + j + 1);
-            const QuadPow q = quad_power(p0, p1.x, px2, py2);
-            float wv = 0.f;
-            uint32_t av = 0;
-#pragma unroll
-            for (int row = 0; row < 2; row++) {
-                float2 G;
-                const float2 al = pair_alpha(row ? q.r1 : q.r0, oi, rc.alpha_max, G);
-                const int k0 = 2 * row, k1 = 2 * row + 1;
-                if (train) { // the training image: render_fwd_kernel's update
-                    const float2 tT = __ffma2_rn(make_float2(-T[row].x, -T[row].y), al, T[row]);
-                    const bool ok0 = !dn[k0] && al.x >= rc.alpha_min, ok1 = !dn[k1] && al.y >= rc.alpha_min;
-                    const bool st0 = ok0 && tT.x < rc.T_min, st1 = ok1 && tT.y < rc.T_min;
-                    const bool c0 = ok0 && !st0, c1 = ok1 && !st1;
-                    dn[k0] = dn[k0] || st0;
-                    dn[k1] = dn[k1] || st1;
-                    const float2 ae = make_float2(c0 ? al.x : 0.f, c1 ? al.y : 0.f);
-                    const float2 w = __fmul2_rn(ae, T[row]);
-                    Cr[row] = __ffma2_rn(w, f2(p1.z), Cr[row]);
-                    Cg[row] = __ffma2_rn(w, f2(p1.w), Cg[row]);
-                    Cb[row] = __ffma2_rn(w, f2(cb), Cb[row]);
-                    T[row] = __ffma2_rn(make_float2(-T[row].x, -T[row].y), ae, T[row]);
-                    last[k0] = c0 ? pos : last[k0];
-                    last[k1] = c1 ? pos : last[k1];
-                }
-                { // the importance sweep: importance_raster_kernel's update
-                    const float2 tT = __ffma2_rn(make_float2(-Ti[row].x, -Ti[row].y), al, Ti[row]);
-                    const bool ok0 = !di[k0] && al.x >= rc.alpha_min, ok1 = !di[k1] && al.y >= rc.alpha_min;
-                    const bool st0 = ok0 && tT.x < rc.T_min, st1 = ok1 && tT.y < rc.T_min;
-                    const bool c0 = ok0 && !st0, c1 = ok1 && !st1;
-                    di[k0] = di[k0] || st0;
-                    di[k1] = di[k1] || st1;
-                    const float2 ae = make_float2(c0 ? al.x : 0.f, c1 ? al.y : 0.f);
-                    const float2 w = __fmul2_rn(ae, Ti[row]);
-                    wv += w.x + w.y;
-                    av += (uint32_t)c0 + (uint32_t)c1;
-                    Ti[row] = __ffma2_rn(make_float2(-Ti[row].x, -Ti[row].y), ae, Ti[row]);
-                }
-            }
-            if (__any_sync(0xffffffffu, av != 0)) {
-                wv = warp_sum_f(wv);
-                av = __reduce_add_sync(0xffffffffu, av);
-            }
-            if (lane == 0) { s_w[warp][j] = wv; s_a[warp][j] = av; }
-        }
-        __syncthreads();
-        if (threadIdx.x < cnt) {
-            float wsum = s_w[0][threadIdx.x];
-            uint32_t asum = s_a[0][threadIdx.x];
-#pragma unroll
-            for (int w = 1; w < kWarps; w++) { wsum += s_w[w][threadIdx.x]; asum += s_a[w][threadIdx.x]; }
-            a.slots[s_slot[threadIdx.x]] = make_float2(wsum, __uint_as_float(asum));
-        }
-    }
-    // entries never reached (every pixel of the tile had stopped in both walks)
-    for (int s = b + threadIdx.x; s < end; s += kRT) {
-        const unsigned long long slot = slot_of(a.inst_off, a.rect, a.vals[s], tg.tx, tg.ty);
-        a.slots[slot] = make_float2(0.f, 0.f);
-    }
-    const long long np = (long long)cam.width * cam.height;
-    float *img = a.rgb_out + 3 * cam.pix_base;
-#pragma unroll
-    for (int k = 0; k < kQ; k++) {
-        const int px = tg.px0 + (k & 1), py = tg.py0 + (k >> 1);
-        if (px >= cam.width || py >= cam.height) continue;
-        const int row = k >> 1;
-        const float Tk = (k & 1) ? T[row].y : T[row].x;
-        const float cr = (k & 1) ? Cr[row].y : Cr[row].x;
-        const float cg = (k & 1) ? Cg[row].y : Cg[row].x;
-        const float cbk = (k & 1) ? Cb[row].y : Cb[row].x;
-        const long long pix = (long long)py * cam.width + px;
-        img[pix] = cr + Tk * rc.bg[0];
-        img[np + pix] = cg + Tk * rc.bg[1];
-        img[2 * np + pix] = cbk + Tk * rc.bg[2];
-        const long long gp = cam.pix_base + pix;
-        if (a.T_out) a.T_out[gp] = Tk;
-        a.T_ws[gp] = Tk;
-        a.n_contrib[gp] = last[k];
-    }
-}
-
-cudaError_t launch_render_fwd_importance(gs_workspace *ws, cudaStream_t st, float *rgb, float *T_out)
-{
-    if (ws->cams.total_tiles == 0) return cudaSuccess;
-    FwdImpArgs a;
-    a.ranges = ws->ranges; a.vals = ws->tval[ws->tile_buf]; a.rd0 = ws->rd0; a.rd1 = ws->rd1; a.rd2 = ws->rd2;
-    a.inst_off = ws->inst_off; a.rect = ws->rect; a.rgb_out = rgb; a.T_out = T_out; a.T_ws = ws->T_final;
-    a.n_contrib = ws->n_contrib; a.slots = ws->imp_slots;
-    const unsigned grid = (unsigned)ws->cams.total_tiles;
-    kt_begin(ws, GS_KT_RENDER_FWD, st);
-    switch (tile_shape_id(ws->cams.tile_w, ws->cams.tile_h)) {
-    case 0: launch_pdl(render_fwd_imp_kernel<16, 16>, grid, TileShape<16, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
-    case 1: launch_pdl(render_fwd_imp_kernel<32, 8>, grid, TileShape<32, 8>::threads, 0, st, a, ws->d_cams, ws->rc); break;
-    case 2: launch_pdl(render_fwd_imp_kernel<8, 32>, grid, TileShape<8, 32>::threads, 0, st, a, ws->d_cams, ws->rc); break;
-    case 3: launch_pdl(render_fwd_imp_kernel<32, 16>, grid, TileShape<32, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
-    case 4: launch_pdl(render_fwd_imp_kernel<16, 8>, grid, TileShape<16, 8>::threads, 0, st, a, ws->d_cams, ws->rc); break;
-    case 5: launch_pdl(render_fwd_imp_kernel<8, 16>, grid, TileShape<8, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
     default: return cudaErrorInvalidValue;
     }
     kt_end(ws, GS_KT_RENDER_FWD, st);
@@ -847,7 +569,21 @@ cudaError_t launch_render_bwd(gs_workspace *ws, cudaStream_t st, const float *dL
     return cudaGetLastError();
 }
 
-// ---- importance sweep (colourless forward) -------------------------------------
+// ---- importance sweep (colourless forward), alone or fused with the forward ----
+//
+// The walk of render_fwd_kernel on warp squares with every record at its own
+// opacity (the importance sweep never applies the Cull column it recomputes):
+// per visited entry the warp sums alpha T and the count of composited pixels
+// over its lanes, and, as in the adjoint, the warps' partials of a batch are
+// summed in warp order by the warp that finishes the batch last and written to
+// the entries' importance slots.  Every warp goes through every batch of the
+// tile (staging only the slot ids once its pixels have stopped), so every
+// slot is written.  With FWD the same walk also composites the training image
+// (records marked culled composite nowhere in it): one evaluation of each
+// entry's alpha serves both, the image, T and n_contrib equal
+// render_fwd_kernel's and the slots this kernel's alone, bit for bit.
+
+constexpr int kImpBufs = 3; // partial buffers: batches a warp may run ahead, plus one
 
 struct ImpArgs {
     const uint2 *ranges;
@@ -855,116 +591,218 @@ struct ImpArgs {
     const float4 *rd0, *rd1, *rd2;
     const uint32_t *inst_off;
     const uint2 *rect;
-    float2 *slots; // [I]: alpha-weight (float), composited pixels (uint32 bits)
+    float2 *slots;         // [I]: alpha-weight (float), composited pixels (uint32 bits)
+    DevCounters *ctr;
+    // FWD only
+    float *rgb_out, *T_out, *T_ws;
+    uint32_t *n_contrib;
 };
 
-template <int TW, int TH>
-__global__ void __launch_bounds__(TileShape<TW, TH>::threads)
+template <int TW, int TH, bool FWD>
+__global__ void __launch_bounds__(SquareShape<TW, TH>::threads)
     importance_raster_kernel(ImpArgs a, const CamTable *__restrict__ ctp, RenderConsts rc)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
-    constexpr int kRT = TileShape<TW, TH>::threads, kWarps = TileShape<TW, TH>::warps;
-    __shared__ float4 s0[kRT];
-    __shared__ float2 s1[kRT];
-    __shared__ float2 s3[kRT];
-    __shared__ unsigned long long s_slot[kRT];
-    __shared__ float s_w[kWarps][kRT];
-    __shared__ uint32_t s_a[kWarps][kRT];
+    constexpr int kWarps = SquareShape<TW, TH>::warps;
+    __shared__ float4 s0[kWarps][32];
+    __shared__ float4 s1[kWarps][32]; // (D scaled, own opacity, training opacity, blue)
+    __shared__ float2 s3[FWD ? kWarps : 1][32]; // (red, green) of the training image
+    __shared__ unsigned long long s_slot[kWarps][32];
+    __shared__ float2 s_part[kImpBufs][kWarps][32];
+    __shared__ unsigned s_mask[kImpBufs][kWarps];
+    __shared__ int s_arrive[kImpBufs], s_done[kImpBufs];
     const CamTable &ct = *ctp;
     if ((int)blockIdx.x >= ct.total_tiles) return;
-    const TileGeom tg = tile_geom<TW, TH>(ct, blockIdx.x);
-    const TileGeom &cam = tg;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const SquareGeom q = square_geom<TW, TH>(ct, blockIdx.x, warp, lane);
+    const CamInfo &cam = *q.ci;
     const uint2 rg = a.ranges[blockIdx.x];
     const int start = (int)rg.x, end = (int)rg.y;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const WarpBox<TW, TH> wb(warp);
-    const float2 px2 = make_float2(tg.lx0, tg.lx0 + 1.f);
-    const float2 py2 = make_float2(tg.ly0, tg.ly0 + 1.f);
-    float2 T[2] = {f2(1.f), f2(1.f)};
-    bool dn[kQ];
-#pragma unroll
-    for (int k = 0; k < kQ; k++)
-        dn[k] = tg.px0 + (k & 1) >= cam.width || tg.py0 + (k >> 1) >= cam.height;
-    int b = start;
-    for (; b < end; b += kRT) {
-        if (__syncthreads_count(dn[0] && dn[1] && dn[2] && dn[3]) == kRT) break;
-        const int cnt = min(kRT, end - b);
-        if (threadIdx.x < cnt) {
-            const uint32_t r = a.vals[b + threadIdx.x];
-            const float4 p0 = a.rd0[r], p1 = a.rd1[r];
-            s0[threadIdx.x] = stage_e0(p0, a.rd2[r], tg);
-            s1[threadIdx.x] = make_float2(stage_D(p1), p1.y);
-            s3[threadIdx.x] = alpha_box(p0.z, p0.w, p1.x, p1.y, rc.alpha_min);
-            s_slot[threadIdx.x] = slot_of(a.inst_off, a.rect, r, tg.tx, tg.ty);
-        }
-        __syncthreads();
-        for (int j = 0; j < cnt; j++) {
-            const float4 p0 = s0[j];
-            if (wb.misses(p0.x, p0.y, s3[j])) { // warp-uniform: nothing to add
-                if (lane == 0) { s_w[warp][j] = 0.f; s_a[warp][j] = 0u; }
-                continue;
+    const int px = q.tx * TW + q.lx, py = q.ty * TH + q.ly;
+    const bool out0 = px >= cam.width || py >= cam.height, out1 = px + 1 >= cam.width || py >= cam.height;
+    float2 Ti = f2(1.f);             // importance transmittance
+    bool di0 = out0, di1 = out1;     // importance walk stopped
+    float2 T = f2(1.f), Cr = f2(0.f), Cg = f2(0.f), Cb = f2(0.f); // training image (FWD)
+    uint32_t last0 = 0, last1 = 0;
+    bool dn0 = out0, dn1 = out1;
+    if (threadIdx.x < kImpBufs) { s_arrive[threadIdx.x] = 0; s_done[threadIdx.x] = 0; }
+    __syncthreads();
+    int bi = 0;
+    for (int b = start; b < end; b += 32, bi++) {
+        const int cnt = min(32, end - b);
+        const int buf = bi % kImpBufs;
+        const bool wdone = __all_sync(0xffffffffu, di0 && di1 && (!FWD || (dn0 && dn1)));
+        bool visit = false;
+        if (lane < cnt) {
+            const uint32_t r = a.vals[b + lane];
+            s_slot[warp][lane] = slot_of(a.inst_off, a.rect, r, q.tx, q.ty);
+            if (!wdone) {
+                const float4 r0 = a.rd0[r], r1 = a.rd1[r], r2 = a.rd2[r];
+                const float4 e0 = stage_e0_at(r0, r2, q.ox, q.oy);
+                s0[warp][lane] = e0;
+                s1[warp][lane] = make_float4(stage_D(r1), r1.y, r2.w != 0.f ? 0.f : r1.y, r2.x);
+                if (FWD) s3[FWD ? warp : 0][lane] = make_float2(r1.z, r1.w);
+                // the record's own opacity: the training opacity is the same or 0
+                const float2 hb = alpha_box(r0.z, r0.w, r1.x, r1.y, rc.alpha_min);
+                visit = !(e0.x + hb.x < q.bx0 || e0.x - hb.x > q.bx1 || e0.y + hb.y < q.by0 || e0.y - hb.y > q.by1);
             }
-            const float2 p1 = s1[j];
-            const QuadPow q = quad_power(p0, p1.x, px2, py2);
-            float wv = 0.f;
-            uint32_t av = 0;
-#pragma unroll
-            for (int row = 0; row < 2; row++) {
-                float2 G;
-                const float2 al = pair_alpha(row ? q.r1 : q.r0, p1.y, rc.alpha_max, G);
-                const float2 tT = __ffma2_rn(make_float2(-T[row].x, -T[row].y), al, T[row]);
-                const int k0 = 2 * row, k1 = 2 * row + 1;
-                const bool ok0 = !dn[k0] && al.x >= rc.alpha_min, ok1 = !dn[k1] && al.y >= rc.alpha_min;
+        }
+        const unsigned vmask = __ballot_sync(0xffffffffu, visit);
+        // the partial buffer of this batch is free once batch bi - kImpBufs has been summed
+        if (bi >= kImpBufs) {
+            const int want = bi / kImpBufs;
+            unsigned long long spins = 0;
+            bool gave_up = false;
+            while (*(volatile int *)&s_done[buf] < want) {
+                if (++spins > kSpinLimit) { gave_up = true; break; }
+                __nanosleep(32);
+            }
+            if (__any_sync(0xffffffffu, gave_up)) {
+                if (lane == 0) set_error(a.ctr, GS_ERR_TIMEOUT, kSiteRender);
+                return;
+            }
+            __threadfence_block();
+        }
+        __syncwarp();
+        if (lane == 0) s_mask[buf][warp] = vmask;
+        for (unsigned m = vmask; m != 0u;) {
+            const int jj = __ffs(m) - 1; // front to back
+            m &= m - 1u;
+            const float4 p0 = s0[warp][jj];
+            const float4 p1 = s1[warp][jj];
+            float2 dx, e;
+            float dy;
+            const float2 pw = pair_power(p0, p1.x, q.pxc, q.pyc, dx, dy, e);
+            float2 G;
+            const float2 al = pair_alpha(pw, p1.y, rc.alpha_max, G);
+            if (FWD && p1.z != 0.f) { // the training image: render_fwd_kernel's update
+                const uint32_t pos = (uint32_t)(b - start + jj + 1);
+                const float2 tT = __ffma2_rn(make_float2(-T.x, -T.y), al, T);
+                const bool ok0 = !dn0 && al.x >= rc.alpha_min, ok1 = !dn1 && al.y >= rc.alpha_min;
                 const bool st0 = ok0 && tT.x < rc.T_min, st1 = ok1 && tT.y < rc.T_min;
                 const bool c0 = ok0 && !st0, c1 = ok1 && !st1;
-                dn[k0] = dn[k0] || st0;
-                dn[k1] = dn[k1] || st1;
+                dn0 = dn0 || st0;
+                dn1 = dn1 || st1;
                 const float2 ae = make_float2(c0 ? al.x : 0.f, c1 ? al.y : 0.f);
-                const float2 w = __fmul2_rn(ae, T[row]);
-                wv += w.x + w.y;
-                av += (uint32_t)c0 + (uint32_t)c1;
-                T[row] = __ffma2_rn(make_float2(-T[row].x, -T[row].y), ae, T[row]);
+                const float2 w = __fmul2_rn(ae, T);
+                const float2 rgc = s3[FWD ? warp : 0][jj];
+                Cr = __ffma2_rn(w, f2(rgc.x), Cr);
+                Cg = __ffma2_rn(w, f2(rgc.y), Cg);
+                Cb = __ffma2_rn(w, f2(p1.w), Cb);
+                T = __ffma2_rn(make_float2(-T.x, -T.y), ae, T);
+                last0 = c0 ? pos : last0;
+                last1 = c1 ? pos : last1;
             }
+            // the importance sweep
+            const float2 tT = __ffma2_rn(make_float2(-Ti.x, -Ti.y), al, Ti);
+            const bool ok0 = !di0 && al.x >= rc.alpha_min, ok1 = !di1 && al.y >= rc.alpha_min;
+            const bool st0 = ok0 && tT.x < rc.T_min, st1 = ok1 && tT.y < rc.T_min;
+            const bool c0 = ok0 && !st0, c1 = ok1 && !st1;
+            di0 = di0 || st0;
+            di1 = di1 || st1;
+            const float2 ae = make_float2(c0 ? al.x : 0.f, c1 ? al.y : 0.f);
+            const float2 w = __fmul2_rn(ae, Ti);
+            float wv = w.x + w.y;
+            uint32_t av = (uint32_t)c0 + (uint32_t)c1;
+            Ti = __ffma2_rn(make_float2(-Ti.x, -Ti.y), ae, Ti);
             if (__any_sync(0xffffffffu, av != 0)) {
                 wv = warp_sum_f(wv);
                 av = __reduce_add_sync(0xffffffffu, av);
             }
-            if (lane == 0) { s_w[warp][j] = wv; s_a[warp][j] = av; }
+            if (lane == 0) s_part[buf][warp][jj] = make_float2(wv, __uint_as_float(av));
         }
-        __syncthreads();
-        if (threadIdx.x < cnt) {
-            float wsum = s_w[0][threadIdx.x];
-            uint32_t asum = s_a[0][threadIdx.x];
+        // arrive; the last warp of the tile to finish this batch sums it
+        __syncwarp();
+        int arrived = 0;
+        if (lane == 0) {
+            __threadfence_block();
+            arrived = atomicAdd(&s_arrive[buf], 1);
+        }
+        arrived = __shfl_sync(0xffffffffu, arrived, 0);
+        if (arrived == kWarps - 1) {
+            __threadfence_block();
+            if (lane < cnt) {
+                float ws = 0.f;
+                uint32_t as = 0;
 #pragma unroll
-            for (int w = 1; w < kWarps; w++) { wsum += s_w[w][threadIdx.x]; asum += s_a[w][threadIdx.x]; }
-            a.slots[s_slot[threadIdx.x]] = make_float2(wsum, __uint_as_float(asum));
+                for (int w = 0; w < kWarps; w++)
+                    if ((s_mask[buf][w] >> lane) & 1u) {
+                        const float2 pv = s_part[buf][w][lane];
+                        ws += pv.x;
+                        as += __float_as_uint(pv.y);
+                    }
+                a.slots[s_slot[warp][lane]] = make_float2(ws, __uint_as_float(as));
+            }
+            __syncwarp();
+            if (lane == 0) {
+                s_arrive[buf] = 0;
+                __threadfence_block();
+                *(volatile int *)&s_done[buf] = bi / kImpBufs + 1;
+            }
         }
     }
-    // entries never reached (every pixel of the tile had stopped)
-    for (int s = b + threadIdx.x; s < end; s += kRT) {
-        const unsigned long long slot = slot_of(a.inst_off, a.rect, a.vals[s], tg.tx, tg.ty);
-        a.slots[slot] = make_float2(0.f, 0.f);
+    if (FWD) {
+        const long long np = (long long)cam.width * cam.height;
+        float *img = a.rgb_out + 3 * cam.pix_base;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            if (px + h >= cam.width || py >= cam.height) continue;
+            const float Tk = h ? T.y : T.x;
+            const long long pix = (long long)py * cam.width + px + h;
+            img[pix] = (h ? Cr.y : Cr.x) + Tk * rc.bg[0];
+            img[np + pix] = (h ? Cg.y : Cg.x) + Tk * rc.bg[1];
+            img[2 * np + pix] = (h ? Cb.y : Cb.x) + Tk * rc.bg[2];
+            const long long gp = cam.pix_base + pix;
+            if (a.T_out) a.T_out[gp] = Tk;
+            a.T_ws[gp] = Tk;
+            a.n_contrib[gp] = h ? last1 : last0;
+        }
     }
+}
+
+template <bool FWD> static cudaError_t importance_launch(gs_workspace *ws, cudaStream_t st, const ImpArgs &a)
+{
+    const unsigned grid = (unsigned)ws->cams.total_tiles;
+    switch (tile_shape_id(ws->cams.tile_w, ws->cams.tile_h)) {
+    case 0: launch_pdl(importance_raster_kernel<16, 16, FWD>, grid, SquareShape<16, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 1: launch_pdl(importance_raster_kernel<32, 8, FWD>, grid, SquareShape<32, 8>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 2: launch_pdl(importance_raster_kernel<8, 32, FWD>, grid, SquareShape<8, 32>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 3: launch_pdl(importance_raster_kernel<32, 16, FWD>, grid, SquareShape<32, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 4: launch_pdl(importance_raster_kernel<16, 8, FWD>, grid, SquareShape<16, 8>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    case 5: launch_pdl(importance_raster_kernel<8, 16, FWD>, grid, SquareShape<8, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
+}
+
+static ImpArgs importance_args(gs_workspace *ws)
+{
+    ImpArgs a{};
+    a.ranges = ws->ranges; a.vals = ws->tval[ws->tile_buf]; a.rd0 = ws->rd0; a.rd1 = ws->rd1; a.rd2 = ws->rd2;
+    a.inst_off = ws->inst_off; a.rect = ws->rect; a.slots = ws->imp_slots; a.ctr = ws->ctr;
+    return a;
 }
 
 cudaError_t launch_importance_raster(gs_workspace *ws, cudaStream_t st)
 {
     if (ws->cams.total_tiles == 0) return cudaSuccess;
-    ImpArgs a;
-    a.ranges = ws->ranges; a.vals = ws->tval[ws->tile_buf]; a.rd0 = ws->rd0; a.rd1 = ws->rd1; a.rd2 = ws->rd2;
-    a.inst_off = ws->inst_off; a.rect = ws->rect; a.slots = ws->imp_slots;
-    const unsigned grid = (unsigned)ws->cams.total_tiles;
     kt_begin(ws, GS_KT_IMPORTANCE, st);
-    switch (tile_shape_id(ws->cams.tile_w, ws->cams.tile_h)) {
-    case 0: launch_pdl(importance_raster_kernel<16, 16>, grid, TileShape<16, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
-    case 1: launch_pdl(importance_raster_kernel<32, 8>, grid, TileShape<32, 8>::threads, 0, st, a, ws->d_cams, ws->rc); break;
-    case 2: launch_pdl(importance_raster_kernel<8, 32>, grid, TileShape<8, 32>::threads, 0, st, a, ws->d_cams, ws->rc); break;
-    case 3: launch_pdl(importance_raster_kernel<32, 16>, grid, TileShape<32, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
-    case 4: launch_pdl(importance_raster_kernel<16, 8>, grid, TileShape<16, 8>::threads, 0, st, a, ws->d_cams, ws->rc); break;
-    case 5: launch_pdl(importance_raster_kernel<8, 16>, grid, TileShape<8, 16>::threads, 0, st, a, ws->d_cams, ws->rc); break;
-    default: return cudaErrorInvalidValue;
-    }
+    cudaError_t e = importance_launch<false>(ws, st, importance_args(ws));
+    if (e != cudaSuccess) return e;
     kt_end(ws, GS_KT_IMPORTANCE, st);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render_fwd_importance(gs_workspace *ws, cudaStream_t st, float *rgb, float *T_out)
+{
+    if (ws->cams.total_tiles == 0) return cudaSuccess;
+    ImpArgs a = importance_args(ws);
+    a.rgb_out = rgb; a.T_out = T_out; a.T_ws = ws->T_final; a.n_contrib = ws->n_contrib;
+    kt_begin(ws, GS_KT_RENDER_FWD, st);
+    cudaError_t e = importance_launch<true>(ws, st, a);
+    if (e != cudaSuccess) return e;
+    kt_end(ws, GS_KT_RENDER_FWD, st);
     note_launch();
     return cudaGetLastError();
 }
