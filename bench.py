@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--n", type=int, default=N_GAUSS, help="Gaussians (default: the 5M workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the short serving run of the default line")
+    ap.add_argument("--no-train8", action="store_true",
+                    help="skip the multi-view training figures (8 views of 1600x1200, 20M Gaussians) of the default line")
     ap.add_argument("--workload", default="city5M", choices=["city5M", "train8-city20M", "batch64-city10M",
                                                               "serve-city30M"],
                     help="city5M: the single-view training step (the default line); the others run the "
@@ -451,6 +453,22 @@ def serving_short(step, torch):
     return out
 
 
+TRAIN8_STEPS, TRAIN8_LFL_STEPS = 10, 3
+
+
+def train8_figures(torch):
+    """The realistic training step: 8 views of 1600x1200 per step cycling
+    through a pool of 64 aerial views of a 20M-Gaussian city, the whole step a
+    CUDA graph (Adam with deferred zero-gradient steps, scale regulariser),
+    and the batched step against the plain per-view path with the same
+    arithmetic (dense gradients, dense Adam, no regulariser) and their losses."""
+    from paper_2605_13794_gb300 import workloads as WL
+    r = WL.train_batch_workload(steps=TRAIN8_STEPS, warmup=2, per_view_steps=TRAIN8_LFL_STEPS)
+    keep = ("n", "views", "width", "height", "steps", "graph_ms", "graph_mpix_per_s", "eager_ms", "eager_mpix_per_s",
+            "graph_equals_eager", "graph_step", "loss_first", "loss_last", "like_for_like")
+    return {k: r[k] for k in keep}
+
+
 # ---- CPU oracle on a bounded sample ------------------------------------------------
 
 class OracleSample:
@@ -825,6 +843,7 @@ def main():
     roof_imp["composited_per_launch"] = imp_composited
     latency = render_latency(step, g, B, torch)
     serving = serving_short(step, torch) if not args.no_serving else None
+    train8 = train8_figures(torch) if not args.no_train8 else None
     line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -849,6 +868,7 @@ def main():
             "alu_peaks_unit": "TFLOP/s (FMA) and T results/s (ex2)",
             "render_latency": latency,
             "serving": serving,
+            "train8": train8,
             "e2e": {"value": job_rate(P, e2e_ms, world) / 1e6, "unit": "Mpix/s", "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,

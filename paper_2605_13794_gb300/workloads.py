@@ -127,21 +127,30 @@ def train_batch_workload(n: int = 20_000_000, views: int = 8, width: int = 1600,
     le = torch.cat(losses_e).cpu().numpy()
     lg = torch.cat(losses_g).cpu().numpy()
     same_params = all(torch.equal(a, b) for a, b in zip(ga.params(), gb.params()))
-    # the plain per-view path: one view at a time, dense gradients, dense Adam
-    per_view = _per_view_path(g, cams, targets, params, views, per_view_steps, capd)
+    eager.ws.close()
+    graph.ws.close()
+    del eager, graph, ga, gb
+    # batched against the plain per-view path, like for like
+    lfl = _like_for_like(g, cams, targets, params, views, per_view_steps, capd)
     pix = views * width * height
+    lfl.update({"batched_mpix_per_s": pix / lfl["batched_ms"] / 1e3,
+                "per_view_mpix_per_s": pix / lfl["per_view_ms"] / 1e3,
+                "speedup": lfl["per_view_ms"] / lfl["batched_ms"],
+                "arithmetic": "dense gradients, dense Adam, no scale regulariser, eager, in both arms"})
     return {"n": n, "views": views, "width": width, "height": height, "steps": steps,
             "graph_ms": graph_ms, "eager_ms": eager_ms, "graph_mpix_per_s": pix / graph_ms / 1e3,
-            "eager_mpix_per_s": pix / eager_ms / 1e3, "per_view_ms": per_view["ms"],
-            "per_view_mpix_per_s": pix / per_view["ms"] / 1e3,
+            "eager_mpix_per_s": pix / eager_ms / 1e3,
+            "graph_step": "views cycling through a pool of 64, L1 + 0.2 D-SSIM, scale regulariser, Adam with "
+                          "deferred zero-gradient steps (exact), flush inside the timed region",
             "graph_equals_eager": bool(np.array_equal(le, lg)) and same_params,
             "loss_first": float(le[0]), "loss_last": float(le[-1]),
-            "per_view_vs_batched_loss_rel": per_view["loss_rel"]}
+            "like_for_like": lfl}
 
 
 class _PerViewPath:
     """The plain per-view path: one view at a time (preprocess, sort, render,
-    loss, dense backward accumulated over the views), then a dense Adam step."""
+    loss, dense backward accumulated over the views), then a dense Adam step.
+    No scale regulariser: like the batched arm it is compared with."""
 
     def __init__(self, g, cams, targets, params, views, capd):
         n = g.n
@@ -164,43 +173,74 @@ class _PerViewPath:
             ws.photometric_loss(self.rgb.view(1, 3, H, W), self.targets[i:i + 1], 0.2, self.l1, self.dL)
             self.dL.mul_(1.0 / views)  # the batch loss is the mean over its views
             self.loss.add_(self.l1, alpha=1.0 / views)
-            # Eq. 5 on the last view's visible set only: the per-view path
-            # never sees the batch's visible set as a whole
-            ws.render_bwd(gt, self.dL, grads, accumulate=j > 0, scale_reg_beta=10.0 if j == views - 1 else 0.0)
+            ws.render_bwd(gt, self.dL, grads, accumulate=j > 0)
         B.adam_step([(p, gr, mm, vv, LRS[q], 0.9, 0.999, 1e-15) for q, (p, gr, mm, vv) in
                      enumerate(zip(gt.params(), grads.params(), m.params(), v.params()))], step=step_no)
         return self.loss
 
 
-def _per_view_path(g, cams, targets, params, views, steps, capd):
-    """The first `steps` steps of the batched loop from the same start, one
-    view at a time; returns its ms per step and the largest relative
-    difference of its losses from the batched eager loop's."""
-    path = _PerViewPath(g, cams, targets, params, views, capd)
+class _BatchedDense:
+    """The batched step with the per-view path's arithmetic: one preprocess /
+    bin_sort / render / loss / backward over all views of the step, dense
+    gradients, a dense Adam step, no scale regulariser."""
+
+    def __init__(self, g, cams, targets, params, views, capd):
+        n = g.n
+        self.H, self.W = targets.shape[2], targets.shape[3]
+        self.cams, self.targets, self.params, self.views = cams, targets, params, views
+        self.ws = B.Workspace(max_gaussians=n, max_records=capd["max_records"], max_instances=capd["max_instances"],
+                              max_tiles=views * B.tiles_of(cams[0]), max_pixels=views * self.W * self.H,
+                              max_cameras=views)
+        self.rgb = torch.empty(views * 3 * self.H * self.W, device="cuda")
+        self.dL = torch.empty_like(self.rgb)
+        self.loss = torch.zeros(1, device="cuda")
+
+    def step(self, gt, m, v, grads, idx, step_no):
+        ws, H, W, V = self.ws, self.H, self.W, self.views
+        ws.preprocess(gt, [self.cams[i] for i in idx], self.params)
+        ws.bin_sort()
+        ws.render_fwd(self.rgb)
+        ws.photometric_loss(self.rgb.view(V, 3, H, W), self.targets[idx], 0.2, self.loss, self.dL)
+        ws.render_bwd(gt, self.dL, grads, accumulate=False)
+        B.adam_step([(p, gr, mm, vv, LRS[q], 0.9, 0.999, 1e-15) for q, (p, gr, mm, vv) in
+                     enumerate(zip(gt.params(), grads.params(), m.params(), v.params()))], step=step_no)
+        return self.loss
+
+
+def _like_for_like(g, cams, targets, params, views, steps, capd):
+    """Batched against per-view at the same accuracy: both arms run the same
+    `steps` steps (views cycling through the pool) from the same start with
+    the same arithmetic -- dense gradients, a dense Adam step, no scale
+    regulariser -- so their losses must agree step by step.  Returns each
+    arm's ms per step and the largest relative difference of their losses."""
     pool = targets.shape[0]
-    # warm-up on scratch state: every kernel of the path is loaded before timing
-    scratch = B.GaussianTensors.from_host(g)
-    path.step(scratch, scratch.zeros_like(), scratch.zeros_like(), scratch.zeros_like(), list(range(views)), 1)
-    torch.cuda.synchronize()
-    del scratch
-    gt = B.GaussianTensors.from_host(g)
-    m, v, grads = gt.zeros_like(), gt.zeros_like(), gt.zeros_like()
-    ref = TrainStep(B.GaussianTensors.from_host(g), cams[:views], targets[:views], params, LRS, capacity=capd)
-    rel, total_ms = 0.0, 0.0
-    for k in range(steps):
-        idx = [(k * views + j) % pool for j in range(views)]
+    out = {}
+    losses = {}
+    for name, cls in (("batched", _BatchedDense), ("per_view", _PerViewPath)):
+        path = cls(g, cams, targets, params, views, capd)
+        # warm-up on scratch state: every kernel of the path is loaded before timing
+        scratch = B.GaussianTensors.from_host(g)
+        path.step(scratch, scratch.zeros_like(), scratch.zeros_like(), scratch.zeros_like(), list(range(views)), 1)
+        torch.cuda.synchronize()
+        del scratch
+        gt = B.GaussianTensors.from_host(g)
+        m, v, grads = gt.zeros_like(), gt.zeros_like(), gt.zeros_like()
+        ls = []
         e0, e1 = _events()
         e0.record()
-        loss = path.step(gt, m, v, grads, idx, k + 1)
+        for k in range(steps):
+            idx = [(k * views + j) % pool for j in range(views)]
+            ls.append(path.step(gt, m, v, grads, idx, k + 1).clone())
         e1.record()
         torch.cuda.synchronize()
-        total_ms += e0.elapsed_time(e1)
-        ref.set_views([cams[i] for i in idx], targets[idx])
-        ref.run(step=k + 1)
-        torch.cuda.synchronize()
-        rel = max(rel, abs(loss.item() - ref.loss.item()) / abs(ref.loss.item()))
-    path.ws.close()
-    return {"ms": total_ms / steps, "loss_rel": rel}
+        path.ws.sync_status()
+        path.ws.close()
+        out[name + "_ms"] = e0.elapsed_time(e1) / steps
+        losses[name] = torch.cat(ls).double().cpu().numpy()
+        del gt, m, v, grads
+    out["loss_rel_max"] = float(np.max(np.abs(losses["per_view"] - losses["batched"]) / np.abs(losses["batched"])))
+    out["steps"] = steps
+    return out
 
 
 # ---- batched render of many cameras -------------------------------------------------
