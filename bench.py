@@ -369,6 +369,50 @@ def bwd_roofline(fragments, composited, instances, pixels, kernel_ms, sm_mhz, pe
     return r
 
 
+# Algorithmic bytes of the memory-bound kernels of the step (each read or
+# written once; the units are the view's counts):
+#   view gate: per Gaussian its mean 12 B, level 1 B and mean drift 4 B; per
+#     candidate its log-scales 12 B and their drift 4 B read, its id 4 B and
+#     camera mask 8 B written
+#   depth sort of the records: per record and pass 16 B (key and value read
+#     and written; the first pass reads no values) and 4 B of the histogram read
+#   tile sort of the instances: the same per instance and pass
+#   slot reduction: per instance 36 B (its slot); per record 16 B of indices
+#     and 36 B of summed gradient written
+#   projection adjoint: per visible Gaussian 44 B of shape and opacity read and
+#     its 236 B gradient row written; per record 64 B (ids, record, gradient)
+#   SSIM statistics / gradient: per pixel and channel 24 B / 28 B
+#   deferred Adam's step: per visible Gaussian 59 parameters x 24 B (p, m, v
+#     read and written) and its 236 B gradient row
+HBM_KERNELS = {
+    "gate_count_kernel": ("GS_KT_GATE", lambda c: 17 * c["n"] + 28 * c["n_candidates"]),
+    "depth_sort": ("GS_KT_DEPTH_SORT", lambda c: 16 * c["depth_passes"] * c["n_records"]),
+    "tile_sort": ("GS_KT_TILE_SORT", lambda c: (16 * c["tile_passes"] + 4) * c["n_instances"]),
+    "reduce_slots_kernel": ("GS_KT_REDUCE_SLOTS", lambda c: 36 * c["n_instances"] + 52 * c["n_records"]),
+    "preprocess_bwd_kernel": ("GS_KT_PREPROCESS_BWD", lambda c: 280 * c["n_visible"] + 64 * c["n_records"]),
+    "ssim_fwd_kernel": ("GS_KT_SSIM_FWD", lambda c: 24 * 3 * c["pixels"]),
+    "ssim_bwd_kernel": ("GS_KT_SSIM_BWD", lambda c: 28 * 3 * c["pixels"]),
+    "lazy_list_vec_kernel (gradient step)": ("GS_KT_ADAM_GRAD", lambda c: (59 * 24 + 236) * c["n_visible"]),
+}
+
+
+def hbm_rooflines(kernel_ms, c, peaks):
+    """Each memory-bound kernel's algorithmic bytes over its mean launch time,
+    against the measured copy bandwidth."""
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    out = {}
+    for name, (_, nbytes) in HBM_KERNELS.items():
+        ms = kernel_ms.get(name)
+        if not ms:
+            continue
+        b = nbytes(c)
+        gbs = b / (ms * 1e-3) / 1e9
+        out[name] = {"bound": "hbm", "kernel_ms": round(ms, 4), "algorithmic_bytes_per_launch": int(b),
+                     "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback", "traffic": None}
+    return out
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -791,13 +835,16 @@ def main():
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(diag)]
     # and the per-launch device time of the forward and the importance raster in
     # these one-stream steps (event pairs around each launch)
-    step.ws.kernel_timing(True, kernels=[B.GS_KT_RENDER_FWD, B.GS_KT_IMPORTANCE])
+    timed = [("render_fwd_kernel", B.GS_KT_RENDER_FWD), ("importance_raster_kernel", B.GS_KT_IMPORTANCE)] + \
+        [(name, getattr(B, kid)) for name, (kid, _) in HBM_KERNELS.items()] + [("project_kernel", B.GS_KT_PROJECT)]
+    step.ws.kernel_timing(True, kernels=[kid for _, kid in timed])
     for k in range(diag):
         step.run(evs[k])
     torch.cuda.synchronize()
-    for name, kid in (("render_fwd_kernel", B.GS_KT_RENDER_FWD), ("importance_raster_kernel", B.GS_KT_IMPORTANCE)):
+    for name, kid in timed:
         t, n_l = step.ws.kernel_time(kid)
-        kernel_ms[name] = max_over_ranks(t / max(n_l, 1), world)
+        if n_l:
+            kernel_ms[name] = max_over_ranks(t / n_l, world)
     step.ws.kernel_timing(False)
     stage_ms = {name: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(diag))
                 for i, name in enumerate(step.stage_names)}
@@ -841,6 +888,10 @@ def main():
     roof_imp = alu_roofline("importance_raster_kernel", BWD_FLOP_EVAL * frag + IMP_FLOP_COMPOSITE * imp_composited,
                             frag, kernel_ms["importance_raster_kernel"], alu, peaks, sm_mhz)
     roof_imp["composited_per_launch"] = imp_composited
+    tw, th = (int(x) for x in args.tile.split("x"))
+    tiles = ((cam.width + tw - 1) // tw) * ((cam.height + th - 1) // th)
+    roof_hbm = hbm_rooflines(kernel_ms, dict(counts, n=g.n, pixels=P, depth_passes=4,
+                                             tile_passes=(max(1, (tiles - 1).bit_length()) + 7) // 8), peaks)
     latency = render_latency(step, g, B, torch)
     serving = serving_short(step, torch) if not args.no_serving else None
     train8 = train8_figures(torch) if not args.no_train8 else None
@@ -863,7 +914,7 @@ def main():
             "counts": {k: counts[k] for k in ("n_records", "n_instances", "n_visible")},
             "kernel_ms": {k: round(v, 4) for k, v in kernel_ms.items()},
             "roofline": roof,
-            "roofline_other": {"render_fwd_kernel": roof_fwd, "importance_raster_kernel": roof_imp},
+            "roofline_other": {"render_fwd_kernel": roof_fwd, "importance_raster_kernel": roof_imp, **roof_hbm},
             "alu_peaks": {k: (round(v / 1e12, 3) if k != "sms" else v) for k, v in alu.items()},
             "alu_peaks_unit": "TFLOP/s (FMA) and T results/s (ex2)",
             "render_latency": latency,

@@ -178,6 +178,7 @@ typedef struct {
                                  last composited one: the (pixel, entry) pairs the backward walks.
                                  Counted by gs_render_bwd, reset by gs_preprocess */
     int64_t composited;       /* those of the pairs above that composite (alpha >= alpha_min) */
+    int64_t n_candidates;     /* Gaussians the view gate passed on to the projection */
 } gs_counts;
 
 typedef struct {
@@ -496,11 +497,20 @@ int gs_workspace_set_spin_limit(gs_workspace *ws, uint64_t spins);
  * it), so a captured graph stays valid while timing is turned off and on; the
  * pairs are numbered again from the first each time timing is turned on. */
 enum {
-    GS_KT_RENDER_FWD = 0, /* gs_render_fwd's compositing kernel */
-    GS_KT_RENDER_BWD = 1, /* the compositing adjoint (per (record, tile) slots) */
-    GS_KT_IMPORTANCE = 2, /* the importance sweep's rasteriser */
-    GS_KT_COUNT = 3,
-    GS_KT_ALL = (1 << 3) - 1 /* mask of every timed kernel */
+    GS_KT_RENDER_FWD = 0,      /* gs_render_fwd's compositing kernel */
+    GS_KT_RENDER_BWD = 1,      /* the compositing adjoint (per (record, tile) slots) */
+    GS_KT_IMPORTANCE = 2,      /* the importance sweep's rasteriser */
+    GS_KT_GATE = 3,            /* the view gate's pass over every Gaussian (gs_preprocess) */
+    GS_KT_PROJECT = 4,         /* the projection of the gate's candidates (gs_preprocess) */
+    GS_KT_DEPTH_SORT = 5,      /* gs_bin_sort's depth sort of the records, all of its kernels */
+    GS_KT_TILE_SORT = 6,       /* gs_bin_sort's sort of the instances by tile, all of its kernels */
+    GS_KT_REDUCE_SLOTS = 7,    /* the per-record sum of the adjoint's gradient slots */
+    GS_KT_PREPROCESS_BWD = 8,  /* the projection adjoint (per Gaussian) */
+    GS_KT_SSIM_FWD = 9,        /* gs_photometric_loss: the SSIM statistics and coefficient maps */
+    GS_KT_SSIM_BWD = 10,       /* gs_photometric_loss: the gradient from the coefficient maps */
+    GS_KT_ADAM_GRAD = 11,      /* the deferred Adam's step of the Gaussians with records */
+    GS_KT_COUNT = 12,
+    GS_KT_ALL = (1 << 12) - 1 /* mask of every timed kernel */
 };
 int gs_kernel_timing(gs_workspace *ws, int32_t kernels);
 int gs_kernel_time(gs_workspace *ws, int32_t kernel, double *total_ms, int64_t *launches);

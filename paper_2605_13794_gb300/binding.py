@@ -40,8 +40,10 @@ EXPORTS = ("gs_default_params", "gs_last_error", "gs_workspace_create", "gs_work
 GS_CULL_OFF, GS_CULL_DROP, GS_CULL_MARK = 0, 1, 2
 
 # kernels gs_kernel_timing brackets with events (include/gsblitz.h)
-GS_KT_RENDER_FWD, GS_KT_RENDER_BWD, GS_KT_IMPORTANCE = range(3)
-GS_KT_ALL = (1 << 3) - 1
+(GS_KT_RENDER_FWD, GS_KT_RENDER_BWD, GS_KT_IMPORTANCE, GS_KT_GATE, GS_KT_PROJECT, GS_KT_DEPTH_SORT, GS_KT_TILE_SORT,
+ GS_KT_REDUCE_SLOTS, GS_KT_PREPROCESS_BWD, GS_KT_SSIM_FWD, GS_KT_SSIM_BWD, GS_KT_ADAM_GRAD) = range(12)
+GS_KT_COUNT = 12
+GS_KT_ALL = (1 << GS_KT_COUNT) - 1
 
 
 class GSError(RuntimeError):
@@ -96,7 +98,7 @@ class GSCounts(ctypes.Structure):
     _fields_ = [("n_records", ctypes.c_int64), ("n_instances", ctypes.c_int64), ("n_visible", ctypes.c_int64),
                 ("records_needed", ctypes.c_int64), ("instances_needed", ctypes.c_int64),
                 ("error", ctypes.c_int32), ("error_site", ctypes.c_int32), ("fragments", ctypes.c_int64),
-                ("composited", ctypes.c_int64)]
+                ("composited", ctypes.c_int64), ("n_candidates", ctypes.c_int64)]
 
 
 class GSAluPeak(ctypes.Structure):

@@ -48,9 +48,9 @@ struct Layout {
 struct Offsets {
     size_t cand_g, cand_mask, gate_g, gate_mask, rec_first, cgrad, rec_g, rec_cam, rd0, rd1, rd2, rect, tt, inst_off, clampm, rgrad, dkey0, dkey1, dval0, dval1;
     size_t tkey0, tkey1, tval0, tval1, slots, imp_slots, ranges, n_contrib, T_final, imp_w, imp_a, sel_cum, sel_bsum;
-    size_t selk0, selk1, selv0, selv1, loss_maps, loss_partial, lb_status, rx_status, rx_hist, rx_off, red_partial,
+    size_t selk0, selk1, selv0, selv1, loss_maps, loss_partial, lb_status, rx_status, red_partial,
         ctr, d_cams, d_adam_step, d_adam_coef;
-    size_t mkey0, mkey1, mval0, mval1, mcum, mbsum, mrx_status, mlb, mhist, moff, mctr;
+    size_t mkey0, mkey1, mval0, mval1, mcum, mbsum, mrx_status, mlb, mhist, mctr;
     size_t total;
     size_t lb_words, rx_words, red_words, loss_partial_words;
 };
@@ -106,10 +106,10 @@ Offsets plan(const gs_capacity &c)
     o.lb_words = nb + 1;
     o.lb_status = L.take<unsigned long long>(o.lb_words);
     const size_t items = (R > I ? R : I);
-    o.rx_words = (items / (gs::kSortThreads * 4) + 1) * 256 + 1; // for the smallest (1024-key) blocks
+    // the histograms, then the look-back state of up to four passes, for the
+    // smallest (1024-key) blocks
+    o.rx_words = gs::kRxHistWords + 4 * ((items / (gs::kSortThreads * 4) + 1) * 256 + 1);
     o.rx_status = L.take<uint32_t>(o.rx_words);
-    o.rx_hist = L.take<uint32_t>(4 * 256);
-    o.rx_off = L.take<uint32_t>(4 * 256);
     o.red_words = R / 128 + 2;
     o.red_partial = L.take<float>(o.red_words);
     o.ctr = L.take<gs::DevCounters>(1);
@@ -126,7 +126,6 @@ Offsets plan(const gs_capacity &c)
     o.mrx_status = L.take<uint32_t>(NM ? (NM / (gs::kSortThreads * 8) + 1) * 256 + 1 : 0);
     o.mlb = L.take<unsigned long long>(NM ? NM / 256 + 3 : 0);
     o.mhist = L.take<uint32_t>(4 * 256);
-    o.moff = L.take<uint32_t>(4 * 256);
     o.mctr = L.take<gs::DevCounters>(1);
     o.total = (L.off + 255) & ~(size_t)255;
     return o;
@@ -298,8 +297,7 @@ int gs_workspace_create(const gs_capacity *cap, gs_workspace **out)
     ws->lb_words = o.lb_words;
     ws->rx_status = (uint32_t *)(b + o.rx_status);
     ws->rx_words = o.rx_words;
-    ws->rx_hist = (uint32_t *)(b + o.rx_hist);
-    ws->rx_off = (uint32_t *)(b + o.rx_off);
+    ws->rx_hist = ws->rx_status; // the first kRxHistWords words
     ws->red_partial = (float *)(b + o.red_partial);
     ws->red_words = o.red_words;
     ws->ctr = (gs::DevCounters *)(b + o.ctr);
@@ -313,7 +311,6 @@ int gs_workspace_create(const gs_capacity *cap, gs_workspace **out)
     ws->mrx_status = (uint32_t *)(b + o.mrx_status);
     ws->mlb = (unsigned long long *)(b + o.mlb);
     ws->mhist = (uint32_t *)(b + o.mhist);
-    ws->moff = (uint32_t *)(b + o.moff);
     ws->mctr = (gs::DevCounters *)(b + o.mctr);
     e = cudaMemset(ws->ctr, 0, sizeof(gs::DevCounters));
     if (e == cudaSuccess) e = cudaMemset(ws->d_cams, 0, sizeof(gs::CamTable));
@@ -547,9 +544,11 @@ int gs_bin_sort(gs_workspace *ws, gs_stream stream)
     cudaStream_t st = (cudaStream_t)stream;
     // 1. depth order of the records
     int ob = 0;
+    gs::kt_begin(ws, GS_KT_DEPTH_SORT, st);
     CK(gs::launch_radix_sort(ws, st, ws->dkey, ws->dval, &ws->ctr->n_records, (unsigned long long)ws->cap.max_records,
                              32, true, false, ob),
        "gs_bin_sort(depth)");
+    gs::kt_end(ws, GS_KT_DEPTH_SORT, st);
     ws->depth_buf = ob;
     // 2. emission of (tile, record) instances in depth order
     CK(cudaMemsetAsync(&ws->ctr->n_instances, 0, sizeof(unsigned long long), st), "gs_bin_sort");
@@ -558,9 +557,11 @@ int gs_bin_sort(gs_workspace *ws, gs_stream stream)
     // 3. stable sort by global tile id
     int bits = 0;
     while ((1ll << bits) < (long long)ws->cams.total_tiles) bits++;
+    gs::kt_begin(ws, GS_KT_TILE_SORT, st);
     CK(gs::launch_radix_sort(ws, st, ws->tkey, ws->tval, &ws->ctr->n_instances,
                              (unsigned long long)ws->cap.max_instances, bits, false, false, ob),
        "gs_bin_sort(tiles)");
+    gs::kt_end(ws, GS_KT_TILE_SORT, st);
     ws->tile_buf = ob;
     // 4. tile ranges
     CK(gs::launch_ranges(ws, st), "gs_bin_sort(ranges)");
@@ -923,6 +924,7 @@ int gs_workspace_counts(gs_workspace *ws, gs_counts *out, gs_stream stream)
     out->error_site = d.error_site;
     out->fragments = (int64_t)d.fragments;
     out->composited = (int64_t)d.composited;
+    out->n_candidates = (int64_t)d.n_candidates;
     return GS_OK;
 }
 

@@ -56,6 +56,7 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
+constexpr size_t kRxHistWords = 4 * 256;  // radix histograms: 256 buckets for each of up to 4 passes
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;          // keys per thread in a radix pass (default)
 constexpr int kSortTile = kSortThreads * kSortItems;
@@ -254,6 +255,51 @@ __device__ __forceinline__ T block_exclusive_scan_256(T v, T *smem_warp /*[8]*/,
     return wpre + x - v;
 }
 
+// ---- bulk copies (cp.async.bulk) and shared-memory barriers ----------------
+// One thread arms a barrier with the bytes it expects and issues bulk copies
+// from global to shared memory that complete on it; the threads that read the
+// data wait on the barrier's phase.  Addresses and sizes of a bulk copy are
+// multiples of 16 bytes.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// makes initialised barriers visible to the bulk-copy engine
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Waits for the phase of the given parity to complete, at most `limit` tries;
+// false when it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, unsigned long long limit)
+{
+    for (unsigned long long i = 0; i < limit; i++) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(smem_addr(bar)), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 } // namespace gs
 
 // ---- workspace (host struct, device buffers) -------------------------------
@@ -306,10 +352,9 @@ struct gs_workspace {
     // scan / sort scratch
     unsigned long long *lb_status; // [max(blocks)+1] single-value look-back + ticket
     size_t lb_words;
-    uint32_t *rx_status; // [blocks * 256 + 1] radix look-back + ticket
+    uint32_t *rx_status; // radix: [4][256] histograms, then per pass [blocks * 256 + 1] look-back + ticket
     size_t rx_words;
-    uint32_t *rx_hist;   // [4][256]
-    uint32_t *rx_off;    // [4][256]
+    uint32_t *rx_hist;   // [4][256]: the first kRxHistWords words of rx_status (also a scratch of 1024 words)
     float *red_partial;  // [blocks] reduction partials of the adjoint (scale regulariser)
     size_t red_words;
     gs::DevCounters *ctr;
@@ -321,7 +366,7 @@ struct gs_workspace {
     double *mbsum;               // [N / 4096 + 2]
     uint32_t *mrx_status;        // radix look-back, [(N / 2048 + 1) * 256 + 1]
     unsigned long long *mlb;     // single-value look-back, [N / 256 + 3]
-    uint32_t *mhist, *moff;      // [4][256]
+    uint32_t *mhist;             // [4][256]
     gs::DevCounters *mctr;       // item count (n_records) and errors of the model-level calls
     int *d_adam_step;      // device Adam step counter (graph-replayable optimizer step)
     // deferred zero-gradient Adam steps (gs_adam_lazy_enable): a Gaussian's p, m,

@@ -22,8 +22,8 @@ namespace gs {
 
 cudaError_t launch_radix_sort_scratch(cudaStream_t st, uint32_t *keys[2], uint32_t *vals[2],
                                       const unsigned long long *count, unsigned long long cap, int bits,
-                                      bool vals_identity, uint32_t *status, uint32_t *hist, uint32_t *off,
-                                      DevCounters *ctr, int &out_buf);
+                                      bool vals_identity, uint32_t *status, uint32_t *hist, DevCounters *ctr,
+                                      int &out_buf);
 cudaError_t launch_mass_scan(cudaStream_t st, const uint32_t *sorted, const float *w, double *bsum, double *cum,
                              const DevCounters *ctr, unsigned long long cap);
 
@@ -218,7 +218,7 @@ __global__ void count_views_kernel(const uint32_t *rec_g, const float4 *rd2, con
 static cudaError_t sort_model_keys(gs_workspace *ws, cudaStream_t st, long long n, int &ob)
 {
     return launch_radix_sort_scratch(st, ws->mkey, ws->mval, &ws->mctr->n_records, (unsigned long long)n, 32, true,
-                                     ws->mrx_status, ws->mhist, ws->moff, ws->mctr, ob);
+                                     ws->mrx_status, ws->mhist, ws->mctr, ob);
 }
 
 cudaError_t launch_prune_sample(gs_workspace *ws, cudaStream_t st, const float *s, const float *expo, long long n,

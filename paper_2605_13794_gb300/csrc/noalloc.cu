@@ -33,8 +33,8 @@ namespace gs {
 
 cudaError_t launch_radix_sort_scratch(cudaStream_t st, uint32_t *keys[2], uint32_t *vals[2],
                                       const unsigned long long *count, unsigned long long cap, int bits,
-                                      bool vals_identity, uint32_t *status, uint32_t *hist, uint32_t *off,
-                                      DevCounters *ctr, int &out_buf);
+                                      bool vals_identity, uint32_t *status, uint32_t *hist, DevCounters *ctr,
+                                      int &out_buf);
 cudaError_t launch_mass_scan_fixed(cudaStream_t st, const uint32_t *sorted, const float *w, unsigned long long *bsum,
                                    unsigned long long *cum, const DevCounters *ctr, unsigned long long cap);
 
@@ -54,8 +54,7 @@ constexpr size_t kOffCum = align256(kOffVal1 + 4 * (size_t)kVisMaxGaussians);
 constexpr size_t kOffBsum = align256(kOffCum + 8 * (size_t)kVisMaxGaussians);
 constexpr size_t kOffStatus = align256(kOffBsum + 8 * (kVisScanBlocks + 1));
 constexpr size_t kOffHist = align256(kOffStatus + 4 * (kVisSortBlocks * 256 + 1));
-constexpr size_t kOffOff = align256(kOffHist + 4 * 1024);
-constexpr size_t kVisScratchBytes = align256(kOffOff + 4 * 1024);
+constexpr size_t kVisScratchBytes = align256(kOffHist + 4 * 1024);
 
 static __device__ __align__(256) unsigned char g_vis_scratch[kVisScratchBytes];
 
@@ -167,7 +166,6 @@ int gs_visible_set_static(const float *w, int64_t n, float vis_mass, uint32_t *c
     unsigned long long *bsum = reinterpret_cast<unsigned long long *>(scratch + kOffBsum);
     uint32_t *status = reinterpret_cast<uint32_t *>(scratch + kOffStatus);
     uint32_t *hist = reinterpret_cast<uint32_t *>(scratch + kOffHist);
-    uint32_t *off = reinterpret_cast<uint32_t *>(scratch + kOffOff);
     const unsigned blocks = (unsigned)((n + 255) / 256);
     const long long words = (n + 31) / 32;
     launch_pdl(vis_init_kernel, blocks, 256, 0, st, w, n, scratch);
@@ -176,7 +174,7 @@ int gs_visible_set_static(const float *w, int64_t n, float vis_mass, uint32_t *c
     note_launch();
     int ob = 0;
     if ((e = launch_radix_sort_scratch(st, keys, vals, &ctr->n_records, (unsigned long long)n, 32, true, status, hist,
-                                       off, ctr, ob)) != cudaSuccess ||
+                                       ctr, ob)) != cudaSuccess ||
         (e = launch_mass_scan_fixed(st, vals[ob], w, bsum, cum, ctr, (unsigned long long)n)) != cudaSuccess)
         return vis_fail(GS_ERR_CUDA, "gs_visible_set_static: a kernel launch failed");
     launch_pdl(vis_apply_kernel, blocks, 256, 0, st, w, n, vals[ob], cum, vis_mass, cull_out, cvis_accum,

@@ -266,9 +266,13 @@ cudaError_t launch_loss(gs_workspace *ws, cudaStream_t st, const float *img, con
     unsigned long long *acc = reinterpret_cast<unsigned long long *>(ws->loss_partial); // [B][2]
     cudaError_t e = cudaMemsetAsync(acc, 0, 2 * (size_t)B * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
+    kt_begin(ws, GS_KT_SSIM_FWD, st);
     launch_pdl(ssim_fwd_kernel, grid, 256, 0, st, img, tgt, H, W, win, 0.01f * 0.01f, 0.03f * 0.03f, maps, acc);
+    kt_end(ws, GS_KT_SSIM_FWD, st);
     note_launch();
+    kt_begin(ws, GS_KT_SSIM_BWD, st);
     launch_pdl(ssim_bwd_kernel, grid, 256, 0, st, img, tgt, H, W, win, maps, lambda, B, dL);
+    kt_end(ws, GS_KT_SSIM_BWD, st);
     note_launch();
     launch_pdl(loss_finalize_kernel, 1, 32, 0, st, acc, B, H, W, lambda, loss_out);
     note_launch();
@@ -652,6 +656,44 @@ __device__ __forceinline__ void lazy_unit(int u, int &k, int &el, int &row)
     else { k = 3; el = 0; row = 10; }                              // opacity
 }
 
+// The gradient step of one unit (a float4 of SH or quaternion, or a scalar)
+// of Gaussian i: the zero-gradient steps it missed, then step t with its
+// gradient, exactly lazy_param's steps.  Every load it needs (last step,
+// p, m, v, gradient) is issued before any is used, so a unit waits for memory
+// once.
+__device__ __forceinline__ void lazy_grad_unit(const LazyArgs &a, const float *grad, long long i, int u, int k,
+                                               long long idx, int t)
+{
+    const int from = a.last[i];
+    if (u > 12) { // a scalar
+        float pv = a.p[k][idx], mv = a.m[k][idx], vv = a.v[k][idx];
+        const float g = grad[0];
+        if (from >= t) return;
+        if ((__float_as_uint(mv) | __float_as_uint(vv)) != 0u)
+            for (int s = from + 1; s <= t - 1; s++)
+                adam_one(pv, 0.f, mv, vv, a.b1, a.b2, a.hist[10 * s + k], a.hist[10 * s + 5 + k], a.eps);
+        adam_one(pv, g, mv, vv, a.b1, a.b2, a.hist[10 * t + k], a.hist[10 * t + 5 + k], a.eps);
+        a.p[k][idx] = pv; a.m[k][idx] = mv; a.v[k][idx] = vv;
+        return;
+    }
+    const float4 p4 = *reinterpret_cast<const float4 *>(a.p[k] + idx);
+    const float4 m4 = *reinterpret_cast<const float4 *>(a.m[k] + idx);
+    const float4 v4 = *reinterpret_cast<const float4 *>(a.v[k] + idx);
+    const float g[4] = {grad[0], grad[1], grad[2], grad[3]};
+    if (from >= t) return;
+    float pv[4] = {p4.x, p4.y, p4.z, p4.w}, mv[4] = {m4.x, m4.y, m4.z, m4.w}, vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        if ((__float_as_uint(mv[c]) | __float_as_uint(vv[c])) != 0u)
+            for (int s = from + 1; s <= t - 1; s++)
+                adam_one(pv[c], 0.f, mv[c], vv[c], a.b1, a.b2, a.hist[10 * s + k], a.hist[10 * s + 5 + k], a.eps);
+        adam_one(pv[c], g[c], mv[c], vv[c], a.b1, a.b2, a.hist[10 * t + k], a.hist[10 * t + 5 + k], a.eps);
+    }
+    *reinterpret_cast<float4 *>(a.p[k] + idx) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+    *reinterpret_cast<float4 *>(a.m[k] + idx) = make_float4(mv[0], mv[1], mv[2], mv[3]);
+    *reinterpret_cast<float4 *>(a.v[k] + idx) = make_float4(vv[0], vv[1], vv[2], vv[3]);
+}
+
 template <int MODE> __global__ void __launch_bounds__(256) lazy_list_vec_kernel(LazyArgs a, LazyItems it)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
@@ -662,20 +704,24 @@ template <int MODE> __global__ void __launch_bounds__(256) lazy_list_vec_kernel(
         const int u = (int)(e - j * kLazyUnits);
         long long i;
         if (!lazy_item<MODE>(it, j, i)) continue;
-        const int from = a.last[i];
-        if (from >= t) continue;
         int k, el, row;
         lazy_unit(u, k, el, row);
         const long long idx = i * group_len(k) + el;
+        if (MODE == kLazyGrad) {
+            lazy_grad_unit(a, it.cgrad + j * kGradRow + row, i, u, k, idx, t);
+            continue;
+        }
+        const int from = a.last[i];
+        if (from >= t) continue;
+        // a catch-up (no gradient): only units with a moment that is not +0 move
         if (u > 12) { // a scalar
-            const float grad = MODE == kLazyGrad ? it.cgrad[j * kGradRow + row] : 0.f;
-            lazy_param<MODE>(a, k, idx, from, t, grad);
+            lazy_param<MODE>(a, k, idx, from, t, 0.f);
             continue;
         }
         const float4 m4 = *reinterpret_cast<const float4 *>(a.m[k] + idx);
         const float4 v4 = *reinterpret_cast<const float4 *>(a.v[k] + idx);
         float mv[4] = {m4.x, m4.y, m4.z, m4.w}, vv[4] = {v4.x, v4.y, v4.z, v4.w};
-        bool zero[4], any = MODE == kLazyGrad;
+        bool zero[4], any = false;
 #pragma unroll
         for (int c = 0; c < 4; c++) {
             zero[c] = (__float_as_uint(mv[c]) | __float_as_uint(vv[c])) == 0u;
@@ -684,15 +730,11 @@ template <int MODE> __global__ void __launch_bounds__(256) lazy_list_vec_kernel(
         if (!any) continue; // every component a fixed point
         const float4 p4 = *reinterpret_cast<const float4 *>(a.p[k] + idx);
         float pv[4] = {p4.x, p4.y, p4.z, p4.w};
-        const int to = MODE == kLazyGrad ? t - 1 : t;
 #pragma unroll
         for (int c = 0; c < 4; c++) {
             if (!zero[c])
-                for (int s2 = from + 1; s2 <= to; s2++)
+                for (int s2 = from + 1; s2 <= t; s2++)
                     adam_one(pv[c], 0.f, mv[c], vv[c], a.b1, a.b2, a.hist[10 * s2 + k], a.hist[10 * s2 + 5 + k], a.eps);
-            if (MODE == kLazyGrad)
-                adam_one(pv[c], it.cgrad[j * kGradRow + row + c], mv[c], vv[c], a.b1, a.b2, a.hist[10 * t + k],
-                         a.hist[10 * t + 5 + k], a.eps);
         }
         *reinterpret_cast<float4 *>(a.p[k] + idx) = make_float4(pv[0], pv[1], pv[2], pv[3]);
         *reinterpret_cast<float4 *>(a.m[k] + idx) = make_float4(mv[0], mv[1], mv[2], mv[3]);
@@ -769,7 +811,9 @@ template <int MODE>
 static cudaError_t launch_lazy_list(gs_workspace *ws, cudaStream_t st, const LazyArgs &a, unsigned long long cap)
 {
     const LazyItems it = lazy_items(ws, 0);
+    if (MODE == kLazyGrad) kt_begin(ws, GS_KT_ADAM_GRAD, st);
     launch_pdl(lazy_list_vec_kernel<MODE>, lazy_grid(ws, cap * kLazyUnits), 256, 0, st, a, it);
+    if (MODE == kLazyGrad) kt_end(ws, GS_KT_ADAM_GRAD, st);
     note_launch();
     launch_pdl(lazy_fin_kernel<MODE>, lazy_grid(ws, cap), 256, 0, st, a, it);
     note_launch();

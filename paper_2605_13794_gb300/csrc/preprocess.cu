@@ -395,9 +395,15 @@ __device__ __forceinline__ void stage_cameras(const CamTable &ct, CamInfo *s_cam
 // plane and the conservative screen test -- everything that is cheap and
 // rejects most of a city scene -- producing an order-preserving list of
 // candidate Gaussians with a bit per camera that may still be active.
-// Thread t of block b owns Gaussians b*256*kGateItems + k*256 + t.  Every load
-// a Gaussian may need (mean, level, log-scale, the Cull word of camera 0) is
-// issued up front, so a thread waits for memory once, not once per test.
+// The Gaussians come in chunks of kGateChunk; thread t of the block that takes
+// chunk c owns Gaussians c*kGateChunk + k*256 + t.  What every test needs
+// (mean, level, mean drift) streams in: either as bulk copies of the chunk into
+// shared memory, double-buffered so that the next chunk is in flight while this
+// one is tested (persistent blocks), or, where the arrays are not 16-byte
+// aligned, as plain loads issued up front.  The log-scales (and their drift)
+// are read only for the few Gaussians past the LOD and near tests.
+constexpr int kGateChunk = 256 * kGateItems;
+
 struct GateShared {
     CamInfo cams[GS_MAX_CAMERAS];
     float thr2[kMaxLod + 1];
@@ -406,38 +412,74 @@ struct GateShared {
     unsigned total;
 };
 
-__device__ __forceinline__ void gate_masks(const GaussPtrs &g, const PreOut &o, const CamTable &ct,
-                                           const RenderConsts &rc, GateShared &sh, long long block0,
-                                           unsigned long long mask[kGateItems])
-{
-    const int ncam = ct.n, tw = ct.tile_w, th = ct.tile_h;
-    const long long n = g.n;
-    // first the loads every test needs (mean, level, Cull word, mean drift) ...
+// One chunk as the bulk copies leave it in shared memory.
+struct GateStage {
+    float mean[3 * kGateChunk];
+    float drift[kGateChunk];     // drift bound of the mean (deferred Adam steps)
+    uint8_t lod[kGateChunk];
+};
+
+struct GateItems {
     float mx[kGateItems], my[kGateItems], mz[kGateItems];
     int lod[kGateItems];
-    uint32_t cw[kGateItems];
-    float dm[kGateItems]; // drift bound of the mean (deferred Adam steps), 0 when up to date
+    uint32_t cw[kGateItems]; // the Cull word of camera 0 (GS_CULL_DROP)
+    float dm[kGateItems];    // drift bound of the mean, 0 when up to date
+};
+
+__device__ __forceinline__ void gate_load_plain(const GaussPtrs &g, const PreOut &o, const RenderConsts &rc,
+                                                long long block0, GateItems &it)
+{
+    const long long n = g.n;
 #pragma unroll
     for (int k = 0; k < kGateItems; k++) {
         const long long i = block0 + k * 256 + threadIdx.x;
         const bool ok = i < n;
-        mx[k] = ok ? g.mean[3 * i] : 0.f;
-        my[k] = ok ? g.mean[3 * i + 1] : 0.f;
-        mz[k] = ok ? g.mean[3 * i + 2] : 0.f;
-        lod[k] = (ok && rc.lod_enable && g.lod) ? (int)g.lod[i] : 0;
-        cw[k] = (ok && rc.cull_enable == GS_CULL_DROP && o.cull) ? o.cull[i >> 5] : 0u;
-        dm[k] = (ok && o.drift) ? o.drift[i] : 0.f;
+        it.mx[k] = ok ? g.mean[3 * i] : 0.f;
+        it.my[k] = ok ? g.mean[3 * i + 1] : 0.f;
+        it.mz[k] = ok ? g.mean[3 * i + 2] : 0.f;
+        it.lod[k] = (ok && rc.lod_enable && g.lod) ? (int)g.lod[i] : 0;
+        it.cw[k] = (ok && rc.cull_enable == GS_CULL_DROP && o.cull) ? o.cull[i >> 5] : 0u;
+        it.dm[k] = (ok && o.drift) ? o.drift[i] : 0.f;
     }
-    // ... in flight while the cameras and LOD thresholds are staged
-    if (threadIdx.x == 0) {
+}
+
+// A whole chunk (every item below n) from its staged copy.
+__device__ __forceinline__ void gate_load_staged(const GateStage &sg, const GaussPtrs &g, const PreOut &o,
+                                                 const RenderConsts &rc, long long block0, GateItems &it)
+{
 #pragma unroll
-        for (int l = 0; l <= kMaxLod; l++) {
-            sh.thr2[l] = rc.lod_thr2[l];
-            sh.thr[l] = sqrtf(rc.lod_thr2[l]);
-        }
+    for (int k = 0; k < kGateItems; k++) {
+        const int j = k * 256 + threadIdx.x;
+        const long long i = block0 + j;
+        it.mx[k] = sg.mean[3 * j];
+        it.my[k] = sg.mean[3 * j + 1];
+        it.mz[k] = sg.mean[3 * j + 2];
+        it.lod[k] = (rc.lod_enable && g.lod) ? (int)sg.lod[j] : 0;
+        it.cw[k] = (rc.cull_enable == GS_CULL_DROP && o.cull) ? o.cull[i >> 5] : 0u;
+        it.dm[k] = o.drift ? sg.drift[j] : 0.f;
     }
-    stage_cameras(ct, sh.cams);
-    if (ncam == 1) {
+}
+
+// Issues the bulk copies of chunk c (a whole chunk) into sg, completing on bar.
+__device__ __forceinline__ void gate_issue(GateStage &sg, unsigned long long *bar, const GaussPtrs &g,
+                                           const PreOut &o, const RenderConsts &rc, long long c)
+{
+    const bool lod = rc.lod_enable && g.lod, drift = o.drift != nullptr;
+    const unsigned bytes = 12u * kGateChunk + (lod ? kGateChunk : 0u) + (drift ? 4u * kGateChunk : 0u);
+    mbar_expect_tx(bar, bytes);
+    bulk_copy_g2s(sg.mean, g.mean + 3 * kGateChunk * c, 12u * kGateChunk, bar);
+    if (lod) bulk_copy_g2s(sg.lod, g.lod + kGateChunk * c, kGateChunk, bar);
+    if (drift) bulk_copy_g2s(sg.drift, o.drift + kGateChunk * c, 4u * kGateChunk, bar);
+}
+
+template <bool kOneCam>
+__device__ __forceinline__ void gate_masks(const GaussPtrs &g, const PreOut &o, const CamTable &ct,
+                                           const RenderConsts &rc, GateShared &sh, long long block0,
+                                           const GateItems &it, unsigned long long mask[kGateItems])
+{
+    const int ncam = ct.n, tw = ct.tile_w, th = ct.tile_h;
+    const long long n = g.n;
+    if (kOneCam) {
         // one camera: the LOD, Cull and near tests of every item, then the
         // shape (log-scales, their drift) of the items still in, then the
         // screen test
@@ -446,12 +488,12 @@ __device__ __forceinline__ void gate_masks(const GaussPtrs &g, const PreOut &o, 
 #pragma unroll
         for (int k = 0; k < kGateItems; k++) {
             const long long i = block0 + k * 256 + threadIdx.x;
-            const float m[3] = {mx[k], my[k], mz[k]};
-            const bool lod_ok = lod_pass_margin(m, lod[k], cam, rc, sh.thr2, sh.thr, dm[k]);
-            const bool culled = rc.cull_enable == GS_CULL_DROP && ((cw[k] >> (i & 31)) & 1u);
+            const float m[3] = {it.mx[k], it.my[k], it.mz[k]};
+            const bool lod_ok = lod_pass_margin(m, it.lod[k], cam, rc, sh.thr2, sh.thr, it.dm[k]);
+            const bool culled = rc.cull_enable == GS_CULL_DROP && ((it.cw[k] >> (i & 31)) & 1u);
             float tz, ez;
             camera_z(m, cam, tz, ez);
-            const bool near_ok = tz + ez + dm[k] > rc.znear; // the exact near test is the projection's
+            const bool near_ok = tz + ez + it.dm[k] > rc.znear; // the exact near test is the projection's
             in[k] = i < n && lod_ok && !culled && near_ok;
         }
         float lsmax[kGateItems];
@@ -468,10 +510,10 @@ __device__ __forceinline__ void gate_masks(const GaussPtrs &g, const PreOut &o, 
         for (int k = 0; k < kGateItems; k++) {
             mask[k] = 0;
             if (!in[k]) continue;
-            const float m[3] = {mx[k], my[k], mz[k]};
+            const float m[3] = {it.mx[k], it.my[k], it.mz[k]};
             float t[3], te[3];
             camera_point(m, cam, t, te);
-            te[0] += dm[k]; te[1] += dm[k]; te[2] += dm[k];
+            te[0] += it.dm[k]; te[1] += it.dm[k]; te[2] += it.dm[k];
             const float smax = 1.0001f * __expf(lsmax[k]);
             mask[k] = maybe_on_screen(t, te, smax, cam, tw, th, rc) ? 1ull : 0ull;
         }
@@ -481,16 +523,17 @@ __device__ __forceinline__ void gate_masks(const GaussPtrs &g, const PreOut &o, 
             mask[k] = 0;
             const long long i = block0 + k * 256 + threadIdx.x;
             if (i >= n) continue;
-            const float m[3] = {mx[k], my[k], mz[k]};
+            const float m[3] = {it.mx[k], it.my[k], it.mz[k]};
+            const float dm = it.dm[k];
             float smax = -1.f;
             for (int c = 0; c < ncam; c++) {
                 const CamInfo &cam = sh.cams[c];
-                if (!lod_pass_margin(m, lod[k], cam, rc, sh.thr2, sh.thr, dm[k])) continue;
-                if (rc.cull_enable == GS_CULL_DROP && (c == 0 ? ((cw[k] >> (i & 31)) & 1u) : cull_bit(o, c, i)))
+                if (!lod_pass_margin(m, it.lod[k], cam, rc, sh.thr2, sh.thr, dm)) continue;
+                if (rc.cull_enable == GS_CULL_DROP && (c == 0 ? ((it.cw[k] >> (i & 31)) & 1u) : cull_bit(o, c, i)))
                     continue;
                 float t[3], te[3];
                 camera_point(m, cam, t, te);
-                te[0] += dm[k]; te[1] += dm[k]; te[2] += dm[k];
+                te[0] += dm; te[1] += dm; te[2] += dm;
                 if (!(t[2] + te[2] > rc.znear)) continue; // the exact near test is the projection's
                 if (smax < 0.f) {
                     const float dl = o.drift ? o.drift[n + i] : 0.f;
@@ -545,29 +588,84 @@ __device__ __forceinline__ unsigned gate_ranks(const unsigned long long mask[kGa
 
 // The gate runs as count, scan, gather: no block waits on another (an
 // in-order look-back chain makes the blocks of a wave, which all finish their
-// counts together, wait for one another); each block first writes its
-// candidates to its own range, and the gather moves only candidates.
-__global__ void __launch_bounds__(256, 3) gate_count_kernel(GaussPtrs g, PreOut o, const CamTable *__restrict__ ctp,
-                                                            RenderConsts rc, unsigned long long *counts)
+// counts together, wait for one another); each chunk's candidates go first to
+// the chunk's own range, and the gather moves only candidates.
+// kBulk: persistent blocks, chunk c, c + gridDim.x, ...; the chunks copied
+// whole (all but a partial last one) arrive by bulk copies one chunk ahead.  A
+// copy that does not complete within spin_limit waits sets GS_ERR_TIMEOUT; the
+// block then waits (again bounded) for its copies in flight, records empty
+// counts for its remaining chunks and returns.
+template <bool kOneCam, bool kBulk>
+__global__ void __launch_bounds__(256, kOneCam ? 4 : 3) gate_count_kernel(GaussPtrs g, PreOut o,
+                                                                         const CamTable *__restrict__ ctp,
+                                                                         RenderConsts rc, unsigned long long *counts,
+                                                                         unsigned long long spin_limit)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     __shared__ GateShared sh;
-    unsigned long long mask[kGateItems];
-    unsigned bal[kGateItems];
-    const long long block0 = (long long)blockIdx.x * 256 * kGateItems;
-    gate_masks(g, o, *ctp, rc, sh, block0, mask);
-    const unsigned total = gate_ranks(mask, bal, sh);
-    if (threadIdx.x == 0) counts[blockIdx.x] = total;
-    // the block's candidates, in order, at the start of its own range
+    __shared__ __align__(16) GateStage stage[kBulk ? 2 : 1];
+    __shared__ __align__(8) unsigned long long bar[2];
+    __shared__ int s_fail;
+    const long long nchunks = (g.n + kGateChunk - 1) / kGateChunk;
+    const long long nwhole = kBulk ? g.n / kGateChunk : 0; // chunks that come by bulk copy
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int l = 0; l <= kMaxLod; l++) {
+            sh.thr2[l] = rc.lod_thr2[l];
+            sh.thr[l] = sqrtf(rc.lod_thr2[l]);
+        }
+        s_fail = 0;
+        if (kBulk) {
+            mbar_init(&bar[0], 1);
+            mbar_init(&bar[1], 1);
+            mbar_init_fence();
+            if ((long long)blockIdx.x < nwhole) gate_issue(stage[0], &bar[0], g, o, rc, blockIdx.x);
+        }
+    }
+    stage_cameras(*ctp, sh.cams); // ends with a block barrier
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-#pragma unroll
-    for (int k = 0; k < kGateItems; k++) {
-        if (mask[k]) {
-            const long long pos = block0 + sh.cnt[k][warp] + __popc(bal[k] & lt);
-            o.gate_g[pos] = (uint32_t)(block0 + k * 256 + threadIdx.x);
-            o.gate_mask[pos] = mask[k];
+    int k = 0;
+    for (long long c = blockIdx.x; c < nchunks; c += gridDim.x, k++) {
+        const long long block0 = c * kGateChunk;
+        GateItems it;
+        if (kBulk && c < nwhole) {
+            const long long cn = c + gridDim.x;
+            // the next chunk's copy, into the buffer the previous chunk used
+            if (threadIdx.x == 0 && cn < nwhole) gate_issue(stage[(k + 1) & 1], &bar[(k + 1) & 1], g, o, rc, cn);
+            if (!mbar_wait(&bar[k & 1], (unsigned)(k >> 1) & 1u, spin_limit)) {
+                set_error(o.ctr, GS_ERR_TIMEOUT, kSitePreprocess);
+                s_fail = 1;
+            }
+            __syncthreads();
+            if (s_fail) {
+                if (threadIdx.x == 0) { // the copies still in flight land before the block's memory is released
+                    mbar_wait(&bar[k & 1], (unsigned)(k >> 1) & 1u, spin_limit);
+                    if (cn < nwhole) mbar_wait(&bar[(k + 1) & 1], (unsigned)((k + 1) >> 1) & 1u, spin_limit);
+                }
+                for (long long r = c + threadIdx.x * (long long)gridDim.x; r < nchunks; r += 256ll * gridDim.x)
+                    counts[r] = 0;
+                return;
+            }
+            gate_load_staged(stage[k & 1], g, o, rc, block0, it);
+        } else {
+            gate_load_plain(g, o, rc, block0, it);
         }
+        unsigned long long mask[kGateItems];
+        unsigned bal[kGateItems];
+        gate_masks<kOneCam>(g, o, *ctp, rc, sh, block0, it, mask);
+        const unsigned total = gate_ranks(mask, bal, sh);
+        if (threadIdx.x == 0) counts[c] = total;
+        // the chunk's candidates, in order, at the start of its own range
+#pragma unroll
+        for (int q = 0; q < kGateItems; q++) {
+            if (mask[q]) {
+                const long long pos = block0 + sh.cnt[q][warp] + __popc(bal[q] & lt);
+                o.gate_g[pos] = (uint32_t)(block0 + q * 256 + threadIdx.x);
+                o.gate_mask[pos] = mask[q];
+            }
+        }
+        __syncthreads(); // the staged chunk and the ranks are free for the next chunk
     }
 }
 
@@ -743,10 +841,12 @@ __global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, 
     } // chunks
 }
 
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
 cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t *cull)
 {
     const long long n = ws->g.n;
-    const unsigned gblocks = (unsigned)((n + 256 * kGateItems - 1) / (256 * kGateItems));
+    const unsigned gblocks = (unsigned)((n + kGateChunk - 1) / kGateChunk); // chunks
     const unsigned pblocks = (unsigned)((n + 255) / 256);
     cudaError_t e;
     // counters, then the look-back state of each stage (ticket in word 0)
@@ -766,7 +866,24 @@ cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t 
     if ((e = cudaMemsetAsync(ws->rec_first, 0xff, (size_t)n * sizeof(uint32_t), st)) != cudaSuccess) return e;
     // gate: per-block counts (in lb_status) and candidates (block-strided), the
     // scan of the counts, the gather into one ordered list
-    launch_pdl(gate_count_kernel, gblocks, 256, 0, st, gp, o, ws->d_cams, ws->rc, ws->lb_status);
+    kt_begin(ws, GS_KT_GATE, st);
+    // the camera count of the upload (a captured graph replays uploads of the
+    // same count); bulk copies where every streamed array is 16-byte aligned
+    const bool one = ws->cams.n == 1;
+    const bool bulk = n >= kGateChunk && aligned16(gp.mean) && (!gp.lod || aligned16(gp.lod)) &&
+                      (!o.drift || aligned16(o.drift));
+    const unsigned per_sm = one ? 4u : 3u;
+    const unsigned ggrid = bulk ? std::min<unsigned>(gblocks, per_sm * (unsigned)ws->sm_count) : gblocks;
+    const unsigned long long spins = kSpinLimit;
+    if (one && bulk)
+        launch_pdl(gate_count_kernel<true, true>, ggrid, 256, 0, st, gp, o, ws->d_cams, ws->rc, ws->lb_status, spins);
+    else if (one)
+        launch_pdl(gate_count_kernel<true, false>, ggrid, 256, 0, st, gp, o, ws->d_cams, ws->rc, ws->lb_status, spins);
+    else if (bulk)
+        launch_pdl(gate_count_kernel<false, true>, ggrid, 256, 0, st, gp, o, ws->d_cams, ws->rc, ws->lb_status, spins);
+    else
+        launch_pdl(gate_count_kernel<false, false>, ggrid, 256, 0, st, gp, o, ws->d_cams, ws->rc, ws->lb_status, spins);
+    kt_end(ws, GS_KT_GATE, st);
     note_launch();
     launch_pdl(gate_scan_kernel, 1, 1024, 0, st, ws->lb_status, (long long)gblocks, ws->ctr);
     note_launch();
@@ -778,46 +895,110 @@ cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t 
     if (ws->lazy.enabled && (e = launch_lazy_catchup(ws, st, ws->g)) != cudaSuccess) return e;
     // projection: two persistent 256-thread blocks per SM
     const unsigned pgrid = std::min<unsigned>(pblocks, 2u * (unsigned)ws->sm_count);
+    kt_begin(ws, GS_KT_PROJECT, st);
     launch_pdl(project_kernel, pgrid, 256, 0, st, gp, o, ws->d_cams, ws->rc);
+    kt_end(ws, GS_KT_PROJECT, st);
     note_launch();
     return cudaGetLastError();
 }
 
 // ---- backward ---------------------------------------------------------------
 
-// Sum of the per-(record, tile) gradient slots of each record.  One warp per
-// record (records in depth order, whose slots are contiguous): lanes read the
-// slots strided by 32, then a fixed shuffle tree adds the lanes, so the sum is
-// the same on every run and no record's size serialises a thread.  Records
-// marked culled are skipped: the projection adjoint never reads them.
+// Sum of the per-(record, tile) gradient slots of each record.  A warp takes
+// kReduceRecs consecutive records of the depth order (whose slots are
+// contiguous); each of its first lanes loads one record's indices.  Records of
+// at most kReduceBig tiles are added up by groups of kReduceLanes lanes, 32 /
+// kReduceLanes records at a time (a group's lanes read the record's slots
+// strided by kReduceLanes, then a fixed shuffle tree adds the lanes), so the
+// loads of a round are in flight together; larger records then take the whole
+// warp each (lanes strided by 32, a fixed tree over 32 lanes).  Which way a
+// record is summed depends only on its tile count, so the sum is the same on
+// every run.  Records marked culled are skipped: the projection adjoint never
+// reads them.
+constexpr int kReduceLanes = 8;
+constexpr int kReduceRecs = 2 * (32 / kReduceLanes); // records per warp: two rounds of the groups
+constexpr uint32_t kReduceBig = 4 * kReduceLanes;    // tiles above which a record takes the whole warp
+static_assert(kReduceLanes < kSlotFloats && kSlotFloats <= 2 * kReduceLanes, "a slot is written by one group");
 __global__ void __launch_bounds__(256) reduce_slots_kernel(const uint32_t *drec, const uint32_t *inst_off,
                                                            const uint32_t *tt, const float4 *rd2, const float *slots,
                                                            float *rgrad, const DevCounters *ctr)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
+    constexpr int kGroups = 32 / kReduceLanes;
+    constexpr uint32_t kSkip = 0xffffffffu;
     const unsigned long long nrec = ctr->n_records, ninst = ctr->n_instances;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, sub = lane & (kReduceLanes - 1), grp = lane / kReduceLanes;
     const unsigned long long nwarps = (unsigned long long)gridDim.x * 8;
-    for (unsigned long long k = (unsigned long long)blockIdx.x * 8 + (threadIdx.x >> 5); k < nrec; k += nwarps) {
-        const uint32_t r = drec[k];
-        const unsigned long long off = inst_off[r], cnt = tt[r];
-        if (off + cnt > ninst || rd2[r].w != 0.f) continue; // capacity error already recorded; marked
-        float acc[kSlotFloats];
-#pragma unroll
-        for (int j = 0; j < kSlotFloats; j++) acc[j] = 0.f;
-        for (unsigned long long t = lane; t < cnt; t += 32) {
-            const float *s = slots + (off + t) * kSlotFloats;
-#pragma unroll
-            for (int j = 0; j < kSlotFloats; j++) acc[j] += s[j];
+    for (unsigned long long k0 = ((unsigned long long)blockIdx.x * 8 + (threadIdx.x >> 5)) * kReduceRecs; k0 < nrec;
+         k0 += nwarps * kReduceRecs) {
+        // lane l < kReduceRecs: record k0 + l
+        uint32_t r = 0, cnt = kSkip;
+        unsigned long long off = 0;
+        if (lane < kReduceRecs && k0 + lane < nrec) {
+            r = drec[k0 + lane];
+            off = inst_off[r];
+            cnt = tt[r];
+            // capacity error already recorded, or marked: nothing to sum
+            if (off + cnt > ninst || rd2[r].w != 0.f) cnt = kSkip;
         }
+        const unsigned big = __ballot_sync(0xffffffffu, cnt != kSkip && cnt > kReduceBig);
 #pragma unroll
-        for (int j = 0; j < kSlotFloats; j++)
-            for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
-        if (lane < kSlotFloats) {
-            float v = acc[0];
+        for (int round = 0; round < kReduceRecs / kGroups; round++) {
+            const int src = round * kGroups + grp; // the record of this group in this round
+            const uint32_t rr = __shfl_sync(0xffffffffu, r, src);
+            const uint32_t c = __shfl_sync(0xffffffffu, cnt, src);
+            const unsigned long long o = __shfl_sync(0xffffffffu, off, src);
+            const bool live = c <= kReduceBig;
+            float acc[kSlotFloats];
 #pragma unroll
-            for (int j = 1; j < kSlotFloats; j++) v = lane == j ? acc[j] : v;
-            rgrad[(unsigned long long)r * kSlotFloats + lane] = v;
+            for (int j = 0; j < kSlotFloats; j++) acc[j] = 0.f;
+            if (live) {
+                for (uint32_t t = sub; t < c; t += kReduceLanes) {
+                    const float *sl = slots + (o + t) * kSlotFloats;
+#pragma unroll
+                    for (int j = 0; j < kSlotFloats; j++) acc[j] += sl[j];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kSlotFloats; j++)
+#pragma unroll
+                for (int x = kReduceLanes / 2; x > 0; x >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], x);
+            if (live) {
+                // lane sub writes component sub, and component sub + kReduceLanes where there is one
+                float v = acc[0];
+#pragma unroll
+                for (int j = 1; j < kReduceLanes; j++) v = sub == j ? acc[j] : v;
+                float w = acc[kReduceLanes];
+#pragma unroll
+                for (int j = kReduceLanes + 1; j < kSlotFloats; j++) w = sub + kReduceLanes == j ? acc[j] : w;
+                float *dst = rgrad + (unsigned long long)rr * kSlotFloats;
+                dst[sub] = v;
+                if (sub + kReduceLanes < kSlotFloats) dst[sub + kReduceLanes] = w;
+            }
+        }
+        for (unsigned rest = big; rest; rest &= rest - 1) {
+            const int src = __ffs(rest) - 1;
+            const uint32_t rr = __shfl_sync(0xffffffffu, r, src);
+            const uint32_t c = __shfl_sync(0xffffffffu, cnt, src);
+            const unsigned long long o = __shfl_sync(0xffffffffu, off, src);
+            float acc[kSlotFloats];
+#pragma unroll
+            for (int j = 0; j < kSlotFloats; j++) acc[j] = 0.f;
+            for (uint32_t t = lane; t < c; t += 32) {
+                const float *sl = slots + (o + t) * kSlotFloats;
+#pragma unroll
+                for (int j = 0; j < kSlotFloats; j++) acc[j] += sl[j];
+            }
+#pragma unroll
+            for (int j = 0; j < kSlotFloats; j++)
+#pragma unroll
+                for (int x = 16; x > 0; x >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], x);
+            if (lane < kSlotFloats) {
+                float v = acc[0];
+#pragma unroll
+                for (int j = 1; j < kSlotFloats; j++) v = lane == j ? acc[j] : v;
+                rgrad[(unsigned long long)rr * kSlotFloats + lane] = v;
+            }
         }
     }
 }
@@ -825,11 +1006,13 @@ __global__ void __launch_bounds__(256) reduce_slots_kernel(const uint32_t *drec,
 cudaError_t launch_reduce_slots(gs_workspace *ws, cudaStream_t st)
 {
     const long long cap = ws->cap.max_records;
-    long long blocks = (cap + 7) / 8;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    long long blocks = (cap + 8 * kReduceRecs - 1) / (8 * kReduceRecs); // kReduceRecs records per warp
+    if (blocks > 16ll * ws->sm_count) blocks = 16ll * ws->sm_count;
     if (blocks < 1) blocks = 1;
+    kt_begin(ws, GS_KT_REDUCE_SLOTS, st);
     launch_pdl(reduce_slots_kernel, (unsigned)blocks, 256, 0, st, ws->dval[ws->depth_buf], ws->inst_off, ws->tt, ws->rd2, ws->slots,
                                                          ws->rgrad, ws->ctr);
+    kt_end(ws, GS_KT_REDUCE_SLOTS, st);
     note_launch();
     return cudaGetLastError();
 }
@@ -1110,7 +1293,9 @@ cudaError_t launch_preprocess_bwd(gs_workspace *ws, cudaStream_t st, const gs_ga
     const bool reduce = beta > 0.f && scale_reg_value && blocks <= ws->red_words;
     a.red_partial = reduce ? ws->red_partial : nullptr;
     a.ctr = ws->ctr;
+    kt_begin(ws, GS_KT_PREPROCESS_BWD, st);
     launch_pdl(preprocess_bwd_kernel, blocks, 128, 0, st, a, ws->d_cams, ws->rc);
+    kt_end(ws, GS_KT_PREPROCESS_BWD, st);
     note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -52,36 +52,18 @@ __global__ void __launch_bounds__(256) radix_hist_kernel(const uint32_t *keys, c
     }
 }
 
-// Exclusive scan of each pass's 256-bucket histogram.
-__global__ void radix_offsets_kernel(const uint32_t *hist, uint32_t *off, int passes)
-{
-    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
-    __shared__ uint32_t s[256];
-    for (int p = 0; p < passes; p++) {
-        uint32_t v = hist[p * 256 + threadIdx.x];
-        s[threadIdx.x] = v;
-        __syncthreads();
-        for (int o = 1; o < 256; o <<= 1) {
-            uint32_t y = threadIdx.x >= o ? s[threadIdx.x - o] : 0u;
-            __syncthreads();
-            s[threadIdx.x] += y;
-            __syncthreads();
-        }
-        off[p * 256 + threadIdx.x] = s[threadIdx.x] - v;
-        __syncthreads();
-    }
-}
-
 // One stable LSD pass over digit (key >> shift) & 255; each block ranks
-// 256 * ITEMS keys.
+// 256 * ITEMS keys.  The global offset of each digit is the exclusive scan of
+// the pass's histogram, which every block computes for itself (256 values).
 template <int ITEMS, bool VALS_IDENTITY, bool WRITE_KEYS>
 __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
     uint32_t *__restrict__ vals_out, const unsigned long long *count, unsigned long long cap, int shift,
-    const uint32_t *__restrict__ bucket_off, uint32_t *status /* ticket at [0], then [blocks][256] */,
+    const uint32_t *__restrict__ hist, uint32_t *status /* ticket at [0], then [blocks][256] */,
     DevCounters *ctr, unsigned long long spin_limit)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
+    const uint32_t hd = hist[threadIdx.x]; // this thread's digit: count over all keys
     constexpr int kTileKeys = kSortThreads * ITEMS;
     __shared__ uint32_t s_keys[kTileKeys];
     __shared__ uint32_t s_vals[kTileKeys];
@@ -136,15 +118,16 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
         run += c;
     }
     const uint32_t dtotal = run;
-    // block-local exclusive scan over digits
+    // block-local exclusive scan over digits, and the global start of each digit
     uint32_t tot;
     const uint32_t dexcl = block_exclusive_scan_256<uint32_t>(dtotal, s_warp, tot);
     s_blk[d] = dexcl;
+    const uint32_t boff = block_exclusive_scan_256<uint32_t>(hd, s_warp, tot);
     // publish aggregate, then per-digit look-back (one thread per digit)
     volatile uint32_t *vst = st;
     if (bid == 0) {
         vst[d] = kRxInc | dtotal;
-        s_glob[d] = bucket_off[d];
+        s_glob[d] = boff;
     } else {
         vst[(unsigned long long)bid * 256 + d] = kRxAgg | dtotal;
         // walk back 8 predecessors at a time (independent loads in flight):
@@ -176,7 +159,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
             __nanosleep(40);
         }
         vst[(unsigned long long)bid * 256 + d] = kRxInc | (excl + dtotal);
-        s_glob[d] = bucket_off[d] + excl;
+        s_glob[d] = boff + excl;
     }
     __syncthreads();
     // scatter into shared memory in block-sorted order
@@ -203,23 +186,29 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
     }
 }
 
+// The passes of one sort.  status: with `region` > 0, pass p's look-back
+// state is status + p * region, all of it zeroed by the caller; with region 0
+// every pass zeroes and uses status itself.
 template <int ITEMS>
 static cudaError_t radix_passes(cudaStream_t st, uint32_t *keys[2], uint32_t *vals[2], const unsigned long long *count,
                                 unsigned long long cap, int passes, bool vals_identity, uint32_t *status,
-                                const uint32_t *off, DevCounters *ctr, int &out_buf, unsigned long long spin_limit)
+                                size_t region, const uint32_t *hist, DevCounters *ctr, int &out_buf,
+                                unsigned long long spin_limit)
 {
     const unsigned long long blocks = (cap + kSortThreads * ITEMS - 1) / (kSortThreads * ITEMS);
     cudaError_t e;
     int src = 0;
     for (int p = 0; p < passes; p++) {
         const int dst = src ^ 1;
-        if ((e = cudaMemsetAsync(status, 0, (blocks * 256 + 1) * sizeof(uint32_t), st)) != cudaSuccess) return e;
+        uint32_t *stp = status + (size_t)p * region;
+        if (region == 0 && (e = cudaMemsetAsync(stp, 0, (blocks * 256 + 1) * sizeof(uint32_t), st)) != cudaSuccess)
+            return e;
         if (vals_identity && p == 0)
             launch_pdl(radix_pass_kernel<ITEMS, true, true>, (unsigned)blocks, kSortThreads, 0, st,
-                keys[src], vals[src], keys[dst], vals[dst], count, cap, 8 * p, off + 256 * p, status, ctr, spin_limit);
+                keys[src], vals[src], keys[dst], vals[dst], count, cap, 8 * p, hist + 256 * p, stp, ctr, spin_limit);
         else
             launch_pdl(radix_pass_kernel<ITEMS, false, true>, (unsigned)blocks, kSortThreads, 0, st,
-                keys[src], vals[src], keys[dst], vals[dst], count, cap, 8 * p, off + 256 * p, status, ctr, spin_limit);
+                keys[src], vals[src], keys[dst], vals[dst], count, cap, 8 * p, hist + 256 * p, stp, ctr, spin_limit);
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         src = dst;
@@ -233,7 +222,10 @@ static cudaError_t radix_passes(cudaStream_t st, uint32_t *keys[2], uint32_t *va
 // result lands in keys[out_buf]/vals[out_buf].  With vals_identity the input
 // values are the item indices and vals[0] is not read.  Blocks rank
 // ws->sort_items * 256 keys (the workspace's tuning: 1024, 2048 or 4096, or
-// chosen by the size of the sort).
+// chosen by the size of the sort).  One memset clears the histograms and the
+// look-back state of every pass (ws->rx_status: [4][256] histogram words,
+// then one region per pass), so the sort's kernels follow one another with
+// programmatic dependent launch.
 cudaError_t launch_radix_sort(gs_workspace *ws, cudaStream_t st, uint32_t *keys[2], uint32_t *vals[2],
                               const unsigned long long *count, unsigned long long cap, int bits, bool vals_identity,
                               bool /*unused*/, int &out_buf, unsigned long long spin_limit)
@@ -242,35 +234,39 @@ cudaError_t launch_radix_sort(gs_workspace *ws, cudaStream_t st, uint32_t *keys[
     cudaError_t e;
     out_buf = 0;
     if (cap == 0) return cudaSuccess;
-    if ((e = cudaMemsetAsync(ws->rx_hist, 0, 4 * 256 * sizeof(uint32_t), st)) != cudaSuccess) return e;
-    unsigned hblocks = (unsigned)((cap + 255) / 256);
-    if (hblocks > 1216) hblocks = 1216;
-    launch_pdl(radix_hist_kernel, hblocks, 256, 0, st, keys[0], count, cap, passes, ws->rx_hist);
-    note_launch();
-    launch_pdl(radix_offsets_kernel, 1, 256, 0, st, ws->rx_hist, ws->rx_off, passes);
-    note_launch();
     // keys per block: the workspace's tuning, or by size (0): small sorts take
     // small blocks so that enough SMs work on them
     int items = ws->sort_items;
     if (items == 0) items = cap <= (1ull << 20) ? 4 : (cap <= (16ull << 20) ? 8 : 16);
+    if (items != 4 && items != 8) items = kSortItems;
+    const unsigned long long blocks = (cap + kSortThreads * items - 1) / (kSortThreads * items);
+    const size_t region = (size_t)blocks * 256 + 1;
+    uint32_t *hist = ws->rx_status, *status = ws->rx_status + kRxHistWords;
+    if (kRxHistWords + passes * region > ws->rx_words) return cudaErrorInvalidValue; // sized for this cap
+    if ((e = cudaMemsetAsync(hist, 0, (kRxHistWords + passes * region) * sizeof(uint32_t), st)) != cudaSuccess)
+        return e;
+    unsigned hblocks = (unsigned)((cap + 255) / 256);
+    if (hblocks > 1216) hblocks = 1216;
+    launch_pdl(radix_hist_kernel, hblocks, 256, 0, st, keys[0], count, cap, passes, hist);
+    note_launch();
     if (items == 4)
-        return radix_passes<4>(st, keys, vals, count, cap, passes, vals_identity, ws->rx_status, ws->rx_off, ws->ctr,
+        return radix_passes<4>(st, keys, vals, count, cap, passes, vals_identity, status, region, hist, ws->ctr,
                                out_buf, spin_limit);
     if (items == 8)
-        return radix_passes<8>(st, keys, vals, count, cap, passes, vals_identity, ws->rx_status, ws->rx_off, ws->ctr,
+        return radix_passes<8>(st, keys, vals, count, cap, passes, vals_identity, status, region, hist, ws->ctr,
                                out_buf, spin_limit);
-    return radix_passes<kSortItems>(st, keys, vals, count, cap, passes, vals_identity, ws->rx_status, ws->rx_off,
-                                    ws->ctr, out_buf, spin_limit);
+    return radix_passes<kSortItems>(st, keys, vals, count, cap, passes, vals_identity, status, region, hist, ws->ctr,
+                                    out_buf, spin_limit);
 }
 
 // The same LSD sort with every scratch buffer passed in (no workspace) and
-// 4096-key blocks: status [ceil(cap / 4096) * 256 + 1] uint32, hist and off
-// [4 * 256] uint32, ctr receives a timeout error.  Used by the entry point
-// without allocation.
+// 4096-key blocks: status [ceil(cap / 4096) * 256 + 1] uint32 (zeroed before
+// each pass), hist [4 * 256] uint32, ctr receives a timeout error.  Used by
+// the entry point without allocation.
 cudaError_t launch_radix_sort_scratch(cudaStream_t st, uint32_t *keys[2], uint32_t *vals[2],
                                       const unsigned long long *count, unsigned long long cap, int bits,
-                                      bool vals_identity, uint32_t *status, uint32_t *hist, uint32_t *off,
-                                      DevCounters *ctr, int &out_buf)
+                                      bool vals_identity, uint32_t *status, uint32_t *hist, DevCounters *ctr,
+                                      int &out_buf)
 {
     const int passes = bits <= 0 ? 1 : (bits + 7) / 8;
     cudaError_t e;
@@ -281,9 +277,7 @@ cudaError_t launch_radix_sort_scratch(cudaStream_t st, uint32_t *keys[2], uint32
     if (hblocks > 1216) hblocks = 1216;
     launch_pdl(radix_hist_kernel, hblocks, 256, 0, st, keys[0], count, cap, passes, hist);
     note_launch();
-    launch_pdl(radix_offsets_kernel, 1, 256, 0, st, hist, off, passes);
-    note_launch();
-    return radix_passes<kSortItems>(st, keys, vals, count, cap, passes, vals_identity, status, off, ctr, out_buf,
+    return radix_passes<kSortItems>(st, keys, vals, count, cap, passes, vals_identity, status, 0, hist, ctr, out_buf,
                                     kSpinLimit);
 }
 

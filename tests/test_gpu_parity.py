@@ -8,6 +8,7 @@ their boundary: a flagged projection decision must be one of the outcomes the
 flag allows and is then taken into the oracle's projection; a flagged
 compositing decision excludes its pixel.  Both stay rare.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -128,6 +129,42 @@ def test_lod_gate_and_cull_mask_parity():
     fwd = _compare_view(run, 0, O.gaussians64(g), cam, P, cull=cull)
     st = fwd["proj"]["status"]
     assert (st == O.GATED_LOD).sum() > 1000 and (st == O.GATED_CULL).sum() > 1000
+
+
+@pytest.mark.parametrize("ncam", [1, 2])
+def test_gate_bulk_copies_equal_plain_loads(ncam):
+    """The view gate streams whole chunks of means and levels by bulk copies
+    when the arrays are 16-byte aligned and by plain loads otherwise: both give
+    the same candidates, records and image, bit for bit (a level array at an
+    odd address takes the plain loads).  9000 Gaussians: eight whole chunks of
+    1024 and a partial one."""
+    rng = np.random.default_rng(41)
+    g = synth.plain_scene(9000, seed=42)
+    g.lod[:] = rng.integers(0, 6, g.n).astype(np.uint8)
+    cams = [synth.plain_camera(160, 144, 200.0), synth.plain_camera(128, 96, 150.0)][:ncam]
+    P = gpu_params(O.Params(lod_enable=True, lod_d0=16.0, lod_Lmax=4))
+    gt = B.GaussianTensors.from_host(g)
+    buf = torch.zeros(g.n + 16, dtype=torch.uint8, device="cuda")
+    odd = buf[1:1 + g.n]
+    odd.copy_(gt.lod)
+    assert odd.data_ptr() % 16 != 0 and gt.lod.data_ptr() % 16 == 0
+    npix = sum(c.width * c.height for c in cams)
+
+    def run(gtx):
+        ws = B.Workspace(**capacity_for(g.n, cams))
+        ws.preprocess(gtx, cams, P, None)
+        ws.bin_sort()
+        rgb = torch.empty(3 * npix, device="cuda")
+        ws.render_fwd(rgb)
+        ws.sync_status()
+        return rgb.cpu().numpy(), ws.counts()
+
+    a, ca = run(gt)
+    b, cb = run(dataclasses.replace(gt, lod=odd))
+    for k in ("n_candidates", "n_records", "n_instances", "n_visible"):
+        assert ca[k] == cb[k], k
+    assert 0 < ca["n_records"] < g.n * ncam
+    assert np.array_equal(a, b)
 
 
 def test_cull_mark_equals_drop_for_training_and_off_for_importance():
