@@ -167,6 +167,17 @@ __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float *img, const f
     const int plane = blockIdx.z;
     const int ox = blockIdx.x * kLT, oy = blockIdx.y * kLT;
     const float4 *Fp = F + (long long)plane * H * W;
+    // the image and target at this thread's outputs, in flight with the staging loads
+    const int c = threadIdx.x % kLT, r0 = (threadIdx.x / kLT) * kVSeg;
+    float xo[kVSeg], yo[kVSeg];
+#pragma unroll
+    for (int o = 0; o < kVSeg; o++) {
+        const int gy = oy + r0 + o, gx = ox + c;
+        const bool in = gy < H && gx < W;
+        const long long p = (long long)plane * H * W + (long long)gy * W + gx;
+        xo[o] = in ? img[p] : 0.f;
+        yo[o] = in ? tgt[p] : 0.f;
+    }
     {
         float4 buf[kStageIters];
 #pragma unroll
@@ -208,7 +219,6 @@ __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float *img, const f
     }
     __syncthreads();
     const float npx = 3.f * (float)H * (float)W; // SSIM and L1 are means over channels and pixels
-    const int c = threadIdx.x % kLT, r0 = (threadIdx.x / kLT) * kVSeg;
     float2 b01[kVSeg];
     float b2[kVSeg];
 #pragma unroll
@@ -231,7 +241,7 @@ __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float *img, const f
         const int gy = oy + r0 + o, gx = ox + c;
         if (gy >= H || gx >= W) continue;
         const long long p = (long long)plane * H * W + (long long)gy * W + gx;
-        const float xv = img[p], yv = tgt[p];
+        const float xv = xo[o], yv = yo[o];
         const float dssim = (b01[o].x + 2.f * xv * b01[o].y + yv * b2[o]) / npx;
         const float d = xv - yv;
         const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);

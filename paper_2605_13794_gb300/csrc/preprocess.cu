@@ -410,6 +410,8 @@ struct GateShared {
     float thr[kMaxLod + 1];  // sqrt of thr2, for the drift margin
     unsigned cnt[kGateItems][8];
     unsigned total;
+    uint16_t surv[8][kGateChunk / 8]; // one camera: each warp's items past the LOD and near tests
+    unsigned hit[8][kGateItems];      // one camera: (warp, item) bits by lane of the candidates
 };
 
 // One chunk as the bulk copies leave it in shared memory.
@@ -472,19 +474,24 @@ __device__ __forceinline__ void gate_issue(GateStage &sg, unsigned long long *ba
     if (drift) bulk_copy_g2s(sg.drift, o.drift + kGateChunk * c, 4u * kGateChunk, bar);
 }
 
+// sg: the chunk's staged copy (bulk copies), or nullptr (plain loads)
 template <bool kOneCam>
 __device__ __forceinline__ void gate_masks(const GaussPtrs &g, const PreOut &o, const CamTable &ct,
                                            const RenderConsts &rc, GateShared &sh, long long block0,
-                                           const GateItems &it, unsigned long long mask[kGateItems])
+                                           const GateItems &it, const GateStage *sg,
+                                           unsigned long long mask[kGateItems])
 {
     const int ncam = ct.n, tw = ct.tile_w, th = ct.tile_h;
     const long long n = g.n;
     if (kOneCam) {
-        // one camera: the LOD, Cull and near tests of every item, then the
-        // shape (log-scales, their drift) of the items still in, then the
-        // screen test
+        // one camera: the LOD, Cull and near tests of every item; the few items
+        // still in (a twentieth of a city scene) are compacted per warp, in
+        // item order, and the warp's lanes take them together through their
+        // shape (log-scales, their drift) and the screen test
         const CamInfo &cam = sh.cams[0];
-        bool in[kGateItems];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const unsigned lt = (1u << lane) - 1u;
+        unsigned nsurv = 0;
 #pragma unroll
         for (int k = 0; k < kGateItems; k++) {
             const long long i = block0 + k * 256 + threadIdx.x;
@@ -494,29 +501,35 @@ __device__ __forceinline__ void gate_masks(const GaussPtrs &g, const PreOut &o, 
             float tz, ez;
             camera_z(m, cam, tz, ez);
             const bool near_ok = tz + ez + it.dm[k] > rc.znear; // the exact near test is the projection's
-            in[k] = i < n && lod_ok && !culled && near_ok;
+            const bool in = i < n && lod_ok && !culled && near_ok;
+            const unsigned b = __ballot_sync(0xffffffffu, in);
+            if (in) sh.surv[warp][nsurv + __popc(b & lt)] = (uint16_t)(k * 256 + threadIdx.x);
+            nsurv += __popc(b);
         }
-        float lsmax[kGateItems];
-#pragma unroll
-        for (int k = 0; k < kGateItems; k++) {
-            const long long i = block0 + k * 256 + threadIdx.x;
-            lsmax[k] = 0.f;
-            if (in[k]) {
-                const float dl = o.drift ? o.drift[n + i] : 0.f;
-                lsmax[k] = fmaxf(g.log_scale[3 * i], fmaxf(g.log_scale[3 * i + 1], g.log_scale[3 * i + 2])) + dl;
+        if (lane < kGateItems) sh.hit[warp][lane] = 0u;
+        __syncwarp();
+        for (unsigned q = lane; q < nsurv; q += 32) {
+            const int j = sh.surv[warp][q]; // chunk-local item: k * 256 + warp * 32 + its lane
+            const long long i = block0 + j;
+            float m[3], dm;
+            if (sg) {
+                m[0] = sg->mean[3 * j]; m[1] = sg->mean[3 * j + 1]; m[2] = sg->mean[3 * j + 2];
+                dm = o.drift ? sg->drift[j] : 0.f;
+            } else {
+                m[0] = g.mean[3 * i]; m[1] = g.mean[3 * i + 1]; m[2] = g.mean[3 * i + 2];
+                dm = o.drift ? o.drift[i] : 0.f;
             }
-        }
-#pragma unroll
-        for (int k = 0; k < kGateItems; k++) {
-            mask[k] = 0;
-            if (!in[k]) continue;
-            const float m[3] = {it.mx[k], it.my[k], it.mz[k]};
+            const float dl = o.drift ? o.drift[n + i] : 0.f;
+            const float lsmax = fmaxf(g.log_scale[3 * i], fmaxf(g.log_scale[3 * i + 1], g.log_scale[3 * i + 2])) + dl;
             float t[3], te[3];
             camera_point(m, cam, t, te);
-            te[0] += it.dm[k]; te[1] += it.dm[k]; te[2] += it.dm[k];
-            const float smax = 1.0001f * __expf(lsmax[k]);
-            mask[k] = maybe_on_screen(t, te, smax, cam, tw, th, rc) ? 1ull : 0ull;
+            te[0] += dm; te[1] += dm; te[2] += dm;
+            const float smax = 1.0001f * __expf(lsmax);
+            if (maybe_on_screen(t, te, smax, cam, tw, th, rc)) atomicOr(&sh.hit[warp][j >> 8], 1u << (j & 31));
         }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < kGateItems; k++) mask[k] = (sh.hit[warp][k] >> lane) & 1u;
     } else {
 #pragma unroll
         for (int k = 0; k < kGateItems; k++) {
@@ -653,7 +666,7 @@ __global__ void __launch_bounds__(256, kOneCam ? 4 : 3) gate_count_kernel(GaussP
         }
         unsigned long long mask[kGateItems];
         unsigned bal[kGateItems];
-        gate_masks<kOneCam>(g, o, *ctp, rc, sh, block0, it, mask);
+        gate_masks<kOneCam>(g, o, *ctp, rc, sh, block0, it, (kBulk && c < nwhole) ? &stage[k & 1] : nullptr, mask);
         const unsigned total = gate_ranks(mask, bal, sh);
         if (threadIdx.x == 0) counts[c] = total;
         // the chunk's candidates, in order, at the start of its own range
@@ -1041,7 +1054,12 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, const Ca
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     __shared__ CamInfo s_cams[GS_MAX_CAMERAS];
     __shared__ float s_red[4];
+    // each thread's gradient row: the SH part accumulates here over the records,
+    // and with a.cgrad the warp copies its 32 consecutive rows out together
+    __shared__ float s_row[4][32 * kGradRow];
     stage_cameras(*ctp, s_cams);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *myrow = &s_row[warp][lane * kGradRow];
     // one thread per Gaussian that has records: the thread of its first record
     const unsigned long long rh = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned long long nrec = a.ctr->n_records;
@@ -1053,7 +1071,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, const Ca
         while (r1 < nrec && a.rec_g[r1] == (uint32_t)i) r1++;
         float gm[3] = {0, 0, 0}, gls[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gop = 0.f;
         bool vis = false; // an unmarked record (the visible set of Eq. 5)
-        float gsh[48];
+        float *gsh = myrow + 11; // the 48 SH gradients, summed over the records
 #pragma unroll
         for (int k = 0; k < 48; k++) gsh[k] = 0.f;
         const float m[3] = {a.g.mean[3 * i], a.g.mean[3 * i + 1], a.g.mean[3 * i + 2]};
@@ -1223,12 +1241,11 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, const Ca
             }
         }
         if (a.cgrad) {
-            // compact row of 59 gradients (mean, log-scale, quat, opacity, SH) at the first record
-            float *row = a.cgrad + rh * kGradRow;
-            for (int k = 0; k < 3; k++) { row[k] = gm[k]; row[3 + k] = gls[k]; }
-            for (int k = 0; k < 4; k++) row[6 + k] = gq[k];
-            row[10] = gop;
-            for (int k = 0; k < 48; k++) row[11 + k] = gsh[k];
+            // compact row of 59 gradients (mean, log-scale, quat, opacity, SH) at the first
+            // record: the SH part is in place, the rest goes beside it
+            for (int k = 0; k < 3; k++) { myrow[k] = gm[k]; myrow[3 + k] = gls[k]; }
+            for (int k = 0; k < 4; k++) myrow[6 + k] = gq[k];
+            myrow[10] = gop;
         } else {
             // the grads of Gaussians without records were zeroed (overwrite mode) or are left as they are
             for (int k = 0; k < 3; k++) {
@@ -1238,6 +1255,18 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs a, const Ca
             for (int k = 0; k < 4; k++) a.gquat[4 * i + k] += gq[k];
             a.gop[i] += gop;
             for (int k = 0; k < 48; k++) a.gsh[48 * i + k] += gsh[k];
+        }
+    }
+    if (a.cgrad) {
+        // rows of records that are not a Gaussian's first are never read: zeros
+        if (!head)
+            for (int k = 0; k < kGradRow; k++) myrow[k] = 0.f;
+        __syncwarp();
+        const unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + warp * 32;
+        if (base < nrec) {
+            const unsigned rows = (unsigned)min(32ull, nrec - base);
+            float *dst = a.cgrad + base * kGradRow;
+            for (unsigned e = lane; e < rows * kGradRow; e += 32) dst[e] = s_row[warp][e];
         }
     }
     if (a.red_partial) {
