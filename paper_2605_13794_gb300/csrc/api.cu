@@ -99,7 +99,7 @@ Offsets plan(const gs_capacity &c)
     o.selk1 = L.take<uint32_t>(R);
     o.selv0 = L.take<uint32_t>(R);
     o.selv1 = L.take<uint32_t>(R);
-    o.loss_maps = L.take<float>(fwd_only ? 0 : P * 3 * 4); // per pixel and channel (F0, F1, F2, 0)
+    o.loss_maps = L.take<float>(fwd_only ? 0 : P * 3 * 3); // per pixel and channel: F0, F1, F2 (planar)
     o.loss_partial_words = fwd_only ? 0 : 2 * 3 * (P / 1024 + 65536);
     o.loss_partial = L.take<float>(o.loss_partial_words);
     const size_t nb = (N > R ? N : R) / 256 + 2;

@@ -36,14 +36,17 @@ __device__ __forceinline__ float ld_zero(const float *p, int H, int W, int y, in
 constexpr int kHSeg = 8;                 // horizontal outputs per thread (42 rows x 4 segments)
 constexpr int kVSeg = 4;                 // vertical outputs per thread (32 columns x 8 segments)
 constexpr int kLTP = kLTH + 1;           // padded row of the staged tile
-constexpr int kStageIters = (kLTH * kLTH + 255) / 256; // staged values per thread
+// staging: warp w loads rows w, w + 8, ... of the tile with its halo, lane l
+// columns l and l + 32
+constexpr int kStageRows = (kLTH + 7) / 8;
+static_assert(kLTH <= 64, "two columns per lane cover a staged row");
 
 __device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
 
-// grid: (tiles_x, tiles_y, batch * 3).  F: per pixel of each plane the three
-// coefficient maps of the SSIM gradient, (F0, F1, F2, 0).
+// grid: (tiles_x, tiles_y, batch * 3).  F: the three coefficient maps of the
+// SSIM gradient of each plane, planar: F[(plane * 3 + m) * H * W + pixel].
 __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *img, const float *tgt, int H, int W, Win win,
-                                                       float C1, float C2, float4 *F, unsigned long long *acc)
+                                                       float C1, float C2, float *F, unsigned long long *acc)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     __shared__ float2 sxy[kLTH][kLTP];
@@ -56,20 +59,24 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *img, const f
     const int ox = blockIdx.x * kLT, oy = blockIdx.y * kLT;
     {
         // every load of the thread issued before the first store
-        float2 buf[kStageIters];
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        float2 buf[kStageRows][2];
 #pragma unroll
-        for (int u = 0; u < kStageIters; u++) {
-            const int k = threadIdx.x + 256 * u;
-            const int r = k / kLTH, c = k % kLTH;
-            buf[u] = k < kLTH * kLTH ? make_float2(ld_zero(x, H, W, oy + r - kHalo, ox + c - kHalo),
-                                                   ld_zero(y, H, W, oy + r - kHalo, ox + c - kHalo))
-                                     : make_float2(0.f, 0.f);
-        }
+        for (int q = 0; q < kStageRows; q++)
 #pragma unroll
-        for (int u = 0; u < kStageIters; u++) {
-            const int k = threadIdx.x + 256 * u;
-            if (k < kLTH * kLTH) sxy[k / kLTH][k % kLTH] = buf[u];
-        }
+            for (int h = 0; h < 2; h++) {
+                const int r = warp + 8 * q, c = lane + 32 * h;
+                const int gy = oy + r - kHalo, gx = ox + c - kHalo;
+                buf[q][h] = r < kLTH && c < kLTH ? make_float2(ld_zero(x, H, W, gy, gx), ld_zero(y, H, W, gy, gx))
+                                                 : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+        for (int q = 0; q < kStageRows; q++)
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int r = warp + 8 * q, c = lane + 32 * h;
+                if (r < kLTH && c < kLTH) sxy[r][c] = buf[q][h];
+            }
     }
     __syncthreads();
     // horizontal blur of (x, y), (x^2, y^2) and xy: 42 rows x (32 / kHSeg) segments,
@@ -132,8 +139,11 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *img, const f
             const float dmx = 2.f * my * A2 * iB - S * 2.f * mx / B1;
             const float dsxx = -S / B2;
             const float dsxy = 2.f * A1 * iB;
-            const long long p = (long long)plane * H * W + (long long)gy * W + gx;
-            F[p] = make_float4(dmx - 2.f * mx * dsxx - my * dsxy, dsxx, dsxy, 0.f);
+            const long long hw = (long long)H * W, p = (long long)gy * W + gx;
+            float *Fp = F + 3 * (long long)plane * hw + p;
+            Fp[0] = dmx - 2.f * mx * dsxx - my * dsxy;
+            Fp[hw] = dsxx;
+            Fp[2 * hw] = dsxy;
             ssum += S;
             const float2 px = sxy[r + kHalo][c + kHalo];
             l1sum += fabsf(px.x - px.y);
@@ -156,8 +166,8 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *img, const f
     }
 }
 
-__global__ void __launch_bounds__(256) ssim_bwd_kernel(const float *img, const float *tgt, int H, int W, Win win,
-                                                       const float4 *F, float lambda, int batch, float *dL)
+__global__ void __launch_bounds__(256, 4) ssim_bwd_kernel(const float *img, const float *tgt, int H, int W, Win win,
+                                                       const float *F, float lambda, int batch, float *dL)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     __shared__ float2 sf01[kLTH][kLTP];
@@ -166,7 +176,8 @@ __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float *img, const f
     __shared__ float hb2[kLTH][kLT + 1];
     const int plane = blockIdx.z;
     const int ox = blockIdx.x * kLT, oy = blockIdx.y * kLT;
-    const float4 *Fp = F + (long long)plane * H * W;
+    const long long hw = (long long)H * W;
+    const float *Fp = F + 3 * (long long)plane * hw;
     // the image and target at this thread's outputs, in flight with the staging loads
     const int c = threadIdx.x % kLT, r0 = (threadIdx.x / kLT) * kVSeg;
     float xo[kVSeg], yo[kVSeg];
@@ -179,23 +190,30 @@ __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float *img, const f
         yo[o] = in ? tgt[p] : 0.f;
     }
     {
-        float4 buf[kStageIters];
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        float2 b01[kStageRows][2];
+        float b2[kStageRows][2];
 #pragma unroll
-        for (int u = 0; u < kStageIters; u++) {
-            const int k = threadIdx.x + 256 * u;
-            const int r = k / kLTH, c = k % kLTH;
-            const int gy = oy + r - kHalo, gx = ox + c - kHalo;
-            buf[u] = (k < kLTH * kLTH && gy >= 0 && gy < H && gx >= 0 && gx < W) ? Fp[(long long)gy * W + gx]
-                                                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
+        for (int q = 0; q < kStageRows; q++)
 #pragma unroll
-        for (int u = 0; u < kStageIters; u++) {
-            const int k = threadIdx.x + 256 * u;
-            if (k < kLTH * kLTH) {
-                sf01[k / kLTH][k % kLTH] = make_float2(buf[u].x, buf[u].y);
-                sf2[k / kLTH][k % kLTH] = buf[u].z;
+            for (int h = 0; h < 2; h++) {
+                const int r = warp + 8 * q, cc = lane + 32 * h;
+                const int gy = oy + r - kHalo, gx = ox + cc - kHalo;
+                const bool in = r < kLTH && cc < kLTH && gy >= 0 && gy < H && gx >= 0 && gx < W;
+                const long long p = (long long)gy * W + gx;
+                b01[q][h] = in ? make_float2(Fp[p], Fp[hw + p]) : make_float2(0.f, 0.f);
+                b2[q][h] = in ? Fp[2 * hw + p] : 0.f;
             }
-        }
+#pragma unroll
+        for (int q = 0; q < kStageRows; q++)
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int r = warp + 8 * q, cc = lane + 32 * h;
+                if (r < kLTH && cc < kLTH) {
+                    sf01[r][cc] = b01[q][h];
+                    sf2[r][cc] = b2[q][h];
+                }
+            }
     }
     __syncthreads();
     for (int wi = threadIdx.x; wi < kLTH * (kLT / kHSeg); wi += 256) {
@@ -272,7 +290,7 @@ cudaError_t launch_loss(gs_workspace *ws, cudaStream_t st, const float *img, con
     for (int k = 0; k < 11; k++) { g[k] = exp(-((k - 5) * (k - 5)) / (2.0 * 1.5 * 1.5)); sum += g[k]; }
     for (int k = 0; k < 11; k++) win.w[k] = (float)(g[k] / sum);
     const dim3 grid((W + kLT - 1) / kLT, (H + kLT - 1) / kLT, B * 3);
-    float4 *maps = reinterpret_cast<float4 *>(ws->loss_maps);
+    float *maps = ws->loss_maps; // three planes per image plane
     unsigned long long *acc = reinterpret_cast<unsigned long long *>(ws->loss_partial); // [B][2]
     cudaError_t e = cudaMemsetAsync(acc, 0, 2 * (size_t)B * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
