@@ -8,14 +8,16 @@ and the importance cull column enabled.  One step runs every stage of the hot
 path through the C ABI on resident device data:
 
   preprocess (gate + projection + SH; Gaussians culled in the view are kept
-  and marked) -> bin_sort -> render_fwd (marked records composite nowhere)
-  -> L1 + 0.2 D-SSIM loss against a target -> render backward (+ scale
-     regulariser) into compact per-Gaussian gradient rows -> Adam over all 59
-     parameters of all Gaussians (zero-gradient steps deferred and replayed
-     exactly); beside them, on a second stream forked after bin_sort, the
-     importance sweep on the same binning, which scores every record as
-     without the Cull column it recomputes (w, a, s, c^rad, c^vis and the next
-     Cull column); the step ends when both streams have.
+  and marked) -> bin_sort -> one walk of the tile lists that composites the
+  image (marked records composite nowhere) and the importance sweep's raster
+  (every record, as without the Cull column) -> L1 + 0.2 D-SSIM loss against
+  a target -> render backward (+ scale regulariser) into compact per-Gaussian
+  gradient rows -> Adam over all 59 parameters of all Gaussians
+  (zero-gradient steps deferred and replayed exactly); beside them, on a
+  second stream forked after the walk, the importance sweep's selection (w,
+  a, s, c^rad, c^vis and the next Cull column); the step ends when both
+  streams have.  (--overlap picks other arrangements: the whole sweep on the
+  second stream after bin_sort, or all on one stream.)
 
 The timed steps are replays of one CUDA graph of the whole step (captured
 after eager warm-up steps; cameras from the workspace's device table, the Adam
@@ -82,9 +84,10 @@ def parse():
                     help="render tile shape of the city5M step")
     ap.add_argument("--dense-adam", action="store_true",
                     help="update every Gaussian every step instead of deferring zero-gradient steps (same results)")
-    ap.add_argument("--overlap", default="step", choices=["fwd", "step", "late", "off"],
+    ap.add_argument("--overlap", default="fused", choices=["fwd", "step", "late", "fused", "off"],
                     help="city5M: the importance sweep on a second stream beside the forward and loss (fwd), "
-                         "beside the whole training pass (step), or on the one stream (off)")
+                         "beside the whole training pass (step), its raster fused into the forward's walk and "
+                         "its selection on a second stream (fused), or on the one stream (off)")
     return ap.parse_args()
 
 
@@ -288,10 +291,18 @@ class Step:
         rec(1)
         ws.bin_sort()
         rec(2)
-        if side is not None and self.overlap != "late":
-            side.wait_stream(main)
-            self._importance(stream=side)
-        ws.render_fwd(self.rgb, self.T)
+        if self.overlap == "fused":
+            # one walk of the lists: the image and the importance raster; the
+            # selection follows on the side stream
+            ws.render_fwd_importance(self.rgb, self.T)
+            if side is not None:
+                side.wait_stream(main)
+                self._importance(stream=side)
+        else:
+            if side is not None and self.overlap != "late":
+                side.wait_stream(main)
+                self._importance(stream=side)
+            ws.render_fwd(self.rgb, self.T)
         rec(3)
         if side is not None and self.overlap == "late":
             side.wait_stream(main)
@@ -309,7 +320,7 @@ class Step:
         rec(6)
         if side is None:
             self._importance()
-        elif self.overlap in ("step", "late"):
+        elif self.overlap in ("step", "late", "fused"):
             main.wait_stream(side)
         rec(7)
 
@@ -835,8 +846,11 @@ def main():
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(diag)]
     # and the per-launch device time of the forward and the importance raster in
     # these one-stream steps (event pairs around each launch)
+    # (the breakdown runs the forward and the importance raster as separate
+    # launches; with --overlap fused, a few more steps time the fused walk)
     timed = [("render_fwd_kernel", B.GS_KT_RENDER_FWD), ("importance_raster_kernel", B.GS_KT_IMPORTANCE)] + \
         [(name, getattr(B, kid)) for name, (kid, _) in HBM_KERNELS.items()] + [("project_kernel", B.GS_KT_PROJECT)]
+    mode, step.overlap = step.overlap, "step"
     step.ws.kernel_timing(True, kernels=[kid for _, kid in timed])
     for k in range(diag):
         step.run(evs[k])
@@ -846,6 +860,15 @@ def main():
         if n_l:
             kernel_ms[name] = max_over_ranks(t / n_l, world)
     step.ws.kernel_timing(False)
+    step.overlap = mode
+    if mode == "fused":
+        step.ws.kernel_timing(True, kernels=[B.GS_KT_RENDER_FWD])
+        for k in range(min(diag, 3)):
+            step.run([torch.cuda.Event(enable_timing=True) for _ in range(8)])
+        torch.cuda.synchronize()
+        t, n_l = step.ws.kernel_time(B.GS_KT_RENDER_FWD)
+        kernel_ms["render_fwd_importance_kernel"] = max_over_ranks(t / max(n_l, 1), world)
+        step.ws.kernel_timing(False)
     stage_ms = {name: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(diag))
                 for i, name in enumerate(step.stage_names)}
     stage_ms["adam_flush_per_step"] = fl0.elapsed_time(fl1) / args.steps
@@ -883,11 +906,20 @@ def main():
     # counted as the adjoint's (the entries up to each pixel's last composited one, a
     # lower bound of the pairs they evaluate)
     frag = counts["fragments"]
-    roof_fwd = alu_roofline("render_fwd_kernel", BWD_FLOP_EVAL * frag + FWD_FLOP_COMPOSITE * counts["composited"],
-                            frag, kernel_ms["render_fwd_kernel"], alu, peaks, sm_mhz)
-    roof_imp = alu_roofline("importance_raster_kernel", BWD_FLOP_EVAL * frag + IMP_FLOP_COMPOSITE * imp_composited,
-                            frag, kernel_ms["importance_raster_kernel"], alu, peaks, sm_mhz)
-    roof_imp["composited_per_launch"] = imp_composited
+    roof_comp = {
+        "render_fwd_kernel": alu_roofline("render_fwd_kernel",
+                                          BWD_FLOP_EVAL * frag + FWD_FLOP_COMPOSITE * counts["composited"],
+                                          frag, kernel_ms["render_fwd_kernel"], alu, peaks, sm_mhz),
+        "importance_raster_kernel": alu_roofline("importance_raster_kernel",
+                                                 BWD_FLOP_EVAL * frag + IMP_FLOP_COMPOSITE * imp_composited,
+                                                 frag, kernel_ms["importance_raster_kernel"], alu, peaks, sm_mhz)}
+    if "render_fwd_importance_kernel" in kernel_ms:
+        # one walk: the pairs' alpha once, then the forward's and the importance's sums
+        roof_comp["render_fwd_importance_kernel"] = alu_roofline(
+            "render_fwd_importance_kernel",
+            BWD_FLOP_EVAL * frag + FWD_FLOP_COMPOSITE * counts["composited"] + IMP_FLOP_COMPOSITE * imp_composited,
+            frag, kernel_ms["render_fwd_importance_kernel"], alu, peaks, sm_mhz)
+    roof_comp["importance_raster_kernel"]["composited_per_launch"] = imp_composited
     tw, th = (int(x) for x in args.tile.split("x"))
     tiles = ((cam.width + tw - 1) // tw) * ((cam.height + th - 1) // th)
     roof_hbm = hbm_rooflines(kernel_ms, dict(counts, n=g.n, pixels=P, depth_passes=4,
@@ -905,6 +937,8 @@ def main():
                        "importance_stream": {"fwd": "second stream beside forward and loss",
                                              "step": "second stream beside the training pass",
                                              "late": "second stream beside loss and adjoint",
+                                             "fused": "raster in the forward's walk, selection on a second stream "
+                                                      "beside the training pass",
                                              "off": "one stream"}[args.overlap],
                        "parallelism": f"replicas{world}"},
             "mgaussian_per_s": gauss,
@@ -914,7 +948,7 @@ def main():
             "counts": {k: counts[k] for k in ("n_records", "n_instances", "n_visible")},
             "kernel_ms": {k: round(v, 4) for k, v in kernel_ms.items()},
             "roofline": roof,
-            "roofline_other": {"render_fwd_kernel": roof_fwd, "importance_raster_kernel": roof_imp, **roof_hbm},
+            "roofline_other": {**roof_comp, **roof_hbm},
             "alu_peaks": {k: (round(v / 1e12, 3) if k != "sms" else v) for k, v in alu.items()},
             "alu_peaks_unit": "TFLOP/s (FMA) and T results/s (ex2)",
             "render_latency": latency,
