@@ -17,33 +17,78 @@ namespace gs {
 
 cudaError_t launch_importance_raster(gs_workspace *ws, cudaStream_t st);
 
-// w and a of each record: one warp per record, lanes strided over its slots
-// (contiguous in depth order), fixed shuffle tree.
+// w and a of each record.  A warp takes 8 consecutive records of the depth
+// order (whose slots are contiguous); records of at most 32 tiles are summed by
+// groups of 8 lanes, 4 records at a time (lanes strided over the record's
+// slots, then a fixed shuffle tree over the group), larger ones by the whole
+// warp each (lanes strided by 32, a fixed tree over 32 lanes).  Which way a
+// record is summed depends only on its tile count: the same sums on every run.
+constexpr int kImpLanes = 8, kImpRecs = 8;
+constexpr uint32_t kImpBig = 4 * kImpLanes;
 __global__ void __launch_bounds__(256) imp_reduce_kernel(const uint32_t *drec, const uint32_t *inst_off,
                                                          const uint32_t *tt, const float2 *slots, float *imp_w,
                                                          uint32_t *imp_a, const DevCounters *ctr)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
+    constexpr int kGroups = 32 / kImpLanes;
+    constexpr uint32_t kSkip = 0xffffffffu;
     const unsigned long long nrec = ctr->n_records, ninst = ctr->n_instances;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, sub = lane & (kImpLanes - 1), grp = lane / kImpLanes;
     const unsigned long long nwarps = (unsigned long long)gridDim.x * 8;
-    for (unsigned long long k = (unsigned long long)blockIdx.x * 8 + (threadIdx.x >> 5); k < nrec; k += nwarps) {
-        const uint32_t r = drec[k];
-        const unsigned long long off = inst_off[r], cnt = tt[r];
-        float w = 0.f;
-        uint32_t a = 0;
-        if (off + cnt <= ninst) {
-            for (unsigned long long t = lane; t < cnt; t += 32) {
-                const float2 s = slots[off + t];
-                w += s.x;
-                a += __float_as_uint(s.y);
+    for (unsigned long long k0 = ((unsigned long long)blockIdx.x * 8 + (threadIdx.x >> 5)) * kImpRecs; k0 < nrec;
+         k0 += nwarps * kImpRecs) {
+        uint32_t r = 0, cnt = kSkip;
+        unsigned long long off = 0;
+        if (lane < kImpRecs && k0 + lane < nrec) {
+            r = drec[k0 + lane];
+            off = inst_off[r];
+            cnt = tt[r];
+            if (off + cnt > ninst) cnt = 0; // capacity error already recorded: zero sums
+        }
+        const unsigned big = __ballot_sync(0xffffffffu, cnt != kSkip && cnt > kImpBig);
+#pragma unroll
+        for (int round = 0; round < kImpRecs / kGroups; round++) {
+            const int src = round * kGroups + grp;
+            const uint32_t rr = __shfl_sync(0xffffffffu, r, src);
+            const uint32_t c = __shfl_sync(0xffffffffu, cnt, src);
+            const unsigned long long o = __shfl_sync(0xffffffffu, off, src);
+            const bool live = c <= kImpBig;
+            float w = 0.f;
+            uint32_t aa = 0;
+            if (live)
+                for (uint32_t t = sub; t < c; t += kImpLanes) {
+                    const float2 sl = slots[o + t];
+                    w += sl.x;
+                    aa += __float_as_uint(sl.y);
+                }
+#pragma unroll
+            for (int x = kImpLanes / 2; x > 0; x >>= 1) {
+                w += __shfl_xor_sync(0xffffffffu, w, x);
+                aa += __shfl_xor_sync(0xffffffffu, aa, x);
+            }
+            if (live && sub == 0) {
+                imp_w[rr] = w;
+                imp_a[rr] = aa;
             }
         }
-        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-        a = __reduce_add_sync(0xffffffffu, a);
-        if (lane == 0) {
-            imp_w[r] = w;
-            imp_a[r] = a;
+        for (unsigned rest = big; rest; rest &= rest - 1) {
+            const int src = __ffs(rest) - 1;
+            const uint32_t rr = __shfl_sync(0xffffffffu, r, src);
+            const uint32_t c = __shfl_sync(0xffffffffu, cnt, src);
+            const unsigned long long o = __shfl_sync(0xffffffffu, off, src);
+            float w = 0.f;
+            uint32_t aa = 0;
+            for (uint32_t t = lane; t < c; t += 32) {
+                const float2 sl = slots[o + t];
+                w += sl.x;
+                aa += __float_as_uint(sl.y);
+            }
+            for (int x = 16; x > 0; x >>= 1) w += __shfl_xor_sync(0xffffffffu, w, x);
+            aa = __reduce_add_sync(0xffffffffu, aa);
+            if (lane == 0) {
+                imp_w[rr] = w;
+                imp_a[rr] = aa;
+            }
         }
     }
 }
@@ -309,8 +354,8 @@ __global__ void cull_init_kernel(uint32_t *cull, long long words, long long n, i
 cudaError_t launch_importance_reduce(gs_workspace *ws, cudaStream_t st)
 {
     const unsigned long long rcap = (unsigned long long)ws->cap.max_records;
-    const unsigned blocks = (unsigned)std::max<unsigned long long>(1, std::min<unsigned long long>((rcap + 7) / 8,
-                                                                                                    16ull * ws->sm_count));
+    const unsigned blocks = (unsigned)std::max<unsigned long long>(
+        1, std::min<unsigned long long>((rcap + 8 * kImpRecs - 1) / (8 * kImpRecs), 16ull * ws->sm_count));
     launch_pdl(imp_reduce_kernel, blocks, 256, 0, st, ws->dval[ws->depth_buf], ws->inst_off, ws->tt,
                                               ws->imp_slots, ws->imp_w, ws->imp_a,
                                               ws->ctr);
