@@ -102,7 +102,9 @@ Offsets plan(const gs_capacity &c)
     o.loss_maps = L.take<float>(fwd_only ? 0 : P * 3 * 3); // per pixel and channel: F0, F1, F2 (planar)
     o.loss_partial_words = fwd_only ? 0 : 2 * 3 * (P / 1024 + 65536);
     o.loss_partial = L.take<float>(o.loss_partial_words);
-    const size_t nb = (N > R ? N : R) / 256 + 2;
+    // look-back words: one per chunk of the smallest chunked pass (the
+    // projection's 64 candidates) plus the ticket
+    const size_t nb = (N > R ? N : R) / 64 + 2;
     o.lb_words = nb + 1;
     o.lb_status = L.take<unsigned long long>(o.lb_words);
     const size_t items = (R > I ? R : I);

@@ -80,6 +80,7 @@ struct DevCounters {
     unsigned long long records_needed;
     unsigned long long instances_needed;
     unsigned long long n_candidates;   // Gaussians passing the gate stage of preprocess
+    unsigned long long n_catchup;      // candidates behind the current Adam step (deferred steps to replay)
     int error;
     int error_site;
     unsigned long long sel_count[GS_MAX_CAMERAS]; // w > 0 entries per camera (importance)
@@ -232,9 +233,9 @@ __device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long l
     return excl;
 }
 
-// Block-wide exclusive scan of one value per thread (blockDim.x == 256).
-template <typename T>
-__device__ __forceinline__ T block_exclusive_scan_256(T v, T *smem_warp /*[8]*/, T &total)
+// Block-wide exclusive scan of one value per thread, NW warps per block.
+template <int NW, typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T *smem_warp /*[NW]*/, T &total)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T x = v;
@@ -245,7 +246,8 @@ __device__ __forceinline__ T block_exclusive_scan_256(T v, T *smem_warp /*[8]*/,
     if (lane == 31) smem_warp[warp] = x;
     __syncthreads();
     T wpre = 0, tot = 0;
-    for (int w = 0; w < 8; w++) {
+#pragma unroll
+    for (int w = 0; w < NW; w++) {
         T s = smem_warp[w];
         if (w < warp) wpre += s;
         tot += s;
@@ -253,6 +255,13 @@ __device__ __forceinline__ T block_exclusive_scan_256(T v, T *smem_warp /*[8]*/,
     __syncthreads();
     total = tot;
     return wpre + x - v;
+}
+
+// The same for blockDim.x == 256.
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan_256(T v, T *smem_warp /*[8]*/, T &total)
+{
+    return block_exclusive_scan<8, T>(v, smem_warp, total);
 }
 
 // ---- bulk copies (cp.async.bulk) and shared-memory barriers ----------------

@@ -570,9 +570,12 @@ __device__ __forceinline__ int group_len(int k) { return k == 4 ? 48 : k == 3 ? 
 // moves by (-lr m) / (sqrt(v) ibc2 + eps) = -0), so its replay is skipped and,
 // without a gradient step, it is not written at all.
 enum LazyMode { kLazyAll = 0, kLazyCandidates = 1, kLazyGrad = 2 };
+// kLazyCandidates runs over the list of the candidates that are behind (the
+// catch-up list), in the order a selection pass appended them: each
+// Gaussian's replay is independent of the others, so the order is immaterial.
 
 struct LazyItems {
-    const uint32_t *cand_g;    // kLazyCandidates: candidate Gaussians of the last gate
+    const uint32_t *cand_g;    // kLazyCandidates: the catch-up list (Gaussians of the gate's candidates that are behind)
     const uint32_t *rec_g;     // kLazyGrad: Gaussian of each record (a Gaussian's records contiguous)
     const uint32_t *rec_first; // kLazyGrad: first record of each Gaussian
     const float *cgrad;        // kLazyGrad: compact gradient rows at the first record
@@ -583,7 +586,7 @@ struct LazyItems {
 template <int MODE> __device__ __forceinline__ unsigned long long lazy_count(const LazyItems &it)
 {
     return MODE == kLazyAll ? (unsigned long long)it.n
-                            : MODE == kLazyCandidates ? it.ctr->n_candidates : it.ctr->n_records;
+                            : MODE == kLazyCandidates ? it.ctr->n_catchup : it.ctr->n_records;
 }
 
 // item j -> Gaussian i; false for a record that is not its Gaussian's first
@@ -848,10 +851,49 @@ static cudaError_t launch_lazy_list(gs_workspace *ws, cudaStream_t st, const Laz
     return cudaGetLastError();
 }
 
+// The catch-up list: the gate's candidates whose p, m, v are behind the
+// current step (in the steady state of a training run, few or none), appended
+// with one atomic per warp.
+__global__ void __launch_bounds__(256) lazy_select_kernel(const uint32_t *cand_g, const int32_t *last,
+                                                          const int *d_step, uint32_t *list, DevCounters *ctr)
+{
+    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
+    const unsigned long long ncand = ctr->n_candidates;
+    const int t = *d_step, lane = threadIdx.x & 31;
+    for (unsigned long long j0 = (unsigned long long)blockIdx.x * 256 + (threadIdx.x & ~31u); j0 < ncand;
+         j0 += (unsigned long long)gridDim.x * 256) {
+        const unsigned long long j = j0 + lane;
+        uint32_t i = 0;
+        bool behind = false;
+        if (j < ncand) {
+            i = cand_g[j];
+            behind = last[i] < t;
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, behind);
+        if (!b) continue;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&ctr->n_catchup, (unsigned long long)__popc(b));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (behind) list[base + __popc(b & ((1u << lane) - 1u))] = i;
+    }
+}
+
 cudaError_t launch_lazy_catchup(gs_workspace *ws, cudaStream_t st, const gs_gaussians &g)
 {
     if (g.n == 0) return cudaSuccess;
-    return launch_lazy_list<kLazyCandidates>(ws, st, lazy_args(ws, params_of(g), g.n), (unsigned long long)g.n);
+    // the list goes to the gate's per-chunk candidate buffer ([n], free once gathered)
+    launch_pdl(lazy_select_kernel, lazy_grid(ws, (unsigned long long)g.n), 256, 0, st, ws->cand_g, ws->lazy.last,
+               ws->d_adam_step, ws->gate_g, ws->ctr);
+    note_launch();
+    LazyArgs a = lazy_args(ws, params_of(g), g.n);
+    LazyItems it = lazy_items(ws, 0);
+    it.cand_g = ws->gate_g;
+    launch_pdl(lazy_list_vec_kernel<kLazyCandidates>, lazy_grid(ws, (unsigned long long)g.n * kLazyUnits), 256, 0,
+               st, a, it);
+    note_launch();
+    launch_pdl(lazy_fin_kernel<kLazyCandidates>, lazy_grid(ws, (unsigned long long)g.n), 256, 0, st, a, it);
+    note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_lazy_flush(gs_workspace *ws, cudaStream_t st, const gs_gaussians &g)

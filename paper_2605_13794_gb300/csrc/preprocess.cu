@@ -730,15 +730,84 @@ __global__ void __launch_bounds__(256) gate_gather_kernel(PreOut o, const unsign
 // projection decides which cameras are active; the records are compacted in
 // (Gaussian, camera) order with a look-back scan and written with their
 // conic, colour, opacity, rectangle and depth key.
-__global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, const CamTable *__restrict__ ctp,
-                                                         RenderConsts rc)
+struct RecOut {
+    float4 rd0, rd1, rd2;
+    uint2 rect;
+    uint32_t tt, dkey;
+    uint8_t clm;
+};
+
+// The record of Gaussian i (loaded as L, opacity op) in camera cam from its
+// (passing) projection p: the colour from the SH coefficients, the rectangle
+// and the depth key.
+__device__ __forceinline__ RecOut make_record(const GaussPtrs &g, long long i, const GaussLoad &L, float op,
+                                              const CamInfo &cam, const Proj &p, const RenderConsts &rc, bool marked)
 {
+    const float dx = L.m[0] - cam.campos[0], dy = L.m[1] - cam.campos[1], dz = L.m[2] - cam.campos[2];
+    const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+    float Y[16];
+    sh_basis(dx * inv, dy * inv, dz * inv, Y);
+    float col[3] = {0.f, 0.f, 0.f};
+    uint8_t clm = 0;
+    const float4 *shv = reinterpret_cast<const float4 *>(g.sh + 48 * i); // [16][3], 16-byte aligned
+#pragma unroll
+    for (int v4 = 0; v4 < 12; v4++) {
+        const float4 c4 = shv[v4];
+        const float cc[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const int flat = 4 * v4 + e; // coefficient flat / 3, channel flat % 3
+            col[flat % 3] = fmaf(cc[e], Y[flat / 3], col[flat % 3]);
+        }
+    }
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        float acc = col[ch] + 0.5f;
+        if (acc < 0.f) { acc = 0.f; clm |= (uint8_t)(1u << ch); }
+        col[ch] = acc;
+    }
+    RecOut o;
+    o.rd0 = make_float4(p.u, p.v, p.A, p.k);
+    o.rd1 = make_float4(p.D, op, col[0], col[1]);
+    o.rd2 = make_float4(col[2], p.u_lo, p.v_lo, marked ? 1.f : 0.f);
+    o.rect = make_uint2((uint32_t)p.x0 | ((uint32_t)p.y0 << 16), (uint32_t)p.x1 | ((uint32_t)p.y1 << 16));
+    o.tt = (uint32_t)((p.x1 - p.x0) * (p.y1 - p.y0));
+    o.dkey = __float_as_uint(p.depth);
+    o.clm = clm;
+    return o;
+}
+
+__device__ __forceinline__ void store_record(const PreOut &o, unsigned long long r, long long i, int c,
+                                             const RecOut &q)
+{
+    o.rec_g[r] = (uint32_t)i;
+    o.rec_cam[r] = (uint16_t)c;
+    o.rd0[r] = q.rd0;
+    o.rd1[r] = q.rd1;
+    o.rd2[r] = q.rd2;
+    o.rect[r] = q.rect;
+    o.tt[r] = q.tt;
+    o.dkey[r] = q.dkey;
+    o.clampm[r] = q.clm;
+}
+
+// kOneCam: a candidate has at most one record, which is computed (colour
+// included, from the projection that decided it) before the block's scan and
+// look-back, so the look-back of one warp does not leave the others idle in
+// front of the colour's loads.  Blocks of kProjThreads take chunks of as many
+// candidates.
+constexpr int kProjThreads = 128;
+template <bool kOneCam>
+__global__ void __launch_bounds__(kProjThreads) project_kernel(GaussPtrs g, PreOut o, const CamTable *__restrict__ ctp,
+                                                               RenderConsts rc)
+{
+    constexpr int kNW = kProjThreads / 32;
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const CamTable &ct = *ctp;
     __shared__ CamInfo s_cams[GS_MAX_CAMERAS];
     __shared__ float s_thr2[kMaxLod + 1];
     __shared__ unsigned s_bid;
-    __shared__ unsigned long long s_warp[8];
+    __shared__ unsigned long long s_warp[kNW];
     __shared__ unsigned long long s_base;
     const unsigned long long ncand = o.ctr->n_candidates;
     const int tw = ct.tile_w, th = ct.tile_h;
@@ -747,23 +816,26 @@ __global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, 
         for (int l = 0; l <= kMaxLod; l++) s_thr2[l] = rc.lod_thr2[l];
     }
     stage_cameras(ct, s_cams);
-    // persistent blocks: each takes the next 256 candidates (tickets in order,
-    // so every look-back waits only on chunks already being processed)
+    // persistent blocks: each takes the next chunk of candidates (tickets in
+    // order, so every look-back waits only on chunks already being processed)
     for (;;) {
     if (threadIdx.x == 0) s_bid = atomicAdd((unsigned *)o.lb_status, 1u);
     __syncthreads();
     const unsigned bid = s_bid;
-    if ((unsigned long long)bid * 256 >= ncand) return;
-    const unsigned long long j = (unsigned long long)bid * 256 + threadIdx.x;
+    if ((unsigned long long)bid * kProjThreads >= ncand) return;
+    const unsigned long long j = (unsigned long long)bid * kProjThreads + threadIdx.x;
     GaussLoad L;
     L.have_shape = false;
     long long i = 0;
     unsigned long long act = 0;
+    float op = 0.f;
+    Proj p_one; // one camera: the projection of the active record
     if (j < ncand) {
         i = o.cand_g[j];
         const unsigned long long cm = o.cand_mask[j];
         L.m[0] = g.mean[3 * i]; L.m[1] = g.mean[3 * i + 1]; L.m[2] = g.mean[3 * i + 2];
         load_shape(g, i, L);
+        const float ol = g.opacity_logit[i];
         const int lod = (rc.lod_enable && g.lod) ? (int)g.lod[i] : 0;
         for (unsigned long long mm = cm; mm; mm &= mm - 1) {
             const int c = __ffsll((long long)mm) - 1;
@@ -773,8 +845,12 @@ __global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, 
             camera_point_df(L.m, s_cams[c], td);
             if (!(td[2].hi > rc.znear)) continue;
             Proj p;
-            if (project_gaussian(L.ls, L.q, td, s_cams[c], tw, th, rc, p)) act |= 1ull << c;
+            if (project_gaussian(L.ls, L.q, td, s_cams[c], tw, th, rc, p)) {
+                act |= 1ull << c;
+                if (kOneCam) p_one = p;
+            }
         }
+        op = 1.f / (1.f + expf(-ol));
     }
     const unsigned long long cnt = __popcll(act);
     // GS_CULL_MARK: records of the cameras whose Cull bit is set are kept and marked
@@ -784,9 +860,11 @@ __global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, 
             const int c = __ffsll((long long)mm) - 1;
             if (cull_bit(o, c, i)) marked |= 1ull << c;
         }
+    RecOut one;
+    if (kOneCam && act) one = make_record(g, i, L, op, s_cams[0], p_one, rc, marked & 1ull);
     unsigned long long total, tvis;
-    const unsigned long long excl = block_exclusive_scan_256<unsigned long long>(cnt, s_warp, total);
-    block_exclusive_scan_256<unsigned long long>((unsigned long long)((act & ~marked) != 0), s_warp, tvis);
+    const unsigned long long excl = block_exclusive_scan<kNW, unsigned long long>(cnt, s_warp, total);
+    block_exclusive_scan<kNW, unsigned long long>((unsigned long long)((act & ~marked) != 0), s_warp, tvis);
     if (threadIdx.x < 32) {
         const unsigned long long b = lookback_exclusive(o.lb_status + 1, bid, total, o.ctr, kSitePreprocess);
         if (threadIdx.x == 0) {
@@ -802,54 +880,27 @@ __global__ void __launch_bounds__(256, 2) project_kernel(GaussPtrs g, PreOut o, 
         o.ctr->n_records = end < (unsigned long long)o.max_records ? end : o.max_records;
     }
     if (act) {
-    if (base < (unsigned long long)o.max_records) o.rec_first[i] = (uint32_t)base;
-    const float op = 1.f / (1.f + expf(-g.opacity_logit[i]));
-    unsigned long long r = base;
-    for (unsigned long long mm = act; mm; mm &= mm - 1, r++) {
-        const int c = __ffsll((long long)mm) - 1;
-        if (r >= (unsigned long long)o.max_records) {
-            set_error(o.ctr, GS_ERR_CAPACITY, kSitePreprocess);
-            break;
-        }
-        const CamInfo &cam = s_cams[c];
-        DF td[3];
-        camera_point_df(L.m, cam, td);
-        Proj p;
-        project_gaussian(L.ls, L.q, td, cam, tw, th, rc, p); // same inputs: same (passing) result
-        const float dx = L.m[0] - cam.campos[0], dy = L.m[1] - cam.campos[1], dz = L.m[2] - cam.campos[2];
-        const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
-        float Y[16];
-        sh_basis(dx * inv, dy * inv, dz * inv, Y);
-        float col[3] = {0.f, 0.f, 0.f};
-        uint8_t clm = 0;
-        const float4 *shv = reinterpret_cast<const float4 *>(g.sh + 48 * i); // [16][3], 16-byte aligned
-#pragma unroll
-        for (int v4 = 0; v4 < 12; v4++) {
-            const float4 c4 = shv[v4];
-            const float cc[4] = {c4.x, c4.y, c4.z, c4.w};
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                const int flat = 4 * v4 + e; // coefficient flat / 3, channel flat % 3
-                col[flat % 3] = fmaf(cc[e], Y[flat / 3], col[flat % 3]);
+        if (base < (unsigned long long)o.max_records) o.rec_first[i] = (uint32_t)base;
+        if (kOneCam) {
+            if (base >= (unsigned long long)o.max_records) set_error(o.ctr, GS_ERR_CAPACITY, kSitePreprocess);
+            else store_record(o, base, i, 0, one);
+        } else {
+            unsigned long long r = base;
+            for (unsigned long long mm = act; mm; mm &= mm - 1, r++) {
+                const int c = __ffsll((long long)mm) - 1;
+                if (r >= (unsigned long long)o.max_records) {
+                    set_error(o.ctr, GS_ERR_CAPACITY, kSitePreprocess);
+                    break;
+                }
+                const CamInfo &cam = s_cams[c];
+                DF td[3];
+                camera_point_df(L.m, cam, td);
+                Proj p;
+                project_gaussian(L.ls, L.q, td, cam, tw, th, rc, p); // same inputs: same (passing) result
+                store_record(o, r, i, c, make_record(g, i, L, op, cam, p, rc, (marked >> c) & 1ull));
             }
         }
-#pragma unroll
-        for (int ch = 0; ch < 3; ch++) {
-            float acc = col[ch] + 0.5f;
-            if (acc < 0.f) { acc = 0.f; clm |= (uint8_t)(1u << ch); }
-            col[ch] = acc;
-        }
-        o.rec_g[r] = (uint32_t)i;
-        o.rec_cam[r] = (uint16_t)c;
-        o.rd0[r] = make_float4(p.u, p.v, p.A, p.k);
-        o.rd1[r] = make_float4(p.D, op, col[0], col[1]);
-        o.rd2[r] = make_float4(col[2], p.u_lo, p.v_lo, ((marked >> c) & 1ull) ? 1.f : 0.f);
-        o.rect[r] = make_uint2((uint32_t)p.x0 | ((uint32_t)p.y0 << 16), (uint32_t)p.x1 | ((uint32_t)p.y1 << 16));
-        o.tt[r] = (uint32_t)((p.x1 - p.x0) * (p.y1 - p.y0));
-        o.dkey[r] = __float_as_uint(p.depth);
-        o.clampm[r] = clm;
     }
-    } // act
     __syncthreads(); // every thread is done with this chunk's shared values
     } // chunks
 }
@@ -860,7 +911,7 @@ cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t 
 {
     const long long n = ws->g.n;
     const unsigned gblocks = (unsigned)((n + kGateChunk - 1) / kGateChunk); // chunks
-    const unsigned pblocks = (unsigned)((n + 255) / 256);
+    const unsigned pchunks = (unsigned)((n + kProjThreads - 1) / kProjThreads); // projection chunks (at most)
     cudaError_t e;
     // counters, then the look-back state of each stage (ticket in word 0)
     if ((e = cudaMemsetAsync(ws->ctr, 0, sizeof(DevCounters), st)) != cudaSuccess) return e;
@@ -902,14 +953,18 @@ cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t 
     note_launch();
     launch_pdl(gate_gather_kernel, gblocks, 256, 0, st, o, ws->lb_status, (long long)gblocks, ws->ctr);
     note_launch();
-    if ((e = cudaMemsetAsync(ws->lb_status, 0, (pblocks + 1) * sizeof(unsigned long long), st)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(ws->lb_status, 0, (pchunks + 1) * sizeof(unsigned long long), st)) != cudaSuccess)
         return e;
     // deferred Adam steps: bring the candidates up to date before projecting them
     if (ws->lazy.enabled && (e = launch_lazy_catchup(ws, st, ws->g)) != cudaSuccess) return e;
-    // projection: two persistent 256-thread blocks per SM
-    const unsigned pgrid = std::min<unsigned>(pblocks, 2u * (unsigned)ws->sm_count);
+    // projection: persistent blocks, about as many as stay resident (five per
+    // SM at their registers), taking the candidates' chunks by ticket
+    const unsigned pgrid = std::min<unsigned>(pchunks, 5u * (unsigned)ws->sm_count);
     kt_begin(ws, GS_KT_PROJECT, st);
-    launch_pdl(project_kernel, pgrid, 256, 0, st, gp, o, ws->d_cams, ws->rc);
+    if (ws->cams.n == 1)
+        launch_pdl(project_kernel<true>, pgrid, kProjThreads, 0, st, gp, o, ws->d_cams, ws->rc);
+    else
+        launch_pdl(project_kernel<false>, pgrid, kProjThreads, 0, st, gp, o, ws->d_cams, ws->rc);
     kt_end(ws, GS_KT_PROJECT, st);
     note_launch();
     return cudaGetLastError();
