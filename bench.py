@@ -387,7 +387,9 @@ def bwd_roofline(fragments, composited, instances, pixels, kernel_ms, sm_mhz, pe
 #     camera mask 8 B written
 #   depth sort of the records: per record and pass 16 B (key and value read
 #     and written; the first pass reads no values) and 4 B of the histogram read
-#   tile sort of the instances: the same per instance and pass
+#   emission and tile sort of the instances: per instance 8 B written (key,
+#     record), then per pass 16 B; per record 16 B read (order, count,
+#     rectangle, camera)
 #   slot reduction: per instance 36 B (its slot); per record 16 B of indices
 #     and 36 B of summed gradient written
 #   projection adjoint: per visible Gaussian 44 B of shape and opacity read and
@@ -398,7 +400,7 @@ def bwd_roofline(fragments, composited, instances, pixels, kernel_ms, sm_mhz, pe
 HBM_KERNELS = {
     "gate_count_kernel": ("GS_KT_GATE", lambda c: 17 * c["n"] + 28 * c["n_candidates"]),
     "depth_sort": ("GS_KT_DEPTH_SORT", lambda c: 16 * c["depth_passes"] * c["n_records"]),
-    "tile_sort": ("GS_KT_TILE_SORT", lambda c: (16 * c["tile_passes"] + 4) * c["n_instances"]),
+    "emit_tile_sort": ("GS_KT_TILE_SORT", lambda c: (16 * c["tile_passes"] + 8) * c["n_instances"] + 16 * c["n_records"]),
     "reduce_slots_kernel": ("GS_KT_REDUCE_SLOTS", lambda c: 36 * c["n_instances"] + 52 * c["n_records"]),
     "preprocess_bwd_kernel": ("GS_KT_PREPROCESS_BWD", lambda c: 280 * c["n_visible"] + 64 * c["n_records"]),
     "ssim_fwd_kernel": ("GS_KT_SSIM_FWD", lambda c: 24 * 3 * c["pixels"]),

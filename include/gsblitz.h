@@ -503,7 +503,7 @@ enum {
     GS_KT_GATE = 3,            /* the view gate's pass over every Gaussian (gs_preprocess) */
     GS_KT_PROJECT = 4,         /* the projection of the gate's candidates (gs_preprocess) */
     GS_KT_DEPTH_SORT = 5,      /* gs_bin_sort's depth sort of the records, all of its kernels */
-    GS_KT_TILE_SORT = 6,       /* gs_bin_sort's sort of the instances by tile, all of its kernels */
+    GS_KT_TILE_SORT = 6,       /* gs_bin_sort: emission of the instances and their sort by tile */
     GS_KT_REDUCE_SLOTS = 7,    /* the per-record sum of the adjoint's gradient slots */
     GS_KT_PREPROCESS_BWD = 8,  /* the projection adjoint (per Gaussian) */
     GS_KT_SSIM_FWD = 9,        /* gs_photometric_loss: the SSIM statistics and coefficient maps */

@@ -546,22 +546,26 @@ int gs_bin_sort(gs_workspace *ws, gs_stream stream)
     cudaStream_t st = (cudaStream_t)stream;
     // 1. depth order of the records
     int ob = 0;
+    // (the projection filled the depth keys' histograms, once per preprocess)
     gs::kt_begin(ws, GS_KT_DEPTH_SORT, st);
     CK(gs::launch_radix_sort(ws, st, ws->dkey, ws->dval, &ws->ctr->n_records, (unsigned long long)ws->cap.max_records,
-                             32, true, false, ob),
+                             32, true, ws->depth_hist_ready != 0, ob),
        "gs_bin_sort(depth)");
     gs::kt_end(ws, GS_KT_DEPTH_SORT, st);
+    ws->depth_hist_ready = 0;
     ws->depth_buf = ob;
-    // 2. emission of (tile, record) instances in depth order
-    CK(cudaMemsetAsync(&ws->ctr->n_instances, 0, sizeof(unsigned long long), st), "gs_bin_sort");
-    CK(cudaMemsetAsync(&ws->ctr->instances_needed, 0, sizeof(unsigned long long), st), "gs_bin_sort");
-    CK(gs::launch_emit(ws, st), "gs_bin_sort(emit)");
-    // 3. stable sort by global tile id
+    // 2. emission of (tile, record) instances in depth order, with the
+    // histograms of their tile keys
     int bits = 0;
     while ((1ll << bits) < (long long)ws->cams.total_tiles) bits++;
+    CK(cudaMemsetAsync(&ws->ctr->n_instances, 0, sizeof(unsigned long long), st), "gs_bin_sort");
+    CK(cudaMemsetAsync(&ws->ctr->instances_needed, 0, sizeof(unsigned long long), st), "gs_bin_sort");
     gs::kt_begin(ws, GS_KT_TILE_SORT, st);
+    CK(gs::launch_radix_clear(ws, st, (unsigned long long)ws->cap.max_instances, bits), "gs_bin_sort(tiles)");
+    CK(gs::launch_emit(ws, st, ws->rx_status, bits <= 0 ? 1 : (bits + 7) / 8), "gs_bin_sort(emit)");
+    // 3. stable sort by global tile id
     CK(gs::launch_radix_sort(ws, st, ws->tkey, ws->tval, &ws->ctr->n_instances,
-                             (unsigned long long)ws->cap.max_instances, bits, false, false, ob),
+                             (unsigned long long)ws->cap.max_instances, bits, false, true, ob),
        "gs_bin_sort(tiles)");
     gs::kt_end(ws, GS_KT_TILE_SORT, st);
     ws->tile_buf = ob;

@@ -363,6 +363,7 @@ struct gs_workspace {
     size_t lb_words;
     uint32_t *rx_status; // radix: [4][256] histograms, then per pass [blocks * 256 + 1] look-back + ticket
     size_t rx_words;
+    int depth_hist_ready; // the last preprocess filled the depth sort's histograms (rx_status)
     uint32_t *rx_hist;   // [4][256]: the first kRxHistWords words of rx_status (also a scratch of 1024 words)
     float *red_partial;  // [blocks] reduction partials of the adjoint (scale regulariser)
     size_t red_words;
@@ -436,8 +437,11 @@ cudaError_t launch_render_fwd_importance(gs_workspace *ws, cudaStream_t st, floa
 cudaError_t launch_importance_reduce(gs_workspace *ws, cudaStream_t st);
 cudaError_t launch_radix_sort(gs_workspace *ws, cudaStream_t st, uint32_t *keys[2], uint32_t *vals[2],
                               const unsigned long long *count, unsigned long long cap, int bits, bool vals_identity,
-                              bool descending_keys_in_place, int &out_buf, unsigned long long spin_limit = kSpinLimit);
-cudaError_t launch_emit(gs_workspace *ws, cudaStream_t st);
+                              bool hist_ready, int &out_buf, unsigned long long spin_limit = kSpinLimit);
+// Clears the histograms and look-back state of a launch_radix_sort of up to cap
+// keys of `bits` bits (for a producer that fills the histograms itself).
+cudaError_t launch_radix_clear(gs_workspace *ws, cudaStream_t st, unsigned long long cap, int bits);
+cudaError_t launch_emit(gs_workspace *ws, cudaStream_t st, uint32_t *hist, int passes);
 cudaError_t launch_ranges(gs_workspace *ws, cudaStream_t st);
 cudaError_t launch_render_fwd(gs_workspace *ws, cudaStream_t st, float *rgb, float *T_out);
 cudaError_t launch_render_bwd(gs_workspace *ws, cudaStream_t st, const float *dL_drgb);

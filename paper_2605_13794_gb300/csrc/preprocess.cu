@@ -354,6 +354,7 @@ struct PreOut {
     long long max_records;
     const uint32_t *cull;
     long long cull_words;
+    uint32_t *dhist;               // [4][256] byte histograms of the depth keys written (cleared), or NULL
 };
 
 struct GaussLoad {
@@ -809,20 +810,33 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(GaussPtrs g, PreO
     __shared__ unsigned s_bid;
     __shared__ unsigned long long s_warp[kNW];
     __shared__ unsigned long long s_base;
+    __shared__ uint32_t s_dh[4][256]; // the block's share of the depth keys' histograms
     const unsigned long long ncand = o.ctr->n_candidates;
     const int tw = ct.tile_w, th = ct.tile_h;
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int l = 0; l <= kMaxLod; l++) s_thr2[l] = rc.lod_thr2[l];
     }
-    stage_cameras(ct, s_cams);
+    for (int q = threadIdx.x; q < 4 * 256; q += kProjThreads) (&s_dh[0][0])[q] = 0u;
+    stage_cameras(ct, s_cams); // ends with a block barrier
+    auto count_key = [&](uint32_t key) {
+#pragma unroll
+        for (int p = 0; p < 4; p++) atomicAdd(&s_dh[p][(key >> (8 * p)) & 255u], 1u);
+    };
     // persistent blocks: each takes the next chunk of candidates (tickets in
     // order, so every look-back waits only on chunks already being processed)
     for (;;) {
     if (threadIdx.x == 0) s_bid = atomicAdd((unsigned *)o.lb_status, 1u);
     __syncthreads();
     const unsigned bid = s_bid;
-    if ((unsigned long long)bid * kProjThreads >= ncand) return;
+    if ((unsigned long long)bid * kProjThreads >= ncand) { // no chunk left: the histograms out
+        if (o.dhist)
+            for (int q = threadIdx.x; q < 4 * 256; q += kProjThreads) {
+                const uint32_t v = (&s_dh[0][0])[q];
+                if (v) atomicAdd(&o.dhist[q], v);
+            }
+        return;
+    }
     const unsigned long long j = (unsigned long long)bid * kProjThreads + threadIdx.x;
     GaussLoad L;
     L.have_shape = false;
@@ -883,7 +897,10 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(GaussPtrs g, PreO
         if (base < (unsigned long long)o.max_records) o.rec_first[i] = (uint32_t)base;
         if (kOneCam) {
             if (base >= (unsigned long long)o.max_records) set_error(o.ctr, GS_ERR_CAPACITY, kSitePreprocess);
-            else store_record(o, base, i, 0, one);
+            else {
+                store_record(o, base, i, 0, one);
+                count_key(one.dkey);
+            }
         } else {
             unsigned long long r = base;
             for (unsigned long long mm = act; mm; mm &= mm - 1, r++) {
@@ -897,7 +914,9 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(GaussPtrs g, PreO
                 camera_point_df(L.m, cam, td);
                 Proj p;
                 project_gaussian(L.ls, L.q, td, cam, tw, th, rc, p); // same inputs: same (passing) result
-                store_record(o, r, i, c, make_record(g, i, L, op, cam, p, rc, (marked >> c) & 1ull));
+                const RecOut q = make_record(g, i, L, op, cam, p, rc, (marked >> c) & 1ull);
+                store_record(o, r, i, c, q);
+                count_key(q.dkey);
             }
         }
     }
@@ -913,6 +932,7 @@ cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t 
     const unsigned gblocks = (unsigned)((n + kGateChunk - 1) / kGateChunk); // chunks
     const unsigned pchunks = (unsigned)((n + kProjThreads - 1) / kProjThreads); // projection chunks (at most)
     cudaError_t e;
+    ws->depth_hist_ready = 0; // until the projection below fills them
     // counters, then the look-back state of each stage (ticket in word 0)
     if ((e = cudaMemsetAsync(ws->ctr, 0, sizeof(DevCounters), st)) != cudaSuccess) return e;
     if (n == 0) return cudaSuccess;
@@ -927,6 +947,7 @@ cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t 
     o.ctr = ws->ctr; o.max_records = ws->cap.max_records;
     o.cull = ws->rc.cull_enable ? cull : nullptr;
     o.cull_words = (n + 31) / 32;
+    o.dhist = nullptr;
     if ((e = cudaMemsetAsync(ws->rec_first, 0xff, (size_t)n * sizeof(uint32_t), st)) != cudaSuccess) return e;
     // gate: per-block counts (in lb_status) and candidates (block-strided), the
     // scan of the counts, the gather into one ordered list
@@ -957,6 +978,10 @@ cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t 
         return e;
     // deferred Adam steps: bring the candidates up to date before projecting them
     if (ws->lazy.enabled && (e = launch_lazy_catchup(ws, st, ws->g)) != cudaSuccess) return e;
+    // the depth sort's scratch, whose histograms the projection fills
+    if ((e = launch_radix_clear(ws, st, (unsigned long long)ws->cap.max_records, 32)) != cudaSuccess) return e;
+    o.dhist = ws->cap.max_records > 0 ? ws->rx_status : nullptr;
+    ws->depth_hist_ready = o.dhist != nullptr;
     // projection: persistent blocks, about as many as stay resident (five per
     // SM at their registers), taking the candidates' chunks by ticket
     const unsigned pgrid = std::min<unsigned>(pchunks, 5u * (unsigned)ws->sm_count);

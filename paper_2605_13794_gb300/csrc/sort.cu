@@ -225,30 +225,58 @@ static cudaError_t radix_passes(cudaStream_t st, uint32_t *keys[2], uint32_t *va
 // chosen by the size of the sort).  One memset clears the histograms and the
 // look-back state of every pass (ws->rx_status: [4][256] histogram words,
 // then one region per pass), so the sort's kernels follow one another with
-// programmatic dependent launch.
+// programmatic dependent launch.  hist_ready: the producer of the keys has
+// filled the histograms after launch_radix_clear for this cap and bits.
+// Keys per block of a sort of up to cap keys: the workspace's tuning, or by
+// size (0): small sorts take small blocks so that enough SMs work on them.
+static int radix_items(const gs_workspace *ws, unsigned long long cap)
+{
+    int items = ws->sort_items;
+    if (items == 0) items = cap <= (1ull << 20) ? 4 : (cap <= (16ull << 20) ? 8 : 16);
+    if (items != 4 && items != 8) items = kSortItems;
+    return items;
+}
+
+// Words of ws->rx_status a sort of up to cap keys of `bits` bits uses: the
+// histograms, then one look-back region per pass.
+static size_t radix_words(const gs_workspace *ws, unsigned long long cap, int bits, size_t &region)
+{
+    const int passes = bits <= 0 ? 1 : (bits + 7) / 8;
+    const int items = radix_items(ws, cap);
+    const unsigned long long blocks = (cap + kSortThreads * items - 1) / (kSortThreads * items);
+    region = (size_t)blocks * 256 + 1;
+    return kRxHistWords + passes * region;
+}
+
+cudaError_t launch_radix_clear(gs_workspace *ws, cudaStream_t st, unsigned long long cap, int bits)
+{
+    size_t region;
+    const size_t words = radix_words(ws, cap, bits, region);
+    if (cap == 0) return cudaSuccess;
+    if (words > ws->rx_words) return cudaErrorInvalidValue; // sized for this cap
+    return cudaMemsetAsync(ws->rx_status, 0, words * sizeof(uint32_t), st);
+}
+
 cudaError_t launch_radix_sort(gs_workspace *ws, cudaStream_t st, uint32_t *keys[2], uint32_t *vals[2],
                               const unsigned long long *count, unsigned long long cap, int bits, bool vals_identity,
-                              bool /*unused*/, int &out_buf, unsigned long long spin_limit)
+                              bool hist_ready, int &out_buf, unsigned long long spin_limit)
 {
     const int passes = bits <= 0 ? 1 : (bits + 7) / 8;
     cudaError_t e;
     out_buf = 0;
     if (cap == 0) return cudaSuccess;
-    // keys per block: the workspace's tuning, or by size (0): small sorts take
-    // small blocks so that enough SMs work on them
-    int items = ws->sort_items;
-    if (items == 0) items = cap <= (1ull << 20) ? 4 : (cap <= (16ull << 20) ? 8 : 16);
-    if (items != 4 && items != 8) items = kSortItems;
-    const unsigned long long blocks = (cap + kSortThreads * items - 1) / (kSortThreads * items);
-    const size_t region = (size_t)blocks * 256 + 1;
+    const int items = radix_items(ws, cap);
+    size_t region;
+    const size_t words = radix_words(ws, cap, bits, region);
     uint32_t *hist = ws->rx_status, *status = ws->rx_status + kRxHistWords;
-    if (kRxHistWords + passes * region > ws->rx_words) return cudaErrorInvalidValue; // sized for this cap
-    if ((e = cudaMemsetAsync(hist, 0, (kRxHistWords + passes * region) * sizeof(uint32_t), st)) != cudaSuccess)
-        return e;
-    unsigned hblocks = (unsigned)((cap + 255) / 256);
-    if (hblocks > 1216) hblocks = 1216;
-    launch_pdl(radix_hist_kernel, hblocks, 256, 0, st, keys[0], count, cap, passes, hist);
-    note_launch();
+    if (words > ws->rx_words) return cudaErrorInvalidValue; // sized for this cap
+    if (!hist_ready) {
+        if ((e = cudaMemsetAsync(hist, 0, words * sizeof(uint32_t), st)) != cudaSuccess) return e;
+        unsigned hblocks = (unsigned)((cap + 255) / 256);
+        if (hblocks > 1216) hblocks = 1216;
+        launch_pdl(radix_hist_kernel, hblocks, 256, 0, st, keys[0], count, cap, passes, hist);
+        note_launch();
+    }
     if (items == 4)
         return radix_passes<4>(st, keys, vals, count, cap, passes, vals_identity, status, region, hist, ws->ctr,
                                out_buf, spin_limit);
@@ -293,6 +321,8 @@ struct EmitArgs {
     unsigned long long *lb_status; // ticket at word 0
     DevCounters *ctr;
     unsigned long long max_instances;
+    uint32_t *hist;  // [4][256] digit histograms of the written keys (the tile sort's), or nullptr
+    int passes;      // digits of the tile keys
 };
 
 __global__ void __launch_bounds__(256) emit_kernel(EmitArgs a, const CamTable *__restrict__ ctp)
@@ -306,7 +336,10 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitArgs a, const CamTable *_
     __shared__ uint32_t s_rec[256];
     __shared__ uint2 s_rect[256];
     __shared__ int s_tb[256], s_tx[256];
+    __shared__ uint32_t s_hist[4][256];
     if (threadIdx.x == 0) s_bid = atomicAdd((unsigned *)a.lb_status, 1u);
+    if (a.hist)
+        for (int q = threadIdx.x; q < 4 * 256; q += 256) (&s_hist[0][0])[q] = 0u;
     __syncthreads();
     const unsigned bid = s_bid;
     const unsigned long long nrec = a.ctr->n_records;
@@ -356,12 +389,24 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitArgs a, const CamTable *_
         unpack_rect(s_rect[lo], x0, y0, x1, y1);
         const uint32_t w = (uint32_t)(x1 - x0);
         const int tx = x0 + (int)(local % w), ty = y0 + (int)(local / w);
-        a.tkey[gi] = (uint32_t)(s_tb[lo] + ty * s_tx[lo] + tx);
+        const uint32_t key = (uint32_t)(s_tb[lo] + ty * s_tx[lo] + tx);
+        a.tkey[gi] = key;
         a.tval[gi] = s_rec[lo];
+        if (a.hist)
+            for (int p = 0; p < a.passes; p++) atomicAdd(&s_hist[p][(key >> (8 * p)) & 255u], 1u);
+    }
+    if (a.hist) {
+        __syncthreads();
+        for (int q = threadIdx.x; q < a.passes * 256; q += 256) {
+            const uint32_t v = (&s_hist[0][0])[q];
+            if (v) atomicAdd(&a.hist[q], v);
+        }
     }
 }
 
-cudaError_t launch_emit(gs_workspace *ws, cudaStream_t st)
+// hist: the tile sort's histograms ([passes][256], cleared), filled as the
+// keys are written; nullptr: none.
+cudaError_t launch_emit(gs_workspace *ws, cudaStream_t st, uint32_t *hist, int passes)
 {
     const unsigned long long cap = (unsigned long long)ws->cap.max_records;
     const unsigned blocks = (unsigned)((cap + 255) / 256);
@@ -373,6 +418,7 @@ cudaError_t launch_emit(gs_workspace *ws, cudaStream_t st)
     a.tt = ws->tt; a.rect = ws->rect; a.rec_cam = ws->rec_cam; a.inst_off = ws->inst_off;
     a.tkey = ws->tkey[0]; a.tval = ws->tval[0];
     a.lb_status = ws->lb_status; a.ctr = ws->ctr; a.max_instances = (unsigned long long)ws->cap.max_instances;
+    a.hist = hist; a.passes = passes;
     launch_pdl(emit_kernel, blocks, 256, 0, st, a, ws->d_cams);
     note_launch();
     return cudaGetLastError();
