@@ -1046,6 +1046,7 @@ __global__ void __launch_bounds__(256) reduce_slots_kernel(const uint32_t *drec,
 #pragma unroll
             for (int j = 0; j < kSlotFloats; j++) acc[j] = 0.f;
             if (live) {
+                #pragma unroll 4 // the loads of four iterations in flight (the adds keep their order)
                 for (uint32_t t = sub; t < c; t += kReduceLanes) {
                     const float *sl = slots + (o + t) * kSlotFloats;
 #pragma unroll
@@ -1077,6 +1078,7 @@ __global__ void __launch_bounds__(256) reduce_slots_kernel(const uint32_t *drec,
             float acc[kSlotFloats];
 #pragma unroll
             for (int j = 0; j < kSlotFloats; j++) acc[j] = 0.f;
+            #pragma unroll 4 // the loads of four iterations in flight (the adds keep their order)
             for (uint32_t t = lane; t < c; t += 32) {
                 const float *sl = slots + (o + t) * kSlotFloats;
 #pragma unroll

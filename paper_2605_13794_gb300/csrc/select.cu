@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(256) imp_reduce_kernel(const uint32_t *drec, c
             float w = 0.f;
             uint32_t aa = 0;
             if (live)
+                #pragma unroll 4 // the loads of four iterations in flight (the adds keep their order)
                 for (uint32_t t = sub; t < c; t += kImpLanes) {
                     const float2 sl = slots[o + t];
                     w += sl.x;
@@ -78,6 +79,7 @@ __global__ void __launch_bounds__(256) imp_reduce_kernel(const uint32_t *drec, c
             const unsigned long long o = __shfl_sync(0xffffffffu, off, src);
             float w = 0.f;
             uint32_t aa = 0;
+            #pragma unroll 4 // the loads of four iterations in flight (the adds keep their order)
             for (uint32_t t = lane; t < c; t += 32) {
                 const float2 sl = slots[o + t];
                 w += sl.x;
