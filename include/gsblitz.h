@@ -222,8 +222,8 @@ int gs_workspace_destroy(gs_workspace *ws);
 int64_t gs_workspace_bytes(const gs_capacity *cap);
 /* Execution tuning that leaves every result unchanged: keys ranked per block
  * by the radix passes of gs_bin_sort and gs_importance, 1024, 2048 or 4096;
- * 0 (the default) picks by the size of each sort (1024 up to 2^20 keys of
- * capacity, 2048 up to 2^24, 4096 above).  Applies to the calls made after it. */
+ * 0 (the default) picks by the size of each sort (1024 up to 2^18 keys of
+ * capacity, 2048 up to 2^20, 4096 above).  Applies to the calls made after it. */
 int gs_workspace_set_sort_chunk(gs_workspace *ws, int32_t keys_per_block);
 
 /* View gate, projection and colour of every Gaussian for each of n_cams
