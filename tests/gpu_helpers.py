@@ -26,7 +26,7 @@ def gpu_params(P, **over):
     return B.RenderParams(**d)
 
 
-class GpuRun:
+class ViewRun:
     """One preprocess + bin_sort + render_fwd of a scene, with readbacks."""
 
     def __init__(self, g: synth.GaussianSet, cams, P, cull=None, ws=None, cap=None):

@@ -11,7 +11,7 @@ import torch
 import oracle as O
 from paper_2605_13794_gb300 import binding as B
 from paper_2605_13794_gb300 import synth
-from tests.gpu_helpers import (GpuRun, PARAM_NAMES, assert_gaussian_grads_close, assert_grad_close, capacity_for, gpu_params,
+from tests.gpu_helpers import (ViewRun, PARAM_NAMES, assert_gaussian_grads_close, assert_grad_close, capacity_for, gpu_params,
                                grads_to_host, oracle_view_matched)
 
 pytestmark = pytest.mark.gpu
@@ -54,7 +54,7 @@ def test_autograd_gradients_match_the_oracle():
     dL = np.random.default_rng(72).standard_normal((3, cam.height, cam.width))
     gg, rgb = _autograd_grads(g, cam, P, dL)
     # the same gradients as a direct gs_render_bwd call on an equal forward
-    run = GpuRun(g, [cam], P)
+    run = ViewRun(g, [cam], P)
     direct = run.gt.zeros_like()
     run.ws.render_bwd(run.gt, torch.from_numpy(dL.astype(np.float32).ravel()).cuda(), direct, accumulate=False)
     run.ws.sync_status()

@@ -9,7 +9,7 @@ import oracle as O
 from paper_2605_13794_gb300 import binding as B
 from paper_2605_13794_gb300 import synth
 from paper_2605_13794_gb300.train import TrainStep
-from tests.gpu_helpers import (GpuRun, assert_grad_close, assert_gaussian_grads_close, assert_param_grad_close, capacity_for, gpu_params,
+from tests.gpu_helpers import (ViewRun, assert_grad_close, assert_gaussian_grads_close, assert_param_grad_close, capacity_for, gpu_params,
                                grads_to_host)
 from tests.test_gpu_parity import _compare_view
 
@@ -36,7 +36,7 @@ def test_tile_shapes_forward_backward_importance(tw, th):
     g = synth.plain_scene(6000, seed=51)
     cams = _uneven_cameras()
     P = O.Params(tile_w=tw, tile_h=th)
-    run = GpuRun(g, cams, P)
+    run = ViewRun(g, cams, P)
     g64 = O.gaussians64(g)
     fwds = [_compare_view(run, c, g64, cam, P) for c, cam in enumerate(cams)]
     # backward over all three views at once
@@ -71,7 +71,7 @@ def test_tile_shapes_give_the_same_image_away_from_tile_dependent_fragments():
     cams = _uneven_cameras()
     imgs = []
     for tw, th in TILE_SHAPES:
-        run = GpuRun(g, cams, O.Params(tile_w=tw, tile_h=th))
+        run = ViewRun(g, cams, O.Params(tile_w=tw, tile_h=th))
         imgs.append(torch.cat([run.rgb]).double().cpu().numpy())
     for im in imgs[1:]:
         assert np.abs(im - imgs[0]).max() <= 1e-5
@@ -178,11 +178,11 @@ def test_sort_chunk_leaves_results_unchanged():
     g = synth.plain_scene(6000, seed=57)
     cams = _uneven_cameras()
     P = O.Params()
-    a = GpuRun(g, cams, P)
+    a = ViewRun(g, cams, P)
     ws = B.Workspace(**capacity_for(g.n, cams))
     for chunk in (1024, 2048, 4096):
         ws.set_sort_chunk(chunk)
-        b = GpuRun(g, cams, P, ws=ws)
+        b = ViewRun(g, cams, P, ws=ws)
         assert np.array_equal(a.sorted_vals, b.sorted_vals) and np.array_equal(a.ranges, b.ranges), chunk
         assert torch.equal(a.rgb, b.rgb) and np.array_equal(a.n_contrib, b.n_contrib), chunk
     with pytest.raises(B.GSError):
@@ -207,9 +207,9 @@ def test_each_view_of_a_batch_equals_its_render_alone():
     g = synth.plain_scene(5000, seed=58)
     cams = _mixed_cameras(64, 59)
     P = O.Params()
-    batch = GpuRun(g, cams, P)
+    batch = ViewRun(g, cams, P)
     for k in (0, 7, 31, 63):
-        alone = GpuRun(g, [cams[k]], P)
+        alone = ViewRun(g, [cams[k]], P)
         assert np.array_equal(batch.image(k), alone.image(0)), k
         assert np.array_equal(batch.T_final(k), alone.T_final(0)), k
 
@@ -230,7 +230,7 @@ def test_autotuner_picks_and_caches(tmp_path):
     assert (again.tile_w, again.tile_h, again.sort_chunk) == (choice.tile_w, choice.tile_h, choice.sort_chunk)
     # the chosen configuration renders what the oracle renders with that tiling
     P = O.Params(tile_w=choice.tile_w, tile_h=choice.tile_h)
-    run = GpuRun(synth.plain_scene(6000, seed=60), cams[:2], P)
+    run = ViewRun(synth.plain_scene(6000, seed=60), cams[:2], P)
     g64 = O.gaussians64(synth.plain_scene(6000, seed=60))
     for c in range(2):
         _compare_view(run, c, g64, cams[c], P)
@@ -258,7 +258,7 @@ def test_serving_batches_match_renders_alone():
     assert stats["slots"] == 3 and stats["max_in_flight"] >= 2 and stats["overlap_frac"] > 0
     P = O.Params()
     for r in (reqs[0], reqs[17], reqs[-1]):
-        alone = GpuRun(g_host, [r.cam], P)
+        alone = ViewRun(g_host, [r.cam], P)
         assert torch.equal(r.image, alone.rgb), r.rid
 
 
@@ -276,4 +276,4 @@ def test_serving_splits_a_batch_that_overflows():
     P = O.Params()
     g_host = synth.plain_scene(5000, seed=63)
     for r in (reqs[0], reqs[-1]):
-        assert torch.equal(r.image, GpuRun(g_host, [r.cam], P).rgb), r.rid
+        assert torch.equal(r.image, ViewRun(g_host, [r.cam], P).rgb), r.rid

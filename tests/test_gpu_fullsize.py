@@ -11,7 +11,7 @@ import torch
 import oracle as O
 from paper_2605_13794_gb300 import binding as B
 from paper_2605_13794_gb300 import synth
-from tests.gpu_helpers import (GpuRun, assert_grad_close, assert_gaussian_grads_close, assert_param_grad_close, assert_record_precision,
+from tests.gpu_helpers import (ViewRun, assert_grad_close, assert_gaussian_grads_close, assert_param_grad_close, assert_record_precision,
                                footprint_power_err, gpu_params, grads_to_host, oracle_view_matched, unpack_rect)
 
 pytestmark = pytest.mark.gpu
@@ -28,7 +28,7 @@ def city():
     P = O.Params(lod_enable=True, lod_d0=1600.0, lod_Lmax=5, cull_enable=True)
     cap = dict(max_gaussians=g.n, max_records=400_000, max_instances=8_000_000, max_tiles=B.tiles_of(cam),
                max_pixels=cam.pixels, max_cameras=1)
-    run = GpuRun(g, [cam], P, cull=cull, cap=cap)
+    run = ViewRun(g, [cam], P, cull=cull, cap=cap)
     g64 = O.gaussians64(g)
     fwd = oracle_view_matched(O, run, 0, g64, cam, P, cull)
     return dict(g=g, cam=cam, cull=cull, P=P, run=run, g64=g64, fwd=fwd)

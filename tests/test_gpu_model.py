@@ -9,7 +9,7 @@ import oracle as O
 from paper_2605_13794_gb300 import binding as B
 from paper_2605_13794_gb300 import model as M
 from paper_2605_13794_gb300 import synth
-from tests.gpu_helpers import GpuRun, assert_grad_close, capacity_for, gpu_params
+from tests.gpu_helpers import ViewRun, assert_grad_close, capacity_for, gpu_params
 
 pytestmark = pytest.mark.gpu
 

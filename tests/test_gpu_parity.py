@@ -18,7 +18,7 @@ import torch
 import oracle as O
 from paper_2605_13794_gb300 import binding as B
 from paper_2605_13794_gb300 import synth
-from tests.gpu_helpers import (GpuRun, assert_grad_close, assert_gaussian_grads_close, assert_param_grad_close, assert_record_precision,
+from tests.gpu_helpers import (ViewRun, assert_grad_close, assert_gaussian_grads_close, assert_param_grad_close, assert_record_precision,
                                capacity_for, footprint_power_err, gpu_params, grads_to_host, oracle_view_matched,
                                unpack_rect)
 
@@ -33,7 +33,7 @@ def _built():
     assert torch.cuda.is_available()
 
 
-def _compare_view(run: GpuRun, c, g64, cam, P, cull=None, check_image=True):
+def _compare_view(run: ViewRun, c, g64, cam, P, cull=None, check_image=True):
     """Compares one camera of a GPU run with the oracle; returns the oracle forward.
 
     Projection decisions (active set, rectangles, tile counts, depth keys) are
@@ -91,7 +91,7 @@ def test_plain_view_forward_parity():
     g = synth.plain_scene()
     cam = synth.plain_camera()
     P = O.Params()
-    run = GpuRun(g, [cam], P)
+    run = ViewRun(g, [cam], P)
     assert run.counts["n_records"] == run.counts["records_needed"]
     _compare_view(run, 0, O.gaussians64(g), cam, P)
 
@@ -102,7 +102,7 @@ def test_ragged_image_and_background(bg):
     g = synth.plain_scene(6000, seed=7)
     cam = synth.plain_camera(250, 170, 260.0)
     P = O.Params(bg=bg)
-    run = GpuRun(g, [cam], P)
+    run = ViewRun(g, [cam], P)
     _compare_view(run, 0, O.gaussians64(g), cam, P)
 
 
@@ -111,7 +111,7 @@ def test_multi_camera_forward_parity():
     cams = [synth.plain_camera(256, 256, 300.0), synth.plain_camera(200, 120, 180.0),
             synth.look_at_camera((0.6, -0.4, -0.5), (0.0, 0.0, 4.0), (0.0, -1.0, 0.0), 160, 144, 60.0)]
     P = O.Params()
-    run = GpuRun(g, cams, P)
+    run = ViewRun(g, cams, P)
     g64 = O.gaussians64(g)
     for c, cam in enumerate(cams):
         _compare_view(run, c, g64, cam, P)
@@ -125,7 +125,7 @@ def test_lod_gate_and_cull_mask_parity():
     cull = synth.random_cull_bits(g.n, 0.3, seed=14)
     # d0 so that distances 2..6 fall across levels 1..3
     P = O.Params(lod_enable=True, lod_d0=16.0, lod_Lmax=4, cull_enable=True)
-    run = GpuRun(g, [cam], P, cull=cull)
+    run = ViewRun(g, [cam], P, cull=cull)
     fwd = _compare_view(run, 0, O.gaussians64(g), cam, P, cull=cull)
     st = fwd["proj"]["status"]
     assert (st == O.GATED_LOD).sum() > 1000 and (st == O.GATED_CULL).sum() > 1000
@@ -195,7 +195,7 @@ def test_cull_mark_equals_drop_for_training_and_off_for_importance():
         views = torch.zeros(n, device="cuda", dtype=torch.int32)
         ws.count_views(views)
         out.update(grads=grads_to_host(grads), absg=absg.cpu().numpy(), reg=reg.item(), views=views.cpu().numpy())
-        out["imp"] = _importance(GpuRunLike(ws), n, len(cams))
+        out["imp"] = _importance(ViewRunLike(ws), n, len(cams))
         return out
 
     drop, mark, off = run(B.GS_CULL_DROP), run(B.GS_CULL_MARK), run(B.GS_CULL_OFF)
@@ -248,7 +248,7 @@ def test_fused_forward_importance_matches_separate(mode):
         nc = ws.read_buffer(B.GS_BUF_N_CONTRIB, np.uint32, npix)
         grads = gt.zeros_like()
         ws.render_bwd(gt, dL, grads, accumulate=False)
-        imp = _importance(GpuRunLike(ws), n, len(cams))
+        imp = _importance(ViewRunLike(ws), n, len(cams))
         return rgb.cpu().numpy(), T.cpu().numpy(), nc, grads_to_host(grads), imp
 
     sep, fus = run(False), run(True)
@@ -349,8 +349,8 @@ def test_importance_on_a_second_stream_matches_one_stream():
             assert np.array_equal(one[k], other[k]), (mode, k)
 
 
-class GpuRunLike:
-    """The one attribute _importance needs from a GpuRun."""
+class ViewRunLike:
+    """The one attribute _importance needs from a ViewRun."""
 
     def __init__(self, ws):
         self.ws = ws
@@ -361,11 +361,11 @@ def test_empty_and_fully_gated_scenes():
     P = O.Params()
     g = synth.plain_scene(500, seed=15)
     g.mean[:, 2] = -1.0  # all behind the camera
-    run = GpuRun(g, [cam], P)
+    run = ViewRun(g, [cam], P)
     assert run.counts["n_records"] == 0 and run.counts["n_instances"] == 0
     assert np.allclose(run.image(0), 0.0) and np.allclose(run.T_final(0), 1.0)
     g0 = synth.plain_scene(0, seed=16)
-    run0 = GpuRun(g0, [cam], P, cap=capacity_for(1, [cam]))
+    run0 = ViewRun(g0, [cam], P, cap=capacity_for(1, [cam]))
     assert run0.counts["n_records"] == 0 and np.allclose(run0.T_final(0), 1.0)
 
 
@@ -375,11 +375,11 @@ def test_capacity_overflow_is_reported():
     P = O.Params()
     cap = capacity_for(g.n, [cam], instances=2000)
     with pytest.raises(B.GSError) as ei:
-        GpuRun(g, [cam], P, cap=cap)
+        ViewRun(g, [cam], P, cap=cap)
     assert ei.value.code == B.GS_ERR_CAPACITY
 
 
-def _backward(run: GpuRun, dL):
+def _backward(run: ViewRun, dL):
     grads = run.gt.zeros_like()
     dLt = torch.from_numpy(np.ascontiguousarray(dL, np.float32).ravel()).cuda()
     run.ws.render_bwd(run.gt, dLt, grads, accumulate=False)
@@ -392,7 +392,7 @@ def test_backward_parity(seed):
     g = synth.plain_scene(3000, seed=seed)
     cam = synth.plain_camera(128, 112, 160.0)
     P = O.Params()
-    run = GpuRun(g, [cam], P)
+    run = ViewRun(g, [cam], P)
     g64 = O.gaussians64(g)
     fwd = _compare_view(run, 0, g64, cam, P)
     dL = np.random.default_rng(seed + 100).standard_normal((3, cam.height, cam.width))
@@ -409,7 +409,7 @@ def test_backward_fragment_counts_and_kernel_timing():
     g = synth.plain_scene(3000, seed=25)
     cam = synth.plain_camera(144, 104, 160.0)
     P = O.Params()
-    run = GpuRun(g, [cam], P)
+    run = ViewRun(g, [cam], P)
     fwd = O.forward_view(O.gaussians64(g), cam, P)
     dL = np.random.default_rng(26).standard_normal((3, cam.height, cam.width))
     assert run.ws.kernel_time(B.GS_KT_RENDER_BWD) == (0.0, 0)
@@ -444,7 +444,7 @@ def test_backward_multi_camera_accumulates():
     g = synth.plain_scene(3000, seed=23)
     cams = [synth.plain_camera(128, 128, 160.0), synth.plain_camera(96, 80, 120.0)]
     P = O.Params(bg=(0.1, 0.2, 0.3))
-    run = GpuRun(g, cams, P)
+    run = ViewRun(g, cams, P)
     g64 = O.gaussians64(g)
     rng = np.random.default_rng(24)
     dLs = [rng.standard_normal((3, c.height, c.width)) for c in cams]
@@ -464,7 +464,7 @@ def test_deterministic_reruns():
     dL = np.random.default_rng(26).standard_normal((3, cam.height, cam.width))
     outs = []
     for _ in range(2):
-        run = GpuRun(g, [cam], P)
+        run = ViewRun(g, [cam], P)
         gg = _backward(run, dL)
         outs.append((run.image(0), gg))
     assert np.array_equal(outs[0][0], outs[1][0])
@@ -472,7 +472,7 @@ def test_deterministic_reruns():
         assert np.array_equal(outs[0][1][k], outs[1][1][k]), k
 
 
-def _importance(run: GpuRun, n, ncam):
+def _importance(run: ViewRun, n, ncam):
     dev = "cuda"
     w = torch.zeros(ncam * n, device=dev)
     a = torch.zeros(ncam * n, device=dev, dtype=torch.int32)
@@ -525,7 +525,7 @@ def test_importance_parity():
     g = synth.plain_scene(6000, seed=31)
     cams = [synth.plain_camera(), synth.plain_camera(160, 200, 200.0)]
     P = O.Params()
-    run = GpuRun(g, cams, P)
+    run = ViewRun(g, cams, P)
     g64 = O.gaussians64(g)
     imp = _importance(run, g.n, len(cams))
     acc = O.new_importance(g.n)
@@ -598,7 +598,7 @@ def test_scale_regulariser_parity():
     g = synth.plain_scene(2000, seed=43)
     cam = synth.plain_camera()
     P = O.Params()
-    run = GpuRun(g, [cam], P)
+    run = ViewRun(g, [cam], P)
     grads = run.gt.zeros_like()
     val = torch.zeros(1, device="cuda")
     zero = torch.zeros(3 * cam.pixels, device="cuda")
@@ -617,7 +617,7 @@ def test_fused_backward_adam_matches_unfused():
     g = synth.plain_scene(4000, seed=44)
     cam = synth.plain_camera(160, 144, 200.0)
     P = O.Params()
-    run = GpuRun(g, [cam], P)
+    run = ViewRun(g, [cam], P)
     rng = np.random.default_rng(45)
     dL = torch.from_numpy(rng.standard_normal(3 * cam.pixels).astype(np.float32)).cuda()
     lr = [1e-2, 5e-3, 1e-3, 5e-2, 2.5e-3]
