@@ -394,7 +394,9 @@ def bwd_roofline(fragments, composited, instances, pixels, kernel_ms, sm_mhz, pe
 #     and 36 B of summed gradient written
 #   projection adjoint: per visible Gaussian 44 B of shape and opacity read and
 #     its 236 B gradient row written; per record 64 B (ids, record, gradient)
-#   SSIM statistics / gradient: per pixel and channel 24 B / 28 B
+#   SSIM statistics / gradient: per pixel and channel 20 B (image and target
+#     read, three coefficient maps written) / 24 B (maps, image and target
+#     read, the gradient written)
 #   deferred Adam's step: per visible Gaussian 59 parameters x 24 B (p, m, v
 #     read and written) and its 236 B gradient row
 HBM_KERNELS = {
@@ -403,8 +405,8 @@ HBM_KERNELS = {
     "emit_tile_sort": ("GS_KT_TILE_SORT", lambda c: (16 * c["tile_passes"] + 8) * c["n_instances"] + 16 * c["n_records"]),
     "reduce_slots_kernel": ("GS_KT_REDUCE_SLOTS", lambda c: 36 * c["n_instances"] + 52 * c["n_records"]),
     "preprocess_bwd_kernel": ("GS_KT_PREPROCESS_BWD", lambda c: 280 * c["n_visible"] + 64 * c["n_records"]),
-    "ssim_fwd_kernel": ("GS_KT_SSIM_FWD", lambda c: 24 * 3 * c["pixels"]),
-    "ssim_bwd_kernel": ("GS_KT_SSIM_BWD", lambda c: 28 * 3 * c["pixels"]),
+    "ssim_fwd_kernel": ("GS_KT_SSIM_FWD", lambda c: 20 * 3 * c["pixels"]),
+    "ssim_bwd_kernel": ("GS_KT_SSIM_BWD", lambda c: 24 * 3 * c["pixels"]),
     "lazy_list_vec_kernel (gradient step)": ("GS_KT_ADAM_GRAD", lambda c: (59 * 24 + 236) * c["n_visible"]),
 }
 
