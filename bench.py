@@ -392,8 +392,9 @@ def bwd_roofline(fragments, composited, instances, pixels, kernel_ms, sm_mhz, pe
 #     rectangle, camera)
 #   slot reduction: per instance 36 B (its slot); per record 16 B of indices
 #     and 36 B of summed gradient written
-#   projection adjoint: per visible Gaussian 44 B of shape and opacity read and
-#     its 236 B gradient row written; per record 64 B (ids, record, gradient)
+#   projection adjoint: per visible Gaussian 44 B of shape and opacity and
+#     192 B of SH read and its 236 B gradient row written; per record 64 B
+#     (ids, record, gradient)
 #   SSIM statistics / gradient: per pixel and channel 20 B (image and target
 #     read, three coefficient maps written) / 24 B (maps, image and target
 #     read, the gradient written)
@@ -404,7 +405,7 @@ HBM_KERNELS = {
     "depth_sort": ("GS_KT_DEPTH_SORT", lambda c: 16 * c["depth_passes"] * c["n_records"]),
     "emit_tile_sort": ("GS_KT_TILE_SORT", lambda c: (16 * c["tile_passes"] + 8) * c["n_instances"] + 16 * c["n_records"]),
     "reduce_slots_kernel": ("GS_KT_REDUCE_SLOTS", lambda c: 36 * c["n_instances"] + 52 * c["n_records"]),
-    "preprocess_bwd_kernel": ("GS_KT_PREPROCESS_BWD", lambda c: 280 * c["n_visible"] + 64 * c["n_records"]),
+    "preprocess_bwd_kernel": ("GS_KT_PREPROCESS_BWD", lambda c: 472 * c["n_visible"] + 64 * c["n_records"]),
     "ssim_fwd_kernel": ("GS_KT_SSIM_FWD", lambda c: 20 * 3 * c["pixels"]),
     "ssim_bwd_kernel": ("GS_KT_SSIM_BWD", lambda c: 24 * 3 * c["pixels"]),
     "lazy_list_vec_kernel (gradient step)": ("GS_KT_ADAM_GRAD", lambda c: (59 * 24 + 236) * c["n_visible"]),
