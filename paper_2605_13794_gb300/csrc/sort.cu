@@ -329,26 +329,29 @@ struct EmitArgs {
     int passes;      // digits of the tile keys
 };
 
-__global__ void __launch_bounds__(256) emit_kernel(EmitArgs a, const CamTable *__restrict__ ctp)
+// Blocks of kEmitThreads records (small blocks spread the records over the
+// SMs evenly: 94k records make 737 blocks, about five per SM).
+constexpr int kEmitThreads = 128;
+__global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a, const CamTable *__restrict__ ctp)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const CamTable &ct = *ctp;
     __shared__ unsigned s_bid;
-    __shared__ unsigned long long s_warp[8];
+    __shared__ unsigned long long s_warp[kEmitThreads / 32];
     __shared__ unsigned long long s_base;
-    __shared__ unsigned long long s_incl[256];
-    __shared__ uint32_t s_rec[256];
-    __shared__ uint2 s_rect[256];
-    __shared__ int s_tb[256], s_tx[256];
+    __shared__ unsigned long long s_incl[kEmitThreads];
+    __shared__ uint32_t s_rec[kEmitThreads];
+    __shared__ uint2 s_rect[kEmitThreads];
+    __shared__ int s_tb[kEmitThreads], s_tx[kEmitThreads];
     __shared__ uint32_t s_hist[4][256];
     if (threadIdx.x == 0) s_bid = atomicAdd((unsigned *)a.lb_status, 1u);
     if (a.hist)
-        for (int q = threadIdx.x; q < 4 * 256; q += 256) (&s_hist[0][0])[q] = 0u;
+        for (int q = threadIdx.x; q < 4 * 256; q += kEmitThreads) (&s_hist[0][0])[q] = 0u;
     __syncthreads();
     const unsigned bid = s_bid;
     const unsigned long long nrec = a.ctr->n_records;
-    const unsigned long long k = (unsigned long long)bid * 256 + threadIdx.x;
-    if ((unsigned long long)bid * 256 >= nrec) return;
+    const unsigned long long k = (unsigned long long)bid * kEmitThreads + threadIdx.x;
+    if ((unsigned long long)bid * kEmitThreads >= nrec) return;
     const bool valid = k < nrec;
     uint32_t r = 0;
     unsigned long long c = 0;
@@ -362,7 +365,7 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitArgs a, const CamTable *_
     }
     s_rec[threadIdx.x] = r;
     unsigned long long total;
-    const unsigned long long excl = block_exclusive_scan_256<unsigned long long>(c, s_warp, total);
+    const unsigned long long excl = block_exclusive_scan<kEmitThreads / 32, unsigned long long>(c, s_warp, total);
     s_incl[threadIdx.x] = excl + c;
     if (threadIdx.x < 32) {
         unsigned long long b = lookback_exclusive(a.lb_status + 1, bid, total, a.ctr, kSiteEmit);
@@ -378,11 +381,11 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitArgs a, const CamTable *_
         if (end > a.max_instances) set_error(a.ctr, GS_ERR_CAPACITY, kSiteEmit);
     }
     // cooperative, coalesced emission of the block's instances
-    for (unsigned long long j = threadIdx.x; j < total; j += 256) {
+    for (unsigned long long j = threadIdx.x; j < total; j += kEmitThreads) {
         const unsigned long long gi = base + j;
         if (gi >= a.max_instances) break;
         // record kk: first with inclusive prefix > j
-        int lo = 0, hi = 255;
+        int lo = 0, hi = kEmitThreads - 1;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
             if (s_incl[mid] > j) hi = mid; else lo = mid + 1;
@@ -401,7 +404,7 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitArgs a, const CamTable *_
     }
     if (a.hist) {
         __syncthreads();
-        for (int q = threadIdx.x; q < a.passes * 256; q += 256) {
+        for (int q = threadIdx.x; q < a.passes * 256; q += kEmitThreads) {
             const uint32_t v = (&s_hist[0][0])[q];
             if (v) atomicAdd(&a.hist[q], v);
         }
@@ -413,7 +416,7 @@ __global__ void __launch_bounds__(256) emit_kernel(EmitArgs a, const CamTable *_
 cudaError_t launch_emit(gs_workspace *ws, cudaStream_t st, uint32_t *hist, int passes)
 {
     const unsigned long long cap = (unsigned long long)ws->cap.max_records;
-    const unsigned blocks = (unsigned)((cap + 255) / 256);
+    const unsigned blocks = (unsigned)((cap + kEmitThreads - 1) / kEmitThreads);
     cudaError_t e;
     if ((e = cudaMemsetAsync(ws->lb_status, 0, (blocks + 1) * sizeof(unsigned long long), st)) != cudaSuccess)
         return e;
@@ -423,7 +426,7 @@ cudaError_t launch_emit(gs_workspace *ws, cudaStream_t st, uint32_t *hist, int p
     a.tkey = ws->tkey[0]; a.tval = ws->tval[0];
     a.lb_status = ws->lb_status; a.ctr = ws->ctr; a.max_instances = (unsigned long long)ws->cap.max_instances;
     a.hist = hist; a.passes = passes;
-    launch_pdl(emit_kernel, blocks, 256, 0, st, a, ws->d_cams);
+    launch_pdl(emit_kernel, blocks, kEmitThreads, 0, st, a, ws->d_cams);
     note_launch();
     return cudaGetLastError();
 }
