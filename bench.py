@@ -385,11 +385,12 @@ def bwd_roofline(fragments, composited, instances, pixels, kernel_ms, sm_mhz, pe
 #   view gate: per Gaussian its mean 12 B, level 1 B and mean drift 4 B; per
 #     candidate its log-scales 12 B and their drift 4 B read, its id 4 B and
 #     camera mask 8 B written
-#   depth sort of the records: per record and pass 16 B (key and value read
-#     and written; the first pass reads no values) and 4 B of the histogram read
-#   emission and tile sort of the instances: per instance 8 B written (key,
-#     record), then per pass 16 B; per record 16 B read (order, count,
-#     rectangle, camera)
+#   binning, count pass: per record 18 B (tile count, rectangle, camera read,
+#     first instance written), per instance 4 B (its tile's count)
+#   binning, ranges, scatter and per-tile sort: per tile 20 B (count read,
+#     range and cursor written), per record 18 B (read again), per instance
+#     28 B (cursor, depth key read; key and record written; both read and the
+#     record written by the per-tile sort)
 #   slot reduction: per instance 36 B (its slot); per record 16 B of indices
 #     and 36 B of summed gradient written
 #   projection adjoint: per visible Gaussian 44 B of shape and opacity and
@@ -402,8 +403,8 @@ def bwd_roofline(fragments, composited, instances, pixels, kernel_ms, sm_mhz, pe
 #     read and written) and its 236 B gradient row
 HBM_KERNELS = {
     "gate_count_kernel": ("GS_KT_GATE", lambda c: 17 * c["n"] + 28 * c["n_candidates"]),
-    "depth_sort": ("GS_KT_DEPTH_SORT", lambda c: 16 * c["depth_passes"] * c["n_records"]),
-    "emit_tile_sort": ("GS_KT_TILE_SORT", lambda c: (16 * c["tile_passes"] + 8) * c["n_instances"] + 16 * c["n_records"]),
+    "bin_count": ("GS_KT_BIN_COUNT", lambda c: 18 * c["n_records"] + 4 * c["n_instances"]),
+    "bin_sort": ("GS_KT_BIN_SORT", lambda c: 20 * c["tiles"] + 18 * c["n_records"] + 28 * c["n_instances"]),
     "reduce_slots_kernel": ("GS_KT_REDUCE_SLOTS", lambda c: 36 * c["n_instances"] + 52 * c["n_records"]),
     "preprocess_bwd_kernel": ("GS_KT_PREPROCESS_BWD", lambda c: 472 * c["n_visible"] + 64 * c["n_records"]),
     "ssim_fwd_kernel": ("GS_KT_SSIM_FWD", lambda c: 20 * 3 * c["pixels"]),
@@ -927,8 +928,7 @@ def main():
     roof_comp["importance_raster_kernel"]["composited_per_launch"] = imp_composited
     tw, th = (int(x) for x in args.tile.split("x"))
     tiles = ((cam.width + tw - 1) // tw) * ((cam.height + th - 1) // th)
-    roof_hbm = hbm_rooflines(kernel_ms, dict(counts, n=g.n, pixels=P, depth_passes=4,
-                                             tile_passes=(max(1, (tiles - 1).bit_length()) + 7) // 8), peaks)
+    roof_hbm = hbm_rooflines(kernel_ms, dict(counts, n=g.n, pixels=P, tiles=tiles), peaks)
     latency = render_latency(step, g, B, torch)
     serving = serving_short(step, torch) if not args.no_serving else None
     train8 = train8_figures(torch) if not args.no_train8 else None

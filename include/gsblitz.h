@@ -198,7 +198,7 @@ typedef enum {
     GS_BUF_REC_CAMERA = 1,   /* uint16 [max_records]: camera of each record */
     GS_BUF_REC_RECT = 2,     /* uint32 [max_records][2]: x0|y0<<16, x1|y1<<16 (tiles) */
     GS_BUF_REC_TILES = 3,    /* uint32 [max_records]: tiles touched */
-    GS_BUF_REC_DEPTH = 4,    /* uint32 [max_records]: FP32 bits of camera z (valid until gs_bin_sort) */
+    GS_BUF_REC_DEPTH = 4,    /* uint32 [max_records]: FP32 bits of camera z */
     GS_BUF_REC_XY_CONIC = 5, /* float4 [max_records]: u, v (the floats nearest the projected mean), A, k */
     GS_BUF_REC_C_OPAC_RG = 6,/* float4 [max_records]: D, opacity, r, g */
     GS_BUF_REC_B_LO = 7,     /* float4 [max_records]: b, u_lo, v_lo, 0; the mean is u + u_lo, v + v_lo.
@@ -502,8 +502,8 @@ enum {
     GS_KT_IMPORTANCE = 2,      /* the importance sweep's rasteriser */
     GS_KT_GATE = 3,            /* the view gate's pass over every Gaussian (gs_preprocess) */
     GS_KT_PROJECT = 4,         /* the projection of the gate's candidates (gs_preprocess) */
-    GS_KT_DEPTH_SORT = 5,      /* gs_bin_sort's depth sort of the records, all of its kernels */
-    GS_KT_TILE_SORT = 6,       /* gs_bin_sort: emission of the instances and their sort by tile */
+    GS_KT_BIN_COUNT = 5,       /* gs_bin_sort: each record's first instance and the tile counts */
+    GS_KT_BIN_SORT = 6,        /* gs_bin_sort: tile ranges, scatter by tile and the per-tile depth sort */
     GS_KT_REDUCE_SLOTS = 7,    /* the per-record sum of the adjoint's gradient slots */
     GS_KT_PREPROCESS_BWD = 8,  /* the projection adjoint (per Gaussian) */
     GS_KT_SSIM_FWD = 9,        /* gs_photometric_loss: the SSIM statistics and coefficient maps */

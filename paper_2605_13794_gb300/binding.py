@@ -40,7 +40,7 @@ EXPORTS = ("gs_default_params", "gs_last_error", "gs_workspace_create", "gs_work
 GS_CULL_OFF, GS_CULL_DROP, GS_CULL_MARK = 0, 1, 2
 
 # kernels gs_kernel_timing brackets with events (include/gsblitz.h)
-(GS_KT_RENDER_FWD, GS_KT_RENDER_BWD, GS_KT_IMPORTANCE, GS_KT_GATE, GS_KT_PROJECT, GS_KT_DEPTH_SORT, GS_KT_TILE_SORT,
+(GS_KT_RENDER_FWD, GS_KT_RENDER_BWD, GS_KT_IMPORTANCE, GS_KT_GATE, GS_KT_PROJECT, GS_KT_BIN_COUNT, GS_KT_BIN_SORT,
  GS_KT_REDUCE_SLOTS, GS_KT_PREPROCESS_BWD, GS_KT_SSIM_FWD, GS_KT_SSIM_BWD, GS_KT_ADAM_GRAD) = range(12)
 GS_KT_COUNT = 12
 GS_KT_ALL = (1 << GS_KT_COUNT) - 1

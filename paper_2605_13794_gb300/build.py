@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgsblitz.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "preprocess.cu", "sort.cu", "render.cu", "select.cu", "optim.cu", "noalloc.cu", "model.cu",
+SOURCES = ["api.cu", "preprocess.cu", "sort.cu", "bin.cu", "render.cu", "select.cu", "optim.cu", "noalloc.cu", "model.cu",
            "peak.cu"]
 
 

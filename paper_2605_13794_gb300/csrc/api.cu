@@ -46,7 +46,7 @@ struct Layout {
 };
 
 struct Offsets {
-    size_t cand_g, cand_mask, gate_g, gate_mask, rec_first, cgrad, rec_g, rec_cam, rd0, rd1, rd2, rect, tt, inst_off, clampm, rgrad, dkey0, dkey1, dval0, dval1;
+    size_t cand_g, cand_mask, gate_g, gate_mask, rec_first, cgrad, rec_g, rec_cam, rd0, rd1, rd2, rect, tt, inst_off, clampm, rgrad, dkey, tile_cnt, tile_cur;
     size_t tkey0, tkey1, tval0, tval1, slots, imp_slots, ranges, n_contrib, T_final, imp_w, imp_a, sel_cum, sel_bsum;
     size_t selk0, selk1, selv0, selv1, loss_maps, loss_partial, lb_status, rx_status, red_partial,
         ctr, d_cams, d_adam_step, d_adam_coef;
@@ -78,10 +78,7 @@ Offsets plan(const gs_capacity &c)
     o.inst_off = L.take<uint32_t>(R);
     o.clampm = L.take<uint8_t>(R);
     o.rgrad = L.take<float>(fwd_only ? 0 : R * gs::kSlotFloats);
-    o.dkey0 = L.take<uint32_t>(R);
-    o.dkey1 = L.take<uint32_t>(R);
-    o.dval0 = L.take<uint32_t>(R);
-    o.dval1 = L.take<uint32_t>(R);
+    o.dkey = L.take<uint32_t>(R);
     o.tkey0 = L.take<uint32_t>(I);
     o.tkey1 = L.take<uint32_t>(I);
     o.tval0 = L.take<uint32_t>(I);
@@ -89,6 +86,8 @@ Offsets plan(const gs_capacity &c)
     o.slots = L.take<float>(fwd_only ? 0 : I * gs::kSlotFloats);
     o.imp_slots = L.take<float2>(I); // importance (w, a) per instance
     o.ranges = L.take<uint2>(T);
+    o.tile_cnt = L.take<uint32_t>(T);
+    o.tile_cur = L.take<uint32_t>(T);
     o.n_contrib = L.take<uint32_t>(P);
     o.T_final = L.take<float>(P);
     o.imp_w = L.take<float>(R);
@@ -103,9 +102,10 @@ Offsets plan(const gs_capacity &c)
     o.loss_partial_words = fwd_only ? 0 : 2 * 3 * (P / 1024 + 65536);
     o.loss_partial = L.take<float>(o.loss_partial_words);
     // look-back words: one per chunk of the smallest chunked pass (the
-    // projection's 64 candidates) plus the ticket
+    // projection's candidates) plus the ticket, and the binning's two regions
+    // (records of its count pass, tiles of its tile scan)
     const size_t nb = (N > R ? N : R) / 64 + 2;
-    o.lb_words = nb + 1;
+    o.lb_words = nb + 1 + T / 1024 + 4;
     o.lb_status = L.take<unsigned long long>(o.lb_words);
     const size_t items = (R > I ? R : I);
     // the histograms, then the look-back state of up to four passes, for the
@@ -277,8 +277,9 @@ int gs_workspace_create(const gs_capacity *cap, gs_workspace **out)
     ws->inst_off = (uint32_t *)(b + o.inst_off);
     ws->clampm = (uint8_t *)(b + o.clampm);
     ws->rgrad = (float *)(b + o.rgrad);
-    ws->dkey[0] = (uint32_t *)(b + o.dkey0); ws->dkey[1] = (uint32_t *)(b + o.dkey1);
-    ws->dval[0] = (uint32_t *)(b + o.dval0); ws->dval[1] = (uint32_t *)(b + o.dval1);
+    ws->dkey = (uint32_t *)(b + o.dkey);
+    ws->tile_cnt = (uint32_t *)(b + o.tile_cnt);
+    ws->tile_cur = (uint32_t *)(b + o.tile_cur);
     ws->tkey[0] = (uint32_t *)(b + o.tkey0); ws->tkey[1] = (uint32_t *)(b + o.tkey1);
     ws->tval[0] = (uint32_t *)(b + o.tval0); ws->tval[1] = (uint32_t *)(b + o.tval1);
     ws->slots = (float *)(b + o.slots);
@@ -544,33 +545,12 @@ int gs_bin_sort(gs_workspace *ws, gs_stream stream)
     if (!ws) return fail(GS_ERR_INVALID_ARG, "gs_bin_sort: NULL workspace");
     if (!ws->have_preprocess) return fail(GS_ERR_INVALID_ARG, "gs_bin_sort: no preprocess on this workspace");
     cudaStream_t st = (cudaStream_t)stream;
-    // 1. depth order of the records
-    int ob = 0;
-    // (the projection filled the depth keys' histograms, once per preprocess)
-    gs::kt_begin(ws, GS_KT_DEPTH_SORT, st);
-    CK(gs::launch_radix_sort(ws, st, ws->dkey, ws->dval, &ws->ctr->n_records, (unsigned long long)ws->cap.max_records,
-                             32, true, ws->depth_hist_ready != 0, ob),
-       "gs_bin_sort(depth)");
-    gs::kt_end(ws, GS_KT_DEPTH_SORT, st);
-    ws->depth_hist_ready = 0;
-    ws->depth_buf = ob;
-    // 2. emission of (tile, record) instances in depth order, with the
-    // histograms of their tile keys
-    int bits = 0;
-    while ((1ll << bits) < (long long)ws->cams.total_tiles) bits++;
+    // the instance counters, then tile counts, ranges, scatter and the
+    // per-tile depth sort (the final order: camera, tile, depth bits, record)
     CK(cudaMemsetAsync(&ws->ctr->n_instances, 0, sizeof(unsigned long long), st), "gs_bin_sort");
     CK(cudaMemsetAsync(&ws->ctr->instances_needed, 0, sizeof(unsigned long long), st), "gs_bin_sort");
-    gs::kt_begin(ws, GS_KT_TILE_SORT, st);
-    CK(gs::launch_radix_clear(ws, st, (unsigned long long)ws->cap.max_instances, bits), "gs_bin_sort(tiles)");
-    CK(gs::launch_emit(ws, st, ws->rx_status, bits <= 0 ? 1 : (bits + 7) / 8), "gs_bin_sort(emit)");
-    // 3. stable sort by global tile id
-    CK(gs::launch_radix_sort(ws, st, ws->tkey, ws->tval, &ws->ctr->n_instances,
-                             (unsigned long long)ws->cap.max_instances, bits, false, true, ob),
-       "gs_bin_sort(tiles)");
-    gs::kt_end(ws, GS_KT_TILE_SORT, st);
-    ws->tile_buf = ob;
-    // 4. tile ranges
-    CK(gs::launch_ranges(ws, st), "gs_bin_sort(ranges)");
+    CK(gs::launch_bin(ws, st), "gs_bin_sort");
+    ws->tile_buf = 0;
     ws->have_binning = 1;
     ws->imp_ready = 0;
     return GS_OK;
@@ -951,7 +931,7 @@ int gs_workspace_buffer(gs_workspace *ws, int32_t which, void **ptr, int64_t *co
     case GS_BUF_REC_CAMERA: *ptr = ws->rec_cam; *count = c.max_records; break;
     case GS_BUF_REC_RECT: *ptr = ws->rect; *count = c.max_records; break;
     case GS_BUF_REC_TILES: *ptr = ws->tt; *count = c.max_records; break;
-    case GS_BUF_REC_DEPTH: *ptr = ws->dkey[0]; *count = c.max_records; break;
+    case GS_BUF_REC_DEPTH: *ptr = ws->dkey; *count = c.max_records; break;
     case GS_BUF_REC_XY_CONIC: *ptr = ws->rd0; *count = c.max_records; break;
     case GS_BUF_REC_C_OPAC_RG: *ptr = ws->rd1; *count = c.max_records; break;
     case GS_BUF_REC_B_LO: *ptr = ws->rd2; *count = c.max_records; break;

@@ -68,7 +68,7 @@ constexpr int kMaxLod = 15;             // largest supported L_max
 
 // Error sites recorded next to the error word (which kernel gave up).
 enum ErrorSite {
-    kSitePreprocess = 1, kSiteEmit = 2, kSiteRadix = 3, kSiteSelect = 4, kSiteScanF64 = 5, kSiteModel = 6,
+    kSitePreprocess = 1, kSiteEmit = 2 /* binning */, kSiteRadix = 3, kSiteSelect = 4, kSiteScanF64 = 5, kSiteModel = 6,
     kSiteRender = 7,
 };
 
@@ -337,7 +337,8 @@ struct gs_workspace {
     uint32_t *inst_off;
     uint8_t *clampm;
     float *rgrad;        // [R][9] per-record summed gradients of u v A B C o r g b
-    uint32_t *dkey[2], *dval[2];
+    uint32_t *dkey;      // [R] FP32 bits of each record's camera depth
+    uint32_t *tile_cnt, *tile_cur; // [T] the binning's tile counts and fill cursors
     // per instance
     uint32_t *tkey[2], *tval[2];
     float *slots;        // [I][9] adjoint slots (training workspaces only)
@@ -363,7 +364,6 @@ struct gs_workspace {
     size_t lb_words;
     uint32_t *rx_status; // radix: [4][256] histograms, then per pass [blocks * 256 + 1] look-back + ticket
     size_t rx_words;
-    int depth_hist_ready; // the last preprocess filled the depth sort's histograms (rx_status)
     uint32_t *rx_hist;   // [4][256]: the first kRxHistWords words of rx_status (also a scratch of 1024 words)
     float *red_partial;  // [blocks] reduction partials of the adjoint (scale regulariser)
     size_t red_words;
@@ -409,8 +409,7 @@ struct gs_workspace {
     int have_binning;
     int have_compact;    // compact gradient rows of the current binning exist
     int imp_ready;       // the importance w, a of the current binning exist (gs_render_fwd_importance)
-    int depth_buf;       // buffer holding sorted depth order
-    int tile_buf;        // buffer holding sorted instances
+    int tile_buf;        // buffer holding sorted instances (0)
     // kernel timing (gs_kernel_timing): event pairs around the rasterisers' launches
     static constexpr int kTimedPairs = 64;
     struct {
@@ -437,12 +436,8 @@ cudaError_t launch_render_fwd_importance(gs_workspace *ws, cudaStream_t st, floa
 cudaError_t launch_importance_reduce(gs_workspace *ws, cudaStream_t st);
 cudaError_t launch_radix_sort(gs_workspace *ws, cudaStream_t st, uint32_t *keys[2], uint32_t *vals[2],
                               const unsigned long long *count, unsigned long long cap, int bits, bool vals_identity,
-                              bool hist_ready, int &out_buf, unsigned long long spin_limit = kSpinLimit);
-// Clears the histograms and look-back state of a launch_radix_sort of up to cap
-// keys of `bits` bits (for a producer that fills the histograms itself).
-cudaError_t launch_radix_clear(gs_workspace *ws, cudaStream_t st, unsigned long long cap, int bits);
-cudaError_t launch_emit(gs_workspace *ws, cudaStream_t st, uint32_t *hist, int passes);
-cudaError_t launch_ranges(gs_workspace *ws, cudaStream_t st);
+                              int &out_buf, unsigned long long spin_limit = kSpinLimit);
+cudaError_t launch_bin(gs_workspace *ws, cudaStream_t st);
 cudaError_t launch_render_fwd(gs_workspace *ws, cudaStream_t st, float *rgb, float *T_out);
 cudaError_t launch_render_bwd(gs_workspace *ws, cudaStream_t st, const float *dL_drgb);
 cudaError_t launch_reduce_slots(gs_workspace *ws, cudaStream_t st);

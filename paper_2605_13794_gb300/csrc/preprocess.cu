@@ -354,7 +354,6 @@ struct PreOut {
     long long max_records;
     const uint32_t *cull;
     long long cull_words;
-    uint32_t *dhist;               // [4][256] byte histograms of the depth keys written (cleared), or NULL
 };
 
 struct GaussLoad {
@@ -810,33 +809,20 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(GaussPtrs g, PreO
     __shared__ unsigned s_bid;
     __shared__ unsigned long long s_warp[kNW];
     __shared__ unsigned long long s_base;
-    __shared__ uint32_t s_dh[4][256]; // the block's share of the depth keys' histograms
     const unsigned long long ncand = o.ctr->n_candidates;
     const int tw = ct.tile_w, th = ct.tile_h;
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int l = 0; l <= kMaxLod; l++) s_thr2[l] = rc.lod_thr2[l];
     }
-    for (int q = threadIdx.x; q < 4 * 256; q += kProjThreads) (&s_dh[0][0])[q] = 0u;
-    stage_cameras(ct, s_cams); // ends with a block barrier
-    auto count_key = [&](uint32_t key) {
-#pragma unroll
-        for (int p = 0; p < 4; p++) atomicAdd(&s_dh[p][(key >> (8 * p)) & 255u], 1u);
-    };
+    stage_cameras(ct, s_cams);
     // persistent blocks: each takes the next chunk of candidates (tickets in
     // order, so every look-back waits only on chunks already being processed)
     for (;;) {
     if (threadIdx.x == 0) s_bid = atomicAdd((unsigned *)o.lb_status, 1u);
     __syncthreads();
     const unsigned bid = s_bid;
-    if ((unsigned long long)bid * kProjThreads >= ncand) { // no chunk left: the histograms out
-        if (o.dhist)
-            for (int q = threadIdx.x; q < 4 * 256; q += kProjThreads) {
-                const uint32_t v = (&s_dh[0][0])[q];
-                if (v) atomicAdd(&o.dhist[q], v);
-            }
-        return;
-    }
+    if ((unsigned long long)bid * kProjThreads >= ncand) return;
     const unsigned long long j = (unsigned long long)bid * kProjThreads + threadIdx.x;
     GaussLoad L;
     L.have_shape = false;
@@ -897,10 +883,7 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(GaussPtrs g, PreO
         if (base < (unsigned long long)o.max_records) o.rec_first[i] = (uint32_t)base;
         if (kOneCam) {
             if (base >= (unsigned long long)o.max_records) set_error(o.ctr, GS_ERR_CAPACITY, kSitePreprocess);
-            else {
-                store_record(o, base, i, 0, one);
-                count_key(one.dkey);
-            }
+            else store_record(o, base, i, 0, one);
         } else {
             unsigned long long r = base;
             for (unsigned long long mm = act; mm; mm &= mm - 1, r++) {
@@ -914,9 +897,7 @@ __global__ void __launch_bounds__(kProjThreads) project_kernel(GaussPtrs g, PreO
                 camera_point_df(L.m, cam, td);
                 Proj p;
                 project_gaussian(L.ls, L.q, td, cam, tw, th, rc, p); // same inputs: same (passing) result
-                const RecOut q = make_record(g, i, L, op, cam, p, rc, (marked >> c) & 1ull);
-                store_record(o, r, i, c, q);
-                count_key(q.dkey);
+                store_record(o, r, i, c, make_record(g, i, L, op, cam, p, rc, (marked >> c) & 1ull));
             }
         }
     }
@@ -932,13 +913,12 @@ cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t 
     const unsigned gblocks = (unsigned)((n + kGateChunk - 1) / kGateChunk); // chunks
     const unsigned pchunks = (unsigned)((n + kProjThreads - 1) / kProjThreads); // projection chunks (at most)
     cudaError_t e;
-    ws->depth_hist_ready = 0; // until the projection below fills them
     // counters, then the look-back state of each stage (ticket in word 0)
     if ((e = cudaMemsetAsync(ws->ctr, 0, sizeof(DevCounters), st)) != cudaSuccess) return e;
     if (n == 0) return cudaSuccess;
     GaussPtrs gp{ws->g.mean, ws->g.log_scale, ws->g.quat, ws->g.opacity_logit, ws->g.sh, ws->g.lod, n};
     PreOut o;
-    o.rec_g = ws->rec_g; o.tt = ws->tt; o.dkey = ws->dkey[0];
+    o.rec_g = ws->rec_g; o.tt = ws->tt; o.dkey = ws->dkey;
     o.rec_cam = ws->rec_cam; o.rd0 = ws->rd0; o.rd1 = ws->rd1; o.rd2 = ws->rd2; o.rect = ws->rect;
     o.clampm = ws->clampm; o.cand_g = ws->cand_g; o.cand_mask = ws->cand_mask; o.rec_first = ws->rec_first;
     o.gate_g = ws->gate_g; o.gate_mask = ws->gate_mask;
@@ -947,7 +927,6 @@ cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t 
     o.ctr = ws->ctr; o.max_records = ws->cap.max_records;
     o.cull = ws->rc.cull_enable ? cull : nullptr;
     o.cull_words = (n + 31) / 32;
-    o.dhist = nullptr;
     if ((e = cudaMemsetAsync(ws->rec_first, 0xff, (size_t)n * sizeof(uint32_t), st)) != cudaSuccess) return e;
     // gate: per-block counts (in lb_status) and candidates (block-strided), the
     // scan of the counts, the gather into one ordered list
@@ -978,10 +957,6 @@ cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t 
         return e;
     // deferred Adam steps: bring the candidates up to date before projecting them
     if (ws->lazy.enabled && (e = launch_lazy_catchup(ws, st, ws->g)) != cudaSuccess) return e;
-    // the depth sort's scratch, whose histograms the projection fills
-    if ((e = launch_radix_clear(ws, st, (unsigned long long)ws->cap.max_records, 32)) != cudaSuccess) return e;
-    o.dhist = ws->cap.max_records > 0 ? ws->rx_status : nullptr;
-    ws->depth_hist_ready = o.dhist != nullptr;
     // projection: persistent blocks, about as many as stay resident (five per
     // SM at their registers), taking the candidates' chunks by ticket
     const unsigned pgrid = std::min<unsigned>(pchunks, 5u * (unsigned)ws->sm_count);
@@ -998,8 +973,9 @@ cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t 
 // ---- backward ---------------------------------------------------------------
 
 // Sum of the per-(record, tile) gradient slots of each record.  A warp takes
-// kReduceRecs consecutive records of the depth order (whose slots are
-// contiguous); each of its first lanes loads one record's indices.  Records of
+// kReduceRecs consecutive records (whose slots are contiguous: a record's
+// first instance follows record order); each of its first lanes loads one
+// record's indices.  Records of
 // at most kReduceBig tiles are added up by groups of kReduceLanes lanes, 32 /
 // kReduceLanes records at a time (a group's lanes read the record's slots
 // strided by kReduceLanes, then a fixed shuffle tree adds the lanes), so the
@@ -1012,7 +988,7 @@ constexpr int kReduceLanes = 8;
 constexpr int kReduceRecs = 2 * (32 / kReduceLanes); // records per warp: two rounds of the groups
 constexpr uint32_t kReduceBig = 4 * kReduceLanes;    // tiles above which a record takes the whole warp
 static_assert(kReduceLanes < kSlotFloats && kSlotFloats <= 2 * kReduceLanes, "a slot is written by one group");
-__global__ void __launch_bounds__(256) reduce_slots_kernel(const uint32_t *drec, const uint32_t *inst_off,
+__global__ void __launch_bounds__(256) reduce_slots_kernel(const uint32_t *inst_off,
                                                            const uint32_t *tt, const float4 *rd2, const float *slots,
                                                            float *rgrad, const DevCounters *ctr)
 {
@@ -1028,7 +1004,7 @@ __global__ void __launch_bounds__(256) reduce_slots_kernel(const uint32_t *drec,
         uint32_t r = 0, cnt = kSkip;
         unsigned long long off = 0;
         if (lane < kReduceRecs && k0 + lane < nrec) {
-            r = drec[k0 + lane];
+            r = (uint32_t)(k0 + lane);
             off = inst_off[r];
             cnt = tt[r];
             // capacity error already recorded, or marked: nothing to sum
@@ -1105,7 +1081,7 @@ cudaError_t launch_reduce_slots(gs_workspace *ws, cudaStream_t st)
     if (blocks > 16ll * ws->sm_count) blocks = 16ll * ws->sm_count;
     if (blocks < 1) blocks = 1;
     kt_begin(ws, GS_KT_REDUCE_SLOTS, st);
-    launch_pdl(reduce_slots_kernel, (unsigned)blocks, 256, 0, st, ws->dval[ws->depth_buf], ws->inst_off, ws->tt, ws->rd2, ws->slots,
+    launch_pdl(reduce_slots_kernel, (unsigned)blocks, 256, 0, st, ws->inst_off, ws->tt, ws->rd2, ws->slots,
                                                          ws->rgrad, ws->ctr);
     kt_end(ws, GS_KT_REDUCE_SLOTS, st);
     note_launch();

@@ -17,15 +17,15 @@ namespace gs {
 
 cudaError_t launch_importance_raster(gs_workspace *ws, cudaStream_t st);
 
-// w and a of each record.  A warp takes 8 consecutive records of the depth
-// order (whose slots are contiguous); records of at most 32 tiles are summed by
+// w and a of each record.  A warp takes 8 consecutive records (whose slots
+// are contiguous: a record's first instance follows record order); records of at most 32 tiles are summed by
 // groups of 8 lanes, 4 records at a time (lanes strided over the record's
 // slots, then a fixed shuffle tree over the group), larger ones by the whole
 // warp each (lanes strided by 32, a fixed tree over 32 lanes).  Which way a
 // record is summed depends only on its tile count: the same sums on every run.
 constexpr int kImpLanes = 8, kImpRecs = 8;
 constexpr uint32_t kImpBig = 4 * kImpLanes;
-__global__ void __launch_bounds__(256) imp_reduce_kernel(const uint32_t *drec, const uint32_t *inst_off,
+__global__ void __launch_bounds__(256) imp_reduce_kernel(const uint32_t *inst_off,
                                                          const uint32_t *tt, const float2 *slots, float *imp_w,
                                                          uint32_t *imp_a, const DevCounters *ctr)
 {
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256) imp_reduce_kernel(const uint32_t *drec, c
         uint32_t r = 0, cnt = kSkip;
         unsigned long long off = 0;
         if (lane < kImpRecs && k0 + lane < nrec) {
-            r = drec[k0 + lane];
+            r = (uint32_t)(k0 + lane);
             off = inst_off[r];
             cnt = tt[r];
             if (off + cnt > ninst) cnt = 0; // capacity error already recorded: zero sums
@@ -358,7 +358,7 @@ cudaError_t launch_importance_reduce(gs_workspace *ws, cudaStream_t st)
     const unsigned long long rcap = (unsigned long long)ws->cap.max_records;
     const unsigned blocks = (unsigned)std::max<unsigned long long>(
         1, std::min<unsigned long long>((rcap + 8 * kImpRecs - 1) / (8 * kImpRecs), 16ull * ws->sm_count));
-    launch_pdl(imp_reduce_kernel, blocks, 256, 0, st, ws->dval[ws->depth_buf], ws->inst_off, ws->tt,
+    launch_pdl(imp_reduce_kernel, blocks, 256, 0, st, ws->inst_off, ws->tt,
                                               ws->imp_slots, ws->imp_w, ws->imp_a,
                                               ws->ctr);
     note_launch();
@@ -401,7 +401,7 @@ cudaError_t launch_importance(gs_workspace *ws, cudaStream_t st, float *w, uint3
     note_launch();
     int ob = 0;
     const unsigned long long *cnt = &ws->ctr->n_records;
-    if ((e = launch_radix_sort(ws, st, sk, sv, cnt, rcap, 32, true, false, ob, ws->sel_spin_limit)) != cudaSuccess)
+    if ((e = launch_radix_sort(ws, st, sk, sv, cnt, rcap, 32, true, ob, ws->sel_spin_limit)) != cudaSuccess)
         return e;
     uint32_t *sorted = sv[ob];
     if (ncam > 1) {
@@ -410,7 +410,7 @@ cudaError_t launch_importance(gs_workspace *ws, cudaStream_t st, float *w, uint3
         launch_pdl(sel_camkeys_kernel, rblocks, 256, 0, st, v2[0], ws->rec_cam, k2[0], ws->ctr);
         note_launch();
         int ob2 = 0;
-        if ((e = launch_radix_sort(ws, st, k2, v2, cnt, rcap, 8, false, false, ob2, ws->sel_spin_limit)) !=
+        if ((e = launch_radix_sort(ws, st, k2, v2, cnt, rcap, 8, false, ob2, ws->sel_spin_limit)) !=
             cudaSuccess)
             return e;
         sorted = v2[ob2];

@@ -1,22 +1,11 @@
-// sort.cu -- tile/depth binning (App. A: tile-based rasterisation of
-// depth-ordered projected Gaussians).
-//
-// Order of the work:
-//   1. depth sort of the active records: LSD radix sort of the FP32 bits of
-//      camera z (positive, so the bits order like the values), stable, so
-//      equal depths keep record order = (Gaussian, camera) order;
-//   2. emission in depth order: each record writes (global tile id, record)
-//      for every tile of its rectangle; a single-pass look-back scan of the
-//      tiles-touched counts gives the offsets;
-//   3. stable LSD radix sort of the instances by global tile id, which keeps
-//      the depth order inside each tile: the final order is
-//      (camera, tile, depth bits, Gaussian) without ever sorting 64-bit keys;
-//   4. tile ranges from the sorted tile ids.
-// The radix passes are single-pass ("onesweep"): each block ranks its 1024,
-// 2048 or 4096 keys (a tuning of the workspace) in shared memory, publishes per-digit counts and finds its global
-// offsets by a per-digit decoupled look-back, so every pass reads and writes
-// each key once.  Item counts stay on the device, so nothing here needs a
-// host synchronisation.
+// sort.cu -- device LSD radix sort of (32-bit key, value) pairs, stable, for
+// the importance selection (records by w, then by camera) and the
+// model-level selections (Gaussians by score).
+// The passes are single-pass ("onesweep"): each block ranks its 1024, 2048
+// or 4096 keys (a tuning of the workspace) in shared memory, publishes
+// per-digit counts and finds its global offsets by a per-digit decoupled
+// look-back, so every pass reads and writes each key once.  Item counts stay
+// on the device, so nothing here needs a host synchronisation.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -225,8 +214,7 @@ static cudaError_t radix_passes(cudaStream_t st, uint32_t *keys[2], uint32_t *va
 // chosen by the size of the sort).  One memset clears the histograms and the
 // look-back state of every pass (ws->rx_status: [4][256] histogram words,
 // then one region per pass), so the sort's kernels follow one another with
-// programmatic dependent launch.  hist_ready: the producer of the keys has
-// filled the histograms after launch_radix_clear for this cap and bits.
+// programmatic dependent launch.
 // Keys per block of a sort of up to cap keys: the workspace's tuning, or by
 // size (0): small sorts take small blocks so that enough SMs work on them,
 // large ones large blocks, whose look-back chains are shorter (measured on the
@@ -252,18 +240,9 @@ static size_t radix_words(const gs_workspace *ws, unsigned long long cap, int bi
     return kRxHistWords + passes * region;
 }
 
-cudaError_t launch_radix_clear(gs_workspace *ws, cudaStream_t st, unsigned long long cap, int bits)
-{
-    size_t region;
-    const size_t words = radix_words(ws, cap, bits, region);
-    if (cap == 0) return cudaSuccess;
-    if (words > ws->rx_words) return cudaErrorInvalidValue; // sized for this cap
-    return cudaMemsetAsync(ws->rx_status, 0, words * sizeof(uint32_t), st);
-}
-
 cudaError_t launch_radix_sort(gs_workspace *ws, cudaStream_t st, uint32_t *keys[2], uint32_t *vals[2],
                               const unsigned long long *count, unsigned long long cap, int bits, bool vals_identity,
-                              bool hist_ready, int &out_buf, unsigned long long spin_limit)
+                              int &out_buf, unsigned long long spin_limit)
 {
     const int passes = bits <= 0 ? 1 : (bits + 7) / 8;
     cudaError_t e;
@@ -274,13 +253,11 @@ cudaError_t launch_radix_sort(gs_workspace *ws, cudaStream_t st, uint32_t *keys[
     const size_t words = radix_words(ws, cap, bits, region);
     uint32_t *hist = ws->rx_status, *status = ws->rx_status + kRxHistWords;
     if (words > ws->rx_words) return cudaErrorInvalidValue; // sized for this cap
-    if (!hist_ready) {
-        if ((e = cudaMemsetAsync(hist, 0, words * sizeof(uint32_t), st)) != cudaSuccess) return e;
-        unsigned hblocks = (unsigned)((cap + 255) / 256);
-        if (hblocks > 1216) hblocks = 1216;
-        launch_pdl(radix_hist_kernel, hblocks, 256, 0, st, keys[0], count, cap, passes, hist);
-        note_launch();
-    }
+    if ((e = cudaMemsetAsync(hist, 0, words * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    unsigned hblocks = (unsigned)((cap + 255) / 256);
+    if (hblocks > 1216) hblocks = 1216;
+    launch_pdl(radix_hist_kernel, hblocks, 256, 0, st, keys[0], count, cap, passes, hist);
+    note_launch();
     if (items == 4)
         return radix_passes<4>(st, keys, vals, count, cap, passes, vals_identity, status, region, hist, ws->ctr,
                                out_buf, spin_limit);
@@ -311,148 +288,6 @@ cudaError_t launch_radix_sort_scratch(cudaStream_t st, uint32_t *keys[2], uint32
     note_launch();
     return radix_passes<kSortItems>(st, keys, vals, count, cap, passes, vals_identity, status, 0, hist, ctr, out_buf,
                                     kSpinLimit);
-}
-
-// ---- emission -------------------------------------------------------------
-
-struct EmitArgs {
-    const uint32_t *drec;   // records in depth order
-    const uint32_t *tt;
-    const uint2 *rect;
-    const uint16_t *rec_cam;
-    uint32_t *inst_off;
-    uint32_t *tkey, *tval;
-    unsigned long long *lb_status; // ticket at word 0
-    DevCounters *ctr;
-    unsigned long long max_instances;
-    uint32_t *hist;  // [4][256] digit histograms of the written keys (the tile sort's), or nullptr
-    int passes;      // digits of the tile keys
-};
-
-// Blocks of kEmitThreads records (small blocks spread the records over the
-// SMs evenly: 94k records make 737 blocks, about five per SM).
-constexpr int kEmitThreads = 128;
-__global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a, const CamTable *__restrict__ ctp)
-{
-    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
-    const CamTable &ct = *ctp;
-    __shared__ unsigned s_bid;
-    __shared__ unsigned long long s_warp[kEmitThreads / 32];
-    __shared__ unsigned long long s_base;
-    __shared__ unsigned long long s_incl[kEmitThreads];
-    __shared__ uint32_t s_rec[kEmitThreads];
-    __shared__ uint2 s_rect[kEmitThreads];
-    __shared__ int s_tb[kEmitThreads], s_tx[kEmitThreads];
-    __shared__ uint32_t s_hist[4][256];
-    if (threadIdx.x == 0) s_bid = atomicAdd((unsigned *)a.lb_status, 1u);
-    if (a.hist)
-        for (int q = threadIdx.x; q < 4 * 256; q += kEmitThreads) (&s_hist[0][0])[q] = 0u;
-    __syncthreads();
-    const unsigned bid = s_bid;
-    const unsigned long long nrec = a.ctr->n_records;
-    const unsigned long long k = (unsigned long long)bid * kEmitThreads + threadIdx.x;
-    if ((unsigned long long)bid * kEmitThreads >= nrec) return;
-    const bool valid = k < nrec;
-    uint32_t r = 0;
-    unsigned long long c = 0;
-    if (valid) {
-        r = a.drec[k];
-        c = a.tt[r];
-        const int cam = a.rec_cam[r];
-        s_rect[threadIdx.x] = a.rect[r];
-        s_tb[threadIdx.x] = ct.c[cam].tile_base;
-        s_tx[threadIdx.x] = ct.c[cam].tiles_x;
-    }
-    s_rec[threadIdx.x] = r;
-    unsigned long long total;
-    const unsigned long long excl = block_exclusive_scan<kEmitThreads / 32, unsigned long long>(c, s_warp, total);
-    s_incl[threadIdx.x] = excl + c;
-    if (threadIdx.x < 32) {
-        unsigned long long b = lookback_exclusive(a.lb_status + 1, bid, total, a.ctr, kSiteEmit);
-        if (threadIdx.x == 0) s_base = b;
-    }
-    __syncthreads();
-    const unsigned long long base = s_base;
-    if (valid) a.inst_off[r] = (uint32_t)(base + excl);
-    if (k == nrec - 1) {
-        const unsigned long long end = base + excl + c;
-        a.ctr->instances_needed = end;
-        a.ctr->n_instances = end < a.max_instances ? end : a.max_instances;
-        if (end > a.max_instances) set_error(a.ctr, GS_ERR_CAPACITY, kSiteEmit);
-    }
-    // cooperative, coalesced emission of the block's instances
-    for (unsigned long long j = threadIdx.x; j < total; j += kEmitThreads) {
-        const unsigned long long gi = base + j;
-        if (gi >= a.max_instances) break;
-        // record kk: first with inclusive prefix > j
-        int lo = 0, hi = kEmitThreads - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (s_incl[mid] > j) hi = mid; else lo = mid + 1;
-        }
-        const unsigned long long first = lo ? s_incl[lo - 1] : 0ull;
-        const uint32_t local = (uint32_t)(j - first);
-        int x0, y0, x1, y1;
-        unpack_rect(s_rect[lo], x0, y0, x1, y1);
-        const uint32_t w = (uint32_t)(x1 - x0);
-        const int tx = x0 + (int)(local % w), ty = y0 + (int)(local / w);
-        const uint32_t key = (uint32_t)(s_tb[lo] + ty * s_tx[lo] + tx);
-        a.tkey[gi] = key;
-        a.tval[gi] = s_rec[lo];
-        if (a.hist)
-            for (int p = 0; p < a.passes; p++) atomicAdd(&s_hist[p][(key >> (8 * p)) & 255u], 1u);
-    }
-    if (a.hist) {
-        __syncthreads();
-        for (int q = threadIdx.x; q < a.passes * 256; q += kEmitThreads) {
-            const uint32_t v = (&s_hist[0][0])[q];
-            if (v) atomicAdd(&a.hist[q], v);
-        }
-    }
-}
-
-// hist: the tile sort's histograms ([passes][256], cleared), filled as the
-// keys are written; nullptr: none.
-cudaError_t launch_emit(gs_workspace *ws, cudaStream_t st, uint32_t *hist, int passes)
-{
-    const unsigned long long cap = (unsigned long long)ws->cap.max_records;
-    const unsigned blocks = (unsigned)((cap + kEmitThreads - 1) / kEmitThreads);
-    cudaError_t e;
-    if ((e = cudaMemsetAsync(ws->lb_status, 0, (blocks + 1) * sizeof(unsigned long long), st)) != cudaSuccess)
-        return e;
-    EmitArgs a;
-    a.drec = ws->dval[ws->depth_buf];
-    a.tt = ws->tt; a.rect = ws->rect; a.rec_cam = ws->rec_cam; a.inst_off = ws->inst_off;
-    a.tkey = ws->tkey[0]; a.tval = ws->tval[0];
-    a.lb_status = ws->lb_status; a.ctr = ws->ctr; a.max_instances = (unsigned long long)ws->cap.max_instances;
-    a.hist = hist; a.passes = passes;
-    launch_pdl(emit_kernel, blocks, kEmitThreads, 0, st, a, ws->d_cams);
-    note_launch();
-    return cudaGetLastError();
-}
-
-// ---- tile ranges ------------------------------------------------------------
-
-__global__ void __launch_bounds__(256) ranges_kernel(const uint32_t *keys, const DevCounters *ctr, uint2 *ranges)
-{
-    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
-    const unsigned long long n = ctr->n_instances;
-    for (unsigned long long s = (unsigned long long)blockIdx.x * 256 + threadIdx.x; s < n;
-         s += (unsigned long long)gridDim.x * 256) {
-        const uint32_t t = keys[s];
-        if (s == 0 || keys[s - 1] != t) ranges[t].x = (uint32_t)s;
-        if (s == n - 1 || keys[s + 1] != t) ranges[t].y = (uint32_t)(s + 1);
-    }
-}
-
-cudaError_t launch_ranges(gs_workspace *ws, cudaStream_t st)
-{
-    cudaError_t e;
-    if ((e = cudaMemsetAsync(ws->ranges, 0, (size_t)ws->cams.total_tiles * sizeof(uint2), st)) != cudaSuccess)
-        return e;
-    launch_pdl(ranges_kernel, 152 * 8, 256, 0, st, ws->tkey[ws->tile_buf], ws->ctr, ws->ranges);
-    note_launch();
-    return cudaGetLastError();
 }
 
 } // namespace gs

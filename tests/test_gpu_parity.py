@@ -167,6 +167,35 @@ def test_gate_bulk_copies_equal_plain_loads(ncam):
     assert np.array_equal(a, b)
 
 
+def test_long_tile_lists_sorted_by_depth():
+    """Tiles whose lists exceed what one warp sorts in shared memory (512
+    entries) are sorted in chunks merged through a scratch copy: every list
+    equals the oracle's binning of the GPU's own records (rectangle and depth
+    key as the GPU computed them), bit for bit, equal depths included."""
+    g = synth.plain_scene(3000, seed=71)
+    g.mean[:, :2] *= 0.05                       # every mean in front of a 48 x 48 view
+    g.mean[1::2, 2] = g.mean[0::2, 2][: g.n // 2]  # pairs of equal depths
+    g.log_scale[:] = np.float32(np.log(0.1))    # footprints over all nine tiles
+    cam = synth.plain_camera(48, 48, 300.0)
+    P = O.Params()
+    run = ViewRun(g, [cam], P)
+    recs = run.records_of(0)
+    both = np.array(sorted(recs.keys()), np.int64)
+    ridx = np.array([recs[i] for i in both], np.int64)
+    n = g.n
+    own = dict(status=np.full(n, O.EMPTY, np.int8), rect=np.zeros((n, 4), np.int32),
+               depth32=np.zeros(n, np.float32), tiles=np.zeros(n, np.int32))
+    own["status"][both] = O.ACTIVE
+    own["rect"][both] = unpack_rect(run.rect[ridx])
+    own["depth32"][both] = run.depth_bits[ridx].view(np.float32)
+    own["tiles"][both] = run.tt[ridx]
+    ts, lst = O.bin_tiles(own, cam, P)
+    glists = run.tile_lists(0)
+    assert max(len(l) for l in glists) > 2048  # three levels of merges
+    for t, gl in enumerate(glists):
+        assert np.array_equal(gl, lst[ts[t]:ts[t + 1]].astype(np.int64)), f"tile {t} list differs"
+
+
 def test_cull_mark_equals_drop_for_training_and_off_for_importance():
     """GS_CULL_MARK keeps culled Gaussians in the lists, marked: the training
     render and its gradients are those of GS_CULL_DROP bit for bit, and the
