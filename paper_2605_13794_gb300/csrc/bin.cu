@@ -24,7 +24,8 @@
 
 namespace gs {
 
-constexpr int kBinThreads = 128;       // records per block of the count and scatter passes
+constexpr int kBinThreads = 128;       // threads (and records) per block of the count pass
+constexpr int kScatterRecs = 32;       // records per block of the scatter pass (kBinThreads threads)
 constexpr int kTileScanItems = 4;      // tiles per thread of the tile scan (1024 per block)
 constexpr int kTileSortMax = 512;      // entries a warp sorts in registers (16 per lane)
 constexpr int kTileSortWarps = 4;      // tiles per block of the per-tile sort
@@ -76,16 +77,16 @@ __device__ __forceinline__ uint32_t bin_instance(const BinBlock &s, unsigned lon
     return (uint32_t)(s.tile_base[lo] + ty * s.tiles_x[lo] + tx);
 }
 
-// Loads the block's records k0 .. k0 + kBinThreads - 1 (those below nrec) and
-// scans their tile counts; returns this thread's exclusive prefix and the
-// block's total.
+// Loads the block's records k0 .. k0 + recs - 1 (those below nrec; recs <=
+// kBinThreads, one per thread) and scans their tile counts; returns this
+// thread's exclusive prefix and the block's total.
 __device__ __forceinline__ unsigned long long bin_load(const BinArgs &a, const CamTable &ct, BinBlock &s,
-                                                       unsigned long long k0, unsigned long long nrec,
+                                                       unsigned long long k0, unsigned long long nrec, int recs,
                                                        unsigned long long &c, unsigned long long &total)
 {
     const unsigned long long k = k0 + threadIdx.x;
     c = 0;
-    if (k < nrec) {
+    if ((int)threadIdx.x < recs && k < nrec) {
         const uint32_t r = (uint32_t)k;
         c = a.tt[r];
         const int cam = a.rec_cam[r];
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(kBinThreads) bin_count_kernel(BinArgs a, const
     const unsigned long long k0 = (unsigned long long)bid * kBinThreads;
     if (k0 >= nrec) return;
     unsigned long long c, total;
-    const unsigned long long excl = bin_load(a, *ctp, s, k0, nrec, c, total);
+    const unsigned long long excl = bin_load(a, *ctp, s, k0, nrec, kBinThreads, c, total);
     if (threadIdx.x < 32) {
         const unsigned long long b = lookback_exclusive(a.lb_count + 1, bid, total, a.ctr, kSiteEmit);
         if (threadIdx.x == 0) s_base = b;
@@ -174,16 +175,18 @@ __global__ void __launch_bounds__(256) tile_scan_kernel(BinArgs a)
     }
 }
 
-// 3. Scatter: every instance to the next position of its tile.
+// 3. Scatter: every instance to the next position of its tile.  A block of
+// kBinThreads threads takes kScatterRecs records, so that twice as many
+// cursor atomics are in flight per SM as records per thread would allow.
 __global__ void __launch_bounds__(kBinThreads) bin_scatter_kernel(BinArgs a, const CamTable *__restrict__ ctp)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     __shared__ BinBlock s;
     const unsigned long long nrec = a.ctr->n_records;
-    const unsigned long long k0 = (unsigned long long)blockIdx.x * kBinThreads;
+    const unsigned long long k0 = (unsigned long long)blockIdx.x * kScatterRecs;
     if (k0 >= nrec) return;
     unsigned long long c, total;
-    bin_load(a, *ctp, s, k0, nrec, c, total);
+    bin_load(a, *ctp, s, k0, nrec, kScatterRecs, c, total);
     // four instances per round: their cursor atomics are in flight together
     constexpr int kRound = 4;
     for (unsigned long long j0 = threadIdx.x; j0 < total; j0 += kRound * kBinThreads) {
@@ -210,10 +213,10 @@ __global__ void __launch_bounds__(kBinThreads) bin_scatter_kernel(BinArgs a, con
 }
 
 // Ascending bitonic sort of the warp's 32 * E keys held in registers: key
-// x[e] of lane l is element g = 32 e + l.  A stage of stride s >= 32 pairs
-// registers of one lane (e, e ^ s / 32); a stage of stride s < 32 pairs lanes
-// (l, l ^ s) by a shuffle.  The network is fixed, so the result is the sorted
-// order of the keys (all distinct) whatever order they came in.
+// x[e] of lane l is element g = E l + e.  A stage of stride s < E pairs
+// registers of one lane (e, e ^ s); a stage of stride s >= E pairs lanes
+// (l, l ^ s / E) by a shuffle.  The network is fixed, so the result is the
+// sorted order of the keys (all distinct) whatever order they came in.
 template <int E> __device__ __forceinline__ void warp_sort_regs(unsigned long long (&x)[E])
 {
     const int lane = threadIdx.x & 31;
@@ -221,28 +224,27 @@ template <int E> __device__ __forceinline__ void warp_sort_regs(unsigned long lo
     for (int size = 2; size <= 32 * E; size <<= 1) {
 #pragma unroll
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            if (stride >= 32) {
-                const int es = stride / 32;
+            if (stride < E) {
 #pragma unroll
                 for (int e = 0; e < E; e++) {
-                    if (e & es) continue; // the lower element of each pair
-                    const bool up = ((e * 32 + lane) & size) == 0;
-                    const unsigned long long u = x[e], v = x[e ^ es];
+                    if (e & stride) continue; // the lower element of each pair
+                    const bool up = ((lane * E + e) & size) == 0;
+                    const unsigned long long u = x[e], v = x[e ^ stride];
                     const bool swap = (u > v) == up;
                     x[e] = swap ? v : u;
-                    x[e ^ es] = swap ? u : v;
+                    x[e ^ stride] = swap ? u : v;
                 }
             } else {
+                const int ls = stride / E;
+                const bool lower = (lane & ls) == 0;
 #pragma unroll
                 for (int e = 0; e < E; e++) {
                     const unsigned long long u = x[e];
-                    const unsigned lo = __shfl_xor_sync(0xffffffffu, (unsigned)u, stride);
-                    const unsigned hi = __shfl_xor_sync(0xffffffffu, (unsigned)(u >> 32), stride);
+                    const unsigned lo = __shfl_xor_sync(0xffffffffu, (unsigned)u, ls);
+                    const unsigned hi = __shfl_xor_sync(0xffffffffu, (unsigned)(u >> 32), ls);
                     const unsigned long long v = ((unsigned long long)hi << 32) | lo;
-                    const bool up = ((e * 32 + lane) & size) == 0;
-                    const bool lower = (lane & stride) == 0;
-                    const bool keep_min = lower == up;
-                    x[e] = (u < v) == keep_min ? u : v;
+                    const bool up = ((lane * E + e) & size) == 0;
+                    x[e] = (u < v) == (lower == up) ? u : v;
                 }
             }
         }
@@ -278,13 +280,13 @@ __device__ __forceinline__ void sort_run(const uint32_t *kk, const uint32_t *vv,
     unsigned long long x[E];
 #pragma unroll
     for (int e = 0; e < E; e++) {
-        const uint32_t g = (uint32_t)(e * 32 + lane);
+        const uint32_t g = (uint32_t)(lane * E + e);
         x[e] = g < n ? key_at(kk, vv, g) : ~0ull;
     }
     warp_sort_regs<E>(x);
 #pragma unroll
     for (int e = 0; e < E; e++) {
-        const uint32_t g = (uint32_t)(e * 32 + lane);
+        const uint32_t g = (uint32_t)(lane * E + e);
         if (g < n) {
             if (rk) rk[g] = (uint32_t)(x[e] >> 32);
             rv[g] = (uint32_t)x[e];
@@ -303,7 +305,7 @@ __device__ __forceinline__ void sort_short(const uint32_t *kk, const uint32_t *v
 
 // 4. Per-tile sort of the scattered (depth bits, record) pairs; the sorted
 // records end in sval.  One warp per tile, keys in registers.
-__global__ void __launch_bounds__(32 * kTileSortWarps) tile_sort_kernel(BinArgs a)
+__global__ void __launch_bounds__(32 * kTileSortWarps, 8) tile_sort_kernel(BinArgs a)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -379,7 +381,8 @@ cudaError_t launch_bin(gs_workspace *ws, cudaStream_t st)
         launch_pdl(tile_scan_kernel, sblocks, 256, 0, st, a);
         note_launch();
     }
-    launch_pdl(bin_scatter_kernel, cblocks, kBinThreads, 0, st, a, ws->d_cams);
+    launch_pdl(bin_scatter_kernel, (unsigned)((rcap + kScatterRecs - 1) / kScatterRecs), kBinThreads, 0, st, a,
+               ws->d_cams);
     note_launch();
     if (tiles > 0) {
         launch_pdl(tile_sort_kernel, (unsigned)((tiles + kTileSortWarps - 1) / kTileSortWarps), 32 * kTileSortWarps,
