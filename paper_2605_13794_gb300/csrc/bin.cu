@@ -190,22 +190,24 @@ __global__ void __launch_bounds__(kBinThreads) bin_scatter_kernel(BinArgs a, con
     // four instances per round: their cursor atomics are in flight together
     constexpr int kRound = 4;
     for (unsigned long long j0 = threadIdx.x; j0 < total; j0 += kRound * kBinThreads) {
-        uint32_t t[kRound], pos[kRound], r[kRound];
+        uint32_t pos[kRound], r[kRound], end[kRound], dk[kRound];
 #pragma unroll
-        for (int q = 0; q < kRound; q++) {
+        for (int q = 0; q < kRound; q++) { // every load and atomic of the round issued first
             const unsigned long long j = j0 + (unsigned long long)q * kBinThreads;
             if (j >= total) break;
             int slot;
-            t[q] = bin_instance(s, j, slot);
+            const uint32_t t = bin_instance(s, j, slot);
             r[q] = s.rec[slot];
-            pos[q] = atomicAdd(&a.tile_cur[t[q]], 1u);
+            pos[q] = atomicAdd(&a.tile_cur[t], 1u);
+            end[q] = a.ranges[t].y;
+            dk[q] = a.dkey[r[q]];
         }
 #pragma unroll
         for (int q = 0; q < kRound; q++) {
             const unsigned long long j = j0 + (unsigned long long)q * kBinThreads;
             if (j >= total) break;
-            if (pos[q] < a.ranges[t[q]].y) { // within the capacity-clamped range
-                a.skey[pos[q]] = a.dkey[r[q]];
+            if (pos[q] < end[q]) { // within the capacity-clamped range
+                a.skey[pos[q]] = dk[q];
                 a.sval[pos[q]] = r[q];
             }
         }
@@ -219,33 +221,34 @@ __global__ void __launch_bounds__(kBinThreads) bin_scatter_kernel(BinArgs a, con
 // sorted order of the keys (all distinct) whatever order they came in.
 template <int E> __device__ __forceinline__ void warp_sort_regs(unsigned long long (&x)[E])
 {
+    // the loops over sizes and lane strides stay loops (a short kernel body
+    // for the instruction cache); the registers' indices are unrolled
     const int lane = threadIdx.x & 31;
-#pragma unroll
     for (int size = 2; size <= 32 * E; size <<= 1) {
+        for (int stride = size >> 1; stride >= E; stride >>= 1) {
+            const int ls = stride / E;
+            const bool lower = (lane & ls) == 0;
 #pragma unroll
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            if (stride < E) {
+            for (int e = 0; e < E; e++) {
+                const unsigned long long u = x[e];
+                const unsigned lo = __shfl_xor_sync(0xffffffffu, (unsigned)u, ls);
+                const unsigned hi = __shfl_xor_sync(0xffffffffu, (unsigned)(u >> 32), ls);
+                const unsigned long long v = ((unsigned long long)hi << 32) | lo;
+                const bool up = ((lane * E + e) & size) == 0;
+                x[e] = (u < v) == (lower == up) ? u : v;
+            }
+        }
 #pragma unroll
-                for (int e = 0; e < E; e++) {
-                    if (e & stride) continue; // the lower element of each pair
-                    const bool up = ((lane * E + e) & size) == 0;
-                    const unsigned long long u = x[e], v = x[e ^ stride];
-                    const bool swap = (u > v) == up;
-                    x[e] = swap ? v : u;
-                    x[e ^ stride] = swap ? u : v;
-                }
-            } else {
-                const int ls = stride / E;
-                const bool lower = (lane & ls) == 0;
+        for (int stride = E / 2; stride > 0; stride >>= 1) {
+            if (stride >= size) continue;
 #pragma unroll
-                for (int e = 0; e < E; e++) {
-                    const unsigned long long u = x[e];
-                    const unsigned lo = __shfl_xor_sync(0xffffffffu, (unsigned)u, ls);
-                    const unsigned hi = __shfl_xor_sync(0xffffffffu, (unsigned)(u >> 32), ls);
-                    const unsigned long long v = ((unsigned long long)hi << 32) | lo;
-                    const bool up = ((lane * E + e) & size) == 0;
-                    x[e] = (u < v) == (lower == up) ? u : v;
-                }
+            for (int e = 0; e < E; e++) {
+                if (e & stride) continue; // the lower element of each pair
+                const bool up = ((lane * E + e) & size) == 0;
+                const unsigned long long u = x[e], v = x[e ^ stride];
+                const bool swap = (u > v) == up;
+                x[e] = swap ? v : u;
+                x[e ^ stride] = swap ? u : v;
             }
         }
     }
