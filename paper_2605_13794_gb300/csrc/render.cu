@@ -5,7 +5,7 @@
 // One block per tile; each warp owns an 8 x 8 pixel square of it (lane l the
 // horizontal pixel pair (2 (l % 4), l / 4), packed FP32x2) and walks the
 // tile's depth-ordered list on its own, staging each batch of 32 entries
-// itself and visiting only the entries whose alpha box meets its square.
+// itself and visiting only the entries that can reach alpha_min in its square.
 // Per-Gaussian quantities are warp reductions (recursive halving for the
 // adjoint's nine values), then the warps' partials summed in warp order,
 // rather than per-pixel global atomics.  The backward and the importance
@@ -57,24 +57,40 @@ __device__ __forceinline__ float2 pair_alpha(float2 p, float o, float amax, floa
     return make_float2(fminf(amax, og.x), fminf(amax, og.y));
 }
 
-// Half-widths of the box around the pixels an entry can composite at:
-// alpha >= alpha_min needs o G >= alpha_min, i.e. the ellipse
-// A (dx + k dy)^2 + D dy^2 <= tau, tau = 2 ln(o / alpha_min), whose bounding box
-// has half-widths sqrt(tau Sx), sqrt(tau Sy) with (Sx, Sy) the diagonal of the
-// inverse of the conic: Sx = 1/A + k^2/D, Sy = 1/D.  Widened (tau by 0.2 % +
-// 2e-3, the widths by 0.1 % + 1/32 px) far beyond the FP32 error of the
-// exponent the kernels evaluate, so no pixel outside the box can reach
-// alpha_min in them; empty (-1e30) when o is below alpha_min.  A warp whose
-// pixels all lie outside an entry's box skips the entry: it composites
-// nowhere in the warp, so skipping it changes nothing.
-__device__ __forceinline__ float2 alpha_box(float A, float k, float D, float o, float alpha_min)
+// Whether an entry can composite anywhere in a warp's square, the box
+// [bx0, bx1] x [by0, by1] of its pixel centres (tile-local; (u, v) the entry's
+// tile-local mean).  alpha >= alpha_min needs o G >= alpha_min, i.e.
+// q = A (dx + k dy)^2 + D dy^2 <= tau, tau = 2 ln(o / alpha_min).  Two
+// conservative tests, both of which must pass:
+//  - the bounding box of that ellipse, half-widths sqrt(tau Sx), sqrt(tau Sy)
+//    with (Sx, Sy) the diagonal of the inverse of the conic (Sx = 1/A +
+//    k^2/D, Sy = 1/D), meets the square;
+//  - a lower bound of q over the square is at most tau: D times the squared
+//    distance of the dy range from 0 plus A times the squared gap between the
+//    dx range and the range of -k dy (each term minimised on its own, so their
+//    sum is below q at every point of the square).  It drops the squares that
+//    only the corners of an elongated, tilted ellipse's box reach.
+// Widened (tau by 0.2 % + 2e-3, the half-widths by 0.1 % + 1/32 px, the gaps
+// narrowed by 1/32 px) far beyond the FP32 error of the exponent the kernels
+// evaluate, so no pixel of a square that fails either test can reach
+// alpha_min in them; false when o is below alpha_min.  A warp skips an entry
+// that fails: it composites nowhere in the warp, so skipping it changes
+// nothing.
+__device__ __forceinline__ bool square_visit(float A, float k, float D, float o, float alpha_min, float u, float v,
+                                             float bx0, float bx1, float by0, float by1)
 {
     float tau = 2.f * logf(o / alpha_min);
     tau = fmaf(tau, 1.002f, 2e-3f);
-    if (!(tau > 0.f)) return make_float2(-1e30f, -1e30f);
+    if (!(tau > 0.f)) return false;
     const float iD = 1.f / D;
-    return make_float2(fmaf(sqrtf(tau * fmaf(k * k, iD, 1.f / A)), 1.001f, 0.03125f),
-                       fmaf(sqrtf(tau * iD), 1.001f, 0.03125f));
+    const float hx = fmaf(sqrtf(tau * fmaf(k * k, iD, 1.f / A)), 1.001f, 0.03125f);
+    const float hy = fmaf(sqrtf(tau * iD), 1.001f, 0.03125f);
+    if (u + hx < bx0 || u - hx > bx1 || v + hy < by0 || v - hy > by1) return false;
+    const float dx0 = bx0 - u, dx1 = bx1 - u, dy0 = by0 - v, dy1 = by1 - v;
+    const float p0 = -k * dy0, p1 = -k * dy1;
+    const float gy = fmaxf(fmaxf(dy0, -dy1) - 0.03125f, 0.f);
+    const float gx = fmaxf(fmaxf(fminf(p0, p1) - dx1, dx0 - fmaxf(p0, p1)) - 0.03125f, 0.f);
+    return fmaf(A * gx, gx, D * gy * gy) <= tau;
 }
 
 __device__ __forceinline__ float warp_sum_f(float v)
@@ -141,7 +157,7 @@ __device__ __forceinline__ unsigned long long slot_of(const uint32_t *inst_off, 
 // tile: lane l holds the horizontal pixel pair (2 (l % 4), l / 4) of it, as
 // FP32x2, and the warp walks the tile's list on its own.  The warp stages each
 // batch of 32 entries itself (lane i the i-th), the staging lane tests its
-// entry's alpha box against the square, and one ballot gives the entries the
+// entry's alpha footprint against the square (square_visit), and one ballot gives the entries the
 // warp visits; an entry whose box misses the square composites nowhere in it.
 
 template <int TW, int TH> struct SquareShape {
@@ -235,8 +251,7 @@ __global__ void __launch_bounds__(SquareShape<TW, TH>::threads)
             s0[warp][lane] = e0;
             s1[warp][lane] = make_float4(stage_D(r1), op, r1.z, r1.w);
             s2[warp][lane] = r2.x;
-            const float2 hb = alpha_box(r0.z, r0.w, r1.x, op, rc.alpha_min);
-            visit = !(e0.x + hb.x < q.bx0 || e0.x - hb.x > q.bx1 || e0.y + hb.y < q.by0 || e0.y - hb.y > q.by1);
+            visit = square_visit(r0.z, r0.w, r1.x, op, rc.alpha_min, e0.x, e0.y, q.bx0, q.bx1, q.by0, q.by1);
         }
         unsigned m = __ballot_sync(0xffffffffu, visit);
         __syncwarp();
@@ -319,7 +334,7 @@ cudaError_t launch_render_fwd(gs_workspace *ws, cudaStream_t st, float *rgb, flo
 // composited, recovering T by T / (1 - alpha) from the final transmittance.
 // It stages each batch of 32 entries itself (one per lane), so no block-wide
 // barrier holds it while another warp of the tile has more to do; the staging
-// lane also tests its entry's alpha box against the warp's square, and one
+// lane also tests its entry's alpha footprint against the warp's square, and one
 // ballot gives the batch's entries the warp must visit.  Per visited entry the
 // warp's gradient is one warp reduction; the warps' partials of a batch are
 // summed in warp order by the warp that finishes that batch last
@@ -435,10 +450,9 @@ __global__ void __launch_bounds__(SquareShape<TW, TH>::threads)
             s1[warp][lane] = make_float4(stage_D(r1), op, r1.z, r1.w);
             s2[warp][lane] = r2.x;
             s_slot[warp][lane] = slot_of(a.inst_off, a.rect, r, tx, ty);
-            // visited: in front of the warp's last contribution, alpha box meeting the square
-            const float2 hb = alpha_box(r0.z, r0.w, r1.x, op, rc.alpha_min);
-            visit = lo + lane - start < wmax && !(e0.x + hb.x < bx0 || e0.x - hb.x > bx1 || e0.y + hb.y < by0 ||
-                                                  e0.y - hb.y > by1);
+            // visited: in front of the warp's last contribution, alpha footprint meeting the square
+            visit = lo + lane - start < wmax &&
+                    square_visit(r0.z, r0.w, r1.x, op, rc.alpha_min, e0.x, e0.y, bx0, bx1, by0, by1);
         }
         const unsigned vmask = __ballot_sync(0xffffffffu, visit);
         // the partial buffer of this batch is free once batch b - kBwdBufs has been summed
@@ -643,8 +657,7 @@ __global__ void __launch_bounds__(SquareShape<TW, TH>::threads)
                 s1[warp][lane] = make_float4(stage_D(r1), r1.y, r2.w != 0.f ? 0.f : r1.y, r2.x);
                 if (FWD) s3[FWD ? warp : 0][lane] = make_float2(r1.z, r1.w);
                 // the record's own opacity: the training opacity is the same or 0
-                const float2 hb = alpha_box(r0.z, r0.w, r1.x, r1.y, rc.alpha_min);
-                visit = !(e0.x + hb.x < q.bx0 || e0.x - hb.x > q.bx1 || e0.y + hb.y < q.by0 || e0.y - hb.y > q.by1);
+                visit = square_visit(r0.z, r0.w, r1.x, r1.y, rc.alpha_min, e0.x, e0.y, q.bx0, q.bx1, q.by0, q.by1);
             }
         }
         const unsigned vmask = __ballot_sync(0xffffffffu, visit);
