@@ -45,7 +45,7 @@ __device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
 
 // grid: (tiles_x, tiles_y, batch * 3).  F: the three coefficient maps of the
 // SSIM gradient of each plane, planar: F[(plane * 3 + m) * H * W + pixel].
-__global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *img, const float *tgt, int H, int W, Win win,
+__global__ void __launch_bounds__(256, 4) ssim_fwd_kernel(const float *img, const float *tgt, int H, int W, Win win,
                                                        float C1, float C2, float *F, unsigned long long *acc)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
@@ -81,25 +81,32 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *img, const f
     __syncthreads();
     // horizontal blur of (x, y), (x^2, y^2) and xy: 42 rows x (32 / kHSeg) segments,
     // consecutive threads on consecutive rows (no bank conflicts)
+    // input by input: each input's products x^2, y^2 and xy are formed once and
+    // added to the kHSeg outputs whose window holds it
     for (int wi = threadIdx.x; wi < kLTH * (kLT / kHSeg); wi += 256) {
         const int r = wi % kLTH, c0 = (wi / kLTH) * kHSeg;
-        float2 v[kHSeg + 10];
+        float2 a01[kHSeg], a23[kHSeg];
+        float a4[kHSeg];
 #pragma unroll
-        for (int j = 0; j < kHSeg + 10; j++) v[j] = sxy[r][c0 + j];
+        for (int o = 0; o < kHSeg; o++) { a01[o] = f2s(0.f); a23[o] = f2s(0.f); a4[o] = 0.f; }
 #pragma unroll
-        for (int o = 0; o < kHSeg; o++) {
-            float2 a01 = f2s(0.f), a23 = f2s(0.f);
-            float a4 = 0.f;
+        for (int j = 0; j < kHSeg + 10; j++) {
+            const float2 vj = sxy[r][c0 + j];
+            const float2 sj = __fmul2_rn(vj, vj);
+            const float xj = vj.x * vj.y;
 #pragma unroll
-            for (int t = 0; t < 11; t++) {
-                const float2 wt = f2s(win.w[t]), vt = v[o + t];
-                const float2 p = __fmul2_rn(wt, vt);
-                a01 = __ffma2_rn(wt, vt, a01);
-                a23 = __ffma2_rn(p, vt, a23);
-                a4 = fmaf(p.x, vt.y, a4);
+            for (int o = 0; o < kHSeg; o++) {
+                const int t = j - o;
+                if (t >= 0 && t < 11) {
+                    const float2 wt = f2s(win.w[t]);
+                    a01[o] = __ffma2_rn(wt, vj, a01[o]);
+                    a23[o] = __ffma2_rn(wt, sj, a23[o]);
+                    a4[o] = fmaf(wt.x, xj, a4[o]);
+                }
             }
-            hb01[r][c0 + o] = a01; hb23[r][c0 + o] = a23; hb4[r][c0 + o] = a4;
         }
+#pragma unroll
+        for (int o = 0; o < kHSeg; o++) { hb01[r][c0 + o] = a01[o]; hb23[r][c0 + o] = a23[o]; hb4[r][c0 + o] = a4[o]; }
     }
     __syncthreads();
     // vertical blur and the SSIM terms: 32 columns x (32 / kVSeg) segments
@@ -134,10 +141,10 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *img, const f
             const float sxx = exx - mx * mx, syy = eyy - my * my, sxy_ = exy - mx * my;
             const float A1 = 2.f * mx * my + C1, A2 = 2.f * sxy_ + C2;
             const float B1 = mx * mx + my * my + C1, B2 = sxx + syy + C2;
-            const float iB = 1.f / (B1 * B2);
+            const float iB = 1.f / (B1 * B2); // 1 / B1 = B2 iB, 1 / B2 = B1 iB
             const float S = A1 * A2 * iB;
-            const float dmx = 2.f * my * A2 * iB - S * 2.f * mx / B1;
-            const float dsxx = -S / B2;
+            const float dmx = 2.f * my * A2 * iB - S * 2.f * mx * (B2 * iB);
+            const float dsxx = -S * (B1 * iB);
             const float dsxy = 2.f * A1 * iB;
             const long long hw = (long long)H * W, p = (long long)gy * W + gx;
             float *Fp = F + 3 * (long long)plane * hw + p;
@@ -166,8 +173,10 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *img, const f
     }
 }
 
+// s_l1 = (1 - lambda) / (3 H W batch), s_ssim = lambda / (3 H W batch): the
+// weights of the two mean terms of the batch's loss.
 __global__ void __launch_bounds__(256, 4) ssim_bwd_kernel(const float *img, const float *tgt, int H, int W, Win win,
-                                                       const float *F, float lambda, int batch, float *dL)
+                                                       const float *F, float s_l1, float s_ssim, float *dL)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     __shared__ float2 sf01[kLTH][kLTP];
@@ -236,7 +245,6 @@ __global__ void __launch_bounds__(256, 4) ssim_bwd_kernel(const float *img, cons
         }
     }
     __syncthreads();
-    const float npx = 3.f * (float)H * (float)W; // SSIM and L1 are means over channels and pixels
     float2 b01[kVSeg];
     float b2[kVSeg];
 #pragma unroll
@@ -260,10 +268,10 @@ __global__ void __launch_bounds__(256, 4) ssim_bwd_kernel(const float *img, cons
         if (gy >= H || gx >= W) continue;
         const long long p = (long long)plane * H * W + (long long)gy * W + gx;
         const float xv = xo[o], yv = yo[o];
-        const float dssim = (b01[o].x + 2.f * xv * b01[o].y + yv * b2[o]) / npx;
+        const float dssim = b01[o].x + 2.f * xv * b01[o].y + yv * b2[o];
         const float d = xv - yv;
         const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-        dL[p] = ((1.f - lambda) * sgn / npx - lambda * dssim) / (float)batch;
+        dL[p] = s_l1 * sgn - s_ssim * dssim;
     }
 }
 
@@ -299,7 +307,9 @@ cudaError_t launch_loss(gs_workspace *ws, cudaStream_t st, const float *img, con
     kt_end(ws, GS_KT_SSIM_FWD, st);
     note_launch();
     kt_begin(ws, GS_KT_SSIM_BWD, st);
-    launch_pdl(ssim_bwd_kernel, grid, 256, 0, st, img, tgt, H, W, win, maps, lambda, B, dL);
+    const double wsum = 3.0 * H * W * B; // SSIM and L1 are means over channels, pixels and views
+    launch_pdl(ssim_bwd_kernel, grid, 256, 0, st, img, tgt, H, W, win, maps, (float)((1.0 - lambda) / wsum),
+               (float)(lambda / wsum), dL);
     kt_end(ws, GS_KT_SSIM_BWD, st);
     note_launch();
     launch_pdl(loss_finalize_kernel, 1, 32, 0, st, acc, B, H, W, lambda, loss_out);
