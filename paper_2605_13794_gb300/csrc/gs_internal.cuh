@@ -61,10 +61,31 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;          // keys per thread in a radix pass (default)
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kScanTile = 4096;         // items per block of the selection's prefix sums
-constexpr int kSlotFloats = 9;          // per (record, tile) gradient slot: du dv dA dB dC do dr dg db
+// per (record, tile) gradient slot, as the compositing adjoint writes it: the
+// dG-weighted moments sum dG e, sum dG dy, sum dG dx^2, sum dG dx dy, sum dG dy^2
+// (dG = dL/do of a pixel, (dx, dy) = pixel centre - mean, e = dx + k dy), then
+// dL/do, dL/dr, dL/dg, dL/db; the per-record sum turns the moments into
+// dL/du dL/dv dL/dA dL/dB dL/dC (slot_grads_from_moments)
+constexpr int kSlotFloats = 9;
 constexpr int kGradRow = 59;            // parameters per Gaussian: mean 3, log-scale 3, quat 4, opacity 1, SH 48
 constexpr unsigned long long kSpinLimit = 1ull << 22;
 constexpr int kMaxLod = 15;             // largest supported L_max
+
+// The mean and conic gradients of a record from the sums of its slots' moments
+// (see kSlotFloats).  With power = -1/2 (A dx^2 + C dy^2) - B dx dy
+// = -1/2 (A e^2 + D dy^2) (k = B / A, D = C - B^2 / A) and dL/dpower = o dG at
+// each pixel:  dL/du = o A sum dG e,  dL/dv = o (k A sum dG e + D sum dG dy),
+// dL/dA = -o/2 sum dG dx^2,  dL/dB = -o sum dG dx dy,  dL/dC = -o/2 sum dG dy^2.
+__device__ __forceinline__ void slot_grads_from_moments(float (&g)[kSlotFloats], float A, float k, float D, float o)
+{
+    const float oAe = o * A * g[0];
+    const float gv = fmaf(k, oAe, o * D * g[1]);
+    g[0] = oAe;
+    g[1] = gv;
+    g[2] = -0.5f * o * g[2];
+    g[3] = -o * g[3];
+    g[4] = -0.5f * o * g[4];
+}
 
 // Error sites recorded next to the error word (which kernel gave up).
 enum ErrorSite {

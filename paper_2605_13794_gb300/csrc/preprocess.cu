@@ -972,7 +972,8 @@ cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t 
 
 // ---- backward ---------------------------------------------------------------
 
-// Sum of the per-(record, tile) gradient slots of each record.  A warp takes
+// Sum of the per-(record, tile) gradient slots of each record, turned into the
+// record's mean and conic gradients by its opacity and conic (slot_grads_from_moments).  A warp takes
 // kReduceRecs consecutive records (whose slots are contiguous: a record's
 // first instance follows record order); each of its first lanes loads one
 // record's indices.  Records of
@@ -988,9 +989,9 @@ constexpr int kReduceLanes = 8;
 constexpr int kReduceRecs = 2 * (32 / kReduceLanes); // records per warp: two rounds of the groups
 constexpr uint32_t kReduceBig = 4 * kReduceLanes;    // tiles above which a record takes the whole warp
 static_assert(kReduceLanes < kSlotFloats && kSlotFloats <= 2 * kReduceLanes, "a slot is written by one group");
-__global__ void __launch_bounds__(256) reduce_slots_kernel(const uint32_t *inst_off,
-                                                           const uint32_t *tt, const float4 *rd2, const float *slots,
-                                                           float *rgrad, const DevCounters *ctr)
+__global__ void __launch_bounds__(256) reduce_slots_kernel(const uint32_t *inst_off, const uint32_t *tt,
+                                                           const float4 *rd0, const float4 *rd1, const float4 *rd2,
+                                                           const float *slots, float *rgrad, const DevCounters *ctr)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     constexpr int kGroups = 32 / kReduceLanes;
@@ -1034,6 +1035,8 @@ __global__ void __launch_bounds__(256) reduce_slots_kernel(const uint32_t *inst_
 #pragma unroll
                 for (int x = kReduceLanes / 2; x > 0; x >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], x);
             if (live) {
+                const float4 q0 = rd0[rr], q1 = rd1[rr];
+                slot_grads_from_moments(acc, q0.z, q0.w, q1.x, q1.y);
                 // lane sub writes component sub, and component sub + kReduceLanes where there is one
                 float v = acc[0];
 #pragma unroll
@@ -1065,6 +1068,8 @@ __global__ void __launch_bounds__(256) reduce_slots_kernel(const uint32_t *inst_
 #pragma unroll
                 for (int x = 16; x > 0; x >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], x);
             if (lane < kSlotFloats) {
+                const float4 q0 = rd0[rr], q1 = rd1[rr];
+                slot_grads_from_moments(acc, q0.z, q0.w, q1.x, q1.y);
                 float v = acc[0];
 #pragma unroll
                 for (int j = 1; j < kSlotFloats; j++) v = lane == j ? acc[j] : v;
@@ -1081,8 +1086,9 @@ cudaError_t launch_reduce_slots(gs_workspace *ws, cudaStream_t st)
     if (blocks > 16ll * ws->sm_count) blocks = 16ll * ws->sm_count;
     if (blocks < 1) blocks = 1;
     kt_begin(ws, GS_KT_REDUCE_SLOTS, st);
-    launch_pdl(reduce_slots_kernel, (unsigned)blocks, 256, 0, st, ws->inst_off, ws->tt, ws->rd2, ws->slots,
-                                                         ws->rgrad, ws->ctr);
+    launch_pdl(reduce_slots_kernel, (unsigned)blocks, 256, 0, st, ws->inst_off, ws->tt, (const float4 *)ws->rd0,
+               (const float4 *)ws->rd1, (const float4 *)ws->rd2, (const float *)ws->slots, ws->rgrad,
+               (const DevCounters *)ws->ctr);
     kt_end(ws, GS_KT_REDUCE_SLOTS, st);
     note_launch();
     return cudaGetLastError();
