@@ -46,7 +46,7 @@ struct Layout {
 };
 
 struct Offsets {
-    size_t cand_g, cand_mask, gate_g, gate_mask, rec_first, cgrad, rec_g, rec_cam, rd0, rd1, rd2, rect, tt, inst_off, clampm, rgrad, dkey, tile_cnt, tile_cur;
+    size_t cand_g, cand_mask, gate_g, gate_mask, rec_first, cgrad, rec_g, rec_cam, rd0, rd1, rd2, rect, tt, inst_off, clampm, rgrad, dkey, tile_cnt, tile_cur, tile_last;
     size_t tkey0, tkey1, tval0, tval1, slots, imp_slots, ranges, n_contrib, T_final, imp_w, imp_a, sel_cum, sel_bsum;
     size_t selk0, selk1, selv0, selv1, loss_maps, loss_partial, lb_status, rx_status, red_partial,
         ctr, d_cams, d_adam_step, d_adam_coef;
@@ -88,6 +88,7 @@ Offsets plan(const gs_capacity &c)
     o.ranges = L.take<uint2>(T);
     o.tile_cnt = L.take<uint32_t>(T);
     o.tile_cur = L.take<uint32_t>(T);
+    o.tile_last = L.take<uint32_t>(T);
     o.n_contrib = L.take<uint32_t>(P);
     o.T_final = L.take<float>(P);
     o.imp_w = L.take<float>(R);
@@ -280,6 +281,7 @@ int gs_workspace_create(const gs_capacity *cap, gs_workspace **out)
     ws->dkey = (uint32_t *)(b + o.dkey);
     ws->tile_cnt = (uint32_t *)(b + o.tile_cnt);
     ws->tile_cur = (uint32_t *)(b + o.tile_cur);
+    ws->tile_last = (uint32_t *)(b + o.tile_last);
     ws->tkey[0] = (uint32_t *)(b + o.tkey0); ws->tkey[1] = (uint32_t *)(b + o.tkey1);
     ws->tval[0] = (uint32_t *)(b + o.tval0); ws->tval[1] = (uint32_t *)(b + o.tval1);
     ws->slots = (float *)(b + o.slots);

@@ -38,6 +38,7 @@ struct BinArgs {
     uint32_t *inst_off;            // first instance of each record (record order)
     uint32_t *tile_cnt;            // [tiles] instances per tile (zeroed before the count)
     uint32_t *tile_cur;            // [tiles] fill cursor of each tile
+    uint32_t *tile_last;           // [tiles] the forward's largest n_contrib per tile: zeroed here
     uint2 *ranges;                 // [tiles] [start, end) of each tile's list
     uint32_t *skey, *sval;         // [instances] scattered depth keys and records; sval ends sorted
     uint32_t *xkey, *xval;         // [instances] scratch of the merges of long lists
@@ -138,7 +139,8 @@ __global__ void __launch_bounds__(kBinThreads) bin_count_kernel(BinArgs a, const
 }
 
 // 2. Tile scan: exclusive scan of the tile counts; ranges clamped to the
-// instance capacity (an overflow is already an error), cursors at the start.
+// instance capacity (an overflow is already an error), cursors at the start,
+// the forward's per-tile maxima of n_contrib cleared.
 __global__ void __launch_bounds__(256) tile_scan_kernel(BinArgs a)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
@@ -171,6 +173,7 @@ __global__ void __launch_bounds__(256) tile_scan_kernel(BinArgs a)
         const unsigned long long e = off + cnt[q];
         a.ranges[t0 + q] = make_uint2((uint32_t)min(off, a.max_instances), (uint32_t)min(e, a.max_instances));
         a.tile_cur[t0 + q] = (uint32_t)min(off, a.max_instances);
+        a.tile_last[t0 + q] = 0u;
         off = e;
     }
 }
@@ -371,7 +374,7 @@ cudaError_t launch_bin(gs_workspace *ws, cudaStream_t st)
     if ((e = cudaMemsetAsync(ws->tile_cnt, 0, (size_t)tiles * sizeof(uint32_t), st)) != cudaSuccess) return e;
     BinArgs a;
     a.tt = ws->tt; a.rect = ws->rect; a.rec_cam = ws->rec_cam; a.dkey = ws->dkey;
-    a.inst_off = ws->inst_off; a.tile_cnt = ws->tile_cnt; a.tile_cur = ws->tile_cur; a.ranges = ws->ranges;
+    a.inst_off = ws->inst_off; a.tile_cnt = ws->tile_cnt; a.tile_cur = ws->tile_cur; a.tile_last = ws->tile_last; a.ranges = ws->ranges;
     a.skey = ws->tkey[0]; a.sval = ws->tval[0]; a.xkey = ws->tkey[1]; a.xval = ws->tval[1];
     a.lb_count = ws->lb_status; a.lb_tiles = ws->lb_status + cblocks + 1;
     a.ctr = ws->ctr; a.max_instances = (unsigned long long)ws->cap.max_instances; a.total_tiles = tiles;

@@ -360,6 +360,7 @@ struct gs_workspace {
     float *rgrad;        // [R][9] per-record summed gradients of u v A B C o r g b
     uint32_t *dkey;      // [R] FP32 bits of each record's camera depth
     uint32_t *tile_cnt, *tile_cur; // [T] the binning's tile counts and fill cursors
+    uint32_t *tile_last;           // [T] largest n_contrib of each tile's pixels (zeroed by the binning, set by the forward)
     // per instance
     uint32_t *tkey[2], *tval[2];
     float *slots;        // [I][9] adjoint slots (training workspaces only)

@@ -165,10 +165,11 @@ template <int TW, int TH> struct SquareShape {
     static constexpr int wx = TW / 8;
     static constexpr int warps = (TW / 8) * (TH / 8);
     static constexpr int threads = 32 * warps;
-    // the adjoint's register budget: at least seven resident blocks of 128 threads per
-    // SM (64 registers, so eight fit); on the 16 x 16 tile 10 % faster than the
-    // compiler's own choice of 86 registers and five blocks
-    static constexpr int bwd_min_blocks = 896 / threads;
+    // the adjoint's register budget: at least six resident blocks of 128 threads per
+    // SM, which ptxas meets with 64 registers (so eight fit); on the 16 x 16 tile
+    // 10-15 % faster than both its own choice (86 registers, five blocks) and tighter
+    // budgets (56-57 registers)
+    static constexpr int bwd_min_blocks = 768 / threads;
     // the importance walk's: eight blocks of 128 threads (64 registers; the fused walk
     // with the training image measured 8 % faster than with the compiler's 60)
     static constexpr int imp_min_blocks = 1024 / threads;
@@ -229,7 +230,8 @@ __global__ void __launch_bounds__(SquareShape<TW, TH>::threads)
     render_fwd_kernel(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
                       const float4 *__restrict__ rd0, const float4 *__restrict__ rd1, const float4 *__restrict__ rd2,
                       const CamTable *__restrict__ ctp, RenderConsts rc, float *__restrict__ rgb_out,
-                      float *__restrict__ T_out, float *__restrict__ T_ws, uint32_t *__restrict__ n_contrib)
+                      float *__restrict__ T_out, float *__restrict__ T_ws, uint32_t *__restrict__ n_contrib,
+                      uint32_t *__restrict__ tile_last)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
     constexpr int kWarps = SquareShape<TW, TH>::warps;
@@ -306,13 +308,16 @@ __global__ void __launch_bounds__(SquareShape<TW, TH>::threads)
         T_ws[gp] = Tk;
         n_contrib[gp] = h ? last1 : last0;
     }
+    // the tile's largest n_contrib, where the adjoint's reverse walk starts
+    const unsigned wl = __reduce_max_sync(0xffffffffu, max(last0, last1));
+    if (lane == 0 && wl != 0u) atomicMax(&tile_last[blockIdx.x], wl);
 }
 
 template <int TW, int TH> static void fwd_launch(gs_workspace *ws, cudaStream_t st, float *rgb, float *T_out)
 {
     launch_pdl(render_fwd_kernel<TW, TH>, ws->cams.total_tiles, SquareShape<TW, TH>::threads, 0, st,
         ws->ranges, ws->tval[ws->tile_buf], ws->rd0, ws->rd1, ws->rd2, ws->d_cams, ws->rc, rgb, T_out, ws->T_final,
-        ws->n_contrib);
+        ws->n_contrib, ws->tile_last);
 }
 
 cudaError_t launch_render_fwd(gs_workspace *ws, cudaStream_t st, float *rgb, float *T_out)
@@ -361,6 +366,7 @@ struct BwdRenderArgs {
     const uint2 *rect;
     const float *T_final;
     const uint32_t *n_contrib;
+    const uint32_t *tile_last; // largest n_contrib of each tile (the forward's)
     const float *dL_drgb;
     float *slots;
     DevCounters *ctr; // fragments += sum of the tile's n_contrib; composited += composited pairs
@@ -379,7 +385,6 @@ __global__ void __launch_bounds__(SquareShape<TW, TH>::threads, SquareShape<TW, 
     __shared__ float s_part[kBwdBufs][kWarps][kBwdBatch][kSlotFloats];
     __shared__ unsigned s_mask[kBwdBufs][kWarps]; // entries of the batch each warp visited
     __shared__ int s_arrive[kBwdBufs], s_done[kBwdBufs];
-    __shared__ int s_max;
     const CamTable &ct = *ctp;
     if ((int)blockIdx.x >= ct.total_tiles) return;
     const int tile = blockIdx.x;
@@ -389,6 +394,11 @@ __global__ void __launch_bounds__(SquareShape<TW, TH>::threads, SquareShape<TW, 
     const float ox = (float)(tx * TW), oy = (float)(ty * TH);
     const uint2 rg = a.ranges[blockIdx.x];
     const int start = (int)rg.x, end = (int)rg.y;
+    // the reverse walk starts after the tile's last contribution (the forward's
+    // largest n_contrib); entries behind it carry zero gradient
+    const int last = start + min((int)a.tile_last[blockIdx.x], end - start);
+    if (threadIdx.x < kBwdBufs) { s_arrive[threadIdx.x] = 0; s_done[threadIdx.x] = 0; }
+    __syncthreads(); // the only block barrier: the arrival counters are set
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool red_own = red9_owner(lane);
     const int red_q = red9_index(lane);
@@ -428,18 +438,6 @@ __global__ void __launch_bounds__(SquareShape<TW, TH>::threads, SquareShape<TW, 
     {
         const unsigned f = __reduce_add_sync(0xffffffffu, (unsigned)(nc0 + nc1));
         if (lane == 0 && f) atomicAdd(&a.ctr->fragments, (unsigned long long)f);
-    }
-    if (threadIdx.x == 0) s_max = 0;
-    if (threadIdx.x < kBwdBufs) { s_arrive[threadIdx.x] = 0; s_done[threadIdx.x] = 0; }
-    __syncthreads();
-    if (lane == 0) atomicMax(&s_max, wmax);
-    __syncthreads();
-    const int last = start + s_max;
-    // entries after the last contribution of every pixel carry zero gradient
-    for (int s = last + threadIdx.x; s < end; s += kRT) {
-        float *dst = a.slots + slot_of(a.inst_off, a.rect, a.vals[s], tx, ty) * kSlotFloats;
-#pragma unroll
-        for (int k = 0; k < kSlotFloats; k++) dst[k] = 0.f;
     }
     int ncomp = 0;
     int b = 0;
@@ -572,6 +570,12 @@ __global__ void __launch_bounds__(SquareShape<TW, TH>::threads, SquareShape<TW, 
             }
         }
     }
+    // entries after the tile's last contribution carry zero gradient
+    for (int s = last + threadIdx.x; s < end; s += kRT) {
+        float *dst = a.slots + slot_of(a.inst_off, a.rect, a.vals[s], tx, ty) * kSlotFloats;
+#pragma unroll
+        for (int k = 0; k < kSlotFloats; k++) dst[k] = 0.f;
+    }
     const unsigned f = __reduce_add_sync(0xffffffffu, (unsigned)ncomp);
     if (lane == 0 && f) atomicAdd(&a.ctr->composited, (unsigned long long)f);
 }
@@ -582,6 +586,7 @@ cudaError_t launch_render_bwd(gs_workspace *ws, cudaStream_t st, const float *dL
     BwdRenderArgs a;
     a.ranges = ws->ranges; a.vals = ws->tval[ws->tile_buf]; a.rd0 = ws->rd0; a.rd1 = ws->rd1; a.rd2 = ws->rd2;
     a.inst_off = ws->inst_off; a.rect = ws->rect; a.T_final = ws->T_final; a.n_contrib = ws->n_contrib;
+    a.tile_last = ws->tile_last;
     a.dL_drgb = dL_drgb; a.slots = ws->slots; a.ctr = ws->ctr;
     const unsigned grid = (unsigned)ws->cams.total_tiles;
     kt_begin(ws, GS_KT_RENDER_BWD, st);
@@ -626,6 +631,7 @@ struct ImpArgs {
     // FWD only
     float *rgb_out, *T_out, *T_ws;
     uint32_t *n_contrib;
+    uint32_t *tile_last;   // the tile's largest n_contrib (atomic max; zeroed by the binning)
 };
 
 template <int TW, int TH, bool FWD>
@@ -786,6 +792,8 @@ __global__ void __launch_bounds__(SquareShape<TW, TH>::threads, SquareShape<TW, 
             a.T_ws[gp] = Tk;
             a.n_contrib[gp] = h ? last1 : last0;
         }
+        const unsigned wl = __reduce_max_sync(0xffffffffu, max(last0, last1));
+        if (lane == 0 && wl != 0u) atomicMax(&a.tile_last[blockIdx.x], wl);
     }
 }
 
@@ -827,7 +835,7 @@ cudaError_t launch_render_fwd_importance(gs_workspace *ws, cudaStream_t st, floa
 {
     if (ws->cams.total_tiles == 0) return cudaSuccess;
     ImpArgs a = importance_args(ws);
-    a.rgb_out = rgb; a.T_out = T_out; a.T_ws = ws->T_final; a.n_contrib = ws->n_contrib;
+    a.rgb_out = rgb; a.T_out = T_out; a.T_ws = ws->T_final; a.n_contrib = ws->n_contrib; a.tile_last = ws->tile_last;
     kt_begin(ws, GS_KT_RENDER_FWD, st);
     cudaError_t e = importance_launch<true>(ws, st, a);
     if (e != cudaSuccess) return e;
