@@ -595,6 +595,79 @@ def cpu_baseline(g, cam, target):
             "seconds_per_step": total, "parts_s": {k: round(v, 3) for k, v in parts.items()}}
 
 
+# The small scene (10k Gaussians in front of one 256x256 camera): the oracle's
+# whole step in full, at one thread and on every host core.
+SMALL_N, SMALL_W, SMALL_F = 10_000, 256, 300.0
+
+
+def _small_inputs():
+    from paper_2605_13794_gb300 import synth
+    g = synth.plain_scene(SMALL_N, seed=1)
+    cam = synth.plain_camera(SMALL_W, SMALL_W, SMALL_F)
+    target = synth.noise_target(SMALL_W, SMALL_W, seed=2)
+    return g, cam, target
+
+
+def _small_step(inputs):
+    """One full oracle step of the small scene: forward, loss, backward, the
+    importance sweep and its visible set; returns its seconds."""
+    import oracle as O
+    g, cam, target = inputs
+    P = O.Params()
+    g64 = O.gaussians64(g)
+    t0 = time.perf_counter()
+    fwd = O.forward_view(g64, cam, P)
+    _, dL = O.photometric_loss(fwd["image"][None], target[None], LAMBDA)
+    O.backward_view(g64, fwd, cam, P, dL[0])
+    imp = O.forward_view(g64, cam, P)
+    O.visible_top_mass(imp["w"])
+    return time.perf_counter() - t0
+
+
+_small_barrier = None
+
+
+def _small_init(barrier):
+    global _small_barrier
+    _small_barrier = barrier
+
+
+def _small_worker(steps):
+    """A spawned process: inputs built before the common start, then `steps`
+    full steps; returns (start, end) wall times."""
+    inputs = _small_inputs()
+    _small_step(inputs)  # warm-up: the oracle library loaded and its pages touched
+    _small_barrier.wait()
+    t0 = time.time()
+    for _ in range(steps):
+        _small_step(inputs)
+    return t0, time.time()
+
+
+def cpu_small_scene(steps=3):
+    """The oracle on the small scene at one thread (a full step, best of
+    `steps`) and on all host cores (one spawned process per core, each running
+    `steps` full steps at once; throughput over the wall time from the common
+    start to the last finish)."""
+    import multiprocessing as mp
+    inputs = _small_inputs()
+    _small_step(inputs)
+    one = min(_small_step(inputs) for _ in range(steps))
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")  # never fork a process that has used the GPU
+    barrier = ctx.Barrier(cores)
+    with ctx.Pool(cores, initializer=_small_init, initargs=(barrier,)) as pool:
+        spans = pool.map(_small_worker, [steps] * cores)
+    wall = max(e for _, e in spans) - min(t for t, _ in spans)
+    pix = SMALL_W * SMALL_W
+    return {"workload": f"{SMALL_N // 1000}k Gaussians, {SMALL_W}x{SMALL_W}, full step (forward, L1 + D-SSIM, "
+                        "backward, importance sweep and visible set)",
+            "unit": "Mpix/s", "kind": "oracle",
+            "one_thread": {"value": pix / one / 1e6, "seconds_per_step": one, "cores": 1},
+            "all_cores": {"value": cores * steps * pix / wall / 1e6, "cores": cores,
+                          "what": f"{cores} spawned processes, {steps} steps each, at once"}}
+
+
 # ---- main -------------------------------------------------------------------------------
 
 def dist_backend():
@@ -965,6 +1038,7 @@ def main():
             "clocks": clocks}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, cam, target)
+        line["cpu_small_scene"] = cpu_small_scene()
     if rank == 0:
         print(json.dumps(line), flush=True)
     # the graphs name the workspace's buffers and events: release them first

@@ -30,3 +30,15 @@ def test_reference_arm_prints_one_line_with_the_keys():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+@pytest.mark.timeout(300)
+def test_small_scene_oracle_on_one_thread_and_all_cores():
+    """The small-scene oracle timing of the default line: a full step at one
+    thread and as spawned processes on every host core."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.cpu_small_scene(steps=1)
+    assert r["kind"] == "oracle" and r["unit"] == "Mpix/s"
+    assert r["one_thread"]["cores"] == 1 and r["one_thread"]["value"] > 0
+    assert r["all_cores"]["cores"] == (os.cpu_count() or 1) and r["all_cores"]["value"] > 0
