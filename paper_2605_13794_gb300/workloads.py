@@ -112,6 +112,7 @@ def train_batch_workload(n: int = 20_000_000, views: int = 8, width: int = 1600,
     torch.cuda.synchronize()
     eager_ms = e0.elapsed_time(e1) / steps
     g0, g1 = _events()
+    torch.cuda.nvtx.range_push("timed_region")  # lets a profiler select the replayed steps
     g0.record()
     for k in range(1 + warmup, 1 + warmup + steps):
         cm, tg = batch(k)
@@ -120,6 +121,7 @@ def train_batch_workload(n: int = 20_000_000, views: int = 8, width: int = 1600,
         losses_g.append(graph.loss.clone())
     graph.flush()
     g1.record()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     graph_ms = g0.elapsed_time(g1) / steps
     eager.ws.sync_status()
