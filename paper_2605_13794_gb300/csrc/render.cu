@@ -342,15 +342,17 @@ cudaError_t launch_render_fwd(gs_workspace *ws, cudaStream_t st, float *rgb, flo
 //
 // Each warp owns an 8 x 8 pixel square of the tile -- lane l the horizontal
 // pixel pair (2 (l % 4), l / 4) of it, packed as FP32x2 -- and walks the
-// tile's list back to front on its own, from the last entry any of its pixels
-// composited, recovering T by T / (1 - alpha) from the final transmittance.
-// It stages each batch of 32 entries itself (one per lane), so no block-wide
-// barrier holds it while another warp of the tile has more to do; the staging
-// lane also tests its entry's alpha footprint against the warp's square, and one
-// ballot gives the batch's entries the warp must visit.  Per visited entry the
-// warp's gradient is one warp reduction; the warps' partials of a batch are
-// summed in warp order by the warp that finishes that batch last
-// (shared-memory arrival counters) and written to the entries' slots.  A warp may run up to
+// tile's list back to front on its own, in batches that start at the tile's
+// last contribution (the forward's largest n_contrib of the tile), visiting
+// only entries in front of its own pixels' last contribution and recovering T
+// by T / (1 - alpha) from the final transmittance.  It stages each batch of 32
+// entries itself (one per lane), so no block-wide barrier holds it while
+// another warp of the tile has more to do; the staging lane also tests its
+// entry's alpha footprint against the warp's square, and one ballot gives the
+// batch's entries the warp must visit.  Per visited entry the warp's nine slot
+// values are one warp reduction; the warps' partials of a batch are summed in
+// warp order by the warp that finishes that batch last (shared-memory arrival
+// counters) and written to the entries' slots.  A warp may run up to
 // kBwdBufs - 1 batches ahead of the slowest warp of its tile; its wait for a
 // partial buffer is bounded.
 
