@@ -430,6 +430,28 @@ def test_backward_parity(seed):
     assert_gaussian_grads_close(gg, og)
 
 
+def test_backward_parity_on_deep_lists():
+    """Deep tile lists: 40k faint Gaussians (opacity about 0.05) packed into the
+    middle of a 96x80 view, so each pixel composites a couple of hundred
+    entries before its walk stops.  The adjoint's slots then sum moments over
+    many composited pairs per entry and the reverse walk recovers T through
+    hundreds of divisions; the gradients stay within the parity rules."""
+    g = synth.plain_scene(40000, seed=27)
+    rng = np.random.default_rng(28)
+    g.mean[:, :2] *= np.float32(0.5)
+    g.opacity_logit[:] = (np.float32(-3.0) + np.float32(0.5) * rng.standard_normal(g.n)).astype(np.float32)
+    cam = synth.plain_camera(96, 80, 160.0)
+    P = O.Params()
+    run = ViewRun(g, [cam], P)
+    g64 = O.gaussians64(g)
+    fwd = _compare_view(run, 0, g64, cam, P)
+    assert run.n_contrib.mean() > 100  # deep lists indeed
+    dL = rng.standard_normal((3, cam.height, cam.width))
+    gg = _backward(run, dL)
+    og = O.grads_per_gaussian(O.backward_view(g64, fwd, cam, P, dL))
+    assert_gaussian_grads_close(gg, og)
+
+
 def test_backward_fragment_counts_and_kernel_timing():
     """The backward's work counters: fragments is the sum of n_contrib (integer,
     exact); composited is the number of composited (pixel, Gaussian) pairs, the
