@@ -432,10 +432,11 @@ def test_backward_parity(seed):
 
 def test_backward_parity_on_deep_lists():
     """Deep tile lists: 40k faint Gaussians (opacity about 0.05) packed into the
-    middle of a 96x80 view, so each pixel composites a couple of hundred
-    entries before its walk stops.  The adjoint's slots then sum moments over
-    many composited pairs per entry and the reverse walk recovers T through
-    hundreds of divisions; the gradients stay within the parity rules."""
+    middle of a 96x80 view, so each pixel's walk passes about two thousand
+    entries (n_contrib) and composites many of them.  The adjoint's slots then
+    sum moments over many composited pairs per entry and the reverse walk
+    recovers T through long chains of divisions; the gradients stay within the
+    parity rules."""
     g = synth.plain_scene(40000, seed=27)
     rng = np.random.default_rng(28)
     g.mean[:, :2] *= np.float32(0.5)
