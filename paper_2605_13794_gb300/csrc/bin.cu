@@ -374,7 +374,8 @@ cudaError_t launch_bin(gs_workspace *ws, cudaStream_t st)
     if ((e = cudaMemsetAsync(ws->tile_cnt, 0, (size_t)tiles * sizeof(uint32_t), st)) != cudaSuccess) return e;
     BinArgs a;
     a.tt = ws->tt; a.rect = ws->rect; a.rec_cam = ws->rec_cam; a.dkey = ws->dkey;
-    a.inst_off = ws->inst_off; a.tile_cnt = ws->tile_cnt; a.tile_cur = ws->tile_cur; a.tile_last = ws->tile_last; a.ranges = ws->ranges;
+    a.inst_off = ws->inst_off; a.tile_cnt = ws->tile_cnt; a.tile_cur = ws->tile_cur; a.ranges = ws->ranges;
+    a.tile_last = ws->tile_last;
     a.skey = ws->tkey[0]; a.sval = ws->tval[0]; a.xkey = ws->tkey[1]; a.xval = ws->tval[1];
     a.lb_count = ws->lb_status; a.lb_tiles = ws->lb_status + cblocks + 1;
     a.ctr = ws->ctr; a.max_instances = (unsigned long long)ws->cap.max_instances; a.total_tiles = tiles;

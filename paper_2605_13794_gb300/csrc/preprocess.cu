@@ -973,10 +973,10 @@ cudaError_t launch_preprocess(gs_workspace *ws, cudaStream_t st, const uint32_t 
 // ---- backward ---------------------------------------------------------------
 
 // Sum of the per-(record, tile) gradient slots of each record, turned into the
-// record's mean and conic gradients by its opacity and conic (slot_grads_from_moments).  A warp takes
-// kReduceRecs consecutive records (whose slots are contiguous: a record's
-// first instance follows record order); each of its first lanes loads one
-// record's indices.  Records of
+// record's mean and conic gradients by its opacity and conic
+// (slot_grads_from_moments).  A warp takes kReduceRecs consecutive records
+// (whose slots are contiguous: a record's first instance follows record
+// order); each of its first lanes loads one record's indices.  Records of
 // at most kReduceBig tiles are added up by groups of kReduceLanes lanes, 32 /
 // kReduceLanes records at a time (a group's lanes read the record's slots
 // strided by kReduceLanes, then a fixed shuffle tree adds the lanes), so the
