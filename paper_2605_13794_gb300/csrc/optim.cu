@@ -173,12 +173,29 @@ __global__ void __launch_bounds__(256, 4) ssim_fwd_kernel(const float *img, cons
     }
 }
 
+// The loss from the views' fixed-point sums (SSIM, L1) of ssim_fwd_kernel,
+// zeroed before it in the same call.
+__device__ __forceinline__ float loss_from_sums(const unsigned long long *acc, int batch, int H, int W, float lambda)
+{
+    const double npx = 3.0 * H * W, unit = 1.0 / 16777216.0;
+    double loss = 0.0;
+    for (int b = 0; b < batch; b++) {
+        const double ssim = (double)(long long)acc[2 * b] * unit, l1 = (double)(long long)acc[2 * b + 1] * unit;
+        loss += ((1.0 - lambda) * l1 / npx + lambda * (1.0 - ssim / npx)) / batch;
+    }
+    return (float)loss;
+}
+
 // s_l1 = (1 - lambda) / (3 H W batch), s_ssim = lambda / (3 H W batch): the
-// weights of the two mean terms of the batch's loss.
+// weights of the two mean terms of the batch's loss.  The first thread also
+// writes the loss: the forward's sums are complete once this kernel runs.
 __global__ void __launch_bounds__(256, 4) ssim_bwd_kernel(const float *img, const float *tgt, int H, int W, Win win,
-                                                       const float *F, float s_l1, float s_ssim, float *dL)
+                                                       const float *F, float s_l1, float s_ssim, float *dL,
+                                                       const unsigned long long *acc, int batch, float lambda,
+                                                       float *loss_out)
 {
     griddep_wait(); // programmatic dependent launch: the previous kernel is complete
+    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x) == 0) *loss_out = loss_from_sums(acc, batch, H, W, lambda);
     __shared__ float2 sf01[kLTH][kLTP];
     __shared__ float sf2[kLTH][kLTP];
     __shared__ float2 hb01[kLTH][kLT + 1];
@@ -275,21 +292,6 @@ __global__ void __launch_bounds__(256, 4) ssim_bwd_kernel(const float *img, cons
     }
 }
 
-// The loss from the views' fixed-point sums (SSIM, L1), zeroed before the
-// SSIM kernel of the same call.
-__global__ void loss_finalize_kernel(const unsigned long long *acc, int batch, int H, int W, float lambda, float *loss_out)
-{
-    griddep_wait(); // programmatic dependent launch: the previous kernel is complete
-    if (threadIdx.x != 0) return;
-    const double npx = 3.0 * H * W, unit = 1.0 / 16777216.0;
-    double loss = 0.0;
-    for (int b = 0; b < batch; b++) {
-        const double ssim = (double)(long long)acc[2 * b] * unit, l1 = (double)(long long)acc[2 * b + 1] * unit;
-        loss += ((1.0 - lambda) * l1 / npx + lambda * (1.0 - ssim / npx)) / batch;
-    }
-    *loss_out = (float)loss;
-}
-
 cudaError_t launch_loss(gs_workspace *ws, cudaStream_t st, const float *img, const float *tgt, int B, int H, int W,
                         float lambda, float *loss_out, float *dL)
 {
@@ -309,10 +311,8 @@ cudaError_t launch_loss(gs_workspace *ws, cudaStream_t st, const float *img, con
     kt_begin(ws, GS_KT_SSIM_BWD, st);
     const double wsum = 3.0 * H * W * B; // SSIM and L1 are means over channels, pixels and views
     launch_pdl(ssim_bwd_kernel, grid, 256, 0, st, img, tgt, H, W, win, maps, (float)((1.0 - lambda) / wsum),
-               (float)(lambda / wsum), dL);
+               (float)(lambda / wsum), dL, (const unsigned long long *)acc, B, lambda, loss_out);
     kt_end(ws, GS_KT_SSIM_BWD, st);
-    note_launch();
-    launch_pdl(loss_finalize_kernel, 1, 32, 0, st, acc, B, H, W, lambda, loss_out);
     note_launch();
     return cudaGetLastError();
 }
